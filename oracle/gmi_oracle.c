@@ -1,0 +1,251 @@
+/*
+ * FP64 brute-force oracle for Gaussian-mixture interpolation on a
+ * non-uniform grid (Skorokhodov, "Interpolating Points on a Non-Uniform
+ * Grid using a Mixture of Gaussians", arXiv 2012.13257).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may call, link or
+ * load this file; it is used by the tests, by the smoke check and by the
+ * benchmark's CPU-baseline leg.  It shares no code with the CUDA library.
+ *
+ * What is computed (paper section 2):
+ *   Every known point i is an isotropic 2D normal N(mu_i, sigma^2 I) with
+ *   mu_i = (x_i, y_i) and a colour c_i in R^C (section 1 introduces
+ *   f: p -> c; section 2 fixes the diagonal covariance sigma^2 I with one
+ *   shared sigma).  The colour at a query pixel q is the expectation
+ *       c(q) = sum_i c_i N(q | mu_i, sigma^2 I) / Z_q            (Eq. 1)
+ *       Z_q  = sum_i N(q | mu_i, sigma^2 I)                       (Eq. 2)
+ *   and every channel is interpolated independently with the same weights
+ *   (end of section 2).
+ *
+ * Readings of what the paper leaves open:
+ *   - Query grid: the H x W output raster (section 1); pixel (i, j) (row i,
+ *     column j) is queried at q = (j + 0.5, i + 0.5) in output-pixel units;
+ *     x runs along W, y along H.
+ *   - EXACT mode (default): the full sums of Eq. 1 and Eq. 2.  Because sigma
+ *     is shared, the Gaussian normaliser 1/(2 pi sigma^2) cancels in the
+ *     ratio, and so does any common factor exp(m/(2 sigma^2)); with
+ *     m = min_i |q - mu_i|^2 the evaluation below is Eq. 1 written with
+ *     weights w_i = exp(-(d_i^2 - m)/(2 sigma^2)) in [0, 1], which cannot
+ *     underflow to 0/0 (the unshifted weights do, even in FP64, once
+ *     d^2/(2 sigma^2) > ~745).
+ *   - TRUNCATED mode: the paper says only points "close enough" to the query
+ *     are considered but gives no radius.  This mode is the literal reading
+ *     with radius k*sigma: sums over d_i <= k sigma of the unshifted weights
+ *     exp(-d_i^2/(2 sigma^2)); a pixel with no point inside the disc gets
+ *     colour 0 and Z = 0.
+ *   - N = 0: colour 0 and Z = 0 everywhere.
+ *   - Backward (the paper has CUDA forward and backward kernels but prints no
+ *     formulas; the derivation is the chain rule applied to Eq. 1):
+ *       dc_c(q)/dc_{i,c}  = w_i / Z
+ *       dc_c(q)/dmu_i     = (w_i / Z) (c_{i,c} - c_c(q)) (q - mu_i) / sigma^2
+ *       dc_c(q)/dsigma    = sum_i (w_i / Z) (c_{i,c} - c_c(q)) d_i^2 / sigma^3
+ *     The shift m and the truncation boundary carry no derivative (the shift
+ *     cancels exactly; the boundary is a measure-zero set).
+ *
+ * All arithmetic is double precision on the float32 inputs; exp() is libm.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORACLE_EXACT 0
+#define ORACLE_TRUNCATED 1
+
+/* Pixel index -> query position (section 1: the output is an H x W raster;
+ * the pixel-centre convention is this oracle's reading). */
+static void pixel_centre(int64_t p, int64_t W, double* qx, double* qy) {
+    int64_t i = p / W, j = p % W;
+    *qx = (double)j + 0.5;
+    *qy = (double)i + 0.5;
+}
+
+static double sqdist(const float* points, int64_t i, double qx, double qy) {
+    double dx = qx - (double)points[2 * i];
+    double dy = qy - (double)points[2 * i + 1];
+    return dx * dx + dy * dy;
+}
+
+int oracle_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/*
+ * Forward pass, Eq. 1 and Eq. 2, at a list of pixels.
+ *   points [N,2] float32 (x, y); values [N,C] float32
+ *   pix    [n_pix] row-major pixel indices, or NULL for all H*W pixels
+ * Outputs (each may be NULL), indexed by position in the pixel list:
+ *   out     [n_pix, C]  c(q)
+ *   den     [n_pix]     exact: Z' = sum_i exp(-(d_i^2 - m)/(2 sigma^2)) (>= 1)
+ *                       truncated: Z = sum_{d_i <= k sigma} exp(-d_i^2/(2 sigma^2))
+ *   shift   [n_pix]     exact: m = min_i d_i^2 ; truncated: 0
+ *   skipped [n_pix]     exact: share of Z' carried by points with
+ *                       d_i^2 > m + k^2 sigma^2 (what a radius rule drops);
+ *                       truncated: share of the in-disc weight carried by
+ *                       points whose inclusion is decided within rounding
+ *                       (|d^2 - k^2 sigma^2| <= 1e-5 k^2 sigma^2)
+ *   pairs   [n_pix]     exact: #{i : d_i^2 <= m + k^2 sigma^2};
+ *                       truncated: #{i : d_i^2 <= k^2 sigma^2}
+ * Returns 0, or -1 on invalid arguments.
+ */
+int oracle_forward(const float* points, const float* values, int64_t N, int C,
+                   int64_t H, int64_t W, double sigma, int mode, double k,
+                   const int64_t* pix, int64_t n_pix,
+                   double* out, double* den, double* shift, double* skipped,
+                   int64_t* pairs) {
+    if (N < 0 || C < 1 || H < 1 || W < 1 || !(sigma > 0) || !(k > 0)) return -1;
+    if (mode != ORACLE_EXACT && mode != ORACLE_TRUNCATED) return -1;
+    if (pix == NULL) n_pix = H * W;
+    const double inv2s2 = 1.0 / (2.0 * sigma * sigma);
+    const double r2 = k * k * sigma * sigma;
+
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t t = 0; t < n_pix; ++t) {
+        int64_t p = pix ? pix[t] : t;
+        double qx, qy;
+        pixel_centre(p, W, &qx, &qy);
+        double num[8];
+        double* acc = C <= 8 ? num : (double*)calloc((size_t)C, sizeof(double));
+        for (int c = 0; c < C; ++c) acc[c] = 0.0;
+        double z = 0.0, m = 0.0, skip = 0.0;
+        int64_t cnt = 0;
+        if (N > 0 && mode == ORACLE_EXACT) {
+            m = INFINITY;
+            for (int64_t i = 0; i < N; ++i) {
+                double d2 = sqdist(points, i, qx, qy);
+                if (d2 < m) m = d2;
+            }
+            for (int64_t i = 0; i < N; ++i) {
+                double d2 = sqdist(points, i, qx, qy);
+                double w = exp(-(d2 - m) * inv2s2);
+                z += w;
+                for (int c = 0; c < C; ++c) acc[c] += w * (double)values[i * C + c];
+                if (d2 <= m + r2) ++cnt; else skip += w;
+            }
+            for (int c = 0; c < C; ++c) acc[c] /= z;
+            skip /= z;
+        } else if (N > 0) {
+            double amb = 0.0;
+            for (int64_t i = 0; i < N; ++i) {
+                double d2 = sqdist(points, i, qx, qy);
+                if (fabs(d2 - r2) <= 1e-5 * r2) amb += exp(-d2 * inv2s2);
+                if (d2 > r2) continue;
+                double w = exp(-d2 * inv2s2);
+                z += w;
+                ++cnt;
+                for (int c = 0; c < C; ++c) acc[c] += w * (double)values[i * C + c];
+            }
+            if (z > 0) {
+                for (int c = 0; c < C; ++c) acc[c] /= z;
+                skip = amb / z;
+            } else {
+                for (int c = 0; c < C; ++c) acc[c] = 0.0;
+                skip = amb > 0 ? 1.0 : 0.0;
+            }
+        }
+        if (out)
+            for (int c = 0; c < C; ++c) out[t * C + c] = acc[c];
+        if (den) den[t] = z;
+        if (shift) shift[t] = m;
+        if (skipped) skipped[t] = skip;
+        if (pairs) pairs[t] = cnt;
+        if (acc != num) free(acc);
+    }
+    return 0;
+}
+
+/*
+ * Backward pass: gradients of L = sum_q sum_c g_c(q) c_c(q) with respect to
+ * the point positions, the point values and sigma (chain rule on Eq. 1; see
+ * the header).  grad [H,W,C] float32 is the upstream gradient dL/dc.
+ * Outputs (each may be NULL): gpoints [N,2], gvalues [N,C], gsigma [1].
+ * O(N*H*W); meant for small cases.
+ */
+int oracle_backward(const float* points, const float* values, int64_t N, int C,
+                    int64_t H, int64_t W, double sigma, int mode, double k,
+                    const float* grad, double* gpoints, double* gvalues,
+                    double* gsigma) {
+    if (N < 0 || C < 1 || C > 8 || H < 1 || W < 1 || !(sigma > 0) || !(k > 0)) return -1;
+    if (mode != ORACLE_EXACT && mode != ORACLE_TRUNCATED) return -1;
+    const double inv2s2 = 1.0 / (2.0 * sigma * sigma);
+    const double s2 = sigma * sigma, s3 = s2 * sigma;
+    const double r2 = k * k * sigma * sigma;
+    const int64_t P = H * W;
+    int nt = oracle_num_threads();
+    size_t per = (size_t)N * (size_t)(2 + C) + 1;
+    double* part = (double*)calloc(per * (size_t)nt, sizeof(double));
+    double* wbuf_all = (double*)malloc(sizeof(double) * (size_t)(N > 0 ? N : 1) * (size_t)nt);
+    if (!part || !wbuf_all) { free(part); free(wbuf_all); return -2; }
+
+#pragma omp parallel
+    {
+        int tid = 0;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+#endif
+        double* acc = part + per * (size_t)tid;   /* [N*2 | N*C | 1] */
+        double* w = wbuf_all + (size_t)(N > 0 ? N : 1) * (size_t)tid;
+        double chat[8], G[8];
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t p = 0; p < P; ++p) {
+            if (N == 0) continue;
+            double qx, qy;
+            pixel_centre(p, W, &qx, &qy);
+            double m = 0.0;
+            if (mode == ORACLE_EXACT) {
+                m = INFINITY;
+                for (int64_t i = 0; i < N; ++i) {
+                    double d2 = sqdist(points, i, qx, qy);
+                    if (d2 < m) m = d2;
+                }
+            }
+            double z = 0.0;
+            for (int c = 0; c < C; ++c) chat[c] = 0.0;
+            for (int64_t i = 0; i < N; ++i) {
+                double d2 = sqdist(points, i, qx, qy);
+                double wi = (mode == ORACLE_TRUNCATED && d2 > r2) ? 0.0 : exp(-(d2 - m) * inv2s2);
+                w[i] = wi;
+                z += wi;
+                for (int c = 0; c < C; ++c) chat[c] += wi * (double)values[i * C + c];
+            }
+            if (!(z > 0)) continue;  /* truncated pixel with no point: constant 0 */
+            for (int c = 0; c < C; ++c) {
+                chat[c] /= z;
+                G[c] = (double)grad[p * C + c] / z;
+            }
+            for (int64_t i = 0; i < N; ++i) {
+                if (w[i] == 0.0) continue;
+                double t = 0.0;
+                for (int c = 0; c < C; ++c) {
+                    acc[2 * N + i * C + c] += w[i] * G[c];
+                    t += G[c] * ((double)values[i * C + c] - chat[c]);
+                }
+                double dx = qx - (double)points[2 * i];
+                double dy = qy - (double)points[2 * i + 1];
+                double wt = w[i] * t;
+                acc[2 * i] += wt * dx / s2;
+                acc[2 * i + 1] += wt * dy / s2;
+                acc[(size_t)N * (2 + C)] += wt * (dx * dx + dy * dy) / s3;
+            }
+        }
+    }
+    for (size_t e = 0; e < per; ++e) {
+        double s = 0.0;
+        for (int t = 0; t < nt; ++t) s += part[per * (size_t)t + e];
+        part[e] = s;
+    }
+    if (gpoints) memcpy(gpoints, part, sizeof(double) * (size_t)N * 2);
+    if (gvalues) memcpy(gvalues, part + 2 * N, sizeof(double) * (size_t)N * (size_t)C);
+    if (gsigma) *gsigma = part[(size_t)N * (2 + C)];
+    free(part);
+    free(wbuf_all);
+    return 0;
+}

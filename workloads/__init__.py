@@ -1,0 +1,249 @@
+"""Seeded synthetic inputs for the Gaussian-mixture interpolation workloads.
+
+This module only draws random numbers and lays them out; it contains none of
+the interpolation arithmetic, so both the FP64 oracle and the CUDA path can be
+fed from it without sharing any code with each other.
+
+Conventions (the paper leaves them open, section 1): positions are in output
+pixel units, ``points[:, 0]`` is x (column direction, along W) and
+``points[:, 1]`` is y (row direction, along H); the output pixel (i, j) sits at
+(j + 0.5, i + 0.5).  Everything is float32, row-major and contiguous.
+
+Workloads (shapes follow the paper's upsampling use case, section 3.2, with
+synthetic fields standing in for the ImageNet images, which are not used):
+
+* ``small_uniform``      N=4096 uniform in [0,64)^2, 64x64x3, sigma=0.75
+* ``upsample_1024``      512^2 jittered source grid -> 1024x1024x3, sigma=1.0,
+                         values from a smooth random field
+* ``batched_uneven``     64 images, sides log-uniform in [128,1024],
+                         N = 0.25*H*W clustered points, sigma U[0.5,2]
+* ``fwd_bwd_512``        16 images 512x512x3, 65536 clustered points each,
+                         sigma=1.0, upstream gradient N(0,1)
+* ``serving``            request stream: Poisson arrivals, sides log-uniform
+                         in [64,2048], N = U[0.1,1]*H*W, uniform or clustered
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List, Optional
+
+import numpy as np
+
+__all__ = [
+    "Image", "uniform_points", "clustered_points", "smooth_field",
+    "small_uniform", "upsample_1024", "batched_uneven", "fwd_bwd_512",
+    "fd_subcase", "serving_stream", "tiny_random",
+]
+
+
+@dataclasses.dataclass
+class Image:
+    """One interpolation problem: points[N,2], values[N,C], sigma, H, W."""
+    points: np.ndarray
+    values: np.ndarray
+    sigma: float
+    H: int
+    W: int
+
+    @property
+    def N(self) -> int:
+        return int(self.points.shape[0])
+
+    @property
+    def C(self) -> int:
+        return int(self.values.shape[1])
+
+
+def _f32(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+
+
+def uniform_points(rng: np.random.Generator, n: int, H: int, W: int) -> np.ndarray:
+    """n positions uniform in [0,W) x [0,H)."""
+    xy = np.empty((n, 2), dtype=np.float64)
+    xy[:, 0] = rng.uniform(0.0, W, n)
+    xy[:, 1] = rng.uniform(0.0, H, n)
+    pts = _f32(xy)
+    # float32 rounding can land exactly on the upper edge; keep [0, W) x [0, H)
+    np.minimum(pts[:, 0], np.nextafter(np.float32(W), np.float32(0)), out=pts[:, 0])
+    np.minimum(pts[:, 1], np.nextafter(np.float32(H), np.float32(0)), out=pts[:, 1])
+    return pts
+
+
+def clustered_points(rng: np.random.Generator, n: int, H: int, W: int,
+                     n_clusters: int = 8) -> np.ndarray:
+    """n positions from a mixture of isotropic 2D Gaussian clusters.
+
+    Centres are uniform in the frame, each cluster's std is U[0.05, 0.2] of
+    min(H, W), the mixture weights are Dirichlet(1); samples falling outside
+    [0,W) x [0,H) are redrawn from the same cluster.
+    """
+    centres = np.stack([rng.uniform(0, W, n_clusters), rng.uniform(0, H, n_clusters)], 1)
+    stds = rng.uniform(0.05, 0.2, n_clusters) * min(H, W)
+    weights = rng.dirichlet(np.ones(n_clusters))
+    labels = rng.choice(n_clusters, size=n, p=weights)
+    out = np.empty((n, 2), dtype=np.float64)
+    todo = np.arange(n)
+    while todo.size:
+        lab = labels[todo]
+        cand = centres[lab] + rng.standard_normal((todo.size, 2)) * stds[lab, None]
+        cand32 = cand.astype(np.float32)
+        ok = (cand32[:, 0] >= 0) & (cand32[:, 0] < W) & (cand32[:, 1] >= 0) & (cand32[:, 1] < H)
+        out[todo[ok]] = cand[ok]
+        todo = todo[~ok]
+    return _f32(out)
+
+
+def smooth_field(rng: np.random.Generator, xy: np.ndarray, C: int, period: float,
+                 n_waves: int = 32, std: float = 0.25) -> np.ndarray:
+    """Per channel: 0.5 + sum of n_waves random 2D sinusoids, clipped to [0,1].
+
+    Frequencies are U[-8,8] cycles per ``period`` pixels, phases U[0,2pi),
+    amplitudes U[0,1] rescaled so the (unclipped) field has the given std.
+    """
+    x = xy[:, 0].astype(np.float64)
+    y = xy[:, 1].astype(np.float64)
+    out = np.empty((xy.shape[0], C), dtype=np.float64)
+    for c in range(C):
+        u = rng.uniform(-8, 8, n_waves)
+        v = rng.uniform(-8, 8, n_waves)
+        phi = rng.uniform(0, 2 * math.pi, n_waves)
+        a = rng.uniform(0, 1, n_waves)
+        a *= std / math.sqrt(0.5 * float(np.sum(a * a)))
+        f = np.full(x.shape, 0.5)
+        for k in range(n_waves):
+            f += a[k] * np.sin(2 * math.pi * (u[k] * x + v[k] * y) / period + phi[k])
+        out[:, c] = f
+    return _f32(np.clip(out, 0.0, 1.0))
+
+
+def small_uniform(seed: int = 1) -> Image:
+    """N=4096 points uniform in [0,64)^2, RGB U[0,1], sigma=0.75, 64x64 output."""
+    rng = np.random.default_rng(seed)
+    pts = uniform_points(rng, 4096, 64, 64)
+    vals = _f32(rng.uniform(0, 1, (4096, 3)))
+    return Image(pts, vals, 0.75, 64, 64)
+
+
+def upsample_1024(seed: int = 2, src: int = 512, factor: int = 2, C: int = 3,
+                  sigma: float = 1.0) -> Image:
+    """A src x src source grid upsampled by ``factor`` (default 512^2 -> 1024^2).
+
+    Source sample (l, k) sits at the centre of its factor x factor block,
+    (factor*l + factor/2, factor*k + factor/2), jittered by U[-0.5, 0.5] px on
+    each axis; its colour is a smooth random field evaluated there.
+    """
+    rng = np.random.default_rng(seed)
+    H = W = src * factor
+    ly, lx = np.meshgrid(np.arange(src), np.arange(src), indexing="ij")
+    base = np.stack([lx.ravel() * factor + factor / 2.0, ly.ravel() * factor + factor / 2.0], 1)
+    jit = rng.uniform(-0.5, 0.5, base.shape)
+    pts = _f32(base + jit)
+    vals = smooth_field(rng, pts, C, period=float(W))
+    return Image(pts, vals, sigma, H, W)
+
+
+def _log_uniform_int(rng, lo, hi, size=None):
+    return np.rint(np.exp(rng.uniform(math.log(lo), math.log(hi), size))).astype(np.int64)
+
+
+def batched_uneven(seed: int = 3, B: int = 64, lo: int = 128, hi: int = 1024,
+                   density: float = 0.25, C: int = 3) -> List[Image]:
+    """B images with sides log-uniform in [lo, hi], N = density*H*W clustered
+    points (8 clusters), RGB U[0,1], sigma U[0.5, 2.0] per image."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(B):
+        H = int(_log_uniform_int(rng, lo, hi))
+        W = int(_log_uniform_int(rng, lo, hi))
+        n = int(round(density * H * W))
+        pts = clustered_points(rng, n, H, W)
+        vals = _f32(rng.uniform(0, 1, (n, C)))
+        sigma = float(np.float32(rng.uniform(0.5, 2.0)))
+        out.append(Image(pts, vals, sigma, H, W))
+    return out
+
+
+def fwd_bwd_512(seed: int = 4, B: int = 16, side: int = 512, n: int = 65536,
+                C: int = 3, sigma: float = 1.0):
+    """B images of side x side from n clustered points each, plus an upstream
+    gradient g ~ N(0,1) of shape [B, side, side, C]."""
+    rng = np.random.default_rng(seed)
+    imgs = []
+    for _ in range(B):
+        pts = clustered_points(rng, n, side, side)
+        vals = _f32(rng.uniform(0, 1, (n, C)))
+        imgs.append(Image(pts, vals, sigma, side, side))
+    grad = _f32(rng.standard_normal((B, side, side, C)))
+    return imgs, grad
+
+
+def fd_subcase(seed: int = 4, side: int = 32, n: int = 256, C: int = 3,
+               sigma: float = 1.0):
+    """Small clustered case for finite-difference gradient checks."""
+    rng = np.random.default_rng(seed + 1000)
+    pts = clustered_points(rng, n, side, side)
+    vals = _f32(rng.uniform(0, 1, (n, C)))
+    grad = _f32(rng.standard_normal((side, side, C)))
+    return Image(pts, vals, sigma, side, side), grad
+
+
+def tiny_random(seed: int, N: int, H: int, W: int, C: int = 3, sigma: float = 1.0,
+                clustered: bool = False, margin: float = 0.0) -> Image:
+    """Small random case; ``margin`` widens the position range beyond the frame
+    so that some points fall outside it."""
+    rng = np.random.default_rng(seed)
+    if clustered:
+        pts = clustered_points(rng, N, H, W)
+    else:
+        xy = np.stack([rng.uniform(-margin, W + margin, N), rng.uniform(-margin, H + margin, N)], 1)
+        pts = _f32(xy)
+    vals = _f32(rng.uniform(0, 1, (N, C)))
+    return Image(pts, vals, float(np.float32(sigma)), H, W)
+
+
+@dataclasses.dataclass
+class Request:
+    """One serving request: arrival time (s from stream start) and its image."""
+    rid: int
+    t_arrival: float
+    H: int
+    W: int
+    N: int
+    clustered: bool
+    sigma: float
+    seed: int
+
+    def materialise(self, C: int = 3) -> Image:
+        rng = np.random.default_rng(self.seed)
+        if self.clustered:
+            pts = clustered_points(rng, self.N, self.H, self.W)
+        else:
+            pts = uniform_points(rng, self.N, self.H, self.W)
+        vals = _f32(rng.uniform(0, 1, (self.N, C)))
+        return Image(pts, vals, self.sigma, self.H, self.W)
+
+
+def serving_stream(seed: int = 5, n_requests: int = 10000, rate: float = 2000.0,
+                   lo: int = 64, hi: int = 2048) -> List[Request]:
+    """Request descriptors with Poisson arrivals at ``rate`` per second.
+
+    Sides are log-uniform in [lo, hi] (independently for H and W), the point
+    count is U[0.1, 1.0] * H * W, a fair coin picks uniform or clustered
+    positions, sigma is U[0.5, 2.0].  Payloads are drawn lazily by
+    ``Request.materialise`` from a per-request seed.
+    """
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / rate, n_requests)
+    t = np.cumsum(gaps) - gaps[0]
+    out = []
+    for r in range(n_requests):
+        H = int(_log_uniform_int(rng, lo, hi))
+        W = int(_log_uniform_int(rng, lo, hi))
+        N = max(1, int(round(rng.uniform(0.1, 1.0) * H * W)))
+        clustered = bool(rng.integers(0, 2))
+        sigma = float(np.float32(rng.uniform(0.5, 2.0)))
+        out.append(Request(r, float(t[r]), H, W, N, clustered, sigma,
+                           int(rng.integers(0, 2**31 - 1))))
+    return out
