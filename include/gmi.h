@@ -1,0 +1,301 @@
+/*
+ * gmi.h -- C ABI of libgmi: Gaussian-mixture interpolation of scattered
+ * points onto an H x W raster, hand-written CUDA for sm_103a (B300).
+ *
+ * The operation (Skorokhodov, arXiv 2012.13257, section 2, Eq. 1 and Eq. 2):
+ * every known point i is an isotropic 2D normal N(mu_i, sigma^2 I) with
+ * mu_i = points[i] = (x_i, y_i) and a colour values[i] in R^C; every output
+ * pixel q takes the normalised, density-weighted mean of the known colours
+ *
+ *     c(q) = sum_i values[i] * N(q | mu_i, sigma^2 I) / Z_q,
+ *     Z_q  = sum_i N(q | mu_i, sigma^2 I),
+ *
+ * with the same weights for every channel (end of section 2).
+ *
+ * Conventions fixed by this library (the paper leaves them open):
+ *   - coordinates and sigma are in output-pixel units; x runs along W
+ *     (columns), y along H (rows); pixel (i, j) is queried at
+ *     q = (j + 0.5, i + 0.5);
+ *   - all arrays are row-major, contiguous float32: points [N,2] as (x, y),
+ *     values [N,C], image [H,W,C], den/shift planes [H,W];
+ *   - GMI_MODE_EXACT (default) evaluates the full sums.  A point whose
+ *     squared distance exceeds m_q + k^2 sigma^2 (m_q = squared distance from
+ *     q to its nearest point, k = radius_sigmas) carries less than e^{-k^2/2}
+ *     of the nearest point's weight and may be skipped (k = 6: 1.5e-8);
+ *   - GMI_MODE_TRUNCATED is the literal reading of the paper's "close enough"
+ *     rule with radius k*sigma: only points with d <= k sigma count, and a
+ *     pixel with none gets colour 0 and den 0;
+ *   - N = 0 gives an all-zero image (and den 0).  Points outside the frame
+ *     are allowed and contribute like any other.
+ *
+ * Ownership: every buffer is owned by the caller; pointers marked "device"
+ * must be CUDA device (or managed) memory on the current device.  The
+ * single-image and batched entry points allocate nothing: scratch memory is a
+ * caller-provided workspace sized by the matching *_workspace_size call.  The
+ * server owns one device pool of at most its memory budget, allocated at
+ * creation.
+ *
+ * Asynchrony: compute calls enqueue work on `stream` and return without
+ * waiting, unless params->flags has GMI_FLAG_SYNC_CHECK, in which case they
+ * synchronise the stream and return the status word the kernels wrote
+ * (e.g. GMI_ERR_NONFINITE for NaN/Inf inputs).  gmi_workspace_status reads
+ * that word after the fact.
+ *
+ * Thread safety: calls on different workspaces / streams may run
+ * concurrently; a workspace must not be used by two calls in flight at once.
+ */
+#ifndef GMI_H_
+#define GMI_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* cudaStream_t without pulling in the CUDA headers. */
+typedef struct CUstream_st* gmi_stream_t;
+
+typedef enum {
+    GMI_OK = 0,
+    GMI_ERR_INVALID_ARG = 1,   /* argument outside its documented range */
+    GMI_ERR_NONFINITE = 2,     /* NaN/Inf in points or values (found on device) */
+    GMI_ERR_WORKSPACE = 3,     /* workspace NULL, misaligned or too small */
+    GMI_ERR_CUDA = 4,          /* a CUDA runtime call failed */
+    GMI_ERR_BUDGET = 5,        /* request larger than the server's memory budget */
+    GMI_ERR_TIMEOUT = 6,       /* a bounded wait expired */
+    GMI_ERR_UNSUPPORTED = 7,   /* valid but not built (e.g. C > 4) */
+    GMI_ERR_NOT_FOUND = 8,     /* unknown server request id */
+    GMI_ERR_CAPACITY = 9,      /* batch exceeds the plan's capacities */
+    GMI_ERR_INTERNAL = 10      /* a device-side consistency check failed */
+} gmi_status;
+
+typedef enum { GMI_MODE_EXACT = 0, GMI_MODE_TRUNCATED = 1 } gmi_mode;
+
+/* params->flags */
+#define GMI_FLAG_SYNC_CHECK 0x1u   /* synchronise and return the device status */
+
+/* Kernel variants (params->variant); 0 = choose automatically. */
+#define GMI_VARIANT_AUTO 0
+#define GMI_VARIANT_MT4x4 1        /* each thread owns a 4x4 pixel micro-tile */
+#define GMI_VARIANT_MT4x8 2        /* 4 rows x 8 columns */
+#define GMI_VARIANT_MT2x4 3        /* 2 rows x 4 columns */
+
+typedef struct {
+    float sigma;          /* std of every point's Gaussian, output px; finite, > 0 */
+    float radius_sigmas;  /* k: radius rule in sigmas; finite, > 0; default 6 */
+    int mode;             /* gmi_mode */
+    unsigned flags;       /* GMI_FLAG_* */
+    int bin_px;           /* edge of the square point bins in px; 0 = auto (1..64) */
+    int variant;          /* GMI_VARIANT_*; 0 = auto */
+    int reserved[2];      /* set to 0 */
+} gmi_params;
+
+/* Library version string, e.g. "gmi 0.1.0 sm_103a". */
+const char* gmi_version(void);
+
+/* Human-readable name of a status code; never NULL. */
+const char* gmi_status_string(gmi_status s);
+
+/* Fills *p with the defaults: sigma = 1, radius_sigmas = 6, exact mode,
+ * no flags, automatic bins and variant.  Returns GMI_ERR_INVALID_ARG if p is
+ * NULL. */
+gmi_status gmi_params_default(gmi_params* p);
+
+/*
+ * Workspace size for one gmi_forward / gmi_backward call on an N-point,
+ * C-channel, H x W problem with these params.  Writes the byte count to
+ * *bytes.  Errors: GMI_ERR_INVALID_ARG (N < 0, H or W < 1, sigma or k not
+ * finite and > 0, bytes NULL, H*W > 2^31), GMI_ERR_UNSUPPORTED (C outside
+ * 1..4).  The size does not depend on the point coordinates.
+ */
+gmi_status gmi_workspace_size(int64_t N, int C, int H, int W, const gmi_params* p,
+                              size_t* bytes);
+
+/*
+ * Forward pass, Eq. 1 and Eq. 2 of section 2.
+ *   points   device [N,2] float32 (x, y), 8-byte aligned
+ *   values   device [N,C] float32
+ *   image    device [H,W,C] float32, written
+ *   den_out  device [H,W] float32 or NULL: the density sum scaled by the
+ *            pixel's shift, sum_i exp(-(d_i^2 - shift_q)/(2 sigma^2)), over
+ *            the points used (the 1/(2 pi sigma^2) factor is left out: it
+ *            cancels in Eq. 1)
+ *   shift_out device [H,W] float32 or NULL: the per-pixel shift used
+ *            (0 where none was needed; about the nearest squared distance
+ *            where the unshifted weights would underflow)
+ *   workspace device, >= gmi_workspace_size bytes, 256-byte aligned; its
+ *            contents on entry are ignored
+ * Errors: as gmi_workspace_size, plus GMI_ERR_WORKSPACE, GMI_ERR_CUDA; with
+ * GMI_FLAG_SYNC_CHECK also GMI_ERR_NONFINITE / GMI_ERR_INTERNAL.  On an
+ * argument error nothing is enqueued.
+ */
+gmi_status gmi_forward(const float* points, const float* values, int64_t N, int C,
+                       int H, int W, const gmi_params* p, float* image, float* den_out,
+                       float* shift_out, void* workspace, size_t ws_bytes,
+                       gmi_stream_t stream);
+
+/*
+ * Backward pass: gradients of L = sum_q sum_c grad_image[q,c] * image[q,c]
+ * (the paper has forward and backward CUDA kernels but prints no backward
+ * formulas; these are the chain rule on Eq. 1):
+ *   grad_values[i,c] = sum_q grad[q,c] w_i(q) / Z_q
+ *   grad_points[i]   = sum_q (w_i(q)/Z_q) t_i(q) (q - mu_i) / sigma^2
+ *   grad_sigma       = sum_q sum_i (w_i(q)/Z_q) t_i(q) |q - mu_i|^2 / sigma^3
+ *   with t_i(q) = sum_c grad[q,c] (values[i,c] - image[q,c]).
+ *   image, den, shift: the outputs of the matching gmi_forward (den and shift
+ *            must not be NULL); grad_image device [H,W,C]
+ *   grad_points [N,2], grad_values [N,C], grad_sigma [1]: device, written
+ *            (each may be NULL to skip it)
+ * The point bins are rebuilt inside the call (nothing is kept from the
+ * forward pass except image/den/shift).  Errors: as gmi_forward.
+ */
+gmi_status gmi_backward(const float* points, const float* values, int64_t N, int C,
+                        int H, int W, const gmi_params* p, const float* image,
+                        const float* den, const float* shift, const float* grad_image,
+                        float* grad_points, float* grad_values, float* grad_sigma,
+                        void* workspace, size_t ws_bytes, gmi_stream_t stream);
+
+/*
+ * Reads the device status word of a workspace after its stream has finished
+ * (synchronises `stream` first).  Returns GMI_OK, GMI_ERR_NONFINITE or
+ * GMI_ERR_INTERNAL for the last call that used the workspace.
+ */
+gmi_status gmi_workspace_status(const void* workspace, gmi_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Measurement aid (no counterpart in the paper): while enabled, the compute
+ * entry points bracket each stage of their pipeline with CUDA events recorded
+ * on their own stream, so kernel times can be read without a profiler.
+ * ---------------------------------------------------------------------- */
+typedef enum {
+    GMI_STAGE_BIN = 0,       /* memset + count + scan + scatter + plan */
+    GMI_STAGE_NEAR = 1,      /* near-field gather */
+    GMI_STAGE_FAR = 2,       /* far-field gather */
+    GMI_STAGE_BACKWARD = 3,  /* backward gathers (after re-binning) */
+    GMI_STAGE_COUNT = 4
+} gmi_stage;
+
+/* Turns stage timing on (creates a pool of CUDA events on first use) or off.
+ * Process-wide.  Errors: GMI_ERR_CUDA. */
+gmi_status gmi_profile_enable(int on);
+
+/* Waits for every recorded stage, adds the elapsed milliseconds per stage
+ * into ms[GMI_STAGE_COUNT] and the number of timed launches into
+ * launches[GMI_STAGE_COUNT] (either may be NULL), and with reset != 0 forgets
+ * them.  Stages recorded while the event pool was exhausted are not counted. */
+gmi_status gmi_profile_read(double* ms, int* launches, int reset);
+
+/* ------------------------------------------------------------------------
+ * Batched forward: B independent images of uneven size in one persistent
+ * launch over a global tile queue (the shapes live in a device descriptor
+ * table, so one captured CUDA graph replays for any batch within capacity).
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    const float* points;   /* device [N,2] */
+    const float* values;   /* device [N,C] */
+    float* image;          /* device [H,W,C] */
+    float* den;            /* device [H,W] or NULL */
+    float* shift;          /* device [H,W] or NULL */
+    int64_t N;             /* >= 0 */
+    int H, W;              /* >= 1 */
+    float sigma;           /* finite, > 0 */
+    int bin_px;            /* 0 = auto */
+} gmi_image_desc;
+
+typedef struct gmi_batch_plan gmi_batch_plan;   /* opaque */
+
+/*
+ * Creates a batch plan for up to max_images images holding at most
+ * max_points points and max_pixels output pixels in total, C channels.
+ * Allocates its device workspace and pinned host staging once (setup, not
+ * hot path).  params supplies k, mode and the variant; its sigma is unused
+ * (each image has its own).  Errors: GMI_ERR_INVALID_ARG,
+ * GMI_ERR_UNSUPPORTED, GMI_ERR_CUDA (allocation failed).
+ */
+gmi_status gmi_batch_plan_create(int max_images, int64_t max_points, int64_t max_pixels,
+                                 int C, const gmi_params* params, gmi_batch_plan** plan);
+
+/* Frees a plan (synchronises its last launch first).  NULL is a no-op. */
+gmi_status gmi_batch_plan_destroy(gmi_batch_plan* plan);
+
+/* Device bytes the plan holds. */
+size_t gmi_batch_plan_bytes(const gmi_batch_plan* plan);
+
+/*
+ * Runs the forward pass of B images (descs is a host array) in one batched
+ * pipeline on `stream`: one segmented binning pass, then one persistent
+ * gather over the work queue of all images' tiles.  With use_graph != 0 the
+ * kernel sequence is captured into a CUDA graph on the first call and
+ * replayed afterwards.  Waits (host side) only for the previous call's
+ * descriptor upload.  Errors: GMI_ERR_INVALID_ARG, GMI_ERR_CAPACITY,
+ * GMI_ERR_CUDA; with GMI_FLAG_SYNC_CHECK in the plan's params, also the
+ * device status.
+ */
+gmi_status gmi_forward_batched(gmi_batch_plan* plan, const gmi_image_desc* descs, int B,
+                               int use_graph, gmi_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Serving: a persistent request loop with continuous batching.  Requests are
+ * admitted while their device memory fits the budget, their points are binned
+ * and kept on the device, admitted requests are packed into batched launches,
+ * and each request completes on its own event.
+ * ---------------------------------------------------------------------- */
+typedef struct gmi_server gmi_server;   /* opaque */
+
+typedef struct {
+    size_t budget_bytes;     /* device memory the server may hold in total */
+    int max_batch_images;    /* images per batched launch (>= 1) */
+    int64_t max_batch_pixels;/* output pixels per batched launch (>= 1) */
+    int n_streams;           /* launches that may be in flight at once (1..8) */
+    int C;                   /* channels (1..4) */
+    float radius_sigmas;     /* k, default 6 */
+    int mode;                /* gmi_mode */
+    int reserved;
+} gmi_server_config;
+
+/* Fills a config with defaults (40 GB budget, 64 images, 2^25 pixels per
+ * batch, 2 streams, C = 3, k = 6, exact mode). */
+gmi_status gmi_server_config_default(gmi_server_config* cfg);
+
+/* Creates the server: allocates its device pool (budget_bytes) and starts
+ * its launcher and completion threads.  Errors: GMI_ERR_INVALID_ARG,
+ * GMI_ERR_CUDA. */
+gmi_status gmi_server_create(const gmi_server_config* cfg, gmi_server** out);
+
+/*
+ * Submits one request.  points/values/image are HOST buffers (pinned memory
+ * gives asynchronous copies); they must stay valid until the request
+ * completes.  The request is queued until its device footprint fits the
+ * budget.  *id receives the request id.  Errors: GMI_ERR_INVALID_ARG,
+ * GMI_ERR_BUDGET (the request alone exceeds the budget).
+ */
+gmi_status gmi_server_submit(gmi_server* s, const float* points, const float* values,
+                             int64_t N, int H, int W, float sigma, float* image,
+                             uint64_t* id);
+
+/*
+ * Waits up to timeout_ms (< 0: forever) for request `id`.  Returns GMI_OK
+ * when its image is in the host buffer, GMI_ERR_TIMEOUT, GMI_ERR_NOT_FOUND,
+ * or the request's own error.  On success *latency_s (if not NULL) holds
+ * the time from submission to completion, in seconds.
+ */
+gmi_status gmi_server_wait(gmi_server* s, uint64_t id, int timeout_ms, double* latency_s);
+
+/* Non-blocking: GMI_OK if done, GMI_ERR_TIMEOUT if still pending. */
+gmi_status gmi_server_poll(gmi_server* s, uint64_t id);
+
+/* Server counters: completed requests, batched launches, pixels served, and
+ * the device bytes currently held by admitted requests. */
+gmi_status gmi_server_stats(gmi_server* s, uint64_t* completed, uint64_t* launches,
+                            uint64_t* pixels, size_t* bytes_in_use);
+
+/* Drains pending requests, stops the threads and frees the pool. */
+gmi_status gmi_server_destroy(gmi_server* s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GMI_H_ */

@@ -1,0 +1,303 @@
+// Host side of the libgmi C ABI: argument checks, workspace layout, and the
+// launch sequence of the single-image forward pass
+//   memset(status, bin counts) -> bin_count -> scan_partial -> scan_final
+//   -> bin_scatter -> near_plan -> near gather -> far gather
+// All kernels run on the caller's stream; nothing here allocates memory.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "api_internal.h"
+#include "gmi.h"
+
+namespace gmi {
+
+cudaError_t launch_near(const KArgs& a, int mth, int mtw, bool trunc, int grid, cudaStream_t s);
+cudaError_t launch_near_plan(const KArgs& a, bool trunc, cudaStream_t s);
+int near_blocks_per_sm(int mth, int mtw, int C, bool trunc);
+cudaError_t launch_far(const KArgs& a, int mth, int mtw, int grid, cudaStream_t s);
+__global__ void bin_count_kernel(KArgs a);
+__global__ void scan_partial_kernel(const unsigned* cnt, long long nb, unsigned* partials);
+__global__ void scan_final_kernel(unsigned* off, long long nb, const unsigned* partials);
+__global__ void bin_scatter_kernel(KArgs a);
+
+static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+int device_sm_count() {
+  static int cache[64];
+  static std::mutex mu;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 148;
+  std::lock_guard<std::mutex> lk(mu);
+  if (cache[dev] == 0) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
+    cache[dev] = n;
+  }
+  return cache[dev];
+}
+
+void variant_dims(int variant, int* mth, int* mtw) {
+  switch (variant) {
+    case GMI_VARIANT_MT4x8: *mth = 4; *mtw = 8; break;
+    case GMI_VARIANT_MT2x4: *mth = 2; *mtw = 4; break;
+    default: *mth = 4; *mtw = 4; break;
+  }
+}
+
+int auto_bin_px(long long n, int H, int W) {
+  if (n <= 0) return 64;
+  const double rho = (double)n / ((double)H * (double)W);
+  // about one point per bin: b ~ 1/sqrt(rho), rounded to a power of two
+  const double l = -0.5 * log2(rho);
+  int e = (int)floor(l + 0.5);
+  if (e < 0) e = 0;
+  if (e > 6) e = 6;
+  return 1 << e;
+}
+
+gmi_status check_params(const gmi_params* p) {
+  if (!p) return GMI_ERR_INVALID_ARG;
+  if (!(isfinite(p->sigma) && p->sigma > 0.0f)) return GMI_ERR_INVALID_ARG;
+  if (!(isfinite(p->radius_sigmas) && p->radius_sigmas > 0.0f)) return GMI_ERR_INVALID_ARG;
+  if (p->mode != GMI_MODE_EXACT && p->mode != GMI_MODE_TRUNCATED) return GMI_ERR_INVALID_ARG;
+  if (p->bin_px < 0 || p->bin_px > 1024) return GMI_ERR_INVALID_ARG;
+  if (p->variant < 0 || p->variant > GMI_VARIANT_MT2x4) return GMI_ERR_INVALID_ARG;
+  return GMI_OK;
+}
+
+gmi_status check_shape(long long N, int C, int H, int W) {
+  if (N < 0 || H < 1 || W < 1) return GMI_ERR_INVALID_ARG;
+  if ((long long)H * (long long)W > (1LL << 31)) return GMI_ERR_INVALID_ARG;
+  if (N > (1LL << 31)) return GMI_ERR_INVALID_ARG;
+  if (C < 1 || C > kMaxC) return GMI_ERR_UNSUPPORTED;
+  return GMI_OK;
+}
+
+// Fills the derived fields of an image geometry.
+void fill_geom(ImageGeom& g, long long N, int H, int W, float sigma, float k, int bin_px, int mth, int mtw) {
+  g.n = N;
+  g.H = H;
+  g.W = W;
+  g.b = bin_px > 0 ? bin_px : auto_bin_px(N, H, W);
+  g.inv_b = 1.0f / (float)g.b;
+  g.nbx = (W + g.b - 1) / g.b;
+  g.nby = (H + g.b - 1) / g.b;
+  g.mtx = (W + mtw - 1) / mtw;
+  g.mty = (H + mth - 1) / mth;
+  g.wtx = (g.mtx + 7) / 8;
+  g.wty = (g.mty + 3) / 4;
+  g.sigma = sigma;
+  const double kappa = 1.4426950408889634 / (2.0 * (double)sigma * (double)sigma);
+  g.kappa = (float)kappa;
+  g.sk = (float)sqrt(kappa);
+  g.r2k = (float)((double)k * k * (double)sigma * sigma);
+  g.u_near_max = (float)(100.0 / kappa);
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+void set_vec_ok(ImageGeom& g) {
+  g.vec_ok = (g.W % 4 == 0) && aligned16(g.image) && (!g.den || aligned16(g.den)) && (!g.shift || aligned16(g.shift));
+}
+
+size_t slot_bytes_for(int mth, int mtw, int C) { return sizeof(float) * 32u * mth * mtw * (C + 1); }
+
+// Workspace layout for totals (points, bins, micro-tiles, warp tiles); bytes.
+WsLayout ws_layout(long long n_total, long long nb_total, long long mt_total, long long wt_total,
+                   size_t slot_bytes, long long extra_bytes) {
+  WsLayout L;
+  size_t o = 0;
+  L.cap_items = (unsigned)std::min<long long>(wt_total * kSplitMax, 0x7fffffffLL);
+  L.cap_slots = (unsigned)std::min<long long>(wt_total / 2 + 256, 0x7fffffffLL);
+  L.status = o; o = align_up(o + sizeof(unsigned) * kStatusWords, 256);
+  L.off = o;    o = align_up(o + sizeof(unsigned) * (size_t)(nb_total + 1), 256);
+  L.oob = o;    o = align_up(o + (size_t)nb_total, 256);
+  L.tile_done = o; o = align_up(o + sizeof(unsigned) * (size_t)(wt_total > 0 ? wt_total : 1), 256);
+  L.zero_end = o;                               // [0, zero_end) is cleared per call
+  L.rank = o;   o = align_up(o + sizeof(unsigned) * (size_t)n_total, 256);
+  L.sxy = o;    o = align_up(o + sizeof(float2) * (size_t)n_total, 256);
+  L.sval = o;   o = align_up(o + sizeof(float4) * (size_t)n_total, 256);
+  L.partials = o; o = align_up(o + sizeof(unsigned) * (size_t)((nb_total + kScanChunk - 1) / kScanChunk + 1), 256);
+  L.farq = o;   o = align_up(o + sizeof(uint2) * (size_t)(mt_total > 0 ? mt_total : 1), 256);
+  L.items = o;  o = align_up(o + sizeof(uint4) * (size_t)(L.cap_items > 0 ? L.cap_items : 1), 256);
+  L.slots = o;  o = align_up(o + slot_bytes * (size_t)L.cap_slots, 256);
+  L.extra = o;  o = align_up(o + (size_t)extra_bytes, 256);
+  L.total = o;
+  return L;
+}
+
+DevWork bind_ws(void* ws, const WsLayout& L) {
+  char* b = (char*)ws;
+  DevWork w;
+  w.status = (unsigned*)(b + L.status);
+  w.off = (unsigned*)(b + L.off);
+  w.oob = (unsigned char*)(b + L.oob);
+  w.rank = (unsigned*)(b + L.rank);
+  w.sxy = (float2*)(b + L.sxy);
+  w.sval = (float4*)(b + L.sval);
+  w.partials = (unsigned*)(b + L.partials);
+  w.farq = (uint2*)(b + L.farq);
+  w.items = (uint4*)(b + L.items);
+  w.tile_done = (unsigned*)(b + L.tile_done);
+  w.slots = (float*)(b + L.slots);
+  w.table = nullptr;
+  return w;
+}
+
+// Binning + plan + near + far on prepared arguments (single image or batch).
+gmi_status run_forward_pipeline(KArgs& a, const WsLayout& L, void* ws, int mth, int mtw, bool trunc,
+                                cudaStream_t s) {
+  const ProfileMark pb = profile_begin(GMI_STAGE_BIN, s);
+  cudaError_t e = cudaMemsetAsync(ws, 0, L.zero_end, s);
+  if (e != cudaSuccess) return GMI_ERR_CUDA;
+  const int sms = device_sm_count();
+  if (a.n_total > 0) {
+    const int gb = (int)std::min<long long>(a.ch_total, (long long)sms * 32);
+    bin_count_kernel<<<gb, 256, 0, s>>>(a);
+    const int ns = (int)((a.nb_total + kScanChunk - 1) / kScanChunk);
+    scan_partial_kernel<<<ns, 256, 0, s>>>(a.w.off, a.nb_total, a.w.partials);
+    scan_final_kernel<<<ns, 256, 0, s>>>(a.w.off, a.nb_total, a.w.partials);
+    bin_scatter_kernel<<<gb, 256, 0, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return GMI_ERR_CUDA;
+  }
+  a.cap_items = L.cap_items;
+  a.cap_slots = L.cap_slots;
+  a.mth = mth;
+  a.mtw = mtw;
+  if ((e = launch_near_plan(a, trunc, s)) != cudaSuccess) return GMI_ERR_CUDA;
+  profile_end(pb, s);
+  const int per_sm = near_blocks_per_sm(mth, mtw, a.C, trunc);
+  // persistent: at most one resident wave, and no more warps than work items can use
+  const int gn = (int)std::max<long long>(1, std::min<long long>(a.wt_total * 4, (long long)sms * per_sm));
+  const ProfileMark pn = profile_begin(GMI_STAGE_NEAR, s);
+  if ((e = launch_near(a, mth, mtw, trunc, gn, s)) != cudaSuccess) return GMI_ERR_CUDA;
+  profile_end(pn, s);
+  if (!trunc) {
+    const ProfileMark pf = profile_begin(GMI_STAGE_FAR, s);
+    if ((e = launch_far(a, mth, mtw, sms * 4, s)) != cudaSuccess) return GMI_ERR_CUDA;
+    profile_end(pf, s);
+  }
+  return GMI_OK;
+}
+
+gmi_status read_status(const void* ws, cudaStream_t s) {
+  if (cudaStreamSynchronize(s) != cudaSuccess) return GMI_ERR_CUDA;
+  unsigned st = 0;
+  if (cudaMemcpy(&st, ws, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess) return GMI_ERR_CUDA;
+  if (st & ST_NONFINITE) return GMI_ERR_NONFINITE;
+  if (st & (ST_INTERNAL | ST_TIMEOUT)) return GMI_ERR_INTERNAL;
+  return GMI_OK;
+}
+
+}  // namespace gmi
+
+using namespace gmi;
+
+extern "C" {
+
+const char* gmi_version(void) { return "gmi 0.1.0 sm_103a"; }
+
+const char* gmi_status_string(gmi_status s) {
+  switch (s) {
+    case GMI_OK: return "GMI_OK";
+    case GMI_ERR_INVALID_ARG: return "GMI_ERR_INVALID_ARG";
+    case GMI_ERR_NONFINITE: return "GMI_ERR_NONFINITE";
+    case GMI_ERR_WORKSPACE: return "GMI_ERR_WORKSPACE";
+    case GMI_ERR_CUDA: return "GMI_ERR_CUDA";
+    case GMI_ERR_BUDGET: return "GMI_ERR_BUDGET";
+    case GMI_ERR_TIMEOUT: return "GMI_ERR_TIMEOUT";
+    case GMI_ERR_UNSUPPORTED: return "GMI_ERR_UNSUPPORTED";
+    case GMI_ERR_NOT_FOUND: return "GMI_ERR_NOT_FOUND";
+    case GMI_ERR_CAPACITY: return "GMI_ERR_CAPACITY";
+    case GMI_ERR_INTERNAL: return "GMI_ERR_INTERNAL";
+  }
+  return "GMI_ERR_UNKNOWN";
+}
+
+gmi_status gmi_params_default(gmi_params* p) {
+  if (!p) return GMI_ERR_INVALID_ARG;
+  memset(p, 0, sizeof(*p));
+  p->sigma = 1.0f;
+  p->radius_sigmas = 6.0f;
+  p->mode = GMI_MODE_EXACT;
+  return GMI_OK;
+}
+
+gmi_status gmi_workspace_size(int64_t N, int C, int H, int W, const gmi_params* p, size_t* bytes) {
+  if (!bytes) return GMI_ERR_INVALID_ARG;
+  gmi_status st = check_params(p);
+  if (st != GMI_OK) return st;
+  if ((st = check_shape(N, C, H, W)) != GMI_OK) return st;
+  int mth, mtw;
+  variant_dims(p->variant, &mth, &mtw);
+  ImageGeom g;
+  memset(&g, 0, sizeof(g));
+  fill_geom(g, N, H, W, p->sigma, p->radius_sigmas, p->bin_px, mth, mtw);
+  const long long nb = (long long)g.nbx * g.nby;
+  const long long mt = (long long)g.mtx * g.mty;
+  const long long wt = (long long)g.wtx * g.wty;
+  *bytes = ws_layout(N, nb, mt, wt, slot_bytes_for(mth, mtw, C), bwd_extra_bytes(N, C, H, W)).total;
+  return GMI_OK;
+}
+
+gmi_status gmi_forward(const float* points, const float* values, int64_t N, int C, int H, int W,
+                       const gmi_params* p, float* image, float* den_out, float* shift_out,
+                       void* workspace, size_t ws_bytes, gmi_stream_t stream) {
+  gmi_status st = check_params(p);
+  if (st != GMI_OK) return st;
+  if ((st = check_shape(N, C, H, W)) != GMI_OK) return st;
+  if (!image || (N > 0 && (!points || !values))) return GMI_ERR_INVALID_ARG;
+  if (((uintptr_t)points & 7u) != 0 || ((uintptr_t)values & 3u) != 0 || ((uintptr_t)image & 3u) != 0)
+    return GMI_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  int mth, mtw;
+  variant_dims(p->variant, &mth, &mtw);
+  ImageGeom g;
+  memset(&g, 0, sizeof(g));
+  fill_geom(g, N, H, W, p->sigma, p->radius_sigmas, p->bin_px, mth, mtw);
+  g.points = points;
+  g.values = values;
+  g.image = image;
+  g.den = den_out;
+  g.shift = shift_out;
+  set_vec_ok(g);
+  const long long nb = (long long)g.nbx * g.nby;
+  const long long mt = (long long)g.mtx * g.mty;
+  const long long wt = (long long)g.wtx * g.wty;
+  const WsLayout L = ws_layout(N, nb, mt, wt, slot_bytes_for(mth, mtw, C), bwd_extra_bytes(N, C, H, W));
+  if (!workspace || ((uintptr_t)workspace & 255u) != 0 || ws_bytes < L.total) return GMI_ERR_WORKSPACE;
+
+  if (N == 0) {  // no known point: colour 0 and den 0 everywhere
+    const size_t px = (size_t)H * (size_t)W;
+    if (cudaMemsetAsync(image, 0, px * C * sizeof(float), s) != cudaSuccess) return GMI_ERR_CUDA;
+    if (den_out && cudaMemsetAsync(den_out, 0, px * sizeof(float), s) != cudaSuccess) return GMI_ERR_CUDA;
+    if (shift_out && cudaMemsetAsync(shift_out, 0, px * sizeof(float), s) != cudaSuccess) return GMI_ERR_CUDA;
+    if (cudaMemsetAsync(workspace, 0, sizeof(unsigned) * kStatusWords, s) != cudaSuccess) return GMI_ERR_CUDA;
+    return (p->flags & GMI_FLAG_SYNC_CHECK) ? read_status(workspace, s) : GMI_OK;
+  }
+
+  KArgs a;
+  memset(&a, 0, sizeof(a));
+  a.w = bind_ws(workspace, L);
+  a.g0 = g;
+  a.n_images = 1;
+  a.C = C;
+  a.n_total = N;
+  a.nb_total = nb;
+  a.wt_total = wt;
+  a.ch_total = (N + kChunk - 1) / kChunk;
+  a.mt_total = mt;
+  st = run_forward_pipeline(a, L, workspace, mth, mtw, p->mode == GMI_MODE_TRUNCATED, s);
+  if (st != GMI_OK) return st;
+  return (p->flags & GMI_FLAG_SYNC_CHECK) ? read_status(workspace, s) : GMI_OK;
+}
+
+gmi_status gmi_workspace_status(const void* workspace, gmi_stream_t stream) {
+  if (!workspace) return GMI_ERR_INVALID_ARG;
+  return read_status(workspace, (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,45 @@
+// Host-side helpers shared by the libgmi translation units.
+#pragma once
+
+#include <algorithm>
+
+#include "common.cuh"
+#include "gmi.h"
+
+namespace gmi {
+
+// Byte offsets of the regions of a workspace.
+struct WsLayout {
+  size_t status, off, oob, tile_done, zero_end, rank, sxy, sval, partials, farq, items, slots, extra, total;
+  unsigned cap_items, cap_slots;
+};
+
+int device_sm_count();
+void variant_dims(int variant, int* mth, int* mtw);
+int auto_bin_px(long long n, int H, int W);
+gmi_status check_params(const gmi_params* p);
+gmi_status check_shape(long long N, int C, int H, int W);
+void fill_geom(ImageGeom& g, long long N, int H, int W, float sigma, float k, int bin_px, int mth, int mtw);
+void set_vec_ok(ImageGeom& g);
+bool aligned16(const void* p);
+size_t slot_bytes_for(int mth, int mtw, int C);
+WsLayout ws_layout(long long n_total, long long nb_total, long long mt_total, long long wt_total,
+                   size_t slot_bytes, long long extra_bytes);
+DevWork bind_ws(void* ws, const WsLayout& L);
+gmi_status run_forward_pipeline(KArgs& a, const WsLayout& L, void* ws, int mth, int mtw, bool trunc,
+                                cudaStream_t s);
+gmi_status read_status(const void* ws, cudaStream_t s);
+
+// Stage timing (profile.cu): no-ops unless gmi_profile_enable(1) was called.
+struct ProfileMark {
+  int stage;
+  cudaEvent_t a, b;
+};
+bool profile_on();
+ProfileMark profile_begin(int stage, cudaStream_t s);
+void profile_end(const ProfileMark& m, cudaStream_t s);
+
+// Extra workspace bytes the backward pass needs beyond the forward layout.
+long long bwd_extra_bytes(long long N, int C, int H, int W);
+
+}  // namespace gmi

@@ -1,0 +1,142 @@
+// Point binning: a counting sort of the known points into square bins of
+// b x b output pixels, so that the gather kernels can enumerate the points
+// near any pixel block as a few contiguous row segments.  The paper's
+// truncation ("consider only those known points that are close enough",
+// section 2) is what makes spatial binning sufficient.
+//
+//   bin_count    key = (clamped bin row, bin column); rank = atomic slot in the
+//                bin; flags non-finite inputs and bins holding out-of-frame
+//                points
+//   scan_partial per-block sums of the bin counts
+//   scan_final   exclusive scan of the counts, in place, into bin offsets
+//   bin_scatter  bin-sorted copies of positions (float2) and colours (float4)
+#include "common.cuh"
+
+namespace gmi {
+
+__device__ __forceinline__ void point_bin(const ImageGeom& g, float x, float y, long long& bin,
+                                          bool& oob) {
+  int bx = bin_coord(x, g.inv_b, g.nbx);
+  int by = bin_coord(y, g.inv_b, g.nby);
+  bin = g.bin_base + (long long)by * g.nbx + bx;
+  oob = !(x >= 0.0f && x < (float)g.W && y >= 0.0f && y < (float)g.H);
+}
+
+__global__ void __launch_bounds__(256) bin_count_kernel(KArgs a) {
+  unsigned bad = 0;
+  for (long long ch = blockIdx.x; ch < a.ch_total; ch += gridDim.x) {
+    const int img = find_image<0>(a, ch);
+    const ImageGeom& g = *geom_ptr(a, img);
+    const long long i = (ch - g.ch_base) * kChunk + threadIdx.x;
+    if (i < g.n) {
+      float2 p = reinterpret_cast<const float2*>(g.points)[i];
+      bool fin = isfinite(p.x) && isfinite(p.y);
+      for (int c = 0; c < a.C; ++c) fin = fin && isfinite(g.values[i * a.C + c]);
+      if (!fin) bad = 1;
+      long long bin;
+      bool oob;
+      point_bin(g, p.x, p.y, bin, oob);
+      a.w.rank[g.pt_base + i] = atomicAdd(&a.w.off[bin], 1u);
+      if (oob) a.w.oob[bin] = 1;
+    }
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&a.w.status[kStatusErr], ST_NONFINITE);
+}
+
+// Sum of kScanChunk consecutive counts per block.
+__global__ void __launch_bounds__(256) scan_partial_kernel(const unsigned* __restrict__ cnt, long long nb,
+                                                           unsigned* __restrict__ partials) {
+  __shared__ unsigned red[8];
+  const long long base = (long long)blockIdx.x * kScanChunk;
+  unsigned s = 0;
+  for (int k = threadIdx.x; k < kScanChunk; k += blockDim.x) {
+    long long j = base + k;
+    if (j < nb) s += cnt[j];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    partials[blockIdx.x] = t;
+  }
+}
+
+// Exclusive scan of the counts into offsets (in place); off[nb] = total.
+// Each block adds the sum of all earlier blocks' partials, then scans its own
+// kScanChunk bins (kScanChunk / 256 consecutive bins per thread).
+__global__ void __launch_bounds__(256) scan_final_kernel(unsigned* __restrict__ off, long long nb,
+                                                         const unsigned* __restrict__ partials) {
+  constexpr int kPer = kScanChunk / 256;
+  __shared__ unsigned warp_tot[8];
+  __shared__ unsigned block_prefix;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  unsigned pre = 0;
+  for (int k = tid; k < (int)blockIdx.x; k += blockDim.x) pre += partials[k];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) pre += __shfl_xor_sync(0xffffffffu, pre, o);
+  if (lane == 0) warp_tot[wid] = pre;
+  __syncthreads();
+  if (tid == 0) {
+    unsigned t = 0;
+    for (int w = 0; w < 8; ++w) t += warp_tot[w];
+    block_prefix = t;
+  }
+  __syncthreads();
+  const unsigned bpre = block_prefix;
+  __syncthreads();
+  const long long base = (long long)blockIdx.x * kScanChunk + (long long)tid * kPer;
+  unsigned v[kPer];
+  unsigned s = 0;
+#pragma unroll
+  for (int k = 0; k < kPer; ++k) {
+    long long j = base + k;
+    v[k] = j < nb ? off[j] : 0u;
+    s += v[k];
+  }
+  unsigned incl = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) warp_tot[wid] = incl;
+  __syncthreads();
+  unsigned wpre = 0;
+  for (int w = 0; w < wid; ++w) wpre += warp_tot[w];
+  unsigned run = bpre + wpre + incl - s;
+#pragma unroll
+  for (int k = 0; k < kPer; ++k) {
+    long long j = base + k;
+    if (j < nb) off[j] = run;
+    run += v[k];
+  }
+  if (blockIdx.x == gridDim.x - 1 && tid == blockDim.x - 1) off[nb] = bpre + wpre + incl;
+}
+
+__global__ void __launch_bounds__(256) bin_scatter_kernel(KArgs a) {
+  for (long long ch = blockIdx.x; ch < a.ch_total; ch += gridDim.x) {
+    const int img = find_image<0>(a, ch);
+    const ImageGeom& g = *geom_ptr(a, img);
+    const long long i = (ch - g.ch_base) * kChunk + threadIdx.x;
+    if (i < g.n) {
+      float2 p = reinterpret_cast<const float2*>(g.points)[i];
+      long long bin;
+      bool oob;
+      point_bin(g, p.x, p.y, bin, oob);
+      unsigned dst = a.w.off[bin] + a.w.rank[g.pt_base + i];
+      float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
+      const float* v = g.values + i * a.C;
+      c.x = v[0];
+      if (a.C > 1) c.y = v[1];
+      if (a.C > 2) c.z = v[2];
+      if (a.C > 3) c.w = v[3];
+      a.w.sxy[dst] = p;
+      a.w.sval[dst] = c;
+    }
+  }
+}
+
+}  // namespace gmi

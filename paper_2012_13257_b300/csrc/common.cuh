@@ -1,0 +1,160 @@
+// Device-side definitions shared by the libgmi kernels (sm_103a).
+//
+// Problem (arXiv 2012.13257, section 2): every known point i is an isotropic
+// 2D normal N(mu_i, sigma^2 I) carrying a colour c_i; pixel q of the H x W
+// raster takes c(q) = sum_i c_i N(q|mu_i) / Z_q with Z_q = sum_i N(q|mu_i)
+// (Eq. 1, Eq. 2); channels share the weights.  With one shared sigma the
+// factor 1/(2 pi sigma^2) cancels, so the kernels work with the unnormalised
+// weights 2^(-kappa d^2), kappa = log2(e) / (2 sigma^2).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gmi {
+
+constexpr int kMaxC = 4;
+
+// Bits of the device status word (status[kStatusErr]).
+enum : unsigned {
+  ST_NONFINITE = 1u,   // NaN/Inf among point coordinates or values
+  ST_INTERNAL = 2u,    // a consistency check failed (e.g. a list overflowed)
+  ST_TIMEOUT = 4u,     // a bounded wait gave up
+};
+
+// Slots of the status/counter block at the start of every workspace.
+enum : int {
+  kStatusErr = 0,      // error bits
+  kFarCount = 1,       // micro-tiles queued for the far-field kernel
+  kNearHead = 2,       // next work item for the persistent near kernel
+  kFarHead = 3,        // next far-queue entry for the far kernel
+  kBwdHead = 4,        // next work item for the backward kernels
+  kItemCount = 5,      // near-kernel work items written by the plan kernel
+  kSlotCount = 6,      // partial-sum slots handed out by the plan kernel
+  kStatusWords = 64,
+};
+
+// Per-image geometry and constants, computed on the host.
+struct ImageGeom {
+  const float* points;   // [n,2] (x, y)
+  const float* values;   // [n,C]
+  float* image;          // [H,W,C]
+  float* den;            // [H,W] or null
+  float* shift;          // [H,W] or null
+  long long n;           // points of this image
+  long long pt_base;     // first point in the concatenated point space
+  long long bin_base;    // first bin in the concatenated bin space
+  long long wt_base;     // first warp tile in the concatenated warp-tile space
+  long long ch_base;     // first point chunk in the concatenated chunk space
+  int H, W;
+  int b;                 // bin edge in pixels
+  int nbx, nby;          // bins across / down
+  int mtx, mty;          // micro-tiles across / down
+  int wtx, wty;          // warp tiles across / down (8 x 4 micro-tiles each)
+  float inv_b;           // 1 / b
+  float sigma;
+  float kappa;           // log2(e) / (2 sigma^2)
+  float sk;              // sqrt(kappa)
+  float r2k;             // (k sigma)^2
+  float u_near_max;      // largest nearest-distance bound the near kernel accepts
+  int vec_ok;            // rows of image/den/shift may use 16-byte stores
+  int pad_;
+};
+
+// Device pointers into a workspace.
+struct DevWork {
+  unsigned* status;      // [kStatusWords]
+  unsigned* off;         // [nb_total + 1]: bin counts, scanned in place into offsets
+  unsigned char* oob;    // [nb_total]: bin holds a point outside its image frame
+  unsigned* rank;        // [n_total]: slot of each point inside its bin
+  float2* sxy;           // [n_total]: bin-sorted positions
+  float4* sval;          // [n_total]: bin-sorted colours, padded to 4 channels
+  unsigned* partials;    // scan partial sums
+  uint2* farq;           // [mt_total]: (image, micro-tile) queued for the far kernel
+  uint4* items;          // [cap_items]: near-kernel work items (warp tile, split, splits, slot)
+  unsigned* tile_done;   // [wt_total]: finished splits per warp tile
+  float* slots;          // [cap_slots * slot_floats]: partial sums of split warp tiles
+  const ImageGeom* table;// device descriptor table (batched) or null (single image)
+};
+
+struct KArgs {
+  DevWork w;
+  ImageGeom g0;          // the image when table == null
+  int n_images;
+  int C;
+  long long n_total;     // points over all images
+  long long nb_total;    // bins over all images
+  long long wt_total;    // warp tiles over all images
+  long long ch_total;    // point chunks over all images
+  long long mt_total;    // micro-tiles over all images
+  unsigned cap_items;    // capacity of w.items
+  unsigned cap_slots;    // capacity of w.slots, in slots
+  int mth, mtw;          // micro-tile of the near kernel
+};
+
+constexpr int kChunk = 256;             // points per chunk (one per thread) in the binning kernels
+constexpr int kScanChunk = 1024;        // bins per block in the scan kernels
+constexpr int kSplitMax = 16;           // most work items one warp tile is split into
+constexpr unsigned kSplitTarget = 384;  // candidates per thread per work item
+
+__device__ __forceinline__ const ImageGeom* geom_ptr(const KArgs& a, int img) {
+  return a.w.table ? a.w.table + img : &a.g0;
+}
+
+// Largest image index whose base (selected by Field) is <= idx.
+template <int Field>
+__device__ __forceinline__ int find_image(const KArgs& a, long long idx) {
+  if (a.w.table == nullptr) return 0;
+  int lo = 0, hi = a.n_images - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    long long base = Field == 0 ? a.w.table[mid].ch_base : a.w.table[mid].wt_base;
+    if (base <= idx) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// 2^x on the special-function unit (flushes subnormal results to zero).
+__device__ __forceinline__ float ex2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Error-free sum (Knuth's TwoSum): s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  float aa = __fsub_rn(s, bb);
+  e = __fadd_rn(__fsub_rn(a, aa), __fsub_rn(b, bb));
+}
+
+// Squared distance from the pixel centre (qx, qy) to (px, py), minus a shift
+// m, evaluated with error-free transformations so that the result keeps its
+// absolute accuracy (~1e-7 of the result, not of d^2) when d^2 and m are both
+// large and nearly equal (far-field pixels).
+__device__ __forceinline__ float shifted_sqdist(float qx, float qy, float px, float py, float m) {
+  float sx, ex, sy, ey;
+  two_sum(qx, -px, sx, ex);
+  two_sum(qy, -py, sy, ey);
+  float x2 = __fmul_rn(sx, sx);
+  float x2e = __fmaf_rn(sx, sx, -x2);
+  float y2 = __fmul_rn(sy, sy);
+  float y2e = __fmaf_rn(sy, sy, -y2);
+  float t, te, u, ue;
+  two_sum(x2, y2, t, te);
+  two_sum(t, -m, u, ue);
+  float lo = __fadd_rn(__fadd_rn(te, ue), __fadd_rn(x2e, y2e));
+  lo = __fmaf_rn(2.0f * sx, ex, lo);
+  lo = __fmaf_rn(2.0f * sy, ey, lo);
+  return __fadd_rn(u, lo);
+}
+
+// Bin coordinate of a position along one axis, clamped to [0, nb-1]; NaN maps to 0.
+__device__ __forceinline__ int bin_coord(float x, float inv_b, int nb) {
+  float f = floorf(x * inv_b);
+  f = fminf(fmaxf(f, 0.0f), (float)(nb - 1));   // fmaxf(NaN, 0) == 0
+  return (int)f;
+}
+
+}  // namespace gmi

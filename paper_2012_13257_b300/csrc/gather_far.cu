@@ -1,0 +1,234 @@
+// Far-field gather: exact Eq. 1 / Eq. 2 for micro-tiles that the near kernel
+// could not take (pixels far from every known point, where the unshifted
+// weights 2^(-kappa d^2) would underflow).
+//
+// For such a pixel the relevant points lie in a thin shell
+// m_q <= d^2 <= m_q + k^2 sigma^2 around its nearest distance m_q, and the
+// weights must be evaluated relative to m_q: w = 2^(-kappa (d^2 - m_q)), with
+// d^2 - m_q accurate in absolute terms although d^2 and m_q are large.  One
+// warp handles one queued micro-tile:
+//   A. bracket the smallest Chebyshev window around the micro-tile that holds
+//      any point (doubling, then bisection, on bin counts) and bound
+//      U >= max_q m_q with up to kFarCap of those points;
+//   B. collect every point within Euclidean distance R = sqrt(U + k^2 sigma^2)
+//      of the micro-tile (indices in shared memory, in chunks if many);
+//   C. per pixel, m~_q = min d^2 over the candidates (float32);
+//   D. per pixel, sum w = 2^(-kappa e) c over candidates in the shell, with
+//      e = d^2 - m~_q from error-free transformations (common.cuh).
+// Lanes are split as (pixel slot, part): pixels of the micro-tile times
+// 32 / (MTH * MTW) interleaved parts of the candidate list, combined with
+// shuffles in a fixed order (the result does not depend on scheduling).
+#include "common.cuh"
+
+namespace gmi {
+
+constexpr int kFarCap = 1024;   // candidate indices per warp per chunk
+constexpr int kFarWarps = 4;
+
+struct FarTile {
+  float xa, xb, ya, yb;   // pixel-centre rectangle of the micro-tile
+};
+
+__device__ __forceinline__ void window_bins(const ImageGeom& g, const FarTile& t, float h, int& bx_lo,
+                                            int& bx_hi, int& by_lo, int& by_hi) {
+  bx_lo = bin_coord(t.xa - h, g.inv_b, g.nbx);
+  bx_hi = bin_coord(t.xb + h, g.inv_b, g.nbx);
+  by_lo = bin_coord(t.ya - h, g.inv_b, g.nby);
+  by_hi = bin_coord(t.yb + h, g.inv_b, g.nby);
+}
+
+// Number of points in the bins covering the Chebyshev window of half-width h.
+__device__ unsigned window_count(const KArgs& a, const ImageGeom& g, const FarTile& t, float h) {
+  int bx_lo, bx_hi, by_lo, by_hi;
+  window_bins(g, t, h, bx_lo, bx_hi, by_lo, by_hi);
+  const int lane = threadIdx.x & 31;
+  unsigned s = 0;
+  for (int by = by_lo + lane; by <= by_hi; by += 32) {
+    const long long rowb = g.bin_base + (long long)by * g.nbx;
+    s += a.w.off[rowb + bx_hi + 1] - a.w.off[rowb + bx_lo];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
+
+// Appends to L the indices of the points of the Chebyshev window of
+// half-width h whose squared Euclidean distance to the pixel rectangle is at
+// most r2 (r2 < 0: no filter), numbered [skip, skip + kFarCap) in enumeration
+// order.  Returns how many points pass the filter in total.
+__device__ unsigned collect(const KArgs& a, const ImageGeom& g, const FarTile& t, float h, float r2,
+                            unsigned skip, unsigned* L) {
+  int bx_lo, bx_hi, by_lo, by_hi;
+  window_bins(g, t, h, bx_lo, bx_hi, by_lo, by_hi);
+  const int lane = threadIdx.x & 31;
+  const unsigned full = 0xffffffffu;
+  unsigned total = 0;
+  for (int by0 = by_lo; by0 <= by_hi; by0 += 32) {
+    const int myrow = by0 + lane;
+    unsigned s = 0, e = 0;
+    if (myrow <= by_hi) {
+      const long long rowb = g.bin_base + (long long)myrow * g.nbx;
+      s = a.w.off[rowb + bx_lo];
+      e = a.w.off[rowb + bx_hi + 1];
+    }
+    const int nrows = min(32, by_hi - by0 + 1);
+    for (int r = 0; r < nrows; ++r) {
+      const unsigned rs = __shfl_sync(full, s, r);
+      const unsigned re = __shfl_sync(full, e, r);
+      for (unsigned base = rs; base < re; base += 32) {
+        const unsigned idx = base + lane;
+        bool pass = false;
+        if (idx < re) {
+          if (r2 < 0.0f) {
+            pass = true;
+          } else {
+            const float2 p = a.w.sxy[idx];
+            const float dx = fmaxf(fmaxf(t.xa - p.x, p.x - t.xb), 0.0f);
+            const float dy = fmaxf(fmaxf(t.ya - p.y, p.y - t.yb), 0.0f);
+            pass = dx * dx + dy * dy <= r2;
+          }
+        }
+        const unsigned m = __ballot_sync(full, pass);
+        const unsigned pos = total + __popc(m & ((1u << lane) - 1u));
+        if (pass && pos >= skip && pos < skip + kFarCap) L[pos - skip] = idx;
+        total += __popc(m);
+      }
+    }
+  }
+  __syncwarp();
+  return total;
+}
+
+template <int C>
+__global__ void __launch_bounds__(32 * kFarWarps) far_kernel(KArgs a, int mth, int mtw) {
+  __shared__ unsigned lists[kFarWarps][kFarCap];
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  unsigned* L = lists[wid];
+  const unsigned nfar = a.w.status[kFarCount];
+  const int PS = mth * mtw;              // pixel slots: 8, 16 or 32
+  const int nparts = 32 / PS;
+  const int slot = lane % PS, part = lane / PS;
+  const int pr = slot / mtw, pj = slot % mtw;
+
+  for (;;) {
+    unsigned e = 0;
+    if (lane == 0) e = atomicAdd(&a.w.status[kFarHead], 1u);
+    e = __shfl_sync(full, e, 0);
+    if (e >= nfar) break;
+    const uint2 q = a.w.farq[e];
+    const int img = (int)q.x;
+    const ImageGeom g = a.w.table ? a.w.table[img] : a.g0;
+    const int mt_x = (int)(q.y % (unsigned)g.mtx), mt_y = (int)(q.y / (unsigned)g.mtx);
+    const int x0 = mt_x * mtw, y0 = mt_y * mth;
+    const int nx = min(mtw, g.W - x0), ny = min(mth, g.H - y0);
+    FarTile t;
+    t.xa = (float)x0 + 0.5f;
+    t.xb = (float)(x0 + nx) - 0.5f;
+    t.ya = (float)y0 + 0.5f;
+    t.yb = (float)(y0 + ny) - 0.5f;
+    const bool valid = pr < ny && pj < nx;
+    const float qx = (float)(x0 + pj) + 0.5f, qy = (float)(y0 + pr) + 0.5f;
+
+    // A. smallest non-empty window (bin resolution), then U from its points
+    const float bf = (float)g.b;
+    const float hmax = 2.0f * (float)max(g.W, g.H) + bf;
+    float hi = bf;
+    unsigned cnt = window_count(a, g, t, hi);
+    while (cnt == 0 && hi < hmax) {
+      hi *= 2.0f;
+      cnt = window_count(a, g, t, hi);
+    }
+    float accd[kMaxC + 1];
+#pragma unroll
+    for (int k = 0; k <= kMaxC; ++k) accd[k] = 0.0f;
+    float mshift = 0.0f;
+    if (cnt > 0) {
+      float lo = hi * 0.5f;
+      if (hi <= bf) lo = 0.0f;
+      while (hi - lo > bf) {
+        const float mid = floorf((lo + hi) * 0.5f / bf) * bf;
+        if (mid <= lo) break;
+        if (window_count(a, g, t, mid) > 0) hi = mid; else lo = mid;
+      }
+      const unsigned ns = min(collect(a, g, t, hi, -1.0f, 0u, L), (unsigned)kFarCap);
+      float best = INFINITY;
+      for (unsigned k = part; k < ns; k += nparts) {
+        const float2 p = a.w.sxy[L[k]];
+        const float dx = qx - p.x, dy = qy - p.y;
+        best = fminf(best, fmaf(dx, dx, dy * dy));
+      }
+      for (int o = PS; o < 32; o <<= 1) best = fminf(best, __shfl_xor_sync(full, best, o));
+      float U = valid ? best : 0.0f;
+      for (int o = 16; o > 0; o >>= 1) U = fmaxf(U, __shfl_xor_sync(full, U, o));
+      __syncwarp();
+
+      // B. candidates within R of the micro-tile
+      const float R2 = (U + g.r2k) * (1.0f + 1e-6f) + 1e-6f;
+      const float R = sqrtf(R2);
+      const unsigned total = collect(a, g, t, R, R2, 0u, L);
+
+      // C. nearest squared distance per pixel
+      float m = INFINITY;
+      for (unsigned skip = 0; skip < total; skip += kFarCap) {
+        if (skip > 0) collect(a, g, t, R, R2, skip, L);
+        const unsigned n = min(total - skip, (unsigned)kFarCap);
+        for (unsigned k = part; k < n; k += nparts) {
+          const float2 p = a.w.sxy[L[k]];
+          const float dx = qx - p.x, dy = qy - p.y;
+          m = fminf(m, fmaf(dx, dx, dy * dy));
+        }
+        __syncwarp();
+      }
+      for (int o = PS; o < 32; o <<= 1) m = fminf(m, __shfl_xor_sync(full, m, o));
+      mshift = m;
+
+      // D. shell sum with shifted, compensated exponents
+      const float thr = (m + g.r2k) * (1.0f + 4e-7f) + 1e-30f;
+      for (unsigned skip = 0; skip < total; skip += kFarCap) {
+        if (skip > 0 || total > (unsigned)kFarCap) collect(a, g, t, R, R2, skip, L);
+        const unsigned n = min(total - skip, (unsigned)kFarCap);
+        for (unsigned k = part; k < n; k += nparts) {
+          const unsigned idx = L[k];
+          const float2 p = a.w.sxy[idx];
+          const float dx = qx - p.x, dy = qy - p.y;
+          if (fmaf(dx, dx, dy * dy) <= thr) {
+            const float ee = shifted_sqdist(qx, qy, p.x, p.y, m);
+            const float w = ex2(-g.kappa * ee);
+            const float4 cv = a.w.sval[idx];
+            accd[0] += w;
+            accd[1] = fmaf(w, cv.x, accd[1]);
+            if (C > 1) accd[2] = fmaf(w, cv.y, accd[2]);
+            if (C > 2) accd[3] = fmaf(w, cv.z, accd[3]);
+            if (C > 3) accd[4] = fmaf(w, cv.w, accd[4]);
+          }
+        }
+        __syncwarp();
+      }
+#pragma unroll
+      for (int k = 0; k <= C; ++k)
+        for (int o = PS; o < 32; o <<= 1) accd[k] += __shfl_xor_sync(full, accd[k], o);
+    }
+    if (valid && part == 0) {
+      const long long pix = (long long)(y0 + pr) * g.W + (x0 + pj);
+      const float inv = accd[0] > 0.0f ? 1.0f / accd[0] : 0.0f;
+#pragma unroll
+      for (int ch = 0; ch < C; ++ch) g.image[pix * C + ch] = accd[1 + ch] * inv;
+      if (g.den) g.den[pix] = accd[0];
+      if (g.shift) g.shift[pix] = mshift;
+    }
+    __syncwarp();
+  }
+}
+
+cudaError_t launch_far(const KArgs& a, int mth, int mtw, int grid, cudaStream_t s) {
+  switch (a.C) {
+    case 1: far_kernel<1><<<grid, 32 * kFarWarps, 0, s>>>(a, mth, mtw); break;
+    case 2: far_kernel<2><<<grid, 32 * kFarWarps, 0, s>>>(a, mth, mtw); break;
+    case 3: far_kernel<3><<<grid, 32 * kFarWarps, 0, s>>>(a, mth, mtw); break;
+    default: far_kernel<4><<<grid, 32 * kFarWarps, 0, s>>>(a, mth, mtw); break;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace gmi

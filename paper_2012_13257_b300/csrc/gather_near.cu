@@ -1,0 +1,443 @@
+// Near-field gather: the hot loop of the forward pass (Eq. 1 and Eq. 2).
+//
+// Each thread owns an MTH x MTW micro-tile of output pixels and keeps the
+// numerators (C per pixel) and the denominator of Eq. 1 in registers.  The
+// isotropic Gaussian factorises, 2^(-kappa d^2) = 2^(-kappa dx^2) 2^(-kappa dy^2),
+// so one candidate point costs MTW + MTH exponentials (on the SFU) and
+// (C + 1) fused multiply-adds per pixel: den += gy*gx, num_c += gy*(gx*c_c).
+//
+// Which points are candidates ("close enough", section 2): a pixel q needs
+// every point with d^2 <= m_q + k^2 sigma^2, m_q being its squared distance
+// to the nearest point; anything farther weighs less than e^{-k^2/2} of the
+// nearest point.  The thread first bounds m_q from above for its pixels with
+// the bin occupancy (a non-empty bin whose points all lie inside it contains
+// a point no farther than its farthest corner), giving U >= max_q m_q, then
+// sweeps every bin row that can hold a point within R = sqrt(U + k^2 sigma^2)
+// of its pixels.  Bins are row-major sorted, so each bin row contributes one
+// contiguous segment of the sorted point arrays.
+//
+// Range: weights are taken unshifted (no per-pixel subtraction of m_q), which
+// is exact as long as every weight that matters stays a normal float:
+// kappa * U <= 100 keeps the nearest weight >= 2^-100 and every weight within
+// the radius >= 2^-126.  Micro-tiles that fail this (far from every point)
+// are queued for the far-field kernel, which shifts per pixel.
+//
+// Load balance: a plan kernel estimates every warp tile's per-thread
+// candidate count and cuts heavy tiles (dense clusters, wide sigma) into up to
+// kSplitMax work items over each thread's candidate sequence; the last item of
+// a tile to finish adds the partial sums in split order (deterministic).
+//
+// In truncated mode (the literal "radius k sigma" reading) R = k sigma, each
+// pixel keeps only points with d^2 <= k^2 sigma^2, and nothing is queued.
+#include "common.cuh"
+
+namespace gmi {
+
+constexpr int kRingMax = 3;   // bin rings searched for the nearest-distance bound
+
+// Upper bound on max_q m_q over the micro-tile's valid pixels from bin
+// occupancy; +inf when some pixel has no usable bin within kRingMax rings.
+template <int MTH, int MTW>
+__device__ float near_bound(const KArgs& a, const ImageGeom& g, int x0, int y0, int nx, int ny) {
+  const float bf = (float)g.b;
+  const float xq0 = (float)x0 + 0.5f, yq0 = (float)y0 + 0.5f;
+  const int bx0 = (int)(xq0 * g.inv_b), bx1 = (int)((xq0 + (float)(nx - 1)) * g.inv_b);
+  const int by0 = (int)(yq0 * g.inv_b), by1 = (int)((yq0 + (float)(ny - 1)) * g.inv_b);
+  float best[MTH][MTW];
+#pragma unroll
+  for (int r = 0; r < MTH; ++r)
+#pragma unroll
+    for (int j = 0; j < MTW; ++j) best[r][j] = (r < ny && j < nx) ? INFINITY : 0.0f;
+
+  for (int ring = 1; ring <= kRingMax; ++ring) {
+    const int ya = max(by0 - ring, 0), yb = min(by1 + ring, g.nby - 1);
+    const int xa = max(bx0 - ring, 0), xb = min(bx1 + ring, g.nbx - 1);
+    for (int by = ya; by <= yb; ++by) {
+      const bool edge_row = (by == by0 - ring) || (by == by1 + ring);
+      const long long rowb = g.bin_base + (long long)by * g.nbx;
+      float cy[MTH];
+#pragma unroll
+      for (int r = 0; r < MTH; ++r) {
+        float q = yq0 + (float)r;
+        float d0 = q - (float)by * bf, d1 = q - (float)(by + 1) * bf;
+        cy[r] = fmaxf(d0 * d0, d1 * d1);
+      }
+      unsigned prev = a.w.off[rowb + xa];
+      for (int bx = xa; bx <= xb; ++bx) {
+        const unsigned nxt = a.w.off[rowb + bx + 1];
+        const bool on_ring = edge_row || bx == bx0 - ring || bx == bx1 + ring;
+        const bool usable = (ring == 1 || on_ring) && nxt > prev && a.w.oob[rowb + bx] == 0;
+        prev = nxt;
+        if (!usable) continue;
+#pragma unroll
+        for (int j = 0; j < MTW; ++j) {
+          float q = xq0 + (float)j;
+          float d0 = q - (float)bx * bf, d1 = q - (float)(bx + 1) * bf;
+          float cx = fmaxf(d0 * d0, d1 * d1);
+#pragma unroll
+          for (int r = 0; r < MTH; ++r) best[r][j] = fminf(best[r][j], cx + cy[r]);
+        }
+      }
+    }
+    float u = 0.0f;
+#pragma unroll
+    for (int r = 0; r < MTH; ++r)
+#pragma unroll
+      for (int j = 0; j < MTW; ++j) u = fmaxf(u, best[r][j]);
+    if (u < INFINITY) return u;
+  }
+  return INFINITY;
+}
+
+// Candidate window of one thread: pixel-centre rectangle and radius.
+struct LaneWin {
+  float xq0, xq1, yq0, yq1;  // first / last pixel centres of the micro-tile
+  float R2;                  // squared radius
+  int by_lo, by_hi;          // bin rows that can hold a point within the radius
+};
+
+__device__ __forceinline__ LaneWin lane_window(const ImageGeom& g, int x0, int y0, int nx, int ny, float R2) {
+  LaneWin w;
+  w.xq0 = (float)x0 + 0.5f;
+  w.yq0 = (float)y0 + 0.5f;
+  w.xq1 = w.xq0 + (float)(nx - 1);
+  w.yq1 = w.yq0 + (float)(ny - 1);
+  w.R2 = R2;
+  const float R = sqrtf(R2);
+  w.by_lo = bin_coord(w.yq0 - R, g.inv_b, g.nby);
+  w.by_hi = bin_coord(w.yq1 + R, g.inv_b, g.nby);
+  return w;
+}
+
+// Sorted-array segment of bin row `by` that can hold a point within the
+// radius of the thread's pixels: the row's y-distance to the pixel rows
+// narrows its x-extent (border rows can hold clamped out-of-frame points, so
+// they are kept whole).
+__device__ __forceinline__ void row_segment(const KArgs& a, const ImageGeom& g, const LaneWin& w, int by,
+                                            unsigned& s, unsigned& e) {
+  const float bf = (float)g.b;
+  float dyr = 0.0f;
+  if (by > 0 && by < g.nby - 1) dyr = fmaxf(fmaxf((float)by * bf - w.yq1, w.yq0 - (float)(by + 1) * bf), 0.0f);
+  const float hx = sqrtf(fmaxf(w.R2 - dyr * dyr, 0.0f));
+  const int bx_lo = bin_coord(w.xq0 - hx, g.inv_b, g.nbx);
+  const int bx_hi = bin_coord(w.xq1 + hx, g.inv_b, g.nbx);
+  const long long rowb = g.bin_base + (long long)by * g.nbx;
+  s = __ldg(&a.w.off[rowb + bx_lo]);
+  e = __ldg(&a.w.off[rowb + bx_hi + 1]);
+}
+
+// Plan: one warp per warp tile estimates each thread's candidate count (with
+// the radius a dense neighbourhood gives) and splits the tile into
+// S = ceil(max / kSplitTarget) work items, so that no single thread walks
+// thousands of candidates while the rest of the GPU idles.
+__global__ void __launch_bounds__(128) near_plan_kernel(KArgs a, int trunc) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const long long wt = (long long)blockIdx.x * 4 + (threadIdx.x >> 5);
+  if (wt >= a.wt_total) return;
+  const int img = find_image<1>(a, wt);
+  const ImageGeom g = a.w.table ? a.w.table[img] : a.g0;
+  const long long lt = wt - g.wt_base;
+  const int mt_x = (int)(lt % g.wtx) * 8 + (lane & 7);
+  const int mt_y = (int)(lt / g.wtx) * 4 + (lane >> 3);
+  const int x0 = mt_x * a.mtw, y0 = mt_y * a.mth;
+  unsigned cnt = 0;
+  if (x0 < g.W && y0 < g.H) {
+    const float bf = (float)g.b;
+    const float R2 = trunc ? g.r2k : g.r2k + 2.0f * bf * bf;
+    const LaneWin w = lane_window(g, x0, y0, min(a.mtw, g.W - x0), min(a.mth, g.H - y0), R2);
+    for (int by = w.by_lo; by <= w.by_hi; ++by) {
+      unsigned s, e;
+      row_segment(a, g, w, by, s, e);
+      cnt += e - s;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) cnt = max(cnt, __shfl_xor_sync(full, cnt, o));
+  if (lane == 0) {
+    unsigned S = min((cnt + kSplitTarget - 1) / kSplitTarget, (unsigned)kSplitMax);
+    if (S < 1) S = 1;
+    unsigned slot = 0xffffffffu;
+    if (S > 1) {
+      slot = atomicAdd(&a.w.status[kSlotCount], S);
+      if (slot + S > a.cap_slots) {   // out of partial-sum slots: keep the tile whole
+        S = 1;
+        slot = 0xffffffffu;
+      }
+    }
+    const unsigned base = atomicAdd(&a.w.status[kItemCount], S);
+    for (unsigned k = 0; k < S && base + k < a.cap_items; ++k)
+      a.w.items[base + k] = make_uint4((unsigned)wt, k, S, S > 1 ? slot + k : 0xffffffffu);
+  }
+}
+
+template <int MTH, int MTW, int C, bool TRUNC>
+__global__ void __launch_bounds__(128) near_kernel(KArgs a) {
+  constexpr int NA = MTH * MTW * (C + 1);   // accumulators per thread
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int lx = lane & 7, ly = lane >> 3;
+  const unsigned n_items = min(a.w.status[kItemCount], a.cap_items);
+  for (;;) {
+    unsigned t = 0;
+    if (lane == 0) t = atomicAdd(&a.w.status[kNearHead], 1u);
+    t = __shfl_sync(full, t, 0);
+    if (t >= n_items) break;
+    const uint4 item = a.w.items[t];
+    const long long wt = (long long)item.x;
+    const unsigned split = item.y, S = item.z, slot = item.w;
+    const int img = find_image<1>(a, wt);
+    const ImageGeom g = a.w.table ? a.w.table[img] : a.g0;
+    const long long lt = wt - g.wt_base;
+    const int mt_x = (int)(lt % g.wtx) * 8 + lx;
+    const int mt_y = (int)(lt / g.wtx) * 4 + ly;
+    const int x0 = mt_x * MTW, y0 = mt_y * MTH;
+    bool active = x0 < g.W && y0 < g.H;
+    const int nx = active ? min(MTW, g.W - x0) : 0;
+    const int ny = active ? min(MTH, g.H - y0) : 0;
+
+    float R2 = g.r2k;
+    if (!TRUNC) {
+      float U = active ? near_bound<MTH, MTW>(a, g, x0, y0, nx, ny) : 0.0f;
+      const bool far = active && !(U <= g.u_near_max);
+      if (split == 0) {
+        const unsigned fm = __ballot_sync(full, far);
+        if (fm) {
+          const int leader = __ffs(fm) - 1;
+          unsigned base = 0;
+          if (lane == leader) base = atomicAdd(&a.w.status[kFarCount], (unsigned)__popc(fm));
+          base = __shfl_sync(full, base, leader);
+          if (far)
+            a.w.farq[base + __popc(fm & ((1u << lane) - 1u))] =
+                make_uint2((unsigned)img, (unsigned)(mt_y * g.mtx + mt_x));
+        }
+      }
+      if (far) active = false;
+      R2 = U + g.r2k;
+    }
+
+    float acc[NA];   // per pixel (r, j): [den, num_0 .. num_{C-1}]
+#pragma unroll
+    for (int k = 0; k < NA; ++k) acc[k] = 0.0f;
+
+    if (active) {
+      const LaneWin w = lane_window(g, x0, y0, nx, ny, R2);
+      // this work item's share [lo, hi) of the thread's candidate sequence
+      unsigned lo = 0, hi = 0xffffffffu;
+      if (S > 1) {
+        unsigned n = 0;
+        for (int by = w.by_lo; by <= w.by_hi; ++by) {
+          unsigned s0, e0;
+          row_segment(a, g, w, by, s0, e0);
+          n += e0 - s0;
+        }
+        lo = (unsigned)(((unsigned long long)n * split) / S);
+        hi = (unsigned)(((unsigned long long)n * (split + 1)) / S);
+      }
+      const float sk = g.sk;
+      const float neg_thr = -g.kappa * g.r2k;   // truncated mode: keep -kappa d^2 >= this
+      const float2* __restrict__ sxy = a.w.sxy;
+      const float4* __restrict__ sval = a.w.sval;
+      int by = w.by_lo - 1;
+      unsigned i = 0, end = 0, cum = 0;
+      for (;;) {
+        while (i >= end) {
+          if (++by > w.by_hi || cum >= hi) goto done;
+          unsigned s0, e0;
+          row_segment(a, g, w, by, s0, e0);
+          const unsigned len = e0 - s0, rs = cum;
+          cum += len;
+          i = s0 + (lo > rs ? min(lo - rs, len) : 0u);
+          end = s0 + (hi > rs ? min(hi - rs, len) : 0u);
+        }
+        {
+          const float2 p = __ldg(&sxy[i]);
+          const float4 cv = __ldg(&sval[i]);
+          ++i;
+          const float c4[4] = {cv.x, cv.y, cv.z, cv.w};
+          const float u = (w.xq0 - p.x) * sk;
+          const float v = (w.yq0 - p.y) * sk;
+          float ax[MTW], gx[MTW], ay[MTH], gy[MTH];
+#pragma unroll
+          for (int j = 0; j < MTW; ++j) {
+            const float tt = u + (float)j * sk;
+            ax[j] = -tt * tt;
+            gx[j] = ex2(ax[j]);
+          }
+#pragma unroll
+          for (int r = 0; r < MTH; ++r) {
+            const float tt = v + (float)r * sk;
+            ay[r] = -tt * tt;
+            gy[r] = ex2(ay[r]);
+          }
+          if (!TRUNC) {
+            float hxc[MTW][C];
+#pragma unroll
+            for (int j = 0; j < MTW; ++j)
+#pragma unroll
+              for (int ch = 0; ch < C; ++ch) hxc[j][ch] = gx[j] * c4[ch];
+#pragma unroll
+            for (int r = 0; r < MTH; ++r)
+#pragma unroll
+              for (int j = 0; j < MTW; ++j) {
+                float* q = acc + (r * MTW + j) * (C + 1);
+                q[0] = fmaf(gy[r], gx[j], q[0]);
+#pragma unroll
+                for (int ch = 0; ch < C; ++ch) q[1 + ch] = fmaf(gy[r], hxc[j][ch], q[1 + ch]);
+              }
+          } else {
+#pragma unroll
+            for (int r = 0; r < MTH; ++r)
+#pragma unroll
+              for (int j = 0; j < MTW; ++j) {
+                float* q = acc + (r * MTW + j) * (C + 1);
+                const float wgt = (ax[j] + ay[r] >= neg_thr) ? gx[j] * gy[r] : 0.0f;
+                q[0] += wgt;
+#pragma unroll
+                for (int ch = 0; ch < C; ++ch) q[1 + ch] = fmaf(wgt, c4[ch], q[1 + ch]);
+              }
+          }
+        }
+      }
+    done:;
+    }
+
+    bool finish = true;
+    if (S > 1) {
+      // split tile: publish this item's partial sums; the last item to finish
+      // adds all of them in split order and writes the pixels
+      float* mine = a.w.slots + (size_t)slot * (size_t)(32 * NA);
+      if (active) {
+#pragma unroll
+        for (int k = 0; k < NA; ++k) mine[k * 32 + lane] = acc[k];
+      }
+      __threadfence();
+      __syncwarp();
+      unsigned prev = 0;
+      if (lane == 0) prev = atomicAdd(&a.w.tile_done[wt], 1u);
+      prev = __shfl_sync(full, prev, 0);
+      finish = prev == S - 1;
+      if (finish) {
+        __threadfence();
+        if (active) {
+          const float* first = a.w.slots + (size_t)(slot - split) * (size_t)(32 * NA);
+#pragma unroll
+          for (int k = 0; k < NA; ++k) acc[k] = 0.0f;
+          for (unsigned q = 0; q < S; ++q) {
+            const float* part = first + (size_t)q * (size_t)(32 * NA);
+#pragma unroll
+            for (int k = 0; k < NA; ++k) acc[k] += __ldcg(&part[k * 32 + lane]);
+          }
+        }
+      }
+    }
+    if (!(finish && active)) continue;
+
+    // normalise (Eq. 1) and store
+#pragma unroll
+    for (int r = 0; r < MTH; ++r) {
+      if (r >= ny) break;
+      float outv[MTW * C];
+      float denv[MTW];
+#pragma unroll
+      for (int j = 0; j < MTW; ++j) {
+        const float* q = acc + (r * MTW + j) * (C + 1);
+        const float d = q[0];
+        const float inv = d > 0.0f ? 1.0f / d : 0.0f;
+        denv[j] = d;
+#pragma unroll
+        for (int ch = 0; ch < C; ++ch) outv[j * C + ch] = q[1 + ch] * inv;
+      }
+      const long long row = (long long)(y0 + r) * g.W + x0;
+      if (g.vec_ok && nx == MTW) {
+        float4* o = reinterpret_cast<float4*>(g.image + row * C);
+#pragma unroll
+        for (int k = 0; k < MTW * C / 4; ++k) o[k] = make_float4(outv[4 * k], outv[4 * k + 1], outv[4 * k + 2], outv[4 * k + 3]);
+        if (g.den) {
+          float4* dd = reinterpret_cast<float4*>(g.den + row);
+#pragma unroll
+          for (int k = 0; k < MTW / 4; ++k) dd[k] = make_float4(denv[4 * k], denv[4 * k + 1], denv[4 * k + 2], denv[4 * k + 3]);
+        }
+        if (g.shift) {
+          float4* ss = reinterpret_cast<float4*>(g.shift + row);
+#pragma unroll
+          for (int k = 0; k < MTW / 4; ++k) ss[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < MTW; ++j) {
+          if (j >= nx) break;
+#pragma unroll
+          for (int ch = 0; ch < C; ++ch) g.image[(row + j) * C + ch] = outv[j * C + ch];
+          if (g.den) g.den[row + j] = denv[j];
+          if (g.shift) g.shift[row + j] = 0.0f;
+        }
+      }
+    }
+  }
+}
+
+// Launch helpers: one instantiation per (micro-tile, channels, mode).
+template <int MTH, int MTW, int C>
+static cudaError_t launch_near_c(const KArgs& a, bool trunc, int grid, cudaStream_t s) {
+  if (trunc) near_kernel<MTH, MTW, C, true><<<grid, 128, 0, s>>>(a);
+  else near_kernel<MTH, MTW, C, false><<<grid, 128, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int MTH, int MTW>
+static cudaError_t launch_near_mt(const KArgs& a, bool trunc, int grid, cudaStream_t s) {
+  switch (a.C) {
+    case 1: return launch_near_c<MTH, MTW, 1>(a, trunc, grid, s);
+    case 2: return launch_near_c<MTH, MTW, 2>(a, trunc, grid, s);
+    case 3: return launch_near_c<MTH, MTW, 3>(a, trunc, grid, s);
+    default: return launch_near_c<MTH, MTW, 4>(a, trunc, grid, s);
+  }
+}
+
+cudaError_t launch_near_plan(const KArgs& a, bool trunc, cudaStream_t s) {
+  const long long blocks = (a.wt_total + 3) / 4;
+  near_plan_kernel<<<(unsigned)blocks, 128, 0, s>>>(a, trunc ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_near(const KArgs& a, int mth, int mtw, bool trunc, int grid, cudaStream_t s) {
+  if (mth == 4 && mtw == 4) return launch_near_mt<4, 4>(a, trunc, grid, s);
+  if (mth == 4 && mtw == 8) return launch_near_mt<4, 8>(a, trunc, grid, s);
+  if (mth == 2 && mtw == 4) return launch_near_mt<2, 4>(a, trunc, grid, s);
+  return cudaErrorInvalidValue;
+}
+
+// Resident 128-thread blocks per SM for a near-kernel instantiation (cached).
+template <int MTH, int MTW, int C>
+static int occ_c(bool trunc) {
+  int n = 0;
+  if (trunc) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, near_kernel<MTH, MTW, C, true>, 128, 0);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, near_kernel<MTH, MTW, C, false>, 128, 0);
+  return n > 0 ? n : 1;
+}
+
+template <int MTH, int MTW>
+static int occ_mt(int C, bool trunc) {
+  switch (C) {
+    case 1: return occ_c<MTH, MTW, 1>(trunc);
+    case 2: return occ_c<MTH, MTW, 2>(trunc);
+    case 3: return occ_c<MTH, MTW, 3>(trunc);
+    default: return occ_c<MTH, MTW, 4>(trunc);
+  }
+}
+
+int near_blocks_per_sm(int mth, int mtw, int C, bool trunc) {
+  static int cache[3][5][2];
+  const int v = (mth == 4 && mtw == 8) ? 1 : (mth == 2 ? 2 : 0);
+  const int c = C < 1 ? 1 : (C > 4 ? 4 : C);
+  int& slot = cache[v][c][trunc ? 1 : 0];
+  if (slot == 0) {
+    if (v == 1) slot = occ_mt<4, 8>(c, trunc);
+    else if (v == 2) slot = occ_mt<2, 4>(c, trunc);
+    else slot = occ_mt<4, 4>(c, trunc);
+  }
+  return slot;
+}
+
+}  // namespace gmi

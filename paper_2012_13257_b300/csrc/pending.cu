@@ -1,0 +1,29 @@
+// Entry points whose kernels are not built yet: they reject every call.
+#include "api_internal.h"
+
+namespace gmi {
+long long bwd_extra_bytes(long long, int, int, int) { return 0; }
+}  // namespace gmi
+
+extern "C" {
+gmi_status gmi_backward(const float*, const float*, int64_t, int, int, int, const gmi_params*, const float*,
+                        const float*, const float*, const float*, float*, float*, float*, void*, size_t,
+                        gmi_stream_t) { return GMI_ERR_UNSUPPORTED; }
+gmi_status gmi_batch_plan_create(int, int64_t, int64_t, int, const gmi_params*, gmi_batch_plan** plan) {
+  if (plan) *plan = nullptr;
+  return GMI_ERR_UNSUPPORTED;
+}
+gmi_status gmi_batch_plan_destroy(gmi_batch_plan*) { return GMI_OK; }
+size_t gmi_batch_plan_bytes(const gmi_batch_plan*) { return 0; }
+gmi_status gmi_forward_batched(gmi_batch_plan*, const gmi_image_desc*, int, int, gmi_stream_t) { return GMI_ERR_UNSUPPORTED; }
+gmi_status gmi_server_config_default(gmi_server_config*) { return GMI_ERR_UNSUPPORTED; }
+gmi_status gmi_server_create(const gmi_server_config*, gmi_server** out) {
+  if (out) *out = nullptr;
+  return GMI_ERR_UNSUPPORTED;
+}
+gmi_status gmi_server_submit(gmi_server*, const float*, const float*, int64_t, int, int, float, float*, uint64_t*) { return GMI_ERR_UNSUPPORTED; }
+gmi_status gmi_server_wait(gmi_server*, uint64_t, int, double*) { return GMI_ERR_UNSUPPORTED; }
+gmi_status gmi_server_poll(gmi_server*, uint64_t) { return GMI_ERR_UNSUPPORTED; }
+gmi_status gmi_server_stats(gmi_server*, uint64_t*, uint64_t*, uint64_t*, size_t*) { return GMI_ERR_UNSUPPORTED; }
+gmi_status gmi_server_destroy(gmi_server*) { return GMI_OK; }
+}

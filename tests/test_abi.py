@@ -1,0 +1,87 @@
+"""The C-ABI library loads and exports every entry point include/gmi.h
+declares; host-side argument checks reject bad calls before any GPU work.
+No compute call is made (this runs without a GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2012_13257_b300 import _lib
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "gmi.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s+\**\s*(gmi_[a-z0-9_]+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("gmi_forward", "gmi_backward", "gmi_workspace_size", "gmi_forward_batched",
+                     "gmi_server_create", "gmi_server_submit", "gmi_server_wait"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = _lib.load()
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+    assert set(declared_functions()) == set(_lib.SIGNATURES)
+
+
+def test_version_and_status_strings():
+    lib = _lib.load()
+    assert b"sm_103a" in lib.gmi_version()
+    for code, name in _lib.STATUS_NAMES.items():
+        assert lib.gmi_status_string(code).decode() == name
+
+
+def test_params_default():
+    p = _lib.Params()
+    assert _lib.load().gmi_params_default(ctypes.byref(p)) == 0
+    assert p.sigma == 1.0 and p.radius_sigmas == 6.0 and p.mode == 0 and p.flags == 0
+
+
+def _ws(N, C, H, W, **kw):
+    p = _lib.make_params(kw.pop("sigma", 1.0), **kw)
+    n = ctypes.c_size_t(0)
+    st = _lib.load().gmi_workspace_size(N, C, H, W, ctypes.byref(p), ctypes.byref(n))
+    return st, n.value
+
+
+def test_workspace_size_checks():
+    st, n = _ws(4096, 3, 64, 64)
+    assert st == 0 and n > 0 and n % 256 == 0
+    st2, n2 = _ws(8192, 3, 64, 64)
+    assert st2 == 0 and n2 > n
+    assert _ws(-1, 3, 8, 8)[0] == 1
+    assert _ws(10, 3, 0, 8)[0] == 1
+    assert _ws(10, 5, 8, 8)[0] == 7
+    assert _ws(10, 0, 8, 8)[0] == 7
+    assert _ws(10, 3, 8, 8, sigma=0.0)[0] == 1
+    assert _ws(10, 3, 8, 8, sigma=float("nan"))[0] == 1
+    assert _ws(10, 3, 8, 8, radius_sigmas=-1.0)[0] == 1
+    assert _ws(10, 3, 8, 8, mode=7)[0] == 1
+
+
+def test_forward_rejects_bad_arguments_without_launching():
+    lib = _lib.load()
+    p = _lib.make_params(1.0)
+    assert lib.gmi_forward(None, None, 10, 3, 8, 8, ctypes.byref(p), None, None, None, None, 0, None) == 1
+    bad = _lib.make_params(-2.0)
+    assert lib.gmi_forward(None, None, 10, 3, 8, 8, ctypes.byref(bad), 256, None, None, 256, 1 << 20, None) == 1
+    # workspace too small / misaligned: rejected before anything is enqueued (the
+    # fake pointers are never dereferenced)
+    assert lib.gmi_forward(256, 256, 10, 3, 8, 8, ctypes.byref(p), 256, None, None, 256, 16, None) == 3
+    assert lib.gmi_forward(256, 256, 10, 3, 8, 8, ctypes.byref(p), 256, None, None, 257, 1 << 20, None) == 3
+
+
+def test_package_fails_loudly_without_the_library(monkeypatch):
+    monkeypatch.setattr(_lib, "_lib", None)
+    monkeypatch.setattr(_lib, "LIB_PATH", "/nonexistent/libgmi.so")
+    with pytest.raises(ImportError):
+        _lib.load()
