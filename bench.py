@@ -1,0 +1,351 @@
+"""Benchmark of the Gaussian-mixture interpolation hot path on B300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gmi|reference]
+
+Headline workload (one "step" = one plain forward pass, binning included, of
+one synthetic image): a 512^2 source grid jittered by U[-0.5, 0.5] px,
+upsampled x2 to 1024 x 1024 x 3 float32 with sigma = 1 px, exact mode, k = 6.
+``value`` is interpolated output Mpix/s (H*W per step, all ranks), timed with
+CUDA events per step on the launching stream with L2 flushed (256 MB write)
+between steps; ``e2e`` repeats the measurement through the public call with the
+host<->device copies of inputs and image inside the timed region.
+
+Further objects on the same line: the dominant kernel's roofline, the FP64
+oracle's CPU throughput, SM clocks sampled during the timed region and, as
+they are built, the batched, fwd+bwd and serving workloads.
+
+``--impl reference`` times the FP64 oracle (the CPU reference of this build)
+on a bounded pixel sample of the same workload, per step.
+
+Multi-GPU: replicas only (each rank runs the same workload on its own GPU;
+weak scaling); ranks synchronise with a barrier and the max time is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "interpolated Mpix/s (batched+served vs plain launch); p50/p99 latency; fwd+bwd Mpix/s"
+WORKLOAD = ("upsample_1024: 512^2 source grid jittered U[-0.5,0.5] px -> 1024x1024x3 float32, "
+            "sigma=1.0 px, exact mode, k=6, values from a smooth random field")
+L2_FLUSH_BYTES = 256 << 20
+SFU_PER_SM_CLK = 16      # ex2 results per SM per clock (cc 10.x throughput table)
+FP32_PER_SM_CLK = 128    # FP32 lanes per SM per clock
+SM_MAX_MHZ = 2032.0      # B300 maximum SM clock
+LAUNCHES_PER_FORWARD = 7 # count, scan x2, scatter, plan, near, far
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gmi", choices=["gmi", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="headline workload only")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+class Dist:
+    """Barrier and max-reduce over ranks (NCCL when launched under torchrun)."""
+
+    def __init__(self, world, device):
+        self.world = world
+        self.device = device
+        if world > 1:
+            import torch.distributed as dist
+            dist.init_process_group("nccl", device_id=device)
+            self.dist = dist
+
+    def barrier(self):
+        if self.world > 1:
+            self.dist.barrier()
+
+    def max(self, v: float) -> float:
+        if self.world == 1:
+            return v
+        import torch
+        t = torch.tensor([v], dtype=torch.float64, device=self.device)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.world > 1:
+            self.dist.destroy_process_group()
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def algorithmic_pairs(im, k=6.0):
+    """Pairs (pixel, point) with d^2 <= m_q + k^2 sigma^2 (the radius rule of
+    exact mode): the work the method must do, counted with a k-d tree."""
+    from scipy.spatial import cKDTree
+    yy, xx = np.meshgrid(np.arange(im.H) + 0.5, np.arange(im.W) + 0.5, indexing="ij")
+    q = np.stack([xx.ravel(), yy.ravel()], 1)
+    tree = cKDTree(im.points.astype(np.float64))
+    d, _ = tree.query(q, workers=-1)
+    rad = np.sqrt(d * d + (k * im.sigma) ** 2) * (1 + 1e-9)
+    cnt = tree.query_ball_point(q, rad, return_length=True, workers=-1)
+    return int(np.sum(cnt))
+
+
+def near_kernel_traffic():
+    """DRAM bytes per launch of the near kernel from the committed ncu summary,
+    or None when the kernel source changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "near_kernel_upsample_1024.txt")
+    src = os.path.join(ROOT, "paper_2012_13257_b300", "csrc", "gather_near.cu")
+    if not os.path.exists(path):
+        return None
+    want = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    kv = {}
+    for line in open(path):
+        if ":" in line:
+            k_, v_ = line.split(":", 1)
+            kv[k_.strip()] = v_.strip()
+    if kv.get("source_sha256_16") != want:
+        return None
+    try:
+        return float(kv["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def cpu_baseline(im, target_s=12.0):
+    """FP64 oracle (as it stands) on a bounded random pixel sample of the
+    workload, on this host's cores; Mpix/s extrapolates exactly because every
+    pixel costs the same N pair evaluations."""
+    import oracle
+    rng = np.random.default_rng(123)
+    n = 64
+    while True:
+        pix = rng.integers(0, im.H * im.W, n)
+        t0 = time.perf_counter()
+        oracle.forward(im.points, im.values, im.H, im.W, im.sigma, pixels=pix)
+        t = time.perf_counter() - t0
+        if t >= target_s / 4 or n >= 1 << 20:
+            break
+        n = int(n * min(8.0, max(2.0, (target_s / 4) / max(t, 1e-3))))
+    return {"value": n / t / 1e6, "unit": "Mpix/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": "%d random pixels of the %dx%d image (%d points each), %.1f s" % (n, im.H, im.W, im.N, t)}
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the FP64 oracle on the host cores, per step a bounded
+    pixel sample of the headline workload."""
+    if rank != 0:
+        return
+    import oracle
+    import workloads as wl
+    im = wl.upsample_1024()
+    rng = np.random.default_rng(7)
+    per_step = 1024
+    for _ in range(args.warmup):
+        oracle.forward(im.points, im.values, im.H, im.W, im.sigma, pixels=rng.integers(0, im.H * im.W, 64))
+    t = 0.0
+    for _ in range(args.steps):
+        pix = rng.integers(0, im.H * im.W, per_step)
+        t0 = time.perf_counter()
+        oracle.forward(im.points, im.values, im.H, im.W, im.sigma, pixels=pix)
+        t += time.perf_counter() - t0
+    v = per_step * args.steps / t / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Mpix/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample_pixels_per_step": per_step},
+            "cpu_baseline": {"value": v, "unit": "Mpix/s", "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": "%d random pixels per step of the %dx%d image" % (per_step, im.H, im.W)},
+            "e2e": {"value": v, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import torch
+    import paper_2012_13257_b300 as gmi
+    from paper_2012_13257_b300 import _lib
+    import workloads as wl
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    D = Dist(world, dev)
+    L = _lib.load()
+
+    im = wl.upsample_1024()
+    P = torch.as_tensor(im.points, device=dev)
+    V = torch.as_tensor(im.values, device=dev)
+    out = torch.empty((im.H, im.W, im.C), dtype=torch.float32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        gmi.interpolate(P, V, im.sigma, im.H, im.W, out=out)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- headline: device-resident inputs, per-step events, L2 flushed between steps
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    L.gmi_profile_enable(1)
+    L.gmi_profile_read(None, None, 1)
+    clocks = ClockSampler(local)
+    D.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    for k in range(args.steps):
+        flush.zero_()
+        starts[k].record(stream)
+        step()
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    D.barrier()
+    ms_steps = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    stage_ms = (ctypes.c_double * 4)()
+    stage_n = (ctypes.c_int * 4)()
+    L.gmi_profile_read(stage_ms, stage_n, 1)
+    L.gmi_profile_enable(0)
+    t_total = D.max(sum(ms_steps))
+    ms_per_step = t_total / args.steps
+    value = im.H * im.W * args.steps * world / (t_total * 1e-3) / 1e6
+
+    # ---- e2e: pinned host buffers, copies inside the timed region
+    hP = torch.as_tensor(im.points).pin_memory()
+    hV = torch.as_tensor(im.values).pin_memory()
+    hO = torch.empty((im.H, im.W, im.C), dtype=torch.float32).pin_memory()
+    dP = torch.empty_like(P)
+    dV = torch.empty_like(V)
+    for _ in range(3):
+        dP.copy_(hP, non_blocking=True)
+        dV.copy_(hV, non_blocking=True)
+        gmi.interpolate(dP, dV, im.sigma, im.H, im.W, out=out)
+        hO.copy_(out, non_blocking=True)
+    torch.cuda.synchronize()
+    D.barrier()
+    for k in range(args.steps):
+        flush.zero_()
+        starts[k].record(stream)
+        dP.copy_(hP, non_blocking=True)
+        dV.copy_(hV, non_blocking=True)
+        gmi.interpolate(dP, dV, im.sigma, im.H, im.W, out=out)
+        hO.copy_(out, non_blocking=True)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    e_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    e_total = D.max(sum(e_ms))
+    e2e = {"value": im.H * im.W * args.steps * world / (e_total * 1e-3) / 1e6, "unit": "Mpix/s",
+           "h2d_bytes_per_step": int(hP.numel() * 4 + hV.numel() * 4),
+           "d2h_bytes_per_step": int(hO.numel() * 4),
+           "ms_per_step": e_total / args.steps}
+
+    # ---- roofline of the dominant kernel (near-field gather), timed live above
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    near_ms = stage_ms[1] / max(1, stage_n[1])
+    pairs = algorithmic_pairs(im) if rank == 0 else 0
+    peak_gpair = sms * SFU_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e9
+    achieved = pairs / (near_ms * 1e-3) / 1e9 if near_ms > 0 else None
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak_gpair, "unit": "Gpair/s",
+            "frac": (achieved / peak_gpair) if achieved else None,
+            "traffic": near_kernel_traffic(),
+            "kernel": "near_kernel<4,4,3,exact>", "launch_ms": near_ms, "pairs_per_launch": pairs,
+            "peak_basis": "%d SMs x %d ex2/clk x %.0f MHz: one exponential per (pixel, point) pair "
+                          "within the exact-mode radius; recipe unit counts and max clock" %
+                          (sms, SFU_PER_SM_CLK, SM_MAX_MHZ),
+            "frac_fma_strict": (pairs * (im.C + 1) / (near_ms * 1e-3) /
+                                (sms * FP32_PER_SM_CLK * SM_MAX_MHZ * 1e6)) if near_ms > 0 else None}
+    stages = {name: (stage_ms[i] / stage_n[i] if stage_n[i] else None) for i, name in enumerate(_lib.STAGES)}
+
+    line = {"metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "points": im.N, "H": im.H, "W": im.W, "C": im.C,
+                       "sigma": im.sigma, "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "flushed between steps (256 MB write), not timed"},
+            "roofline": roof, "e2e": e2e, "gpu_launches": LAUNCHES_PER_FORWARD * args.steps, "clocks": clk,
+            "stage_ms": stages}
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(im)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    D.close()
+
+
+if __name__ == "__main__":
+    main()
