@@ -164,6 +164,39 @@ gmi_status gmi_backward(const float* points, const float* values, int64_t N, int
  */
 gmi_status gmi_workspace_status(const void* workspace, gmi_stream_t stream);
 
+/*
+ * Forward pass without a caller-provided workspace (the paper has no
+ * counterpart: this is an integration convenience).
+ *
+ * Some callers cannot allocate device memory at all: plug-ins running inside
+ * a host application that owns the GPU memory pool, latency-critical loops in
+ * which a cudaMalloc/cudaFree would stall the device, and bindings whose own
+ * API has no way to size and pass a workspace.  This entry point takes the
+ * same arguments as gmi_forward minus the workspace and computes the same
+ * result, using as scratch one statically sized device array of
+ * GMI_NOALLOC_SCRATCH_BYTES that lives in the library (every GPU that loads
+ * the library holds it until the process exits).  It calls no cudaMalloc,
+ * cudaFree or other allocating routine.
+ *
+ *   - Limit: problems whose gmi_workspace_size exceeds
+ *     GMI_NOALLOC_SCRATCH_BYTES are rejected with GMI_ERR_CAPACITY before
+ *     anything is enqueued (a 1024x1024 output from 262,144 points with C = 3
+ *     needs about 19 MiB and fits; use gmi_forward beyond the limit).
+ *   - The first call on each device looks up the device address of the array
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - Every call on a device shares the one array, which keeps the previous
+ *     call's contents (the call clears what must start at zero itself).
+ *     Calls that overlap on the GPU race on it: serialise them, e.g. issue
+ *     them on one stream.
+ * Errors: as gmi_forward, plus GMI_ERR_CAPACITY.
+ */
+#define GMI_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
+
+gmi_status gmi_forward_noalloc(const float* points, const float* values, int64_t N, int C,
+                               int H, int W, const gmi_params* p, float* image,
+                               float* den_out, float* shift_out, gmi_stream_t stream);
+
 /* ------------------------------------------------------------------------
  * Measurement aid (no counterpart in the paper): while enabled, the compute
  * entry points bracket each stage of their pipeline with CUDA events recorded

@@ -23,6 +23,7 @@ MODE_TRUNCATED = 1
 FLAG_SYNC_CHECK = 0x1
 VARIANT_AUTO, VARIANT_MT4x4, VARIANT_MT4x8, VARIANT_MT2x4 = 0, 1, 2, 3
 STAGES = ("bin", "near", "far", "backward")
+NOALLOC_SCRATCH_BYTES = 32 << 20   # GMI_NOALLOC_SCRATCH_BYTES
 
 
 class GmiError(RuntimeError):
@@ -63,6 +64,8 @@ SIGNATURES = {
     "gmi_backward": (_int, [_vp, _vp, _i64, _int, _int, _int, ctypes.POINTER(Params), _vp, _vp, _vp, _vp,
                             _vp, _vp, _vp, _vp, _sz, _vp]),
     "gmi_workspace_status": (_int, [_vp, _vp]),
+    "gmi_forward_noalloc": (_int, [_vp, _vp, _i64, _int, _int, _int, ctypes.POINTER(Params), _vp, _vp, _vp,
+                                   _vp]),
     "gmi_profile_enable": (_int, [_int]),
     "gmi_profile_read": (_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), _int]),
     "gmi_batch_plan_create": (_int, [_int, _i64, _i64, _int, ctypes.POINTER(Params), ctypes.POINTER(_vp)]),

@@ -1,0 +1,51 @@
+// gmi_forward_noalloc: the forward pass for callers that cannot allocate
+// device memory (host applications that own the GPU memory pool, loops that
+// must not stall on cudaMalloc/cudaFree, bindings that cannot pass a
+// workspace).  Its scratch is one statically sized device array compiled into
+// this library; the pipeline it runs is gmi_forward's, unchanged.
+#include <mutex>
+
+#include "api_internal.h"
+
+namespace {
+
+constexpr size_t kScratchBytes = GMI_NOALLOC_SCRATCH_BYTES;
+constexpr int kMaxDevices = 64;
+
+// The scratch array.  Its name is only a host-side stand-in in host code; the
+// device address is looked up below, once per device.
+static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
+
+std::mutex g_mu;
+void* g_addr[kMaxDevices];   // device address of g_scratch, per device
+
+// Device address of the scratch array on the current device (looked up on
+// the first call for that device, with that device current).
+gmi_status scratch_address(void** out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return GMI_ERR_CUDA;
+  if (dev < 0 || dev >= kMaxDevices) return GMI_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (g_addr[dev] == nullptr) {
+    void* a = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&a, g_scratch);
+    if (e != cudaSuccess || a == nullptr) return GMI_ERR_CUDA;
+    g_addr[dev] = a;
+  }
+  *out = g_addr[dev];
+  return GMI_OK;
+}
+
+}  // namespace
+
+extern "C" gmi_status gmi_forward_noalloc(const float* points, const float* values, int64_t N, int C, int H,
+                                          int W, const gmi_params* p, float* image, float* den_out,
+                                          float* shift_out, gmi_stream_t stream) {
+  size_t need = 0;
+  gmi_status st = gmi_workspace_size(N, C, H, W, p, &need);
+  if (st != GMI_OK) return st;
+  if (need > kScratchBytes) return GMI_ERR_CAPACITY;   // too large for the static scratch
+  void* ws = nullptr;
+  if ((st = scratch_address(&ws)) != GMI_OK) return st;
+  return gmi_forward(points, values, N, C, H, W, p, image, den_out, shift_out, ws, kScratchBytes, stream);
+}
