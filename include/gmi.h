@@ -181,7 +181,7 @@ gmi_status gmi_workspace_status(const void* workspace, gmi_stream_t stream);
  *   - Limit: problems whose gmi_workspace_size exceeds
  *     GMI_NOALLOC_SCRATCH_BYTES are rejected with GMI_ERR_CAPACITY before
  *     anything is enqueued (a 1024x1024 output from 262,144 points with C = 3
- *     needs about 19 MiB and fits; use gmi_forward beyond the limit).
+ *     needs about 28 MiB and fits; use gmi_forward beyond the limit).
  *   - The first call on each device looks up the device address of the array
  *     (cudaGetSymbolAddress) with that device current; make that first call
  *     before any stream capture.

@@ -111,7 +111,7 @@ WsLayout ws_layout(long long n_total, long long nb_total, long long mt_total, lo
   WsLayout L;
   size_t o = 0;
   L.cap_items = (unsigned)std::min<long long>(wt_total * kSplitMax, 0x7fffffffLL);
-  L.cap_slots = (unsigned)std::min<long long>(wt_total / 2 + 256, 0x7fffffffLL);
+  L.cap_slots = (unsigned)std::min<long long>(wt_total > 0 ? wt_total : 1, 0x7fffffffLL);
   L.status = o; o = align_up(o + sizeof(unsigned) * kStatusWords, 256);
   L.off = o;    o = align_up(o + sizeof(unsigned) * (size_t)(nb_total + 1), 256);
   L.oob = o;    o = align_up(o + (size_t)nb_total, 256);
@@ -124,6 +124,7 @@ WsLayout ws_layout(long long n_total, long long nb_total, long long mt_total, lo
   L.farq = o;   o = align_up(o + sizeof(uint2) * (size_t)(mt_total > 0 ? mt_total : 1), 256);
   L.items = o;  o = align_up(o + sizeof(uint4) * (size_t)(L.cap_items > 0 ? L.cap_items : 1), 256);
   L.slots = o;  o = align_up(o + slot_bytes * (size_t)L.cap_slots, 256);
+  L.ubound = o; o = align_up(o + sizeof(float) * 32u * (size_t)(wt_total > 0 ? wt_total : 1), 256);
   L.extra = o;  o = align_up(o + (size_t)extra_bytes, 256);
   L.total = o;
   return L;
@@ -143,6 +144,7 @@ DevWork bind_ws(void* ws, const WsLayout& L) {
   w.items = (uint4*)(b + L.items);
   w.tile_done = (unsigned*)(b + L.tile_done);
   w.slots = (float*)(b + L.slots);
+  w.ubound = (float*)(b + L.ubound);
   w.table = nullptr;
   return w;
 }

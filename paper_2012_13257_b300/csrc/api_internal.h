@@ -10,7 +10,7 @@ namespace gmi {
 
 // Byte offsets of the regions of a workspace.
 struct WsLayout {
-  size_t status, off, oob, tile_done, zero_end, rank, sxy, sval, partials, farq, items, slots, extra, total;
+  size_t status, off, oob, tile_done, zero_end, rank, sxy, sval, partials, farq, items, slots, ubound, extra, total;
   unsigned cap_items, cap_slots;
 };
 

@@ -73,7 +73,9 @@ struct DevWork {
   uint2* farq;           // [mt_total]: (image, micro-tile) queued for the far kernel
   uint4* items;          // [cap_items]: near-kernel work items (warp tile, split, splits, slot)
   unsigned* tile_done;   // [wt_total]: finished splits per warp tile
-  float* slots;          // [cap_slots * slot_floats]: partial sums of split warp tiles
+  float* slots;          // [cap_slots * slot_floats]: sums of the work items of split warp tiles
+  float* ubound;         // [wt_total * 32]: per micro-tile bound U on the nearest squared
+                         //   distance (+inf: far-field micro-tile), written by the plan
   const ImageGeom* table;// device descriptor table (batched) or null (single image)
 };
 
@@ -94,8 +96,8 @@ struct KArgs {
 
 constexpr int kChunk = 256;             // points per chunk (one per thread) in the binning kernels
 constexpr int kScanChunk = 1024;        // bins per block in the scan kernels
-constexpr int kSplitMax = 16;           // most work items one warp tile is split into
-constexpr unsigned kSplitTarget = 384;  // candidates per thread per work item
+constexpr int kSplitMax = 64;           // most work items one warp tile is split into
+constexpr unsigned kSplitTarget = 160;  // candidates per thread per work item
 
 __device__ __forceinline__ const ImageGeom* geom_ptr(const KArgs& a, int img) {
   return a.w.table ? a.w.table + img : &a.g0;

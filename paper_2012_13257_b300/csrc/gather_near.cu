@@ -24,8 +24,10 @@
 //
 // Load balance: a plan kernel estimates every warp tile's per-thread
 // candidate count and cuts heavy tiles (dense clusters, wide sigma) into up to
-// kSplitMax work items over each thread's candidate sequence; the last item of
-// a tile to finish adds the partial sums in split order (deterministic).
+// kSplitMax work items over each thread's candidate sequence; the items add
+// their partial sums into one slot per tile (float reductions, so the order of
+// those few additions varies from run to run) and the last one to finish
+// writes the pixels.
 //
 // In truncated mode (the literal "radius k sigma" reading) R = k sigma, each
 // pixel keeps only points with d^2 <= k^2 sigma^2, and nothing is queued.
@@ -33,50 +35,105 @@
 
 namespace gmi {
 
-constexpr int kRingMax = 3;   // bin rings searched for the nearest-distance bound
+constexpr int kRingMax = 16;   // most bin rings searched for the nearest-distance bound
 
 // Upper bound on max_q m_q over the micro-tile's valid pixels from bin
-// occupancy; +inf when some pixel has no usable bin within kRingMax rings.
+// occupancy, searched ring by ring around the micro-tile's bins (ring 1 is the
+// full 3x3-bin neighbourhood, later rings only their perimeter) until every
+// pixel has a usable bin; +inf when that takes more rings than the near kernel
+// can use (the micro-tile then belongs to the far-field kernel).
 template <int MTH, int MTW>
 __device__ float near_bound(const KArgs& a, const ImageGeom& g, int x0, int y0, int nx, int ny) {
   const float bf = (float)g.b;
   const float xq0 = (float)x0 + 0.5f, yq0 = (float)y0 + 0.5f;
   const int bx0 = (int)(xq0 * g.inv_b), bx1 = (int)((xq0 + (float)(nx - 1)) * g.inv_b);
   const int by0 = (int)(yq0 * g.inv_b), by1 = (int)((yq0 + (float)(ny - 1)) * g.inv_b);
+  const int ring_max = min(kRingMax, max(3, (int)ceilf(sqrtf(g.u_near_max) * g.inv_b) + 1));
   float best[MTH][MTW];
 #pragma unroll
   for (int r = 0; r < MTH; ++r)
 #pragma unroll
     for (int j = 0; j < MTW; ++j) best[r][j] = (r < ny && j < nx) ? INFINITY : 0.0f;
 
-  for (int ring = 1; ring <= kRingMax; ++ring) {
-    const int ya = max(by0 - ring, 0), yb = min(by1 + ring, g.nby - 1);
-    const int xa = max(bx0 - ring, 0), xb = min(bx1 + ring, g.nbx - 1);
-    for (int by = ya; by <= yb; ++by) {
-      const bool edge_row = (by == by0 - ring) || (by == by1 + ring);
-      const long long rowb = g.bin_base + (long long)by * g.nbx;
-      float cy[MTH];
+  // folds the usable bins of row `by`, columns [xa, xb], into best[][]
+  auto scan_row = [&](int by, int xa, int xb) {
+    if (by < 0 || by >= g.nby) return;
+    xa = max(xa, 0);
+    xb = min(xb, g.nbx - 1);
+    if (xa > xb) return;
+    const long long rowb = g.bin_base + (long long)by * g.nbx;
+    float cy[MTH];
 #pragma unroll
-      for (int r = 0; r < MTH; ++r) {
-        float q = yq0 + (float)r;
-        float d0 = q - (float)by * bf, d1 = q - (float)(by + 1) * bf;
-        cy[r] = fmaxf(d0 * d0, d1 * d1);
+    for (int r = 0; r < MTH; ++r) {
+      const float q = yq0 + (float)r;
+      const float d0 = q - (float)by * bf, d1 = q - (float)(by + 1) * bf;
+      cy[r] = fmaxf(d0 * d0, d1 * d1);
+    }
+    unsigned prev = __ldg(&a.w.off[rowb + xa]);
+    for (int bx = xa; bx <= xb; ++bx) {
+      const unsigned nxt = __ldg(&a.w.off[rowb + bx + 1]);
+      const bool usable = nxt > prev && __ldg(&a.w.oob[rowb + bx]) == 0;
+      prev = nxt;
+      if (!usable) continue;
+#pragma unroll
+      for (int j = 0; j < MTW; ++j) {
+        const float q = xq0 + (float)j;
+        const float d0 = q - (float)bx * bf, d1 = q - (float)(bx + 1) * bf;
+        const float cx = fmaxf(d0 * d0, d1 * d1);
+#pragma unroll
+        for (int r = 0; r < MTH; ++r) best[r][j] = fminf(best[r][j], cx + cy[r]);
       }
-      unsigned prev = a.w.off[rowb + xa];
-      for (int bx = xa; bx <= xb; ++bx) {
-        const unsigned nxt = a.w.off[rowb + bx + 1];
-        const bool on_ring = edge_row || bx == bx0 - ring || bx == bx1 + ring;
-        const bool usable = (ring == 1 || on_ring) && nxt > prev && a.w.oob[rowb + bx] == 0;
-        prev = nxt;
-        if (!usable) continue;
-#pragma unroll
-        for (int j = 0; j < MTW; ++j) {
-          float q = xq0 + (float)j;
-          float d0 = q - (float)bx * bf, d1 = q - (float)(bx + 1) * bf;
-          float cx = fmaxf(d0 * d0, d1 * d1);
-#pragma unroll
-          for (int r = 0; r < MTH; ++r) best[r][j] = fminf(best[r][j], cx + cy[r]);
-        }
+    }
+  };
+
+  for (int ring = 1; ring <= ring_max; ++ring) {
+    if (ring == 4) {
+      // before walking more rings: if no point at all lies within the near-range
+      // radius of the micro-tile (Chebyshev window), every pixel is far
+      const float h = sqrtf(g.u_near_max);
+      const int wx_lo = bin_coord(xq0 - h, g.inv_b, g.nbx);
+      const int wx_hi = bin_coord(xq0 + (float)(nx - 1) + h, g.inv_b, g.nbx);
+      const int wy_lo = bin_coord(yq0 - h, g.inv_b, g.nby);
+      const int wy_hi = bin_coord(yq0 + (float)(ny - 1) + h, g.inv_b, g.nby);
+      unsigned cnt = 0;
+#pragma unroll 8
+      for (int by = wy_lo; by <= wy_hi; ++by) {
+        const long long rowb = g.bin_base + (long long)by * g.nbx;
+        cnt += __ldg(&a.w.off[rowb + wx_hi + 1]) - __ldg(&a.w.off[rowb + wx_lo]);
+      }
+      if (cnt == 0) return INFINITY;
+    }
+    const int xa = bx0 - ring, xb = bx1 + ring;
+    if (ring >= 2) {
+      // points on this ring at all?  one row-segment count per side (independent
+      // loads), so empty rings cost no per-bin work
+      const int ca = max(xa, 0), cb = min(xb, g.nbx - 1);
+      unsigned on_ring = 0;
+      if (by0 - ring >= 0) {
+        const long long rowb = g.bin_base + (long long)(by0 - ring) * g.nbx;
+        on_ring += __ldg(&a.w.off[rowb + cb + 1]) - __ldg(&a.w.off[rowb + ca]);
+      }
+      if (by1 + ring < g.nby) {
+        const long long rowb = g.bin_base + (long long)(by1 + ring) * g.nbx;
+        on_ring += __ldg(&a.w.off[rowb + cb + 1]) - __ldg(&a.w.off[rowb + ca]);
+      }
+      const int ya = max(by0 - ring + 1, 0), yb = min(by1 + ring - 1, g.nby - 1);
+#pragma unroll 4
+      for (int by = ya; by <= yb; ++by) {
+        const long long rowb = g.bin_base + (long long)by * g.nbx;
+        if (xa >= 0) on_ring += __ldg(&a.w.off[rowb + xa + 1]) - __ldg(&a.w.off[rowb + xa]);
+        if (xb < g.nbx) on_ring += __ldg(&a.w.off[rowb + xb + 1]) - __ldg(&a.w.off[rowb + xb]);
+      }
+      if (on_ring == 0) continue;
+    }
+    if (ring == 1) {
+      for (int by = by0 - 1; by <= by1 + 1; ++by) scan_row(by, xa, xb);
+    } else {
+      scan_row(by0 - ring, xa, xb);
+      scan_row(by1 + ring, xa, xb);
+      for (int by = by0 - ring + 1; by <= by1 + ring - 1; ++by) {
+        scan_row(by, xa, xa);
+        scan_row(by, xb, xb);
       }
     }
     float u = 0.0f;
@@ -126,10 +183,13 @@ __device__ __forceinline__ void row_segment(const KArgs& a, const ImageGeom& g, 
   e = __ldg(&a.w.off[rowb + bx_hi + 1]);
 }
 
-// Plan: one warp per warp tile estimates each thread's candidate count (with
-// the radius a dense neighbourhood gives) and splits the tile into
-// S = ceil(max / kSplitTarget) work items, so that no single thread walks
-// thousands of candidates while the rest of the GPU idles.
+// Plan: one warp per warp tile.  Each thread bounds the nearest squared
+// distance U of its micro-tile once (stored for the gather), queues far-field
+// micro-tiles for the far kernel, and counts its candidates within
+// R = sqrt(U + k^2 sigma^2); the tile is cut into S = ceil(max / kSplitTarget)
+// work items, so that no single thread walks thousands of candidates while
+// the rest of the GPU idles.
+template <int MTH, int MTW>
 __global__ void __launch_bounds__(128) near_plan_kernel(KArgs a, int trunc) {
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
@@ -140,12 +200,32 @@ __global__ void __launch_bounds__(128) near_plan_kernel(KArgs a, int trunc) {
   const long long lt = wt - g.wt_base;
   const int mt_x = (int)(lt % g.wtx) * 8 + (lane & 7);
   const int mt_y = (int)(lt / g.wtx) * 4 + (lane >> 3);
-  const int x0 = mt_x * a.mtw, y0 = mt_y * a.mth;
+  const int x0 = mt_x * MTW, y0 = mt_y * MTH;
+  const bool active = x0 < g.W && y0 < g.H;
+  const int nx = active ? min(MTW, g.W - x0) : 0;
+  const int ny = active ? min(MTH, g.H - y0) : 0;
+  float U = 0.0f;
+  bool far = false;
+  if (!trunc && active) {
+    U = near_bound<MTH, MTW>(a, g, x0, y0, nx, ny);
+    far = !(U <= g.u_near_max);
+  }
+  if (!trunc) {
+    const unsigned fm = __ballot_sync(full, far);
+    if (fm) {
+      const int leader = __ffs(fm) - 1;
+      unsigned base = 0;
+      if (lane == leader) base = atomicAdd(&a.w.status[kFarCount], (unsigned)__popc(fm));
+      base = __shfl_sync(full, base, leader);
+      if (far)
+        a.w.farq[base + __popc(fm & ((1u << lane) - 1u))] = make_uint2((unsigned)img, (unsigned)(mt_y * g.mtx + mt_x));
+    }
+  }
+  a.w.ubound[wt * 32 + lane] = far ? INFINITY : U;
   unsigned cnt = 0;
-  if (x0 < g.W && y0 < g.H) {
-    const float bf = (float)g.b;
-    const float R2 = trunc ? g.r2k : g.r2k + 2.0f * bf * bf;
-    const LaneWin w = lane_window(g, x0, y0, min(a.mtw, g.W - x0), min(a.mth, g.H - y0), R2);
+  if (active && !far) {
+    const LaneWin w = lane_window(g, x0, y0, nx, ny, U + g.r2k);
+#pragma unroll 4
     for (int by = w.by_lo; by <= w.by_hi; ++by) {
       unsigned s, e;
       row_segment(a, g, w, by, s, e);
@@ -154,25 +234,36 @@ __global__ void __launch_bounds__(128) near_plan_kernel(KArgs a, int trunc) {
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) cnt = max(cnt, __shfl_xor_sync(full, cnt, o));
-  if (lane == 0) {
-    unsigned S = min((cnt + kSplitTarget - 1) / kSplitTarget, (unsigned)kSplitMax);
-    if (S < 1) S = 1;
-    unsigned slot = 0xffffffffu;
-    if (S > 1) {
-      slot = atomicAdd(&a.w.status[kSlotCount], S);
-      if (slot + S > a.cap_slots) {   // out of partial-sum slots: keep the tile whole
-        S = 1;
-        slot = 0xffffffffu;
-      }
+  unsigned S = min((cnt + kSplitTarget - 1) / kSplitTarget, (unsigned)kSplitMax);
+  if (S < 1) S = 1;
+  unsigned slot = 0xffffffffu;
+  if (S > 1) {
+    // one accumulation slot per split tile, zeroed here; its items add into it
+    if (lane == 0) slot = atomicAdd(&a.w.status[kSlotCount], 1u);
+    slot = __shfl_sync(full, slot, 0);
+    if (slot >= a.cap_slots) {   // cannot happen (one slot per warp tile); keep the tile whole
+      S = 1;
+      slot = 0xffffffffu;
+    } else {
+      const int na = a.mth * a.mtw * (a.C + 1);
+      float4* z = reinterpret_cast<float4*>(a.w.slots + ((size_t)slot * 32 + lane) * na);
+      for (int k = 0; k < na / 4; ++k) z[k] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
+  }
+  if (lane == 0) {
     const unsigned base = atomicAdd(&a.w.status[kItemCount], S);
-    for (unsigned k = 0; k < S && base + k < a.cap_items; ++k)
-      a.w.items[base + k] = make_uint4((unsigned)wt, k, S, S > 1 ? slot + k : 0xffffffffu);
+    for (unsigned k = 0; k < S && base + k < a.cap_items; ++k) a.w.items[base + k] = make_uint4((unsigned)wt, k, S, slot);
   }
 }
 
+// Resident 128-thread blocks per SM the register budget is sized for.
+template <int MTH, int MTW>
+struct NearOcc {
+  static constexpr int value = MTH * MTW <= 8 ? 5 : (MTH * MTW <= 16 ? 4 : 2);
+};
+
 template <int MTH, int MTW, int C, bool TRUNC>
-__global__ void __launch_bounds__(128) near_kernel(KArgs a) {
+__global__ void __launch_bounds__(128, NearOcc<MTH, MTW>::value) near_kernel(KArgs a) {
   constexpr int NA = MTH * MTW * (C + 1);   // accumulators per thread
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
@@ -198,21 +289,9 @@ __global__ void __launch_bounds__(128) near_kernel(KArgs a) {
 
     float R2 = g.r2k;
     if (!TRUNC) {
-      float U = active ? near_bound<MTH, MTW>(a, g, x0, y0, nx, ny) : 0.0f;
-      const bool far = active && !(U <= g.u_near_max);
-      if (split == 0) {
-        const unsigned fm = __ballot_sync(full, far);
-        if (fm) {
-          const int leader = __ffs(fm) - 1;
-          unsigned base = 0;
-          if (lane == leader) base = atomicAdd(&a.w.status[kFarCount], (unsigned)__popc(fm));
-          base = __shfl_sync(full, base, leader);
-          if (far)
-            a.w.farq[base + __popc(fm & ((1u << lane) - 1u))] =
-                make_uint2((unsigned)img, (unsigned)(mt_y * g.mtx + mt_x));
-        }
-      }
-      if (far) active = false;
+      // bound from the plan; +inf marks a far-field micro-tile (queued there)
+      const float U = __ldcg(&a.w.ubound[wt * 32 + lane]);
+      if (!(U <= g.u_near_max)) active = false;
       R2 = U + g.r2k;
     }
 
@@ -240,6 +319,8 @@ __global__ void __launch_bounds__(128) near_kernel(KArgs a) {
       const float4* __restrict__ sval = a.w.sval;
       int by = w.by_lo - 1;
       unsigned i = 0, end = 0, cum = 0;
+      float2 pn = make_float2(0.f, 0.f);
+      float4 cn = make_float4(0.f, 0.f, 0.f, 0.f);
       for (;;) {
         while (i >= end) {
           if (++by > w.by_hi || cum >= hi) goto done;
@@ -249,11 +330,20 @@ __global__ void __launch_bounds__(128) near_kernel(KArgs a) {
           cum += len;
           i = s0 + (lo > rs ? min(lo - rs, len) : 0u);
           end = s0 + (hi > rs ? min(hi - rs, len) : 0u);
+          if (i < end) {
+            pn = __ldg(&sxy[i]);
+            cn = __ldg(&sval[i]);
+          }
         }
         {
-          const float2 p = __ldg(&sxy[i]);
-          const float4 cv = __ldg(&sval[i]);
+          // the candidate loaded one iteration ahead; start loading the next
+          const float2 p = pn;
+          const float4 cv = cn;
           ++i;
+          if (i < end) {
+            pn = __ldg(&sxy[i]);
+            cn = __ldg(&sval[i]);
+          }
           const float c4[4] = {cv.x, cv.y, cv.z, cv.w};
           const float u = (w.xq0 - p.x) * sk;
           const float v = (w.yq0 - p.y) * sk;
@@ -304,12 +394,15 @@ __global__ void __launch_bounds__(128) near_kernel(KArgs a) {
 
     bool finish = true;
     if (S > 1) {
-      // split tile: publish this item's partial sums; the last item to finish
-      // adds all of them in split order and writes the pixels
-      float* mine = a.w.slots + (size_t)slot * (size_t)(32 * NA);
+      // split tile: add this item's partial sums into the tile's slot; the
+      // last item to finish reads the totals and writes the pixels
+      float* mine = a.w.slots + ((size_t)slot * 32 + lane) * NA;
       if (active) {
 #pragma unroll
-        for (int k = 0; k < NA; ++k) mine[k * 32 + lane] = acc[k];
+        for (int k = 0; k < NA; k += 4)
+          asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(mine + k), "f"(acc[k]),
+                       "f"(acc[k + 1]), "f"(acc[k + 2]), "f"(acc[k + 3])
+                       : "memory");
       }
       __threadfence();
       __syncwarp();
@@ -320,13 +413,13 @@ __global__ void __launch_bounds__(128) near_kernel(KArgs a) {
       if (finish) {
         __threadfence();
         if (active) {
-          const float* first = a.w.slots + (size_t)(slot - split) * (size_t)(32 * NA);
 #pragma unroll
-          for (int k = 0; k < NA; ++k) acc[k] = 0.0f;
-          for (unsigned q = 0; q < S; ++q) {
-            const float* part = first + (size_t)q * (size_t)(32 * NA);
-#pragma unroll
-            for (int k = 0; k < NA; ++k) acc[k] += __ldcg(&part[k * 32 + lane]);
+          for (int k = 0; k < NA; k += 4) {
+            const float4 v = __ldcg(reinterpret_cast<const float4*>(mine + k));
+            acc[k] = v.x;
+            acc[k + 1] = v.y;
+            acc[k + 2] = v.z;
+            acc[k + 3] = v.w;
           }
         }
       }
@@ -396,8 +489,10 @@ static cudaError_t launch_near_mt(const KArgs& a, bool trunc, int grid, cudaStre
 }
 
 cudaError_t launch_near_plan(const KArgs& a, bool trunc, cudaStream_t s) {
-  const long long blocks = (a.wt_total + 3) / 4;
-  near_plan_kernel<<<(unsigned)blocks, 128, 0, s>>>(a, trunc ? 1 : 0);
+  const unsigned blocks = (unsigned)((a.wt_total + 3) / 4);
+  if (a.mth == 4 && a.mtw == 8) near_plan_kernel<4, 8><<<blocks, 128, 0, s>>>(a, trunc ? 1 : 0);
+  else if (a.mth == 2 && a.mtw == 4) near_plan_kernel<2, 4><<<blocks, 128, 0, s>>>(a, trunc ? 1 : 0);
+  else near_plan_kernel<4, 4><<<blocks, 128, 0, s>>>(a, trunc ? 1 : 0);
   return cudaGetLastError();
 }
 
