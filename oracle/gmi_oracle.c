@@ -197,6 +197,9 @@ int oracle_backward(const float* points, const float* values, int64_t N, int C,
 #pragma omp for schedule(dynamic, 16)
         for (int64_t p = 0; p < P; ++p) {
             if (N == 0) continue;
+            int any = 0;   /* pixels with a zero upstream gradient contribute nothing */
+            for (int c = 0; c < C; ++c) any |= grad[p * C + c] != 0.0f;
+            if (!any) continue;
             double qx, qy;
             pixel_centre(p, W, &qx, &qy);
             double m = 0.0;

@@ -18,7 +18,7 @@ import ctypes
 from . import _lib
 from ._lib import GmiError, MODE_EXACT, MODE_TRUNCATED
 
-__all__ = ["interpolate", "workspace_size", "GmiError", "MODE_EXACT", "MODE_TRUNCATED", "version", "lib"]
+__all__ = ["interpolate", "interpolate_backward", "gmi_interpolate", "workspace_size", "GmiError", "MODE_EXACT", "MODE_TRUNCATED", "version", "lib"]
 
 
 def lib():
@@ -96,3 +96,88 @@ def interpolate(points, values, sigma: float, H: int, W: int, *, radius_sigmas: 
     if return_aux:
         return out, den, shift
     return out
+
+
+def interpolate_backward(points, values, sigma: float, H: int, W: int, image, den, shift, grad_image, *,
+                         radius_sigmas: float = 6.0, mode="exact", bin_px: int = 0, variant: int = 0,
+                         need=(True, True, True), check: bool = False):
+    """Gradients of sum(grad_image * image) w.r.t. points, values and sigma
+    (``image``, ``den``, ``shift`` from ``interpolate(..., return_aux=True)``).
+    Returns ``(grad_points [N,2], grad_values [N,C], grad_sigma [1])``;
+    entries not in ``need`` are None."""
+    import torch
+    points, values = _check_inputs(points, values)
+    N, C = int(points.shape[0]), int(values.shape[1])
+    dev = points.device
+    for t in (image, den, shift, grad_image):
+        if t.device != dev or t.dtype != torch.float32:
+            raise ValueError("image, den, shift and grad_image must be float32 on the points' device")
+    image, den, shift, grad_image = (t.contiguous() for t in (image, den, shift, grad_image))
+    flags = _lib.FLAG_SYNC_CHECK if check else 0
+    p = _lib.make_params(sigma, radius_sigmas, _mode(mode), flags, bin_px, variant)
+    L = _lib.load()
+    nbytes = ctypes.c_size_t(0)
+    _lib.check(L.gmi_workspace_size(N, C, int(H), int(W), ctypes.byref(p), ctypes.byref(nbytes)),
+               "gmi_workspace_size")
+    gp = torch.empty((N, 2), dtype=torch.float32, device=dev) if need[0] else None
+    gv = torch.empty((N, C), dtype=torch.float32, device=dev) if need[1] else None
+    gs = torch.empty((1,), dtype=torch.float32, device=dev) if need[2] else None
+    ws = torch.empty(int(nbytes.value), dtype=torch.uint8, device=dev)
+    with torch.cuda.device(dev):
+        stream = torch.cuda.current_stream(dev).cuda_stream
+        st = L.gmi_backward(points.data_ptr(), values.data_ptr(), N, C, int(H), int(W), ctypes.byref(p),
+                            image.data_ptr(), den.data_ptr(), shift.data_ptr(), grad_image.data_ptr(),
+                            gp.data_ptr() if gp is not None else None, gv.data_ptr() if gv is not None else None,
+                            gs.data_ptr() if gs is not None else None, ws.data_ptr(), int(nbytes.value), stream)
+    _lib.check(st, "gmi_backward")
+    return gp, gv, gs
+
+
+def _autograd_function():
+    import torch
+
+    class GMIFunction(torch.autograd.Function):
+        """Eq. 1 / Eq. 2 as a differentiable op: forward and backward both run
+        in libgmi's kernels; the forward saves image, den and shift (the bins
+        are rebuilt in the backward)."""
+
+        @staticmethod
+        def forward(ctx, points, values, sigma_t, H, W, radius_sigmas, mode, bin_px, variant):
+            sigma = float(sigma_t)
+            img, den, shift = interpolate(points, values, sigma, H, W, radius_sigmas=radius_sigmas, mode=mode,
+                                          bin_px=bin_px, variant=variant, return_aux=True)
+            ctx.save_for_backward(points, values, img, den, shift)
+            ctx.cfg = (sigma, H, W, radius_sigmas, mode, bin_px, variant, isinstance(sigma_t, torch.Tensor))
+            ctx.mark_non_differentiable(den, shift)
+            return img, den, shift
+
+        @staticmethod
+        def backward(ctx, g, _gden, _gshift):
+            points, values, img, den, shift = ctx.saved_tensors
+            sigma, H, W, k, mode, bin_px, variant, sig_is_t = ctx.cfg
+            need = (ctx.needs_input_grad[0], ctx.needs_input_grad[1], ctx.needs_input_grad[2] and sig_is_t)
+            if g is None:
+                return (None,) * 9
+            gp, gv, gs = interpolate_backward(points, values, sigma, H, W, img, den, shift, g.float(),
+                                              radius_sigmas=k, mode=mode, bin_px=bin_px, variant=variant,
+                                              need=(need[0], need[1], need[2]))
+            gsig = gs.reshape(()) if gs is not None else None
+            return gp, gv, gsig, None, None, None, None, None, None
+
+    return GMIFunction
+
+
+_GMIFunction = None
+
+
+def gmi_interpolate(points, values, sigma, H: int, W: int, *, radius_sigmas: float = 6.0, mode="exact",
+                    bin_px: int = 0, variant: int = 0):
+    """Differentiable interpolation (torch.autograd): gradients flow to
+    ``points``, ``values`` and, when it is a tensor, ``sigma``.  Returns the
+    image [H, W, C]."""
+    global _GMIFunction
+    if _GMIFunction is None:
+        _GMIFunction = _autograd_function()
+    img, _, _ = _GMIFunction.apply(points, values, sigma, int(H), int(W), float(radius_sigmas), mode,
+                                   int(bin_px), int(variant))
+    return img

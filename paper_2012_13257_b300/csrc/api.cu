@@ -120,6 +120,7 @@ WsLayout ws_layout(long long n_total, long long nb_total, long long mt_total, lo
   L.rank = o;   o = align_up(o + sizeof(unsigned) * (size_t)n_total, 256);
   L.sxy = o;    o = align_up(o + sizeof(float2) * (size_t)n_total, 256);
   L.sval = o;   o = align_up(o + sizeof(float4) * (size_t)n_total, 256);
+  L.perm = o;   o = align_up(o + sizeof(unsigned) * (size_t)n_total, 256);
   L.partials = o; o = align_up(o + sizeof(unsigned) * (size_t)((nb_total + kScanChunk - 1) / kScanChunk + 1), 256);
   L.farq = o;   o = align_up(o + sizeof(uint2) * (size_t)(mt_total > 0 ? mt_total : 1), 256);
   L.items = o;  o = align_up(o + sizeof(uint4) * (size_t)(L.cap_items > 0 ? L.cap_items : 1), 256);
@@ -145,13 +146,18 @@ DevWork bind_ws(void* ws, const WsLayout& L) {
   w.tile_done = (unsigned*)(b + L.tile_done);
   w.slots = (float*)(b + L.slots);
   w.ubound = (float*)(b + L.ubound);
+  w.perm = (unsigned*)(b + L.perm);
+  w.pplane = nullptr;
+  w.fbflag = nullptr;
+  w.fbq = nullptr;
+  w.sig_part = nullptr;
   w.table = nullptr;
   return w;
 }
 
-// Binning + plan + near + far on prepared arguments (single image or batch).
-gmi_status run_forward_pipeline(KArgs& a, const WsLayout& L, void* ws, int mth, int mtw, bool trunc,
-                                cudaStream_t s) {
+// Binning (memset, count, scan, scatter) and the near-kernel plan.
+gmi_status run_bin_and_plan(KArgs& a, const WsLayout& L, void* ws, int mth, int mtw, bool trunc,
+                            cudaStream_t s) {
   const ProfileMark pb = profile_begin(GMI_STAGE_BIN, s);
   cudaError_t e = cudaMemsetAsync(ws, 0, L.zero_end, s);
   if (e != cudaSuccess) return GMI_ERR_CUDA;
@@ -171,6 +177,16 @@ gmi_status run_forward_pipeline(KArgs& a, const WsLayout& L, void* ws, int mth, 
   a.mtw = mtw;
   if ((e = launch_near_plan(a, trunc, s)) != cudaSuccess) return GMI_ERR_CUDA;
   profile_end(pb, s);
+  return GMI_OK;
+}
+
+// Binning + plan + near + far on prepared arguments (single image or batch).
+gmi_status run_forward_pipeline(KArgs& a, const WsLayout& L, void* ws, int mth, int mtw, bool trunc,
+                                cudaStream_t s) {
+  gmi_status st = run_bin_and_plan(a, L, ws, mth, mtw, trunc, s);
+  if (st != GMI_OK) return st;
+  cudaError_t e;
+  const int sms = device_sm_count();
   const int per_sm = near_blocks_per_sm(mth, mtw, a.C, trunc);
   // persistent: at most one resident wave, and no more warps than work items can use
   const int gn = (int)std::max<long long>(1, std::min<long long>(a.wt_total * 4, (long long)sms * per_sm));

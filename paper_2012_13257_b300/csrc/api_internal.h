@@ -10,7 +10,7 @@ namespace gmi {
 
 // Byte offsets of the regions of a workspace.
 struct WsLayout {
-  size_t status, off, oob, tile_done, zero_end, rank, sxy, sval, partials, farq, items, slots, ubound, extra, total;
+  size_t status, off, oob, tile_done, zero_end, rank, sxy, sval, perm, partials, farq, items, slots, ubound, extra, total;
   unsigned cap_items, cap_slots;
 };
 
@@ -26,6 +26,8 @@ size_t slot_bytes_for(int mth, int mtw, int C);
 WsLayout ws_layout(long long n_total, long long nb_total, long long mt_total, long long wt_total,
                    size_t slot_bytes, long long extra_bytes);
 DevWork bind_ws(void* ws, const WsLayout& L);
+gmi_status run_bin_and_plan(KArgs& a, const WsLayout& L, void* ws, int mth, int mtw, bool trunc,
+                            cudaStream_t s);
 gmi_status run_forward_pipeline(KArgs& a, const WsLayout& L, void* ws, int mth, int mtw, bool trunc,
                                 cudaStream_t s);
 gmi_status read_status(const void* ws, cudaStream_t s);
@@ -39,7 +41,9 @@ bool profile_on();
 ProfileMark profile_begin(int stage, cudaStream_t s);
 void profile_end(const ProfileMark& m, cudaStream_t s);
 
-// Extra workspace bytes the backward pass needs beyond the forward layout.
+// Extra workspace bytes the backward pass needs beyond the forward layout,
+// and where its regions start inside the extra block.
 long long bwd_extra_bytes(long long N, int C, int H, int W);
+void bind_bwd(DevWork& w, void* extra, long long N, int C, int H, int W, long long mt_total);
 
 }  // namespace gmi

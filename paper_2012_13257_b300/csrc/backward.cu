@@ -1,0 +1,374 @@
+// Backward pass: gradients of L = sum_q sum_c g_c(q) c_c(q) with respect to
+// the point colours, the point positions and sigma.  The paper has a backward
+// CUDA kernel but prints no formulas; with w_i(q) the weight of point i at
+// pixel q, Z_q their sum and t_i(q) = sum_c g_c(q) (c_{i,c} - c_c(q)), the
+// chain rule on Eq. 1 gives
+//   dL/dc_{i,c} = sum_q g_c(q) w_i(q) / Z_q
+//   dL/dmu_i    = sum_q (w_i(q) / Z_q) t_i(q) (q - mu_i) / sigma^2
+//   dL/dsigma   = sum_q sum_i (w_i(q) / Z_q) t_i(q) |q - mu_i|^2 / sigma^3.
+// From the forward pass only the image c(q), den_q and shift_q are kept
+// (w_i(q) / Z_q = 2^(-kappa (d^2 - shift_q)) / den_q); the bins are rebuilt.
+//
+// Work is split by pixel:
+//   * core pixels (no shift, den_q >= 2^-12): point-centric.  One thread per
+//     bin-sorted point sweeps the disc of pixels within R_core, with
+//     kappa R_core^2 = 26 + 12, which holds every pair whose weight is at least
+//     2^-26 of its pixel's density sum; the thread owns its point's gradient,
+//     so it is stored without atomics.
+//   * other pixels (sparse neighbourhoods and the far field): one warp per
+//     micro-tile holding such pixels collects the points within the largest
+//     radius its pixels need, and adds the pairs' contributions atomically
+//     (few pairs: these regions are sparse).
+#include <string.h>
+
+#include "api_internal.h"
+#include "far_collect.cuh"
+
+namespace gmi {
+
+constexpr float kCoreLog2 = 12.0f;   // core pixel: den >= 2^-kCoreLog2 and no shift
+constexpr float kRelLog2 = 26.0f;    // pairs below 2^-kRelLog2 of their pixel's den are dropped
+
+struct BwdArgs {
+  const float* image;   // [H,W,C] forward output
+  const float* den;     // [H,W]
+  const float* shift;   // [H,W]
+  const float* grad;    // [H,W,C] upstream gradient
+  float* gpts;          // [N,2] or null
+  float* gvals;         // [N,C] or null
+  float* gsig;          // [1] or null
+  int trunc;
+  float inv_s2, inv_s3; // 1/sigma^2, 1/sigma^3
+};
+
+// Per pixel: G_c = g_c / den and s' = sum_c G_c c_c(q) for core pixels (zero
+// elsewhere); micro-tiles with a non-core pixel are queued for the fallback.
+template <int C>
+__global__ void __launch_bounds__(256) bwd_prep_kernel(KArgs a, BwdArgs b) {
+  const ImageGeom& g = a.g0;
+  const long long px = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long npx = (long long)g.H * g.W;
+  if (px >= npx) return;
+  const float d = b.den[px];
+  const float sh = b.shift[px];
+  float G[4] = {0.f, 0.f, 0.f, 0.f};
+  float sp = 0.0f;
+  if (d > 0.0f) {
+    const float inv = 1.0f / d;
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      G[c] = b.grad[px * C + c] * inv;
+      sp = fmaf(G[c], b.image[px * C + c], sp);
+    }
+  }
+  const bool core = d > 0.0f && (b.trunc || (sh == 0.0f && d >= exp2f(-kCoreLog2)));
+  float4 v0, v1 = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (!core) {
+    v0 = make_float4(0.f, 0.f, 0.f, 0.f);
+  } else if (C == 4) {
+    v0 = make_float4(G[0], G[1], G[2], G[3]);
+    v1.x = sp;
+  } else {
+    v0 = make_float4(G[0], G[1], G[2], 0.0f);
+    if (C == 1) v0.y = 0.0f;
+    v0.w = sp;
+  }
+  a.w.pplane[px] = v0;
+  if (C == 4) a.w.pplane[npx + px] = v1;
+  if (!core && d > 0.0f) {
+    const int y = (int)(px / g.W), x = (int)(px % g.W);
+    const unsigned mt = (unsigned)((y / a.mth) * g.mtx + x / a.mtw);
+    if (atomicOr(&a.w.fbflag[mt], 1u) == 0u) {
+      const unsigned q = atomicAdd(&a.w.status[kFbCount], 1u);
+      a.w.fbq[q] = mt;
+    }
+  }
+}
+
+// Point-centric gradients over core pixels; one thread per bin-sorted point.
+template <int C, bool TRUNC>
+__global__ void __launch_bounds__(256) bwd_point_kernel(KArgs a, BwdArgs b, float rcore2) {
+  const ImageGeom& g = a.g0;
+  const long long npx = (long long)g.H * g.W;
+  float D = 0.0f;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < g.n; i += (long long)gridDim.x * blockDim.x) {
+    const float2 p = a.w.sxy[i];
+    const float4 cv = a.w.sval[i];
+    const float c4[4] = {cv.x, cv.y, cv.z, cv.w};
+    float A[4] = {0.f, 0.f, 0.f, 0.f};
+    float Bx = 0.0f, By = 0.0f;
+    const float R = sqrtf(rcore2);
+    const int iy0 = max(0, (int)ceilf(p.y - R - 0.5f));
+    const int iy1 = min(g.H - 1, (int)floorf(p.y + R - 0.5f));
+    for (int iy = iy0; iy <= iy1; ++iy) {
+      const float dy = (float)iy + 0.5f - p.y;
+      const float dy2 = dy * dy;
+      const float rem = rcore2 - dy2;
+      if (rem < 0.0f) continue;
+      const float h = sqrtf(rem);
+      const int ix0 = max(0, (int)ceilf(p.x - h - 0.5f));
+      const int ix1 = min(g.W - 1, (int)floorf(p.x + h - 0.5f));
+      const float4* __restrict__ P = a.w.pplane + (long long)iy * g.W;
+      float rowWt = 0.0f;
+      float dx = (float)ix0 + 0.5f - p.x;
+      for (int ix = ix0; ix <= ix1; ++ix, dx += 1.0f) {
+        const float d2 = fmaf(dx, dx, dy2);
+        float w = ex2(-g.kappa * d2);
+        if (TRUNC && !(d2 <= g.r2k)) w = 0.0f;
+        const float4 pv = __ldg(&P[ix]);
+        float Gv[4] = {pv.x, pv.y, pv.z, pv.w};
+        float sp;
+        if (C == 4) {
+          sp = __ldg(&a.w.pplane[npx + (long long)iy * g.W + ix]).x;
+        } else {
+          sp = pv.w;
+        }
+        float t = -sp;
+#pragma unroll
+        for (int c = 0; c < C; ++c) t = fmaf(Gv[c], c4[c], t);
+#pragma unroll
+        for (int c = 0; c < C; ++c) A[c] = fmaf(w, Gv[c], A[c]);
+        const float wt = w * t;
+        Bx = fmaf(wt, dx, Bx);
+        rowWt += wt;
+        D = fmaf(wt, d2, D);
+      }
+      By = fmaf(rowWt, dy, By);
+    }
+    const unsigned o = a.w.perm[i];
+    if (b.gvals) {
+#pragma unroll
+      for (int c = 0; c < C; ++c) b.gvals[(long long)o * C + c] = A[c];
+    }
+    if (b.gpts) {
+      b.gpts[2LL * o] = Bx * b.inv_s2;
+      b.gpts[2LL * o + 1] = By * b.inv_s2;
+    }
+  }
+  // sigma: block sum -> partial; the last block adds the partials in order
+  __shared__ float red[8];
+  __shared__ bool last;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) D += __shfl_xor_sync(0xffffffffu, D, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = D;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.0f;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
+    a.w.sig_part[blockIdx.x] = t;
+    __threadfence();
+    last = atomicAdd(&a.w.status[kSigDone], 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    float t = 0.0f;
+    for (unsigned k = 0; k < gridDim.x; ++k) t += __ldcg(&a.w.sig_part[k]);
+    if (b.gsig) *b.gsig = t * b.inv_s3;
+  }
+}
+
+// Non-core pixels: one warp per queued micro-tile, lanes = (pixel, part).
+template <int C>
+__global__ void __launch_bounds__(32 * kFarWarps) bwd_fallback_kernel(KArgs a, BwdArgs b) {
+  __shared__ unsigned lists[kFarWarps][kFarCap];
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  unsigned* L = lists[wid];
+  const ImageGeom& g = a.g0;
+  const unsigned nq = a.w.status[kFbCount];
+  const int PS = a.mth * a.mtw, nparts = 32 / PS;
+  const int slot = lane % PS, part = lane / PS;
+  const int pr = slot / a.mtw, pj = slot % a.mtw;
+  for (;;) {
+    unsigned e = 0;
+    if (lane == 0) e = atomicAdd(&a.w.status[kFbHead], 1u);
+    e = __shfl_sync(full, e, 0);
+    if (e >= nq) break;
+    const unsigned mt = a.w.fbq[e];
+    const int mt_x = (int)(mt % (unsigned)g.mtx), mt_y = (int)(mt / (unsigned)g.mtx);
+    const int x0 = mt_x * a.mtw, y0 = mt_y * a.mth;
+    const int nx = min(a.mtw, g.W - x0), ny = min(a.mth, g.H - y0);
+    FarTile t;
+    t.xa = (float)x0 + 0.5f;
+    t.xb = (float)(x0 + nx) - 0.5f;
+    t.ya = (float)y0 + 0.5f;
+    t.yb = (float)(y0 + ny) - 0.5f;
+    const bool valid = pr < ny && pj < nx;
+    const float qx = (float)(x0 + pj) + 0.5f, qy = (float)(y0 + pr) + 0.5f;
+    const long long px = (long long)(y0 + pr) * g.W + (x0 + pj);
+    float d = 0.0f, sh = 0.0f, G[4] = {0.f, 0.f, 0.f, 0.f}, sp = 0.0f;
+    bool mine = false;
+    if (valid) {
+      d = b.den[px];
+      sh = b.shift[px];
+      mine = d > 0.0f && !(sh == 0.0f && d >= exp2f(-kCoreLog2));
+      if (mine) {
+        const float inv = 1.0f / d;
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          G[c] = b.grad[px * C + c] * inv;
+          sp = fmaf(G[c], b.image[px * C + c], sp);
+        }
+      }
+    }
+    // this pixel keeps pairs with kappa (d^2 - shift) <= kRelLog2 - log2(den)
+    const float emax = mine ? (kRelLog2 - log2f(d)) / g.kappa : 0.0f;
+    // sum_i (w_i / Z) t_i = 0 at every pixel, so the sigma term may use
+    // d^2 - s0 for any per-pixel constant s0; taking s0 close to the nearest
+    // squared distance keeps the float32 rounding of t_i from being amplified
+    // by a large d^2 (far field)
+    const float s0 = sh > 0.0f ? 0.0f : (mine ? fmaxf(-log2f(d) / g.kappa, 0.0f) : 0.0f);
+    float R2 = mine ? sh + emax : 0.0f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) R2 = fmaxf(R2, __shfl_xor_sync(full, R2, o));
+    R2 = R2 * (1.0f + 1e-6f) + 1e-6f;
+    const float R = sqrtf(R2);
+    const unsigned total = collect(a, g, t, R, R2, 0u, L);
+    float sig = 0.0f;
+    for (unsigned skip = 0; skip < total; skip += kFarCap) {
+      if (skip > 0) collect(a, g, t, R, R2, skip, L);
+      const unsigned n = min(total - skip, (unsigned)kFarCap);
+      if (mine) {
+        for (unsigned k = part; k < n; k += nparts) {
+          const unsigned idx = L[k];
+          const float2 p = a.w.sxy[idx];
+          const float dx = qx - p.x, dy = qy - p.y;
+          const float ee = sh > 0.0f ? shifted_sqdist(qx, qy, p.x, p.y, sh) : fmaf(dx, dx, dy * dy);
+          if (!(ee <= emax)) continue;
+          const float w = ex2(-g.kappa * ee);
+          const float4 cv = a.w.sval[idx];
+          const float c4[4] = {cv.x, cv.y, cv.z, cv.w};
+          float tt = -sp;
+#pragma unroll
+          for (int c = 0; c < C; ++c) tt = fmaf(G[c], c4[c], tt);
+          const float wt = w * tt;
+          const unsigned o = a.w.perm[idx];
+          if (b.gvals) {
+#pragma unroll
+            for (int c = 0; c < C; ++c) atomicAdd(&b.gvals[(long long)o * C + c], w * G[c]);
+          }
+          if (b.gpts) {
+            atomicAdd(&b.gpts[2LL * o], wt * dx * b.inv_s2);
+            atomicAdd(&b.gpts[2LL * o + 1], wt * dy * b.inv_s2);
+          }
+          sig = fmaf(wt, ee - s0, sig);   // ee is already d^2 - shift when shift > 0
+        }
+      }
+      __syncwarp();
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sig += __shfl_xor_sync(full, sig, o);
+    if (lane == 0 && sig != 0.0f && b.gsig) atomicAdd(b.gsig, sig * b.inv_s3);
+  }
+}
+
+long long bwd_extra_bytes(long long N, int C, int H, int W) {
+  const long long px = (long long)H * W;
+  const long long mt = ((long long)H + 1) / 2 * (((long long)W + 3) / 4);   // smallest micro-tile: 2x4
+  const long long planes = px * 16 * (C == 4 ? 2 : 1);
+  auto al = [](long long v) { return (v + 255) / 256 * 256; };
+  (void)N;
+  return al(planes) + al(mt * 4) + al(mt * 4) + al((long long)kSigParts * 4);
+}
+
+void bind_bwd(DevWork& w, void* extra, long long N, int C, int H, int W, long long mt_total) {
+  (void)N;
+  (void)mt_total;
+  const long long px = (long long)H * W;
+  const long long mt = ((long long)H + 1) / 2 * (((long long)W + 3) / 4);
+  auto al = [](long long v) { return (v + 255) / 256 * 256; };
+  char* p = (char*)extra;
+  w.pplane = (float4*)p;
+  p += al(px * 16 * (C == 4 ? 2 : 1));
+  w.fbflag = (unsigned*)p;
+  p += al(mt * 4);
+  w.fbq = (unsigned*)p;
+  p += al(mt * 4);
+  w.sig_part = (float*)p;
+}
+
+template <int C>
+static cudaError_t launch_bwd_c(const KArgs& a, const BwdArgs& b, cudaStream_t s) {
+  const ImageGeom& g = a.g0;
+  const long long npx = (long long)g.H * g.W;
+  bwd_prep_kernel<C><<<(unsigned)((npx + 255) / 256), 256, 0, s>>>(a, b);
+  const float rcore2 = b.trunc ? g.r2k : (kRelLog2 + kCoreLog2) / g.kappa;
+  const unsigned blocks = (unsigned)std::max<long long>(1, std::min<long long>((g.n + 255) / 256, kSigParts));
+  if (b.trunc) bwd_point_kernel<C, true><<<blocks, 256, 0, s>>>(a, b, rcore2);
+  else bwd_point_kernel<C, false><<<blocks, 256, 0, s>>>(a, b, rcore2);
+  if (!b.trunc) bwd_fallback_kernel<C><<<device_sm_count() * 4, 32 * kFarWarps, 0, s>>>(a, b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_backward(const KArgs& a, const BwdArgs& b, cudaStream_t s) {
+  switch (a.C) {
+    case 1: return launch_bwd_c<1>(a, b, s);
+    case 2: return launch_bwd_c<2>(a, b, s);
+    case 3: return launch_bwd_c<3>(a, b, s);
+    default: return launch_bwd_c<4>(a, b, s);
+  }
+}
+
+}  // namespace gmi
+
+using namespace gmi;
+
+extern "C" gmi_status gmi_backward(const float* points, const float* values, int64_t N, int C, int H, int W,
+                                   const gmi_params* p, const float* image, const float* den, const float* shift,
+                                   const float* grad_image, float* grad_points, float* grad_values,
+                                   float* grad_sigma, void* workspace, size_t ws_bytes, gmi_stream_t stream) {
+  gmi_status st = check_params(p);
+  if (st != GMI_OK) return st;
+  if ((st = check_shape(N, C, H, W)) != GMI_OK) return st;
+  if (!image || !den || !shift || !grad_image || (N > 0 && (!points || !values))) return GMI_ERR_INVALID_ARG;
+  if (((uintptr_t)points & 7u) != 0 || ((uintptr_t)values & 3u) != 0) return GMI_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  int mth, mtw;
+  variant_dims(p->variant, &mth, &mtw);
+  ImageGeom g;
+  memset(&g, 0, sizeof(g));
+  fill_geom(g, N, H, W, p->sigma, p->radius_sigmas, p->bin_px, mth, mtw);
+  g.points = points;
+  g.values = values;
+  const long long nb = (long long)g.nbx * g.nby;
+  const long long mt = (long long)g.mtx * g.mty;
+  const long long wt = (long long)g.wtx * g.wty;
+  const WsLayout L = ws_layout(N, nb, mt, wt, slot_bytes_for(mth, mtw, C), bwd_extra_bytes(N, C, H, W));
+  if (!workspace || ((uintptr_t)workspace & 255u) != 0 || ws_bytes < L.total) return GMI_ERR_WORKSPACE;
+  if (grad_points && cudaMemsetAsync(grad_points, 0, sizeof(float) * 2 * (size_t)N, s) != cudaSuccess) return GMI_ERR_CUDA;
+  if (grad_values && cudaMemsetAsync(grad_values, 0, sizeof(float) * (size_t)C * (size_t)N, s) != cudaSuccess) return GMI_ERR_CUDA;
+  if (grad_sigma && cudaMemsetAsync(grad_sigma, 0, sizeof(float), s) != cudaSuccess) return GMI_ERR_CUDA;
+  if (N == 0) return GMI_OK;
+
+  KArgs a;
+  memset(&a, 0, sizeof(a));
+  a.w = bind_ws(workspace, L);
+  bind_bwd(a.w, (char*)workspace + L.extra, N, C, H, W, mt);
+  a.g0 = g;
+  a.n_images = 1;
+  a.C = C;
+  a.n_total = N;
+  a.nb_total = nb;
+  a.wt_total = wt;
+  a.ch_total = (N + kChunk - 1) / kChunk;
+  a.mt_total = mt;
+  const bool trunc = p->mode == GMI_MODE_TRUNCATED;
+  if ((st = run_bin_and_plan(a, L, workspace, mth, mtw, trunc, s)) != GMI_OK) return st;
+  if (cudaMemsetAsync(a.w.fbflag, 0, sizeof(unsigned) * (size_t)mt, s) != cudaSuccess) return GMI_ERR_CUDA;
+  BwdArgs b;
+  b.image = image;
+  b.den = den;
+  b.shift = shift;
+  b.grad = grad_image;
+  b.gpts = grad_points;
+  b.gvals = grad_values;
+  b.gsig = grad_sigma;
+  b.trunc = trunc ? 1 : 0;
+  b.inv_s2 = (float)(1.0 / ((double)p->sigma * p->sigma));
+  b.inv_s3 = (float)(1.0 / ((double)p->sigma * p->sigma * p->sigma));
+  const ProfileMark pm = profile_begin(GMI_STAGE_BACKWARD, s);
+  if (launch_backward(a, b, s) != cudaSuccess) return GMI_ERR_CUDA;
+  profile_end(pm, s);
+  return (p->flags & GMI_FLAG_SYNC_CHECK) ? read_status(workspace, s) : GMI_OK;
+}

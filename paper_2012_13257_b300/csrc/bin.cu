@@ -135,6 +135,7 @@ __global__ void __launch_bounds__(256) bin_scatter_kernel(KArgs a) {
       if (a.C > 3) c.w = v[3];
       a.w.sxy[dst] = p;
       a.w.sval[dst] = c;
+      a.w.perm[dst] = (unsigned)i;
     }
   }
 }

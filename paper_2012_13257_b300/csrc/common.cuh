@@ -31,6 +31,9 @@ enum : int {
   kBwdHead = 4,        // next work item for the backward kernels
   kItemCount = 5,      // near-kernel work items written by the plan kernel
   kSlotCount = 6,      // partial-sum slots handed out by the plan kernel
+  kFbCount = 7,        // micro-tiles queued for the backward fallback kernel
+  kFbHead = 8,         // next entry of that queue
+  kSigDone = 9,        // blocks of the point-centric backward that have finished
   kStatusWords = 64,
 };
 
@@ -76,6 +79,12 @@ struct DevWork {
   float* slots;          // [cap_slots * slot_floats]: sums of the work items of split warp tiles
   float* ubound;         // [wt_total * 32]: per micro-tile bound U on the nearest squared
                          //   distance (+inf: far-field micro-tile), written by the plan
+  unsigned* perm;        // [n_total]: input index of each bin-sorted point
+  // backward pass only
+  float4* pplane;        // [pixels * (C == 4 ? 2 : 1)]: g_c / den and s' per core pixel
+  unsigned* fbflag;      // [mt_total]: micro-tile holds a non-core pixel
+  unsigned* fbq;         // [mt_total]: queue of such micro-tiles
+  float* sig_part;       // [kSigParts]: per-block sigma-gradient partials
   const ImageGeom* table;// device descriptor table (batched) or null (single image)
 };
 
@@ -96,6 +105,7 @@ struct KArgs {
 
 constexpr int kChunk = 256;             // points per chunk (one per thread) in the binning kernels
 constexpr int kScanChunk = 1024;        // bins per block in the scan kernels
+constexpr int kSigParts = 4096;         // sigma-gradient partials (one per backward block)
 constexpr int kSplitMax = 64;           // most work items one warp tile is split into
 constexpr unsigned kSplitTarget = 160;  // candidates per thread per work item
 

@@ -1,14 +1,8 @@
 // Entry points whose kernels are not built yet: they reject every call.
 #include "api_internal.h"
 
-namespace gmi {
-long long bwd_extra_bytes(long long, int, int, int) { return 0; }
-}  // namespace gmi
 
 extern "C" {
-gmi_status gmi_backward(const float*, const float*, int64_t, int, int, int, const gmi_params*, const float*,
-                        const float*, const float*, const float*, float*, float*, float*, void*, size_t,
-                        gmi_stream_t) { return GMI_ERR_UNSUPPORTED; }
 gmi_status gmi_batch_plan_create(int, int64_t, int64_t, int, const gmi_params*, gmi_batch_plan** plan) {
   if (plan) *plan = nullptr;
   return GMI_ERR_UNSUPPORTED;

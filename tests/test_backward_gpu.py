@@ -1,0 +1,134 @@
+"""Backward-pass parity: gradients w.r.t. point positions, colours and sigma
+from the CUDA path against the FP64 oracle's analytic gradient (itself pinned
+by finite differences and torch autograd in test_oracle.py).
+
+Bar, per tensor: max|g_gpu - g_ref| <= 1e-3 * max|g_ref|; sigma: relative
+1e-3.  Elementwise relative error is meaningless for near-zero gradients."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as wl
+from gpu_helpers import to_dev
+
+pytestmark = pytest.mark.gpu
+
+TOL_BWD = 1e-3
+
+
+def gmi():
+    import paper_2012_13257_b300 as g
+    return g
+
+
+def gpu_grads(im, g_up, dev, **kw):
+    import torch
+    G = gmi()
+    P, V = to_dev(im.points, dev), to_dev(im.values, dev)
+    img, den, shift = G.interpolate(P, V, im.sigma, im.H, im.W, return_aux=True, **kw)
+    gp, gv, gs = G.interpolate_backward(P, V, im.sigma, im.H, im.W, img, den, shift, to_dev(g_up, dev),
+                                        check=True, **kw)
+    torch.cuda.synchronize()
+    return gp.cpu().numpy(), gv.cpu().numpy(), float(gs.cpu().numpy()[0])
+
+
+def assert_grads(got, ref, tol=TOL_BWD):
+    gp, gv, gs = got
+    for name, a, b in (("points", gp, ref["points"]), ("values", gv, ref["values"])):
+        scale = np.abs(b).max()
+        err = np.abs(a.astype(np.float64) - b).max()
+        assert np.isfinite(a).all(), name
+        assert err <= tol * max(scale, 1e-30), "%s: max err %.3g vs scale %.3g" % (name, err, scale)
+    assert abs(gs - ref["sigma"]) <= tol * max(abs(ref["sigma"]), 1e-6), (gs, ref["sigma"])
+
+
+def test_fd_subcase(cuda_device):
+    im, g = wl.fd_subcase()
+    assert_grads(gpu_grads(im, g, cuda_device), oracle.backward(im.points, im.values, im.H, im.W, im.sigma, g))
+
+
+CASES = [  # (seed, N, H, W, C, sigma, margin, clustered)
+    (1, 64, 16, 16, 3, 1.0, 0.0, False),
+    (2, 400, 37, 53, 3, 0.7, 3.0, False),
+    (3, 200, 29, 31, 1, 2.5, 0.0, False),
+    (4, 300, 40, 24, 2, 0.6, 8.0, False),
+    (5, 600, 48, 64, 4, 1.3, 0.0, True),
+    (6, 800, 64, 96, 3, 0.5, 0.0, True),
+    (7, 800, 64, 96, 3, 2.0, 0.0, True),
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: "s%d_N%d_%dx%d_C%d" % c[:5])
+def test_random_cases_exact(cuda_device, case):
+    seed, N, H, W, C, s, margin, clustered = case
+    im = wl.tiny_random(seed, N, H, W, C=C, sigma=s, margin=margin, clustered=clustered)
+    g = np.random.default_rng(seed + 100).standard_normal((H, W, C)).astype(np.float32)
+    assert_grads(gpu_grads(im, g, cuda_device), oracle.backward(im.points, im.values, H, W, im.sigma, g))
+
+
+@pytest.mark.parametrize("variant", [1, 2, 3])
+def test_variants(cuda_device, variant):
+    im = wl.tiny_random(9, 500, 40, 44, C=3, sigma=0.9, clustered=True)
+    g = np.random.default_rng(9).standard_normal((40, 44, 3)).astype(np.float32)
+    assert_grads(gpu_grads(im, g, cuda_device, variant=variant),
+                 oracle.backward(im.points, im.values, im.H, im.W, im.sigma, g))
+
+
+def test_far_field_corner_cluster(cuda_device):
+    """Pixels hundreds of pixels from every point: the fallback kernel with
+    shifted, compensated weights carries their gradient."""
+    rng = np.random.default_rng(17)
+    pts = rng.uniform(0, 10, (30, 2)).astype(np.float32)
+    vals = rng.uniform(0, 1, (30, 3)).astype(np.float32)
+    im = wl.Image(pts, vals, 0.8, 90, 120)
+    g = rng.standard_normal((90, 120, 3)).astype(np.float32)
+    assert_grads(gpu_grads(im, g, cuda_device), oracle.backward(im.points, im.values, im.H, im.W, im.sigma, g))
+
+
+def test_truncated_mode(cuda_device):
+    im = wl.tiny_random(21, 400, 45, 61, C=3, sigma=0.9, clustered=True)
+    g = np.random.default_rng(21).standard_normal((45, 61, 3)).astype(np.float32)
+    k = 3.0
+    ref = oracle.backward(im.points, im.values, im.H, im.W, im.sigma, g, mode=oracle.TRUNCATED, k=k)
+    assert_grads(gpu_grads(im, g, cuda_device, mode="truncated", radius_sigmas=k), ref)
+
+
+def test_dense_blob(cuda_device):
+    rng = np.random.default_rng(31)
+    pts = np.concatenate([rng.uniform(10, 22, (3000, 2)), rng.uniform(0, 40, (100, 2))]).astype(np.float32)
+    vals = rng.uniform(0, 1, (pts.shape[0], 3)).astype(np.float32)
+    im = wl.Image(pts, vals, 1.4, 40, 40)
+    g = rng.standard_normal((40, 40, 3)).astype(np.float32)
+    assert_grads(gpu_grads(im, g, cuda_device), oracle.backward(im.points, im.values, im.H, im.W, im.sigma, g))
+
+
+def test_autograd_function(cuda_device):
+    import torch
+    G = gmi()
+    im, g = wl.fd_subcase(side=24, n=150)
+    P = to_dev(im.points, cuda_device).requires_grad_(True)
+    V = to_dev(im.values, cuda_device).requires_grad_(True)
+    S = torch.tensor(im.sigma, dtype=torch.float32, device=cuda_device, requires_grad=True)
+    img = G.gmi_interpolate(P, V, S, im.H, im.W)
+    (img * to_dev(g, cuda_device)).sum().backward()
+    ref = oracle.backward(im.points, im.values, im.H, im.W, im.sigma, g)
+    assert_grads((P.grad.cpu().numpy(), V.grad.cpu().numpy(), float(S.grad)), ref)
+
+
+def test_fwd_bwd_512_windows(cuda_device):
+    """The 16 x 512^2 fwd+bwd workload at full size (one image here): the
+    upstream gradient is kept on three 32x32 windows so the O(N*H*W) oracle
+    finishes; all point gradients are compared.  With the full N(0,1)
+    gradient, the colour gradients must sum to the upstream sum per channel
+    (the weights of every pixel sum to one)."""
+    imgs, gfull = wl.fwd_bwd_512(B=1)
+    im = imgs[0]
+    rng = np.random.default_rng(3)
+    g = np.zeros_like(gfull[0])
+    for _ in range(3):
+        y, x = rng.integers(0, 512 - 32, 2)
+        g[y:y + 32, x:x + 32] = gfull[0][y:y + 32, x:x + 32]
+    assert_grads(gpu_grads(im, g, cuda_device), oracle.backward(im.points, im.values, im.H, im.W, im.sigma, g))
+    _, gv, _ = gpu_grads(im, gfull[0], cuda_device)
+    np.testing.assert_allclose(gv.astype(np.float64).sum(0), gfull[0].astype(np.float64).reshape(-1, 3).sum(0),
+                               rtol=1e-4, atol=1e-2)
