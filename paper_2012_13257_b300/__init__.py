@@ -18,7 +18,7 @@ import ctypes
 from . import _lib
 from ._lib import GmiError, MODE_EXACT, MODE_TRUNCATED
 
-__all__ = ["interpolate", "interpolate_backward", "gmi_interpolate", "workspace_size", "GmiError", "MODE_EXACT", "MODE_TRUNCATED", "version", "lib"]
+__all__ = ["interpolate", "interpolate_backward", "gmi_interpolate", "BatchPlan", "workspace_size", "GmiError", "MODE_EXACT", "MODE_TRUNCATED", "version", "lib"]
 
 
 def lib():
@@ -181,3 +181,65 @@ def gmi_interpolate(points, values, sigma, H: int, W: int, *, radius_sigmas: flo
     img, _, _ = _GMIFunction.apply(points, values, sigma, int(H), int(W), float(radius_sigmas), mode,
                                    int(bin_px), int(variant))
     return img
+
+
+class BatchPlan:
+    """A reusable batched-forward plan (device workspace + pinned staging
+    allocated once).  ``forward(images)`` interpolates a list of images, each a
+    dict with ``points``, ``values`` (CUDA float32), ``sigma``, ``H``, ``W`` and
+    optionally ``out``, ``den``, ``shift``, ``bin_px``, in one batched
+    pipeline; with ``use_graph`` the launch sequence is a replayed CUDA graph."""
+
+    def __init__(self, max_images: int, max_points: int, max_pixels: int, C: int = 3, *,
+                 radius_sigmas: float = 6.0, mode="exact", variant: int = 0, bin_px: int = 0,
+                 check: bool = False):
+        p = _lib.make_params(1.0, radius_sigmas, _mode(mode), _lib.FLAG_SYNC_CHECK if check else 0, bin_px, variant)
+        h = ctypes.c_void_p()
+        _lib.check(_lib.load().gmi_batch_plan_create(int(max_images), int(max_points), int(max_pixels), int(C),
+                                                     ctypes.byref(p), ctypes.byref(h)), "gmi_batch_plan_create")
+        self._h = h
+        self.C = int(C)
+
+    @property
+    def nbytes(self) -> int:
+        return int(_lib.load().gmi_batch_plan_bytes(self._h))
+
+    def forward(self, images, use_graph: bool = True):
+        import torch
+        n = len(images)
+        descs = (_lib.ImageDesc * max(1, n))()
+        outs = []
+        keep = []
+        dev = None
+        for i, im in enumerate(images):
+            P, V = _check_inputs(im["points"], im["values"])
+            dev = P.device
+            H, W = int(im["H"]), int(im["W"])
+            out = im.get("out")
+            if out is None:
+                out = torch.empty((H, W, self.C), dtype=torch.float32, device=dev)
+            keep += [P, V]
+            d = descs[i]
+            d.points, d.values, d.image = P.data_ptr(), V.data_ptr(), out.data_ptr()
+            d.den = im["den"].data_ptr() if im.get("den") is not None else None
+            d.shift = im["shift"].data_ptr() if im.get("shift") is not None else None
+            d.N, d.H, d.W = int(P.shape[0]), H, W
+            d.sigma = float(im["sigma"])
+            d.bin_px = int(im.get("bin_px", 0))
+            outs.append(out)
+        stream = torch.cuda.current_stream(dev).cuda_stream if dev is not None else None
+        _lib.check(_lib.load().gmi_forward_batched(self._h, descs, n, 1 if use_graph else 0, stream),
+                   "gmi_forward_batched")
+        self._keep = keep   # inputs stay referenced until the next call
+        return outs
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.load().gmi_batch_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -19,9 +19,10 @@ cudaError_t launch_near_plan(const KArgs& a, bool trunc, cudaStream_t s);
 int near_blocks_per_sm(int mth, int mtw, int C, bool trunc);
 cudaError_t launch_far(const KArgs& a, int mth, int mtw, int grid, cudaStream_t s);
 __global__ void bin_count_kernel(KArgs a);
-__global__ void scan_partial_kernel(const unsigned* cnt, long long nb, unsigned* partials);
-__global__ void scan_final_kernel(unsigned* off, long long nb, const unsigned* partials);
+__global__ void scan_partial_kernel(const unsigned* cnt, long long nb, unsigned* partials, const long long* totals);
+__global__ void scan_final_kernel(unsigned* off, long long nb, const unsigned* partials, const long long* totals);
 __global__ void bin_scatter_kernel(KArgs a);
+__global__ void batch_clear_kernel(KArgs a);
 
 static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -155,26 +156,32 @@ DevWork bind_ws(void* ws, const WsLayout& L) {
   return w;
 }
 
-// Binning (memset, count, scan, scatter) and the near-kernel plan.
+// Binning (memset, count, scan, scatter) and the near-kernel plan.  Grid
+// sizes come from a's totals; in a batched call (a.totals set) they are the
+// plan's capacities and the kernels read the real totals from the device.
 gmi_status run_bin_and_plan(KArgs& a, const WsLayout& L, void* ws, int mth, int mtw, bool trunc,
                             cudaStream_t s) {
   const ProfileMark pb = profile_begin(GMI_STAGE_BIN, s);
-  cudaError_t e = cudaMemsetAsync(ws, 0, L.zero_end, s);
-  if (e != cudaSuccess) return GMI_ERR_CUDA;
+  cudaError_t e;
   const int sms = device_sm_count();
-  if (a.n_total > 0) {
-    const int gb = (int)std::min<long long>(a.ch_total, (long long)sms * 32);
-    bin_count_kernel<<<gb, 256, 0, s>>>(a);
-    const int ns = (int)((a.nb_total + kScanChunk - 1) / kScanChunk);
-    scan_partial_kernel<<<ns, 256, 0, s>>>(a.w.off, a.nb_total, a.w.partials);
-    scan_final_kernel<<<ns, 256, 0, s>>>(a.w.off, a.nb_total, a.w.partials);
-    bin_scatter_kernel<<<gb, 256, 0, s>>>(a);
-    if ((e = cudaGetLastError()) != cudaSuccess) return GMI_ERR_CUDA;
+  if (a.totals) {
+    batch_clear_kernel<<<sms * 4, 256, 0, s>>>(a);
+  } else if ((e = cudaMemsetAsync(ws, 0, L.zero_end, s)) != cudaSuccess) {
+    return GMI_ERR_CUDA;
   }
   a.cap_items = L.cap_items;
   a.cap_slots = L.cap_slots;
   a.mth = mth;
   a.mtw = mtw;
+  if (a.n_total > 0) {
+    const int gb = (int)std::min<long long>(a.ch_total, (long long)sms * 32);
+    bin_count_kernel<<<gb, 256, 0, s>>>(a);
+    const int ns = (int)((a.nb_total + kScanChunk - 1) / kScanChunk);
+    scan_partial_kernel<<<ns, 256, 0, s>>>(a.w.off, a.nb_total, a.w.partials, a.totals);
+    scan_final_kernel<<<ns, 256, 0, s>>>(a.w.off, a.nb_total, a.w.partials, a.totals);
+    bin_scatter_kernel<<<gb, 256, 0, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return GMI_ERR_CUDA;
+  }
   if ((e = launch_near_plan(a, trunc, s)) != cudaSuccess) return GMI_ERR_CUDA;
   profile_end(pb, s);
   return GMI_OK;

@@ -22,7 +22,8 @@ __device__ __forceinline__ void point_bin(const ImageGeom& g, float x, float y, 
   oob = !(x >= 0.0f && x < (float)g.W && y >= 0.0f && y < (float)g.H);
 }
 
-__global__ void __launch_bounds__(256) bin_count_kernel(KArgs a) {
+__global__ void __launch_bounds__(256) bin_count_kernel(KArgs a_in) {
+  const KArgs a = resolve(a_in);
   unsigned bad = 0;
   for (long long ch = blockIdx.x; ch < a.ch_total; ch += gridDim.x) {
     const int img = find_image<0>(a, ch);
@@ -45,8 +46,9 @@ __global__ void __launch_bounds__(256) bin_count_kernel(KArgs a) {
 
 // Sum of kScanChunk consecutive counts per block.
 __global__ void __launch_bounds__(256) scan_partial_kernel(const unsigned* __restrict__ cnt, long long nb,
-                                                           unsigned* __restrict__ partials) {
+                                                           unsigned* __restrict__ partials, const long long* totals) {
   __shared__ unsigned red[8];
+  if (totals) nb = totals[kTotBins];
   const long long base = (long long)blockIdx.x * kScanChunk;
   unsigned s = 0;
   for (int k = threadIdx.x; k < kScanChunk; k += blockDim.x) {
@@ -68,8 +70,9 @@ __global__ void __launch_bounds__(256) scan_partial_kernel(const unsigned* __res
 // Each block adds the sum of all earlier blocks' partials, then scans its own
 // kScanChunk bins (kScanChunk / 256 consecutive bins per thread).
 __global__ void __launch_bounds__(256) scan_final_kernel(unsigned* __restrict__ off, long long nb,
-                                                         const unsigned* __restrict__ partials) {
+                                                         const unsigned* __restrict__ partials, const long long* totals) {
   constexpr int kPer = kScanChunk / 256;
+  if (totals) nb = totals[kTotBins];
   __shared__ unsigned warp_tot[8];
   __shared__ unsigned block_prefix;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -113,10 +116,13 @@ __global__ void __launch_bounds__(256) scan_final_kernel(unsigned* __restrict__ 
     if (j < nb) off[j] = run;
     run += v[k];
   }
-  if (blockIdx.x == gridDim.x - 1 && tid == blockDim.x - 1) off[nb] = bpre + wpre + incl;
+  // the thread owning the last bin also writes the total into off[nb]
+  if (nb > 0 && base <= nb - 1 && nb - 1 < base + kPer) off[nb] = run;
+  if (nb == 0 && blockIdx.x == 0 && tid == 0) off[0] = 0;
 }
 
-__global__ void __launch_bounds__(256) bin_scatter_kernel(KArgs a) {
+__global__ void __launch_bounds__(256) bin_scatter_kernel(KArgs a_in) {
+  const KArgs a = resolve(a_in);
   for (long long ch = blockIdx.x; ch < a.ch_total; ch += gridDim.x) {
     const int img = find_image<0>(a, ch);
     const ImageGeom& g = *geom_ptr(a, img);
@@ -138,6 +144,21 @@ __global__ void __launch_bounds__(256) bin_scatter_kernel(KArgs a) {
       a.w.perm[dst] = (unsigned)i;
     }
   }
+}
+
+}  // namespace gmi
+
+namespace gmi {
+
+// Clears what a batched call needs at zero (sizes from the device totals).
+__global__ void __launch_bounds__(256) batch_clear_kernel(KArgs a_in) {
+  const KArgs a = resolve(a_in);
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  for (long long i = t0; i < kStatusWords; i += stride) a.w.status[i] = 0u;
+  for (long long i = t0; i <= a.nb_total; i += stride) a.w.off[i] = 0u;
+  for (long long i = t0; i < a.nb_total; i += stride) a.w.oob[i] = 0;
+  for (long long i = t0; i < a.wt_total; i += stride) a.w.tile_done[i] = 0u;
 }
 
 }  // namespace gmi

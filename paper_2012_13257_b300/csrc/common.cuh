@@ -101,7 +101,26 @@ struct KArgs {
   unsigned cap_items;    // capacity of w.items
   unsigned cap_slots;    // capacity of w.slots, in slots
   int mth, mtw;          // micro-tile of the near kernel
+  const long long* totals;  // batched: device copy of the totals below (else null)
 };
+
+// Layout of the device totals of a batch (uploaded with its descriptor table),
+// so that one captured launch sequence serves any batch within capacity.
+enum : int { kTotImages = 0, kTotPoints, kTotBins, kTotWarpTiles, kTotChunks, kTotMicroTiles, kTotCount = 8 };
+
+// Kernel arguments with the totals of a batched call read from the device.
+__device__ __forceinline__ KArgs resolve(const KArgs& in) {
+  KArgs a = in;
+  if (in.totals) {
+    a.n_images = (int)in.totals[kTotImages];
+    a.n_total = in.totals[kTotPoints];
+    a.nb_total = in.totals[kTotBins];
+    a.wt_total = in.totals[kTotWarpTiles];
+    a.ch_total = in.totals[kTotChunks];
+    a.mt_total = in.totals[kTotMicroTiles];
+  }
+  return a;
+}
 
 constexpr int kChunk = 256;             // points per chunk (one per thread) in the binning kernels
 constexpr int kScanChunk = 1024;        // bins per block in the scan kernels

@@ -190,7 +190,8 @@ __device__ __forceinline__ void row_segment(const KArgs& a, const ImageGeom& g, 
 // work items, so that no single thread walks thousands of candidates while
 // the rest of the GPU idles.
 template <int MTH, int MTW>
-__global__ void __launch_bounds__(128) near_plan_kernel(KArgs a, int trunc) {
+__global__ void __launch_bounds__(128) near_plan_kernel(KArgs a_in, int trunc) {
+  const KArgs a = resolve(a_in);
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const long long wt = (long long)blockIdx.x * 4 + (threadIdx.x >> 5);
@@ -263,7 +264,8 @@ struct NearOcc {
 };
 
 template <int MTH, int MTW, int C, bool TRUNC>
-__global__ void __launch_bounds__(128, NearOcc<MTH, MTW>::value) near_kernel(KArgs a) {
+__global__ void __launch_bounds__(128, NearOcc<MTH, MTW>::value) near_kernel(KArgs a_in) {
+  const KArgs a = resolve(a_in);
   constexpr int NA = MTH * MTW * (C + 1);   // accumulators per thread
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;

@@ -3,13 +3,6 @@
 
 
 extern "C" {
-gmi_status gmi_batch_plan_create(int, int64_t, int64_t, int, const gmi_params*, gmi_batch_plan** plan) {
-  if (plan) *plan = nullptr;
-  return GMI_ERR_UNSUPPORTED;
-}
-gmi_status gmi_batch_plan_destroy(gmi_batch_plan*) { return GMI_OK; }
-size_t gmi_batch_plan_bytes(const gmi_batch_plan*) { return 0; }
-gmi_status gmi_forward_batched(gmi_batch_plan*, const gmi_image_desc*, int, int, gmi_stream_t) { return GMI_ERR_UNSUPPORTED; }
 gmi_status gmi_server_config_default(gmi_server_config*) { return GMI_ERR_UNSUPPORTED; }
 gmi_status gmi_server_create(const gmi_server_config*, gmi_server** out) {
   if (out) *out = nullptr;

@@ -26,6 +26,8 @@ bool profile_on() { return g_on; }
 ProfileMark profile_begin(int stage, cudaStream_t s) {
   ProfileMark m{-1, nullptr, nullptr};
   if (!g_on) return m;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return m;  // not inside graphs
   std::lock_guard<std::mutex> lk(g_mu);
   if (g_free.size() < 2) return m;
   m.stage = stage;
