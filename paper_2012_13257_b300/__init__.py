@@ -18,7 +18,7 @@ import ctypes
 from . import _lib
 from ._lib import GmiError, MODE_EXACT, MODE_TRUNCATED
 
-__all__ = ["interpolate", "interpolate_backward", "gmi_interpolate", "BatchPlan", "workspace_size", "GmiError", "MODE_EXACT", "MODE_TRUNCATED", "version", "lib"]
+__all__ = ["interpolate", "interpolate_backward", "gmi_interpolate", "BatchPlan", "Server", "workspace_size", "GmiError", "MODE_EXACT", "MODE_TRUNCATED", "version", "lib"]
 
 
 def lib():
@@ -237,6 +237,90 @@ class BatchPlan:
         if getattr(self, "_h", None):
             _lib.load().gmi_batch_plan_destroy(self._h)
             self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching request server (native threads inside libgmi).
+
+    ``submit(points, values, sigma, H, W, out)`` takes HOST tensors/arrays
+    (pinned memory for asynchronous copies; they must stay alive until the
+    request completes) and returns a request id; ``wait(id, timeout_ms)``
+    returns the latency in seconds once ``out`` holds the image."""
+
+    def __init__(self, budget_bytes: int = 40 << 30, max_batch_images: int = 64,
+                 max_batch_pixels: int = 1 << 25, n_streams: int = 2, C: int = 3,
+                 radius_sigmas: float = 6.0, mode="exact"):
+        L = _lib.load()
+        cfg = _lib.ServerConfig()
+        L.gmi_server_config_default(ctypes.byref(cfg))
+        cfg.budget_bytes = int(budget_bytes)
+        cfg.max_batch_images = int(max_batch_images)
+        cfg.max_batch_pixels = int(max_batch_pixels)
+        cfg.n_streams = int(n_streams)
+        cfg.C = int(C)
+        cfg.radius_sigmas = float(radius_sigmas)
+        cfg.mode = _mode(mode)
+        h = ctypes.c_void_p()
+        _lib.check(L.gmi_server_create(ctypes.byref(cfg), ctypes.byref(h)), "gmi_server_create")
+        self._h = h
+        self.C = int(C)
+        self._keep = {}
+
+    @staticmethod
+    def _ptr(a):
+        import numpy as np
+        if hasattr(a, "data_ptr"):
+            if a.device.type != "cpu" or not a.is_contiguous() or a.dtype.__str__() != "torch.float32":
+                raise ValueError("server buffers must be contiguous float32 host tensors")
+            return a.data_ptr()
+        a = np.ascontiguousarray(a)
+        if a.dtype != np.float32:
+            raise ValueError("server buffers must be float32")
+        return a.ctypes.data
+
+    def submit(self, points, values, sigma: float, H: int, W: int, out) -> int:
+        rid = ctypes.c_uint64(0)
+        n = int(points.shape[0])
+        _lib.check(_lib.load().gmi_server_submit(self._h, self._ptr(points) if n else None,
+                                                 self._ptr(values) if n else None, n, int(H), int(W),
+                                                 float(sigma), self._ptr(out), ctypes.byref(rid)),
+                   "gmi_server_submit")
+        self._keep[rid.value] = (points, values, out)
+        return int(rid.value)
+
+    def wait(self, rid: int, timeout_ms: int = -1) -> float:
+        lat = ctypes.c_double(0.0)
+        st = _lib.load().gmi_server_wait(self._h, int(rid), int(timeout_ms), ctypes.byref(lat))
+        if st != 6:   # finished (or unknown): its buffers may be released
+            self._keep.pop(int(rid), None)
+        _lib.check(st, "gmi_server_wait")
+        return float(lat.value)
+
+    def poll(self, rid: int) -> bool:
+        st = _lib.load().gmi_server_poll(self._h, int(rid))
+        if st == 6:
+            return False
+        _lib.check(st, "gmi_server_poll")
+        return True
+
+    def stats(self):
+        c, l, p = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+        b = ctypes.c_size_t()
+        _lib.check(_lib.load().gmi_server_stats(self._h, ctypes.byref(c), ctypes.byref(l), ctypes.byref(p),
+                                                ctypes.byref(b)), "gmi_server_stats")
+        return {"completed": c.value, "launches": l.value, "pixels": p.value, "bytes_in_use": b.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.load().gmi_server_destroy(self._h)
+            self._h = None
+            self._keep.clear()
 
     def __del__(self):
         try:
