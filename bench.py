@@ -199,6 +199,215 @@ def cpu_baseline(im, target_s=12.0):
             "sample": "%d random pixels of the %dx%d image (%d points each), %.1f s" % (n, im.H, im.W, im.N, t)}
 
 
+def pair_estimate(imgs, k=6.0, frac=16, seed=0):
+    """Algorithmic pairs of a batch, estimated on a 1/frac random pixel sample
+    of every image (k-d tree counts as in algorithmic_pairs)."""
+    from scipy.spatial import cKDTree
+    rng = np.random.default_rng(seed)
+    total = 0.0
+    for im in imgs:
+        if im.N == 0:
+            continue
+        n = max(64, im.H * im.W // frac)
+        pix = rng.integers(0, im.H * im.W, n)
+        q = np.stack([pix % im.W + 0.5, pix // im.W + 0.5], 1)
+        tree = cKDTree(im.points.astype(np.float64))
+        d, _ = tree.query(q, workers=-1)
+        cnt = tree.query_ball_point(q, np.sqrt(d * d + (k * im.sigma) ** 2) * (1 + 1e-9), return_length=True,
+                                    workers=-1)
+        total += float(np.mean(cnt)) * im.H * im.W
+    return total
+
+
+def timed_steps(fn, steps, flush, stream):
+    """Per-step CUDA-event times (ms) with an untimed L2 flush before each step."""
+    import torch
+    st = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    en = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for k in range(steps):
+        flush.zero_()
+        st[k].record(stream)
+        fn()
+        en[k].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in zip(st, en)]
+
+
+def bench_batched(dev, steps, warmup, flush, stream):
+    """64 uneven clustered images (sides log-uniform in [128, 1024],
+    N = 0.25 H W, sigma U[0.5, 2]): one batched graph launch per step versus
+    64 plain single-image launches, autotuned bin sizes and micro-tile."""
+    import torch
+    import paper_2012_13257_b300 as gmi
+    from paper_2012_13257_b300.autotune import Autotuner, bucket
+    import workloads as wl
+    imgs = wl.batched_uneven()
+    dimgs = [{"points": torch.as_tensor(im.points, device=dev), "values": torch.as_tensor(im.values, device=dev),
+              "sigma": im.sigma, "H": im.H, "W": im.W,
+              "out": torch.empty((im.H, im.W, 3), dtype=torch.float32, device=dev)} for im in imgs]
+    # autotune one representative image per bucket (the largest), in a scratch cache
+    tuner = Autotuner(path=os.path.join(tempfile.gettempdir(), "gmi_autotune_bench.json"))
+    rep = {}
+    for i, im in enumerate(imgs):
+        key = bucket(im.sigma, im.N / float(im.H * im.W), 3)
+        if key not in rep or im.H * im.W > imgs[rep[key]].H * imgs[rep[key]].W:
+            rep[key] = i
+    t0 = time.perf_counter()
+    work = {}
+    for key, i in rep.items():
+        best, _ = tuner.tune(dimgs[i]["points"], dimgs[i]["values"], imgs[i].sigma, imgs[i].H, imgs[i].W,
+                             reps=3, warmup=1, save=False)
+        work.setdefault(best["variant"], 0)
+        work[best["variant"]] += sum(im.H * im.W for im in imgs
+                                     if bucket(im.sigma, im.N / float(im.H * im.W), 3) == key)
+        for j, im in enumerate(imgs):
+            if bucket(im.sigma, im.N / float(im.H * im.W), 3) == key:
+                dimgs[j]["bin_px"] = best["bin_px"]
+    variant = max(work, key=work.get)
+    tune_s = time.perf_counter() - t0
+    plan = gmi.BatchPlan(64, sum(im.N for im in imgs), sum(im.H * im.W for im in imgs), 3, variant=variant)
+    for _ in range(max(3, warmup)):
+        plan.forward(dimgs, use_graph=True)
+    torch.cuda.synchronize()
+    tb = timed_steps(lambda: plan.forward(dimgs, use_graph=True), steps, flush, stream)
+
+    def plain():
+        for d in dimgs:
+            gmi.interpolate(d["points"], d["values"], d["sigma"], d["H"], d["W"], out=d["out"])
+    for _ in range(2):
+        plain()
+    torch.cuda.synchronize()
+    tp = timed_steps(plain, steps, flush, stream)
+    px = sum(im.H * im.W for im in imgs)
+    pairs = pair_estimate(imgs)
+    mb = px / (sum(tb) / steps * 1e-3) / 1e6
+    mp = px / (sum(tp) / steps * 1e-3) / 1e6
+    plan.close()
+    return {"value": mb, "unit": "Mpix/s", "ms_per_step": sum(tb) / steps, "plain_per_image_value": mp,
+            "plain_ms_per_step": sum(tp) / steps, "speedup_vs_plain": mb / mp, "images": len(imgs),
+            "pixels": px, "points": int(sum(im.N for im in imgs)),
+            "pairs_est": pairs, "pair_rate_gpair_s": pairs / (sum(tb) / steps * 1e-3) / 1e9,
+            "autotune": {"variant": variant, "buckets": len(rep), "tune_s": tune_s},
+            "workload": "64 images, sides log-uniform [128,1024], N=0.25HW clustered (8 clusters), "
+                        "sigma U[0.5,2], RGB f32; one CUDA-graph batched launch per step vs 64 plain launches"}
+
+
+def bench_fwd_bwd(dev, steps, warmup, flush, stream):
+    """16 images 512x512x3 from 65,536 clustered points each, sigma = 1:
+    forward + backward (values, positions, sigma) through the autograd op."""
+    import torch
+    import paper_2012_13257_b300 as gmi
+    import workloads as wl
+    imgs, grad = wl.fwd_bwd_512()
+    P = [torch.as_tensor(im.points, device=dev).requires_grad_(True) for im in imgs]
+    V = [torch.as_tensor(im.values, device=dev).requires_grad_(True) for im in imgs]
+    S = [torch.tensor(im.sigma, dtype=torch.float32, device=dev, requires_grad=True) for im in imgs]
+    G = torch.as_tensor(grad, device=dev)
+
+    def step():
+        for b, im in enumerate(imgs):
+            img = gmi.gmi_interpolate(P[b], V[b], S[b], im.H, im.W)
+            img.backward(G[b])
+    for _ in range(max(3, warmup)):
+        step()
+    torch.cuda.synchronize()
+    t = timed_steps(step, steps, flush, stream)
+    px = sum(im.H * im.W for im in imgs)
+    return {"value": px / (sum(t) / steps * 1e-3) / 1e6, "unit": "Mpix/s", "ms_per_step": sum(t) / steps,
+            "images": len(imgs), "pixels": px,
+            "workload": "16 x 512x512x3 f32 from 65,536 clustered points, sigma=1, upstream N(0,1); "
+                        "forward + backward w.r.t. values, positions and sigma via torch.autograd.Function"}
+
+
+def bench_serving(dev, n_requests=10000, rate=2000.0, n_templates=128):
+    """Open-loop serving: Poisson arrivals at `rate`, sides log-uniform in
+    [64, 2048], N = U[0.1, 1] H W, uniform or clustered, sigma U[0.5, 2];
+    payloads cycle through `n_templates` pre-generated pinned requests.
+    Latency = completion - scheduled arrival.  Compared with plain
+    per-request launches (copy in, forward, copy out, one at a time)."""
+    import threading
+    import torch
+    import paper_2012_13257_b300 as gmi
+    import workloads as wl
+    stream_spec = wl.serving_stream(n_requests=n_requests, rate=rate)
+    tmpl = [r.materialise() for r in stream_spec[:n_templates]]
+    hP = [torch.as_tensor(t.points).pin_memory() for t in tmpl]
+    hV = [torch.as_tensor(t.values).pin_memory() for t in tmpl]
+    hO = [torch.empty((t.H, t.W, 3), dtype=torch.float32).pin_memory() for t in tmpl]
+
+    def run_server():
+        srv = gmi.Server(budget_bytes=40 << 30, max_batch_images=64, max_batch_pixels=1 << 25, n_streams=2)
+        # warm-up (graph capture for both slots)
+        for j in range(4):
+            srv.wait(srv.submit(hP[j], hV[j], tmpl[j].sigma, tmpl[j].H, tmpl[j].W, hO[j]))
+        sched, ids, sub = [], [], []
+        lat = [0.0] * n_requests
+        t0 = time.perf_counter()
+        done_ev = threading.Event()
+
+        def waiter():
+            for r in range(n_requests):
+                while len(ids) <= r:
+                    time.sleep(0.0002)
+                lat[r] = (sub[r] - sched[r]) + srv.wait(ids[r])
+            done_ev.set()
+        th = threading.Thread(target=waiter)
+        th.start()
+        for r, spec in enumerate(stream_spec):
+            t_sched = t0 + spec.t_arrival
+            while True:
+                now = time.perf_counter()
+                if now >= t_sched:
+                    break
+                time.sleep(min(0.0005, t_sched - now))
+            j = r % n_templates
+            t = tmpl[j]
+            sched.append(t_sched)
+            sub.append(time.perf_counter())
+            ids.append(srv.submit(hP[j], hV[j], t.sigma, t.H, t.W, hO[j]))
+        done_ev.wait()
+        th.join()
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+        srv.close()
+        return lat, wall, st
+
+    def run_plain():
+        s = torch.cuda.Stream(dev)
+        dP = [torch.empty_like(p, device=dev) for p in hP]
+        dV = [torch.empty_like(v, device=dev) for v in hV]
+        dO = [torch.empty_like(o, device=dev) for o in hO]
+        lat = []
+        t0 = time.perf_counter()
+        with torch.cuda.stream(s):
+            for r, spec in enumerate(stream_spec):
+                t_sched = t0 + spec.t_arrival
+                now = time.perf_counter()
+                if now < t_sched:
+                    time.sleep(t_sched - now)
+                j = r % n_templates
+                t = tmpl[j]
+                dP[j].copy_(hP[j], non_blocking=True)
+                dV[j].copy_(hV[j], non_blocking=True)
+                gmi.interpolate(dP[j], dV[j], t.sigma, t.H, t.W, out=dO[j])
+                hO[j].copy_(dO[j], non_blocking=True)
+                s.synchronize()
+                lat.append(time.perf_counter() - t_sched)
+        return lat, time.perf_counter() - t0
+
+    px = sum(tmpl[r % n_templates].H * tmpl[r % n_templates].W for r in range(n_requests))
+    lat_s, wall_s, st = run_server()
+    lat_p, wall_p = run_plain()
+    q = lambda v, p: float(np.percentile(np.asarray(v) * 1e3, p))
+    return {"p50_ms": q(lat_s, 50), "p99_ms": q(lat_s, 99), "value": px / wall_s / 1e6, "unit": "Mpix/s",
+            "wall_s": wall_s, "launches": st["launches"], "requests": n_requests,
+            "plain_p50_ms": q(lat_p, 50), "plain_p99_ms": q(lat_p, 99), "plain_value": px / wall_p / 1e6,
+            "plain_wall_s": wall_p, "offered_req_s": rate,
+            "workload": "%d requests, Poisson %.0f req/s, sides log-uniform [64,2048], N=U[0.1,1]HW, "
+                        "uniform/clustered, sigma U[0.5,2]; payloads cycle %d pinned templates; 40 GB budget, "
+                        "2 batch slots; latency from scheduled arrival" % (n_requests, rate, n_templates)}
+
+
 def run_reference(args, rank, world):
     """--impl reference: the FP64 oracle on the host cores, per step a bounded
     pixel sample of the headline workload."""
@@ -340,6 +549,15 @@ def main():
                        "l2": "flushed between steps (256 MB write), not timed"},
             "roofline": roof, "e2e": e2e, "gpu_launches": LAUNCHES_PER_FORWARD * args.steps, "clocks": clk,
             "stage_ms": stages}
+    if rank == 0 and not args.no_extras:
+        for name, fn in (("batched", lambda: bench_batched(dev, args.steps, args.warmup, flush, stream)),
+                         ("fwd_bwd", lambda: bench_fwd_bwd(dev, args.steps, args.warmup, flush, stream)),
+                         ("serving", lambda: bench_serving(dev))):
+            try:
+                line[name] = fn()
+            except Exception as e:   # a failed extra must not hide the headline
+                line[name] = {"error": "%s: %s" % (type(e).__name__, e)}
+    D.barrier()
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(im)
     if rank == 0:
