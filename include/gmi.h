@@ -269,6 +269,35 @@ size_t gmi_batch_plan_bytes(const gmi_batch_plan* plan);
 gmi_status gmi_forward_batched(gmi_batch_plan* plan, const gmi_image_desc* descs, int B,
                                int use_graph, gmi_stream_t stream);
 
+/* Per-image arguments of the batched backward pass (see gmi_backward). */
+typedef struct {
+    const float* points;     /* device [N,2], as in the forward */
+    const float* values;     /* device [N,C] */
+    const float* image;      /* device [H,W,C]: forward output */
+    const float* den;        /* device [H,W]: forward den (not NULL) */
+    const float* shift;      /* device [H,W]: forward shift (not NULL) */
+    const float* grad_image; /* device [H,W,C]: upstream gradient */
+    float* grad_points;      /* device [N,2] or NULL */
+    float* grad_values;      /* device [N,C] or NULL */
+    float* grad_sigma;       /* device [1] or NULL */
+    int64_t N;
+    int H, W;
+    float sigma;
+    int bin_px;              /* 0 = auto; use the value the forward used */
+} gmi_grad_desc;
+
+/*
+ * Backward pass of B images (descs is a host array) in one batched pipeline
+ * on `stream`: one segmented re-binning, then the per-pixel preparation, the
+ * point-centric gradient kernel and the fallback kernel over all images at
+ * once (gradients as in gmi_backward).  Uses the plan's workspace: a plan
+ * serves one forward or backward call at a time.  The sigma gradients are
+ * accumulated with float atomics, so their last bits may differ between
+ * runs.  Errors: GMI_ERR_INVALID_ARG, GMI_ERR_CAPACITY, GMI_ERR_CUDA.
+ */
+gmi_status gmi_backward_batched(gmi_batch_plan* plan, const gmi_grad_desc* descs, int B,
+                                gmi_stream_t stream);
+
 /* ------------------------------------------------------------------------
  * Serving: a persistent request loop with continuous batching.  Requests are
  * admitted while their device memory fits the budget, their points are binned

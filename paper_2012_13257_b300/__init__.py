@@ -18,7 +18,7 @@ import ctypes
 from . import _lib
 from ._lib import GmiError, MODE_EXACT, MODE_TRUNCATED
 
-__all__ = ["interpolate", "interpolate_backward", "gmi_interpolate", "BatchPlan", "Server", "workspace_size", "GmiError", "MODE_EXACT", "MODE_TRUNCATED", "version", "lib"]
+__all__ = ["release_workspaces", "interpolate", "interpolate_backward", "gmi_interpolate", "BatchPlan", "gmi_interpolate_batch", "Server", "workspace_size", "GmiError", "MODE_EXACT", "MODE_TRUNCATED", "version", "lib"]
 
 
 def lib():
@@ -35,6 +35,49 @@ def _mode(mode) -> int:
     if mode in ("truncated", MODE_TRUNCATED):
         return MODE_TRUNCATED
     raise ValueError("mode must be 'exact' or 'truncated'")
+
+
+_param_cache = {}
+_ws_size_cache = {}
+_ws_buffers = {}
+
+
+def _params(sigma, radius_sigmas, mode, flags, bin_px, variant):
+    key = (float(sigma), float(radius_sigmas), mode, flags, bin_px, variant)
+    p = _param_cache.get(key)
+    if p is None:
+        if len(_param_cache) > 4096:
+            _param_cache.clear()
+        p = _param_cache[key] = _lib.make_params(sigma, radius_sigmas, mode, flags, bin_px, variant)
+    return p
+
+
+def _ws_bytes(N, C, H, W, p, key):
+    n = _ws_size_cache.get(key)
+    if n is None:
+        c = ctypes.c_size_t(0)
+        _lib.check(_lib.load().gmi_workspace_size(N, C, H, W, ctypes.byref(p), ctypes.byref(c)), "gmi_workspace_size")
+        if len(_ws_size_cache) > 4096:
+            _ws_size_cache.clear()
+        n = _ws_size_cache[key] = int(c.value)
+    return n
+
+
+def _workspace(dev, stream, nbytes):
+    """Scratch reused per (device, stream): calls on one stream run in order,
+    so consecutive calls may share it; other streams get their own."""
+    import torch
+    key = (dev.index, stream)
+    buf = _ws_buffers.get(key)
+    if buf is None or buf.numel() < nbytes:
+        buf = torch.empty(max(nbytes, 1 << 20), dtype=torch.uint8, device=dev)
+        _ws_buffers[key] = buf
+    return buf
+
+
+def release_workspaces():
+    """Drops the cached per-stream scratch buffers."""
+    _ws_buffers.clear()
 
 
 def workspace_size(N: int, C: int, H: int, W: int, sigma: float = 1.0, radius_sigmas: float = 6.0,
@@ -74,24 +117,26 @@ def interpolate(points, values, sigma: float, H: int, W: int, *, radius_sigmas: 
     import torch
     points, values = _check_inputs(points, values)
     N, C = int(points.shape[0]), int(values.shape[1])
+    H, W = int(H), int(W)
     dev = points.device
     flags = _lib.FLAG_SYNC_CHECK if check else 0
-    p = _lib.make_params(sigma, radius_sigmas, _mode(mode), flags, bin_px, variant)
-    L = _lib.load()
-    nbytes = ctypes.c_size_t(0)
-    _lib.check(L.gmi_workspace_size(N, C, int(H), int(W), ctypes.byref(p), ctypes.byref(nbytes)),
-               "gmi_workspace_size")
+    md = _mode(mode)
+    p = _params(sigma, radius_sigmas, md, flags, bin_px, variant)
+    nbytes = _ws_bytes(N, C, H, W, p, (N, C, H, W, float(sigma), float(radius_sigmas), md, bin_px, variant))
     if out is None:
         out = torch.empty((H, W, C), dtype=torch.float32, device=dev)
     den = torch.empty((H, W), dtype=torch.float32, device=dev) if return_aux else None
     shift = torch.empty((H, W), dtype=torch.float32, device=dev) if return_aux else None
-    ws = torch.empty(int(nbytes.value), dtype=torch.uint8, device=dev)
-    with torch.cuda.device(dev):
-        stream = torch.cuda.current_stream(dev).cuda_stream
-        st = L.gmi_forward(points.data_ptr(), values.data_ptr(), N, C, int(H), int(W), ctypes.byref(p),
-                           out.data_ptr(), den.data_ptr() if den is not None else None,
-                           shift.data_ptr() if shift is not None else None, ws.data_ptr(),
-                           int(nbytes.value), stream)
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    ws = _workspace(dev, stream, nbytes)
+    if torch.cuda.current_device() != dev.index:
+        with torch.cuda.device(dev):
+            return interpolate(points, values, sigma, H, W, radius_sigmas=radius_sigmas, mode=mode,
+                               bin_px=bin_px, variant=variant, return_aux=return_aux, check=check, out=out)
+    st = _lib.load().gmi_forward(points.data_ptr(), values.data_ptr(), N, C, H, W, ctypes.byref(p),
+                                 out.data_ptr(), den.data_ptr() if den is not None else None,
+                                 shift.data_ptr() if shift is not None else None, ws.data_ptr(),
+                                 ws.numel(), stream)
     _lib.check(st, "gmi_forward")
     if return_aux:
         return out, den, shift
@@ -113,24 +158,49 @@ def interpolate_backward(points, values, sigma: float, H: int, W: int, image, de
         if t.device != dev or t.dtype != torch.float32:
             raise ValueError("image, den, shift and grad_image must be float32 on the points' device")
     image, den, shift, grad_image = (t.contiguous() for t in (image, den, shift, grad_image))
+    H, W = int(H), int(W)
     flags = _lib.FLAG_SYNC_CHECK if check else 0
-    p = _lib.make_params(sigma, radius_sigmas, _mode(mode), flags, bin_px, variant)
-    L = _lib.load()
-    nbytes = ctypes.c_size_t(0)
-    _lib.check(L.gmi_workspace_size(N, C, int(H), int(W), ctypes.byref(p), ctypes.byref(nbytes)),
-               "gmi_workspace_size")
+    md = _mode(mode)
+    p = _params(sigma, radius_sigmas, md, flags, bin_px, variant)
+    nbytes = _ws_bytes(N, C, H, W, p, (N, C, H, W, float(sigma), float(radius_sigmas), md, bin_px, variant))
     gp = torch.empty((N, 2), dtype=torch.float32, device=dev) if need[0] else None
     gv = torch.empty((N, C), dtype=torch.float32, device=dev) if need[1] else None
     gs = torch.empty((1,), dtype=torch.float32, device=dev) if need[2] else None
-    ws = torch.empty(int(nbytes.value), dtype=torch.uint8, device=dev)
-    with torch.cuda.device(dev):
-        stream = torch.cuda.current_stream(dev).cuda_stream
-        st = L.gmi_backward(points.data_ptr(), values.data_ptr(), N, C, int(H), int(W), ctypes.byref(p),
-                            image.data_ptr(), den.data_ptr(), shift.data_ptr(), grad_image.data_ptr(),
-                            gp.data_ptr() if gp is not None else None, gv.data_ptr() if gv is not None else None,
-                            gs.data_ptr() if gs is not None else None, ws.data_ptr(), int(nbytes.value), stream)
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    ws = _workspace(dev, stream, nbytes)
+    if torch.cuda.current_device() != dev.index:
+        with torch.cuda.device(dev):
+            return interpolate_backward(points, values, sigma, H, W, image, den, shift, grad_image,
+                                        radius_sigmas=radius_sigmas, mode=mode, bin_px=bin_px, variant=variant,
+                                        need=need, check=check)
+    st = _lib.load().gmi_backward(points.data_ptr(), values.data_ptr(), N, C, H, W, ctypes.byref(p),
+                                  image.data_ptr(), den.data_ptr(), shift.data_ptr(), grad_image.data_ptr(),
+                                  gp.data_ptr() if gp is not None else None,
+                                  gv.data_ptr() if gv is not None else None,
+                                  gs.data_ptr() if gs is not None else None, ws.data_ptr(), ws.numel(), stream)
     _lib.check(st, "gmi_backward")
     return gp, gv, gs
+
+
+_sigma_cache = {}
+
+
+def _sigma_value(sigma_t) -> float:
+    """Host value of sigma.  Reading a CUDA scalar synchronises the device, so
+    the value is cached per (tensor, version): an unchanged sigma tensor costs
+    one read, a sigma updated in place (optimizer step) is read again."""
+    import torch
+    if not isinstance(sigma_t, torch.Tensor):
+        return float(sigma_t)
+    if sigma_t.device.type == "cpu":
+        return float(sigma_t)
+    key = (sigma_t.data_ptr(), sigma_t._version)
+    v = _sigma_cache.get(key)
+    if v is None:
+        if len(_sigma_cache) > 4096:
+            _sigma_cache.clear()
+        v = _sigma_cache[key] = float(sigma_t)
+    return v
 
 
 def _autograd_function():
@@ -138,29 +208,31 @@ def _autograd_function():
 
     class GMIFunction(torch.autograd.Function):
         """Eq. 1 / Eq. 2 as a differentiable op: forward and backward both run
-        in libgmi's kernels; the forward saves image, den and shift (the bins
-        are rebuilt in the backward)."""
+        in libgmi's kernels; the forward keeps image, den and shift for the
+        backward (the bins are rebuilt there)."""
 
         @staticmethod
         def forward(ctx, points, values, sigma_t, H, W, radius_sigmas, mode, bin_px, variant):
-            sigma = float(sigma_t)
+            sigma = _sigma_value(sigma_t)
             img, den, shift = interpolate(points, values, sigma, H, W, radius_sigmas=radius_sigmas, mode=mode,
                                           bin_px=bin_px, variant=variant, return_aux=True)
-            ctx.save_for_backward(points, values, img, den, shift)
+            ctx.set_materialize_grads(False)
+            ctx.save_for_backward(points, values)
+            ctx.aux = (img, den, shift)
             ctx.cfg = (sigma, H, W, radius_sigmas, mode, bin_px, variant, isinstance(sigma_t, torch.Tensor))
-            ctx.mark_non_differentiable(den, shift)
-            return img, den, shift
+            return img
 
         @staticmethod
-        def backward(ctx, g, _gden, _gshift):
-            points, values, img, den, shift = ctx.saved_tensors
-            sigma, H, W, k, mode, bin_px, variant, sig_is_t = ctx.cfg
-            need = (ctx.needs_input_grad[0], ctx.needs_input_grad[1], ctx.needs_input_grad[2] and sig_is_t)
+        def backward(ctx, g):
             if g is None:
                 return (None,) * 9
-            gp, gv, gs = interpolate_backward(points, values, sigma, H, W, img, den, shift, g.float(),
-                                              radius_sigmas=k, mode=mode, bin_px=bin_px, variant=variant,
-                                              need=(need[0], need[1], need[2]))
+            points, values = ctx.saved_tensors
+            img, den, shift = ctx.aux
+            sigma, H, W, k, mode, bin_px, variant, sig_is_t = ctx.cfg
+            need = (ctx.needs_input_grad[0], ctx.needs_input_grad[1], ctx.needs_input_grad[2] and sig_is_t)
+            gp, gv, gs = interpolate_backward(points.detach(), values.detach(), sigma, H, W, img, den, shift,
+                                              g.float(), radius_sigmas=k, mode=mode, bin_px=bin_px,
+                                              variant=variant, need=need)
             gsig = gs.reshape(()) if gs is not None else None
             return gp, gv, gsig, None, None, None, None, None, None
 
@@ -178,9 +250,8 @@ def gmi_interpolate(points, values, sigma, H: int, W: int, *, radius_sigmas: flo
     global _GMIFunction
     if _GMIFunction is None:
         _GMIFunction = _autograd_function()
-    img, _, _ = _GMIFunction.apply(points, values, sigma, int(H), int(W), float(radius_sigmas), mode,
-                                   int(bin_px), int(variant))
-    return img
+    return _GMIFunction.apply(points, values, sigma, int(H), int(W), float(radius_sigmas), mode,
+                              int(bin_px), int(variant))
 
 
 class BatchPlan:
@@ -232,6 +303,42 @@ class BatchPlan:
                    "gmi_forward_batched")
         self._keep = keep   # inputs stay referenced until the next call
         return outs
+
+    def backward(self, images):
+        """Batched backward.  Each entry: ``points``, ``values``, ``sigma``,
+        ``H``, ``W``, ``image``, ``den``, ``shift`` (forward outputs),
+        ``grad`` (upstream [H,W,C]) and optionally ``bin_px`` and ``need``
+        (points, values, sigma).  Returns a list of (grad_points, grad_values,
+        grad_sigma) tuples (None where not needed)."""
+        import torch
+        n = len(images)
+        descs = (_lib.GradDesc * max(1, n))()
+        res, keep, dev = [], [], None
+        for i, im in enumerate(images):
+            P, V = _check_inputs(im["points"], im["values"])
+            dev = P.device
+            N, C = int(P.shape[0]), int(V.shape[1])
+            need = im.get("need", (True, True, True))
+            gp = torch.empty((N, 2), dtype=torch.float32, device=dev) if need[0] else None
+            gv = torch.empty((N, C), dtype=torch.float32, device=dev) if need[1] else None
+            gs = torch.empty((1,), dtype=torch.float32, device=dev) if need[2] else None
+            img, den, shift = im["image"].contiguous(), im["den"].contiguous(), im["shift"].contiguous()
+            g = im["grad"].contiguous().float()
+            keep += [P, V, img, den, shift, g]
+            d = descs[i]
+            d.points, d.values = P.data_ptr(), V.data_ptr()
+            d.image, d.den, d.shift, d.grad_image = img.data_ptr(), den.data_ptr(), shift.data_ptr(), g.data_ptr()
+            d.grad_points = gp.data_ptr() if gp is not None else None
+            d.grad_values = gv.data_ptr() if gv is not None else None
+            d.grad_sigma = gs.data_ptr() if gs is not None else None
+            d.N, d.H, d.W = N, int(im["H"]), int(im["W"])
+            d.sigma = float(im["sigma"])
+            d.bin_px = int(im.get("bin_px", 0))
+            res.append((gp, gv, gs))
+        stream = torch.cuda.current_stream(dev).cuda_stream if dev is not None else None
+        _lib.check(_lib.load().gmi_backward_batched(self._h, descs, n, stream), "gmi_backward_batched")
+        self._keep_bwd = keep
+        return res
 
     def close(self):
         if getattr(self, "_h", None):
@@ -327,3 +434,66 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def _batch_function():
+    import torch
+
+    class GMIBatchFunction(torch.autograd.Function):
+        """B images through one batched forward (CUDA-graph replay) and one
+        batched backward.  Inputs are flattened: points_0, values_0, sigma_0,
+        points_1, ...; returns the B images."""
+
+        @staticmethod
+        def forward(ctx, plan, sizes, *flat):
+            B = len(sizes)
+            ims = []
+            for b in range(B):
+                P, V, S = flat[3 * b], flat[3 * b + 1], flat[3 * b + 2]
+                H, W = sizes[b]
+                C = V.shape[1]
+                ims.append({"points": P, "values": V, "sigma": _sigma_value(S), "H": H, "W": W,
+                            "den": torch.empty((H, W), dtype=torch.float32, device=P.device),
+                            "shift": torch.empty((H, W), dtype=torch.float32, device=P.device)})
+            outs = plan.forward(ims, use_graph=True)
+            for im, o in zip(ims, outs):
+                im["image"] = o
+            ctx.set_materialize_grads(False)
+            ctx.plan, ctx.ims = plan, ims
+            ctx.sig_t = [isinstance(flat[3 * b + 2], torch.Tensor) for b in range(B)]
+            return tuple(outs)
+
+        @staticmethod
+        def backward(ctx, *grads):
+            ims = ctx.ims
+            req = []
+            for b, (im, g) in enumerate(zip(ims, grads)):
+                if g is None:
+                    g = torch.zeros_like(im["image"])
+                need = (ctx.needs_input_grad[2 + 3 * b], ctx.needs_input_grad[3 + 3 * b],
+                        ctx.needs_input_grad[4 + 3 * b] and ctx.sig_t[b])
+                req.append(dict(im, points=im["points"].detach(), values=im["values"].detach(), grad=g, need=need))
+            res = ctx.plan.backward(req)
+            out = [None, None]
+            for gp, gv, gs in res:
+                out += [gp, gv, gs.reshape(()) if gs is not None else None]
+            return tuple(out)
+
+    return GMIBatchFunction
+
+
+_GMIBatchFunction = None
+
+
+def gmi_interpolate_batch(plan, points, values, sigmas, sizes):
+    """Differentiable batched interpolation on a BatchPlan: lists of points
+    [N_b,2], values [N_b,C], sigmas (floats or 0-d tensors) and sizes (H, W);
+    returns the list of images.  The whole batch is one forward launch (graph
+    replay) and one batched backward."""
+    global _GMIBatchFunction
+    if _GMIBatchFunction is None:
+        _GMIBatchFunction = _batch_function()
+    flat = []
+    for P, V, S in zip(points, values, sigmas):
+        flat += [P, V, S]
+    return list(_GMIBatchFunction.apply(plan, [tuple(map(int, hw)) for hw in sizes], *flat))

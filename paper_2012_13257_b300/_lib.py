@@ -45,6 +45,14 @@ class ImageDesc(ctypes.Structure):
                 ("H", ctypes.c_int), ("W", ctypes.c_int), ("sigma", ctypes.c_float), ("bin_px", ctypes.c_int)]
 
 
+class GradDesc(ctypes.Structure):
+    _fields_ = [("points", ctypes.c_void_p), ("values", ctypes.c_void_p), ("image", ctypes.c_void_p),
+                ("den", ctypes.c_void_p), ("shift", ctypes.c_void_p), ("grad_image", ctypes.c_void_p),
+                ("grad_points", ctypes.c_void_p), ("grad_values", ctypes.c_void_p), ("grad_sigma", ctypes.c_void_p),
+                ("N", ctypes.c_int64), ("H", ctypes.c_int), ("W", ctypes.c_int), ("sigma", ctypes.c_float),
+                ("bin_px", ctypes.c_int)]
+
+
 class ServerConfig(ctypes.Structure):
     _fields_ = [("budget_bytes", ctypes.c_size_t), ("max_batch_images", ctypes.c_int),
                 ("max_batch_pixels", ctypes.c_int64), ("n_streams", ctypes.c_int), ("C", ctypes.c_int),
@@ -72,6 +80,7 @@ SIGNATURES = {
     "gmi_batch_plan_destroy": (_int, [_vp]),
     "gmi_batch_plan_bytes": (_sz, [_vp]),
     "gmi_forward_batched": (_int, [_vp, ctypes.POINTER(ImageDesc), _int, _int, _vp]),
+    "gmi_backward_batched": (_int, [_vp, ctypes.POINTER(GradDesc), _int, _vp]),
     "gmi_server_config_default": (_int, [ctypes.POINTER(ServerConfig)]),
     "gmi_server_create": (_int, [ctypes.POINTER(ServerConfig), ctypes.POINTER(_vp)]),
     "gmi_server_submit": (_int, [_vp, _vp, _vp, _i64, _int, _int, _f, _vp, _u64p]),

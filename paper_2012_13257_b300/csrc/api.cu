@@ -15,7 +15,7 @@
 namespace gmi {
 
 cudaError_t launch_near(const KArgs& a, int mth, int mtw, bool trunc, int grid, cudaStream_t s);
-cudaError_t launch_near_plan(const KArgs& a, bool trunc, cudaStream_t s);
+cudaError_t launch_scatter_plan(const KArgs& a, bool trunc, int n_scatter, cudaStream_t s);
 int near_blocks_per_sm(int mth, int mtw, int C, bool trunc);
 cudaError_t launch_far(const KArgs& a, int mth, int mtw, int grid, cudaStream_t s);
 __global__ void bin_count_kernel(KArgs a);
@@ -156,11 +156,12 @@ DevWork bind_ws(void* ws, const WsLayout& L) {
   return w;
 }
 
-// Binning (memset, count, scan, scatter) and the near-kernel plan.  Grid
-// sizes come from a's totals; in a batched call (a.totals set) they are the
-// plan's capacities and the kernels read the real totals from the device.
+// Binning (memset, count, scan, scatter) and, with plan set, the near-kernel
+// plan.  Grid sizes come from a's totals; in a batched call (a.totals set)
+// they are the plan's capacities and the kernels read the real totals from
+// the device.
 gmi_status run_bin_and_plan(KArgs& a, const WsLayout& L, void* ws, int mth, int mtw, bool trunc,
-                            cudaStream_t s) {
+                            cudaStream_t s, bool plan) {
   const ProfileMark pb = profile_begin(GMI_STAGE_BIN, s);
   cudaError_t e;
   const int sms = device_sm_count();
@@ -173,16 +174,21 @@ gmi_status run_bin_and_plan(KArgs& a, const WsLayout& L, void* ws, int mth, int 
   a.cap_slots = L.cap_slots;
   a.mth = mth;
   a.mtw = mtw;
+  int gb = 0;
   if (a.n_total > 0) {
-    const int gb = (int)std::min<long long>(a.ch_total, (long long)sms * 32);
+    gb = (int)std::min<long long>(a.ch_total, (long long)sms * 32);
     bin_count_kernel<<<gb, 256, 0, s>>>(a);
     const int ns = (int)((a.nb_total + kScanChunk - 1) / kScanChunk);
     scan_partial_kernel<<<ns, 256, 0, s>>>(a.w.off, a.nb_total, a.w.partials, a.totals);
     scan_final_kernel<<<ns, 256, 0, s>>>(a.w.off, a.nb_total, a.w.partials, a.totals);
+    if ((e = cudaGetLastError()) != cudaSuccess) return GMI_ERR_CUDA;
+  }
+  if (plan) {
+    if ((e = launch_scatter_plan(a, trunc, gb, s)) != cudaSuccess) return GMI_ERR_CUDA;
+  } else if (gb > 0) {
     bin_scatter_kernel<<<gb, 256, 0, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return GMI_ERR_CUDA;
   }
-  if ((e = launch_near_plan(a, trunc, s)) != cudaSuccess) return GMI_ERR_CUDA;
   profile_end(pb, s);
   return GMI_OK;
 }
@@ -190,7 +196,7 @@ gmi_status run_bin_and_plan(KArgs& a, const WsLayout& L, void* ws, int mth, int 
 // Binning + plan + near + far on prepared arguments (single image or batch).
 gmi_status run_forward_pipeline(KArgs& a, const WsLayout& L, void* ws, int mth, int mtw, bool trunc,
                                 cudaStream_t s) {
-  gmi_status st = run_bin_and_plan(a, L, ws, mth, mtw, trunc, s);
+  gmi_status st = run_bin_and_plan(a, L, ws, mth, mtw, trunc, s, true);
   if (st != GMI_OK) return st;
   cudaError_t e;
   const int sms = device_sm_count();

@@ -27,7 +27,7 @@ WsLayout ws_layout(long long n_total, long long nb_total, long long mt_total, lo
                    size_t slot_bytes, long long extra_bytes);
 DevWork bind_ws(void* ws, const WsLayout& L);
 gmi_status run_bin_and_plan(KArgs& a, const WsLayout& L, void* ws, int mth, int mtw, bool trunc,
-                            cudaStream_t s);
+                            cudaStream_t s, bool plan);
 gmi_status run_forward_pipeline(KArgs& a, const WsLayout& L, void* ws, int mth, int mtw, bool trunc,
                                 cudaStream_t s);
 gmi_status read_status(const void* ws, cudaStream_t s);

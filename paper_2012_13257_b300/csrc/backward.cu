@@ -23,133 +23,152 @@
 
 #include "api_internal.h"
 #include "far_collect.cuh"
+#include "bwd_args.h"
 
 namespace gmi {
 
 constexpr float kCoreLog2 = 12.0f;   // core pixel: den >= 2^-kCoreLog2 and no shift
 constexpr float kRelLog2 = 26.0f;    // pairs below 2^-kRelLog2 of their pixel's den are dropped
 
-struct BwdArgs {
-  const float* image;   // [H,W,C] forward output
-  const float* den;     // [H,W]
-  const float* shift;   // [H,W]
-  const float* grad;    // [H,W,C] upstream gradient
-  float* gpts;          // [N,2] or null
-  float* gvals;         // [N,C] or null
-  float* gsig;          // [1] or null
-  int trunc;
-  float inv_s2, inv_s3; // 1/sigma^2, 1/sigma^3
-};
+__device__ __forceinline__ BwdImage bwd_image(const BwdArgs& b, int img) { return b.table ? b.table[img] : b.one; }
 
 // Per pixel: G_c = g_c / den and s' = sum_c G_c c_c(q) for core pixels (zero
 // elsewhere); micro-tiles with a non-core pixel are queued for the fallback.
 template <int C>
-__global__ void __launch_bounds__(256) bwd_prep_kernel(KArgs a, BwdArgs b) {
-  const ImageGeom& g = a.g0;
-  const long long px = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long npx = (long long)g.H * g.W;
-  if (px >= npx) return;
-  const float d = b.den[px];
-  const float sh = b.shift[px];
-  float G[4] = {0.f, 0.f, 0.f, 0.f};
-  float sp = 0.0f;
-  if (d > 0.0f) {
-    const float inv = 1.0f / d;
+__global__ void __launch_bounds__(256) bwd_prep_kernel(KArgs a_in, BwdArgs b) {
+  const KArgs a = resolve(a_in);
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long gp = (long long)blockIdx.x * blockDim.x + threadIdx.x; gp < a.px_total; gp += stride) {
+    const int img = find_image<3>(a, gp);
+    const ImageGeom& g = *geom_ptr(a, img);
+    const BwdImage bi = bwd_image(b, img);
+    const long long px = gp - g.px_base;
+    if (px == 0 && bi.gsig) *bi.gsig = 0.0f;   // accumulated by the later kernels
+    const float d = bi.den[px];
+    const float sh = bi.shift[px];
+    float G[4] = {0.f, 0.f, 0.f, 0.f};
+    float sp = 0.0f;
+    if (d > 0.0f) {
+      const float inv = 1.0f / d;
 #pragma unroll
-    for (int c = 0; c < C; ++c) {
-      G[c] = b.grad[px * C + c] * inv;
-      sp = fmaf(G[c], b.image[px * C + c], sp);
+      for (int c = 0; c < C; ++c) {
+        G[c] = bi.grad[px * C + c] * inv;
+        sp = fmaf(G[c], bi.image[px * C + c], sp);
+      }
     }
-  }
-  const bool core = d > 0.0f && (b.trunc || (sh == 0.0f && d >= exp2f(-kCoreLog2)));
-  float4 v0, v1 = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (!core) {
-    v0 = make_float4(0.f, 0.f, 0.f, 0.f);
-  } else if (C == 4) {
-    v0 = make_float4(G[0], G[1], G[2], G[3]);
-    v1.x = sp;
-  } else {
-    v0 = make_float4(G[0], G[1], G[2], 0.0f);
-    if (C == 1) v0.y = 0.0f;
-    v0.w = sp;
-  }
-  a.w.pplane[px] = v0;
-  if (C == 4) a.w.pplane[npx + px] = v1;
-  if (!core && d > 0.0f) {
-    const int y = (int)(px / g.W), x = (int)(px % g.W);
-    const unsigned mt = (unsigned)((y / a.mth) * g.mtx + x / a.mtw);
-    if (atomicOr(&a.w.fbflag[mt], 1u) == 0u) {
-      const unsigned q = atomicAdd(&a.w.status[kFbCount], 1u);
-      a.w.fbq[q] = mt;
+    const bool core = d > 0.0f && (b.trunc || (sh == 0.0f && d >= exp2f(-kCoreLog2)));
+    float4 v0, v1 = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (!core) {
+      v0 = make_float4(0.f, 0.f, 0.f, 0.f);
+    } else if (C == 4) {
+      v0 = make_float4(G[0], G[1], G[2], G[3]);
+      v1.x = sp;
+    } else {
+      v0 = make_float4(G[0], G[1], G[2], 0.0f);
+      if (C == 1) v0.y = 0.0f;
+      v0.w = sp;
+    }
+    a.w.pplane[gp] = v0;
+    if (C == 4) a.w.pplane[a.px_total + gp] = v1;
+    if (!core && d > 0.0f) {
+      const int y = (int)(px / g.W), x = (int)(px % g.W);
+      const unsigned mt = (unsigned)((y / a.mth) * g.mtx + x / a.mtw);
+      if (atomicOr(&a.w.fbflag[g.mt_base + mt], 1u) == 0u) {
+        const unsigned q = atomicAdd(&a.w.status[kFbCount], 1u);
+        a.w.fbq[q] = make_uint2((unsigned)img, mt);
+      }
     }
   }
 }
 
 // Point-centric gradients over core pixels; one thread per bin-sorted point.
 template <int C, bool TRUNC>
-__global__ void __launch_bounds__(256) bwd_point_kernel(KArgs a, BwdArgs b, float rcore2) {
-  const ImageGeom& g = a.g0;
-  const long long npx = (long long)g.H * g.W;
+__global__ void __launch_bounds__(256) bwd_point_kernel(KArgs a_in, BwdArgs b, float rcore_log2) {
+  const KArgs a = resolve(a_in);
+  const unsigned full = 0xffffffffu;
   float D = 0.0f;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < g.n; i += (long long)gridDim.x * blockDim.x) {
-    const float2 p = a.w.sxy[i];
-    const float4 cv = a.w.sval[i];
-    const float c4[4] = {cv.x, cv.y, cv.z, cv.w};
-    float A[4] = {0.f, 0.f, 0.f, 0.f};
-    float Bx = 0.0f, By = 0.0f;
-    const float R = sqrtf(rcore2);
-    const int iy0 = max(0, (int)ceilf(p.y - R - 0.5f));
-    const int iy1 = min(g.H - 1, (int)floorf(p.y + R - 0.5f));
-    for (int iy = iy0; iy <= iy1; ++iy) {
-      const float dy = (float)iy + 0.5f - p.y;
-      const float dy2 = dy * dy;
-      const float rem = rcore2 - dy2;
-      if (rem < 0.0f) continue;
-      const float h = sqrtf(rem);
-      const int ix0 = max(0, (int)ceilf(p.x - h - 0.5f));
-      const int ix1 = min(g.W - 1, (int)floorf(p.x + h - 0.5f));
-      const float4* __restrict__ P = a.w.pplane + (long long)iy * g.W;
-      float rowWt = 0.0f;
-      float dx = (float)ix0 + 0.5f - p.x;
-      for (int ix = ix0; ix <= ix1; ++ix, dx += 1.0f) {
-        const float d2 = fmaf(dx, dx, dy2);
-        float w = ex2(-g.kappa * d2);
-        if (TRUNC && !(d2 <= g.r2k)) w = 0.0f;
-        const float4 pv = __ldg(&P[ix]);
-        float Gv[4] = {pv.x, pv.y, pv.z, pv.w};
-        float sp;
-        if (C == 4) {
-          sp = __ldg(&a.w.pplane[npx + (long long)iy * g.W + ix]).x;
-        } else {
-          sp = pv.w;
+  for (long long i0 = (long long)blockIdx.x * blockDim.x; i0 < a.n_total; i0 += (long long)gridDim.x * blockDim.x) {
+    const long long i = i0 + threadIdx.x;
+    const bool valid = i < a.n_total;
+    int img = 0;
+    float Dp = 0.0f;
+    if (valid) {
+      img = find_image<2>(a, i);
+      const ImageGeom& g = *geom_ptr(a, img);
+      const BwdImage bi = bwd_image(b, img);
+      const float4* __restrict__ plane = a.w.pplane + g.px_base;
+      const float4* __restrict__ plane2 = a.w.pplane + a.px_total + g.px_base;
+      const float rcore2 = TRUNC ? g.r2k : rcore_log2 / g.kappa;
+      const float2 p = a.w.sxy[i];
+      const float4 cv = a.w.sval[i];
+      const float c4[4] = {cv.x, cv.y, cv.z, cv.w};
+      float A[4] = {0.f, 0.f, 0.f, 0.f};
+      float Bx = 0.0f, By = 0.0f;
+      const float R = sqrtf(rcore2);
+      const int iy0 = max(0, (int)ceilf(p.y - R - 0.5f));
+      const int iy1 = min(g.H - 1, (int)floorf(p.y + R - 0.5f));
+      for (int iy = iy0; iy <= iy1; ++iy) {
+        const float dy = (float)iy + 0.5f - p.y;
+        const float dy2 = dy * dy;
+        const float rem = rcore2 - dy2;
+        if (rem < 0.0f) continue;
+        const float h = sqrtf(rem);
+        const int ix0 = max(0, (int)ceilf(p.x - h - 0.5f));
+        const int ix1 = min(g.W - 1, (int)floorf(p.x + h - 0.5f));
+        const float4* __restrict__ P = plane + (long long)iy * g.W;
+        float rowWt = 0.0f;
+        float dx = (float)ix0 + 0.5f - p.x;
+#pragma unroll 4
+        for (int ix = ix0; ix <= ix1; ++ix, dx += 1.0f) {
+          const float d2 = fmaf(dx, dx, dy2);
+          float w = ex2(-g.kappa * d2);
+          if (TRUNC && !(d2 <= g.r2k)) w = 0.0f;
+          const float4 pv = __ldg(&P[ix]);
+          const float Gv[4] = {pv.x, pv.y, pv.z, pv.w};
+          const float sp = C == 4 ? __ldg(&plane2[(long long)iy * g.W + ix]).x : pv.w;
+          float t = -sp;
+#pragma unroll
+          for (int c = 0; c < C; ++c) t = fmaf(Gv[c], c4[c], t);
+#pragma unroll
+          for (int c = 0; c < C; ++c) A[c] = fmaf(w, Gv[c], A[c]);
+          const float wt = w * t;
+          Bx = fmaf(wt, dx, Bx);
+          rowWt += wt;
+          Dp = fmaf(wt, d2, Dp);
         }
-        float t = -sp;
-#pragma unroll
-        for (int c = 0; c < C; ++c) t = fmaf(Gv[c], c4[c], t);
-#pragma unroll
-        for (int c = 0; c < C; ++c) A[c] = fmaf(w, Gv[c], A[c]);
-        const float wt = w * t;
-        Bx = fmaf(wt, dx, Bx);
-        rowWt += wt;
-        D = fmaf(wt, d2, D);
+        By = fmaf(rowWt, dy, By);
       }
-      By = fmaf(rowWt, dy, By);
-    }
-    const unsigned o = a.w.perm[i];
-    if (b.gvals) {
+      const unsigned o = a.w.perm[i];
+      if (bi.gvals) {
 #pragma unroll
-      for (int c = 0; c < C; ++c) b.gvals[(long long)o * C + c] = A[c];
+        for (int c = 0; c < C; ++c) bi.gvals[(long long)o * C + c] = A[c];
+      }
+      if (bi.gpts) {
+        bi.gpts[2LL * o] = Bx * bi.inv_s2;
+        bi.gpts[2LL * o + 1] = By * bi.inv_s2;
+      }
     }
-    if (b.gpts) {
-      b.gpts[2LL * o] = Bx * b.inv_s2;
-      b.gpts[2LL * o + 1] = By * b.inv_s2;
+    if (b.table) {
+      // batched: one float atomic per (warp, image) into that image's sigma gradient
+      const unsigned same = __match_any_sync(full, valid ? img : -1);
+      if (valid) {
+        float s2 = 0.0f;
+        for (unsigned m = same; m; m &= m - 1) s2 += __shfl_sync(same, Dp, __ffs(m) - 1);
+        if ((int)(threadIdx.x & 31) == __ffs(same) - 1) {
+          const BwdImage bi = bwd_image(b, img);
+          if (bi.gsig) atomicAdd(bi.gsig, s2 * bi.inv_s3);
+        }
+      }
+    } else {
+      D += Dp;
     }
   }
-  // sigma: block sum -> partial; the last block adds the partials in order
+  if (b.table) return;
+  // single image: block sum -> partial; the last block adds the partials in order
   __shared__ float red[8];
   __shared__ bool last;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) D += __shfl_xor_sync(0xffffffffu, D, o);
+  for (int o = 16; o > 0; o >>= 1) D += __shfl_xor_sync(full, D, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = D;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -164,18 +183,18 @@ __global__ void __launch_bounds__(256) bwd_point_kernel(KArgs a, BwdArgs b, floa
     __threadfence();
     float t = 0.0f;
     for (unsigned k = 0; k < gridDim.x; ++k) t += __ldcg(&a.w.sig_part[k]);
-    if (b.gsig) *b.gsig = t * b.inv_s3;
+    if (b.one.gsig) *b.one.gsig += t * b.one.inv_s3;
   }
 }
 
 // Non-core pixels: one warp per queued micro-tile, lanes = (pixel, part).
 template <int C>
-__global__ void __launch_bounds__(32 * kFarWarps) bwd_fallback_kernel(KArgs a, BwdArgs b) {
+__global__ void __launch_bounds__(32 * kFarWarps) bwd_fallback_kernel(KArgs a_in, BwdArgs b) {
+  const KArgs a = resolve(a_in);
   __shared__ unsigned lists[kFarWarps][kFarCap];
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   unsigned* L = lists[wid];
-  const ImageGeom& g = a.g0;
   const unsigned nq = a.w.status[kFbCount];
   const int PS = a.mth * a.mtw, nparts = 32 / PS;
   const int slot = lane % PS, part = lane / PS;
@@ -185,7 +204,11 @@ __global__ void __launch_bounds__(32 * kFarWarps) bwd_fallback_kernel(KArgs a, B
     if (lane == 0) e = atomicAdd(&a.w.status[kFbHead], 1u);
     e = __shfl_sync(full, e, 0);
     if (e >= nq) break;
-    const unsigned mt = a.w.fbq[e];
+    const uint2 qe = a.w.fbq[e];
+    const int img = (int)qe.x;
+    const unsigned mt = qe.y;
+    const ImageGeom g = a.w.table ? a.w.table[img] : a.g0;
+    const BwdImage bi = bwd_image(b, img);
     const int mt_x = (int)(mt % (unsigned)g.mtx), mt_y = (int)(mt / (unsigned)g.mtx);
     const int x0 = mt_x * a.mtw, y0 = mt_y * a.mth;
     const int nx = min(a.mtw, g.W - x0), ny = min(a.mth, g.H - y0);
@@ -200,15 +223,15 @@ __global__ void __launch_bounds__(32 * kFarWarps) bwd_fallback_kernel(KArgs a, B
     float d = 0.0f, sh = 0.0f, G[4] = {0.f, 0.f, 0.f, 0.f}, sp = 0.0f;
     bool mine = false;
     if (valid) {
-      d = b.den[px];
-      sh = b.shift[px];
+      d = bi.den[px];
+      sh = bi.shift[px];
       mine = d > 0.0f && !(sh == 0.0f && d >= exp2f(-kCoreLog2));
       if (mine) {
         const float inv = 1.0f / d;
 #pragma unroll
         for (int c = 0; c < C; ++c) {
-          G[c] = b.grad[px * C + c] * inv;
-          sp = fmaf(G[c], b.image[px * C + c], sp);
+          G[c] = bi.grad[px * C + c] * inv;
+          sp = fmaf(G[c], bi.image[px * C + c], sp);
         }
       }
     }
@@ -244,13 +267,13 @@ __global__ void __launch_bounds__(32 * kFarWarps) bwd_fallback_kernel(KArgs a, B
           for (int c = 0; c < C; ++c) tt = fmaf(G[c], c4[c], tt);
           const float wt = w * tt;
           const unsigned o = a.w.perm[idx];
-          if (b.gvals) {
+          if (bi.gvals) {
 #pragma unroll
-            for (int c = 0; c < C; ++c) atomicAdd(&b.gvals[(long long)o * C + c], w * G[c]);
+            for (int c = 0; c < C; ++c) atomicAdd(&bi.gvals[(long long)o * C + c], w * G[c]);
           }
-          if (b.gpts) {
-            atomicAdd(&b.gpts[2LL * o], wt * dx * b.inv_s2);
-            atomicAdd(&b.gpts[2LL * o + 1], wt * dy * b.inv_s2);
+          if (bi.gpts) {
+            atomicAdd(&bi.gpts[2LL * o], wt * dx * bi.inv_s2);
+            atomicAdd(&bi.gpts[2LL * o + 1], wt * dy * bi.inv_s2);
           }
           sig = fmaf(wt, ee - s0, sig);   // ee is already d^2 - shift when shift > 0
         }
@@ -259,7 +282,7 @@ __global__ void __launch_bounds__(32 * kFarWarps) bwd_fallback_kernel(KArgs a, B
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) sig += __shfl_xor_sync(full, sig, o);
-    if (lane == 0 && sig != 0.0f && b.gsig) atomicAdd(b.gsig, sig * b.inv_s3);
+    if (lane == 0 && sig != 0.0f && bi.gsig) atomicAdd(bi.gsig, sig * bi.inv_s3);
   }
 }
 
@@ -269,7 +292,7 @@ long long bwd_extra_bytes(long long N, int C, int H, int W) {
   const long long planes = px * 16 * (C == 4 ? 2 : 1);
   auto al = [](long long v) { return (v + 255) / 256 * 256; };
   (void)N;
-  return al(planes) + al(mt * 4) + al(mt * 4) + al((long long)kSigParts * 4);
+  return al(planes) + al(mt * 4) + al(mt * 8) + al((long long)kSigParts * 4);
 }
 
 void bind_bwd(DevWork& w, void* extra, long long N, int C, int H, int W, long long mt_total) {
@@ -283,21 +306,21 @@ void bind_bwd(DevWork& w, void* extra, long long N, int C, int H, int W, long lo
   p += al(px * 16 * (C == 4 ? 2 : 1));
   w.fbflag = (unsigned*)p;
   p += al(mt * 4);
-  w.fbq = (unsigned*)p;
-  p += al(mt * 4);
+  w.fbq = (uint2*)p;
+  p += al(mt * 8);
   w.sig_part = (float*)p;
 }
 
 template <int C>
 static cudaError_t launch_bwd_c(const KArgs& a, const BwdArgs& b, cudaStream_t s) {
-  const ImageGeom& g = a.g0;
-  const long long npx = (long long)g.H * g.W;
-  bwd_prep_kernel<C><<<(unsigned)((npx + 255) / 256), 256, 0, s>>>(a, b);
-  const float rcore2 = b.trunc ? g.r2k : (kRelLog2 + kCoreLog2) / g.kappa;
-  const unsigned blocks = (unsigned)std::max<long long>(1, std::min<long long>((g.n + 255) / 256, kSigParts));
-  if (b.trunc) bwd_point_kernel<C, true><<<blocks, 256, 0, s>>>(a, b, rcore2);
-  else bwd_point_kernel<C, false><<<blocks, 256, 0, s>>>(a, b, rcore2);
-  if (!b.trunc) bwd_fallback_kernel<C><<<device_sm_count() * 4, 32 * kFarWarps, 0, s>>>(a, b);
+  const int sms = device_sm_count();
+  const unsigned prep_blocks = (unsigned)std::max<long long>(1, std::min<long long>((a.px_total + 255) / 256, sms * 32LL));
+  bwd_prep_kernel<C><<<prep_blocks, 256, 0, s>>>(a, b);
+  const float rcore_log2 = kRelLog2 + kCoreLog2;   // kappa * R_core^2
+  const unsigned blocks = (unsigned)std::max<long long>(1, std::min<long long>((a.n_total + 255) / 256, kSigParts));
+  if (b.trunc) bwd_point_kernel<C, true><<<blocks, 256, 0, s>>>(a, b, rcore_log2);
+  else bwd_point_kernel<C, false><<<blocks, 256, 0, s>>>(a, b, rcore_log2);
+  if (!b.trunc) bwd_fallback_kernel<C><<<sms * 4, 32 * kFarWarps, 0, s>>>(a, b);
   return cudaGetLastError();
 }
 
@@ -354,19 +377,23 @@ extern "C" gmi_status gmi_backward(const float* points, const float* values, int
   a.ch_total = (N + kChunk - 1) / kChunk;
   a.mt_total = mt;
   const bool trunc = p->mode == GMI_MODE_TRUNCATED;
-  if ((st = run_bin_and_plan(a, L, workspace, mth, mtw, trunc, s)) != GMI_OK) return st;
+  // the bins only: the fallback derives its radii from den, not from the plan
+  if ((st = run_bin_and_plan(a, L, workspace, mth, mtw, trunc, s, false)) != GMI_OK) return st;
   if (cudaMemsetAsync(a.w.fbflag, 0, sizeof(unsigned) * (size_t)mt, s) != cudaSuccess) return GMI_ERR_CUDA;
+  a.px_total = (long long)H * W;
   BwdArgs b;
-  b.image = image;
-  b.den = den;
-  b.shift = shift;
-  b.grad = grad_image;
-  b.gpts = grad_points;
-  b.gvals = grad_values;
-  b.gsig = grad_sigma;
+  memset(&b, 0, sizeof(b));
+  b.one.image = image;
+  b.one.den = den;
+  b.one.shift = shift;
+  b.one.grad = grad_image;
+  b.one.gpts = grad_points;
+  b.one.gvals = grad_values;
+  b.one.gsig = grad_sigma;
+  b.one.inv_s2 = (float)(1.0 / ((double)p->sigma * p->sigma));
+  b.one.inv_s3 = (float)(1.0 / ((double)p->sigma * p->sigma * p->sigma));
+  b.table = nullptr;
   b.trunc = trunc ? 1 : 0;
-  b.inv_s2 = (float)(1.0 / ((double)p->sigma * p->sigma));
-  b.inv_s3 = (float)(1.0 / ((double)p->sigma * p->sigma * p->sigma));
   const ProfileMark pm = profile_begin(GMI_STAGE_BACKWARD, s);
   if (launch_backward(a, b, s) != cudaSuccess) return GMI_ERR_CUDA;
   profile_end(pm, s);

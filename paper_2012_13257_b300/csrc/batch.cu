@@ -13,6 +13,7 @@
 #include <mutex>
 
 #include "api_internal.h"
+#include "bwd_args.h"
 
 namespace gmi {
 
@@ -41,6 +42,17 @@ struct gmi_batch_plan {
   gmi::BatchSlot slot[2];
   int next = 0;
   cudaStream_t cap_stream = nullptr; // private stream the launch sequence is captured on
+  // backward pass: per-pixel planes, fallback queue and its own staging
+  char* bwd_base = nullptr;
+  size_t bwd_bytes = 0;
+  float4* pplane = nullptr;
+  unsigned* fbflag = nullptr;
+  uint2* fbq = nullptr;
+  char* bwd_host = nullptr;
+  char* bwd_dev = nullptr;
+  size_t bwd_stage = 0;
+  cudaEvent_t bwd_done = nullptr;
+  bool bwd_used = false;
   std::mutex mu;
 };
 
@@ -48,6 +60,31 @@ namespace gmi {
 
 static size_t stage_size(int max_images) {
   return (size_t)kTotCount * sizeof(long long) + sizeof(ImageGeom) * (size_t)max_images;
+}
+
+static size_t bwd_stage_size(int max_images) {
+  return stage_size(max_images) + sizeof(BwdImage) * (size_t)max_images;
+}
+
+static size_t al256(size_t v) { return (v + 255) / 256 * 256; }
+
+// Geometry of image i of a batch (bases from the running totals).
+static void batch_geom(ImageGeom& g, const gmi_batch_plan* p, long long N, int H, int W, float sigma, int bin_px,
+                       long long* npt, long long* nb, long long* nwt, long long* nch, long long* nmt, long long* npx) {
+  memset(&g, 0, sizeof(g));
+  fill_geom(g, N, H, W, sigma, p->params.radius_sigmas, bin_px > 0 ? bin_px : p->params.bin_px, p->mth, p->mtw);
+  g.pt_base = *npt;
+  g.bin_base = *nb;
+  g.wt_base = *nwt;
+  g.ch_base = *nch;
+  g.mt_base = *nmt;
+  g.px_base = *npx;
+  *npt += N;
+  *nb += (long long)g.nbx * g.nby;
+  *nwt += (long long)g.wtx * g.wty;
+  *nch += (N + kChunk - 1) / kChunk;
+  *nmt += (long long)g.mtx * g.mty;
+  *npx += (long long)H * W;
 }
 
 }  // namespace gmi
@@ -83,6 +120,21 @@ extern "C" gmi_status gmi_batch_plan_create(int max_images, int64_t max_points, 
     delete p;
     return GMI_ERR_CUDA;
   }
+  // backward regions (planes over all pixels, fallback queue, staging)
+  const size_t planes = al256(sizeof(float4) * (size_t)max_pixels * (C == 4 ? 2 : 1));
+  p->bwd_stage = al256(bwd_stage_size(max_images));
+  p->bwd_bytes = planes + al256(sizeof(unsigned) * (size_t)p->cap_mt) + al256(sizeof(uint2) * (size_t)p->cap_mt) +
+                 p->bwd_stage;
+  if (cudaMalloc((void**)&p->bwd_base, p->bwd_bytes) != cudaSuccess ||
+      cudaMallocHost((void**)&p->bwd_host, p->bwd_stage) != cudaSuccess ||
+      cudaEventCreateWithFlags(&p->bwd_done, cudaEventDisableTiming) != cudaSuccess) {
+    gmi_batch_plan_destroy(p);
+    return GMI_ERR_CUDA;
+  }
+  p->pplane = (float4*)p->bwd_base;
+  p->fbflag = (unsigned*)(p->bwd_base + planes);
+  p->fbq = (uint2*)(p->bwd_base + planes + al256(sizeof(unsigned) * (size_t)p->cap_mt));
+  p->bwd_dev = p->bwd_base + planes + al256(sizeof(unsigned) * (size_t)p->cap_mt) + al256(sizeof(uint2) * (size_t)p->cap_mt);
   for (int k = 0; k < 2; ++k) {
     p->slot[k].dev = (char*)p->base + p->L.total + k * p->stage_bytes;
     if (cudaMallocHost((void**)&p->slot[k].host, p->stage_bytes) != cudaSuccess ||
@@ -107,12 +159,18 @@ extern "C" gmi_status gmi_batch_plan_destroy(gmi_batch_plan* p) {
     if (p->slot[k].host) cudaFreeHost(p->slot[k].host);
   }
   if (p->base) cudaFree(p->base);
+  if (p->bwd_done) {
+    cudaEventSynchronize(p->bwd_done);
+    cudaEventDestroy(p->bwd_done);
+  }
+  if (p->bwd_base) cudaFree(p->bwd_base);
+  if (p->bwd_host) cudaFreeHost(p->bwd_host);
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
   delete p;
   return GMI_OK;
 }
 
-extern "C" size_t gmi_batch_plan_bytes(const gmi_batch_plan* p) { return p ? p->base_bytes : 0; }
+extern "C" size_t gmi_batch_plan_bytes(const gmi_batch_plan* p) { return p ? p->base_bytes + p->bwd_bytes : 0; }
 
 extern "C" gmi_status gmi_forward_batched(gmi_batch_plan* p, const gmi_image_desc* descs, int B, int use_graph,
                                           gmi_stream_t stream) {
@@ -134,30 +192,20 @@ extern "C" gmi_status gmi_forward_batched(gmi_batch_plan* p, const gmi_image_des
 
   long long* tot = (long long*)sl.host;
   ImageGeom* table = (ImageGeom*)(sl.host + kTotCount * sizeof(long long));
-  long long npt = 0, nb = 0, nwt = 0, nch = 0, nmt = 0;
+  long long npt = 0, nb = 0, nwt = 0, nch = 0, nmt = 0, npx = 0;
   for (int i = 0; i < B; ++i) {
     const gmi_image_desc& d = descs[i];
     ImageGeom& g = table[i];
-    memset(&g, 0, sizeof(g));
-    fill_geom(g, d.N, d.H, d.W, d.sigma, p->params.radius_sigmas, d.bin_px > 0 ? d.bin_px : p->params.bin_px,
-              p->mth, p->mtw);
+    batch_geom(g, p, d.N, d.H, d.W, d.sigma, d.bin_px, &npt, &nb, &nwt, &nch, &nmt, &npx);
     g.points = d.points;
     g.values = d.values;
     g.image = d.image;
     g.den = d.den;
     g.shift = d.shift;
     set_vec_ok(g);
-    g.pt_base = npt;
-    g.bin_base = nb;
-    g.wt_base = nwt;
-    g.ch_base = nch;
-    npt += d.N;
-    nb += (long long)g.nbx * g.nby;
-    nwt += (long long)g.wtx * g.wty;
-    nch += (d.N + kChunk - 1) / kChunk;
-    nmt += (long long)g.mtx * g.mty;
   }
-  if (npt > p->max_points || nb > p->cap_nb || nwt > p->cap_wt || nch > p->cap_ch || nmt > p->cap_mt)
+  if (npt > p->max_points || nb > p->cap_nb || nwt > p->cap_wt || nch > p->cap_ch || nmt > p->cap_mt ||
+      npx > p->max_pixels)
     return GMI_ERR_CAPACITY;
   tot[kTotImages] = B;
   tot[kTotPoints] = npt;
@@ -165,6 +213,7 @@ extern "C" gmi_status gmi_forward_batched(gmi_batch_plan* p, const gmi_image_des
   tot[kTotWarpTiles] = nwt;
   tot[kTotChunks] = nch;
   tot[kTotMicroTiles] = nmt;
+  tot[kTotPixels] = npx;
 
   KArgs a;
   memset(&a, 0, sizeof(a));
@@ -210,5 +259,84 @@ extern "C" gmi_status gmi_forward_batched(gmi_batch_plan* p, const gmi_image_des
   }
   if (cudaEventRecord(sl.done, s) != cudaSuccess) return GMI_ERR_CUDA;
   sl.used = true;
+  return (p->params.flags & GMI_FLAG_SYNC_CHECK) ? read_status(p->base, s) : GMI_OK;
+}
+
+extern "C" gmi_status gmi_backward_batched(gmi_batch_plan* p, const gmi_grad_desc* descs, int B, gmi_stream_t stream) {
+  if (!p || (B > 0 && !descs) || B < 0) return GMI_ERR_INVALID_ARG;
+  if (B > p->max_images) return GMI_ERR_CAPACITY;
+  cudaStream_t s = (cudaStream_t)stream;
+  for (int i = 0; i < B; ++i) {
+    const gmi_grad_desc& d = descs[i];
+    if (d.N < 0 || d.H < 1 || d.W < 1 || (long long)d.H * d.W > (1LL << 31)) return GMI_ERR_INVALID_ARG;
+    if (!d.image || !d.den || !d.shift || !d.grad_image) return GMI_ERR_INVALID_ARG;
+    if (!(isfinite(d.sigma) && d.sigma > 0.0f) || d.bin_px < 0 || d.bin_px > 1024) return GMI_ERR_INVALID_ARG;
+    if (d.N > 0 && (!d.points || !d.values)) return GMI_ERR_INVALID_ARG;
+    if (((uintptr_t)d.points & 7u) || ((uintptr_t)d.values & 3u)) return GMI_ERR_INVALID_ARG;
+  }
+  std::lock_guard<std::mutex> lk(p->mu);
+  if (p->bwd_used && cudaEventSynchronize(p->bwd_done) != cudaSuccess) return GMI_ERR_CUDA;
+  long long* tot = (long long*)p->bwd_host;
+  ImageGeom* table = (ImageGeom*)(p->bwd_host + kTotCount * sizeof(long long));
+  BwdImage* btab = (BwdImage*)(p->bwd_host + stage_size(p->max_images));
+  long long npt = 0, nb = 0, nwt = 0, nch = 0, nmt = 0, npx = 0;
+  for (int i = 0; i < B; ++i) {
+    const gmi_grad_desc& d = descs[i];
+    ImageGeom& g = table[i];
+    batch_geom(g, p, d.N, d.H, d.W, d.sigma, d.bin_px, &npt, &nb, &nwt, &nch, &nmt, &npx);
+    g.points = d.points;
+    g.values = d.values;
+    BwdImage& bi = btab[i];
+    bi.image = d.image;
+    bi.den = d.den;
+    bi.shift = d.shift;
+    bi.grad = d.grad_image;
+    bi.gpts = d.grad_points;
+    bi.gvals = d.grad_values;
+    bi.gsig = d.grad_sigma;
+    bi.inv_s2 = (float)(1.0 / ((double)d.sigma * d.sigma));
+    bi.inv_s3 = (float)(1.0 / ((double)d.sigma * d.sigma * d.sigma));
+  }
+  if (npt > p->max_points || nb > p->cap_nb || nwt > p->cap_wt || nch > p->cap_ch || nmt > p->cap_mt ||
+      npx > p->max_pixels)
+    return GMI_ERR_CAPACITY;
+  tot[kTotImages] = B;
+  tot[kTotPoints] = npt;
+  tot[kTotBins] = nb;
+  tot[kTotWarpTiles] = nwt;
+  tot[kTotChunks] = nch;
+  tot[kTotMicroTiles] = nmt;
+  tot[kTotPixels] = npx;
+  if (cudaMemcpyAsync(p->bwd_dev, p->bwd_host, bwd_stage_size(p->max_images), cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return GMI_ERR_CUDA;
+
+  KArgs a;
+  memset(&a, 0, sizeof(a));
+  a.w = bind_ws(p->base, p->L);
+  a.w.table = (const ImageGeom*)(p->bwd_dev + kTotCount * sizeof(long long));
+  a.w.pplane = p->pplane;
+  a.w.fbflag = p->fbflag;
+  a.w.fbq = p->fbq;
+  a.totals = (const long long*)p->bwd_dev;
+  a.n_images = p->max_images;
+  a.C = p->C;
+  a.n_total = p->max_points;   // grid sizes: capacities
+  a.nb_total = p->cap_nb;
+  a.wt_total = p->cap_wt;
+  a.ch_total = p->cap_ch;
+  a.mt_total = p->cap_mt;
+  a.px_total = p->max_pixels;
+  const bool trunc = p->params.mode == GMI_MODE_TRUNCATED;
+  gmi_status st = run_bin_and_plan(a, p->L, p->base, p->mth, p->mtw, trunc, s, false);
+  if (st != GMI_OK) return st;
+  BwdArgs b;
+  memset(&b, 0, sizeof(b));
+  b.table = (const BwdImage*)(p->bwd_dev + stage_size(p->max_images));
+  b.trunc = trunc ? 1 : 0;
+  const ProfileMark pm = profile_begin(GMI_STAGE_BACKWARD, s);
+  if (launch_backward(a, b, s) != cudaSuccess) return GMI_ERR_CUDA;
+  profile_end(pm, s);
+  if (cudaEventRecord(p->bwd_done, s) != cudaSuccess) return GMI_ERR_CUDA;
+  p->bwd_used = true;
   return (p->params.flags & GMI_FLAG_SYNC_CHECK) ? read_status(p->base, s) : GMI_OK;
 }

@@ -10,17 +10,9 @@
 //   scan_partial per-block sums of the bin counts
 //   scan_final   exclusive scan of the counts, in place, into bin offsets
 //   bin_scatter  bin-sorted copies of positions (float2) and colours (float4)
-#include "common.cuh"
+#include "bin_body.cuh"
 
 namespace gmi {
-
-__device__ __forceinline__ void point_bin(const ImageGeom& g, float x, float y, long long& bin,
-                                          bool& oob) {
-  int bx = bin_coord(x, g.inv_b, g.nbx);
-  int by = bin_coord(y, g.inv_b, g.nby);
-  bin = g.bin_base + (long long)by * g.nbx + bx;
-  oob = !(x >= 0.0f && x < (float)g.W && y >= 0.0f && y < (float)g.H);
-}
 
 __global__ void __launch_bounds__(256) bin_count_kernel(KArgs a_in) {
   const KArgs a = resolve(a_in);
@@ -121,29 +113,10 @@ __global__ void __launch_bounds__(256) scan_final_kernel(unsigned* __restrict__ 
   if (nb == 0 && blockIdx.x == 0 && tid == 0) off[0] = 0;
 }
 
+
 __global__ void __launch_bounds__(256) bin_scatter_kernel(KArgs a_in) {
   const KArgs a = resolve(a_in);
-  for (long long ch = blockIdx.x; ch < a.ch_total; ch += gridDim.x) {
-    const int img = find_image<0>(a, ch);
-    const ImageGeom& g = *geom_ptr(a, img);
-    const long long i = (ch - g.ch_base) * kChunk + threadIdx.x;
-    if (i < g.n) {
-      float2 p = reinterpret_cast<const float2*>(g.points)[i];
-      long long bin;
-      bool oob;
-      point_bin(g, p.x, p.y, bin, oob);
-      unsigned dst = a.w.off[bin] + a.w.rank[g.pt_base + i];
-      float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
-      const float* v = g.values + i * a.C;
-      c.x = v[0];
-      if (a.C > 1) c.y = v[1];
-      if (a.C > 2) c.z = v[2];
-      if (a.C > 3) c.w = v[3];
-      a.w.sxy[dst] = p;
-      a.w.sval[dst] = c;
-      a.w.perm[dst] = (unsigned)i;
-    }
-  }
+  bin_scatter_body(a, gridDim.x);
 }
 
 }  // namespace gmi
@@ -159,6 +132,8 @@ __global__ void __launch_bounds__(256) batch_clear_kernel(KArgs a_in) {
   for (long long i = t0; i <= a.nb_total; i += stride) a.w.off[i] = 0u;
   for (long long i = t0; i < a.nb_total; i += stride) a.w.oob[i] = 0;
   for (long long i = t0; i < a.wt_total; i += stride) a.w.tile_done[i] = 0u;
+  if (a.w.fbflag)
+    for (long long i = t0; i < a.mt_total; i += stride) a.w.fbflag[i] = 0u;
 }
 
 }  // namespace gmi

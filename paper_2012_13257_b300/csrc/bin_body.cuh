@@ -1,0 +1,42 @@
+// Bin key of a point and the scatter into bin-sorted arrays, shared by the
+// binning kernels and the fused scatter + plan launch.
+#pragma once
+
+#include "common.cuh"
+
+namespace gmi {
+
+static __device__ __forceinline__ void point_bin(const ImageGeom& g, float x, float y, long long& bin,
+                                          bool& oob) {
+  int bx = bin_coord(x, g.inv_b, g.nbx);
+  int by = bin_coord(y, g.inv_b, g.nby);
+  bin = g.bin_base + (long long)by * g.nbx + bx;
+  oob = !(x >= 0.0f && x < (float)g.W && y >= 0.0f && y < (float)g.H);
+}
+
+// Scatter body; `nblocks` blocks starting at block 0 stride over the chunks.
+static __device__ __forceinline__ void bin_scatter_body(const KArgs& a, int nblocks) {
+  for (long long ch = blockIdx.x; ch < a.ch_total; ch += nblocks) {
+    const int img = find_image<0>(a, ch);
+    const ImageGeom& g = *geom_ptr(a, img);
+    const long long i = (ch - g.ch_base) * kChunk + threadIdx.x;
+    if (i < g.n) {
+      float2 p = reinterpret_cast<const float2*>(g.points)[i];
+      long long bin;
+      bool oob;
+      point_bin(g, p.x, p.y, bin, oob);
+      unsigned dst = a.w.off[bin] + a.w.rank[g.pt_base + i];
+      float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
+      const float* v = g.values + i * a.C;
+      c.x = v[0];
+      if (a.C > 1) c.y = v[1];
+      if (a.C > 2) c.z = v[2];
+      if (a.C > 3) c.w = v[3];
+      a.w.sxy[dst] = p;
+      a.w.sval[dst] = c;
+      a.w.perm[dst] = (unsigned)i;
+    }
+  }
+}
+
+}  // namespace gmi

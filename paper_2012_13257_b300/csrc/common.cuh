@@ -62,6 +62,8 @@ struct ImageGeom {
   float u_near_max;      // largest nearest-distance bound the near kernel accepts
   int vec_ok;            // rows of image/den/shift may use 16-byte stores
   int pad_;
+  long long px_base;     // first pixel in the concatenated pixel space
+  long long mt_base;     // first micro-tile in the concatenated micro-tile space
 };
 
 // Device pointers into a workspace.
@@ -83,7 +85,7 @@ struct DevWork {
   // backward pass only
   float4* pplane;        // [pixels * (C == 4 ? 2 : 1)]: g_c / den and s' per core pixel
   unsigned* fbflag;      // [mt_total]: micro-tile holds a non-core pixel
-  unsigned* fbq;         // [mt_total]: queue of such micro-tiles
+  uint2* fbq;            // [mt_total]: queue of such micro-tiles (image, micro-tile)
   float* sig_part;       // [kSigParts]: per-block sigma-gradient partials
   const ImageGeom* table;// device descriptor table (batched) or null (single image)
 };
@@ -98,6 +100,7 @@ struct KArgs {
   long long wt_total;    // warp tiles over all images
   long long ch_total;    // point chunks over all images
   long long mt_total;    // micro-tiles over all images
+  long long px_total;    // output pixels over all images
   unsigned cap_items;    // capacity of w.items
   unsigned cap_slots;    // capacity of w.slots, in slots
   int mth, mtw;          // micro-tile of the near kernel
@@ -106,7 +109,7 @@ struct KArgs {
 
 // Layout of the device totals of a batch (uploaded with its descriptor table),
 // so that one captured launch sequence serves any batch within capacity.
-enum : int { kTotImages = 0, kTotPoints, kTotBins, kTotWarpTiles, kTotChunks, kTotMicroTiles, kTotCount = 8 };
+enum : int { kTotImages = 0, kTotPoints, kTotBins, kTotWarpTiles, kTotChunks, kTotMicroTiles, kTotPixels, kTotCount = 8 };
 
 // Kernel arguments with the totals of a batched call read from the device.
 __device__ __forceinline__ KArgs resolve(const KArgs& in) {
@@ -118,6 +121,7 @@ __device__ __forceinline__ KArgs resolve(const KArgs& in) {
     a.wt_total = in.totals[kTotWarpTiles];
     a.ch_total = in.totals[kTotChunks];
     a.mt_total = in.totals[kTotMicroTiles];
+    a.px_total = in.totals[kTotPixels];
   }
   return a;
 }
@@ -132,14 +136,16 @@ __device__ __forceinline__ const ImageGeom* geom_ptr(const KArgs& a, int img) {
   return a.w.table ? a.w.table + img : &a.g0;
 }
 
-// Largest image index whose base (selected by Field) is <= idx.
+// Largest image index whose base (Field 0: chunks, 1: warp tiles, 2: points,
+// 3: pixels) is <= idx.
 template <int Field>
 __device__ __forceinline__ int find_image(const KArgs& a, long long idx) {
   if (a.w.table == nullptr) return 0;
   int lo = 0, hi = a.n_images - 1;
   while (lo < hi) {
     int mid = (lo + hi + 1) >> 1;
-    long long base = Field == 0 ? a.w.table[mid].ch_base : a.w.table[mid].wt_base;
+    const ImageGeom& t = a.w.table[mid];
+    const long long base = Field == 0 ? t.ch_base : (Field == 1 ? t.wt_base : (Field == 2 ? t.pt_base : t.px_base));
     if (base <= idx) lo = mid; else hi = mid - 1;
   }
   return lo;

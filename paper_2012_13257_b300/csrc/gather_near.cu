@@ -31,7 +31,7 @@
 //
 // In truncated mode (the literal "radius k sigma" reading) R = k sigma, each
 // pixel keeps only points with d^2 <= k^2 sigma^2, and nothing is queued.
-#include "common.cuh"
+#include "bin_body.cuh"
 
 namespace gmi {
 
@@ -190,11 +190,9 @@ __device__ __forceinline__ void row_segment(const KArgs& a, const ImageGeom& g, 
 // work items, so that no single thread walks thousands of candidates while
 // the rest of the GPU idles.
 template <int MTH, int MTW>
-__global__ void __launch_bounds__(128) near_plan_kernel(KArgs a_in, int trunc) {
-  const KArgs a = resolve(a_in);
+__device__ void near_plan_body(const KArgs& a, int trunc, long long wt) {
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
-  const long long wt = (long long)blockIdx.x * 4 + (threadIdx.x >> 5);
   if (wt >= a.wt_total) return;
   const int img = find_image<1>(a, wt);
   const ImageGeom g = a.w.table ? a.w.table[img] : a.g0;
@@ -235,7 +233,10 @@ __global__ void __launch_bounds__(128) near_plan_kernel(KArgs a_in, int trunc) {
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) cnt = max(cnt, __shfl_xor_sync(full, cnt, o));
-  unsigned S = min((cnt + kSplitTarget - 1) / kSplitTarget, (unsigned)kSplitMax);
+  // small problems: finer items, so that there are about as many items as
+  // resident warps (latency hiding needs several warps per scheduler)
+  const unsigned target = (unsigned)max(48LL, min((long long)kSplitTarget, (long long)kSplitTarget * a.wt_total / 2368));
+  unsigned S = min((cnt + target - 1) / target, (unsigned)kSplitMax);
   if (S < 1) S = 1;
   unsigned slot = 0xffffffffu;
   if (S > 1) {
@@ -254,6 +255,20 @@ __global__ void __launch_bounds__(128) near_plan_kernel(KArgs a_in, int trunc) {
   if (lane == 0) {
     const unsigned base = atomicAdd(&a.w.status[kItemCount], S);
     for (unsigned k = 0; k < S && base + k < a.cap_items; ++k) a.w.items[base + k] = make_uint4((unsigned)wt, k, S, slot);
+  }
+}
+
+// Scatter (blocks [0, n_scatter)) and plan (the remaining blocks, one warp per
+// warp tile) in one launch: the plan needs only the bin offsets and flags,
+// which the scan has already produced, so the two run side by side.
+template <int MTH, int MTW>
+__global__ void __launch_bounds__(256) scatter_plan_kernel(KArgs a_in, int trunc, int n_scatter) {
+  const KArgs a = resolve(a_in);
+  if ((int)blockIdx.x < n_scatter) {
+    bin_scatter_body(a, n_scatter);
+  } else {
+    const long long wt = (long long)(blockIdx.x - n_scatter) * 8 + (threadIdx.x >> 5);
+    near_plan_body<MTH, MTW>(a, trunc, wt);
   }
 }
 
@@ -490,11 +505,13 @@ static cudaError_t launch_near_mt(const KArgs& a, bool trunc, int grid, cudaStre
   }
 }
 
-cudaError_t launch_near_plan(const KArgs& a, bool trunc, cudaStream_t s) {
-  const unsigned blocks = (unsigned)((a.wt_total + 3) / 4);
-  if (a.mth == 4 && a.mtw == 8) near_plan_kernel<4, 8><<<blocks, 128, 0, s>>>(a, trunc ? 1 : 0);
-  else if (a.mth == 2 && a.mtw == 4) near_plan_kernel<2, 4><<<blocks, 128, 0, s>>>(a, trunc ? 1 : 0);
-  else near_plan_kernel<4, 4><<<blocks, 128, 0, s>>>(a, trunc ? 1 : 0);
+// n_scatter scatter blocks (0: scatter not needed) followed by the plan's blocks.
+cudaError_t launch_scatter_plan(const KArgs& a, bool trunc, int n_scatter, cudaStream_t s) {
+  const unsigned blocks = (unsigned)(n_scatter + (a.wt_total + 7) / 8);
+  const int t = trunc ? 1 : 0;
+  if (a.mth == 4 && a.mtw == 8) scatter_plan_kernel<4, 8><<<blocks, 256, 0, s>>>(a, t, n_scatter);
+  else if (a.mth == 2 && a.mtw == 4) scatter_plan_kernel<2, 4><<<blocks, 256, 0, s>>>(a, t, n_scatter);
+  else scatter_plan_kernel<4, 4><<<blocks, 256, 0, s>>>(a, t, n_scatter);
   return cudaGetLastError();
 }
 

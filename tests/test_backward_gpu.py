@@ -132,3 +132,32 @@ def test_fwd_bwd_512_windows(cuda_device):
     _, gv, _ = gpu_grads(im, gfull[0], cuda_device)
     np.testing.assert_allclose(gv.astype(np.float64).sum(0), gfull[0].astype(np.float64).reshape(-1, 3).sum(0),
                                rtol=1e-4, atol=1e-2)
+
+
+def test_batched_backward_matches_oracle(cuda_device):
+    """Uneven images through one batched forward and one batched backward:
+    every image's gradients against the oracle."""
+    import torch
+    G = gmi()
+    rng = np.random.default_rng(77)
+    imgs, ups = [], []
+    for b in range(7):
+        H, W = int(rng.integers(12, 40)), int(rng.integers(12, 40))
+        im = wl.tiny_random(700 + b, int(rng.integers(20, 300)), H, W, C=3, sigma=float(rng.uniform(0.6, 1.8)),
+                            clustered=bool(b % 2))
+        imgs.append(im)
+        ups.append(rng.standard_normal((H, W, 3)).astype(np.float32))
+    plan = G.BatchPlan(16, 5000, 20000, 3)
+    P = [to_dev(im.points, cuda_device).requires_grad_(True) for im in imgs]
+    V = [to_dev(im.values, cuda_device).requires_grad_(True) for im in imgs]
+    S = [torch.tensor(im.sigma, dtype=torch.float32, device=cuda_device, requires_grad=True) for im in imgs]
+    outs = G.gmi_interpolate_batch(plan, P, V, S, [(im.H, im.W) for im in imgs])
+    loss = sum((o * to_dev(u, cuda_device)).sum() for o, u in zip(outs, ups))
+    loss.backward()
+    torch.cuda.synchronize()
+    for b, im in enumerate(imgs):
+        ref = oracle.backward(im.points, im.values, im.H, im.W, im.sigma, ups[b])
+        assert_grads((P[b].grad.cpu().numpy(), V[b].grad.cpu().numpy(), float(S[b].grad)), ref)
+        fwd = oracle.forward(im.points, im.values, im.H, im.W, im.sigma)["image"]
+        assert np.abs(outs[b].detach().cpu().numpy() - fwd).max() <= 1e-4
+    plan.close()
