@@ -294,7 +294,10 @@ def bench_batched(dev, steps, warmup, flush, stream):
 
 def bench_fwd_bwd(dev, steps, warmup, flush, stream):
     """16 images 512x512x3 from 65,536 clustered points each, sigma = 1:
-    forward + backward (values, positions, sigma) through the autograd op."""
+    forward + backward (values, positions, sigma) through the batched
+    torch.autograd.Function (one graph-replayed forward launch and one
+    batched backward for all 16 images); the same through the per-image
+    autograd op for comparison."""
     import torch
     import paper_2012_13257_b300 as gmi
     import workloads as wl
@@ -303,20 +306,32 @@ def bench_fwd_bwd(dev, steps, warmup, flush, stream):
     V = [torch.as_tensor(im.values, device=dev).requires_grad_(True) for im in imgs]
     S = [torch.tensor(im.sigma, dtype=torch.float32, device=dev, requires_grad=True) for im in imgs]
     G = torch.as_tensor(grad, device=dev)
+    plan = gmi.BatchPlan(len(imgs), sum(im.N for im in imgs), sum(im.H * im.W for im in imgs), 3)
+    sizes = [(im.H, im.W) for im in imgs]
 
     def step():
+        outs = gmi.gmi_interpolate_batch(plan, P, V, S, sizes)
+        torch.autograd.backward(outs, [G[b] for b in range(len(imgs))])
+
+    def step_single():
         for b, im in enumerate(imgs):
-            img = gmi.gmi_interpolate(P[b], V[b], S[b], im.H, im.W)
-            img.backward(G[b])
+            gmi.gmi_interpolate(P[b], V[b], S[b], im.H, im.W).backward(G[b])
     for _ in range(max(3, warmup)):
         step()
     torch.cuda.synchronize()
     t = timed_steps(step, steps, flush, stream)
+    for _ in range(2):
+        step_single()
+    torch.cuda.synchronize()
+    t1 = timed_steps(step_single, max(3, steps // 4), flush, stream)
+    plan.close()
     px = sum(im.H * im.W for im in imgs)
     return {"value": px / (sum(t) / steps * 1e-3) / 1e6, "unit": "Mpix/s", "ms_per_step": sum(t) / steps,
-            "images": len(imgs), "pixels": px,
+            "per_image_autograd_value": px / (sum(t1) / len(t1) * 1e-3) / 1e6,
+            "per_image_ms_per_step": sum(t1) / len(t1), "images": len(imgs), "pixels": px,
             "workload": "16 x 512x512x3 f32 from 65,536 clustered points, sigma=1, upstream N(0,1); "
-                        "forward + backward w.r.t. values, positions and sigma via torch.autograd.Function"}
+                        "forward + backward w.r.t. values, positions and sigma via the batched "
+                        "torch.autograd.Function (per-image autograd op for comparison)"}
 
 
 def bench_serving(dev, n_requests=10000, rate=2000.0, n_templates=128):
