@@ -18,7 +18,7 @@ import ctypes
 from . import _lib
 from ._lib import GmiError, MODE_EXACT, MODE_TRUNCATED
 
-__all__ = ["release_workspaces", "interpolate", "interpolate_backward", "gmi_interpolate", "BatchPlan", "gmi_interpolate_batch", "Server", "workspace_size", "GmiError", "MODE_EXACT", "MODE_TRUNCATED", "version", "lib"]
+__all__ = ["release_workspaces", "interpolate", "interpolate_backward", "gmi_interpolate", "BatchPlan", "gmi_interpolate_batch", "gmi_interpolate_stacked", "Server", "workspace_size", "GmiError", "MODE_EXACT", "MODE_TRUNCATED", "version", "lib"]
 
 
 def lib():
@@ -254,6 +254,31 @@ def gmi_interpolate(points, values, sigma, H: int, W: int, *, radius_sigmas: flo
                               int(bin_px), int(variant))
 
 
+def _flat_views(shapes, dev, dtype=None):
+    """One allocation for several tensors: views of the given shapes, each
+    starting on a 16-byte boundary (so the kernels may use vector stores)."""
+    import math
+    import torch
+    sizes = [int(math.prod(sh)) for sh in shapes]
+    offs, o = [], 0
+    for n in sizes:
+        offs.append(o)
+        o += (n + 3) // 4 * 4
+    buf = torch.empty(max(o, 1), dtype=dtype or torch.float32, device=dev)
+    return [buf[a:a + n].view(sh) for a, n, sh in zip(offs, sizes, shapes)]
+
+
+def _np_table(ctype, n):
+    """numpy structured array laid out exactly like the ctypes Structure."""
+    import numpy as np
+    fields = ctype._fields_
+    names = [f[0] for f in fields]
+    fmt = {ctypes.c_void_p: np.uint64, ctypes.c_int64: np.int64, ctypes.c_int: np.int32, ctypes.c_float: np.float32}
+    dt = np.dtype({"names": names, "formats": [fmt[f[1]] for f in fields],
+                   "offsets": [getattr(ctype, nm).offset for nm in names], "itemsize": ctypes.sizeof(ctype)})
+    return np.zeros(max(n, 1), dtype=dt)
+
+
 class BatchPlan:
     """A reusable batched-forward plan (device workspace + pinned staging
     allocated once).  ``forward(images)`` interpolates a list of images, each a
@@ -276,33 +301,48 @@ class BatchPlan:
         return int(_lib.load().gmi_batch_plan_bytes(self._h))
 
     def forward(self, images, use_graph: bool = True):
+        import numpy as np
         import torch
         n = len(images)
-        descs = (_lib.ImageDesc * max(1, n))()
-        outs = []
+        tab = _np_table(_lib.ImageDesc, n)
+        dev = images[0]["points"].device if n else None
+        need_out = [i for i, im in enumerate(images) if im.get("out") is None]
+        fresh = _flat_views([(int(images[i]["H"]), int(images[i]["W"]), self.C) for i in need_out], dev) \
+            if need_out else []
+        outs = [im.get("out") for im in images]
+        for i, v in zip(need_out, fresh):
+            outs[i] = v
         keep = []
-        dev = None
         for i, im in enumerate(images):
             P, V = _check_inputs(im["points"], im["values"])
-            dev = P.device
-            H, W = int(im["H"]), int(im["W"])
-            out = im.get("out")
-            if out is None:
-                out = torch.empty((H, W, self.C), dtype=torch.float32, device=dev)
             keep += [P, V]
-            d = descs[i]
-            d.points, d.values, d.image = P.data_ptr(), V.data_ptr(), out.data_ptr()
-            d.den = im["den"].data_ptr() if im.get("den") is not None else None
-            d.shift = im["shift"].data_ptr() if im.get("shift") is not None else None
-            d.N, d.H, d.W = int(P.shape[0]), H, W
-            d.sigma = float(im["sigma"])
-            d.bin_px = int(im.get("bin_px", 0))
-            outs.append(out)
+            tab["points"][i], tab["values"][i], tab["image"][i] = P.data_ptr(), V.data_ptr(), outs[i].data_ptr()
+            if im.get("den") is not None:
+                tab["den"][i] = im["den"].data_ptr()
+            if im.get("shift") is not None:
+                tab["shift"][i] = im["shift"].data_ptr()
+            tab["N"][i] = P.shape[0]
+            tab["H"][i], tab["W"][i] = int(im["H"]), int(im["W"])
+            tab["sigma"][i] = float(im["sigma"])
+            tab["bin_px"][i] = int(im.get("bin_px", 0))
         stream = torch.cuda.current_stream(dev).cuda_stream if dev is not None else None
-        _lib.check(_lib.load().gmi_forward_batched(self._h, descs, n, 1 if use_graph else 0, stream),
-                   "gmi_forward_batched")
-        self._keep = keep   # inputs stay referenced until the next call
+        _lib.check(_lib.load().gmi_forward_batched(
+            self._h, ctypes.cast(tab.ctypes.data, ctypes.POINTER(_lib.ImageDesc)), n, 1 if use_graph else 0,
+            stream), "gmi_forward_batched")
+        self._keep = (keep, tab)   # inputs stay referenced until the next call
         return outs
+
+    def forward_table(self, tab, n: int, stream, use_graph: bool = True):
+        """Launch from a prebuilt numpy ImageDesc table (see _np_table)."""
+        _lib.check(_lib.load().gmi_forward_batched(
+            self._h, ctypes.cast(tab.ctypes.data, ctypes.POINTER(_lib.ImageDesc)), int(n), 1 if use_graph else 0,
+            stream), "gmi_forward_batched")
+
+    def backward_table(self, tab, n: int, stream):
+        """Launch the batched backward from a prebuilt numpy GradDesc table."""
+        _lib.check(_lib.load().gmi_backward_batched(
+            self._h, ctypes.cast(tab.ctypes.data, ctypes.POINTER(_lib.GradDesc)), int(n), stream),
+            "gmi_backward_batched")
 
     def backward(self, images):
         """Batched backward.  Each entry: ``points``, ``values``, ``sigma``,
@@ -312,32 +352,42 @@ class BatchPlan:
         grad_sigma) tuples (None where not needed)."""
         import torch
         n = len(images)
-        descs = (_lib.GradDesc * max(1, n))()
-        res, keep, dev = [], [], None
+        tab = _np_table(_lib.GradDesc, n)
+        dev = images[0]["points"].device if n else None
+        needs = [im.get("need", (True, True, True)) for im in images]
+        Ns = [int(im["points"].shape[0]) for im in images]
+        Cs = [int(im["values"].shape[1]) for im in images]
+        gps = iter(_flat_views([(N, 2) for N, nd in zip(Ns, needs) if nd[0]], dev))
+        gvs = iter(_flat_views([(N, C) for N, C, nd in zip(Ns, Cs, needs) if nd[1]], dev))
+        gss = iter(_flat_views([(1,) for nd in needs if nd[2]], dev))
+        res, keep = [], []
         for i, im in enumerate(images):
             P, V = _check_inputs(im["points"], im["values"])
-            dev = P.device
-            N, C = int(P.shape[0]), int(V.shape[1])
-            need = im.get("need", (True, True, True))
-            gp = torch.empty((N, 2), dtype=torch.float32, device=dev) if need[0] else None
-            gv = torch.empty((N, C), dtype=torch.float32, device=dev) if need[1] else None
-            gs = torch.empty((1,), dtype=torch.float32, device=dev) if need[2] else None
+            nd = needs[i]
+            gp = next(gps) if nd[0] else None
+            gv = next(gvs) if nd[1] else None
+            gs = next(gss) if nd[2] else None
             img, den, shift = im["image"].contiguous(), im["den"].contiguous(), im["shift"].contiguous()
             g = im["grad"].contiguous().float()
             keep += [P, V, img, den, shift, g]
-            d = descs[i]
-            d.points, d.values = P.data_ptr(), V.data_ptr()
-            d.image, d.den, d.shift, d.grad_image = img.data_ptr(), den.data_ptr(), shift.data_ptr(), g.data_ptr()
-            d.grad_points = gp.data_ptr() if gp is not None else None
-            d.grad_values = gv.data_ptr() if gv is not None else None
-            d.grad_sigma = gs.data_ptr() if gs is not None else None
-            d.N, d.H, d.W = N, int(im["H"]), int(im["W"])
-            d.sigma = float(im["sigma"])
-            d.bin_px = int(im.get("bin_px", 0))
+            tab["points"][i], tab["values"][i] = P.data_ptr(), V.data_ptr()
+            tab["image"][i], tab["den"][i] = img.data_ptr(), den.data_ptr()
+            tab["shift"][i], tab["grad_image"][i] = shift.data_ptr(), g.data_ptr()
+            if gp is not None:
+                tab["grad_points"][i] = gp.data_ptr()
+            if gv is not None:
+                tab["grad_values"][i] = gv.data_ptr()
+            if gs is not None:
+                tab["grad_sigma"][i] = gs.data_ptr()
+            tab["N"][i] = Ns[i]
+            tab["H"][i], tab["W"][i] = int(im["H"]), int(im["W"])
+            tab["sigma"][i] = float(im["sigma"])
+            tab["bin_px"][i] = int(im.get("bin_px", 0))
             res.append((gp, gv, gs))
         stream = torch.cuda.current_stream(dev).cuda_stream if dev is not None else None
-        _lib.check(_lib.load().gmi_backward_batched(self._h, descs, n, stream), "gmi_backward_batched")
-        self._keep_bwd = keep
+        _lib.check(_lib.load().gmi_backward_batched(
+            self._h, ctypes.cast(tab.ctypes.data, ctypes.POINTER(_lib.GradDesc)), n, stream), "gmi_backward_batched")
+        self._keep_bwd = (keep, tab)
         return res
 
     def close(self):
@@ -447,14 +497,14 @@ def _batch_function():
         @staticmethod
         def forward(ctx, plan, sizes, *flat):
             B = len(sizes)
+            dev = flat[0].device
+            aux = _flat_views([(H, W) for H, W in sizes] * 2, dev)
             ims = []
             for b in range(B):
                 P, V, S = flat[3 * b], flat[3 * b + 1], flat[3 * b + 2]
                 H, W = sizes[b]
-                C = V.shape[1]
                 ims.append({"points": P, "values": V, "sigma": _sigma_value(S), "H": H, "W": W,
-                            "den": torch.empty((H, W), dtype=torch.float32, device=P.device),
-                            "shift": torch.empty((H, W), dtype=torch.float32, device=P.device)})
+                            "den": aux[b], "shift": aux[B + b]})
             outs = plan.forward(ims, use_graph=True)
             for im, o in zip(ims, outs):
                 im["image"] = o
@@ -497,3 +547,92 @@ def gmi_interpolate_batch(plan, points, values, sigmas, sizes):
     for P, V, S in zip(points, values, sigmas):
         flat += [P, V, S]
     return list(_GMIBatchFunction.apply(plan, [tuple(map(int, hw)) for hw in sizes], *flat))
+
+
+def _stacked_function():
+    import numpy as np
+    import torch
+
+    def ptrs(t, B):
+        return np.uint64(t.data_ptr()) + np.arange(B, dtype=np.uint64) * np.uint64(t[0].numel() * t.element_size())
+
+    class GMIStackedFunction(torch.autograd.Function):
+        """B equal-shaped images ([B,N,2] points, [B,N,C] values, [B] sigmas)
+        through one batched forward and one batched backward; descriptor
+        tables are built with vector operations, so the host work does not
+        grow with B."""
+
+        @staticmethod
+        def forward(ctx, plan, H, W, points, values, sigmas):
+            B, N = int(points.shape[0]), int(points.shape[1])
+            C = int(values.shape[2])
+            dev = points.device
+            points, values = points.contiguous(), values.contiguous()
+            sig = _sigma_list(sigmas, B)
+            out, den, shift = _flat_views([(B, H, W, C), (B, H, W), (B, H, W)], dev)
+            tab = _np_table(_lib.ImageDesc, B)
+            tab["points"], tab["values"], tab["image"] = ptrs(points, B), ptrs(values, B), ptrs(out, B)
+            tab["den"], tab["shift"] = ptrs(den, B), ptrs(shift, B)
+            tab["N"], tab["H"], tab["W"], tab["sigma"] = N, H, W, sig
+            stream = torch.cuda.current_stream(dev).cuda_stream
+            plan.forward_table(tab, B, stream)
+            ctx.set_materialize_grads(False)
+            ctx.plan, ctx.keep = plan, (tab,)
+            ctx.save_for_backward(points, values)
+            ctx.aux = (out, den, shift, sig, H, W, isinstance(sigmas, torch.Tensor))
+            return out
+
+        @staticmethod
+        def backward(ctx, g):
+            if g is None:
+                return (None,) * 6
+            points, values = ctx.saved_tensors
+            out, den, shift, sig, H, W, sig_t = ctx.aux
+            B, N, C = int(points.shape[0]), int(points.shape[1]), int(values.shape[2])
+            dev = points.device
+            g = g.contiguous().float()
+            need = ctx.needs_input_grad
+            gp, gv, gs = _flat_views([(B, N, 2), (B, N, C), (B,)], dev)
+            tab = _np_table(_lib.GradDesc, B)
+            tab["points"], tab["values"] = ptrs(points, B), ptrs(values, B)
+            tab["image"], tab["den"], tab["shift"], tab["grad_image"] = ptrs(out, B), ptrs(den, B), ptrs(shift, B), ptrs(g, B)
+            if need[3]:
+                tab["grad_points"] = ptrs(gp, B)
+            if need[4]:
+                tab["grad_values"] = ptrs(gv, B)
+            if need[5] and sig_t:
+                tab["grad_sigma"] = np.uint64(gs.data_ptr()) + np.arange(B, dtype=np.uint64) * np.uint64(4)
+            tab["N"], tab["H"], tab["W"], tab["sigma"] = N, H, W, sig
+            ctx.plan.backward_table(tab, B, torch.cuda.current_stream(dev).cuda_stream)
+            ctx.keep = (tab, g)
+            return (None, None, None, gp if need[3] else None, gv if need[4] else None,
+                    gs if (need[5] and sig_t) else None)
+
+    return GMIStackedFunction
+
+
+def _sigma_list(sigmas, B):
+    import numpy as np
+    import torch
+    if isinstance(sigmas, torch.Tensor):
+        if sigmas.device.type != "cpu":
+            key = (sigmas.data_ptr(), sigmas._version, B)
+            v = _sigma_cache.get(key)
+            if v is None:
+                v = _sigma_cache[key] = sigmas.detach().float().cpu().numpy().reshape(B)
+            return v
+        return sigmas.detach().float().numpy().reshape(B)
+    return np.broadcast_to(np.asarray(sigmas, dtype=np.float32), (B,))
+
+
+_GMIStackedFunction = None
+
+
+def gmi_interpolate_stacked(plan, points, values, sigmas, H: int, W: int):
+    """Differentiable batched interpolation of B equal-shaped images:
+    points [B,N,2], values [B,N,C], sigmas [B] (tensor: differentiable) ->
+    images [B,H,W,C], one batched forward and one batched backward."""
+    global _GMIStackedFunction
+    if _GMIStackedFunction is None:
+        _GMIStackedFunction = _stacked_function()
+    return _GMIStackedFunction.apply(plan, int(H), int(W), points, values, sigmas)
