@@ -38,9 +38,9 @@ namespace gmi {
 constexpr int kRingMax = 16;   // most bin rings searched for the nearest-distance bound
 
 // Upper bound on max_q m_q over the micro-tile's valid pixels from bin
-// occupancy, searched ring by ring around the micro-tile's bins (ring 1 is the
-// full 3x3-bin neighbourhood, later rings only their perimeter) until every
-// pixel has a usable bin; +inf when that takes more rings than the near kernel
+// occupancy, searched ring by ring around the micro-tile's bins (ring 0 its
+// own bins, ring 1 the full neighbourhood one bin wider, later rings only
+// their perimeter) until every pixel has a usable bin; +inf when that takes more rings than the near kernel
 // can use (the micro-tile then belongs to the far-field kernel).
 template <int MTH, int MTW>
 __device__ float near_bound(const KArgs& a, const ImageGeom& g, int x0, int y0, int nx, int ny) {
@@ -69,12 +69,7 @@ __device__ float near_bound(const KArgs& a, const ImageGeom& g, int x0, int y0, 
       const float d0 = q - (float)by * bf, d1 = q - (float)(by + 1) * bf;
       cy[r] = fmaxf(d0 * d0, d1 * d1);
     }
-    unsigned prev = __ldg(&a.w.off[rowb + xa]);
-    for (int bx = xa; bx <= xb; ++bx) {
-      const unsigned nxt = __ldg(&a.w.off[rowb + bx + 1]);
-      const bool usable = nxt > prev && __ldg(&a.w.oob[rowb + bx]) == 0;
-      prev = nxt;
-      if (!usable) continue;
+    auto fold = [&](int bx) {
 #pragma unroll
       for (int j = 0; j < MTW; ++j) {
         const float q = xq0 + (float)j;
@@ -83,9 +78,26 @@ __device__ float near_bound(const KArgs& a, const ImageGeom& g, int x0, int y0, 
 #pragma unroll
         for (int r = 0; r < MTH; ++r) best[r][j] = fminf(best[r][j], cx + cy[r]);
       }
+    };
+    unsigned prev = __ldg(&a.w.off[rowb + xa]);
+    for (int bx = xa; bx <= xb; ++bx) {
+      const unsigned nxt = __ldg(&a.w.off[rowb + bx + 1]);
+      const bool usable = nxt > prev && __ldg(&a.w.oob[rowb + bx]) == 0;
+      prev = nxt;
+      if (usable) fold(bx);
     }
   };
 
+  // ring 0: the micro-tile's own bins; in dense regions they bound every pixel
+  for (int by = by0; by <= by1; ++by) scan_row(by, bx0, bx1);
+  {
+    float u = 0.0f;
+#pragma unroll
+    for (int r = 0; r < MTH; ++r)
+#pragma unroll
+      for (int j = 0; j < MTW; ++j) u = fmaxf(u, best[r][j]);
+    if (u < INFINITY) return u;
+  }
   for (int ring = 1; ring <= ring_max; ++ring) {
     if (ring == 4) {
       // before walking more rings: if no point at all lies within the near-range
@@ -338,11 +350,14 @@ __global__ void __launch_bounds__(128, NearOcc<MTH, MTW>::value) near_kernel(KAr
       unsigned i = 0, end = 0, cum = 0;
       float2 pn = make_float2(0.f, 0.f);
       float4 cn = make_float4(0.f, 0.f, 0.f, 0.f);
+      // bounds of the next bin row, loaded one row ahead
+      unsigned ns = 0, ne = 0;
+      row_segment(a, g, w, w.by_lo, ns, ne);
       for (;;) {
         while (i >= end) {
           if (++by > w.by_hi || cum >= hi) goto done;
-          unsigned s0, e0;
-          row_segment(a, g, w, by, s0, e0);
+          const unsigned s0 = ns, e0 = ne;
+          if (by < w.by_hi) row_segment(a, g, w, by + 1, ns, ne);
           const unsigned len = e0 - s0, rs = cum;
           cum += len;
           i = s0 + (lo > rs ? min(lo - rs, len) : 0u);
