@@ -2,13 +2,15 @@
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gmi|reference]
 
-Headline workload (one "step" = one plain forward pass, binning included, of
-one synthetic image): a 512^2 source grid jittered by U[-0.5, 0.5] px,
-upsampled x2 to 1024 x 1024 x 3 float32 with sigma = 1 px, exact mode, k = 6.
-``value`` is interpolated output Mpix/s (H*W per step, all ranks), timed with
-CUDA events per step on the launching stream with L2 flushed (256 MB write)
-between steps; ``e2e`` repeats the measurement through the public call with the
-host<->device copies of inputs and image inside the timed region.
+Headline workload (one "step" = one forward pass, binning included, of one
+synthetic image): a 512^2 source grid jittered by U[-0.5, 0.5] px, upsampled
+x2 to 1024 x 1024 x 3 float32 with sigma = 1 px, exact mode, k = 6.  ``value``
+is interpolated output Mpix/s (H*W per step, all ranks) through
+``gmi.interpolate(..., graph=True)`` (the six kernels replayed as one CUDA
+graph), timed with CUDA events per step on the launching stream with L2
+flushed (256 MB write) between steps; ``plain_launch`` is the same without
+graph replay; ``e2e`` repeats the measurement through the public call with
+the host<->device copies of inputs and image inside the timed region.
 
 Further objects on the same line: the dominant kernel's roofline, the FP64
 oracle's CPU throughput, SM clocks sampled during the timed region and, as
@@ -45,7 +47,7 @@ L2_FLUSH_BYTES = 256 << 20
 SFU_PER_SM_CLK = 16      # ex2 results per SM per clock (cc 10.x throughput table)
 FP32_PER_SM_CLK = 128    # FP32 lanes per SM per clock
 SM_MAX_MHZ = 2032.0      # B300 maximum SM clock
-LAUNCHES_PER_FORWARD = 7 # count, scan x2, scatter, plan, near, far
+LAUNCHES_PER_FORWARD = 6  # count, scan x2, scatter+plan, near, far
 
 
 def parse():
@@ -489,17 +491,20 @@ def main():
     stream = torch.cuda.current_stream(dev)
 
     def step():
+        # the public call with graph replay: one host launch per forward
+        gmi.interpolate(P, V, im.sigma, im.H, im.W, out=out, graph=True)
+
+    def step_plain():
         gmi.interpolate(P, V, im.sigma, im.H, im.W, out=out)
 
     for _ in range(max(3, args.warmup)):
         step()
+        step_plain()
     torch.cuda.synchronize()
 
     # ---- headline: device-resident inputs, per-step events, L2 flushed between steps
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    L.gmi_profile_enable(1)
-    L.gmi_profile_read(None, None, 1)
     clocks = ClockSampler(local)
     D.barrier()
     torch.cuda.synchronize()
@@ -514,11 +519,28 @@ def main():
     clk = clocks.stop()
     D.barrier()
     ms_steps = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    t_total = D.max(sum(ms_steps))
+
+    # ---- the same steps as plain launches (seven host calls per forward)
+    tp = timed_steps(step_plain, args.steps, flush, stream)
+    plain = {"value": im.H * im.W * args.steps * world / (D.max(sum(tp)) * 1e-3) / 1e6, "unit": "Mpix/s",
+             "ms_per_step": D.max(sum(tp)) / args.steps,
+             "note": "gmi.interpolate without graph replay; host-launch bound when the host is slow"}
+
+    # ---- per-stage times (events around each stage on the launching stream),
+    # in a separate pass: the steps are queued behind a short device spin so
+    # that no stage waits for the host inside its events
+    L.gmi_profile_enable(1)
+    L.gmi_profile_read(None, None, 1)
+    torch.cuda._sleep(int(args.steps * 400e-6 * SM_MAX_MHZ * 1e6))
+    for k in range(args.steps):
+        flush.zero_()
+        step_plain()
+    torch.cuda.synchronize()
     stage_ms = (ctypes.c_double * 4)()
     stage_n = (ctypes.c_int * 4)()
     L.gmi_profile_read(stage_ms, stage_n, 1)
     L.gmi_profile_enable(0)
-    t_total = D.max(sum(ms_steps))
     ms_per_step = t_total / args.steps
     value = im.H * im.W * args.steps * world / (t_total * 1e-3) / 1e6
 
@@ -531,7 +553,7 @@ def main():
     for _ in range(3):
         dP.copy_(hP, non_blocking=True)
         dV.copy_(hV, non_blocking=True)
-        gmi.interpolate(dP, dV, im.sigma, im.H, im.W, out=out)
+        gmi.interpolate(dP, dV, im.sigma, im.H, im.W, out=out, graph=True)
         hO.copy_(out, non_blocking=True)
     torch.cuda.synchronize()
     D.barrier()
@@ -540,7 +562,7 @@ def main():
         starts[k].record(stream)
         dP.copy_(hP, non_blocking=True)
         dV.copy_(hV, non_blocking=True)
-        gmi.interpolate(dP, dV, im.sigma, im.H, im.W, out=out)
+        gmi.interpolate(dP, dV, im.sigma, im.H, im.W, out=out, graph=True)
         hO.copy_(out, non_blocking=True)
         ends[k].record(stream)
     torch.cuda.synchronize()
@@ -576,7 +598,7 @@ def main():
                        "sigma": im.sigma, "parallelism": "replicas" if world > 1 else "single",
                        "l2": "flushed between steps (256 MB write), not timed"},
             "roofline": roof, "e2e": e2e, "gpu_launches": LAUNCHES_PER_FORWARD * args.steps, "clocks": clk,
-            "stage_ms": stages}
+            "stage_ms": stages, "plain_launch": plain}
     if rank == 0 and not args.no_extras:
         for name, fn in (("batched", lambda: bench_batched(dev, args.steps, args.warmup, flush, stream)),
                          ("fwd_bwd", lambda: bench_fwd_bwd(dev, args.steps, args.warmup, flush, stream)),

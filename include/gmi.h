@@ -75,6 +75,16 @@ typedef enum { GMI_MODE_EXACT = 0, GMI_MODE_TRUNCATED = 1 } gmi_mode;
 
 /* params->flags */
 #define GMI_FLAG_SYNC_CHECK 0x1u   /* synchronise and return the device status */
+/* gmi_forward only: run the launch sequence as a cached CUDA graph.  The first
+ * call with a given device, set of pointers (points, values, image, den_out,
+ * shift_out, workspace), sizes (N, C, H, W, ws_bytes) and params captures it;
+ * later calls with the same ones replay it (one host launch, shorter gaps
+ * between the kernels on the device).  The kernels read the buffers when they
+ * run, so replay is correct whatever they hold.  Up to 32 graphs are kept per
+ * process (least recently used dropped).  Ignored while the stream is being
+ * captured or stage profiling is on.  Worth it for repeated calls on the same
+ * buffers; a call on new buffers pays one capture (~0.1-1 ms). */
+#define GMI_FLAG_GRAPH 0x2u
 
 /* Kernel variants (params->variant); 0 = choose automatically. */
 #define GMI_VARIANT_AUTO 0

@@ -106,20 +106,23 @@ def _check_inputs(points, values):
 
 def interpolate(points, values, sigma: float, H: int, W: int, *, radius_sigmas: float = 6.0,
                 mode="exact", bin_px: int = 0, variant: int = 0, return_aux: bool = False,
-                check: bool = False, out=None):
+                check: bool = False, graph: bool = False, out=None):
     """Forward pass of Eq. 1 / Eq. 2 onto an H x W raster.
 
     Returns the image ``[H, W, C]``; with ``return_aux`` also the per-pixel
     ``den`` and ``shift`` planes (den = sum_i exp(-(d_i^2 - shift)/(2 sigma^2))).
     ``check=True`` synchronises and raises on device-detected errors
-    (non-finite inputs).  Runs on the current CUDA stream.
+    (non-finite inputs).  ``graph=True`` replays a cached CUDA graph of the
+    launch sequence when the same tensors (``out`` included) and sizes come
+    again: pass ``out`` to reuse buffers across calls.  Runs on the current
+    CUDA stream.
     """
     import torch
     points, values = _check_inputs(points, values)
     N, C = int(points.shape[0]), int(values.shape[1])
     H, W = int(H), int(W)
     dev = points.device
-    flags = _lib.FLAG_SYNC_CHECK if check else 0
+    flags = (_lib.FLAG_SYNC_CHECK if check else 0) | (_lib.FLAG_GRAPH if graph else 0)
     md = _mode(mode)
     p = _params(sigma, radius_sigmas, md, flags, bin_px, variant)
     nbytes = _ws_bytes(N, C, H, W, p, (N, C, H, W, float(sigma), float(radius_sigmas), md, bin_px, variant))
@@ -132,7 +135,8 @@ def interpolate(points, values, sigma: float, H: int, W: int, *, radius_sigmas: 
     if torch.cuda.current_device() != dev.index:
         with torch.cuda.device(dev):
             return interpolate(points, values, sigma, H, W, radius_sigmas=radius_sigmas, mode=mode,
-                               bin_px=bin_px, variant=variant, return_aux=return_aux, check=check, out=out)
+                               bin_px=bin_px, variant=variant, return_aux=return_aux, check=check,
+                               graph=graph, out=out)
     st = _lib.load().gmi_forward(points.data_ptr(), values.data_ptr(), N, C, H, W, ctypes.byref(p),
                                  out.data_ptr(), den.data_ptr() if den is not None else None,
                                  shift.data_ptr() if shift is not None else None, ws.data_ptr(),

@@ -21,6 +21,7 @@ STATUS_NAMES = {
 MODE_EXACT = 0
 MODE_TRUNCATED = 1
 FLAG_SYNC_CHECK = 0x1
+FLAG_GRAPH = 0x2
 VARIANT_AUTO, VARIANT_MT4x4, VARIANT_MT4x8, VARIANT_MT2x4 = 0, 1, 2, 3
 STAGES = ("bin", "near", "far", "backward")
 NOALLOC_SCRATCH_BYTES = 32 << 20   # GMI_NOALLOC_SCRATCH_BYTES

@@ -41,6 +41,23 @@ bool profile_on();
 ProfileMark profile_begin(int stage, cudaStream_t s);
 void profile_end(const ProfileMark& m, cudaStream_t s);
 
+// Everything a single-image forward launch sequence depends on: the key of a
+// cached graph (graph_cache.cu).  Built from a zeroed struct so that it
+// compares bytewise.
+struct FwdGraphKey {
+  int device;
+  int C, H, W;
+  long long N;
+  const void *points, *values, *image, *den, *shift, *ws;
+  size_t ws_bytes;
+  gmi_params params;
+};
+
+// Launches the sequence `launch(ctx, stream)` records as a graph: replays the
+// cached graph for `key`, or captures, instantiates, caches and launches one.
+gmi_status forward_graphed(const FwdGraphKey& key, gmi_status (*launch)(void*, cudaStream_t), void* ctx,
+                           cudaStream_t s);
+
 // Extra workspace bytes the backward pass needs beyond the forward layout,
 // and where its regions start inside the extra block.
 long long bwd_extra_bytes(long long N, int C, int H, int W);

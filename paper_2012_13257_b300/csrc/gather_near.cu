@@ -284,25 +284,34 @@ __global__ void __launch_bounds__(256) scatter_plan_kernel(KArgs a_in, int trunc
   }
 }
 
-// Resident 128-thread blocks per SM the register budget is sized for.
-template <int MTH, int MTW>
+// Resident 128-thread blocks per SM the register budget is sized for, from
+// the accumulators a thread holds (MTH * MTW pixels times C + 1 sums).
+template <int MTH, int MTW, int C>
 struct NearOcc {
-  static constexpr int value = MTH * MTW <= 8 ? 5 : (MTH * MTW <= 16 ? 4 : 2);
+  static constexpr int acc = MTH * MTW * (C + 1);
+  static constexpr int value = acc <= 32 ? 5 : (acc <= 64 ? 4 : (acc <= 80 ? 3 : 2));
 };
 
+constexpr int kNearWarps = 4;   // warps per near-kernel block
+
 template <int MTH, int MTW, int C, bool TRUNC>
-__global__ void __launch_bounds__(128, NearOcc<MTH, MTW>::value) near_kernel(KArgs a_in) {
+__global__ void __launch_bounds__(128, NearOcc<MTH, MTW, C>::value) near_kernel(KArgs a_in) {
   const KArgs a = resolve(a_in);
   constexpr int NA = MTH * MTW * (C + 1);   // accumulators per thread
+  constexpr int NP = (C + 1) / 2;           // packed accumulator pairs per pixel
+  constexpr int ODD = (C + 1) & 1;          // one scalar accumulator left over (C even)
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const int lx = lane & 7, ly = lane >> 3;
+  const int warp = threadIdx.x >> 5;
+
   const unsigned n_items = min(a.w.status[kItemCount], a.cap_items);
-  for (;;) {
-    unsigned t = 0;
-    if (lane == 0) t = atomicAdd(&a.w.status[kNearHead], 1u);
-    t = __shfl_sync(full, t, 0);
-    if (t >= n_items) break;
+  const unsigned n_warps = gridDim.x * kNearWarps;
+  // first item by warp index, later ones claimed from the queue (the claim is
+  // made once the item's sums are complete, so that its latency overlaps the
+  // stores without holding an item while this one is still being computed)
+  unsigned t = blockIdx.x * kNearWarps + warp;
+  while (t < n_items) {
     const uint4 item = a.w.items[t];
     const long long wt = (long long)item.x;
     const unsigned split = item.y, S = item.z, slot = item.w;
@@ -324,9 +333,82 @@ __global__ void __launch_bounds__(128, NearOcc<MTH, MTW>::value) near_kernel(KAr
       R2 = U + g.r2k;
     }
 
-    float acc[NA];   // per pixel (r, j): [den, num_0 .. num_{C-1}]
+    // Accumulators in packed pairs (FFMA2 updates two per instruction): per
+    // pixel (r, j) the pairs (den, num_0), (num_1, num_2), plus num_{C-1}
+    // alone when C is even.
+    float2 accp[MTH * MTW * NP];
+    float accs[MTH * MTW * ODD + 1 - ODD];
 #pragma unroll
-    for (int k = 0; k < NA; ++k) acc[k] = 0.0f;
+    for (int k = 0; k < MTH * MTW * NP; ++k) accp[k] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < MTH * MTW * ODD + 1 - ODD; ++k) accs[k] = 0.0f;
+
+    // one candidate point (position p, colour cv) into every pixel of the micro-tile
+    const float sk = g.sk;
+    const float neg_thr = -g.kappa * g.r2k;   // truncated mode: keep -kappa d^2 >= this
+    const float xq0 = (float)x0 + 0.5f, yq0 = (float)y0 + 0.5f;
+    auto consume = [&](const float2 p, const float4 cv) {
+      const float c4[4] = {cv.x, cv.y, cv.z, cv.w};
+      float2 cp[NP];   // (1, c_0), (c_1, c_2)
+      cp[0] = make_float2(1.0f, c4[0]);
+#pragma unroll
+      for (int q = 1; q < NP; ++q) cp[q] = make_float2(c4[2 * q - 1], c4[2 * q]);
+      const float clast = c4[C - 1];   // the scalar accumulator's value (C even)
+      const float u = (xq0 - p.x) * sk;
+      const float v = (yq0 - p.y) * sk;
+      float ax[MTW], gx[MTW], ay[MTH], gy[MTH];
+#pragma unroll
+      for (int j = 0; j < MTW; ++j) {
+        const float tt = u + (float)j * sk;
+        ax[j] = -tt * tt;
+        gx[j] = ex2(ax[j]);
+      }
+#pragma unroll
+      for (int r = 0; r < MTH; ++r) {
+        const float tt = v + (float)r * sk;
+        ay[r] = -tt * tt;
+        gy[r] = ex2(ay[r]);
+      }
+      if (!TRUNC) {
+        // separable weight gy[r] * gx[j]: the column factors times the
+        // point's values once, then one FFMA2 per pair and pixel
+        float2 hx[MTW][NP];
+        float hs[MTW];
+#pragma unroll
+        for (int j = 0; j < MTW; ++j) {
+#pragma unroll
+          for (int q = 0; q < NP; ++q) hx[j][q] = __fmul2_rn(make_float2(gx[j], gx[j]), cp[q]);
+          if (ODD) hs[j] = gx[j] * clast;
+        }
+#pragma unroll
+        for (int r = 0; r < MTH; ++r) {
+          const float2 gg = make_float2(gy[r], gy[r]);
+#pragma unroll
+          for (int j = 0; j < MTW; ++j) {
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+              float2& acq = accp[(r * MTW + j) * NP + q];
+              acq = __ffma2_rn(gg, hx[j][q], acq);
+            }
+            if (ODD) accs[(r * MTW + j) * ODD] = fmaf(gy[r], hs[j], accs[(r * MTW + j) * ODD]);
+          }
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < MTH; ++r)
+#pragma unroll
+          for (int j = 0; j < MTW; ++j) {
+            const float wgt = (ax[j] + ay[r] >= neg_thr) ? gx[j] * gy[r] : 0.0f;
+            const float2 ww = make_float2(wgt, wgt);
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+              float2& acq = accp[(r * MTW + j) * NP + q];
+              acq = __ffma2_rn(ww, cp[q], acq);
+            }
+            if (ODD) accs[(r * MTW + j) * ODD] = fmaf(wgt, clast, accs[(r * MTW + j) * ODD]);
+          }
+      }
+    };
 
     if (active) {
       const LaneWin w = lane_window(g, x0, y0, nx, ny, R2);
@@ -334,95 +416,67 @@ __global__ void __launch_bounds__(128, NearOcc<MTH, MTW>::value) near_kernel(KAr
       unsigned lo = 0, hi = 0xffffffffu;
       if (S > 1) {
         unsigned n = 0;
-        for (int by = w.by_lo; by <= w.by_hi; ++by) {
+        for (int yb = w.by_lo; yb <= w.by_hi; ++yb) {
           unsigned s0, e0;
-          row_segment(a, g, w, by, s0, e0);
+          row_segment(a, g, w, yb, s0, e0);
           n += e0 - s0;
         }
         lo = (unsigned)(((unsigned long long)n * split) / S);
         hi = (unsigned)(((unsigned long long)n * (split + 1)) / S);
       }
-      const float sk = g.sk;
-      const float neg_thr = -g.kappa * g.r2k;   // truncated mode: keep -kappa d^2 >= this
       const float2* __restrict__ sxy = a.w.sxy;
       const float4* __restrict__ sval = a.w.sval;
       int by = w.by_lo - 1;
       unsigned i = 0, end = 0, cum = 0;
-      float2 pn = make_float2(0.f, 0.f);
-      float4 cn = make_float4(0.f, 0.f, 0.f, 0.f);
       // bounds of the next bin row, loaded one row ahead
       unsigned ns = 0, ne = 0;
       row_segment(a, g, w, w.by_lo, ns, ne);
-      for (;;) {
-        while (i >= end) {
-          if (++by > w.by_hi || cum >= hi) goto done;
+      // moves [i, end) to the next bin row holding part of [lo, hi); false at the end
+      auto next_row = [&]() -> bool {
+        for (;;) {
+          if (++by > w.by_hi || cum >= hi) return false;
           const unsigned s0 = ns, e0 = ne;
           if (by < w.by_hi) row_segment(a, g, w, by + 1, ns, ne);
           const unsigned len = e0 - s0, rs = cum;
           cum += len;
           i = s0 + (lo > rs ? min(lo - rs, len) : 0u);
           end = s0 + (hi > rs ? min(hi - rs, len) : 0u);
-          if (i < end) {
-            pn = __ldg(&sxy[i]);
-            cn = __ldg(&sval[i]);
-          }
+          if (i < end) return true;
         }
-        {
-          // the candidate loaded one iteration ahead; start loading the next
+      };
+      if (next_row()) {
+        // the candidate is always loaded one iteration ahead, across bin rows too
+        float2 pn = __ldg(&sxy[i]);
+        float4 cn = __ldg(&sval[i]);
+        bool more = true;
+        while (more) {
           const float2 p = pn;
           const float4 cv = cn;
-          ++i;
-          if (i < end) {
+          if (++i >= end) more = next_row();
+          if (more) {
             pn = __ldg(&sxy[i]);
             cn = __ldg(&sval[i]);
           }
-          const float c4[4] = {cv.x, cv.y, cv.z, cv.w};
-          const float u = (w.xq0 - p.x) * sk;
-          const float v = (w.yq0 - p.y) * sk;
-          float ax[MTW], gx[MTW], ay[MTH], gy[MTH];
-#pragma unroll
-          for (int j = 0; j < MTW; ++j) {
-            const float tt = u + (float)j * sk;
-            ax[j] = -tt * tt;
-            gx[j] = ex2(ax[j]);
-          }
-#pragma unroll
-          for (int r = 0; r < MTH; ++r) {
-            const float tt = v + (float)r * sk;
-            ay[r] = -tt * tt;
-            gy[r] = ex2(ay[r]);
-          }
-          if (!TRUNC) {
-            float hxc[MTW][C];
-#pragma unroll
-            for (int j = 0; j < MTW; ++j)
-#pragma unroll
-              for (int ch = 0; ch < C; ++ch) hxc[j][ch] = gx[j] * c4[ch];
-#pragma unroll
-            for (int r = 0; r < MTH; ++r)
-#pragma unroll
-              for (int j = 0; j < MTW; ++j) {
-                float* q = acc + (r * MTW + j) * (C + 1);
-                q[0] = fmaf(gy[r], gx[j], q[0]);
-#pragma unroll
-                for (int ch = 0; ch < C; ++ch) q[1 + ch] = fmaf(gy[r], hxc[j][ch], q[1 + ch]);
-              }
-          } else {
-#pragma unroll
-            for (int r = 0; r < MTH; ++r)
-#pragma unroll
-              for (int j = 0; j < MTW; ++j) {
-                float* q = acc + (r * MTW + j) * (C + 1);
-                const float wgt = (ax[j] + ay[r] >= neg_thr) ? gx[j] * gy[r] : 0.0f;
-                q[0] += wgt;
-#pragma unroll
-                for (int ch = 0; ch < C; ++ch) q[1 + ch] = fmaf(wgt, c4[ch], q[1 + ch]);
-              }
-          }
+          consume(p, cv);
         }
       }
-    done:;
     }
+
+    unsigned nt = 0;
+    if (lane == 0) nt = n_warps + atomicAdd(&a.w.status[kNearHead], 1u);
+
+    float acc[NA];   // per pixel (r, j): [den, num_0 .. num_{C-1}]
+#pragma unroll
+    for (int px = 0; px < MTH * MTW; ++px)
+#pragma unroll
+      for (int k = 0; k <= C; ++k) {
+        if (k < 2 * NP) {
+          const float2 pr = accp[px * NP + k / 2];
+          acc[px * (C + 1) + k] = (k & 1) ? pr.y : pr.x;
+        } else {
+          acc[px * (C + 1) + k] = accs[px * ODD];
+        }
+      }
 
     bool finish = true;
     if (S > 1) {
@@ -456,58 +510,74 @@ __global__ void __launch_bounds__(128, NearOcc<MTH, MTW>::value) near_kernel(KAr
         }
       }
     }
-    if (!(finish && active)) continue;
-
-    // normalise (Eq. 1) and store
+    if (finish && active) {
+      // normalise (Eq. 1) and store
 #pragma unroll
-    for (int r = 0; r < MTH; ++r) {
-      if (r >= ny) break;
-      float outv[MTW * C];
-      float denv[MTW];
-#pragma unroll
-      for (int j = 0; j < MTW; ++j) {
-        const float* q = acc + (r * MTW + j) * (C + 1);
-        const float d = q[0];
-        const float inv = d > 0.0f ? 1.0f / d : 0.0f;
-        denv[j] = d;
-#pragma unroll
-        for (int ch = 0; ch < C; ++ch) outv[j * C + ch] = q[1 + ch] * inv;
-      }
-      const long long row = (long long)(y0 + r) * g.W + x0;
-      if (g.vec_ok && nx == MTW) {
-        float4* o = reinterpret_cast<float4*>(g.image + row * C);
-#pragma unroll
-        for (int k = 0; k < MTW * C / 4; ++k) o[k] = make_float4(outv[4 * k], outv[4 * k + 1], outv[4 * k + 2], outv[4 * k + 3]);
-        if (g.den) {
-          float4* dd = reinterpret_cast<float4*>(g.den + row);
-#pragma unroll
-          for (int k = 0; k < MTW / 4; ++k) dd[k] = make_float4(denv[4 * k], denv[4 * k + 1], denv[4 * k + 2], denv[4 * k + 3]);
-        }
-        if (g.shift) {
-          float4* ss = reinterpret_cast<float4*>(g.shift + row);
-#pragma unroll
-          for (int k = 0; k < MTW / 4; ++k) ss[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-      } else {
+      for (int r = 0; r < MTH; ++r) {
+        if (r >= ny) break;
+        float outv[MTW * C];
+        float denv[MTW];
 #pragma unroll
         for (int j = 0; j < MTW; ++j) {
-          if (j >= nx) break;
+          const float* q = acc + (r * MTW + j) * (C + 1);
+          const float d = q[0];
+          const float inv = d > 0.0f ? 1.0f / d : 0.0f;
+          denv[j] = d;
 #pragma unroll
-          for (int ch = 0; ch < C; ++ch) g.image[(row + j) * C + ch] = outv[j * C + ch];
-          if (g.den) g.den[row + j] = denv[j];
-          if (g.shift) g.shift[row + j] = 0.0f;
+          for (int ch = 0; ch < C; ++ch) outv[j * C + ch] = q[1 + ch] * inv;
+        }
+        const long long row = (long long)(y0 + r) * g.W + x0;
+        if (g.vec_ok && nx == MTW) {
+          float4* o = reinterpret_cast<float4*>(g.image + row * C);
+#pragma unroll
+          for (int k = 0; k < MTW * C / 4; ++k) o[k] = make_float4(outv[4 * k], outv[4 * k + 1], outv[4 * k + 2], outv[4 * k + 3]);
+          if (g.den) {
+            float4* dd = reinterpret_cast<float4*>(g.den + row);
+#pragma unroll
+            for (int k = 0; k < MTW / 4; ++k) dd[k] = make_float4(denv[4 * k], denv[4 * k + 1], denv[4 * k + 2], denv[4 * k + 3]);
+          }
+          if (g.shift) {
+            float4* ss = reinterpret_cast<float4*>(g.shift + row);
+#pragma unroll
+            for (int k = 0; k < MTW / 4; ++k) ss[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < MTW; ++j) {
+            if (j >= nx) break;
+#pragma unroll
+            for (int ch = 0; ch < C; ++ch) g.image[(row + j) * C + ch] = outv[j * C + ch];
+            if (g.den) g.den[row + j] = denv[j];
+            if (g.shift) g.shift[row + j] = 0.0f;
+          }
         }
       }
     }
+    t = __shfl_sync(full, nt, 0);
   }
 }
 
-// Launch helpers: one instantiation per (micro-tile, channels, mode).
+// Resident blocks per SM of one near-kernel instantiation (register-limited,
+// as the launch bounds ask), cached; all devices of a process are taken to be alike.
+template <int MTH, int MTW, int C, bool TRUNC>
+static int near_occ() {
+  static const int n = [] {
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, near_kernel<MTH, MTW, C, TRUNC>, 32 * kNearWarps, 0);
+    return b > 0 ? b : 1;
+  }();
+  return n;
+}
+
+template <int MTH, int MTW, int C, bool TRUNC>
+static cudaError_t launch_near_k(const KArgs& a, int grid, cudaStream_t s) {
+  near_kernel<MTH, MTW, C, TRUNC><<<grid, 32 * kNearWarps, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
 template <int MTH, int MTW, int C>
 static cudaError_t launch_near_c(const KArgs& a, bool trunc, int grid, cudaStream_t s) {
-  if (trunc) near_kernel<MTH, MTW, C, true><<<grid, 128, 0, s>>>(a);
-  else near_kernel<MTH, MTW, C, false><<<grid, 128, 0, s>>>(a);
-  return cudaGetLastError();
+  return trunc ? launch_near_k<MTH, MTW, C, true>(a, grid, s) : launch_near_k<MTH, MTW, C, false>(a, grid, s);
 }
 
 template <int MTH, int MTW>
@@ -537,13 +607,10 @@ cudaError_t launch_near(const KArgs& a, int mth, int mtw, bool trunc, int grid, 
   return cudaErrorInvalidValue;
 }
 
-// Resident 128-thread blocks per SM for a near-kernel instantiation (cached).
+// Resident near-kernel blocks per SM for an instantiation (cached).
 template <int MTH, int MTW, int C>
 static int occ_c(bool trunc) {
-  int n = 0;
-  if (trunc) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, near_kernel<MTH, MTW, C, true>, 128, 0);
-  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, near_kernel<MTH, MTW, C, false>, 128, 0);
-  return n > 0 ? n : 1;
+  return trunc ? near_occ<MTH, MTW, C, true>() : near_occ<MTH, MTW, C, false>();
 }
 
 template <int MTH, int MTW>
@@ -557,16 +624,10 @@ static int occ_mt(int C, bool trunc) {
 }
 
 int near_blocks_per_sm(int mth, int mtw, int C, bool trunc) {
-  static int cache[3][5][2];
-  const int v = (mth == 4 && mtw == 8) ? 1 : (mth == 2 ? 2 : 0);
   const int c = C < 1 ? 1 : (C > 4 ? 4 : C);
-  int& slot = cache[v][c][trunc ? 1 : 0];
-  if (slot == 0) {
-    if (v == 1) slot = occ_mt<4, 8>(c, trunc);
-    else if (v == 2) slot = occ_mt<2, 4>(c, trunc);
-    else slot = occ_mt<4, 4>(c, trunc);
-  }
-  return slot;
+  if (mth == 4 && mtw == 8) return occ_mt<4, 8>(c, trunc);
+  if (mth == 2 && mtw == 4) return occ_mt<2, 4>(c, trunc);
+  return occ_mt<4, 4>(c, trunc);
 }
 
 }  // namespace gmi

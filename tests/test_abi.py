@@ -66,6 +66,15 @@ def test_workspace_size_checks():
     assert _ws(10, 3, 8, 8, sigma=float("nan"))[0] == 1
     assert _ws(10, 3, 8, 8, radius_sigmas=-1.0)[0] == 1
     assert _ws(10, 3, 8, 8, mode=7)[0] == 1
+    assert _ws(10, 3, 8, 8, flags=0x4)[0] == 1       # unknown flag bit
+    assert _ws(10, 3, 8, 8, flags=_lib.FLAG_GRAPH | _lib.FLAG_SYNC_CHECK)[0] == 0
+
+
+def test_flag_values_match_the_header():
+    src = open(os.path.join(ROOT, "include", "gmi.h")).read()
+    defs = dict(re.findall(r"#define\s+GMI_(FLAG_[A-Z_]+)\s+(0x[0-9a-fA-F]+)u", src))
+    assert {k: int(v, 16) for k, v in defs.items()} == {"FLAG_SYNC_CHECK": _lib.FLAG_SYNC_CHECK,
+                                                       "FLAG_GRAPH": _lib.FLAG_GRAPH}
 
 
 def test_forward_rejects_bad_arguments_without_launching():

@@ -182,3 +182,52 @@ def test_dense_blob_split_tiles(cuda_device, variant):
     assert_parity(im, out, ref)
     np.testing.assert_allclose(log_scaled_den(den, shift, im.sigma),
                                log_scaled_den(ref["den"], ref["shift"], im.sigma), rtol=0, atol=1e-4)
+
+
+def test_graph_replay(cuda_device):
+    """GMI_FLAG_GRAPH: the first call captures the launch sequence, later
+    calls on the same buffers replay it.  Replays read the buffers' current
+    contents (values changed in place change the result), new buffers get a
+    graph of their own, and inside an outer capture the flag is ignored.
+    (Split warp tiles add their partial sums with float atomics in a varying
+    order, so two runs agree to rounding, not bitwise.)"""
+    import torch
+    g = gmi()
+
+    def same(a, b):
+        return torch.allclose(a, b, rtol=0, atol=2e-6)
+
+    im = wl.tiny_random(7, 3000, 70, 90, sigma=1.1)
+    P, V = to_dev(im.points, cuda_device), to_dev(im.values, cuda_device)
+    plain = g.interpolate(P, V, im.sigma, im.H, im.W)
+    out = torch.empty_like(plain)
+    for _ in range(3):
+        g.interpolate(P, V, im.sigma, im.H, im.W, graph=True, out=out)
+        torch.cuda.synchronize()
+        assert same(out, plain)
+    ref = oracle.forward(im.points, im.values, im.H, im.W, im.sigma)
+    assert np.abs(out.cpu().numpy() - ref["image"]).max() <= TOL_FWD
+    # in-place change of the inputs: the replay sees it
+    V.mul_(0.5)
+    g.interpolate(P, V, im.sigma, im.H, im.W, graph=True, out=out)
+    torch.cuda.synchronize()
+    ref2 = oracle.forward(im.points, (im.values * np.float32(0.5)).astype(np.float32), im.H, im.W, im.sigma)
+    assert np.abs(out.cpu().numpy() - ref2["image"]).max() <= TOL_FWD
+    # another output buffer: its own graph
+    out2 = torch.empty_like(plain)
+    g.interpolate(P, V, im.sigma, im.H, im.W, graph=True, out=out2)
+    torch.cuda.synchronize()
+    assert same(out2, out)
+    # inside a torch graph capture the flag is ignored and the kernels are captured
+    s = torch.cuda.Stream()
+    out3 = torch.empty_like(plain)
+    with torch.cuda.stream(s):
+        g.interpolate(P, V, im.sigma, im.H, im.W, out=out3)
+    torch.cuda.synchronize()
+    gr = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(gr, stream=s):
+        g.interpolate(P, V, im.sigma, im.H, im.W, graph=True, out=out3)
+    out3.zero_()
+    gr.replay()
+    torch.cuda.synchronize()
+    assert same(out3, out)
