@@ -194,9 +194,9 @@ def cpu_baseline(im, target_s=12.0):
         t0 = time.perf_counter()
         oracle.forward(im.points, im.values, im.H, im.W, im.sigma, pixels=pix)
         t = time.perf_counter() - t0
-        if t >= target_s / 4 or n >= 1 << 20:
+        if t >= 10.0 or n >= 1 << 20:
             break
-        n = int(n * min(8.0, max(2.0, (target_s / 4) / max(t, 1e-3))))
+        n = int(n * min(8.0, max(1.2, target_s / max(t, 1e-3))))
     return {"value": n / t / 1e6, "unit": "Mpix/s", "cores": oracle.num_threads(), "kind": "oracle",
             "sample": "%d random pixels of the %dx%d image (%d points each), %.1f s" % (n, im.H, im.W, im.N, t)}
 
