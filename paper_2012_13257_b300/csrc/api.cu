@@ -194,9 +194,30 @@ gmi_status run_bin_and_plan(KArgs& a, const WsLayout& L, void* ws, int mth, int 
   return GMI_OK;
 }
 
+bool SideStream::create() {
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+    s = nullptr;
+    return false;
+  }
+  if (cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&join, cudaEventDisableTiming) != cudaSuccess) {
+    destroy();
+    return false;
+  }
+  return true;
+}
+
+void SideStream::destroy() {
+  if (fork) cudaEventDestroy(fork);
+  if (join) cudaEventDestroy(join);
+  if (s) cudaStreamDestroy(s);
+  s = nullptr;
+  fork = join = nullptr;
+}
+
 // Binning + plan + near + far on prepared arguments (single image or batch).
 gmi_status run_forward_pipeline(KArgs& a, const WsLayout& L, void* ws, int mth, int mtw, bool trunc,
-                                cudaStream_t s) {
+                                cudaStream_t s, const SideStream* side) {
   gmi_status st = run_bin_and_plan(a, L, ws, mth, mtw, trunc, s, true);
   if (st != GMI_OK) return st;
   cudaError_t e;
@@ -204,6 +225,15 @@ gmi_status run_forward_pipeline(KArgs& a, const WsLayout& L, void* ws, int mth, 
   const int per_sm = near_blocks_per_sm(mth, mtw, a.C, trunc);
   // persistent: at most one resident wave, and no more warps than work items can use
   const int gn = (int)std::max<long long>(1, std::min<long long>(a.wt_total * 4, (long long)sms * per_sm));
+  if (side && !trunc) {
+    // far-field kernel as a parallel branch: it fills the SMs the persistent
+    // near kernel leaves as its work runs out
+    if (cudaEventRecord(side->fork, s) != cudaSuccess || cudaStreamWaitEvent(side->s, side->fork, 0) != cudaSuccess ||
+        launch_far(a, mth, mtw, sms * 4, side->s) != cudaSuccess || cudaEventRecord(side->join, side->s) != cudaSuccess ||
+        launch_near(a, mth, mtw, trunc, gn, s) != cudaSuccess || cudaStreamWaitEvent(s, side->join, 0) != cudaSuccess)
+      return GMI_ERR_CUDA;
+    return GMI_OK;
+  }
   const ProfileMark pn = profile_begin(GMI_STAGE_NEAR, s);
   if ((e = launch_near(a, mth, mtw, trunc, gn, s)) != cudaSuccess) return GMI_ERR_CUDA;
   profile_end(pn, s);
@@ -351,10 +381,10 @@ gmi_status gmi_forward(const float* points, const float* values, int64_t N, int 
       int mth, mtw;
       bool trunc;
     } ctx{&a, &L, workspace, mth, mtw, trunc};
-    auto launch = [](void* c, cudaStream_t cs) -> gmi_status {
+    auto launch = [](void* c, cudaStream_t cs, const SideStream* side) -> gmi_status {
       const Ctx* x = static_cast<const Ctx*>(c);
       KArgs ka = *x->a;
-      return run_forward_pipeline(ka, *x->L, x->ws, x->mth, x->mtw, x->trunc, cs);
+      return run_forward_pipeline(ka, *x->L, x->ws, x->mth, x->mtw, x->trunc, cs, side);
     };
     st = forward_graphed(key, launch, &ctx, s);
   } else {

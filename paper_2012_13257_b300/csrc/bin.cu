@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(256) scan_final_kernel(unsigned* __restrict__ 
 
 __global__ void __launch_bounds__(256) bin_scatter_kernel(KArgs a_in) {
   const KArgs a = resolve(a_in);
-  bin_scatter_body(a, gridDim.x);
+  bin_scatter_body(a, gridDim.x, blockIdx.x);
 }
 
 }  // namespace gmi

@@ -14,9 +14,10 @@ static __device__ __forceinline__ void point_bin(const ImageGeom& g, float x, fl
   oob = !(x >= 0.0f && x < (float)g.W && y >= 0.0f && y < (float)g.H);
 }
 
-// Scatter body; `nblocks` blocks starting at block 0 stride over the chunks.
-static __device__ __forceinline__ void bin_scatter_body(const KArgs& a, int nblocks) {
-  for (long long ch = blockIdx.x; ch < a.ch_total; ch += nblocks) {
+// Scatter body: `nblocks` blocks stride over the chunks; this block is number
+// `block` of them.
+static __device__ __forceinline__ void bin_scatter_body(const KArgs& a, int nblocks, int block) {
+  for (long long ch = block; ch < a.ch_total; ch += nblocks) {
     const int img = find_image<0>(a, ch);
     const ImageGeom& g = *geom_ptr(a, img);
     const long long i = (ch - g.ch_base) * kChunk + threadIdx.x;

@@ -35,11 +35,11 @@ __global__ void __launch_bounds__(32 * kFarWarps) far_kernel(KArgs a_in, int mth
   const int slot = lane % PS, part = lane / PS;
   const int pr = slot / mtw, pj = slot % mtw;
 
-  for (;;) {
-    unsigned e = 0;
-    if (lane == 0) e = atomicAdd(&a.w.status[kFarHead], 1u);
-    e = __shfl_sync(full, e, 0);
-    if (e >= nfar) break;
+  // first entry by warp index, later ones claimed from the queue; with an
+  // empty queue (the usual case for dense inputs) warps leave at once
+  const unsigned n_warps = gridDim.x * kFarWarps;
+  unsigned e = blockIdx.x * kFarWarps + wid;
+  while (e < nfar) {
     const uint2 q = a.w.farq[e];
     const int img = (int)q.x;
     const ImageGeom g = a.w.table ? a.w.table[img] : a.g0;
@@ -141,7 +141,10 @@ __global__ void __launch_bounds__(32 * kFarWarps) far_kernel(KArgs a_in, int mth
       if (g.den) g.den[pix] = accd[0];
       if (g.shift) g.shift[pix] = mshift;
     }
-    __syncwarp();
+    __syncwarp();   // the candidate list is rewritten by the next entry
+    unsigned ne = 0;
+    if (lane == 0) ne = n_warps + atomicAdd(&a.w.status[kFarHead], 1u);
+    e = __shfl_sync(full, ne, 0);
   }
 }
 

@@ -270,17 +270,19 @@ __device__ void near_plan_body(const KArgs& a, int trunc, long long wt) {
   }
 }
 
-// Scatter (blocks [0, n_scatter)) and plan (the remaining blocks, one warp per
-// warp tile) in one launch: the plan needs only the bin offsets and flags,
-// which the scan has already produced, so the two run side by side.
+// Plan (blocks [0, n_plan), one warp per warp tile) and scatter (the
+// remaining n_scatter blocks) in one launch: the plan needs only the bin
+// offsets and flags, which the scan has already produced, so the two run side
+// by side.  The plan's warps are latency-bound chains of small loads, so they
+// get the low block indices and start first; the scatter streams around them.
 template <int MTH, int MTW>
-__global__ void __launch_bounds__(256) scatter_plan_kernel(KArgs a_in, int trunc, int n_scatter) {
+__global__ void __launch_bounds__(256) scatter_plan_kernel(KArgs a_in, int trunc, int n_scatter, int n_plan) {
   const KArgs a = resolve(a_in);
-  if ((int)blockIdx.x < n_scatter) {
-    bin_scatter_body(a, n_scatter);
-  } else {
-    const long long wt = (long long)(blockIdx.x - n_scatter) * 8 + (threadIdx.x >> 5);
+  if ((int)blockIdx.x < n_plan) {
+    const long long wt = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
     near_plan_body<MTH, MTW>(a, trunc, wt);
+  } else {
+    bin_scatter_body(a, n_scatter, (int)blockIdx.x - n_plan);
   }
 }
 
@@ -592,11 +594,12 @@ static cudaError_t launch_near_mt(const KArgs& a, bool trunc, int grid, cudaStre
 
 // n_scatter scatter blocks (0: scatter not needed) followed by the plan's blocks.
 cudaError_t launch_scatter_plan(const KArgs& a, bool trunc, int n_scatter, cudaStream_t s) {
-  const unsigned blocks = (unsigned)(n_scatter + (a.wt_total + 7) / 8);
+  const int n_plan = (int)((a.wt_total + 7) / 8);
+  const unsigned blocks = (unsigned)(n_scatter + n_plan);
   const int t = trunc ? 1 : 0;
-  if (a.mth == 4 && a.mtw == 8) scatter_plan_kernel<4, 8><<<blocks, 256, 0, s>>>(a, t, n_scatter);
-  else if (a.mth == 2 && a.mtw == 4) scatter_plan_kernel<2, 4><<<blocks, 256, 0, s>>>(a, t, n_scatter);
-  else scatter_plan_kernel<4, 4><<<blocks, 256, 0, s>>>(a, t, n_scatter);
+  if (a.mth == 4 && a.mtw == 8) scatter_plan_kernel<4, 8><<<blocks, 256, 0, s>>>(a, t, n_scatter, n_plan);
+  else if (a.mth == 2 && a.mtw == 4) scatter_plan_kernel<2, 4><<<blocks, 256, 0, s>>>(a, t, n_scatter, n_plan);
+  else scatter_plan_kernel<4, 4><<<blocks, 256, 0, s>>>(a, t, n_scatter, n_plan);
   return cudaGetLastError();
 }
 
