@@ -44,8 +44,9 @@ METRIC = "interpolated Mpix/s (batched+served vs plain launch); p50/p99 latency;
 WORKLOAD = ("upsample_1024: 512^2 source grid jittered U[-0.5,0.5] px -> 1024x1024x3 float32, "
             "sigma=1.0 px, exact mode, k=6, values from a smooth random field")
 L2_FLUSH_BYTES = 256 << 20
-SFU_PER_SM_CLK = 16      # ex2 results per SM per clock (cc 10.x throughput table)
-FP32_PER_SM_CLK = 128    # FP32 lanes per SM per clock
+FP32_PER_SM_CLK = 128    # FP32 FMA results per SM per clock (4 x 32 lanes; measured ~123)
+SFU_PER_SM_CLK = 32      # ex2 results per SM per clock on B300 (measured 32.0)
+FP32_OPS_PER_PAIR = 8    # per algorithmic pair: ~4 for d^2, 1 exponent scale, C + 1 = 4 accumulations (C = 3)
 SM_MAX_MHZ = 2032.0      # B300 maximum SM clock
 LAUNCHES_PER_FORWARD = 6  # count, scan x2, scatter+plan, near, far
 
@@ -61,6 +62,12 @@ def parse():
     return ap.parse_args()
 
 
+def replica_throughput(pixels_per_step: int, steps: int, world: int, t_max_ms: float) -> float:
+    """Whole-job Mpix/s of `world` replicas that each ran `steps` steps of
+    `pixels_per_step` output pixels, the slowest taking t_max_ms."""
+    return pixels_per_step * steps * world / (t_max_ms * 1e-3) / 1e6
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -69,14 +76,19 @@ def dist_env():
 
 
 class Dist:
-    """Barrier and max-reduce over ranks (NCCL when launched under torchrun)."""
+    """Barrier and max-reduce over ranks when launched under torchrun: NCCL
+    between GPUs, gloo for CPU devices (the multi-rank tests).  Replicas only:
+    the workload does not shard, so no data crosses ranks."""
 
     def __init__(self, world, device):
         self.world = world
         self.device = device
         if world > 1:
             import torch.distributed as dist
-            dist.init_process_group("nccl", device_id=device)
+            if device.type == "cuda":
+                dist.init_process_group("nccl", device_id=device)
+            else:
+                dist.init_process_group("gloo")
             self.dist = dist
 
     def barrier(self):
@@ -523,7 +535,7 @@ def main():
 
     # ---- the same steps as plain launches (seven host calls per forward)
     tp = timed_steps(step_plain, args.steps, flush, stream)
-    plain = {"value": im.H * im.W * args.steps * world / (D.max(sum(tp)) * 1e-3) / 1e6, "unit": "Mpix/s",
+    plain = {"value": replica_throughput(im.H * im.W, args.steps, world, D.max(sum(tp))), "unit": "Mpix/s",
              "ms_per_step": D.max(sum(tp)) / args.steps,
              "note": "gmi.interpolate without graph replay; host-launch bound when the host is slow"}
 
@@ -542,7 +554,7 @@ def main():
     L.gmi_profile_read(stage_ms, stage_n, 1)
     L.gmi_profile_enable(0)
     ms_per_step = t_total / args.steps
-    value = im.H * im.W * args.steps * world / (t_total * 1e-3) / 1e6
+    value = replica_throughput(im.H * im.W, args.steps, world, t_total)
 
     # ---- e2e: pinned host buffers, copies inside the timed region
     hP = torch.as_tensor(im.points).pin_memory()
@@ -568,7 +580,7 @@ def main():
     torch.cuda.synchronize()
     e_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     e_total = D.max(sum(e_ms))
-    e2e = {"value": im.H * im.W * args.steps * world / (e_total * 1e-3) / 1e6, "unit": "Mpix/s",
+    e2e = {"value": replica_throughput(im.H * im.W, args.steps, world, e_total), "unit": "Mpix/s",
            "h2d_bytes_per_step": int(hP.numel() * 4 + hV.numel() * 4),
            "d2h_bytes_per_step": int(hO.numel() * 4),
            "ms_per_step": e_total / args.steps}
@@ -578,17 +590,25 @@ def main():
     sms = props.multi_processor_count
     near_ms = stage_ms[1] / max(1, stage_n[1])
     pairs = algorithmic_pairs(im) if rank == 0 else 0
-    peak_gpair = sms * SFU_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e9
+    rates = gmi.measure_unit_rates() if rank == 0 else None
+    clk_mhz = clk.get("sm_mhz") or SM_MAX_MHZ
+    # per-pair peaks of the two units the pair work uses; the FP32 pipe binds
+    fp32_gpair = sms * FP32_PER_SM_CLK / FP32_OPS_PER_PAIR * clk_mhz * 1e6 / 1e9
+    sfu_gpair = sms * SFU_PER_SM_CLK * clk_mhz * 1e6 / 1e9
+    peak_gpair = min(fp32_gpair, sfu_gpair)
     achieved = pairs / (near_ms * 1e-3) / 1e9 if near_ms > 0 else None
     roof = {"bound": "alu", "achieved": achieved, "peak": peak_gpair, "unit": "Gpair/s",
             "frac": (achieved / peak_gpair) if achieved else None,
             "traffic": near_kernel_traffic(),
             "kernel": "near_kernel<4,4,3,exact>", "launch_ms": near_ms, "pairs_per_launch": pairs,
-            "peak_basis": "%d SMs x %d ex2/clk x %.0f MHz: one exponential per (pixel, point) pair "
-                          "within the exact-mode radius; recipe unit counts and max clock" %
-                          (sms, SFU_PER_SM_CLK, SM_MAX_MHZ),
+            "peak_basis": "FP32 pipe: %d SMs x %d FMA/clk / %d FP32 ops per algorithmic pair x %.0f MHz "
+                          "(SM clock sampled during the timed steps); the SFU allows %.0f Gpair/s "
+                          "(%d ex2/clk, one per pair); per-clock rates from the unit counts, checked by "
+                          "unit_rates_measured (results per SM per clock)" %
+                          (sms, FP32_PER_SM_CLK, FP32_OPS_PER_PAIR, clk_mhz, sfu_gpair, SFU_PER_SM_CLK),
+            "unit_rates_measured": rates,
             "frac_fma_strict": (pairs * (im.C + 1) / (near_ms * 1e-3) /
-                                (sms * FP32_PER_SM_CLK * SM_MAX_MHZ * 1e6)) if near_ms > 0 else None}
+                                (sms * FP32_PER_SM_CLK * clk_mhz * 1e6)) if near_ms > 0 else None}
     stages = {name: (stage_ms[i] / stage_n[i] if stage_n[i] else None) for i, name in enumerate(_lib.STAGES)}
 
     line = {"metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,

@@ -230,6 +230,17 @@ gmi_status gmi_profile_enable(int on);
  * them.  Stages recorded while the event pool was exhausted are not counted. */
 gmi_status gmi_profile_read(double* ms, int* launches, int reset);
 
+/* Measurement aid (no counterpart in the paper): the issue rates of the units
+ * the near-field gather is bound by, measured on the current device with
+ * streams of independent dependency chains, one 1024-thread block per SM
+ * timed by the SM's own clock.  Writes, per SM per clock,
+ *   rates[0]  ex2.approx.ftz.f32 results (the SFU),
+ *   rates[1]  FP32 fused multiply-adds issued as FFMA,
+ *   rates[2]  FP32 fused multiply-adds issued as packed FFMA2 (two each).
+ * Synchronous (device-wide), a few milliseconds; allocates and frees two small
+ * device buffers.  Errors: GMI_ERR_INVALID_ARG (rates NULL), GMI_ERR_CUDA. */
+gmi_status gmi_measure_unit_rates(double* rates);
+
 /* ------------------------------------------------------------------------
  * Batched forward: B independent images of uneven size in one persistent
  * launch over a global tile queue (the shapes live in a device descriptor

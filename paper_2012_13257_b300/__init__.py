@@ -640,3 +640,14 @@ def gmi_interpolate_stacked(plan, points, values, sigmas, H: int, W: int):
     if _GMIStackedFunction is None:
         _GMIStackedFunction = _stacked_function()
     return _GMIStackedFunction.apply(plan, int(H), int(W), points, values, sigmas)
+
+
+def measure_unit_rates(device=None) -> dict:
+    """Measured results per SM per clock of the units the near-field gather
+    is bound by on this GPU: ``ex2`` (SFU), ``ffma`` and ``ffma2`` (FP32 FMA
+    pipe, scalar and packed).  Synchronous, a few milliseconds."""
+    import torch
+    r = (ctypes.c_double * 3)()
+    with torch.cuda.device(device if device is not None else torch.cuda.current_device()):
+        _lib.check(_lib.load().gmi_measure_unit_rates(r), "gmi_measure_unit_rates")
+    return {"ex2": r[0], "ffma": r[1], "ffma2": r[2]}
