@@ -17,7 +17,7 @@ namespace gmi {
 cudaError_t launch_near(const KArgs& a, int mth, int mtw, bool trunc, int grid, cudaStream_t s);
 cudaError_t launch_scatter_plan(const KArgs& a, bool trunc, int n_scatter, cudaStream_t s);
 int near_blocks_per_sm(int mth, int mtw, int C, bool trunc);
-cudaError_t launch_far(const KArgs& a, int mth, int mtw, int grid, cudaStream_t s);
+cudaError_t launch_far(const KArgs& a, int mth, int mtw, int sms, cudaStream_t s);
 __global__ void bin_count_kernel(KArgs a);
 __global__ void scan_partial_kernel(const unsigned* cnt, long long nb, unsigned* partials, const long long* totals);
 __global__ void scan_final_kernel(unsigned* off, long long nb, const unsigned* partials, const long long* totals);
@@ -194,30 +194,9 @@ gmi_status run_bin_and_plan(KArgs& a, const WsLayout& L, void* ws, int mth, int 
   return GMI_OK;
 }
 
-bool SideStream::create() {
-  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
-    s = nullptr;
-    return false;
-  }
-  if (cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&join, cudaEventDisableTiming) != cudaSuccess) {
-    destroy();
-    return false;
-  }
-  return true;
-}
-
-void SideStream::destroy() {
-  if (fork) cudaEventDestroy(fork);
-  if (join) cudaEventDestroy(join);
-  if (s) cudaStreamDestroy(s);
-  s = nullptr;
-  fork = join = nullptr;
-}
-
 // Binning + plan + near + far on prepared arguments (single image or batch).
 gmi_status run_forward_pipeline(KArgs& a, const WsLayout& L, void* ws, int mth, int mtw, bool trunc,
-                                cudaStream_t s, const SideStream* side) {
+                                cudaStream_t s) {
   gmi_status st = run_bin_and_plan(a, L, ws, mth, mtw, trunc, s, true);
   if (st != GMI_OK) return st;
   cudaError_t e;
@@ -225,21 +204,12 @@ gmi_status run_forward_pipeline(KArgs& a, const WsLayout& L, void* ws, int mth, 
   const int per_sm = near_blocks_per_sm(mth, mtw, a.C, trunc);
   // persistent: at most one resident wave, and no more warps than work items can use
   const int gn = (int)std::max<long long>(1, std::min<long long>(a.wt_total * 4, (long long)sms * per_sm));
-  if (side && !trunc) {
-    // far-field kernel as a parallel branch: it fills the SMs the persistent
-    // near kernel leaves as its work runs out
-    if (cudaEventRecord(side->fork, s) != cudaSuccess || cudaStreamWaitEvent(side->s, side->fork, 0) != cudaSuccess ||
-        launch_far(a, mth, mtw, sms * 4, side->s) != cudaSuccess || cudaEventRecord(side->join, side->s) != cudaSuccess ||
-        launch_near(a, mth, mtw, trunc, gn, s) != cudaSuccess || cudaStreamWaitEvent(s, side->join, 0) != cudaSuccess)
-      return GMI_ERR_CUDA;
-    return GMI_OK;
-  }
   const ProfileMark pn = profile_begin(GMI_STAGE_NEAR, s);
   if ((e = launch_near(a, mth, mtw, trunc, gn, s)) != cudaSuccess) return GMI_ERR_CUDA;
   profile_end(pn, s);
   if (!trunc) {
     const ProfileMark pf = profile_begin(GMI_STAGE_FAR, s);
-    if ((e = launch_far(a, mth, mtw, sms * 4, s)) != cudaSuccess) return GMI_ERR_CUDA;
+    if ((e = launch_far(a, mth, mtw, sms, s)) != cudaSuccess) return GMI_ERR_CUDA;
     profile_end(pf, s);
   }
   return GMI_OK;
@@ -381,10 +351,10 @@ gmi_status gmi_forward(const float* points, const float* values, int64_t N, int 
       int mth, mtw;
       bool trunc;
     } ctx{&a, &L, workspace, mth, mtw, trunc};
-    auto launch = [](void* c, cudaStream_t cs, const SideStream* side) -> gmi_status {
+    auto launch = [](void* c, cudaStream_t cs) -> gmi_status {
       const Ctx* x = static_cast<const Ctx*>(c);
       KArgs ka = *x->a;
-      return run_forward_pipeline(ka, *x->L, x->ws, x->mth, x->mtw, x->trunc, cs, side);
+      return run_forward_pipeline(ka, *x->L, x->ws, x->mth, x->mtw, x->trunc, cs);
     };
     st = forward_graphed(key, launch, &ctx, s);
   } else {

@@ -28,18 +28,8 @@ WsLayout ws_layout(long long n_total, long long nb_total, long long mt_total, lo
 DevWork bind_ws(void* ws, const WsLayout& L);
 gmi_status run_bin_and_plan(KArgs& a, const WsLayout& L, void* ws, int mth, int mtw, bool trunc,
                             cudaStream_t s, bool plan);
-// A second stream with fork/join events for graph captures: work launched on
-// it between the fork and the join becomes a parallel branch of the graph.
-struct SideStream {
-  cudaStream_t s = nullptr;
-  cudaEvent_t fork = nullptr, join = nullptr;
-  bool create();    // false on failure (nothing left allocated)
-  void destroy();
-};
-// With `side`, the far-field kernel runs on the side stream beside the near
-// kernel (both need only the plan); without it, after the near kernel.
 gmi_status run_forward_pipeline(KArgs& a, const WsLayout& L, void* ws, int mth, int mtw, bool trunc,
-                                cudaStream_t s, const SideStream* side = nullptr);
+                                cudaStream_t s);
 gmi_status read_status(const void* ws, cudaStream_t s);
 
 // Stage timing (profile.cu): no-ops unless gmi_profile_enable(1) was called.
@@ -65,8 +55,8 @@ struct FwdGraphKey {
 
 // Launches the sequence `launch(ctx, stream)` records as a graph: replays the
 // cached graph for `key`, or captures, instantiates, caches and launches one.
-gmi_status forward_graphed(const FwdGraphKey& key, gmi_status (*launch)(void*, cudaStream_t, const SideStream*),
-                           void* ctx, cudaStream_t s);
+gmi_status forward_graphed(const FwdGraphKey& key, gmi_status (*launch)(void*, cudaStream_t), void* ctx,
+                           cudaStream_t s);
 
 // Extra workspace bytes the backward pass needs beyond the forward layout,
 // and where its regions start inside the extra block.

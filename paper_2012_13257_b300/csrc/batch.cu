@@ -42,7 +42,6 @@ struct gmi_batch_plan {
   gmi::BatchSlot slot[2];
   int next = 0;
   cudaStream_t cap_stream = nullptr; // private stream the launch sequence is captured on
-  gmi::SideStream side;               // parallel branch of the captured graph (far-field kernel)
   // backward pass: per-pixel planes, fallback queue and its own staging
   char* bwd_base = nullptr;
   size_t bwd_bytes = 0;
@@ -117,7 +116,7 @@ extern "C" gmi_status gmi_batch_plan_create(int max_images, int64_t max_points, 
   p->stage_bytes = (stage_size(max_images) + 255) / 256 * 256;
   p->base_bytes = p->L.total + 2 * p->stage_bytes;
   if (cudaGetDevice(&p->device) != cudaSuccess || cudaMalloc(&p->base, p->base_bytes) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking) != cudaSuccess || !p->side.create()) {
+      cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
     if (p->base) cudaFree(p->base);
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
     delete p;
@@ -169,7 +168,6 @@ extern "C" gmi_status gmi_batch_plan_destroy(gmi_batch_plan* p) {
   if (p->bwd_base) cudaFree(p->bwd_base);
   if (p->bwd_host) cudaFreeHost(p->bwd_host);
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
-  p->side.destroy();
   delete p;
   return GMI_OK;
 }
@@ -242,8 +240,7 @@ extern "C" gmi_status gmi_forward_batched(gmi_batch_plan* p, const gmi_image_des
       cudaStream_t cs = p->cap_stream;
       if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return GMI_ERR_CUDA;
       cudaError_t e = cudaMemcpyAsync(sl.dev, sl.host, copy_bytes, cudaMemcpyHostToDevice, cs);
-      gmi_status st =
-          e == cudaSuccess ? run_forward_pipeline(a, p->L, p->base, p->mth, p->mtw, trunc, cs, &p->side) : GMI_ERR_CUDA;
+      gmi_status st = e == cudaSuccess ? run_forward_pipeline(a, p->L, p->base, p->mth, p->mtw, trunc, cs) : GMI_ERR_CUDA;
       const cudaError_t ec = cudaStreamEndCapture(cs, &graph);
       if (st != GMI_OK || ec != cudaSuccess) {
         if (graph) cudaGraphDestroy(graph);

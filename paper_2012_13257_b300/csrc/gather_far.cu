@@ -55,26 +55,12 @@ __global__ void __launch_bounds__(32 * kFarWarps) far_kernel(KArgs a_in, int mth
     const float qx = (float)(x0 + pj) + 0.5f, qy = (float)(y0 + pr) + 0.5f;
 
     // A. smallest non-empty window (bin resolution), then U from its points
-    const float bf = (float)g.b;
-    const float hmax = 2.0f * (float)max(g.W, g.H) + bf;
-    float hi = bf;
-    unsigned cnt = window_count(a, g, t, hi);
-    while (cnt == 0 && hi < hmax) {
-      hi *= 2.0f;
-      cnt = window_count(a, g, t, hi);
-    }
+    const float hi = smallest_window(a, g, t);
     float accd[kMaxC + 1];
 #pragma unroll
     for (int k = 0; k <= kMaxC; ++k) accd[k] = 0.0f;
     float mshift = 0.0f;
-    if (cnt > 0) {
-      float lo = hi * 0.5f;
-      if (hi <= bf) lo = 0.0f;
-      while (hi - lo > bf) {
-        const float mid = floorf((lo + hi) * 0.5f / bf) * bf;
-        if (mid <= lo) break;
-        if (window_count(a, g, t, mid) > 0) hi = mid; else lo = mid;
-      }
+    if (hi >= 0.0f) {
       const unsigned ns = min(collect(a, g, t, hi, -1.0f, 0u, L), (unsigned)kFarCap);
       float best = INFINITY;
       for (unsigned k = part; k < ns; k += nparts) {
@@ -148,7 +134,26 @@ __global__ void __launch_bounds__(32 * kFarWarps) far_kernel(KArgs a_in, int mth
   }
 }
 
-cudaError_t launch_far(const KArgs& a, int mth, int mtw, int grid, cudaStream_t s) {
+// Resident far-kernel blocks per SM for C channels (cached).
+static int far_blocks_per_sm(int C) {
+  static int cache[kMaxC + 1];
+  const int c = C < 1 ? 1 : (C > kMaxC ? kMaxC : C);
+  if (cache[c] == 0) {
+    int n = 0;
+    switch (c) {
+      case 1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, far_kernel<1>, 32 * kFarWarps, 0); break;
+      case 2: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, far_kernel<2>, 32 * kFarWarps, 0); break;
+      case 3: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, far_kernel<3>, 32 * kFarWarps, 0); break;
+      default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, far_kernel<4>, 32 * kFarWarps, 0); break;
+    }
+    cache[c] = n > 0 ? n : 1;
+  }
+  return cache[c];
+}
+
+// Persistent launch: every resident warp slot (the work is latency-bound).
+cudaError_t launch_far(const KArgs& a, int mth, int mtw, int sms, cudaStream_t s) {
+  const int grid = sms * far_blocks_per_sm(a.C);
   switch (a.C) {
     case 1: far_kernel<1><<<grid, 32 * kFarWarps, 0, s>>>(a, mth, mtw); break;
     case 2: far_kernel<2><<<grid, 32 * kFarWarps, 0, s>>>(a, mth, mtw); break;

@@ -34,8 +34,8 @@ bool same_key(const FwdGraphKey& a, const FwdGraphKey& b) { return memcmp(&a, &b
 
 }  // namespace
 
-gmi_status forward_graphed(const FwdGraphKey& key, gmi_status (*launch)(void*, cudaStream_t, const SideStream*),
-                           void* ctx, cudaStream_t s) {
+gmi_status forward_graphed(const FwdGraphKey& key, gmi_status (*launch)(void*, cudaStream_t), void* ctx,
+                           cudaStream_t s) {
   {
     std::lock_guard<std::mutex> lk(g_mu);
     for (auto it = g_lru.begin(); it != g_lru.end(); ++it) {
@@ -45,28 +45,21 @@ gmi_status forward_graphed(const FwdGraphKey& key, gmi_status (*launch)(void*, c
       }
     }
   }
-  // capture the launch sequence on a private stream (nothing runs), with a
-  // side stream for parallel branches; instantiate; launch
+  // capture the launch sequence on a private stream (nothing runs), instantiate, launch
   cudaStream_t cs;
   if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return GMI_ERR_CUDA;
-  SideStream side;
-  if (!side.create()) {
-    cudaStreamDestroy(cs);
-    return GMI_ERR_CUDA;
-  }
   gmi_status st = GMI_OK;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
     st = GMI_ERR_CUDA;
   } else {
-    st = launch(ctx, cs, &side);
+    st = launch(ctx, cs);
     const cudaError_t e = cudaStreamEndCapture(cs, &graph);
     if (st == GMI_OK && e != cudaSuccess) st = GMI_ERR_CUDA;
   }
   if (st == GMI_OK && cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) st = GMI_ERR_CUDA;
   if (graph) cudaGraphDestroy(graph);
-  side.destroy();
   cudaStreamDestroy(cs);
   if (st != GMI_OK) {
     cudaGetLastError();
