@@ -39,6 +39,18 @@ def _mode(mode) -> int:
 
 _param_cache = {}
 _ws_size_cache = {}
+_table_cache = {}
+_offset_cache = {}
+
+
+def _stream_handle(dev):
+    """Raw handle of the current CUDA stream of `dev` (a cheap query where
+    torch offers one)."""
+    import torch
+    raw = getattr(torch._C, "_cuda_getCurrentRawStream", None)
+    if raw is not None:
+        return raw(dev.index if dev.index is not None else torch.cuda.current_device())
+    return torch.cuda.current_stream(dev).cuda_stream
 _ws_buffers = {}
 
 
@@ -130,7 +142,7 @@ def interpolate(points, values, sigma: float, H: int, W: int, *, radius_sigmas: 
         out = torch.empty((H, W, C), dtype=torch.float32, device=dev)
     den = torch.empty((H, W), dtype=torch.float32, device=dev) if return_aux else None
     shift = torch.empty((H, W), dtype=torch.float32, device=dev) if return_aux else None
-    stream = torch.cuda.current_stream(dev).cuda_stream
+    stream = _stream_handle(dev)
     ws = _workspace(dev, stream, nbytes)
     if torch.cuda.current_device() != dev.index:
         with torch.cuda.device(dev):
@@ -170,7 +182,7 @@ def interpolate_backward(points, values, sigma: float, H: int, W: int, image, de
     gp = torch.empty((N, 2), dtype=torch.float32, device=dev) if need[0] else None
     gv = torch.empty((N, C), dtype=torch.float32, device=dev) if need[1] else None
     gs = torch.empty((1,), dtype=torch.float32, device=dev) if need[2] else None
-    stream = torch.cuda.current_stream(dev).cuda_stream
+    stream = _stream_handle(dev)
     ws = _workspace(dev, stream, nbytes)
     if torch.cuda.current_device() != dev.index:
         with torch.cuda.device(dev):
@@ -189,22 +201,31 @@ def interpolate_backward(points, values, sigma: float, H: int, W: int, image, de
 _sigma_cache = {}
 
 
+def _cached_host_copy(t, read):
+    """read(t) for a CUDA tensor, cached per (tensor object, version): reading
+    device memory synchronises, so an unchanged sigma tensor is read once and
+    one updated in place (an optimizer step) is read again.  The entry holds a
+    weak reference to the very tensor, so a new tensor that reuses a freed
+    address or object id never sees another tensor's values."""
+    import weakref
+    e = _sigma_cache.get(id(t))
+    if e is not None and e[0]() is t and e[1] == t._version:
+        return e[2]
+    v = read(t)
+    if len(_sigma_cache) > 4096:
+        _sigma_cache.clear()
+    _sigma_cache[id(t)] = (weakref.ref(t), t._version, v)
+    return v
+
+
 def _sigma_value(sigma_t) -> float:
-    """Host value of sigma.  Reading a CUDA scalar synchronises the device, so
-    the value is cached per (tensor, version): an unchanged sigma tensor costs
-    one read, a sigma updated in place (optimizer step) is read again."""
+    """Host value of sigma (a float, or a CPU or CUDA scalar tensor)."""
     import torch
     if not isinstance(sigma_t, torch.Tensor):
         return float(sigma_t)
     if sigma_t.device.type == "cpu":
         return float(sigma_t)
-    key = (sigma_t.data_ptr(), sigma_t._version)
-    v = _sigma_cache.get(key)
-    if v is None:
-        if len(_sigma_cache) > 4096:
-            _sigma_cache.clear()
-        v = _sigma_cache[key] = float(sigma_t)
-    return v
+    return _cached_host_copy(sigma_t, lambda t: float(t))
 
 
 def _autograd_function():
@@ -221,8 +242,10 @@ def _autograd_function():
             img, den, shift = interpolate(points, values, sigma, H, W, radius_sigmas=radius_sigmas, mode=mode,
                                           bin_px=bin_px, variant=variant, return_aux=True)
             ctx.set_materialize_grads(False)
-            ctx.save_for_backward(points, values)
-            ctx.aux = (img, den, shift)
+            # tensors (the output included) go through save_for_backward: kept
+            # on ctx directly, the output would form a reference cycle with its
+            # grad_fn and outlive the step until Python's cycle collector ran
+            ctx.save_for_backward(points, values, img, den, shift)
             ctx.cfg = (sigma, H, W, radius_sigmas, mode, bin_px, variant, isinstance(sigma_t, torch.Tensor))
             return img
 
@@ -230,8 +253,7 @@ def _autograd_function():
         def backward(ctx, g):
             if g is None:
                 return (None,) * 9
-            points, values = ctx.saved_tensors
-            img, den, shift = ctx.aux
+            points, values, img, den, shift = ctx.saved_tensors
             sigma, H, W, k, mode, bin_px, variant, sig_is_t = ctx.cfg
             need = (ctx.needs_input_grad[0], ctx.needs_input_grad[1], ctx.needs_input_grad[2] and sig_is_t)
             gp, gv, gs = interpolate_backward(points.detach(), values.detach(), sigma, H, W, img, den, shift,
@@ -283,6 +305,31 @@ def _np_table(ctype, n):
     return np.zeros(max(n, 1), dtype=dt)
 
 
+def _scratch_table(ctype, n):
+    """A zeroed table reused across calls (the batched C calls copy their
+    table into the plan's staging before returning, so it is free again)."""
+    key = (ctype, n)
+    t = _table_cache.get(key)
+    if t is None:
+        t = _table_cache[key] = _np_table(ctype, n)
+    else:
+        t.fill(0)
+    return t
+
+
+def _ptrs(t, B):
+    """Addresses of the B equal slices t[0], ..., t[B-1] of a contiguous tensor."""
+    import numpy as np
+    step = t[0].numel() * t.element_size() if B else 0
+    key = (B, step)
+    off = _offset_cache.get(key)
+    if off is None:
+        if len(_offset_cache) > 1024:
+            _offset_cache.clear()
+        off = _offset_cache[key] = np.arange(B, dtype=np.uint64) * np.uint64(step)
+    return off + np.uint64(t.data_ptr())
+
+
 class BatchPlan:
     """A reusable batched-forward plan (device workspace + pinned staging
     allocated once).  ``forward(images)`` interpolates a list of images, each a
@@ -329,7 +376,7 @@ class BatchPlan:
             tab["H"][i], tab["W"][i] = int(im["H"]), int(im["W"])
             tab["sigma"][i] = float(im["sigma"])
             tab["bin_px"][i] = int(im.get("bin_px", 0))
-        stream = torch.cuda.current_stream(dev).cuda_stream if dev is not None else None
+        stream = _stream_handle(dev) if dev is not None else None
         _lib.check(_lib.load().gmi_forward_batched(
             self._h, ctypes.cast(tab.ctypes.data, ctypes.POINTER(_lib.ImageDesc)), n, 1 if use_graph else 0,
             stream), "gmi_forward_batched")
@@ -388,7 +435,7 @@ class BatchPlan:
             tab["sigma"][i] = float(im["sigma"])
             tab["bin_px"][i] = int(im.get("bin_px", 0))
             res.append((gp, gv, gs))
-        stream = torch.cuda.current_stream(dev).cuda_stream if dev is not None else None
+        stream = _stream_handle(dev) if dev is not None else None
         _lib.check(_lib.load().gmi_backward_batched(
             self._h, ctypes.cast(tab.ctypes.data, ctypes.POINTER(_lib.GradDesc)), n, stream), "gmi_backward_batched")
         self._keep_bwd = (keep, tab)
@@ -510,23 +557,31 @@ def _batch_function():
                 ims.append({"points": P, "values": V, "sigma": _sigma_value(S), "H": H, "W": W,
                             "den": aux[b], "shift": aux[B + b]})
             outs = plan.forward(ims, use_graph=True)
-            for im, o in zip(ims, outs):
-                im["image"] = o
             ctx.set_materialize_grads(False)
-            ctx.plan, ctx.ims = plan, ims
+            # every tensor through save_for_backward (no reference cycle with
+            # the outputs); the rest as plain values
+            saved = []
+            for b in range(B):
+                saved += [flat[3 * b], flat[3 * b + 1], outs[b], aux[b], aux[B + b]]
+            ctx.save_for_backward(*saved)
+            ctx.plan = plan
+            ctx.meta = [(ims[b]["sigma"], ims[b]["H"], ims[b]["W"]) for b in range(B)]
             ctx.sig_t = [isinstance(flat[3 * b + 2], torch.Tensor) for b in range(B)]
             return tuple(outs)
 
         @staticmethod
         def backward(ctx, *grads):
-            ims = ctx.ims
+            sv = ctx.saved_tensors
             req = []
-            for b, (im, g) in enumerate(zip(ims, grads)):
+            for b, g in enumerate(grads):
+                P, V, img, den, shift = sv[5 * b:5 * b + 5]
+                sigma, H, W = ctx.meta[b]
                 if g is None:
-                    g = torch.zeros_like(im["image"])
+                    g = torch.zeros_like(img)
                 need = (ctx.needs_input_grad[2 + 3 * b], ctx.needs_input_grad[3 + 3 * b],
                         ctx.needs_input_grad[4 + 3 * b] and ctx.sig_t[b])
-                req.append(dict(im, points=im["points"].detach(), values=im["values"].detach(), grad=g, need=need))
+                req.append({"points": P.detach(), "values": V.detach(), "sigma": sigma, "H": H, "W": W,
+                            "image": img, "den": den, "shift": shift, "grad": g, "need": need})
             res = ctx.plan.backward(req)
             out = [None, None]
             for gp, gv, gs in res:
@@ -557,8 +612,7 @@ def _stacked_function():
     import numpy as np
     import torch
 
-    def ptrs(t, B):
-        return np.uint64(t.data_ptr()) + np.arange(B, dtype=np.uint64) * np.uint64(t[0].numel() * t.element_size())
+    ptrs = _ptrs
 
     class GMIStackedFunction(torch.autograd.Function):
         """B equal-shaped images ([B,N,2] points, [B,N,C] values, [B] sigmas)
@@ -574,30 +628,31 @@ def _stacked_function():
             points, values = points.contiguous(), values.contiguous()
             sig = _sigma_list(sigmas, B)
             out, den, shift = _flat_views([(B, H, W, C), (B, H, W), (B, H, W)], dev)
-            tab = _np_table(_lib.ImageDesc, B)
+            tab = _scratch_table(_lib.ImageDesc, B)
             tab["points"], tab["values"], tab["image"] = ptrs(points, B), ptrs(values, B), ptrs(out, B)
             tab["den"], tab["shift"] = ptrs(den, B), ptrs(shift, B)
             tab["N"], tab["H"], tab["W"], tab["sigma"] = N, H, W, sig
-            stream = torch.cuda.current_stream(dev).cuda_stream
-            plan.forward_table(tab, B, stream)
+            plan.forward_table(tab, B, _stream_handle(dev))
             ctx.set_materialize_grads(False)
-            ctx.plan, ctx.keep = plan, (tab,)
-            ctx.save_for_backward(points, values)
-            ctx.aux = (out, den, shift, sig, H, W, isinstance(sigmas, torch.Tensor))
+            # tensors (the output included) through save_for_backward: no
+            # reference cycle between the output and its grad_fn
+            ctx.plan = plan
+            ctx.save_for_backward(points, values, out, den, shift)
+            ctx.aux = (sig, H, W, isinstance(sigmas, torch.Tensor))
             return out
 
         @staticmethod
         def backward(ctx, g):
             if g is None:
                 return (None,) * 6
-            points, values = ctx.saved_tensors
-            out, den, shift, sig, H, W, sig_t = ctx.aux
+            points, values, out, den, shift = ctx.saved_tensors
+            sig, H, W, sig_t = ctx.aux
             B, N, C = int(points.shape[0]), int(points.shape[1]), int(values.shape[2])
             dev = points.device
             g = g.contiguous().float()
             need = ctx.needs_input_grad
             gp, gv, gs = _flat_views([(B, N, 2), (B, N, C), (B,)], dev)
-            tab = _np_table(_lib.GradDesc, B)
+            tab = _scratch_table(_lib.GradDesc, B)
             tab["points"], tab["values"] = ptrs(points, B), ptrs(values, B)
             tab["image"], tab["den"], tab["shift"], tab["grad_image"] = ptrs(out, B), ptrs(den, B), ptrs(shift, B), ptrs(g, B)
             if need[3]:
@@ -605,10 +660,9 @@ def _stacked_function():
             if need[4]:
                 tab["grad_values"] = ptrs(gv, B)
             if need[5] and sig_t:
-                tab["grad_sigma"] = np.uint64(gs.data_ptr()) + np.arange(B, dtype=np.uint64) * np.uint64(4)
+                tab["grad_sigma"] = ptrs(gs, B)
             tab["N"], tab["H"], tab["W"], tab["sigma"] = N, H, W, sig
-            ctx.plan.backward_table(tab, B, torch.cuda.current_stream(dev).cuda_stream)
-            ctx.keep = (tab, g)
+            ctx.plan.backward_table(tab, B, _stream_handle(dev))
             return (None, None, None, gp if need[3] else None, gv if need[4] else None,
                     gs if (need[5] and sig_t) else None)
 
@@ -620,11 +674,7 @@ def _sigma_list(sigmas, B):
     import torch
     if isinstance(sigmas, torch.Tensor):
         if sigmas.device.type != "cpu":
-            key = (sigmas.data_ptr(), sigmas._version, B)
-            v = _sigma_cache.get(key)
-            if v is None:
-                v = _sigma_cache[key] = sigmas.detach().float().cpu().numpy().reshape(B)
-            return v
+            return _cached_host_copy(sigmas, lambda t: t.detach().float().cpu().numpy().reshape(B))
         return sigmas.detach().float().numpy().reshape(B)
     return np.broadcast_to(np.asarray(sigmas, dtype=np.float32), (B,))
 

@@ -48,11 +48,15 @@ struct gmi_batch_plan {
   float4* pplane = nullptr;
   unsigned* fbflag = nullptr;
   uint2* fbq = nullptr;
-  char* bwd_host = nullptr;
+  // two pinned host buffers for the backward's tables, so that one call's
+  // table can be written while the previous call's upload is pending; one
+  // device copy (calls on a plan are ordered on one stream)
+  char* bwd_host[2] = {nullptr, nullptr};
   char* bwd_dev = nullptr;
   size_t bwd_stage = 0;
-  cudaEvent_t bwd_done = nullptr;
-  bool bwd_used = false;
+  cudaEvent_t bwd_done[2] = {nullptr, nullptr};
+  bool bwd_used[2] = {false, false};
+  int bwd_next = 0;
   std::mutex mu;
 };
 
@@ -128,8 +132,10 @@ extern "C" gmi_status gmi_batch_plan_create(int max_images, int64_t max_points, 
   p->bwd_bytes = planes + al256(sizeof(unsigned) * (size_t)p->cap_mt) + al256(sizeof(uint2) * (size_t)p->cap_mt) +
                  p->bwd_stage;
   if (cudaMalloc((void**)&p->bwd_base, p->bwd_bytes) != cudaSuccess ||
-      cudaMallocHost((void**)&p->bwd_host, p->bwd_stage) != cudaSuccess ||
-      cudaEventCreateWithFlags(&p->bwd_done, cudaEventDisableTiming) != cudaSuccess) {
+      cudaMallocHost((void**)&p->bwd_host[0], p->bwd_stage) != cudaSuccess ||
+      cudaMallocHost((void**)&p->bwd_host[1], p->bwd_stage) != cudaSuccess ||
+      cudaEventCreateWithFlags(&p->bwd_done[0], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&p->bwd_done[1], cudaEventDisableTiming) != cudaSuccess) {
     gmi_batch_plan_destroy(p);
     return GMI_ERR_CUDA;
   }
@@ -161,12 +167,15 @@ extern "C" gmi_status gmi_batch_plan_destroy(gmi_batch_plan* p) {
     if (p->slot[k].host) cudaFreeHost(p->slot[k].host);
   }
   if (p->base) cudaFree(p->base);
-  if (p->bwd_done) {
-    cudaEventSynchronize(p->bwd_done);
-    cudaEventDestroy(p->bwd_done);
+  for (int k = 0; k < 2; ++k) {
+    if (p->bwd_done[k]) {
+      cudaEventSynchronize(p->bwd_done[k]);
+      cudaEventDestroy(p->bwd_done[k]);
+    }
   }
   if (p->bwd_base) cudaFree(p->bwd_base);
-  if (p->bwd_host) cudaFreeHost(p->bwd_host);
+  for (int k = 0; k < 2; ++k)
+    if (p->bwd_host[k]) cudaFreeHost(p->bwd_host[k]);
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
   delete p;
   return GMI_OK;
@@ -277,10 +286,12 @@ extern "C" gmi_status gmi_backward_batched(gmi_batch_plan* p, const gmi_grad_des
     if (((uintptr_t)d.points & 7u) || ((uintptr_t)d.values & 3u)) return GMI_ERR_INVALID_ARG;
   }
   std::lock_guard<std::mutex> lk(p->mu);
-  if (p->bwd_used && cudaEventSynchronize(p->bwd_done) != cudaSuccess) return GMI_ERR_CUDA;
-  long long* tot = (long long*)p->bwd_host;
-  ImageGeom* table = (ImageGeom*)(p->bwd_host + kTotCount * sizeof(long long));
-  BwdImage* btab = (BwdImage*)(p->bwd_host + stage_size(p->max_images));
+  const int hs = p->bwd_next;
+  char* host = p->bwd_host[hs];
+  if (p->bwd_used[hs] && cudaEventSynchronize(p->bwd_done[hs]) != cudaSuccess) return GMI_ERR_CUDA;   // buffer free
+  long long* tot = (long long*)host;
+  ImageGeom* table = (ImageGeom*)(host + kTotCount * sizeof(long long));
+  BwdImage* btab = (BwdImage*)(host + stage_size(p->max_images));
   long long npt = 0, nb = 0, nwt = 0, nch = 0, nmt = 0, npx = 0;
   for (int i = 0; i < B; ++i) {
     const gmi_grad_desc& d = descs[i];
@@ -309,7 +320,7 @@ extern "C" gmi_status gmi_backward_batched(gmi_batch_plan* p, const gmi_grad_des
   tot[kTotChunks] = nch;
   tot[kTotMicroTiles] = nmt;
   tot[kTotPixels] = npx;
-  if (cudaMemcpyAsync(p->bwd_dev, p->bwd_host, bwd_stage_size(p->max_images), cudaMemcpyHostToDevice, s) != cudaSuccess)
+  if (cudaMemcpyAsync(p->bwd_dev, host, bwd_stage_size(p->max_images), cudaMemcpyHostToDevice, s) != cudaSuccess)
     return GMI_ERR_CUDA;
 
   KArgs a;
@@ -338,7 +349,8 @@ extern "C" gmi_status gmi_backward_batched(gmi_batch_plan* p, const gmi_grad_des
   const ProfileMark pm = profile_begin(GMI_STAGE_BACKWARD, s);
   if (launch_backward(a, b, s) != cudaSuccess) return GMI_ERR_CUDA;
   profile_end(pm, s);
-  if (cudaEventRecord(p->bwd_done, s) != cudaSuccess) return GMI_ERR_CUDA;
-  p->bwd_used = true;
+  if (cudaEventRecord(p->bwd_done[hs], s) != cudaSuccess) return GMI_ERR_CUDA;
+  p->bwd_used[hs] = true;
+  p->bwd_next = hs ^ 1;
   return (p->params.flags & GMI_FLAG_SYNC_CHECK) ? read_status(p->base, s) : GMI_OK;
 }

@@ -184,3 +184,66 @@ def test_stacked_autograd_matches_oracle(cuda_device):
         fwd = oracle.forward(im.points, im.values, H, W, im.sigma)["image"]
         assert np.abs(out[b].detach().cpu().numpy() - fwd).max() <= 1e-4
     plan.close()
+
+
+@pytest.mark.parametrize("op", ["single", "list", "stacked"])
+def test_autograd_ops_free_their_buffers_each_step(cuda_device, op):
+    """The autograd ops keep their tensors through save_for_backward, so a
+    forward + backward step leaves no reference cycle: the device memory in
+    use returns to the same level after every step without Python's cycle
+    collector (a cycle through the output kept whole images alive and forced
+    a device allocation per step)."""
+    import gc
+    import torch
+    g = gmi()
+    imgs = [wl.tiny_random(40 + k, 600, 48, 56, sigma=1.0) for k in range(3)]
+    P = [to_dev(im.points, cuda_device).requires_grad_(True) for im in imgs]
+    V = [to_dev(im.values, cuda_device).requires_grad_(True) for im in imgs]
+    S = [torch.tensor(1.0, device=cuda_device, requires_grad=True) for _ in imgs]
+    plan = g.BatchPlan(3, sum(im.N for im in imgs), sum(im.H * im.W for im in imgs), 3)
+
+    def step():
+        if op == "single":
+            out = g.gmi_interpolate(P[0], V[0], S[0], 48, 56)
+            out.sum().backward()
+        elif op == "list":
+            outs = g.gmi_interpolate_batch(plan, P, V, S, [(48, 56)] * 3)
+            sum(o.sum() for o in outs).backward()
+        else:
+            out = g.gmi_interpolate_stacked(plan, torch.stack(P), torch.stack(V), torch.stack(S), 48, 56)
+            out.sum().backward()
+
+    gc.disable()
+    try:
+        for _ in range(3):
+            step()
+        torch.cuda.synchronize()
+        base = torch.cuda.memory_allocated()
+        for _ in range(4):
+            step()
+            torch.cuda.synchronize()
+            assert torch.cuda.memory_allocated() == base
+    finally:
+        gc.enable()
+        plan.close()
+
+
+def test_sigma_tensors_are_read_per_tensor(cuda_device):
+    """Fresh sigma tensors with new values (which the caching allocator tends
+    to place at a just-freed address) are each read for what they hold; an
+    in-place update of one tensor is seen too."""
+    import torch
+    g = gmi()
+    im = wl.tiny_random(77, 500, 40, 44, sigma=1.0)
+    P, V = to_dev(im.points, cuda_device), to_dev(im.values, cuda_device)
+    for v in (0.8, 1.3, 0.8, 1.7, 1.1):
+        S = torch.tensor(v, dtype=torch.float32, device=cuda_device)
+        got = g.gmi_interpolate(P, V, S, 40, 44)
+        ref = g.interpolate(P, V, float(np.float32(v)), 40, 44)
+        assert torch.allclose(got, ref, rtol=0, atol=2e-6), v
+        del S, got
+    S = torch.tensor(0.9, dtype=torch.float32, device=cuda_device)
+    g.gmi_interpolate(P, V, S, 40, 44)
+    S.fill_(1.6)
+    assert torch.allclose(g.gmi_interpolate(P, V, S, 40, 44), g.interpolate(P, V, float(np.float32(1.6)), 40, 44),
+                          rtol=0, atol=2e-6)
