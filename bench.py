@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--impl", default="gmi", choices=["gmi", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="headline workload only")
+    ap.add_argument("--only", choices=["batched", "fwd_bwd", "serving"],
+                    help="run only this secondary workload and print its object (for profiling it)")
     return ap.parse_args()
 
 
@@ -500,6 +502,15 @@ def main():
     V = torch.as_tensor(im.values, device=dev)
     out = torch.empty((im.H, im.W, im.C), dtype=torch.float32, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    if args.only:
+        stream = torch.cuda.current_stream(dev)
+        fn = {"batched": lambda: bench_batched(dev, args.steps, args.warmup, flush, stream),
+              "fwd_bwd": lambda: bench_fwd_bwd(dev, args.steps, args.warmup, flush, stream),
+              "serving": lambda: bench_serving(dev)}[args.only]
+        if rank == 0:
+            print(json.dumps({args.only: fn()}), flush=True)
+        D.close()
+        return
     stream = torch.cuda.current_stream(dev)
 
     def step():
