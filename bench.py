@@ -59,7 +59,7 @@ def parse():
     ap.add_argument("--impl", default="gmi", choices=["gmi", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="headline workload only")
-    ap.add_argument("--only", choices=["batched", "fwd_bwd", "serving"],
+    ap.add_argument("--only", choices=["batched", "fwd_bwd", "serving", "reconstruction", "point_optimization"],
                     help="run only this secondary workload and print its object (for profiling it)")
     return ap.parse_args()
 
@@ -363,6 +363,74 @@ def bench_fwd_bwd(dev, steps, warmup, flush, stream):
                         "torch.autograd.Function (list-batched and per-image autograd ops for comparison)"}
 
 
+def bench_reconstruction(dev, side=768, factors=(2, 3, 4, 6, 8), sigma_scales=(0.2, 0.25, 0.35, 0.5, 0.7)):
+    """Reconstruction quality (the paper's downsample-then-upsample study,
+    section 3.2, on a smooth random field instead of ImageNet images): a field
+    with up to 24 cycles across a side x side image is point-sampled at the
+    centres of f x f blocks and brought back to full size by this method (best
+    sigma of a small sweep, sigma = scale * f) and by torch's nearest, bilinear
+    and bicubic resampling; mean L1 error against the full-resolution field."""
+    import torch
+    import torch.nn.functional as F
+    import paper_2012_13257_b300 as gmi
+    import workloads as wl
+    rows = {}
+    for f in factors:
+        pts, vals, low, truth = wl.reconstruction_case(f, side)
+        T = torch.as_tensor(truth, device=dev)
+        P, V = torch.as_tensor(pts, device=dev), torch.as_tensor(vals, device=dev)
+        errs = {}
+        for sc in sigma_scales:
+            out = gmi.interpolate(P, V, sc * f, side, side)
+            errs[sc * f] = float((out - T).abs().mean())
+        best = min(errs, key=errs.get)
+        row = {"gmi": errs[best], "gmi_sigma": best, "gmi_by_sigma": errs}
+        lowt = torch.as_tensor(low, device=dev).permute(2, 0, 1)[None]
+        for mode in ("nearest", "bilinear", "bicubic"):
+            kw = {} if mode == "nearest" else {"align_corners": False}
+            up = F.interpolate(lowt, size=(side, side), mode=mode, **kw)[0].permute(1, 2, 0).clamp(0.0, 1.0)
+            row[mode] = float((up - T).abs().mean())
+        rows["x%d" % f] = row
+    return {"metric": "mean L1 error vs the full-resolution field (lower is better)", "side": side,
+            "factors": rows, "workload": "smooth random field (32 sinusoids, up to 24 cycles per image, 3 "
+            "channels) point-sampled at block centres; torch resampling with align_corners=False"}
+
+
+def bench_point_optimization(dev, side=256, n=4096, sigma=2.0, iters=200, lr=0.05):
+    """Optimising the point positions by gradient descent (section 3.3) on a
+    synthetic image: n uniformly random points carry the field's colours at
+    their starting positions; Adam moves them to minimise the L1 error of the
+    interpolated image, forward and backward through the autograd op."""
+    import torch
+    import paper_2012_13257_b300 as gmi
+    import workloads as wl
+    rng = np.random.default_rng(8)
+    params = wl.field_params(rng, 3, max_cycles=8.0)
+    yy, xx = np.meshgrid(np.arange(side) + 0.5, np.arange(side) + 0.5, indexing="ij")
+    target = torch.as_tensor(wl.eval_field(params, np.stack([xx.ravel(), yy.ravel()], 1), float(side))
+                             .reshape(side, side, 3), device=dev)
+    p0 = wl.uniform_points(rng, n, side, side)
+    mu = torch.as_tensor(p0, device=dev).clone().requires_grad_(True)
+    vals = torch.as_tensor(wl.eval_field(params, p0, float(side)), device=dev)
+    opt = torch.optim.Adam([mu], lr=lr)
+    losses = []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(iters):
+        opt.zero_grad(set_to_none=True)
+        loss = (gmi.gmi_interpolate(mu, vals, sigma, side, side) - target).abs().mean()
+        loss.backward()
+        opt.step()
+        losses.append(loss.detach())
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    moved = float((mu.detach() - torch.as_tensor(p0, device=dev)).norm(dim=1).mean())
+    return {"loss_start": float(losses[0]), "loss_end": float(losses[-1]), "iters": iters,
+            "iters_per_s": iters / t, "mean_displacement_px": moved, "sigma": sigma, "points": n,
+            "workload": "%dx%dx3 smooth field, %d uniform points, colours fixed at their start, "
+                        "Adam lr %g on positions, L1 loss" % (side, side, n, lr)}
+
+
 def bench_serving(dev, n_requests=10000, rate=2000.0, n_templates=128):
     """Open-loop serving: Poisson arrivals at `rate`, sides log-uniform in
     [64, 2048], N = U[0.1, 1] H W, uniform or clustered, sigma U[0.5, 2];
@@ -506,7 +574,9 @@ def main():
         stream = torch.cuda.current_stream(dev)
         fn = {"batched": lambda: bench_batched(dev, args.steps, args.warmup, flush, stream),
               "fwd_bwd": lambda: bench_fwd_bwd(dev, args.steps, args.warmup, flush, stream),
-              "serving": lambda: bench_serving(dev)}[args.only]
+              "serving": lambda: bench_serving(dev),
+              "reconstruction": lambda: bench_reconstruction(dev),
+              "point_optimization": lambda: bench_point_optimization(dev)}[args.only]
         if rank == 0:
             print(json.dumps({args.only: fn()}), flush=True)
         D.close()
@@ -633,7 +703,9 @@ def main():
     if rank == 0 and not args.no_extras:
         for name, fn in (("batched", lambda: bench_batched(dev, args.steps, args.warmup, flush, stream)),
                          ("fwd_bwd", lambda: bench_fwd_bwd(dev, args.steps, args.warmup, flush, stream)),
-                         ("serving", lambda: bench_serving(dev))):
+                         ("serving", lambda: bench_serving(dev)),
+                         ("reconstruction", lambda: bench_reconstruction(dev)),
+                         ("point_optimization", lambda: bench_point_optimization(dev))):
             try:
                 line[name] = fn()
             except Exception as e:   # a failed extra must not hide the headline

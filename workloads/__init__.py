@@ -33,7 +33,7 @@ import numpy as np
 __all__ = [
     "Image", "uniform_points", "clustered_points", "smooth_field",
     "small_uniform", "upsample_1024", "batched_uneven", "fwd_bwd_512",
-    "fd_subcase", "serving_stream", "tiny_random",
+    "fd_subcase", "serving_stream", "tiny_random", "field_params", "eval_field", "reconstruction_case",
 ]
 
 
@@ -95,27 +95,41 @@ def clustered_points(rng: np.random.Generator, n: int, H: int, W: int,
     return _f32(out)
 
 
-def smooth_field(rng: np.random.Generator, xy: np.ndarray, C: int, period: float,
-                 n_waves: int = 32, std: float = 0.25) -> np.ndarray:
-    """Per channel: 0.5 + sum of n_waves random 2D sinusoids, clipped to [0,1].
-
-    Frequencies are U[-8,8] cycles per ``period`` pixels, phases U[0,2pi),
-    amplitudes U[0,1] rescaled so the (unclipped) field has the given std.
-    """
-    x = xy[:, 0].astype(np.float64)
-    y = xy[:, 1].astype(np.float64)
-    out = np.empty((xy.shape[0], C), dtype=np.float64)
-    for c in range(C):
-        u = rng.uniform(-8, 8, n_waves)
-        v = rng.uniform(-8, 8, n_waves)
+def field_params(rng: np.random.Generator, C: int, n_waves: int = 32, std: float = 0.25,
+                 max_cycles: float = 8.0):
+    """Random sinusoid parameters of a smooth field, per channel (u, v, phi, a):
+    frequencies U[-max_cycles, max_cycles] cycles per period, phases U[0,2pi),
+    amplitudes U[0,1] rescaled so the (unclipped) field has the given std."""
+    params = []
+    for _ in range(C):
+        u = rng.uniform(-max_cycles, max_cycles, n_waves)
+        v = rng.uniform(-max_cycles, max_cycles, n_waves)
         phi = rng.uniform(0, 2 * math.pi, n_waves)
         a = rng.uniform(0, 1, n_waves)
         a *= std / math.sqrt(0.5 * float(np.sum(a * a)))
+        params.append((u, v, phi, a))
+    return params
+
+
+def eval_field(params, xy: np.ndarray, period: float) -> np.ndarray:
+    """Per channel 0.5 + the sum of the sinusoids at positions xy[:, (x, y)],
+    clipped to [0,1], float32 [n, C]."""
+    x = xy[:, 0].astype(np.float64)
+    y = xy[:, 1].astype(np.float64)
+    out = np.empty((xy.shape[0], len(params)), dtype=np.float64)
+    for c, (u, v, phi, a) in enumerate(params):
         f = np.full(x.shape, 0.5)
-        for k in range(n_waves):
+        for k in range(len(a)):
             f += a[k] * np.sin(2 * math.pi * (u[k] * x + v[k] * y) / period + phi[k])
         out[:, c] = f
     return _f32(np.clip(out, 0.0, 1.0))
+
+
+def smooth_field(rng: np.random.Generator, xy: np.ndarray, C: int, period: float,
+                 n_waves: int = 32, std: float = 0.25) -> np.ndarray:
+    """Per channel: 0.5 + sum of n_waves random 2D sinusoids (frequencies
+    U[-8,8] cycles per ``period`` pixels), clipped to [0,1]."""
+    return eval_field(field_params(rng, C, n_waves, std), xy, period)
 
 
 def small_uniform(seed: int = 1) -> Image:
@@ -142,6 +156,25 @@ def upsample_1024(seed: int = 2, src: int = 512, factor: int = 2, C: int = 3,
     pts = _f32(base + jit)
     vals = smooth_field(rng, pts, C, period=float(W))
     return Image(pts, vals, sigma, H, W)
+
+
+def reconstruction_case(factor: int, side: int = 768, C: int = 3, seed: int = 6, max_cycles: float = 24.0):
+    """A smooth random field (up to ``max_cycles`` cycles across the image)
+    seen at full resolution (side x side pixel centres: the truth) and point-
+    sampled at the centres of the factor x factor blocks (the low-resolution
+    image).  Returns (points [n,2] in full-resolution pixel units, values
+    [n,C], low [side/f, side/f, C], truth [side, side, C]); the low-resolution
+    pixel (l, k) sits at ((k + 0.5) f, (l + 0.5) f), which is where
+    align_corners=False resampling places it too."""
+    rng = np.random.default_rng(seed)
+    params = field_params(rng, C, max_cycles=max_cycles)
+    n = side // factor
+    ly, lx = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    pts = _f32(np.stack([(lx.ravel() + 0.5) * factor, (ly.ravel() + 0.5) * factor], 1))
+    vals = eval_field(params, pts, float(side))
+    yy, xx = np.meshgrid(np.arange(side) + 0.5, np.arange(side) + 0.5, indexing="ij")
+    truth = eval_field(params, np.stack([xx.ravel(), yy.ravel()], 1), float(side)).reshape(side, side, C)
+    return pts, vals, vals.reshape(n, n, C), truth
 
 
 def _log_uniform_int(rng, lo, hi, size=None):
