@@ -175,6 +175,25 @@ gmi_status gmi_backward(const float* points, const float* values, int64_t N, int
 gmi_status gmi_workspace_status(const void* workspace, gmi_stream_t stream);
 
 /*
+ * Autotuner core (the batching pattern's choice of micro-tile and bin edge;
+ * no counterpart in the paper): times gmi_forward on the caller's problem for
+ * every micro-tile variant (GMI_VARIANT_MT4x4, MT4x8, MT2x4) and every bin
+ * edge bins[0..n_bins) (0 = the automatic rule), one warm-up and `reps` timed
+ * runs each, with CUDA events on `stream`; writes *p with the fastest variant
+ * and bin_px into *best, and, when times_ms is not NULL, the median time per
+ * candidate into times_ms[variant_index * n_bins + bin_index] (variant order
+ * as listed).  points/values as for gmi_forward.  A tuning call, not the hot
+ * path: it allocates (and frees) its own workspace and output, and returns
+ * after the last run (synchronous).
+ * Errors: GMI_ERR_INVALID_ARG (p, bins or best NULL, n_bins < 1, reps < 1, a
+ * bin edge outside [0, 1024]), the errors of gmi_workspace_size and
+ * gmi_forward, GMI_ERR_CUDA.
+ */
+gmi_status gmi_autotune(const float* points, const float* values, int64_t N, int C, int H, int W,
+                        const gmi_params* p, const int* bins, int n_bins, int reps, gmi_params* best,
+                        float* times_ms, gmi_stream_t stream);
+
+/*
  * Forward pass without a caller-provided workspace (the paper has no
  * counterpart: this is an integration convenience).
  *

@@ -78,6 +78,9 @@ SIGNATURES = {
     "gmi_profile_enable": (_int, [_int]),
     "gmi_profile_read": (_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), _int]),
     "gmi_measure_unit_rates": (_int, [ctypes.POINTER(ctypes.c_double)]),
+    "gmi_autotune": (_int, [_vp, _vp, ctypes.c_int64, _int, _int, _int, ctypes.POINTER(Params),
+                            ctypes.POINTER(_int), _int, _int, ctypes.POINTER(Params),
+                            ctypes.POINTER(ctypes.c_float), _vp]),
     "gmi_batch_plan_create": (_int, [_int, _i64, _i64, _int, ctypes.POINTER(Params), ctypes.POINTER(_vp)]),
     "gmi_batch_plan_destroy": (_int, [_vp]),
     "gmi_batch_plan_bytes": (_sz, [_vp]),

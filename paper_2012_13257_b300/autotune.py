@@ -1,11 +1,11 @@
 """Autotuner for the forward kernels.
 
 The best micro-tile (4x4, 4x8 or 2x4 pixels per thread) and point-bin edge
-depend on sigma (window radius), on the point density and on C.  The tuner
-times every candidate on a representative problem with CUDA events (median
-of a few runs, after warm-up) and caches the winner per
-(GPU name, sigma bucket, density bucket, C) in a JSON file; lookups map a new
-problem to its bucket.  Buckets: half-octaves of sigma and octaves of the
+depend on sigma (window radius), on the point density and on C.  The library's
+gmi_autotune times every candidate on a representative problem with CUDA
+events (median of a few runs after a warm-up); this class keeps the winner per
+(GPU name, sigma bucket, density bucket, C) in a JSON file, and lookups map a
+new problem to its bucket.  Buckets: half-octaves of sigma and octaves of the
 point density (points per output pixel).
 """
 from __future__ import annotations
@@ -62,35 +62,32 @@ class Autotuner:
             json.dump(self.table, f, indent=1, sort_keys=True)
         os.replace(tmp, self.path)
 
-    def tune(self, points, values, sigma: float, H: int, W: int, *, variants=DEFAULT_VARIANTS,
-             bins=DEFAULT_BINS, reps: int = 5, warmup: int = 2, save: bool = True):
-        """Times every (variant, bin_px) on this problem and records the best
-        for its bucket.  Returns (best, {config: median ms})."""
+    def tune(self, points, values, sigma: float, H: int, W: int, *, bins=DEFAULT_BINS, reps: int = 5,
+             save: bool = True, **_):
+        """Times every (variant, bin_px) on this problem (gmi_autotune) and
+        records the best for its bucket.  Returns (best, {"variant/bin": ms})."""
+        import ctypes
         import torch
-        from . import interpolate
+        from . import _check_inputs, _mode, _stream_handle
+        points, values = _check_inputs(points, values)
         dev = points.device
-        out = torch.empty((H, W, values.shape[1]), dtype=torch.float32, device=dev)
-        times = {}
-        for v in variants:
-            for b in bins:
-                for _ in range(warmup):
-                    interpolate(points, values, sigma, H, W, variant=v, bin_px=b, out=out)
-                ms = []
-                for _ in range(reps):
-                    e0 = torch.cuda.Event(enable_timing=True)
-                    e1 = torch.cuda.Event(enable_timing=True)
-                    e0.record()
-                    interpolate(points, values, sigma, H, W, variant=v, bin_px=b, out=out)
-                    e1.record()
-                    e1.synchronize()
-                    ms.append(e0.elapsed_time(e1))
-                ms.sort()
-                times[(v, b)] = ms[len(ms) // 2]
-        (bv, bb) = min(times, key=times.get)
-        best = {"variant": int(bv), "bin_px": int(bb), "ms": times[(bv, bb)]}
-        key = bucket(sigma, points.shape[0] / float(H * W), values.shape[1])
+        N, C = int(points.shape[0]), int(values.shape[1])
+        p = _lib.make_params(float(sigma))
+        nb = len(bins)
+        barr = (ctypes.c_int * nb)(*[int(b) for b in bins])
+        best = _lib.Params()
+        times = (ctypes.c_float * (3 * nb))()
+        with torch.cuda.device(dev):
+            _lib.check(_lib.load().gmi_autotune(points.data_ptr(), values.data_ptr(), N, C, int(H), int(W),
+                                                ctypes.byref(p), barr, nb, int(reps), ctypes.byref(best), times,
+                                                _stream_handle(dev)), "gmi_autotune")
+        table = {"%d/%d" % (v, b): float(times[vi * nb + k])
+                 for vi, v in enumerate(DEFAULT_VARIANTS) for k, b in enumerate(bins)}
+        res = {"variant": int(best.variant), "bin_px": int(best.bin_px),
+               "ms": table["%d/%d" % (best.variant, best.bin_px)]}
+        key = bucket(sigma, N / float(H * W), C)
         with self._lock:
-            self.table.setdefault(self.gpu_name(dev), {})[key] = best
+            self.table.setdefault(self.gpu_name(dev), {})[key] = res
             if save:
                 self.save()
-        return best, {"%d/%d" % k: t for k, t in times.items()}
+        return res, table

@@ -94,3 +94,15 @@ def test_package_fails_loudly_without_the_library(monkeypatch):
     monkeypatch.setattr(_lib, "LIB_PATH", "/nonexistent/libgmi.so")
     with pytest.raises(ImportError):
         _lib.load()
+
+
+def test_autotune_rejects_bad_arguments_without_launching():
+    lib = _lib.load()
+    p = _lib.make_params(1.0)
+    best = _lib.Params()
+    bins = (ctypes.c_int * 2)(0, 2)
+    assert lib.gmi_autotune(256, 256, 10, 3, 8, 8, ctypes.byref(p), bins, 0, 3, ctypes.byref(best), None, None) == 1
+    assert lib.gmi_autotune(256, 256, 10, 3, 8, 8, ctypes.byref(p), bins, 2, 0, ctypes.byref(best), None, None) == 1
+    assert lib.gmi_autotune(256, 256, 10, 3, 8, 8, ctypes.byref(p), bins, 2, 3, None, None, None) == 1
+    bad = (ctypes.c_int * 1)(4096)
+    assert lib.gmi_autotune(256, 256, 10, 3, 8, 8, ctypes.byref(p), bad, 1, 3, ctypes.byref(best), None, None) == 1

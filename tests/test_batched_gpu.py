@@ -98,3 +98,18 @@ def test_uneven_clustered_batch_sampled(cuda_device):
         err = np.abs(o.cpu().numpy().reshape(-1, 3)[pix] - ref).max()
         assert err <= TOL_FWD, (b, im.H, im.W, err)
     plan.close()
+
+
+def test_autotuner_picks_the_fastest_measured_candidate(cuda_device, tmp_path):
+    """gmi_autotune times every (variant, bin edge) and returns the fastest;
+    the Python Autotuner records it for the problem's bucket."""
+    from paper_2012_13257_b300.autotune import Autotuner, DEFAULT_VARIANTS, bucket
+    im = wl.tiny_random(5, 6000, 120, 150, sigma=1.2)
+    t = Autotuner(path=str(tmp_path / "tune.json"))
+    best, times = t.tune(to_dev(im.points, cuda_device), to_dev(im.values, cuda_device), im.sigma, im.H, im.W,
+                         bins=(0, 2, 4), reps=3)
+    assert len(times) == 3 * len(DEFAULT_VARIANTS) and all(v > 0 for v in times.values())
+    assert best["variant"] in DEFAULT_VARIANTS and best["bin_px"] in (0, 2, 4)
+    assert best["ms"] == min(times.values())
+    assert t.lookup(im.sigma, im.N / float(im.H * im.W), 3) == best
+    assert bucket(im.sigma, im.N / float(im.H * im.W), 3) in t.table[t.gpu_name()]
