@@ -301,8 +301,10 @@ size_t gmi_batch_plan_bytes(const gmi_batch_plan* plan);
  * pipeline on `stream`: one segmented binning pass, then one persistent
  * gather over the work queue of all images' tiles.  With use_graph != 0 the
  * kernel sequence is captured into a CUDA graph on the first call and
- * replayed afterwards.  Waits (host side) only for the previous call's
- * descriptor upload.  Errors: GMI_ERR_INVALID_ARG, GMI_ERR_CAPACITY,
+ * replayed afterwards.  Two staging slots alternate: a call waits (host
+ * side) only for the forward two calls back, whose slot it reuses.  The calls
+ * on one plan share its workspace and must be ordered on one stream.
+ * Errors: GMI_ERR_INVALID_ARG, GMI_ERR_CAPACITY,
  * GMI_ERR_CUDA; with GMI_FLAG_SYNC_CHECK in the plan's params, also the
  * device status.
  */
@@ -330,10 +332,13 @@ typedef struct {
  * Backward pass of B images (descs is a host array) in one batched pipeline
  * on `stream`: one segmented re-binning, then the per-pixel preparation, the
  * point-centric gradient kernel and the fallback kernel over all images at
- * once (gradients as in gmi_backward).  Uses the plan's workspace: a plan
- * serves one forward or backward call at a time.  The sigma gradients are
- * accumulated with float atomics, so their last bits may differ between
- * runs.  Errors: GMI_ERR_INVALID_ARG, GMI_ERR_CAPACITY, GMI_ERR_CUDA.
+ * once (gradients as in gmi_backward).  Uses the plan's workspace, so the
+ * calls on one plan (forward and backward) must be ordered on one stream; a
+ * call returns once its descriptor tables are staged (two pinned staging
+ * buffers alternate, so the host may prepare the next call while the previous
+ * one runs).  The sigma gradients are accumulated with float atomics, so
+ * their last bits may differ between runs.
+ * Errors: GMI_ERR_INVALID_ARG, GMI_ERR_CAPACITY, GMI_ERR_CUDA.
  */
 gmi_status gmi_backward_batched(gmi_batch_plan* plan, const gmi_grad_desc* descs, int B,
                                 gmi_stream_t stream);

@@ -1,8 +1,9 @@
 // Host side of the libgmi C ABI: argument checks, workspace layout, and the
 // launch sequence of the single-image forward pass
 //   memset(status, bin counts) -> bin_count -> scan_partial -> scan_final
-//   -> bin_scatter -> near_plan -> near gather -> far gather
-// All kernels run on the caller's stream; nothing here allocates memory.
+//   -> scatter + plan (one launch) -> near gather -> far gather
+// (replayed as one cached CUDA graph with GMI_FLAG_GRAPH).  All kernels run
+// on the caller's stream; nothing here allocates device memory.
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
