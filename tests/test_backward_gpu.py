@@ -247,3 +247,29 @@ def test_sigma_tensors_are_read_per_tensor(cuda_device):
     S.fill_(1.6)
     assert torch.allclose(g.gmi_interpolate(P, V, S, 40, 44), g.interpolate(P, V, float(np.float32(1.6)), 40, 44),
                           rtol=0, atol=2e-6)
+
+
+@pytest.mark.parametrize("C", [1, 4])
+def test_batched_backward_other_channel_counts(cuda_device, C):
+    """The batched backward for one and four channels (the four-channel
+    planes take two float4 per pixel) against the oracle."""
+    import torch
+    G = gmi()
+    rng = np.random.default_rng(300 + C)
+    imgs, ups = [], []
+    for b in range(4):
+        H, W = int(rng.integers(12, 36)), int(rng.integers(12, 36))
+        imgs.append(wl.tiny_random(800 + 10 * C + b, int(rng.integers(20, 250)), H, W, C=C,
+                                   sigma=float(rng.uniform(0.6, 1.6)), clustered=bool(b % 2)))
+        ups.append(rng.standard_normal((H, W, C)).astype(np.float32))
+    plan = G.BatchPlan(8, 2000, 8000, C)
+    P = [to_dev(im.points, cuda_device).requires_grad_(True) for im in imgs]
+    V = [to_dev(im.values, cuda_device).requires_grad_(True) for im in imgs]
+    S = [torch.tensor(im.sigma, dtype=torch.float32, device=cuda_device, requires_grad=True) for im in imgs]
+    outs = G.gmi_interpolate_batch(plan, P, V, S, [(im.H, im.W) for im in imgs])
+    sum((o * to_dev(u, cuda_device)).sum() for o, u in zip(outs, ups)).backward()
+    torch.cuda.synchronize()
+    for b, im in enumerate(imgs):
+        ref = oracle.backward(im.points, im.values, im.H, im.W, im.sigma, ups[b])
+        assert_grads((P[b].grad.cpu().numpy(), V[b].grad.cpu().numpy(), float(S[b].grad)), ref)
+    plan.close()

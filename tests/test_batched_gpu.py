@@ -113,3 +113,29 @@ def test_autotuner_picks_the_fastest_measured_candidate(cuda_device, tmp_path):
     assert best["ms"] == min(times.values())
     assert t.lookup(im.sigma, im.N / float(im.H * im.W), 3) == best
     assert bucket(im.sigma, im.N / float(im.H * im.W), 3) in t.table[t.gpu_name()]
+
+
+@pytest.mark.parametrize("C,mode,variant", [(1, "exact", 1), (2, "exact", 3), (4, "exact", 2),
+                                            (3, "truncated", 1), (4, "truncated", 3)])
+def test_batch_channels_modes_variants(cuda_device, C, mode, variant):
+    """Batched forward (graph replay) for other channel counts, the truncated
+    reading and the other micro-tiles, image by image against the oracle."""
+    import torch
+    G = gmi()
+    rng = np.random.default_rng(40 + C + variant)
+    imgs = []
+    for b in range(6):
+        H, W = int(rng.integers(9, 70)), int(rng.integers(9, 70))
+        imgs.append(wl.tiny_random(4000 + 10 * C + variant + b, int(rng.integers(1, 300)), H, W, C=C,
+                                   sigma=float(rng.uniform(0.5, 1.8)), clustered=bool(b % 2)))
+    plan = G.BatchPlan(8, 3000, 40000, C, mode=mode, variant=variant)
+    outs = plan.forward(dev_images(imgs, cuda_device), use_graph=True)
+    torch.cuda.synchronize()
+    om = oracle.TRUNCATED if mode == "truncated" else oracle.EXACT
+    for im, o in zip(imgs, outs):
+        ref = oracle.forward(im.points, im.values, im.H, im.W, im.sigma, mode=om)
+        err = np.abs(o.cpu().numpy().astype(np.float64) - ref["image"])
+        if mode == "truncated":
+            err = err[ref["skipped"] < 1e-3]   # pixels not decided by a point on the radius
+        assert err.max() <= TOL_FWD, (C, mode, variant, im.H, im.W, im.N)
+    plan.close()
