@@ -58,6 +58,14 @@ def _load():
                                             ctypes.c_int64, ctypes.c_int64, ctypes.c_double,
                                             ctypes.c_int, ctypes.c_double, f32p, f64p, f64p, f64p]
             lib.oracle_backward.restype = ctypes.c_int
+            lib.oracle_forward_pp.argtypes = [f32p, f32p, f32p, ctypes.c_int64, ctypes.c_int,
+                                              ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_double,
+                                              i64p, ctypes.c_int64, f64p, f64p, f64p, f64p, i64p]
+            lib.oracle_forward_pp.restype = ctypes.c_int
+            lib.oracle_backward_pp.argtypes = [f32p, f32p, f32p, ctypes.c_int64, ctypes.c_int,
+                                               ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_double,
+                                               f32p, f64p, f64p, f64p]
+            lib.oracle_backward_pp.restype = ctypes.c_int
             lib.oracle_num_threads.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -137,3 +145,58 @@ def backward(points, values, H: int, W: int, sigma: float, grad, mode: int = EXA
     if rc != 0:
         raise ValueError("oracle_backward rejected its arguments (rc=%d)" % rc)
     return {"points": gp, "values": gv, "sigma": float(gs[0])}
+
+
+def forward_pp(points, values, sigmas, H: int, W: int, mode: int = EXACT, k: float = 6.0, pixels=None):
+    """Eq. 1 / Eq. 2 with a sigma per point (normalisers kept; see
+    ``oracle_forward_pp``).  Same outputs as ``forward``; ``shift`` is the
+    largest log-weight at the pixel in exact mode."""
+    lib = _load()
+    pts = _f32(points).reshape(-1, 2)
+    N = pts.shape[0]
+    vals = _f32(values).reshape(N, -1) if N else _f32(values).reshape(0, np.asarray(values).shape[-1])
+    C = int(vals.shape[1])
+    sig = _f32(sigmas).reshape(N)
+    if pixels is None:
+        n = H * W
+        pix = None
+    else:
+        pix = np.ascontiguousarray(np.asarray(pixels, dtype=np.int64).ravel())
+        n = pix.size
+    out = np.empty((n, C), np.float64)
+    den = np.empty(n, np.float64)
+    shift = np.empty(n, np.float64)
+    skipped = np.empty(n, np.float64)
+    pairs = np.empty(n, np.int64)
+    rc = lib.oracle_forward_pp(_ptr(pts, ctypes.c_float), _ptr(vals, ctypes.c_float), _ptr(sig, ctypes.c_float),
+                               N, C, H, W, int(mode), float(k), _ptr(pix, ctypes.c_int64), n,
+                               _ptr(out, ctypes.c_double), _ptr(den, ctypes.c_double),
+                               _ptr(shift, ctypes.c_double), _ptr(skipped, ctypes.c_double),
+                               _ptr(pairs, ctypes.c_int64))
+    if rc != 0:
+        raise ValueError("oracle_forward_pp rejected its arguments (rc=%d)" % rc)
+    if pixels is None:
+        out, den, shift = out.reshape(H, W, C), den.reshape(H, W), shift.reshape(H, W)
+        skipped, pairs = skipped.reshape(H, W), pairs.reshape(H, W)
+    return {"image": out, "den": den, "shift": shift, "skipped": skipped, "pairs": pairs}
+
+
+def backward_pp(points, values, sigmas, H: int, W: int, grad, mode: int = EXACT, k: float = 6.0):
+    """Analytic gradient of sum(grad * image) w.r.t. points, values and the
+    per-point sigmas."""
+    lib = _load()
+    pts = _f32(points).reshape(-1, 2)
+    N = pts.shape[0]
+    vals = _f32(values).reshape(N, -1)
+    C = vals.shape[1]
+    sig = _f32(sigmas).reshape(N)
+    g = _f32(grad).reshape(H, W, C)
+    gp = np.zeros((N, 2), np.float64)
+    gv = np.zeros((N, C), np.float64)
+    gs = np.zeros(N, np.float64)
+    rc = lib.oracle_backward_pp(_ptr(pts, ctypes.c_float), _ptr(vals, ctypes.c_float), _ptr(sig, ctypes.c_float),
+                                N, C, H, W, int(mode), float(k), _ptr(g, ctypes.c_float),
+                                _ptr(gp, ctypes.c_double), _ptr(gv, ctypes.c_double), _ptr(gs, ctypes.c_double))
+    if rc != 0:
+        raise ValueError("oracle_backward_pp rejected its arguments (rc=%d)" % rc)
+    return {"points": gp, "values": gv, "sigmas": gs}

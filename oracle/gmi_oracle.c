@@ -252,3 +252,181 @@ int oracle_backward(const float* points, const float* values, int64_t N, int C,
     free(wbuf_all);
     return 0;
 }
+
+/*
+ * Per-point sigma: an extension the paper does not make (its section 2
+ * fixes one sigma for all points).  Point i is the normal N(mu_i,
+ * sigma_i^2 I), and its normaliser 1/(2 pi sigma_i^2) no longer cancels in
+ * Eq. 1; with the common 1/(2 pi) cancelled,
+ *     w_i(q) = exp(-d_i^2 / (2 sigma_i^2)) / sigma_i^2,
+ *     c(q)   = sum_i w_i c_i / sum_i w_i .
+ * EXACT: all points, evaluated relative to the largest weight at q:
+ *   w_i / w_max = exp(ln w_i - L), L = max_i ln w_i (no underflow);
+ *   den = sum_i w_i / w_max (>= 1), shift = L.
+ * TRUNCATED: only points with d_i <= k sigma_i, weights unshifted;
+ *   den = sum of those w_i, shift 0; skipped = share of the in-disc weight
+ *   carried by points within rounding of their radius
+ *   (|d_i^2 - k^2 sigma_i^2| <= 1e-5 k^2 sigma_i^2); pairs counts the points
+ *   inside their radius.
+ * sigmas [N] float32, each > 0.  Returns 0, or -1 on invalid arguments.
+ */
+static double log_weight_pp(double d2, double s) { return -d2 / (2.0 * s * s) - 2.0 * log(s); }
+
+int oracle_forward_pp(const float* points, const float* values, const float* sigmas, int64_t N, int C,
+                      int64_t H, int64_t W, int mode, double k, const int64_t* pix, int64_t n_pix,
+                      double* out, double* den, double* shift, double* skipped, int64_t* pairs) {
+    if (N < 0 || C < 1 || H < 1 || W < 1 || !(k > 0) || (N > 0 && !sigmas)) return -1;
+    if (mode != ORACLE_EXACT && mode != ORACLE_TRUNCATED) return -1;
+    for (int64_t i = 0; i < N; ++i)
+        if (!((double)sigmas[i] > 0)) return -1;
+    if (pix == NULL) n_pix = H * W;
+
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t t = 0; t < n_pix; ++t) {
+        int64_t p = pix ? pix[t] : t;
+        double qx, qy;
+        pixel_centre(p, W, &qx, &qy);
+        double num[8];
+        double* acc = C <= 8 ? num : (double*)calloc((size_t)C, sizeof(double));
+        for (int c = 0; c < C; ++c) acc[c] = 0.0;
+        double z = 0.0, L = 0.0, skip = 0.0;
+        int64_t cnt = 0;
+        if (N > 0 && mode == ORACLE_EXACT) {
+            L = -INFINITY;
+            for (int64_t i = 0; i < N; ++i) {
+                double lw = log_weight_pp(sqdist(points, i, qx, qy), (double)sigmas[i]);
+                if (lw > L) L = lw;
+            }
+            for (int64_t i = 0; i < N; ++i) {
+                double w = exp(log_weight_pp(sqdist(points, i, qx, qy), (double)sigmas[i]) - L);
+                z += w;
+                ++cnt;
+                for (int c = 0; c < C; ++c) acc[c] += w * (double)values[i * C + c];
+            }
+            for (int c = 0; c < C; ++c) acc[c] /= z;
+        } else if (N > 0) {
+            double amb = 0.0;
+            for (int64_t i = 0; i < N; ++i) {
+                double s = (double)sigmas[i];
+                double d2 = sqdist(points, i, qx, qy);
+                double r2 = k * k * s * s;
+                if (fabs(d2 - r2) <= 1e-5 * r2) amb += exp(log_weight_pp(d2, s));
+                if (d2 > r2) continue;
+                double w = exp(log_weight_pp(d2, s));
+                z += w;
+                ++cnt;
+                for (int c = 0; c < C; ++c) acc[c] += w * (double)values[i * C + c];
+            }
+            if (z > 0) {
+                for (int c = 0; c < C; ++c) acc[c] /= z;
+                skip = amb / z;
+            } else {
+                for (int c = 0; c < C; ++c) acc[c] = 0.0;
+                skip = amb > 0 ? 1.0 : 0.0;
+            }
+        }
+        if (out)
+            for (int c = 0; c < C; ++c) out[t * C + c] = acc[c];
+        if (den) den[t] = z;
+        if (shift) shift[t] = L;
+        if (skipped) skipped[t] = skip;
+        if (pairs) pairs[t] = cnt;
+        if (acc != num) free(acc);
+    }
+    return 0;
+}
+
+/*
+ * Backward pass with per-point sigma: gradients of L = sum_q sum_c g_c(q)
+ * c_c(q) with respect to the positions, values and per-point sigmas.  With
+ * t_i(q) = sum_c (g_c(q) / Z_q) (c_{i,c} - c_c(q)) and the chain rule on
+ * the per-point Eq. 1 (d ln w_i / d mu_i = (q - mu_i) / sigma_i^2,
+ * d ln w_i / d sigma_i = d_i^2 / sigma_i^3 - 2 / sigma_i):
+ *     dL/dc_{i,c}   = sum_q (w_i / Z_q) g_c(q)
+ *     dL/dmu_i      = sum_q (w_i / Z_q) t_i(q) (q - mu_i) / sigma_i^2
+ *     dL/dsigma_i   = sum_q (w_i / Z_q) t_i(q) (d_i^2 / sigma_i^3 - 2 / sigma_i)
+ * Outputs (each may be NULL): gpoints [N,2], gvalues [N,C], gsigmas [N].
+ */
+int oracle_backward_pp(const float* points, const float* values, const float* sigmas, int64_t N, int C,
+                       int64_t H, int64_t W, int mode, double k, const float* grad, double* gpoints,
+                       double* gvalues, double* gsigmas) {
+    if (N < 0 || C < 1 || C > 8 || H < 1 || W < 1 || !(k > 0) || (N > 0 && !sigmas)) return -1;
+    if (mode != ORACLE_EXACT && mode != ORACLE_TRUNCATED) return -1;
+    for (int64_t i = 0; i < N; ++i)
+        if (!((double)sigmas[i] > 0)) return -1;
+    const int64_t P = H * W;
+    int nt = oracle_num_threads();
+    size_t per = (size_t)N * (size_t)(3 + C) + 1;
+    double* part = (double*)calloc(per * (size_t)nt, sizeof(double));
+    double* wbuf_all = (double*)malloc(sizeof(double) * (size_t)(N > 0 ? N : 1) * (size_t)nt);
+    if (!part || !wbuf_all) { free(part); free(wbuf_all); return -2; }
+
+#pragma omp parallel
+    {
+        int tid = 0;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+#endif
+        double* acc = part + per * (size_t)tid;   /* [N*2 | N*C | N] */
+        double* w = wbuf_all + (size_t)(N > 0 ? N : 1) * (size_t)tid;
+        double chat[8], G[8];
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t p = 0; p < P; ++p) {
+            if (N == 0) continue;
+            int any = 0;
+            for (int c = 0; c < C; ++c) any |= grad[p * C + c] != 0.0f;
+            if (!any) continue;
+            double qx, qy;
+            pixel_centre(p, W, &qx, &qy);
+            double L = 0.0;
+            if (mode == ORACLE_EXACT) {
+                L = -INFINITY;
+                for (int64_t i = 0; i < N; ++i) {
+                    double lw = log_weight_pp(sqdist(points, i, qx, qy), (double)sigmas[i]);
+                    if (lw > L) L = lw;
+                }
+            }
+            double z = 0.0;
+            for (int c = 0; c < C; ++c) chat[c] = 0.0;
+            for (int64_t i = 0; i < N; ++i) {
+                double s = (double)sigmas[i];
+                double d2 = sqdist(points, i, qx, qy);
+                double wi = (mode == ORACLE_TRUNCATED && d2 > k * k * s * s) ? 0.0 : exp(log_weight_pp(d2, s) - L);
+                w[i] = wi;
+                z += wi;
+                for (int c = 0; c < C; ++c) chat[c] += wi * (double)values[i * C + c];
+            }
+            if (!(z > 0)) continue;
+            for (int c = 0; c < C; ++c) {
+                chat[c] /= z;
+                G[c] = (double)grad[p * C + c] / z;
+            }
+            for (int64_t i = 0; i < N; ++i) {
+                if (w[i] == 0.0) continue;
+                double s = (double)sigmas[i];
+                double t = 0.0;
+                for (int c = 0; c < C; ++c) {
+                    acc[2 * N + i * C + c] += w[i] * G[c];
+                    t += G[c] * ((double)values[i * C + c] - chat[c]);
+                }
+                double dx = qx - (double)points[2 * i];
+                double dy = qy - (double)points[2 * i + 1];
+                double wt = w[i] * t;
+                acc[2 * i] += wt * dx / (s * s);
+                acc[2 * i + 1] += wt * dy / (s * s);
+                acc[(size_t)N * (2 + C) + i] += wt * ((dx * dx + dy * dy) / (s * s * s) - 2.0 / s);
+            }
+        }
+    }
+    for (size_t e = 0; e < per; ++e) {
+        double s = 0.0;
+        for (int t = 0; t < nt; ++t) s += part[per * (size_t)t + e];
+        part[e] = s;
+    }
+    if (gpoints) memcpy(gpoints, part, sizeof(double) * (size_t)N * 2);
+    if (gvalues) memcpy(gvalues, part + 2 * N, sizeof(double) * (size_t)N * (size_t)C);
+    if (gsigmas) memcpy(gsigmas, part + (size_t)N * (2 + C), sizeof(double) * (size_t)N);
+    free(part);
+    free(wbuf_all);
+    return 0;
+}

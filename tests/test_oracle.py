@@ -297,3 +297,116 @@ def test_value_gradient_sums_to_upstream_sum():
     fd = (_loss(im.points + sh, im.values, im.H, im.W, im.sigma, g)
           - _loss(im.points - sh, im.values, im.H, im.W, im.sigma, g)) / (2 * h)
     assert abs(fd - gr["points"][:, 0].sum()) <= 2e-4 * max(1.0, abs(fd))
+
+
+# ------------------------------------------------------ per-point sigma (extension)
+def _pp_case(seed, n, H, W, C=3, lo=0.5, hi=2.0):
+    rng = np.random.default_rng(seed)
+    pts = np.stack([rng.uniform(0, W, n), rng.uniform(0, H, n)], 1).astype(np.float32)
+    vals = rng.uniform(0, 1, (n, C)).astype(np.float32)
+    sig = rng.uniform(lo, hi, n).astype(np.float32)
+    return pts, vals, sig
+
+
+@pytest.mark.parametrize("mode", [oracle.EXACT, oracle.TRUNCATED])
+def test_pp_equal_sigmas_reduce_to_the_shared_oracle(mode):
+    """With every sigma_i = sigma the normalisers are equal and cancel: the
+    per-point evaluation is the (pinned) shared-sigma one, and the per-point
+    sigma gradients sum to the shared sigma gradient (the -2/sigma terms
+    cancel over the normalised weights)."""
+    pts, vals, _ = _pp_case(1, 40, 13, 17)
+    s = np.float32(1.3)
+    sig = np.full(40, s, np.float32)
+    k = 6.0 if mode == oracle.EXACT else 2.5
+    a = oracle.forward_pp(pts, vals, sig, 13, 17, mode=mode, k=k)
+    b = oracle.forward(pts, vals, 13, 17, float(s), mode=mode, k=k)
+    np.testing.assert_allclose(a["image"], b["image"], rtol=0, atol=1e-13)
+    g = np.random.default_rng(2).standard_normal((13, 17, 3)).astype(np.float32)
+    ga = oracle.backward_pp(pts, vals, sig, 13, 17, g, mode=mode, k=k)
+    gb = oracle.backward(pts, vals, 13, 17, float(s), g, mode=mode, k=k)
+    np.testing.assert_allclose(ga["points"], gb["points"], rtol=1e-10, atol=1e-12)
+    np.testing.assert_allclose(ga["values"], gb["values"], rtol=1e-10, atol=1e-12)
+    assert math.isclose(ga["sigmas"].sum(), gb["sigma"], rel_tol=1e-9, abs_tol=1e-11)
+
+
+def test_pp_single_and_two_points():
+    H, W = 9, 11
+    xx, yy = _grid(H, W)
+    p1 = np.float32([[3.3, 4.6]])
+    c1 = np.float32([[0.2, 0.7, 0.9]])
+    r = oracle.forward_pp(p1, c1, np.float32([0.8]), H, W)
+    np.testing.assert_allclose(r["image"], np.broadcast_to(c1[0], (H, W, 3)), rtol=0, atol=1e-15)
+    rt = oracle.forward_pp(p1, c1, np.float32([0.8]), H, W, mode=oracle.TRUNCATED, k=2.0)
+    inside = (xx - float(p1[0, 0])) ** 2 + (yy - float(p1[0, 1])) ** 2 <= (2.0 * float(np.float32(0.8))) ** 2
+    np.testing.assert_allclose(rt["image"][inside], np.broadcast_to(c1[0], (inside.sum(), 3)), atol=1e-15)
+    assert (rt["image"][~inside] == 0).all()
+    # two points with sigmas s1, s2: a logistic sigmoid of the log-weight difference
+    p2 = np.float32([[2.1, 3.0], [7.4, 5.5]])
+    c2 = np.float32([[1.0, 0.0, 0.0], [0.0, 1.0, 0.0]])
+    s2 = np.float32([0.9, 1.7])
+    r2 = oracle.forward_pp(p2, c2, s2, H, W)
+    p64 = p2.astype(np.float64)   # the oracle sees the float32 positions
+    d1 = (xx - p64[0, 0]) ** 2 + (yy - p64[0, 1]) ** 2
+    d2 = (xx - p64[1, 0]) ** 2 + (yy - p64[1, 1]) ** 2
+    l1 = -d1 / (2 * float(s2[0]) ** 2) - 2 * math.log(float(s2[0]))
+    l2 = -d2 / (2 * float(s2[1]) ** 2) - 2 * math.log(float(s2[1]))
+    np.testing.assert_allclose(r2["image"][..., 1], expit(l2 - l1), rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("mode", [oracle.EXACT, oracle.TRUNCATED])
+def test_pp_torch_autograd(mode):
+    """An independent FP64 torch evaluation of the per-point Eq. 1 (a softmax
+    of the log-weights in exact mode, masked weights in truncated mode) and
+    its autograd gradients, including each point's sigma."""
+    torch = pytest.importorskip("torch")
+    H, W, k = 14, 12, 2.5
+    pts, vals, sig = _pp_case(7, 30, H, W)
+    g = np.random.default_rng(8).standard_normal((H, W, 3)).astype(np.float32)
+    P = torch.tensor(pts, dtype=torch.float64, requires_grad=True)
+    V = torch.tensor(vals, dtype=torch.float64, requires_grad=True)
+    S = torch.tensor(sig, dtype=torch.float64, requires_grad=True)
+    yy, xx = torch.meshgrid(torch.arange(H, dtype=torch.float64) + 0.5,
+                            torch.arange(W, dtype=torch.float64) + 0.5, indexing="ij")
+    q = torch.stack([xx.reshape(-1), yy.reshape(-1)], 1)
+    d2 = ((q[:, None, :] - P[None]) ** 2).sum(-1)
+    logw = -d2 / (2 * S * S) - 2 * torch.log(S)
+    if mode == oracle.EXACT:
+        wgt = torch.softmax(logw, dim=1)
+    else:
+        w = torch.where(d2 <= (k * S) ** 2, torch.exp(logw), torch.zeros_like(d2))
+        z = w.sum(1, keepdim=True)
+        wgt = torch.where(z > 0, w / torch.where(z > 0, z, torch.ones_like(z)), torch.zeros_like(w))
+    img = (wgt @ V).reshape(H, W, 3)
+    (img * torch.tensor(g, dtype=torch.float64)).sum().backward()
+    ref = oracle.forward_pp(pts, vals, sig, H, W, mode=mode, k=k)
+    np.testing.assert_allclose(ref["image"], img.detach().numpy(), rtol=0, atol=1e-12)
+    gr = oracle.backward_pp(pts, vals, sig, H, W, g, mode=mode, k=k)
+    np.testing.assert_allclose(gr["points"], P.grad.numpy(), rtol=1e-8, atol=1e-10)
+    np.testing.assert_allclose(gr["values"], V.grad.numpy(), rtol=1e-8, atol=1e-10)
+    np.testing.assert_allclose(gr["sigmas"], S.grad.numpy(), rtol=1e-8, atol=1e-10)
+
+
+def test_pp_sigma_gradient_finite_differences():
+    H, W = 10, 12
+    pts, vals, sig = _pp_case(11, 16, H, W)
+    g = np.random.default_rng(12).standard_normal((H, W, 3)).astype(np.float32)
+
+    def loss(s):
+        return float((oracle.forward_pp(pts, vals, s, H, W)["image"] * g).sum())
+
+    gr = oracle.backward_pp(pts, vals, sig, H, W, g)
+    h = 2.0 ** -10
+    for i in (0, 5, 11):
+        sp, sm = sig.copy(), sig.copy()
+        sp[i] += h
+        sm[i] -= h
+        fd = (loss(sp) - loss(sm)) / (float(sp[i]) - float(sm[i]))
+        assert abs(fd - gr["sigmas"][i]) <= 1e-4 * max(1.0, abs(fd)), (i, fd, gr["sigmas"][i])
+
+
+def test_pp_permutation_invariance():
+    pts, vals, sig = _pp_case(13, 25, 8, 9)
+    perm = np.random.default_rng(14).permutation(25)
+    a = oracle.forward_pp(pts, vals, sig, 8, 9)["image"]
+    b = oracle.forward_pp(pts[perm], vals[perm], sig[perm], 8, 9)["image"]
+    np.testing.assert_allclose(a, b, rtol=0, atol=1e-14)
