@@ -75,9 +75,10 @@ typedef enum { GMI_MODE_EXACT = 0, GMI_MODE_TRUNCATED = 1 } gmi_mode;
 
 /* params->flags */
 #define GMI_FLAG_SYNC_CHECK 0x1u   /* synchronise and return the device status */
-/* gmi_forward only: run the launch sequence as a cached CUDA graph.  The first
- * call with a given device, set of pointers (points, values, image, den_out,
- * shift_out, workspace), sizes (N, C, H, W, ws_bytes) and params captures it;
+/* gmi_forward and gmi_forward_pp only: run the launch sequence as a cached
+ * CUDA graph.  The first call with a given device, set of pointers (points,
+ * values, sigmas, image, den_out, shift_out, workspace), sizes (N, C, H, W,
+ * ws_bytes) and params captures it;
  * later calls with the same ones replay it (one host launch, shorter gaps
  * between the kernels on the device).  The kernels read the buffers when they
  * run, so replay is correct whatever they hold.  Up to 32 graphs are kept per
@@ -166,6 +167,56 @@ gmi_status gmi_backward(const float* points, const float* values, int64_t N, int
                         const float* den, const float* shift, const float* grad_image,
                         float* grad_points, float* grad_values, float* grad_sigma,
                         void* workspace, size_t ws_bytes, gmi_stream_t stream);
+
+/*
+ * Forward pass with a sigma per point: Eq. 2's normal of point i becomes
+ * N(mu_i, sigmas[i]^2 I), so its normaliser 1/(2 pi sigma_i^2) no longer
+ * cancels in Eq. 1 and is kept.  An extension: section 2 gives every point
+ * one fixed sigma, and the point-optimisation experiment (section 3, Fig. 4)
+ * finds the choice of sigma to matter more than the point positions; with
+ * gmi_backward_pp a sigma per point can be fitted by gradient descent.
+ * Truncated mode only: point i counts at pixel q when |q - mu_i| <= k
+ * sigma_i (k = radius_sigmas).
+ *   sigmas   device [N] float32, 4-byte aligned; each finite and in
+ *            [p->sigma * 2^-32, p->sigma]
+ *   p        p->mode must be GMI_MODE_TRUNCATED; p->sigma is an upper bound
+ *            on every sigmas[i] (it sets the search radius k * p->sigma, so
+ *            a tight bound is faster) and the reference scale of den_out
+ *   den_out  device [H,W] float32 or NULL: sum_i (sigma/sigma_i)^2
+ *            exp(-d_i^2 / (2 sigma_i^2)) over the points that count
+ *            (sigma = p->sigma; with every sigma_i = sigma it is
+ *            gmi_forward's den); no shift plane (truncated mode never shifts)
+ *   points, values, image, workspace (gmi_workspace_size with the same N,
+ *   C, H, W and params), GMI_FLAG_GRAPH: as gmi_forward
+ * Errors: as gmi_forward, plus GMI_ERR_UNSUPPORTED (exact mode) and
+ * GMI_ERR_INVALID_ARG (sigmas NULL or misaligned with N > 0; with
+ * GMI_FLAG_SYNC_CHECK also a sigma outside its range, found on the device,
+ * and GMI_ERR_NONFINITE for a NaN/Inf sigma).  Out-of-range sigmas without
+ * the check give a wrong image, never a fault.
+ */
+gmi_status gmi_forward_pp(const float* points, const float* values, const float* sigmas,
+                          int64_t N, int C, int H, int W, const gmi_params* p,
+                          float* image, float* den_out, void* workspace, size_t ws_bytes,
+                          gmi_stream_t stream);
+
+/*
+ * Backward pass of gmi_forward_pp: gradients of L = sum_q sum_c
+ * grad_image[q,c] image[q,c] with w_i(q) the kept weight of point i:
+ *   grad_values[i,c] = sum_q grad[q,c] w_i(q) / Z_q
+ *   grad_points[i]   = sum_q (w_i(q)/Z_q) t_i(q) (q - mu_i) / sigma_i^2
+ *   grad_sigmas[i]   = sum_q (w_i(q)/Z_q) t_i(q) (|q - mu_i|^2 / sigma_i^3
+ *                      - 2 / sigma_i)
+ *   with t_i(q) as for gmi_backward.  image, den: the outputs of the matching
+ *   gmi_forward_pp (den must not be NULL); grad_points [N,2], grad_values
+ *   [N,C], grad_sigmas [N]: device, written (each may be NULL to skip it).
+ * Each gradient is written by one thread (no atomics): the result does not
+ * vary from run to run.  Errors: as gmi_forward_pp.
+ */
+gmi_status gmi_backward_pp(const float* points, const float* values, const float* sigmas,
+                           int64_t N, int C, int H, int W, const gmi_params* p,
+                           const float* image, const float* den, const float* grad_image,
+                           float* grad_points, float* grad_values, float* grad_sigmas,
+                           void* workspace, size_t ws_bytes, gmi_stream_t stream);
 
 /*
  * Reads the device status word of a workspace after its stream has finished

@@ -18,7 +18,8 @@ import ctypes
 from . import _lib
 from ._lib import GmiError, MODE_EXACT, MODE_TRUNCATED
 
-__all__ = ["release_workspaces", "interpolate", "interpolate_backward", "gmi_interpolate", "BatchPlan", "gmi_interpolate_batch", "gmi_interpolate_stacked", "Server", "workspace_size", "GmiError", "MODE_EXACT", "MODE_TRUNCATED", "version", "lib"]
+__all__ = ["release_workspaces", "interpolate", "interpolate_backward", "gmi_interpolate", "interpolate_pp",
+           "interpolate_backward_pp", "gmi_interpolate_pp", "BatchPlan", "gmi_interpolate_batch", "gmi_interpolate_stacked", "Server", "workspace_size", "GmiError", "MODE_EXACT", "MODE_TRUNCATED", "version", "lib"]
 
 
 def lib():
@@ -278,6 +279,142 @@ def gmi_interpolate(points, values, sigma, H: int, W: int, *, radius_sigmas: flo
         _GMIFunction = _autograd_function()
     return _GMIFunction.apply(points, values, sigma, int(H), int(W), float(radius_sigmas), mode,
                               int(bin_px), int(variant))
+
+
+def _check_sigmas(sigmas, points):
+    import torch
+    if not isinstance(sigmas, torch.Tensor) or sigmas.dtype != torch.float32 or sigmas.device != points.device:
+        raise TypeError("sigmas must be a float32 tensor on the points' device")
+    if sigmas.numel() != points.shape[0]:
+        raise ValueError("sigmas must hold one sigma per point")
+    return sigmas.reshape(-1).contiguous()
+
+
+def interpolate_pp(points, values, sigmas, sigma_bound: float, H: int, W: int, *, radius_sigmas: float = 6.0,
+                   bin_px: int = 0, variant: int = 0, return_aux: bool = False, check: bool = False,
+                   graph: bool = False, out=None):
+    """Forward pass with a sigma per point (``sigmas[N]``; normalisers
+    1/sigma_i^2 kept), truncated at ``radius_sigmas * sigma_i``.
+    ``sigma_bound`` must bound every sigma_i from above (it sets the search
+    radius; a tight bound is faster).  With ``return_aux`` also returns
+    ``den`` = sum_i (sigma_bound/sigma_i)^2 exp(-d_i^2/(2 sigma_i^2)).
+    ``check=True`` synchronises and raises on out-of-range or non-finite
+    sigmas (and the other device-detected errors)."""
+    import torch
+    points, values = _check_inputs(points, values)
+    sigmas = _check_sigmas(sigmas, points)
+    N, C = int(points.shape[0]), int(values.shape[1])
+    H, W = int(H), int(W)
+    dev = points.device
+    flags = (_lib.FLAG_SYNC_CHECK if check else 0) | (_lib.FLAG_GRAPH if graph else 0)
+    md = MODE_TRUNCATED
+    p = _params(sigma_bound, radius_sigmas, md, flags, bin_px, variant)
+    nbytes = _ws_bytes(N, C, H, W, p, (N, C, H, W, float(sigma_bound), float(radius_sigmas), md, bin_px, variant))
+    if out is None:
+        out = torch.empty((H, W, C), dtype=torch.float32, device=dev)
+    den = torch.empty((H, W), dtype=torch.float32, device=dev) if return_aux else None
+    if torch.cuda.current_device() != dev.index:
+        with torch.cuda.device(dev):
+            return interpolate_pp(points, values, sigmas, sigma_bound, H, W, radius_sigmas=radius_sigmas,
+                                  bin_px=bin_px, variant=variant, return_aux=return_aux, check=check,
+                                  graph=graph, out=out)
+    stream = _stream_handle(dev)
+    ws = _workspace(dev, stream, nbytes)
+    st = _lib.load().gmi_forward_pp(points.data_ptr(), values.data_ptr(), sigmas.data_ptr(), N, C, H, W,
+                                    ctypes.byref(p), out.data_ptr(), den.data_ptr() if den is not None else None,
+                                    ws.data_ptr(), ws.numel(), stream)
+    _lib.check(st, "gmi_forward_pp")
+    if return_aux:
+        return out, den
+    return out
+
+
+def interpolate_backward_pp(points, values, sigmas, sigma_bound: float, H: int, W: int, image, den, grad_image, *,
+                            radius_sigmas: float = 6.0, bin_px: int = 0, variant: int = 0,
+                            need=(True, True, True), check: bool = False):
+    """Gradients of sum(grad_image * image) w.r.t. points, values and the
+    per-point sigmas (``image``, ``den`` from ``interpolate_pp(...,
+    return_aux=True)``).  Returns ``(grad_points [N,2], grad_values [N,C],
+    grad_sigmas [N])``; entries not in ``need`` are None."""
+    import torch
+    points, values = _check_inputs(points, values)
+    sigmas = _check_sigmas(sigmas, points)
+    N, C = int(points.shape[0]), int(values.shape[1])
+    dev = points.device
+    for t in (image, den, grad_image):
+        if t.device != dev or t.dtype != torch.float32:
+            raise ValueError("image, den and grad_image must be float32 on the points' device")
+    image, den, grad_image = (t.contiguous() for t in (image, den, grad_image))
+    H, W = int(H), int(W)
+    flags = _lib.FLAG_SYNC_CHECK if check else 0
+    md = MODE_TRUNCATED
+    p = _params(sigma_bound, radius_sigmas, md, flags, bin_px, variant)
+    nbytes = _ws_bytes(N, C, H, W, p, (N, C, H, W, float(sigma_bound), float(radius_sigmas), md, bin_px, variant))
+    gp = torch.empty((N, 2), dtype=torch.float32, device=dev) if need[0] else None
+    gv = torch.empty((N, C), dtype=torch.float32, device=dev) if need[1] else None
+    gs = torch.empty((N,), dtype=torch.float32, device=dev) if need[2] else None
+    if torch.cuda.current_device() != dev.index:
+        with torch.cuda.device(dev):
+            return interpolate_backward_pp(points, values, sigmas, sigma_bound, H, W, image, den, grad_image,
+                                           radius_sigmas=radius_sigmas, bin_px=bin_px, variant=variant,
+                                           need=need, check=check)
+    stream = _stream_handle(dev)
+    ws = _workspace(dev, stream, nbytes)
+    st = _lib.load().gmi_backward_pp(points.data_ptr(), values.data_ptr(), sigmas.data_ptr(), N, C, H, W,
+                                     ctypes.byref(p), image.data_ptr(), den.data_ptr(), grad_image.data_ptr(),
+                                     gp.data_ptr() if gp is not None else None,
+                                     gv.data_ptr() if gv is not None else None,
+                                     gs.data_ptr() if gs is not None else None, ws.data_ptr(), ws.numel(), stream)
+    _lib.check(st, "gmi_backward_pp")
+    return gp, gv, gs
+
+
+def _pp_function():
+    import torch
+
+    class GMIPPFunction(torch.autograd.Function):
+        """Per-point-sigma interpolation as a differentiable op; forward and
+        backward run in libgmi's kernels."""
+
+        @staticmethod
+        def forward(ctx, points, values, sigmas, sigma_bound, H, W, radius_sigmas, bin_px, variant):
+            img, den = interpolate_pp(points, values, sigmas, sigma_bound, H, W, radius_sigmas=radius_sigmas,
+                                      bin_px=bin_px, variant=variant, return_aux=True)
+            ctx.set_materialize_grads(False)
+            ctx.save_for_backward(points, values, sigmas, img, den)
+            ctx.cfg = (sigma_bound, H, W, radius_sigmas, bin_px, variant)
+            return img
+
+        @staticmethod
+        def backward(ctx, g):
+            if g is None:
+                return (None,) * 9
+            points, values, sigmas, img, den = ctx.saved_tensors
+            bound, H, W, k, bin_px, variant = ctx.cfg
+            need = tuple(ctx.needs_input_grad[:3])
+            gp, gv, gs = interpolate_backward_pp(points.detach(), values.detach(), sigmas.detach(), bound, H, W,
+                                                 img, den, g.float(), radius_sigmas=k, bin_px=bin_px,
+                                                 variant=variant, need=need)
+            if gs is not None:
+                gs = gs.reshape(sigmas.shape)
+            return gp, gv, gs, None, None, None, None, None, None
+
+    return GMIPPFunction
+
+
+_GMIPPFunction = None
+
+
+def gmi_interpolate_pp(points, values, sigmas, sigma_bound: float, H: int, W: int, *, radius_sigmas: float = 6.0,
+                       bin_px: int = 0, variant: int = 0):
+    """Differentiable per-point-sigma interpolation (truncated at
+    ``radius_sigmas * sigma_i``): gradients flow to ``points``, ``values``
+    and ``sigmas``.  ``sigma_bound`` >= every sigma_i.  Returns [H, W, C]."""
+    global _GMIPPFunction
+    if _GMIPPFunction is None:
+        _GMIPPFunction = _pp_function()
+    return _GMIPPFunction.apply(points, values, sigmas, float(sigma_bound), int(H), int(W), float(radius_sigmas),
+                                int(bin_px), int(variant))
 
 
 def _flat_views(shapes, dev, dtype=None):

@@ -15,9 +15,9 @@
 
 namespace gmi {
 
-cudaError_t launch_near(const KArgs& a, int mth, int mtw, bool trunc, int grid, cudaStream_t s);
+cudaError_t launch_near(const KArgs& a, int mth, int mtw, bool trunc, bool pp, int grid, cudaStream_t s);
 cudaError_t launch_scatter_plan(const KArgs& a, bool trunc, int n_scatter, cudaStream_t s);
-int near_blocks_per_sm(int mth, int mtw, int C, bool trunc);
+int near_blocks_per_sm(int mth, int mtw, int C, bool trunc, bool pp);
 cudaError_t launch_far(const KArgs& a, int mth, int mtw, int sms, cudaStream_t s);
 __global__ void bin_count_kernel(KArgs a);
 __global__ void scan_partial_kernel(const unsigned* cnt, long long nb, unsigned* partials, const long long* totals);
@@ -98,6 +98,7 @@ void fill_geom(ImageGeom& g, long long N, int H, int W, float sigma, float k, in
   g.sk = (float)sqrt(kappa);
   g.r2k = (float)((double)k * k * (double)sigma * sigma);
   g.u_near_max = (float)(100.0 / kappa);
+  g.e_trunc = (float)((double)k * k * 1.4426950408889634 / 2.0);
 }
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
@@ -124,6 +125,7 @@ WsLayout ws_layout(long long n_total, long long nb_total, long long mt_total, lo
   L.sxy = o;    o = align_up(o + sizeof(float2) * (size_t)n_total, 256);
   L.sval = o;   o = align_up(o + sizeof(float4) * (size_t)n_total, 256);
   L.perm = o;   o = align_up(o + sizeof(unsigned) * (size_t)n_total, 256);
+  L.spp = o;    o = align_up(o + sizeof(float2) * (size_t)n_total, 256);
   L.partials = o; o = align_up(o + sizeof(unsigned) * (size_t)((nb_total + kScanChunk - 1) / kScanChunk + 1), 256);
   L.farq = o;   o = align_up(o + sizeof(uint2) * (size_t)(mt_total > 0 ? mt_total : 1), 256);
   L.items = o;  o = align_up(o + sizeof(uint4) * (size_t)(L.cap_items > 0 ? L.cap_items : 1), 256);
@@ -150,6 +152,7 @@ DevWork bind_ws(void* ws, const WsLayout& L) {
   w.slots = (float*)(b + L.slots);
   w.ubound = (float*)(b + L.ubound);
   w.perm = (unsigned*)(b + L.perm);
+  w.spp = (float2*)(b + L.spp);
   w.pplane = nullptr;
   w.fbflag = nullptr;
   w.fbq = nullptr;
@@ -165,11 +168,10 @@ DevWork bind_ws(void* ws, const WsLayout& L) {
 gmi_status run_bin_and_plan(KArgs& a, const WsLayout& L, void* ws, int mth, int mtw, bool trunc,
                             cudaStream_t s, bool plan) {
   const ProfileMark pb = profile_begin(GMI_STAGE_BIN, s);
-  cudaError_t e;
   const int sms = device_sm_count();
   if (a.totals) {
     batch_clear_kernel<<<sms * 4, 256, 0, s>>>(a);
-  } else if ((e = cudaMemsetAsync(ws, 0, L.zero_end, s)) != cudaSuccess) {
+  } else if (cudaMemsetAsync(ws, 0, L.zero_end, s) != cudaSuccess) {
     return GMI_ERR_CUDA;
   }
   a.cap_items = L.cap_items;
@@ -183,13 +185,13 @@ gmi_status run_bin_and_plan(KArgs& a, const WsLayout& L, void* ws, int mth, int 
     const int ns = (int)((a.nb_total + kScanChunk - 1) / kScanChunk);
     scan_partial_kernel<<<ns, 256, 0, s>>>(a.w.off, a.nb_total, a.w.partials, a.totals);
     scan_final_kernel<<<ns, 256, 0, s>>>(a.w.off, a.nb_total, a.w.partials, a.totals);
-    if ((e = cudaGetLastError()) != cudaSuccess) return GMI_ERR_CUDA;
+    if (cudaGetLastError() != cudaSuccess) return GMI_ERR_CUDA;
   }
   if (plan) {
-    if ((e = launch_scatter_plan(a, trunc, gb, s)) != cudaSuccess) return GMI_ERR_CUDA;
+    if (launch_scatter_plan(a, trunc, gb, s) != cudaSuccess) return GMI_ERR_CUDA;
   } else if (gb > 0) {
     bin_scatter_kernel<<<gb, 256, 0, s>>>(a);
-    if ((e = cudaGetLastError()) != cudaSuccess) return GMI_ERR_CUDA;
+    if (cudaGetLastError() != cudaSuccess) return GMI_ERR_CUDA;
   }
   profile_end(pb, s);
   return GMI_OK;
@@ -197,20 +199,19 @@ gmi_status run_bin_and_plan(KArgs& a, const WsLayout& L, void* ws, int mth, int 
 
 // Binning + plan + near + far on prepared arguments (single image or batch).
 gmi_status run_forward_pipeline(KArgs& a, const WsLayout& L, void* ws, int mth, int mtw, bool trunc,
-                                cudaStream_t s) {
+                                cudaStream_t s, bool pp) {
   gmi_status st = run_bin_and_plan(a, L, ws, mth, mtw, trunc, s, true);
   if (st != GMI_OK) return st;
-  cudaError_t e;
   const int sms = device_sm_count();
-  const int per_sm = near_blocks_per_sm(mth, mtw, a.C, trunc);
+  const int per_sm = near_blocks_per_sm(mth, mtw, a.C, trunc, pp);
   // persistent: at most one resident wave, and no more warps than work items can use
   const int gn = (int)std::max<long long>(1, std::min<long long>(a.wt_total * 4, (long long)sms * per_sm));
   const ProfileMark pn = profile_begin(GMI_STAGE_NEAR, s);
-  if ((e = launch_near(a, mth, mtw, trunc, gn, s)) != cudaSuccess) return GMI_ERR_CUDA;
+  if (launch_near(a, mth, mtw, trunc, pp, gn, s) != cudaSuccess) return GMI_ERR_CUDA;
   profile_end(pn, s);
   if (!trunc) {
     const ProfileMark pf = profile_begin(GMI_STAGE_FAR, s);
-    if ((e = launch_far(a, mth, mtw, sms, s)) != cudaSuccess) return GMI_ERR_CUDA;
+    if (launch_far(a, mth, mtw, sms, s) != cudaSuccess) return GMI_ERR_CUDA;
     profile_end(pf, s);
   }
   return GMI_OK;
@@ -221,6 +222,7 @@ gmi_status read_status(const void* ws, cudaStream_t s) {
   unsigned st = 0;
   if (cudaMemcpy(&st, ws, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess) return GMI_ERR_CUDA;
   if (st & ST_NONFINITE) return GMI_ERR_NONFINITE;
+  if (st & ST_SIGMA) return GMI_ERR_INVALID_ARG;
   if (st & (ST_INTERNAL | ST_TIMEOUT)) return GMI_ERR_INTERNAL;
   return GMI_OK;
 }
@@ -228,6 +230,99 @@ gmi_status read_status(const void* ws, cudaStream_t s) {
 }  // namespace gmi
 
 using namespace gmi;
+
+// Forward pass with one shared sigma (sigmas == null) or per-point sigmas.
+static gmi_status forward_impl(const float* points, const float* values, const float* sigmas, int64_t N, int C,
+                               int H, int W, const gmi_params* p, float* image, float* den_out, float* shift_out,
+                               void* workspace, size_t ws_bytes, gmi_stream_t stream) {
+  gmi_status st = check_params(p);
+  if (st != GMI_OK) return st;
+  if ((st = check_shape(N, C, H, W)) != GMI_OK) return st;
+  if (!image || (N > 0 && (!points || !values))) return GMI_ERR_INVALID_ARG;
+  if (((uintptr_t)points & 7u) != 0 || ((uintptr_t)values & 3u) != 0 || ((uintptr_t)image & 3u) != 0)
+    return GMI_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  int mth, mtw;
+  variant_dims(p->variant, &mth, &mtw);
+  ImageGeom g;
+  memset(&g, 0, sizeof(g));
+  fill_geom(g, N, H, W, p->sigma, p->radius_sigmas, p->bin_px, mth, mtw);
+  g.points = points;
+  g.values = values;
+  g.image = image;
+  g.den = den_out;
+  g.shift = shift_out;
+  g.sigmas = sigmas;
+  set_vec_ok(g);
+  const long long nb = (long long)g.nbx * g.nby;
+  const long long mt = (long long)g.mtx * g.mty;
+  const long long wt = (long long)g.wtx * g.wty;
+  const WsLayout L = ws_layout(N, nb, mt, wt, slot_bytes_for(mth, mtw, C), bwd_extra_bytes(N, C, H, W));
+  if (!workspace || ((uintptr_t)workspace & 255u) != 0 || ws_bytes < L.total) return GMI_ERR_WORKSPACE;
+
+  if (N == 0) {  // no known point: colour 0 and den 0 everywhere
+    const size_t px = (size_t)H * (size_t)W;
+    if (cudaMemsetAsync(image, 0, px * C * sizeof(float), s) != cudaSuccess) return GMI_ERR_CUDA;
+    if (den_out && cudaMemsetAsync(den_out, 0, px * sizeof(float), s) != cudaSuccess) return GMI_ERR_CUDA;
+    if (shift_out && cudaMemsetAsync(shift_out, 0, px * sizeof(float), s) != cudaSuccess) return GMI_ERR_CUDA;
+    if (cudaMemsetAsync(workspace, 0, sizeof(unsigned) * kStatusWords, s) != cudaSuccess) return GMI_ERR_CUDA;
+    return (p->flags & GMI_FLAG_SYNC_CHECK) ? read_status(workspace, s) : GMI_OK;
+  }
+
+  KArgs a;
+  memset(&a, 0, sizeof(a));
+  a.w = bind_ws(workspace, L);
+  a.g0 = g;
+  a.n_images = 1;
+  a.C = C;
+  a.n_total = N;
+  a.nb_total = nb;
+  a.wt_total = wt;
+  a.ch_total = (N + kChunk - 1) / kChunk;
+  a.mt_total = mt;
+  const bool trunc = p->mode == GMI_MODE_TRUNCATED;
+  const bool pp = sigmas != nullptr;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if ((p->flags & GMI_FLAG_GRAPH) && !profile_on() && cudaStreamIsCapturing(s, &cap) == cudaSuccess &&
+      cap == cudaStreamCaptureStatusNone) {
+    FwdGraphKey key;
+    memset(&key, 0, sizeof(key));
+    cudaGetDevice(&key.device);
+    key.C = C;
+    key.H = H;
+    key.W = W;
+    key.N = N;
+    key.points = points;
+    key.values = values;
+    key.sigmas = sigmas;
+    key.image = image;
+    key.den = den_out;
+    key.shift = shift_out;
+    key.ws = workspace;
+    key.ws_bytes = ws_bytes;
+    key.params = *p;
+    // fill the host-side caches the launch sequence reads before any capture starts
+    device_sm_count();
+    near_blocks_per_sm(mth, mtw, C, trunc, pp);
+    struct Ctx {
+      const KArgs* a;
+      const WsLayout* L;
+      void* ws;
+      int mth, mtw;
+      bool trunc, pp;
+    } ctx{&a, &L, workspace, mth, mtw, trunc, pp};
+    auto launch = [](void* c, cudaStream_t cs) -> gmi_status {
+      const Ctx* x = static_cast<const Ctx*>(c);
+      KArgs ka = *x->a;
+      return run_forward_pipeline(ka, *x->L, x->ws, x->mth, x->mtw, x->trunc, cs, x->pp);
+    };
+    st = forward_graphed(key, launch, &ctx, s);
+  } else {
+    st = run_forward_pipeline(a, L, workspace, mth, mtw, trunc, s, pp);
+  }
+  if (st != GMI_OK) return st;
+  return (p->flags & GMI_FLAG_SYNC_CHECK) ? read_status(workspace, s) : GMI_OK;
+}
 
 extern "C" {
 
@@ -279,90 +374,19 @@ gmi_status gmi_workspace_size(int64_t N, int C, int H, int W, const gmi_params* 
 gmi_status gmi_forward(const float* points, const float* values, int64_t N, int C, int H, int W,
                        const gmi_params* p, float* image, float* den_out, float* shift_out,
                        void* workspace, size_t ws_bytes, gmi_stream_t stream) {
+  return forward_impl(points, values, nullptr, N, C, H, W, p, image, den_out, shift_out, workspace, ws_bytes,
+                      stream);
+}
+
+gmi_status gmi_forward_pp(const float* points, const float* values, const float* sigmas, int64_t N, int C, int H,
+                          int W, const gmi_params* p, float* image, float* den_out, void* workspace,
+                          size_t ws_bytes, gmi_stream_t stream) {
   gmi_status st = check_params(p);
   if (st != GMI_OK) return st;
-  if ((st = check_shape(N, C, H, W)) != GMI_OK) return st;
-  if (!image || (N > 0 && (!points || !values))) return GMI_ERR_INVALID_ARG;
-  if (((uintptr_t)points & 7u) != 0 || ((uintptr_t)values & 3u) != 0 || ((uintptr_t)image & 3u) != 0)
-    return GMI_ERR_INVALID_ARG;
-  cudaStream_t s = (cudaStream_t)stream;
-  int mth, mtw;
-  variant_dims(p->variant, &mth, &mtw);
-  ImageGeom g;
-  memset(&g, 0, sizeof(g));
-  fill_geom(g, N, H, W, p->sigma, p->radius_sigmas, p->bin_px, mth, mtw);
-  g.points = points;
-  g.values = values;
-  g.image = image;
-  g.den = den_out;
-  g.shift = shift_out;
-  set_vec_ok(g);
-  const long long nb = (long long)g.nbx * g.nby;
-  const long long mt = (long long)g.mtx * g.mty;
-  const long long wt = (long long)g.wtx * g.wty;
-  const WsLayout L = ws_layout(N, nb, mt, wt, slot_bytes_for(mth, mtw, C), bwd_extra_bytes(N, C, H, W));
-  if (!workspace || ((uintptr_t)workspace & 255u) != 0 || ws_bytes < L.total) return GMI_ERR_WORKSPACE;
-
-  if (N == 0) {  // no known point: colour 0 and den 0 everywhere
-    const size_t px = (size_t)H * (size_t)W;
-    if (cudaMemsetAsync(image, 0, px * C * sizeof(float), s) != cudaSuccess) return GMI_ERR_CUDA;
-    if (den_out && cudaMemsetAsync(den_out, 0, px * sizeof(float), s) != cudaSuccess) return GMI_ERR_CUDA;
-    if (shift_out && cudaMemsetAsync(shift_out, 0, px * sizeof(float), s) != cudaSuccess) return GMI_ERR_CUDA;
-    if (cudaMemsetAsync(workspace, 0, sizeof(unsigned) * kStatusWords, s) != cudaSuccess) return GMI_ERR_CUDA;
-    return (p->flags & GMI_FLAG_SYNC_CHECK) ? read_status(workspace, s) : GMI_OK;
-  }
-
-  KArgs a;
-  memset(&a, 0, sizeof(a));
-  a.w = bind_ws(workspace, L);
-  a.g0 = g;
-  a.n_images = 1;
-  a.C = C;
-  a.n_total = N;
-  a.nb_total = nb;
-  a.wt_total = wt;
-  a.ch_total = (N + kChunk - 1) / kChunk;
-  a.mt_total = mt;
-  const bool trunc = p->mode == GMI_MODE_TRUNCATED;
-  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-  if ((p->flags & GMI_FLAG_GRAPH) && !profile_on() && cudaStreamIsCapturing(s, &cap) == cudaSuccess &&
-      cap == cudaStreamCaptureStatusNone) {
-    FwdGraphKey key;
-    memset(&key, 0, sizeof(key));
-    cudaGetDevice(&key.device);
-    key.C = C;
-    key.H = H;
-    key.W = W;
-    key.N = N;
-    key.points = points;
-    key.values = values;
-    key.image = image;
-    key.den = den_out;
-    key.shift = shift_out;
-    key.ws = workspace;
-    key.ws_bytes = ws_bytes;
-    key.params = *p;
-    // fill the host-side caches the launch sequence reads before any capture starts
-    device_sm_count();
-    near_blocks_per_sm(mth, mtw, C, trunc);
-    struct Ctx {
-      const KArgs* a;
-      const WsLayout* L;
-      void* ws;
-      int mth, mtw;
-      bool trunc;
-    } ctx{&a, &L, workspace, mth, mtw, trunc};
-    auto launch = [](void* c, cudaStream_t cs) -> gmi_status {
-      const Ctx* x = static_cast<const Ctx*>(c);
-      KArgs ka = *x->a;
-      return run_forward_pipeline(ka, *x->L, x->ws, x->mth, x->mtw, x->trunc, cs);
-    };
-    st = forward_graphed(key, launch, &ctx, s);
-  } else {
-    st = run_forward_pipeline(a, L, workspace, mth, mtw, trunc, s);
-  }
-  if (st != GMI_OK) return st;
-  return (p->flags & GMI_FLAG_SYNC_CHECK) ? read_status(workspace, s) : GMI_OK;
+  if (p->mode != GMI_MODE_TRUNCATED) return GMI_ERR_UNSUPPORTED;
+  if (N > 0 && (!sigmas || ((uintptr_t)sigmas & 3u) != 0)) return GMI_ERR_INVALID_ARG;
+  return forward_impl(points, values, N > 0 ? sigmas : nullptr, N, C, H, W, p, image, den_out, nullptr, workspace,
+                      ws_bytes, stream);
 }
 
 gmi_status gmi_workspace_status(const void* workspace, gmi_stream_t stream) {

@@ -10,7 +10,7 @@ namespace gmi {
 
 // Byte offsets of the regions of a workspace.
 struct WsLayout {
-  size_t status, off, oob, tile_done, zero_end, rank, sxy, sval, perm, partials, farq, items, slots, ubound, extra, total;
+  size_t status, off, oob, tile_done, zero_end, rank, sxy, sval, perm, spp, partials, farq, items, slots, ubound, extra, total;
   unsigned cap_items, cap_slots;
 };
 
@@ -28,8 +28,9 @@ WsLayout ws_layout(long long n_total, long long nb_total, long long mt_total, lo
 DevWork bind_ws(void* ws, const WsLayout& L);
 gmi_status run_bin_and_plan(KArgs& a, const WsLayout& L, void* ws, int mth, int mtw, bool trunc,
                             cudaStream_t s, bool plan);
+// pp: per-point sigmas (a.g0.sigmas set; truncated mode)
 gmi_status run_forward_pipeline(KArgs& a, const WsLayout& L, void* ws, int mth, int mtw, bool trunc,
-                                cudaStream_t s);
+                                cudaStream_t s, bool pp = false);
 gmi_status read_status(const void* ws, cudaStream_t s);
 
 // Stage timing (profile.cu): no-ops unless gmi_profile_enable(1) was called.
@@ -48,7 +49,7 @@ struct FwdGraphKey {
   int device;
   int C, H, W;
   long long N;
-  const void *points, *values, *image, *den, *shift, *ws;
+  const void *points, *values, *sigmas, *image, *den, *shift, *ws;
   size_t ws_bytes;
   gmi_params params;
 };

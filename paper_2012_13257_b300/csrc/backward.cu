@@ -9,6 +9,14 @@
 // From the forward pass only the image c(q), den_q and shift_q are kept
 // (w_i(q) / Z_q = 2^(-kappa (d^2 - shift_q)) / den_q); the bins are rebuilt.
 //
+// With a sigma per point (truncated mode), w_i(q) = 2^(la_i - kappa_i d^2)
+// (pp_consts) and each point has its own terms
+//   dL/dmu_i    = sum_q (w_i(q) / Z_q) t_i(q) (q - mu_i) / sigma_i^2
+//   dL/dsigma_i = sum_q (w_i(q) / Z_q) t_i(q) (|q - mu_i|^2 / sigma_i^3 - 2 / sigma_i),
+// the last term from the normaliser 1/sigma_i^2 of the 2D normal (it no longer
+// cancels); every pair lies inside its point's disc d <= k sigma_i, so the
+// point-centric kernel covers all of them.
+//
 // Work is split by pixel:
 //   * core pixels (no shift, den_q >= 2^-12): point-centric.  One thread per
 //     bin-sorted point sweeps the disc of pixels within R_core, with
@@ -45,7 +53,7 @@ __global__ void __launch_bounds__(256) bwd_prep_kernel(KArgs a_in, BwdArgs b) {
     const long long px = gp - g.px_base;
     if (px == 0 && bi.gsig) *bi.gsig = 0.0f;   // accumulated by the later kernels
     const float d = bi.den[px];
-    const float sh = bi.shift[px];
+    const float sh = bi.shift ? bi.shift[px] : 0.0f;
     float G[4] = {0.f, 0.f, 0.f, 0.f};
     float sp = 0.0f;
     if (d > 0.0f) {
@@ -81,90 +89,10 @@ __global__ void __launch_bounds__(256) bwd_prep_kernel(KArgs a_in, BwdArgs b) {
   }
 }
 
-// Point-centric gradients over core pixels; one thread per bin-sorted point.
-template <int C, bool TRUNC>
-__global__ void __launch_bounds__(256) bwd_point_kernel(KArgs a_in, BwdArgs b, float rcore_log2) {
-  const KArgs a = resolve(a_in);
+// Single-image sigma gradient: block sum of D -> one partial per block; the
+// last block to finish adds the partials in block order.
+__device__ void sigma_block_total(const KArgs& a, const BwdArgs& b, float D) {
   const unsigned full = 0xffffffffu;
-  float D = 0.0f;
-  for (long long i0 = (long long)blockIdx.x * blockDim.x; i0 < a.n_total; i0 += (long long)gridDim.x * blockDim.x) {
-    const long long i = i0 + threadIdx.x;
-    const bool valid = i < a.n_total;
-    int img = 0;
-    float Dp = 0.0f;
-    if (valid) {
-      img = find_image<2>(a, i);
-      const ImageGeom& g = *geom_ptr(a, img);
-      const BwdImage bi = bwd_image(b, img);
-      const float4* __restrict__ plane = a.w.pplane + g.px_base;
-      const float4* __restrict__ plane2 = a.w.pplane + a.px_total + g.px_base;
-      const float rcore2 = TRUNC ? g.r2k : rcore_log2 / g.kappa;
-      const float2 p = a.w.sxy[i];
-      const float4 cv = a.w.sval[i];
-      const float c4[4] = {cv.x, cv.y, cv.z, cv.w};
-      float A[4] = {0.f, 0.f, 0.f, 0.f};
-      float Bx = 0.0f, By = 0.0f;
-      const float R = sqrtf(rcore2);
-      const int iy0 = max(0, (int)ceilf(p.y - R - 0.5f));
-      const int iy1 = min(g.H - 1, (int)floorf(p.y + R - 0.5f));
-      for (int iy = iy0; iy <= iy1; ++iy) {
-        const float dy = (float)iy + 0.5f - p.y;
-        const float dy2 = dy * dy;
-        const float rem = rcore2 - dy2;
-        if (rem < 0.0f) continue;
-        const float h = sqrtf(rem);
-        const int ix0 = max(0, (int)ceilf(p.x - h - 0.5f));
-        const int ix1 = min(g.W - 1, (int)floorf(p.x + h - 0.5f));
-        const float4* __restrict__ P = plane + (long long)iy * g.W;
-        float rowWt = 0.0f;
-        float dx = (float)ix0 + 0.5f - p.x;
-#pragma unroll 4
-        for (int ix = ix0; ix <= ix1; ++ix, dx += 1.0f) {
-          const float d2 = fmaf(dx, dx, dy2);
-          float w = ex2(-g.kappa * d2);
-          if (TRUNC && !(d2 <= g.r2k)) w = 0.0f;
-          const float4 pv = __ldg(&P[ix]);
-          const float Gv[4] = {pv.x, pv.y, pv.z, pv.w};
-          const float sp = C == 4 ? __ldg(&plane2[(long long)iy * g.W + ix]).x : pv.w;
-          float t = -sp;
-#pragma unroll
-          for (int c = 0; c < C; ++c) t = fmaf(Gv[c], c4[c], t);
-#pragma unroll
-          for (int c = 0; c < C; ++c) A[c] = fmaf(w, Gv[c], A[c]);
-          const float wt = w * t;
-          Bx = fmaf(wt, dx, Bx);
-          rowWt += wt;
-          Dp = fmaf(wt, d2, Dp);
-        }
-        By = fmaf(rowWt, dy, By);
-      }
-      const unsigned o = a.w.perm[i];
-      if (bi.gvals) {
-#pragma unroll
-        for (int c = 0; c < C; ++c) bi.gvals[(long long)o * C + c] = A[c];
-      }
-      if (bi.gpts) {
-        bi.gpts[2LL * o] = Bx * bi.inv_s2;
-        bi.gpts[2LL * o + 1] = By * bi.inv_s2;
-      }
-    }
-    if (b.table) {
-      // batched: one float atomic per (warp, image) into that image's sigma gradient
-      const unsigned same = __match_any_sync(full, valid ? img : -1);
-      if (valid) {
-        float s2 = 0.0f;
-        for (unsigned m = same; m; m &= m - 1) s2 += __shfl_sync(same, Dp, __ffs(m) - 1);
-        if ((int)(threadIdx.x & 31) == __ffs(same) - 1) {
-          const BwdImage bi = bwd_image(b, img);
-          if (bi.gsig) atomicAdd(bi.gsig, s2 * bi.inv_s3);
-        }
-      }
-    } else {
-      D += Dp;
-    }
-  }
-  if (b.table) return;
-  // single image: block sum -> partial; the last block adds the partials in order
   __shared__ float red[8];
   __shared__ bool last;
 #pragma unroll
@@ -184,6 +112,129 @@ __global__ void __launch_bounds__(256) bwd_point_kernel(KArgs a_in, BwdArgs b, f
     float t = 0.0f;
     for (unsigned k = 0; k < gridDim.x; ++k) t += __ldcg(&a.w.sig_part[k]);
     if (b.one.gsig) *b.one.gsig += t * b.one.inv_s3;
+  }
+}
+
+// Point-centric gradients over core pixels; one thread per bin-sorted point.
+template <int C, bool TRUNC, bool PP>
+__global__ void __launch_bounds__(256) bwd_point_kernel(KArgs a_in, BwdArgs b, float rcore_log2) {
+  static_assert(TRUNC || !PP, "per-point sigma is built for truncated mode only");
+  const KArgs a = resolve(a_in);
+  const unsigned full = 0xffffffffu;
+  float D = 0.0f;
+  for (long long i0 = (long long)blockIdx.x * blockDim.x; i0 < a.n_total; i0 += (long long)gridDim.x * blockDim.x) {
+    const long long i = i0 + threadIdx.x;
+    const bool valid = i < a.n_total;
+    int img = 0;
+    float Dp = 0.0f;
+    if (valid) {
+      img = find_image<2>(a, i);
+      const ImageGeom& g = *geom_ptr(a, img);
+      const BwdImage bi = bwd_image(b, img);
+      const float4* __restrict__ plane = a.w.pplane + g.px_base;
+      const float4* __restrict__ plane2 = a.w.pplane + a.px_total + g.px_base;
+      // per-point sigma: kappa_i and la_i of this point, its own disc kappa_i d^2 <= e_trunc
+      const float2 spc = PP ? a.w.spp[i] : make_float2(0.f, 0.f);
+      const float kap = PP ? spc.x * spc.x : g.kappa;
+      // (the disc is widened a little: the forward's test below decides membership)
+      const float rcore2 = PP ? 1.0001f * g.e_trunc / kap : (TRUNC ? g.r2k : rcore_log2 / g.kappa);
+      const float neg_thr = -g.e_trunc;
+      const float2 p = a.w.sxy[i];
+      const float4 cv = a.w.sval[i];
+      const float c4[4] = {cv.x, cv.y, cv.z, cv.w};
+      float A[4] = {0.f, 0.f, 0.f, 0.f};
+      float Bx = 0.0f, By = 0.0f, Sw = 0.0f;
+      const float R = sqrtf(rcore2);
+      const int iy0 = max(0, (int)ceilf(p.y - R - 0.5f));
+      const int iy1 = min(g.H - 1, (int)floorf(p.y + R - 0.5f));
+      for (int iy = iy0; iy <= iy1; ++iy) {
+        const float dy = (float)iy + 0.5f - p.y;
+        const float dy2 = dy * dy;
+        const float rem = rcore2 - dy2;
+        if (rem < 0.0f) continue;
+        const float h = sqrtf(rem);
+        const int ix0 = max(0, (int)ceilf(p.x - h - 0.5f));
+        const int ix1 = min(g.W - 1, (int)floorf(p.x + h - 0.5f));
+        const float4* __restrict__ P = plane + (long long)iy * g.W;
+        // per-point sigma: the row factor exactly as the forward kernel forms it
+        // from its micro-tile's first pixel centre, so that both keep the same pairs
+        float ayp = 0.0f, gyp = 0.0f;
+        if (PP) {
+          const int y0 = iy & ~(a.mth - 1);
+          const float v = ((float)y0 + 0.5f - p.y) * spc.x;
+          const float tv = __fmaf_rn((float)(iy - y0), spc.x, v);
+          ayp = __fmul_rn(-tv, tv);
+          gyp = ex2(__fadd_rn(ayp, spc.y));
+        }
+        float rowWt = 0.0f;
+        float dx = (float)ix0 + 0.5f - p.x;
+#pragma unroll 4
+        for (int ix = ix0; ix <= ix1; ++ix, dx += 1.0f) {
+          const float d2 = fmaf(dx, dx, dy2);
+          float w;
+          if (PP) {
+            const int x0 = ix & ~(a.mtw - 1);
+            const float u = ((float)x0 + 0.5f - p.x) * spc.x;
+            const float tu = __fmaf_rn((float)(ix - x0), spc.x, u);
+            const float ax = __fmul_rn(-tu, tu);
+            w = __fadd_rn(ax, ayp) >= neg_thr ? ex2(ax) * gyp : 0.0f;
+          } else {
+            w = ex2(-g.kappa * d2);
+            if (TRUNC && !(d2 <= g.r2k)) w = 0.0f;
+          }
+          const float4 pv = __ldg(&P[ix]);
+          const float Gv[4] = {pv.x, pv.y, pv.z, pv.w};
+          const float sp = C == 4 ? __ldg(&plane2[(long long)iy * g.W + ix]).x : pv.w;
+          float t = -sp;
+#pragma unroll
+          for (int c = 0; c < C; ++c) t = fmaf(Gv[c], c4[c], t);
+#pragma unroll
+          for (int c = 0; c < C; ++c) A[c] = fmaf(w, Gv[c], A[c]);
+          const float wt = w * t;
+          Bx = fmaf(wt, dx, Bx);
+          rowWt += wt;
+          Dp = fmaf(wt, d2, Dp);
+        }
+        By = fmaf(rowWt, dy, By);
+        if (PP) Sw += rowWt;
+      }
+      const unsigned o = a.w.perm[i];
+      if (PP) {
+        const float si = g.sigmas[o];
+        const float is2 = 1.0f / (si * si);
+        if (bi.gpts) {
+          bi.gpts[2LL * o] = Bx * is2;
+          bi.gpts[2LL * o + 1] = By * is2;
+        }
+        if (bi.gsigs) bi.gsigs[o] = (Dp * is2 - 2.0f * Sw) / si;
+      }
+      if (bi.gvals) {
+#pragma unroll
+        for (int c = 0; c < C; ++c) bi.gvals[(long long)o * C + c] = A[c];
+      }
+      if (bi.gpts && !PP) {
+        bi.gpts[2LL * o] = Bx * bi.inv_s2;
+        bi.gpts[2LL * o + 1] = By * bi.inv_s2;
+      }
+    }
+    if (PP) continue;   // no shared sigma to reduce into
+    if (b.table) {
+      // batched: one float atomic per (warp, image) into that image's sigma gradient
+      const unsigned same = __match_any_sync(full, valid ? img : -1);
+      if (valid) {
+        float s2 = 0.0f;
+        for (unsigned m = same; m; m &= m - 1) s2 += __shfl_sync(same, Dp, __ffs(m) - 1);
+        if ((int)(threadIdx.x & 31) == __ffs(same) - 1) {
+          const BwdImage bi = bwd_image(b, img);
+          if (bi.gsig) atomicAdd(bi.gsig, s2 * bi.inv_s3);
+        }
+      }
+    } else {
+      D += Dp;
+    }
+  }
+  if constexpr (!PP) {
+    if (!b.table) sigma_block_total(a, b, D);
   }
 }
 
@@ -318,8 +369,9 @@ static cudaError_t launch_bwd_c(const KArgs& a, const BwdArgs& b, cudaStream_t s
   bwd_prep_kernel<C><<<prep_blocks, 256, 0, s>>>(a, b);
   const float rcore_log2 = kRelLog2 + kCoreLog2;   // kappa * R_core^2
   const unsigned blocks = (unsigned)std::max<long long>(1, std::min<long long>((a.n_total + 255) / 256, kSigParts));
-  if (b.trunc) bwd_point_kernel<C, true><<<blocks, 256, 0, s>>>(a, b, rcore_log2);
-  else bwd_point_kernel<C, false><<<blocks, 256, 0, s>>>(a, b, rcore_log2);
+  if (b.pp) bwd_point_kernel<C, true, true><<<blocks, 256, 0, s>>>(a, b, rcore_log2);
+  else if (b.trunc) bwd_point_kernel<C, true, false><<<blocks, 256, 0, s>>>(a, b, rcore_log2);
+  else bwd_point_kernel<C, false, false><<<blocks, 256, 0, s>>>(a, b, rcore_log2);
   if (!b.trunc) bwd_fallback_kernel<C><<<sms * 4, 32 * kFarWarps, 0, s>>>(a, b);
   return cudaGetLastError();
 }
@@ -337,14 +389,18 @@ cudaError_t launch_backward(const KArgs& a, const BwdArgs& b, cudaStream_t s) {
 
 using namespace gmi;
 
-extern "C" gmi_status gmi_backward(const float* points, const float* values, int64_t N, int C, int H, int W,
-                                   const gmi_params* p, const float* image, const float* den, const float* shift,
-                                   const float* grad_image, float* grad_points, float* grad_values,
-                                   float* grad_sigma, void* workspace, size_t ws_bytes, gmi_stream_t stream) {
+// Backward pass with one shared sigma (sigmas == null: grad_sigma [1]) or
+// per-point sigmas (grad_sigmas [N], shift may be null).
+static gmi_status backward_impl(const float* points, const float* values, const float* sigmas, int64_t N, int C,
+                                int H, int W, const gmi_params* p, const float* image, const float* den,
+                                const float* shift, const float* grad_image, float* grad_points,
+                                float* grad_values, float* grad_sigma, float* grad_sigmas, bool per_point,
+                                void* workspace, size_t ws_bytes, gmi_stream_t stream) {
   gmi_status st = check_params(p);
   if (st != GMI_OK) return st;
   if ((st = check_shape(N, C, H, W)) != GMI_OK) return st;
-  if (!image || !den || !shift || !grad_image || (N > 0 && (!points || !values))) return GMI_ERR_INVALID_ARG;
+  if (!image || !den || (!shift && !per_point) || !grad_image || (N > 0 && (!points || !values)))
+    return GMI_ERR_INVALID_ARG;
   if (((uintptr_t)points & 7u) != 0 || ((uintptr_t)values & 3u) != 0) return GMI_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   int mth, mtw;
@@ -354,6 +410,7 @@ extern "C" gmi_status gmi_backward(const float* points, const float* values, int
   fill_geom(g, N, H, W, p->sigma, p->radius_sigmas, p->bin_px, mth, mtw);
   g.points = points;
   g.values = values;
+  g.sigmas = sigmas;
   const long long nb = (long long)g.nbx * g.nby;
   const long long mt = (long long)g.mtx * g.mty;
   const long long wt = (long long)g.wtx * g.wty;
@@ -362,6 +419,7 @@ extern "C" gmi_status gmi_backward(const float* points, const float* values, int
   if (grad_points && cudaMemsetAsync(grad_points, 0, sizeof(float) * 2 * (size_t)N, s) != cudaSuccess) return GMI_ERR_CUDA;
   if (grad_values && cudaMemsetAsync(grad_values, 0, sizeof(float) * (size_t)C * (size_t)N, s) != cudaSuccess) return GMI_ERR_CUDA;
   if (grad_sigma && cudaMemsetAsync(grad_sigma, 0, sizeof(float), s) != cudaSuccess) return GMI_ERR_CUDA;
+  if (grad_sigmas && cudaMemsetAsync(grad_sigmas, 0, sizeof(float) * (size_t)N, s) != cudaSuccess) return GMI_ERR_CUDA;
   if (N == 0) return GMI_OK;
 
   KArgs a;
@@ -390,12 +448,35 @@ extern "C" gmi_status gmi_backward(const float* points, const float* values, int
   b.one.gpts = grad_points;
   b.one.gvals = grad_values;
   b.one.gsig = grad_sigma;
+  b.one.gsigs = grad_sigmas;
   b.one.inv_s2 = (float)(1.0 / ((double)p->sigma * p->sigma));
   b.one.inv_s3 = (float)(1.0 / ((double)p->sigma * p->sigma * p->sigma));
   b.table = nullptr;
   b.trunc = trunc ? 1 : 0;
+  b.pp = sigmas ? 1 : 0;
   const ProfileMark pm = profile_begin(GMI_STAGE_BACKWARD, s);
   if (launch_backward(a, b, s) != cudaSuccess) return GMI_ERR_CUDA;
   profile_end(pm, s);
   return (p->flags & GMI_FLAG_SYNC_CHECK) ? read_status(workspace, s) : GMI_OK;
+}
+
+extern "C" gmi_status gmi_backward(const float* points, const float* values, int64_t N, int C, int H, int W,
+                                   const gmi_params* p, const float* image, const float* den, const float* shift,
+                                   const float* grad_image, float* grad_points, float* grad_values,
+                                   float* grad_sigma, void* workspace, size_t ws_bytes, gmi_stream_t stream) {
+  return backward_impl(points, values, nullptr, N, C, H, W, p, image, den, shift, grad_image, grad_points,
+                       grad_values, grad_sigma, nullptr, false, workspace, ws_bytes, stream);
+}
+
+extern "C" gmi_status gmi_backward_pp(const float* points, const float* values, const float* sigmas, int64_t N,
+                                      int C, int H, int W, const gmi_params* p, const float* image,
+                                      const float* den, const float* grad_image, float* grad_points,
+                                      float* grad_values, float* grad_sigmas, void* workspace, size_t ws_bytes,
+                                      gmi_stream_t stream) {
+  gmi_status st = check_params(p);
+  if (st != GMI_OK) return st;
+  if (p->mode != GMI_MODE_TRUNCATED) return GMI_ERR_UNSUPPORTED;
+  if (N > 0 && (!sigmas || ((uintptr_t)sigmas & 3u) != 0)) return GMI_ERR_INVALID_ARG;
+  return backward_impl(points, values, N > 0 ? sigmas : nullptr, N, C, H, W, p, image, den, nullptr, grad_image,
+                       grad_points, grad_values, nullptr, grad_sigmas, true, workspace, ws_bytes, stream);
 }

@@ -5,8 +5,8 @@
 // section 2) is what makes spatial binning sufficient.
 //
 //   bin_count    key = (clamped bin row, bin column); rank = atomic slot in the
-//                bin; flags non-finite inputs and bins holding out-of-frame
-//                points
+//                bin; flags non-finite inputs, per-point sigmas out of range
+//                and bins holding out-of-frame points
 //   scan_partial per-block sums of the bin counts
 //   scan_final   exclusive scan of the counts, in place, into bin offsets
 //   bin_scatter  bin-sorted copies of positions (float2) and colours (float4)
@@ -16,7 +16,7 @@ namespace gmi {
 
 __global__ void __launch_bounds__(256) bin_count_kernel(KArgs a_in) {
   const KArgs a = resolve(a_in);
-  unsigned bad = 0;
+  unsigned bad = 0, bad_sigma = 0;
   for (long long ch = blockIdx.x; ch < a.ch_total; ch += gridDim.x) {
     const int img = find_image<0>(a, ch);
     const ImageGeom& g = *geom_ptr(a, img);
@@ -25,6 +25,11 @@ __global__ void __launch_bounds__(256) bin_count_kernel(KArgs a_in) {
       float2 p = reinterpret_cast<const float2*>(g.points)[i];
       bool fin = isfinite(p.x) && isfinite(p.y);
       for (int c = 0; c < a.C; ++c) fin = fin && isfinite(g.values[i * a.C + c]);
+      if (g.sigmas) {
+        const float si = g.sigmas[i];
+        fin = fin && isfinite(si);
+        if (isfinite(si) && !(si <= g.sigma && si >= g.sigma * 0x1p-32f)) bad_sigma = 1;
+      }
       if (!fin) bad = 1;
       long long bin;
       bool oob;
@@ -34,6 +39,7 @@ __global__ void __launch_bounds__(256) bin_count_kernel(KArgs a_in) {
     }
   }
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&a.w.status[kStatusErr], ST_NONFINITE);
+  if (__any_sync(0xffffffffu, bad_sigma) && (threadIdx.x & 31) == 0) atomicOr(&a.w.status[kStatusErr], ST_SIGMA);
 }
 
 // Sum of kScanChunk consecutive counts per block.

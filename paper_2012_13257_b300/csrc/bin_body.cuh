@@ -36,6 +36,7 @@ static __device__ __forceinline__ void bin_scatter_body(const KArgs& a, int nblo
       a.w.sxy[dst] = p;
       a.w.sval[dst] = c;
       a.w.perm[dst] = (unsigned)i;
+      if (g.sigmas) a.w.spp[dst] = pp_consts(g.sigma, g.sigmas[i]);
     }
   }
 }

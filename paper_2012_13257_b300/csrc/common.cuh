@@ -20,6 +20,7 @@ enum : unsigned {
   ST_NONFINITE = 1u,   // NaN/Inf among point coordinates or values
   ST_INTERNAL = 2u,    // a consistency check failed (e.g. a list overflowed)
   ST_TIMEOUT = 4u,     // a bounded wait gave up
+  ST_SIGMA = 8u,       // a per-point sigma outside [sigma * 2^-32, sigma]
 };
 
 // Slots of the status/counter block at the start of every workspace.
@@ -44,6 +45,7 @@ struct ImageGeom {
   float* image;          // [H,W,C]
   float* den;            // [H,W] or null
   float* shift;          // [H,W] or null
+  const float* sigmas;   // [n] per-point sigma (bounded by `sigma`), or null: all equal `sigma`
   long long n;           // points of this image
   long long pt_base;     // first point in the concatenated point space
   long long bin_base;    // first bin in the concatenated bin space
@@ -55,13 +57,13 @@ struct ImageGeom {
   int mtx, mty;          // micro-tiles across / down
   int wtx, wty;          // warp tiles across / down (8 x 4 micro-tiles each)
   float inv_b;           // 1 / b
-  float sigma;
+  float sigma;           // the shared sigma; with per-point sigmas their upper bound
   float kappa;           // log2(e) / (2 sigma^2)
   float sk;              // sqrt(kappa)
   float r2k;             // (k sigma)^2
   float u_near_max;      // largest nearest-distance bound the near kernel accepts
+  float e_trunc;         // k^2 log2(e) / 2: per-point sigma keeps kappa_i d^2 <= this
   int vec_ok;            // rows of image/den/shift may use 16-byte stores
-  int pad_;
   long long px_base;     // first pixel in the concatenated pixel space
   long long mt_base;     // first micro-tile in the concatenated micro-tile space
 };
@@ -82,6 +84,8 @@ struct DevWork {
   float* ubound;         // [wt_total * 32]: per micro-tile bound U on the nearest squared
                          //   distance (+inf: far-field micro-tile), written by the plan
   unsigned* perm;        // [n_total]: input index of each bin-sorted point
+  float2* spp;           // [n_total]: per-point sigma constants of each bin-sorted point
+                         //   (sqrt(kappa_i), log2(sigma^2 / sigma_i^2)); written only with sigmas
   // backward pass only
   float4* pplane;        // [pixels * (C == 4 ? 2 : 1)]: g_c / den and s' per core pixel
   unsigned* fbflag;      // [mt_total]: micro-tile holds a non-core pixel
@@ -185,6 +189,17 @@ __device__ __forceinline__ float shifted_sqdist(float qx, float qy, float px, fl
   lo = __fmaf_rn(2.0f * sx, ex, lo);
   lo = __fmaf_rn(2.0f * sy, ey, lo);
   return __fadd_rn(u, lo);
+}
+
+// Per-point sigma (Eq. 2 with sigma_i in place of the shared sigma): the
+// weight of point i at squared distance d^2 is N(q | mu_i, sigma_i^2 I), which
+// up to the common factor 2 pi / sigma^2 (it cancels in Eq. 1) is
+//   2^(la_i - kappa_i d^2),  kappa_i = log2(e) / (2 sigma_i^2),
+//   la_i = log2(sigma^2 / sigma_i^2) >= 0,
+// sigma being the bound given with the call.  Returns (sqrt(kappa_i), la_i).
+__device__ __forceinline__ float2 pp_consts(float sigma, float sigma_i) {
+  constexpr float kSqrtHalfLog2e = 0.84932180028801907f;   // sqrt(log2(e) / 2)
+  return make_float2(kSqrtHalfLog2e / sigma_i, 2.0f * log2f(sigma / sigma_i));
 }
 
 // Bin coordinate of a position along one axis, clamped to [0, nb-1]; NaN maps to 0.

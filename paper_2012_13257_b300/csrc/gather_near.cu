@@ -31,6 +31,11 @@
 //
 // In truncated mode (the literal "radius k sigma" reading) R = k sigma, each
 // pixel keeps only points with d^2 <= k^2 sigma^2, and nothing is queued.
+//
+// Per-point sigma (truncated mode only): point i weighs 2^(la_i - kappa_i d^2)
+// (pp_consts) and counts where d^2 <= k^2 sigma_i^2; the candidate window is
+// that of the bound sigma >= sigma_i, and the factorisation is unchanged:
+// gx = 2^(-kappa_i dx^2), gy = 2^(la_i - kappa_i dy^2).
 #include "bin_body.cuh"
 
 namespace gmi {
@@ -296,8 +301,9 @@ struct NearOcc {
 
 constexpr int kNearWarps = 4;   // warps per near-kernel block
 
-template <int MTH, int MTW, int C, bool TRUNC>
+template <int MTH, int MTW, int C, bool TRUNC, bool PP>
 __global__ void __launch_bounds__(128, NearOcc<MTH, MTW, C>::value) near_kernel(KArgs a_in) {
+  static_assert(TRUNC || !PP, "per-point sigma is built for truncated mode only");
   const KArgs a = resolve(a_in);
   constexpr int NA = MTH * MTW * (C + 1);   // accumulators per thread
   constexpr int NP = (C + 1) / 2;           // packed accumulator pairs per pixel
@@ -345,11 +351,13 @@ __global__ void __launch_bounds__(128, NearOcc<MTH, MTW, C>::value) near_kernel(
 #pragma unroll
     for (int k = 0; k < MTH * MTW * ODD + 1 - ODD; ++k) accs[k] = 0.0f;
 
-    // one candidate point (position p, colour cv) into every pixel of the micro-tile
-    const float sk = g.sk;
-    const float neg_thr = -g.kappa * g.r2k;   // truncated mode: keep -kappa d^2 >= this
+    // one candidate point (position p, colour cv, per-point sigma constants
+    // spc when PP) into every pixel of the micro-tile
+    // truncated mode: keep -kappa d^2 >= this
+    const float neg_thr = PP ? -g.e_trunc : -g.kappa * g.r2k;
     const float xq0 = (float)x0 + 0.5f, yq0 = (float)y0 + 0.5f;
-    auto consume = [&](const float2 p, const float4 cv) {
+    auto consume = [&](const float2 p, const float4 cv, const float2 spc) {
+      const float sk = PP ? spc.x : g.sk;
       const float c4[4] = {cv.x, cv.y, cv.z, cv.w};
       float2 cp[NP];   // (1, c_0), (c_1, c_2)
       cp[0] = make_float2(1.0f, c4[0]);
@@ -359,17 +367,19 @@ __global__ void __launch_bounds__(128, NearOcc<MTH, MTW, C>::value) near_kernel(
       const float u = (xq0 - p.x) * sk;
       const float v = (yq0 - p.y) * sk;
       float ax[MTW], gx[MTW], ay[MTH], gy[MTH];
+      // (per-point sigma: explicit roundings, which the backward pass repeats
+      // to keep exactly the same pairs)
 #pragma unroll
       for (int j = 0; j < MTW; ++j) {
-        const float tt = u + (float)j * sk;
-        ax[j] = -tt * tt;
+        const float tt = PP ? __fmaf_rn((float)j, sk, u) : u + (float)j * sk;
+        ax[j] = PP ? __fmul_rn(-tt, tt) : -tt * tt;
         gx[j] = ex2(ax[j]);
       }
 #pragma unroll
       for (int r = 0; r < MTH; ++r) {
-        const float tt = v + (float)r * sk;
-        ay[r] = -tt * tt;
-        gy[r] = ex2(ay[r]);
+        const float tt = PP ? __fmaf_rn((float)r, sk, v) : v + (float)r * sk;
+        ay[r] = PP ? __fmul_rn(-tt, tt) : -tt * tt;
+        gy[r] = ex2(PP ? __fadd_rn(ay[r], spc.y) : ay[r]);
       }
       if (!TRUNC) {
         // separable weight gy[r] * gx[j]: the column factors times the
@@ -400,7 +410,8 @@ __global__ void __launch_bounds__(128, NearOcc<MTH, MTW, C>::value) near_kernel(
         for (int r = 0; r < MTH; ++r)
 #pragma unroll
           for (int j = 0; j < MTW; ++j) {
-            const float wgt = (ax[j] + ay[r] >= neg_thr) ? gx[j] * gy[r] : 0.0f;
+            const float e = PP ? __fadd_rn(ax[j], ay[r]) : ax[j] + ay[r];
+            const float wgt = (e >= neg_thr) ? gx[j] * gy[r] : 0.0f;
             const float2 ww = make_float2(wgt, wgt);
 #pragma unroll
             for (int q = 0; q < NP; ++q) {
@@ -428,6 +439,7 @@ __global__ void __launch_bounds__(128, NearOcc<MTH, MTW, C>::value) near_kernel(
       }
       const float2* __restrict__ sxy = a.w.sxy;
       const float4* __restrict__ sval = a.w.sval;
+      const float2* __restrict__ spp = a.w.spp;
       int by = w.by_lo - 1;
       unsigned i = 0, end = 0, cum = 0;
       // bounds of the next bin row, loaded one row ahead
@@ -450,16 +462,19 @@ __global__ void __launch_bounds__(128, NearOcc<MTH, MTW, C>::value) near_kernel(
         // the candidate is always loaded one iteration ahead, across bin rows too
         float2 pn = __ldg(&sxy[i]);
         float4 cn = __ldg(&sval[i]);
+        float2 sn = PP ? __ldg(&spp[i]) : make_float2(0.f, 0.f);
         bool more = true;
         while (more) {
           const float2 p = pn;
           const float4 cv = cn;
+          const float2 spc = sn;
           if (++i >= end) more = next_row();
           if (more) {
             pn = __ldg(&sxy[i]);
             cn = __ldg(&sval[i]);
+            if (PP) sn = __ldg(&spp[i]);
           }
-          consume(p, cv);
+          consume(p, cv, spc);
         }
       }
     }
@@ -561,34 +576,39 @@ __global__ void __launch_bounds__(128, NearOcc<MTH, MTW, C>::value) near_kernel(
 
 // Resident blocks per SM of one near-kernel instantiation (register-limited,
 // as the launch bounds ask), cached; all devices of a process are taken to be alike.
-template <int MTH, int MTW, int C, bool TRUNC>
+template <int MTH, int MTW, int C, bool TRUNC, bool PP>
 static int near_occ() {
   static const int n = [] {
     int b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, near_kernel<MTH, MTW, C, TRUNC>, 32 * kNearWarps, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, near_kernel<MTH, MTW, C, TRUNC, PP>, 32 * kNearWarps, 0);
     return b > 0 ? b : 1;
   }();
   return n;
 }
 
-template <int MTH, int MTW, int C, bool TRUNC>
+template <int MTH, int MTW, int C, bool TRUNC, bool PP>
 static cudaError_t launch_near_k(const KArgs& a, int grid, cudaStream_t s) {
-  near_kernel<MTH, MTW, C, TRUNC><<<grid, 32 * kNearWarps, 0, s>>>(a);
+  near_kernel<MTH, MTW, C, TRUNC, PP><<<grid, 32 * kNearWarps, 0, s>>>(a);
   return cudaGetLastError();
 }
 
+// mode: 0 exact, 1 truncated, 2 truncated with per-point sigma
 template <int MTH, int MTW, int C>
-static cudaError_t launch_near_c(const KArgs& a, bool trunc, int grid, cudaStream_t s) {
-  return trunc ? launch_near_k<MTH, MTW, C, true>(a, grid, s) : launch_near_k<MTH, MTW, C, false>(a, grid, s);
+static cudaError_t launch_near_c(const KArgs& a, int mode, int grid, cudaStream_t s) {
+  switch (mode) {
+    case 0: return launch_near_k<MTH, MTW, C, false, false>(a, grid, s);
+    case 1: return launch_near_k<MTH, MTW, C, true, false>(a, grid, s);
+    default: return launch_near_k<MTH, MTW, C, true, true>(a, grid, s);
+  }
 }
 
 template <int MTH, int MTW>
-static cudaError_t launch_near_mt(const KArgs& a, bool trunc, int grid, cudaStream_t s) {
+static cudaError_t launch_near_mt(const KArgs& a, int mode, int grid, cudaStream_t s) {
   switch (a.C) {
-    case 1: return launch_near_c<MTH, MTW, 1>(a, trunc, grid, s);
-    case 2: return launch_near_c<MTH, MTW, 2>(a, trunc, grid, s);
-    case 3: return launch_near_c<MTH, MTW, 3>(a, trunc, grid, s);
-    default: return launch_near_c<MTH, MTW, 4>(a, trunc, grid, s);
+    case 1: return launch_near_c<MTH, MTW, 1>(a, mode, grid, s);
+    case 2: return launch_near_c<MTH, MTW, 2>(a, mode, grid, s);
+    case 3: return launch_near_c<MTH, MTW, 3>(a, mode, grid, s);
+    default: return launch_near_c<MTH, MTW, 4>(a, mode, grid, s);
   }
 }
 
@@ -603,34 +623,42 @@ cudaError_t launch_scatter_plan(const KArgs& a, bool trunc, int n_scatter, cudaS
   return cudaGetLastError();
 }
 
-cudaError_t launch_near(const KArgs& a, int mth, int mtw, bool trunc, int grid, cudaStream_t s) {
-  if (mth == 4 && mtw == 4) return launch_near_mt<4, 4>(a, trunc, grid, s);
-  if (mth == 4 && mtw == 8) return launch_near_mt<4, 8>(a, trunc, grid, s);
-  if (mth == 2 && mtw == 4) return launch_near_mt<2, 4>(a, trunc, grid, s);
+static int near_mode(bool trunc, bool pp) { return pp ? 2 : (trunc ? 1 : 0); }
+
+cudaError_t launch_near(const KArgs& a, int mth, int mtw, bool trunc, bool pp, int grid, cudaStream_t s) {
+  const int m = near_mode(trunc, pp);
+  if (mth == 4 && mtw == 4) return launch_near_mt<4, 4>(a, m, grid, s);
+  if (mth == 4 && mtw == 8) return launch_near_mt<4, 8>(a, m, grid, s);
+  if (mth == 2 && mtw == 4) return launch_near_mt<2, 4>(a, m, grid, s);
   return cudaErrorInvalidValue;
 }
 
 // Resident near-kernel blocks per SM for an instantiation (cached).
 template <int MTH, int MTW, int C>
-static int occ_c(bool trunc) {
-  return trunc ? near_occ<MTH, MTW, C, true>() : near_occ<MTH, MTW, C, false>();
-}
-
-template <int MTH, int MTW>
-static int occ_mt(int C, bool trunc) {
-  switch (C) {
-    case 1: return occ_c<MTH, MTW, 1>(trunc);
-    case 2: return occ_c<MTH, MTW, 2>(trunc);
-    case 3: return occ_c<MTH, MTW, 3>(trunc);
-    default: return occ_c<MTH, MTW, 4>(trunc);
+static int occ_c(int mode) {
+  switch (mode) {
+    case 0: return near_occ<MTH, MTW, C, false, false>();
+    case 1: return near_occ<MTH, MTW, C, true, false>();
+    default: return near_occ<MTH, MTW, C, true, true>();
   }
 }
 
-int near_blocks_per_sm(int mth, int mtw, int C, bool trunc) {
+template <int MTH, int MTW>
+static int occ_mt(int C, int mode) {
+  switch (C) {
+    case 1: return occ_c<MTH, MTW, 1>(mode);
+    case 2: return occ_c<MTH, MTW, 2>(mode);
+    case 3: return occ_c<MTH, MTW, 3>(mode);
+    default: return occ_c<MTH, MTW, 4>(mode);
+  }
+}
+
+int near_blocks_per_sm(int mth, int mtw, int C, bool trunc, bool pp) {
   const int c = C < 1 ? 1 : (C > 4 ? 4 : C);
-  if (mth == 4 && mtw == 8) return occ_mt<4, 8>(c, trunc);
-  if (mth == 2 && mtw == 4) return occ_mt<2, 4>(c, trunc);
-  return occ_mt<4, 4>(c, trunc);
+  const int m = near_mode(trunc, pp);
+  if (mth == 4 && mtw == 8) return occ_mt<4, 8>(c, m);
+  if (mth == 2 && mtw == 4) return occ_mt<2, 4>(c, m);
+  return occ_mt<4, 4>(c, m);
 }
 
 }  // namespace gmi
