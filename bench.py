@@ -59,7 +59,8 @@ def parse():
     ap.add_argument("--impl", default="gmi", choices=["gmi", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="headline workload only")
-    ap.add_argument("--only", choices=["batched", "fwd_bwd", "serving", "reconstruction", "point_optimization"],
+    ap.add_argument("--only", choices=["batched", "fwd_bwd", "serving", "reconstruction", "point_optimization",
+                                       "per_point_sigma"],
                     help="run only this secondary workload and print its object (for profiling it)")
     return ap.parse_args()
 
@@ -417,6 +418,53 @@ def bench_fwd_bwd(dev, steps, warmup, flush, stream):
                         "torch.autograd.Function (list-batched and per-image autograd ops for comparison)"}
 
 
+def bench_per_point_sigma(dev, steps, warmup, flush, stream, lo=0.5, hi=1.5, k=3.0):
+    """The 1024^2 upsampling workload with a sigma per point (log-uniform in
+    [lo, hi] px, bound hi, truncated at k sigma_i): the graph-replayed forward
+    and forward + backward (positions, values, every sigma_i) through the
+    autograd op, beside the same calls with one shared sigma = hi (the same
+    search window)."""
+    import torch
+    import paper_2012_13257_b300 as gmi
+    import workloads as wl
+    im = wl.upsample_1024()
+    P = torch.as_tensor(im.points, device=dev)
+    V = torch.as_tensor(im.values, device=dev)
+    S = torch.as_tensor(wl.point_sigmas(22, im.N, lo, hi), device=dev)
+    out = torch.empty((im.H, im.W, im.C), dtype=torch.float32, device=dev)
+    G = torch.randn((im.H, im.W, im.C), generator=torch.Generator(device=dev).manual_seed(9), device=dev)
+
+    def fwd_pp():
+        gmi.interpolate_pp(P, V, S, hi, im.H, im.W, radius_sigmas=k, graph=True, out=out)
+
+    def fwd_shared():
+        gmi.interpolate(P, V, hi, im.H, im.W, mode="truncated", radius_sigmas=k, graph=True, out=out)
+
+    Pg, Vg, Sg = (t.clone().requires_grad_(True) for t in (P, V, S))
+    sg = torch.tensor(hi, dtype=torch.float32, device=dev, requires_grad=True)
+
+    def fb_pp():
+        gmi.gmi_interpolate_pp(Pg, Vg, Sg, hi, im.H, im.W, radius_sigmas=k).backward(G)
+
+    def fb_shared():
+        gmi.gmi_interpolate(Pg, Vg, sg, im.H, im.W, mode="truncated", radius_sigmas=k).backward(G)
+
+    res = {}
+    for name, fn in (("forward_pp", fwd_pp), ("forward_shared", fwd_shared), ("fwd_bwd_pp", fb_pp),
+                     ("fwd_bwd_shared", fb_shared)):
+        for _ in range(max(3, warmup)):
+            fn()
+        torch.cuda.synchronize()
+        t = timed_steps(fn, steps, flush, stream)
+        ms = sum(t) / len(t)
+        res[name] = {"ms_per_step": ms, "value": im.H * im.W / (ms * 1e-3) / 1e6}
+    res["unit"] = "Mpix/s"
+    res["workload"] = ("1024x1024x3 f32 from 262,144 jittered-grid points, sigma_i log-uniform in [%g, %g] px "
+                       "(bound %g), truncated at %g sigma_i; shared-sigma rows use sigma = %g with the same "
+                       "window; fwd_bwd through the autograd ops (positions, values, sigmas), upstream N(0,1)"
+                       % (lo, hi, hi, k, hi))
+    return res
+
 def bench_reconstruction(dev, side=768, factors=(2, 3, 4, 6, 8), sigma_scales=(0.2, 0.25, 0.35, 0.5, 0.7)):
     """Reconstruction quality (the paper's downsample-then-upsample study,
     section 3.2, on a smooth random field instead of ImageNet images): a field
@@ -630,7 +678,8 @@ def main():
               "fwd_bwd": lambda: bench_fwd_bwd(dev, args.steps, args.warmup, flush, stream),
               "serving": lambda: bench_serving(dev),
               "reconstruction": lambda: bench_reconstruction(dev),
-              "point_optimization": lambda: bench_point_optimization(dev)}[args.only]
+              "point_optimization": lambda: bench_point_optimization(dev),
+              "per_point_sigma": lambda: bench_per_point_sigma(dev, args.steps, args.warmup, flush, stream)}[args.only]
         if rank == 0:
             print(json.dumps({args.only: fn()}), flush=True)
         D.close()
@@ -760,7 +809,9 @@ def main():
                          ("fwd_bwd", lambda: bench_fwd_bwd(dev, args.steps, args.warmup, flush, stream)),
                          ("serving", lambda: bench_serving(dev)),
                          ("reconstruction", lambda: bench_reconstruction(dev)),
-                         ("point_optimization", lambda: bench_point_optimization(dev))):
+                         ("point_optimization", lambda: bench_point_optimization(dev)),
+                         ("per_point_sigma", lambda: bench_per_point_sigma(dev, args.steps, args.warmup, flush,
+                                                                           stream))):
             try:
                 line[name] = fn()
             except Exception as e:   # a failed extra must not hide the headline
