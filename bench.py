@@ -418,6 +418,33 @@ def bench_fwd_bwd(dev, steps, warmup, flush, stream):
                         "torch.autograd.Function (list-batched and per-image autograd ops for comparison)"}
 
 
+def pp_pairs(im, sig, k):
+    """Pairs (pixel, point) with d <= k sigma_i: the per-point truncated
+    method's work, counted with a k-d tree over the pixel centres."""
+    from scipy.spatial import cKDTree
+    yy, xx = np.meshgrid(np.arange(im.H) + 0.5, np.arange(im.W) + 0.5, indexing="ij")
+    tree = cKDTree(np.stack([xx.ravel(), yy.ravel()], 1))
+    cnt = tree.query_ball_point(im.points.astype(np.float64), k * sig.astype(np.float64), return_length=True,
+                                workers=-1)
+    return int(np.sum(cnt))
+
+
+def pp_oracle_rate(im, sig, k, target_s=4.0):
+    """The FP64 per-point oracle on a bounded random pixel sample (Mpix/s)."""
+    import oracle
+    rng = np.random.default_rng(321)
+    n = 64
+    while True:
+        pix = rng.integers(0, im.H * im.W, n)
+        t0 = time.perf_counter()
+        oracle.forward_pp(im.points, im.values, sig, im.H, im.W, mode=oracle.TRUNCATED, k=k, pixels=pix)
+        t = time.perf_counter() - t0
+        if t >= target_s or n >= 1 << 20:
+            break
+        n = int(n * min(8.0, max(1.2, 1.2 * target_s / max(t, 1e-3))))
+    return {"value": n / t / 1e6, "unit": "Mpix/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": "%d random pixels, %.1f s" % (n, t)}
+
 def bench_per_point_sigma(dev, steps, warmup, flush, stream, lo=0.5, hi=1.5, k=3.0):
     """The 1024^2 upsampling workload with a sigma per point (log-uniform in
     [lo, hi] px, bound hi, truncated at k sigma_i): the graph-replayed forward
@@ -459,6 +486,34 @@ def bench_per_point_sigma(dev, steps, warmup, flush, stream, lo=0.5, hi=1.5, k=3
         ms = sum(t) / len(t)
         res[name] = {"ms_per_step": ms, "value": im.H * im.W / (ms * 1e-3) / 1e6}
     res["unit"] = "Mpix/s"
+    # near-kernel time of the per-point forward (stage events, queued behind a
+    # device spin), against the algorithmic pairs d <= k sigma_i
+    from paper_2012_13257_b300 import _lib
+    L = _lib.load()
+    L.gmi_profile_enable(1)
+    L.gmi_profile_read(None, None, 1)
+    torch.cuda._sleep(int(steps * 200e-6 * SM_MAX_MHZ * 1e6))
+    for _ in range(steps):
+        flush.zero_()
+        gmi.interpolate_pp(P, V, S, hi, im.H, im.W, radius_sigmas=k, out=out)
+    torch.cuda.synchronize()
+    st_ms = (ctypes.c_double * 4)()
+    st_n = (ctypes.c_int * 4)()
+    L.gmi_profile_read(st_ms, st_n, 1)
+    L.gmi_profile_enable(0)
+    near_ms = st_ms[1] / max(1, st_n[1])
+    sig = S.cpu().numpy()
+    pairs = pp_pairs(im, sig, k)
+    clk = SM_MAX_MHZ
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = sms * FP32_PER_SM_CLK / FP32_OPS_PER_PAIR * clk * 1e6 / 1e9
+    achieved = pairs / (near_ms * 1e-3) / 1e9 if near_ms > 0 else None
+    res["roofline"] = {"bound": "alu", "kernel": "near_kernel<4,4,3,truncated,per-point>", "launch_ms": near_ms,
+                       "pairs_per_launch": pairs, "achieved": achieved, "peak": peak, "unit": "Gpair/s",
+                       "frac": achieved / peak if achieved else None,
+                       "peak_basis": "FP32 pipe at the maximum SM clock %d MHz (%d SMs x %d / %d ops per pair)"
+                                     % (clk, sms, FP32_PER_SM_CLK, FP32_OPS_PER_PAIR)}
+    res["oracle"] = pp_oracle_rate(im, sig, k)
     res["workload"] = ("1024x1024x3 f32 from 262,144 jittered-grid points, sigma_i log-uniform in [%g, %g] px "
                        "(bound %g), truncated at %g sigma_i; shared-sigma rows use sigma = %g with the same "
                        "window; fwd_bwd through the autograd ops (positions, values, sigmas), upstream N(0,1)"
