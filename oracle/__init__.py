@@ -9,7 +9,11 @@ It shares no code with the CUDA library.
 Every function here is pinned by ``tests/test_oracle.py`` against closed forms,
 invariants and library routines (see that file's docstring).  Parity status of
 each function: forward exact/truncated pinned; backward pinned (finite
-differences and torch autograd); pair counts pinned against a k-d tree count.
+differences and torch autograd); pair counts pinned against a k-d tree count;
+the per-point and anisotropic extensions (forward_pp, backward_pp,
+forward_aniso, backward_aniso) pinned by their reductions to the shared-sigma
+and isotropic forms, closed forms, an independent torch evaluation with
+autograd and finite differences.
 """
 from __future__ import annotations
 
@@ -66,6 +70,10 @@ def _load():
                                                ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_double,
                                                f32p, f64p, f64p, f64p]
             lib.oracle_backward_pp.restype = ctypes.c_int
+            lib.oracle_forward_aniso.argtypes = lib.oracle_forward_pp.argtypes
+            lib.oracle_forward_aniso.restype = ctypes.c_int
+            lib.oracle_backward_aniso.argtypes = lib.oracle_backward_pp.argtypes
+            lib.oracle_backward_aniso.restype = ctypes.c_int
             lib.oracle_num_threads.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -200,3 +208,59 @@ def backward_pp(points, values, sigmas, H: int, W: int, grad, mode: int = EXACT,
     if rc != 0:
         raise ValueError("oracle_backward_pp rejected its arguments (rc=%d)" % rc)
     return {"points": gp, "values": gv, "sigmas": gs}
+
+
+def forward_aniso(points, values, sigmas_xy, H: int, W: int, mode: int = EXACT, k: float = 6.0, pixels=None):
+    """Eq. 1 / Eq. 2 with an axis-aligned covariance diag(sx_i^2, sy_i^2)
+    per point (``sigmas_xy[N,2]``, normalisers kept; see
+    ``oracle_forward_aniso``).  Same outputs as ``forward_pp``."""
+    lib = _load()
+    pts = _f32(points).reshape(-1, 2)
+    N = pts.shape[0]
+    vals = _f32(values).reshape(N, -1) if N else _f32(values).reshape(0, np.asarray(values).shape[-1])
+    C = int(vals.shape[1])
+    sig = _f32(sigmas_xy).reshape(N, 2)
+    if pixels is None:
+        n = H * W
+        pix = None
+    else:
+        pix = np.ascontiguousarray(np.asarray(pixels, dtype=np.int64).ravel())
+        n = pix.size
+    out = np.empty((n, C), np.float64)
+    den = np.empty(n, np.float64)
+    shift = np.empty(n, np.float64)
+    skipped = np.empty(n, np.float64)
+    pairs = np.empty(n, np.int64)
+    rc = lib.oracle_forward_aniso(_ptr(pts, ctypes.c_float), _ptr(vals, ctypes.c_float),
+                                  _ptr(sig, ctypes.c_float), N, C, H, W, int(mode), float(k),
+                                  _ptr(pix, ctypes.c_int64), n, _ptr(out, ctypes.c_double),
+                                  _ptr(den, ctypes.c_double), _ptr(shift, ctypes.c_double),
+                                  _ptr(skipped, ctypes.c_double), _ptr(pairs, ctypes.c_int64))
+    if rc != 0:
+        raise ValueError("oracle_forward_aniso rejected its arguments (rc=%d)" % rc)
+    if pixels is None:
+        out, den, shift = out.reshape(H, W, C), den.reshape(H, W), shift.reshape(H, W)
+        skipped, pairs = skipped.reshape(H, W), pairs.reshape(H, W)
+    return {"image": out, "den": den, "shift": shift, "skipped": skipped, "pairs": pairs}
+
+
+def backward_aniso(points, values, sigmas_xy, H: int, W: int, grad, mode: int = EXACT, k: float = 6.0):
+    """Analytic gradient of sum(grad * image) w.r.t. points, values and the
+    per-point (sx, sy)."""
+    lib = _load()
+    pts = _f32(points).reshape(-1, 2)
+    N = pts.shape[0]
+    vals = _f32(values).reshape(N, -1)
+    C = vals.shape[1]
+    sig = _f32(sigmas_xy).reshape(N, 2)
+    g = _f32(grad).reshape(H, W, C)
+    gp = np.zeros((N, 2), np.float64)
+    gv = np.zeros((N, C), np.float64)
+    gs = np.zeros((N, 2), np.float64)
+    rc = lib.oracle_backward_aniso(_ptr(pts, ctypes.c_float), _ptr(vals, ctypes.c_float),
+                                   _ptr(sig, ctypes.c_float), N, C, H, W, int(mode), float(k),
+                                   _ptr(g, ctypes.c_float), _ptr(gp, ctypes.c_double), _ptr(gv, ctypes.c_double),
+                                   _ptr(gs, ctypes.c_double))
+    if rc != 0:
+        raise ValueError("oracle_backward_aniso rejected its arguments (rc=%d)" % rc)
+    return {"points": gp, "values": gv, "sigmas_xy": gs}

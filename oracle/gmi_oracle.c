@@ -430,3 +430,185 @@ int oracle_backward_pp(const float* points, const float* values, const float* si
     free(wbuf_all);
     return 0;
 }
+
+/*
+ * Anisotropic (axis-aligned) extension: point i is N(mu_i, diag(sx_i^2,
+ * sy_i^2)).  Its normaliser 1/(2 pi sx_i sy_i) is kept; with the common
+ * 1/(2 pi) cancelled,
+ *     ln w_i(q) = -dx^2 / (2 sx_i^2) - dy^2 / (2 sy_i^2) - ln sx_i - ln sy_i,
+ *     c(q) = sum_i w_i c_i / sum_i w_i                          (Eq. 1)
+ * dx = qx - x_i, dy = qy - y_i.  EXACT: all points, relative to the largest
+ * weight at q (den >= 1, shift = L = max ln w_i).  TRUNCATED: only points
+ * inside their ellipse, dx^2/sx^2 + dy^2/sy^2 <= k^2, unshifted; skipped and
+ * pairs as for oracle_forward_pp (the ellipse's Mahalanobis radius in place
+ * of d^2 <= k^2 sigma^2).  sigmas_xy [N,2] = (sx, sy), each > 0.
+ */
+static double maha2(double dx, double dy, double sx, double sy) { return dx * dx / (sx * sx) + dy * dy / (sy * sy); }
+static double log_weight_an(double dx, double dy, double sx, double sy) {
+    return -0.5 * maha2(dx, dy, sx, sy) - log(sx) - log(sy);
+}
+
+int oracle_forward_aniso(const float* points, const float* values, const float* sigmas_xy, int64_t N, int C,
+                         int64_t H, int64_t W, int mode, double k, const int64_t* pix, int64_t n_pix,
+                         double* out, double* den, double* shift, double* skipped, int64_t* pairs) {
+    if (N < 0 || C < 1 || H < 1 || W < 1 || !(k > 0) || (N > 0 && !sigmas_xy)) return -1;
+    if (mode != ORACLE_EXACT && mode != ORACLE_TRUNCATED) return -1;
+    for (int64_t i = 0; i < 2 * N; ++i)
+        if (!((double)sigmas_xy[i] > 0)) return -1;
+    if (pix == NULL) n_pix = H * W;
+
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t t = 0; t < n_pix; ++t) {
+        int64_t p = pix ? pix[t] : t;
+        double qx, qy;
+        pixel_centre(p, W, &qx, &qy);
+        double num[8];
+        double* acc = C <= 8 ? num : (double*)calloc((size_t)C, sizeof(double));
+        for (int c = 0; c < C; ++c) acc[c] = 0.0;
+        double z = 0.0, L = 0.0, skip = 0.0;
+        int64_t cnt = 0;
+        if (N > 0 && mode == ORACLE_EXACT) {
+            L = -INFINITY;
+            for (int64_t i = 0; i < N; ++i) {
+                double lw = log_weight_an(qx - (double)points[2 * i], qy - (double)points[2 * i + 1],
+                                          (double)sigmas_xy[2 * i], (double)sigmas_xy[2 * i + 1]);
+                if (lw > L) L = lw;
+            }
+            for (int64_t i = 0; i < N; ++i) {
+                double w = exp(log_weight_an(qx - (double)points[2 * i], qy - (double)points[2 * i + 1],
+                                             (double)sigmas_xy[2 * i], (double)sigmas_xy[2 * i + 1]) - L);
+                z += w;
+                ++cnt;
+                for (int c = 0; c < C; ++c) acc[c] += w * (double)values[i * C + c];
+            }
+            for (int c = 0; c < C; ++c) acc[c] /= z;
+        } else if (N > 0) {
+            double amb = 0.0;
+            for (int64_t i = 0; i < N; ++i) {
+                double sx = (double)sigmas_xy[2 * i], sy = (double)sigmas_xy[2 * i + 1];
+                double dx = qx - (double)points[2 * i], dy = qy - (double)points[2 * i + 1];
+                double m2 = maha2(dx, dy, sx, sy);
+                double r2 = k * k;
+                if (fabs(m2 - r2) <= 1e-5 * r2) amb += exp(log_weight_an(dx, dy, sx, sy));
+                if (m2 > r2) continue;
+                double w = exp(log_weight_an(dx, dy, sx, sy));
+                z += w;
+                ++cnt;
+                for (int c = 0; c < C; ++c) acc[c] += w * (double)values[i * C + c];
+            }
+            if (z > 0) {
+                for (int c = 0; c < C; ++c) acc[c] /= z;
+                skip = amb / z;
+            } else {
+                for (int c = 0; c < C; ++c) acc[c] = 0.0;
+                skip = amb > 0 ? 1.0 : 0.0;
+            }
+        }
+        if (out)
+            for (int c = 0; c < C; ++c) out[t * C + c] = acc[c];
+        if (den) den[t] = z;
+        if (shift) shift[t] = L;
+        if (skipped) skipped[t] = skip;
+        if (pairs) pairs[t] = cnt;
+        if (acc != num) free(acc);
+    }
+    return 0;
+}
+
+/*
+ * Backward pass of the anisotropic extension, by the chain rule on Eq. 1:
+ * with t_i(q) = sum_c (g_c(q) / Z_q) (c_{i,c} - c_c(q)),
+ *   d ln w_i / d x_i  = dx / sx_i^2,      d ln w_i / d y_i  = dy / sy_i^2,
+ *   d ln w_i / d sx_i = dx^2 / sx_i^3 - 1 / sx_i,
+ *   d ln w_i / d sy_i = dy^2 / sy_i^3 - 1 / sy_i,
+ * and every gradient is sum_q (w_i / Z_q) t_i(q) times that factor
+ * (dL/dc_{i,c} = sum_q (w_i / Z_q) g_c(q)).
+ * Outputs (each may be NULL): gpoints [N,2], gvalues [N,C], gsigmas_xy [N,2].
+ */
+int oracle_backward_aniso(const float* points, const float* values, const float* sigmas_xy, int64_t N, int C,
+                          int64_t H, int64_t W, int mode, double k, const float* grad, double* gpoints,
+                          double* gvalues, double* gsigmas_xy) {
+    if (N < 0 || C < 1 || C > 8 || H < 1 || W < 1 || !(k > 0) || (N > 0 && !sigmas_xy)) return -1;
+    if (mode != ORACLE_EXACT && mode != ORACLE_TRUNCATED) return -1;
+    for (int64_t i = 0; i < 2 * N; ++i)
+        if (!((double)sigmas_xy[i] > 0)) return -1;
+    const int64_t P = H * W;
+    int nt = oracle_num_threads();
+    size_t per = (size_t)N * (size_t)(4 + C) + 1;
+    double* part = (double*)calloc(per * (size_t)nt, sizeof(double));
+    double* wbuf_all = (double*)malloc(sizeof(double) * (size_t)(N > 0 ? N : 1) * (size_t)nt);
+    if (!part || !wbuf_all) { free(part); free(wbuf_all); return -2; }
+
+#pragma omp parallel
+    {
+        int tid = 0;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+#endif
+        double* acc = part + per * (size_t)tid;   /* [N*2 | N*C | N*2] */
+        double* w = wbuf_all + (size_t)(N > 0 ? N : 1) * (size_t)tid;
+        double chat[8], G[8];
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t p = 0; p < P; ++p) {
+            if (N == 0) continue;
+            int any = 0;
+            for (int c = 0; c < C; ++c) any |= grad[p * C + c] != 0.0f;
+            if (!any) continue;
+            double qx, qy;
+            pixel_centre(p, W, &qx, &qy);
+            double L = 0.0;
+            if (mode == ORACLE_EXACT) {
+                L = -INFINITY;
+                for (int64_t i = 0; i < N; ++i) {
+                    double lw = log_weight_an(qx - (double)points[2 * i], qy - (double)points[2 * i + 1],
+                                              (double)sigmas_xy[2 * i], (double)sigmas_xy[2 * i + 1]);
+                    if (lw > L) L = lw;
+                }
+            }
+            double z = 0.0;
+            for (int c = 0; c < C; ++c) chat[c] = 0.0;
+            for (int64_t i = 0; i < N; ++i) {
+                double sx = (double)sigmas_xy[2 * i], sy = (double)sigmas_xy[2 * i + 1];
+                double dx = qx - (double)points[2 * i], dy = qy - (double)points[2 * i + 1];
+                double wi = (mode == ORACLE_TRUNCATED && maha2(dx, dy, sx, sy) > k * k)
+                                ? 0.0 : exp(log_weight_an(dx, dy, sx, sy) - L);
+                w[i] = wi;
+                z += wi;
+                for (int c = 0; c < C; ++c) chat[c] += wi * (double)values[i * C + c];
+            }
+            if (!(z > 0)) continue;
+            for (int c = 0; c < C; ++c) {
+                chat[c] /= z;
+                G[c] = (double)grad[p * C + c] / z;
+            }
+            for (int64_t i = 0; i < N; ++i) {
+                if (w[i] == 0.0) continue;
+                double sx = (double)sigmas_xy[2 * i], sy = (double)sigmas_xy[2 * i + 1];
+                double t = 0.0;
+                for (int c = 0; c < C; ++c) {
+                    acc[2 * N + i * C + c] += w[i] * G[c];
+                    t += G[c] * ((double)values[i * C + c] - chat[c]);
+                }
+                double dx = qx - (double)points[2 * i];
+                double dy = qy - (double)points[2 * i + 1];
+                double wt = w[i] * t;
+                double* gs = acc + (size_t)N * (2 + C);
+                acc[2 * i] += wt * dx / (sx * sx);
+                acc[2 * i + 1] += wt * dy / (sy * sy);
+                gs[2 * i] += wt * (dx * dx / (sx * sx * sx) - 1.0 / sx);
+                gs[2 * i + 1] += wt * (dy * dy / (sy * sy * sy) - 1.0 / sy);
+            }
+        }
+    }
+    for (size_t e = 0; e < per; ++e) {
+        double s = 0.0;
+        for (int t = 0; t < nt; ++t) s += part[per * (size_t)t + e];
+        part[e] = s;
+    }
+    if (gpoints) memcpy(gpoints, part, sizeof(double) * (size_t)N * 2);
+    if (gvalues) memcpy(gvalues, part + 2 * N, sizeof(double) * (size_t)N * (size_t)C);
+    if (gsigmas_xy) memcpy(gsigmas_xy, part + (size_t)N * (2 + C), sizeof(double) * (size_t)N * 2);
+    free(part);
+    free(wbuf_all);
+    return 0;
+}

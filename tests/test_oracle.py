@@ -410,3 +410,139 @@ def test_pp_permutation_invariance():
     a = oracle.forward_pp(pts, vals, sig, 8, 9)["image"]
     b = oracle.forward_pp(pts[perm], vals[perm], sig[perm], 8, 9)["image"]
     np.testing.assert_allclose(a, b, rtol=0, atol=1e-14)
+
+
+# ------------------------------------------- anisotropic (axis-aligned) sigma (extension)
+def _an_case(seed, n, H, W, C=3, lo=0.5, hi=2.0):
+    pts, vals, _ = _pp_case(seed, n, H, W, C=C)
+    rng = np.random.default_rng(seed + 1000)
+    sxy = rng.uniform(lo, hi, (n, 2)).astype(np.float32)
+    return pts, vals, sxy
+
+
+@pytest.mark.parametrize("mode", [oracle.EXACT, oracle.TRUNCATED])
+def test_aniso_equal_axes_reduce_to_per_point(mode):
+    """sx_i = sy_i = sigma_i is the (pinned) per-point isotropic evaluation;
+    the two axis gradients of a point sum to its sigma gradient."""
+    pts, vals, sig = _pp_case(21, 35, 12, 15)
+    sxy = np.stack([sig, sig], 1)
+    k = 6.0 if mode == oracle.EXACT else 2.5
+    a = oracle.forward_aniso(pts, vals, sxy, 12, 15, mode=mode, k=k)
+    b = oracle.forward_pp(pts, vals, sig, 12, 15, mode=mode, k=k)
+    for key in ("image", "den", "shift"):
+        np.testing.assert_allclose(a[key], b[key], rtol=1e-13, atol=1e-13)
+    assert (a["pairs"] == b["pairs"]).all()
+    g = np.random.default_rng(22).standard_normal((12, 15, 3)).astype(np.float32)
+    ga = oracle.backward_aniso(pts, vals, sxy, 12, 15, g, mode=mode, k=k)
+    gb = oracle.backward_pp(pts, vals, sig, 12, 15, g, mode=mode, k=k)
+    np.testing.assert_allclose(ga["points"], gb["points"], rtol=1e-10, atol=1e-12)
+    np.testing.assert_allclose(ga["values"], gb["values"], rtol=1e-10, atol=1e-12)
+    np.testing.assert_allclose(ga["sigmas_xy"].sum(1), gb["sigmas"], rtol=1e-10, atol=1e-12)
+
+
+def test_aniso_single_and_two_points():
+    H, W = 10, 13
+    xx, yy = _grid(H, W)
+    p1 = np.float32([[5.3, 4.1]])
+    c1 = np.float32([[0.3, 0.6, 0.1]])
+    s1 = np.float32([[2.2, 0.7]])
+    sx, sy = float(s1[0, 0]), float(s1[0, 1])
+    dx, dy = xx - float(p1[0, 0]), yy - float(p1[0, 1])
+    r = oracle.forward_aniso(p1, c1, s1, H, W, mode=oracle.TRUNCATED, k=2.0)
+    maha = dx * dx / (sx * sx) + dy * dy / (sy * sy)
+    inside = maha <= 4.0
+    assert inside.sum() > 3 and (~inside).sum() > 3
+    np.testing.assert_allclose(r["image"][inside], np.broadcast_to(c1[0], (inside.sum(), 3)), atol=1e-15)
+    assert (r["image"][~inside] == 0).all()
+    # den is the 2D normal's density (times 2 pi): exp(-maha/2) / (sx sy)
+    np.testing.assert_allclose(r["den"][inside], np.exp(-0.5 * maha[inside]) / (sx * sy), rtol=1e-13)
+    # two points: a logistic sigmoid of the log-weight difference
+    p2 = np.float32([[2.5, 3.2], [9.1, 6.4]])
+    c2 = np.float32([[1.0, 0.0, 0.0], [0.0, 1.0, 0.0]])
+    s2 = np.float32([[0.8, 1.9], [2.4, 1.1]])
+    r2 = oracle.forward_aniso(p2, c2, s2, H, W)
+    p64, s64 = p2.astype(np.float64), s2.astype(np.float64)
+
+    def logw(i):
+        ex, ey = xx - p64[i, 0], yy - p64[i, 1]
+        return -0.5 * (ex * ex / s64[i, 0] ** 2 + ey * ey / s64[i, 1] ** 2) - math.log(s64[i, 0] * s64[i, 1])
+
+    np.testing.assert_allclose(r2["image"][..., 1], expit(logw(1) - logw(0)), rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("mode", [oracle.EXACT, oracle.TRUNCATED])
+def test_aniso_axis_swap_transposes(mode):
+    """Swapping x and y in the points and the sigmas, and H with W, transposes
+    the image and swaps the gradients' axes."""
+    H, W = 11, 8
+    pts, vals, sxy = _an_case(23, 30, H, W)
+    k = 6.0 if mode == oracle.EXACT else 2.0
+    a = oracle.forward_aniso(pts, vals, sxy, H, W, mode=mode, k=k)
+    b = oracle.forward_aniso(pts[:, ::-1].copy(), vals, sxy[:, ::-1].copy(), W, H, mode=mode, k=k)
+    np.testing.assert_allclose(b["image"], a["image"].transpose(1, 0, 2), rtol=0, atol=1e-13)
+    g = np.random.default_rng(24).standard_normal((H, W, 3)).astype(np.float32)
+    ga = oracle.backward_aniso(pts, vals, sxy, H, W, g, mode=mode, k=k)
+    gb = oracle.backward_aniso(pts[:, ::-1].copy(), vals, sxy[:, ::-1].copy(), W, H,
+                               g.transpose(1, 0, 2).copy(), mode=mode, k=k)
+    np.testing.assert_allclose(gb["points"], ga["points"][:, ::-1], rtol=1e-10, atol=1e-12)
+    np.testing.assert_allclose(gb["sigmas_xy"], ga["sigmas_xy"][:, ::-1], rtol=1e-10, atol=1e-12)
+
+
+@pytest.mark.parametrize("mode", [oracle.EXACT, oracle.TRUNCATED])
+def test_aniso_torch_autograd(mode):
+    """An independent FP64 torch evaluation (softmax of the anisotropic
+    log-weights, or masked weights inside the ellipses) and its autograd
+    gradients, including both axes of every point's sigma."""
+    torch = pytest.importorskip("torch")
+    H, W, k = 13, 14, 2.5
+    pts, vals, sxy = _an_case(25, 28, H, W)
+    g = np.random.default_rng(26).standard_normal((H, W, 3)).astype(np.float32)
+    P = torch.tensor(pts, dtype=torch.float64, requires_grad=True)
+    V = torch.tensor(vals, dtype=torch.float64, requires_grad=True)
+    S = torch.tensor(sxy, dtype=torch.float64, requires_grad=True)
+    yy, xx = torch.meshgrid(torch.arange(H, dtype=torch.float64) + 0.5,
+                            torch.arange(W, dtype=torch.float64) + 0.5, indexing="ij")
+    q = torch.stack([xx.reshape(-1), yy.reshape(-1)], 1)
+    e = (q[:, None, :] - P[None]) / S[None]
+    m2 = (e * e).sum(-1)
+    logw = -0.5 * m2 - torch.log(S[:, 0] * S[:, 1])
+    if mode == oracle.EXACT:
+        wgt = torch.softmax(logw, dim=1)
+    else:
+        w = torch.where(m2 <= k * k, torch.exp(logw), torch.zeros_like(m2))
+        z = w.sum(1, keepdim=True)
+        wgt = torch.where(z > 0, w / torch.where(z > 0, z, torch.ones_like(z)), torch.zeros_like(w))
+    img = (wgt @ V).reshape(H, W, 3)
+    (img * torch.tensor(g, dtype=torch.float64)).sum().backward()
+    ref = oracle.forward_aniso(pts, vals, sxy, H, W, mode=mode, k=k)
+    np.testing.assert_allclose(ref["image"], img.detach().numpy(), rtol=0, atol=1e-12)
+    gr = oracle.backward_aniso(pts, vals, sxy, H, W, g, mode=mode, k=k)
+    np.testing.assert_allclose(gr["points"], P.grad.numpy(), rtol=1e-8, atol=1e-10)
+    np.testing.assert_allclose(gr["values"], V.grad.numpy(), rtol=1e-8, atol=1e-10)
+    np.testing.assert_allclose(gr["sigmas_xy"], S.grad.numpy(), rtol=1e-8, atol=1e-10)
+
+
+def test_aniso_sigma_gradient_finite_differences():
+    H, W = 10, 11
+    pts, vals, sxy = _an_case(27, 14, H, W)
+    g = np.random.default_rng(28).standard_normal((H, W, 3)).astype(np.float32)
+
+    def loss(s):
+        return float((oracle.forward_aniso(pts, vals, s, H, W)["image"] * g).sum())
+
+    gr = oracle.backward_aniso(pts, vals, sxy, H, W, g)
+    h = 2.0 ** -10
+    for i, ax in ((0, 0), (4, 1), (9, 0), (13, 1)):
+        sp, sm = sxy.copy(), sxy.copy()
+        sp[i, ax] += h
+        sm[i, ax] -= h
+        fd = (loss(sp) - loss(sm)) / (float(sp[i, ax]) - float(sm[i, ax]))
+        assert abs(fd - gr["sigmas_xy"][i, ax]) <= 1e-4 * max(1.0, abs(fd)), (i, ax, fd, gr["sigmas_xy"][i, ax])
+
+
+def test_aniso_permutation_invariance():
+    pts, vals, sxy = _an_case(29, 25, 8, 9)
+    perm = np.random.default_rng(30).permutation(25)
+    a = oracle.forward_aniso(pts, vals, sxy, 8, 9)["image"]
+    b = oracle.forward_aniso(pts[perm], vals[perm], sxy[perm], 8, 9)["image"]
+    np.testing.assert_allclose(a, b, rtol=0, atol=1e-14)
