@@ -467,6 +467,11 @@ def bench_per_point_sigma(dev, steps, warmup, flush, stream, lo=0.5, hi=1.5, k=3
     def fwd_shared():
         gmi.interpolate(P, V, hi, im.H, im.W, mode="truncated", radius_sigmas=k, graph=True, out=out)
 
+    Sxy = torch.as_tensor(wl.point_sigmas(23, im.N, lo, hi, axes=2), device=dev)
+
+    def fwd_aniso():
+        gmi.interpolate_pp(P, V, Sxy, hi, im.H, im.W, radius_sigmas=k, graph=True, out=out)
+
     Pg, Vg, Sg = (t.clone().requires_grad_(True) for t in (P, V, S))
     sg = torch.tensor(hi, dtype=torch.float32, device=dev, requires_grad=True)
 
@@ -477,7 +482,8 @@ def bench_per_point_sigma(dev, steps, warmup, flush, stream, lo=0.5, hi=1.5, k=3
         gmi.gmi_interpolate(Pg, Vg, sg, im.H, im.W, mode="truncated", radius_sigmas=k).backward(G)
 
     res = {}
-    for name, fn in (("forward_pp", fwd_pp), ("forward_shared", fwd_shared), ("fwd_bwd_pp", fb_pp),
+    for name, fn in (("forward_pp", fwd_pp), ("forward_shared", fwd_shared), ("forward_aniso", fwd_aniso),
+                     ("fwd_bwd_pp", fb_pp),
                      ("fwd_bwd_shared", fb_shared)):
         for _ in range(max(3, warmup)):
             fn()
@@ -515,9 +521,9 @@ def bench_per_point_sigma(dev, steps, warmup, flush, stream, lo=0.5, hi=1.5, k=3
                                      % (clk, sms, FP32_PER_SM_CLK, FP32_OPS_PER_PAIR)}
     res["oracle"] = pp_oracle_rate(im, sig, k)
     res["workload"] = ("1024x1024x3 f32 from 262,144 jittered-grid points, sigma_i log-uniform in [%g, %g] px "
-                       "(bound %g), truncated at %g sigma_i; shared-sigma rows use sigma = %g with the same "
-                       "window; fwd_bwd through the autograd ops (positions, values, sigmas), upstream N(0,1)"
-                       % (lo, hi, hi, k, hi))
+                       "(bound %g), truncated at %g sigma_i; forward_aniso draws sx_i, sy_i independently from "
+                       "the same range; shared-sigma rows use sigma = %g with the same window; fwd_bwd through "
+                       "the autograd ops (positions, values, sigmas), upstream N(0,1)" % (lo, hi, hi, k, hi))
     return res
 
 def bench_reconstruction(dev, side=768, factors=(2, 3, 4, 6, 8), sigma_scales=(0.2, 0.25, 0.35, 0.5, 0.7)):

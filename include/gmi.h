@@ -75,16 +75,16 @@ typedef enum { GMI_MODE_EXACT = 0, GMI_MODE_TRUNCATED = 1 } gmi_mode;
 
 /* params->flags */
 #define GMI_FLAG_SYNC_CHECK 0x1u   /* synchronise and return the device status */
-/* gmi_forward and gmi_forward_pp only: run the launch sequence as a cached
- * CUDA graph.  The first call with a given device, set of pointers (points,
- * values, sigmas, image, den_out, shift_out, workspace), sizes (N, C, H, W,
- * ws_bytes) and params captures it;
- * later calls with the same ones replay it (one host launch, shorter gaps
- * between the kernels on the device).  The kernels read the buffers when they
- * run, so replay is correct whatever they hold.  Up to 32 graphs are kept per
- * process (least recently used dropped).  Ignored while the stream is being
- * captured or stage profiling is on.  Worth it for repeated calls on the same
- * buffers; a call on new buffers pays one capture (~0.1-1 ms). */
+/* gmi_forward, gmi_forward_pp and gmi_forward_aniso only: run the launch
+ * sequence as a cached CUDA graph.  The first call with a given device, set of
+ * pointers (points, values, sigmas, image, den_out, shift_out, workspace),
+ * sizes (N, C, H, W, ws_bytes) and params captures it; later calls with the
+ * same ones replay it (one host launch, shorter gaps between the kernels on
+ * the device).  The kernels read the buffers when they run, so replay is
+ * correct whatever they hold.  Up to 32 graphs are kept per process (least
+ * recently used dropped).  Ignored while the stream is being captured or
+ * stage profiling is on.  Worth it for repeated calls on the same buffers; a
+ * call on new buffers pays one capture (~0.1-1 ms). */
 #define GMI_FLAG_GRAPH 0x2u
 
 /* Kernel variants (params->variant); 0 = choose automatically. */
@@ -217,6 +217,33 @@ gmi_status gmi_backward_pp(const float* points, const float* values, const float
                            const float* image, const float* den, const float* grad_image,
                            float* grad_points, float* grad_values, float* grad_sigmas,
                            void* workspace, size_t ws_bytes, gmi_stream_t stream);
+
+/*
+ * Forward and backward passes with an axis-aligned covariance per point:
+ * point i is N(mu_i, diag(sx_i^2, sy_i^2)) with its normaliser
+ * 1/(2 pi sx_i sy_i) kept, and counts at pixel q inside its ellipse
+ * dx^2/sx_i^2 + dy^2/sy_i^2 <= k^2 (truncated mode only).  With sx_i = sy_i
+ * they compute what gmi_forward_pp / gmi_backward_pp compute.
+ *   sigmas_xy      device [N,2] float32 (sx, sy) per point, 4-byte aligned;
+ *                  each finite and in [p->sigma * 2^-32, p->sigma]
+ *   den_out / den  sum_i sigma^2 / (sx_i sy_i) exp(-(dx^2/sx_i^2 +
+ *                  dy^2/sy_i^2) / 2) over the points that count
+ *   grad_points    [N,2]: sum_q (w_i/Z_q) t_i(q) (dx / sx_i^2, dy / sy_i^2)
+ *   grad_sigmas_xy [N,2]: sum_q (w_i/Z_q) t_i(q) (dx^2/sx_i^3 - 1/sx_i,
+ *                  dy^2/sy_i^3 - 1/sy_i)
+ * Everything else (arguments, workspace, flags, errors, determinism of the
+ * backward) as for gmi_forward_pp / gmi_backward_pp.
+ */
+gmi_status gmi_forward_aniso(const float* points, const float* values, const float* sigmas_xy,
+                             int64_t N, int C, int H, int W, const gmi_params* p,
+                             float* image, float* den_out, void* workspace, size_t ws_bytes,
+                             gmi_stream_t stream);
+
+gmi_status gmi_backward_aniso(const float* points, const float* values, const float* sigmas_xy,
+                              int64_t N, int C, int H, int W, const gmi_params* p,
+                              const float* image, const float* den, const float* grad_image,
+                              float* grad_points, float* grad_values, float* grad_sigmas_xy,
+                              void* workspace, size_t ws_bytes, gmi_stream_t stream);
 
 /*
  * Reads the device status word of a workspace after its stream has finished

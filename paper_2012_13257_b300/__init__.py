@@ -282,27 +282,32 @@ def gmi_interpolate(points, values, sigma, H: int, W: int, *, radius_sigmas: flo
 
 
 def _check_sigmas(sigmas, points):
+    """(contiguous sigmas, anisotropic?): [N] isotropic, [N,2] = (sx, sy)."""
     import torch
     if not isinstance(sigmas, torch.Tensor) or sigmas.dtype != torch.float32 or sigmas.device != points.device:
         raise TypeError("sigmas must be a float32 tensor on the points' device")
-    if sigmas.numel() != points.shape[0]:
-        raise ValueError("sigmas must hold one sigma per point")
-    return sigmas.reshape(-1).contiguous()
+    N = points.shape[0]
+    if sigmas.dim() == 2 and tuple(sigmas.shape) == (N, 2):
+        return sigmas.contiguous(), True
+    if sigmas.dim() == 1 and sigmas.shape[0] == N:
+        return sigmas.contiguous(), False
+    raise ValueError("sigmas must have shape [N] (isotropic) or [N, 2] (sx, sy)")
 
 
 def interpolate_pp(points, values, sigmas, sigma_bound: float, H: int, W: int, *, radius_sigmas: float = 6.0,
                    bin_px: int = 0, variant: int = 0, return_aux: bool = False, check: bool = False,
                    graph: bool = False, out=None):
-    """Forward pass with a sigma per point (``sigmas[N]``; normalisers
-    1/sigma_i^2 kept), truncated at ``radius_sigmas * sigma_i``.
-    ``sigma_bound`` must bound every sigma_i from above (it sets the search
+    """Forward pass with a sigma per point, truncated inside each point's
+    ``radius_sigmas``-sigma disc or ellipse; normalisers kept.  ``sigmas`` is
+    ``[N]`` (isotropic sigma_i) or ``[N, 2]`` (axis-aligned (sx_i, sy_i)).
+    ``sigma_bound`` must bound every sigma from above (it sets the search
     radius; a tight bound is faster).  With ``return_aux`` also returns
-    ``den`` = sum_i (sigma_bound/sigma_i)^2 exp(-d_i^2/(2 sigma_i^2)).
-    ``check=True`` synchronises and raises on out-of-range or non-finite
-    sigmas (and the other device-detected errors)."""
+    ``den`` = sum_i sigma_bound^2 / (sx_i sy_i) exp(-(dx^2/sx_i^2 +
+    dy^2/sy_i^2)/2).  ``check=True`` synchronises and raises on out-of-range
+    or non-finite sigmas (and the other device-detected errors)."""
     import torch
     points, values = _check_inputs(points, values)
-    sigmas = _check_sigmas(sigmas, points)
+    sigmas, aniso = _check_sigmas(sigmas, points)
     N, C = int(points.shape[0]), int(values.shape[1])
     H, W = int(H), int(W)
     dev = points.device
@@ -320,10 +325,10 @@ def interpolate_pp(points, values, sigmas, sigma_bound: float, H: int, W: int, *
                                   graph=graph, out=out)
     stream = _stream_handle(dev)
     ws = _workspace(dev, stream, nbytes)
-    st = _lib.load().gmi_forward_pp(points.data_ptr(), values.data_ptr(), sigmas.data_ptr(), N, C, H, W,
-                                    ctypes.byref(p), out.data_ptr(), den.data_ptr() if den is not None else None,
-                                    ws.data_ptr(), ws.numel(), stream)
-    _lib.check(st, "gmi_forward_pp")
+    fn = _lib.load().gmi_forward_aniso if aniso else _lib.load().gmi_forward_pp
+    st = fn(points.data_ptr(), values.data_ptr(), sigmas.data_ptr(), N, C, H, W, ctypes.byref(p), out.data_ptr(),
+            den.data_ptr() if den is not None else None, ws.data_ptr(), ws.numel(), stream)
+    _lib.check(st, "gmi_forward_aniso" if aniso else "gmi_forward_pp")
     if return_aux:
         return out, den
     return out
@@ -335,10 +340,11 @@ def interpolate_backward_pp(points, values, sigmas, sigma_bound: float, H: int, 
     """Gradients of sum(grad_image * image) w.r.t. points, values and the
     per-point sigmas (``image``, ``den`` from ``interpolate_pp(...,
     return_aux=True)``).  Returns ``(grad_points [N,2], grad_values [N,C],
-    grad_sigmas [N])``; entries not in ``need`` are None."""
+    grad_sigmas)``, the last shaped like ``sigmas``; entries not in ``need``
+    are None."""
     import torch
     points, values = _check_inputs(points, values)
-    sigmas = _check_sigmas(sigmas, points)
+    sigmas, aniso = _check_sigmas(sigmas, points)
     N, C = int(points.shape[0]), int(values.shape[1])
     dev = points.device
     for t in (image, den, grad_image):
@@ -352,7 +358,7 @@ def interpolate_backward_pp(points, values, sigmas, sigma_bound: float, H: int, 
     nbytes = _ws_bytes(N, C, H, W, p, (N, C, H, W, float(sigma_bound), float(radius_sigmas), md, bin_px, variant))
     gp = torch.empty((N, 2), dtype=torch.float32, device=dev) if need[0] else None
     gv = torch.empty((N, C), dtype=torch.float32, device=dev) if need[1] else None
-    gs = torch.empty((N,), dtype=torch.float32, device=dev) if need[2] else None
+    gs = torch.empty(tuple(sigmas.shape), dtype=torch.float32, device=dev) if need[2] else None
     if torch.cuda.current_device() != dev.index:
         with torch.cuda.device(dev):
             return interpolate_backward_pp(points, values, sigmas, sigma_bound, H, W, image, den, grad_image,
@@ -360,12 +366,12 @@ def interpolate_backward_pp(points, values, sigmas, sigma_bound: float, H: int, 
                                            need=need, check=check)
     stream = _stream_handle(dev)
     ws = _workspace(dev, stream, nbytes)
-    st = _lib.load().gmi_backward_pp(points.data_ptr(), values.data_ptr(), sigmas.data_ptr(), N, C, H, W,
-                                     ctypes.byref(p), image.data_ptr(), den.data_ptr(), grad_image.data_ptr(),
-                                     gp.data_ptr() if gp is not None else None,
-                                     gv.data_ptr() if gv is not None else None,
-                                     gs.data_ptr() if gs is not None else None, ws.data_ptr(), ws.numel(), stream)
-    _lib.check(st, "gmi_backward_pp")
+    fn = _lib.load().gmi_backward_aniso if aniso else _lib.load().gmi_backward_pp
+    st = fn(points.data_ptr(), values.data_ptr(), sigmas.data_ptr(), N, C, H, W, ctypes.byref(p), image.data_ptr(),
+            den.data_ptr(), grad_image.data_ptr(), gp.data_ptr() if gp is not None else None,
+            gv.data_ptr() if gv is not None else None, gs.data_ptr() if gs is not None else None, ws.data_ptr(),
+            ws.numel(), stream)
+    _lib.check(st, "gmi_backward_aniso" if aniso else "gmi_backward_pp")
     return gp, gv, gs
 
 
@@ -407,9 +413,10 @@ _GMIPPFunction = None
 
 def gmi_interpolate_pp(points, values, sigmas, sigma_bound: float, H: int, W: int, *, radius_sigmas: float = 6.0,
                        bin_px: int = 0, variant: int = 0):
-    """Differentiable per-point-sigma interpolation (truncated at
-    ``radius_sigmas * sigma_i``): gradients flow to ``points``, ``values``
-    and ``sigmas``.  ``sigma_bound`` >= every sigma_i.  Returns [H, W, C]."""
+    """Differentiable per-point-sigma interpolation (truncated inside each
+    point's ``radius_sigmas``-sigma disc or ellipse): gradients flow to
+    ``points``, ``values`` and ``sigmas`` ([N] isotropic or [N, 2] axis-aligned
+    (sx, sy)).  ``sigma_bound`` >= every sigma.  Returns [H, W, C]."""
     global _GMIPPFunction
     if _GMIPPFunction is None:
         _GMIPPFunction = _pp_function()

@@ -76,6 +76,10 @@ SIGNATURES = {
                               _vp, _sz, _vp]),
     "gmi_backward_pp": (_int, [_vp, _vp, _vp, _i64, _int, _int, _int, ctypes.POINTER(Params), _vp, _vp,
                                _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "gmi_forward_aniso": (_int, [_vp, _vp, _vp, _i64, _int, _int, _int, ctypes.POINTER(Params), _vp, _vp,
+                                 _vp, _sz, _vp]),
+    "gmi_backward_aniso": (_int, [_vp, _vp, _vp, _i64, _int, _int, _int, ctypes.POINTER(Params), _vp, _vp,
+                                  _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "gmi_workspace_status": (_int, [_vp, _vp]),
     "gmi_forward_noalloc": (_int, [_vp, _vp, _i64, _int, _int, _int, ctypes.POINTER(Params), _vp, _vp, _vp,
                                    _vp]),

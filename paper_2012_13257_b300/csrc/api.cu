@@ -125,7 +125,7 @@ WsLayout ws_layout(long long n_total, long long nb_total, long long mt_total, lo
   L.sxy = o;    o = align_up(o + sizeof(float2) * (size_t)n_total, 256);
   L.sval = o;   o = align_up(o + sizeof(float4) * (size_t)n_total, 256);
   L.perm = o;   o = align_up(o + sizeof(unsigned) * (size_t)n_total, 256);
-  L.spp = o;    o = align_up(o + sizeof(float2) * (size_t)n_total, 256);
+  L.spp = o;    o = align_up(o + sizeof(float4) * (size_t)n_total, 256);
   L.partials = o; o = align_up(o + sizeof(unsigned) * (size_t)((nb_total + kScanChunk - 1) / kScanChunk + 1), 256);
   L.farq = o;   o = align_up(o + sizeof(uint2) * (size_t)(mt_total > 0 ? mt_total : 1), 256);
   L.items = o;  o = align_up(o + sizeof(uint4) * (size_t)(L.cap_items > 0 ? L.cap_items : 1), 256);
@@ -152,7 +152,7 @@ DevWork bind_ws(void* ws, const WsLayout& L) {
   w.slots = (float*)(b + L.slots);
   w.ubound = (float*)(b + L.ubound);
   w.perm = (unsigned*)(b + L.perm);
-  w.spp = (float2*)(b + L.spp);
+  w.spp = (float4*)(b + L.spp);
   w.pplane = nullptr;
   w.fbflag = nullptr;
   w.fbq = nullptr;
@@ -231,10 +231,11 @@ gmi_status read_status(const void* ws, cudaStream_t s) {
 
 using namespace gmi;
 
-// Forward pass with one shared sigma (sigmas == null) or per-point sigmas.
-static gmi_status forward_impl(const float* points, const float* values, const float* sigmas, int64_t N, int C,
-                               int H, int W, const gmi_params* p, float* image, float* den_out, float* shift_out,
-                               void* workspace, size_t ws_bytes, gmi_stream_t stream) {
+// Forward pass with one shared sigma (sigmas == null) or per-point sigmas
+// (isotropic [N], or axis-aligned [N,2] with aniso).
+static gmi_status forward_impl(const float* points, const float* values, const float* sigmas, bool aniso,
+                               int64_t N, int C, int H, int W, const gmi_params* p, float* image, float* den_out,
+                               float* shift_out, void* workspace, size_t ws_bytes, gmi_stream_t stream) {
   gmi_status st = check_params(p);
   if (st != GMI_OK) return st;
   if ((st = check_shape(N, C, H, W)) != GMI_OK) return st;
@@ -253,6 +254,7 @@ static gmi_status forward_impl(const float* points, const float* values, const f
   g.den = den_out;
   g.shift = shift_out;
   g.sigmas = sigmas;
+  g.aniso = sigmas && aniso ? 1 : 0;
   set_vec_ok(g);
   const long long nb = (long long)g.nbx * g.nby;
   const long long mt = (long long)g.mtx * g.mty;
@@ -295,6 +297,7 @@ static gmi_status forward_impl(const float* points, const float* values, const f
     key.points = points;
     key.values = values;
     key.sigmas = sigmas;
+    key.aniso = g.aniso;
     key.image = image;
     key.den = den_out;
     key.shift = shift_out;
@@ -374,19 +377,33 @@ gmi_status gmi_workspace_size(int64_t N, int C, int H, int W, const gmi_params* 
 gmi_status gmi_forward(const float* points, const float* values, int64_t N, int C, int H, int W,
                        const gmi_params* p, float* image, float* den_out, float* shift_out,
                        void* workspace, size_t ws_bytes, gmi_stream_t stream) {
-  return forward_impl(points, values, nullptr, N, C, H, W, p, image, den_out, shift_out, workspace, ws_bytes,
-                      stream);
+  return forward_impl(points, values, nullptr, false, N, C, H, W, p, image, den_out, shift_out, workspace,
+                      ws_bytes, stream);
+}
+
+static gmi_status forward_per_point(const float* points, const float* values, const float* sigmas, bool aniso,
+                                    int64_t N, int C, int H, int W, const gmi_params* p, float* image,
+                                    float* den_out, void* workspace, size_t ws_bytes, gmi_stream_t stream) {
+  gmi_status st = check_params(p);
+  if (st != GMI_OK) return st;
+  if (p->mode != GMI_MODE_TRUNCATED) return GMI_ERR_UNSUPPORTED;
+  if (N > 0 && (!sigmas || ((uintptr_t)sigmas & 3u) != 0)) return GMI_ERR_INVALID_ARG;
+  return forward_impl(points, values, N > 0 ? sigmas : nullptr, aniso, N, C, H, W, p, image, den_out, nullptr,
+                      workspace, ws_bytes, stream);
 }
 
 gmi_status gmi_forward_pp(const float* points, const float* values, const float* sigmas, int64_t N, int C, int H,
                           int W, const gmi_params* p, float* image, float* den_out, void* workspace,
                           size_t ws_bytes, gmi_stream_t stream) {
-  gmi_status st = check_params(p);
-  if (st != GMI_OK) return st;
-  if (p->mode != GMI_MODE_TRUNCATED) return GMI_ERR_UNSUPPORTED;
-  if (N > 0 && (!sigmas || ((uintptr_t)sigmas & 3u) != 0)) return GMI_ERR_INVALID_ARG;
-  return forward_impl(points, values, N > 0 ? sigmas : nullptr, N, C, H, W, p, image, den_out, nullptr, workspace,
-                      ws_bytes, stream);
+  return forward_per_point(points, values, sigmas, false, N, C, H, W, p, image, den_out, workspace, ws_bytes,
+                           stream);
+}
+
+gmi_status gmi_forward_aniso(const float* points, const float* values, const float* sigmas_xy, int64_t N, int C,
+                             int H, int W, const gmi_params* p, float* image, float* den_out, void* workspace,
+                             size_t ws_bytes, gmi_stream_t stream) {
+  return forward_per_point(points, values, sigmas_xy, true, N, C, H, W, p, image, den_out, workspace, ws_bytes,
+                           stream);
 }
 
 gmi_status gmi_workspace_status(const void* workspace, gmi_stream_t stream) {

@@ -50,6 +50,7 @@ struct FwdGraphKey {
   int C, H, W;
   long long N;
   const void *points, *values, *sigmas, *image, *den, *shift, *ws;
+  int aniso;
   size_t ws_bytes;
   gmi_params params;
 };

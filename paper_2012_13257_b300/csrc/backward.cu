@@ -9,13 +9,14 @@
 // From the forward pass only the image c(q), den_q and shift_q are kept
 // (w_i(q) / Z_q = 2^(-kappa (d^2 - shift_q)) / den_q); the bins are rebuilt.
 //
-// With a sigma per point (truncated mode), w_i(q) = 2^(la_i - kappa_i d^2)
-// (pp_consts) and each point has its own terms
-//   dL/dmu_i    = sum_q (w_i(q) / Z_q) t_i(q) (q - mu_i) / sigma_i^2
-//   dL/dsigma_i = sum_q (w_i(q) / Z_q) t_i(q) (|q - mu_i|^2 / sigma_i^3 - 2 / sigma_i),
-// the last term from the normaliser 1/sigma_i^2 of the 2D normal (it no longer
-// cancels); every pair lies inside its point's disc d <= k sigma_i, so the
-// point-centric kernel covers all of them.
+// With a sigma per point (truncated mode), w_i(q) = 2^(la_i - kx_i dx^2 -
+// ky_i dy^2) (pp_consts) and each point has its own terms
+//   dL/dx_i  = sum_q (w_i(q) / Z_q) t_i(q) dx / sx_i^2      (y likewise)
+//   dL/dsx_i = sum_q (w_i(q) / Z_q) t_i(q) (dx^2 / sx_i^3 - 1 / sx_i),
+// the -1/sx_i from the normaliser 1/(sx_i sy_i) of the 2D normal (it no
+// longer cancels); an isotropic sigma_i gets the sum of its two axis terms.
+// Every pair lies inside its point's ellipse, so the point-centric kernel
+// covers all of them.
 //
 // Work is split by pixel:
 //   * core pixels (no shift, den_q >= 2^-12): point-centric.  One thread per
@@ -133,26 +134,28 @@ __global__ void __launch_bounds__(256) bwd_point_kernel(KArgs a_in, BwdArgs b, f
       const BwdImage bi = bwd_image(b, img);
       const float4* __restrict__ plane = a.w.pplane + g.px_base;
       const float4* __restrict__ plane2 = a.w.pplane + a.px_total + g.px_base;
-      // per-point sigma: kappa_i and la_i of this point, its own disc kappa_i d^2 <= e_trunc
-      const float2 spc = PP ? a.w.spp[i] : make_float2(0.f, 0.f);
-      const float kap = PP ? spc.x * spc.x : g.kappa;
-      // (the disc is widened a little: the forward's test below decides membership)
-      const float rcore2 = PP ? 1.0001f * g.e_trunc / kap : (TRUNC ? g.r2k : rcore_log2 / g.kappa);
+      // per-point sigma: (sqrt(kx_i), sqrt(ky_i), la_i) of this point and its own
+      // ellipse kx_i dx^2 + ky_i dy^2 <= e_trunc, walked a little wider (the
+      // forward's test below decides membership)
+      const float4 spc = PP ? a.w.spp[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float kx = spc.x * spc.x, ky = spc.y * spc.y;
+      const float e_walk = 1.0001f * g.e_trunc;
+      const float rcore2 = TRUNC ? g.r2k : rcore_log2 / g.kappa;
       const float neg_thr = -g.e_trunc;
       const float2 p = a.w.sxy[i];
       const float4 cv = a.w.sval[i];
       const float c4[4] = {cv.x, cv.y, cv.z, cv.w};
       float A[4] = {0.f, 0.f, 0.f, 0.f};
-      float Bx = 0.0f, By = 0.0f, Sw = 0.0f;
-      const float R = sqrtf(rcore2);
+      float Bx = 0.0f, By = 0.0f, Sw = 0.0f, Dy = 0.0f;
+      const float R = PP ? sqrtf(e_walk / ky) : sqrtf(rcore2);
       const int iy0 = max(0, (int)ceilf(p.y - R - 0.5f));
       const int iy1 = min(g.H - 1, (int)floorf(p.y + R - 0.5f));
       for (int iy = iy0; iy <= iy1; ++iy) {
         const float dy = (float)iy + 0.5f - p.y;
         const float dy2 = dy * dy;
-        const float rem = rcore2 - dy2;
+        const float rem = PP ? e_walk - ky * dy2 : rcore2 - dy2;
         if (rem < 0.0f) continue;
-        const float h = sqrtf(rem);
+        const float h = PP ? sqrtf(rem / kx) : sqrtf(rem);
         const int ix0 = max(0, (int)ceilf(p.x - h - 0.5f));
         const int ix1 = min(g.W - 1, (int)floorf(p.x + h - 0.5f));
         const float4* __restrict__ P = plane + (long long)iy * g.W;
@@ -161,10 +164,10 @@ __global__ void __launch_bounds__(256) bwd_point_kernel(KArgs a_in, BwdArgs b, f
         float ayp = 0.0f, gyp = 0.0f;
         if (PP) {
           const int y0 = iy & ~(a.mth - 1);
-          const float v = ((float)y0 + 0.5f - p.y) * spc.x;
-          const float tv = __fmaf_rn((float)(iy - y0), spc.x, v);
+          const float v = ((float)y0 + 0.5f - p.y) * spc.y;
+          const float tv = __fmaf_rn((float)(iy - y0), spc.y, v);
           ayp = __fmul_rn(-tv, tv);
-          gyp = ex2(__fadd_rn(ayp, spc.y));
+          gyp = ex2(__fadd_rn(ayp, spc.z));
         }
         float rowWt = 0.0f;
         float dx = (float)ix0 + 0.5f - p.x;
@@ -193,20 +196,33 @@ __global__ void __launch_bounds__(256) bwd_point_kernel(KArgs a_in, BwdArgs b, f
           const float wt = w * t;
           Bx = fmaf(wt, dx, Bx);
           rowWt += wt;
-          Dp = fmaf(wt, d2, Dp);
+          Dp = fmaf(wt, PP ? dx * dx : d2, Dp);   // per-point sigma: the x part only
         }
         By = fmaf(rowWt, dy, By);
-        if (PP) Sw += rowWt;
+        if (PP) {
+          Sw += rowWt;
+          Dy = fmaf(rowWt, dy2, Dy);
+        }
       }
       const unsigned o = a.w.perm[i];
       if (PP) {
-        const float si = g.sigmas[o];
-        const float is2 = 1.0f / (si * si);
+        // d ln w / d sx = dx^2 / sx^3 - 1 / sx (likewise y); isotropic: their sum
+        const float sx = g.sigmas[g.aniso ? 2LL * o : o];
+        const float sy = g.aniso ? g.sigmas[2LL * o + 1] : sx;
+        const float isx2 = 1.0f / (sx * sx), isy2 = 1.0f / (sy * sy);
         if (bi.gpts) {
-          bi.gpts[2LL * o] = Bx * is2;
-          bi.gpts[2LL * o + 1] = By * is2;
+          bi.gpts[2LL * o] = Bx * isx2;
+          bi.gpts[2LL * o + 1] = By * isy2;
         }
-        if (bi.gsigs) bi.gsigs[o] = (Dp * is2 - 2.0f * Sw) / si;
+        if (bi.gsigs) {
+          const float gx = (Dp * isx2 - Sw) / sx, gy = (Dy * isy2 - Sw) / sy;
+          if (g.aniso) {
+            bi.gsigs[2LL * o] = gx;
+            bi.gsigs[2LL * o + 1] = gy;
+          } else {
+            bi.gsigs[o] = gx + gy;
+          }
+        }
       }
       if (bi.gvals) {
 #pragma unroll
@@ -395,7 +411,7 @@ static gmi_status backward_impl(const float* points, const float* values, const 
                                 int H, int W, const gmi_params* p, const float* image, const float* den,
                                 const float* shift, const float* grad_image, float* grad_points,
                                 float* grad_values, float* grad_sigma, float* grad_sigmas, bool per_point,
-                                void* workspace, size_t ws_bytes, gmi_stream_t stream) {
+                                bool aniso, void* workspace, size_t ws_bytes, gmi_stream_t stream) {
   gmi_status st = check_params(p);
   if (st != GMI_OK) return st;
   if ((st = check_shape(N, C, H, W)) != GMI_OK) return st;
@@ -411,6 +427,7 @@ static gmi_status backward_impl(const float* points, const float* values, const 
   g.points = points;
   g.values = values;
   g.sigmas = sigmas;
+  g.aniso = aniso ? 1 : 0;
   const long long nb = (long long)g.nbx * g.nby;
   const long long mt = (long long)g.mtx * g.mty;
   const long long wt = (long long)g.wtx * g.wty;
@@ -419,7 +436,8 @@ static gmi_status backward_impl(const float* points, const float* values, const 
   if (grad_points && cudaMemsetAsync(grad_points, 0, sizeof(float) * 2 * (size_t)N, s) != cudaSuccess) return GMI_ERR_CUDA;
   if (grad_values && cudaMemsetAsync(grad_values, 0, sizeof(float) * (size_t)C * (size_t)N, s) != cudaSuccess) return GMI_ERR_CUDA;
   if (grad_sigma && cudaMemsetAsync(grad_sigma, 0, sizeof(float), s) != cudaSuccess) return GMI_ERR_CUDA;
-  if (grad_sigmas && cudaMemsetAsync(grad_sigmas, 0, sizeof(float) * (size_t)N, s) != cudaSuccess) return GMI_ERR_CUDA;
+  if (grad_sigmas && cudaMemsetAsync(grad_sigmas, 0, sizeof(float) * (size_t)N * (aniso ? 2 : 1), s) != cudaSuccess)
+    return GMI_ERR_CUDA;
   if (N == 0) return GMI_OK;
 
   KArgs a;
@@ -465,7 +483,21 @@ extern "C" gmi_status gmi_backward(const float* points, const float* values, int
                                    const float* grad_image, float* grad_points, float* grad_values,
                                    float* grad_sigma, void* workspace, size_t ws_bytes, gmi_stream_t stream) {
   return backward_impl(points, values, nullptr, N, C, H, W, p, image, den, shift, grad_image, grad_points,
-                       grad_values, grad_sigma, nullptr, false, workspace, ws_bytes, stream);
+                       grad_values, grad_sigma, nullptr, false, false, workspace, ws_bytes, stream);
+}
+
+// Per-point sigmas, isotropic ([N]) or axis-aligned ([N,2]).
+static gmi_status backward_per_point(const float* points, const float* values, const float* sigmas, int64_t N,
+                                     int C, int H, int W, const gmi_params* p, const float* image,
+                                     const float* den, const float* grad_image, float* grad_points,
+                                     float* grad_values, float* grad_sigmas, bool aniso, void* workspace,
+                                     size_t ws_bytes, gmi_stream_t stream) {
+  gmi_status st = check_params(p);
+  if (st != GMI_OK) return st;
+  if (p->mode != GMI_MODE_TRUNCATED) return GMI_ERR_UNSUPPORTED;
+  if (N > 0 && (!sigmas || ((uintptr_t)sigmas & 3u) != 0)) return GMI_ERR_INVALID_ARG;
+  return backward_impl(points, values, N > 0 ? sigmas : nullptr, N, C, H, W, p, image, den, nullptr, grad_image,
+                       grad_points, grad_values, nullptr, grad_sigmas, true, aniso, workspace, ws_bytes, stream);
 }
 
 extern "C" gmi_status gmi_backward_pp(const float* points, const float* values, const float* sigmas, int64_t N,
@@ -473,10 +505,15 @@ extern "C" gmi_status gmi_backward_pp(const float* points, const float* values, 
                                       const float* den, const float* grad_image, float* grad_points,
                                       float* grad_values, float* grad_sigmas, void* workspace, size_t ws_bytes,
                                       gmi_stream_t stream) {
-  gmi_status st = check_params(p);
-  if (st != GMI_OK) return st;
-  if (p->mode != GMI_MODE_TRUNCATED) return GMI_ERR_UNSUPPORTED;
-  if (N > 0 && (!sigmas || ((uintptr_t)sigmas & 3u) != 0)) return GMI_ERR_INVALID_ARG;
-  return backward_impl(points, values, N > 0 ? sigmas : nullptr, N, C, H, W, p, image, den, nullptr, grad_image,
-                       grad_points, grad_values, nullptr, grad_sigmas, true, workspace, ws_bytes, stream);
+  return backward_per_point(points, values, sigmas, N, C, H, W, p, image, den, grad_image, grad_points,
+                            grad_values, grad_sigmas, false, workspace, ws_bytes, stream);
+}
+
+extern "C" gmi_status gmi_backward_aniso(const float* points, const float* values, const float* sigmas_xy,
+                                         int64_t N, int C, int H, int W, const gmi_params* p, const float* image,
+                                         const float* den, const float* grad_image, float* grad_points,
+                                         float* grad_values, float* grad_sigmas_xy, void* workspace,
+                                         size_t ws_bytes, gmi_stream_t stream) {
+  return backward_per_point(points, values, sigmas_xy, N, C, H, W, p, image, den, grad_image, grad_points,
+                            grad_values, grad_sigmas_xy, true, workspace, ws_bytes, stream);
 }

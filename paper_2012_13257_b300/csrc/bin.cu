@@ -25,8 +25,8 @@ __global__ void __launch_bounds__(256) bin_count_kernel(KArgs a_in) {
       float2 p = reinterpret_cast<const float2*>(g.points)[i];
       bool fin = isfinite(p.x) && isfinite(p.y);
       for (int c = 0; c < a.C; ++c) fin = fin && isfinite(g.values[i * a.C + c]);
-      if (g.sigmas) {
-        const float si = g.sigmas[i];
+      for (int e = 0; g.sigmas && e <= g.aniso; ++e) {
+        const float si = g.sigmas[(1 + g.aniso) * i + e];
         fin = fin && isfinite(si);
         if (isfinite(si) && !(si <= g.sigma && si >= g.sigma * 0x1p-32f)) bad_sigma = 1;
       }

@@ -36,7 +36,10 @@ static __device__ __forceinline__ void bin_scatter_body(const KArgs& a, int nblo
       a.w.sxy[dst] = p;
       a.w.sval[dst] = c;
       a.w.perm[dst] = (unsigned)i;
-      if (g.sigmas) a.w.spp[dst] = pp_consts(g.sigma, g.sigmas[i]);
+      if (g.sigmas) {
+        const float sx = g.sigmas[g.aniso ? 2 * i : i];
+        a.w.spp[dst] = pp_consts(g.sigma, sx, g.aniso ? g.sigmas[2 * i + 1] : sx);
+      }
     }
   }
 }

@@ -45,7 +45,8 @@ struct ImageGeom {
   float* image;          // [H,W,C]
   float* den;            // [H,W] or null
   float* shift;          // [H,W] or null
-  const float* sigmas;   // [n] per-point sigma (bounded by `sigma`), or null: all equal `sigma`
+  const float* sigmas;   // per-point sigmas (bounded by `sigma`): [n], or [n,2] = (sx, sy) when
+                         //   aniso; null: every point has `sigma`
   long long n;           // points of this image
   long long pt_base;     // first point in the concatenated point space
   long long bin_base;    // first bin in the concatenated bin space
@@ -64,6 +65,7 @@ struct ImageGeom {
   float u_near_max;      // largest nearest-distance bound the near kernel accepts
   float e_trunc;         // k^2 log2(e) / 2: per-point sigma keeps kappa_i d^2 <= this
   int vec_ok;            // rows of image/den/shift may use 16-byte stores
+  int aniso;             // sigmas holds an axis-aligned (sx, sy) pair per point
   long long px_base;     // first pixel in the concatenated pixel space
   long long mt_base;     // first micro-tile in the concatenated micro-tile space
 };
@@ -84,8 +86,8 @@ struct DevWork {
   float* ubound;         // [wt_total * 32]: per micro-tile bound U on the nearest squared
                          //   distance (+inf: far-field micro-tile), written by the plan
   unsigned* perm;        // [n_total]: input index of each bin-sorted point
-  float2* spp;           // [n_total]: per-point sigma constants of each bin-sorted point
-                         //   (sqrt(kappa_i), log2(sigma^2 / sigma_i^2)); written only with sigmas
+  float4* spp;           // [n_total]: per-point sigma constants of each bin-sorted point
+                         //   (pp_consts); written only with sigmas
   // backward pass only
   float4* pplane;        // [pixels * (C == 4 ? 2 : 1)]: g_c / den and s' per core pixel
   unsigned* fbflag;      // [mt_total]: micro-tile holds a non-core pixel
@@ -191,15 +193,16 @@ __device__ __forceinline__ float shifted_sqdist(float qx, float qy, float px, fl
   return __fadd_rn(u, lo);
 }
 
-// Per-point sigma (Eq. 2 with sigma_i in place of the shared sigma): the
-// weight of point i at squared distance d^2 is N(q | mu_i, sigma_i^2 I), which
-// up to the common factor 2 pi / sigma^2 (it cancels in Eq. 1) is
-//   2^(la_i - kappa_i d^2),  kappa_i = log2(e) / (2 sigma_i^2),
-//   la_i = log2(sigma^2 / sigma_i^2) >= 0,
-// sigma being the bound given with the call.  Returns (sqrt(kappa_i), la_i).
-__device__ __forceinline__ float2 pp_consts(float sigma, float sigma_i) {
+// Per-point sigma (Eq. 2 with point i's own covariance): the weight of
+// point i at offset (dx, dy) is N(q | mu_i, diag(sx_i^2, sy_i^2)), which up to
+// the common factor 2 pi / sigma^2 (it cancels in Eq. 1) is
+//   2^(la_i - kx_i dx^2 - ky_i dy^2),  kx_i = log2(e) / (2 sx_i^2),
+//   ky_i = log2(e) / (2 sy_i^2),  la_i = log2(sigma^2 / (sx_i sy_i)) >= 0,
+// sigma being the bound given with the call (isotropic: sx_i = sy_i).
+// Returns (sqrt(kx_i), sqrt(ky_i), la_i, 0).
+__device__ __forceinline__ float4 pp_consts(float sigma, float sx, float sy) {
   constexpr float kSqrtHalfLog2e = 0.84932180028801907f;   // sqrt(log2(e) / 2)
-  return make_float2(kSqrtHalfLog2e / sigma_i, 2.0f * log2f(sigma / sigma_i));
+  return make_float4(kSqrtHalfLog2e / sx, kSqrtHalfLog2e / sy, log2f(sigma / sx) + log2f(sigma / sy), 0.0f);
 }
 
 // Bin coordinate of a position along one axis, clamped to [0, nb-1]; NaN maps to 0.

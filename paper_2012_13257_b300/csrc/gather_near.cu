@@ -32,10 +32,11 @@
 // In truncated mode (the literal "radius k sigma" reading) R = k sigma, each
 // pixel keeps only points with d^2 <= k^2 sigma^2, and nothing is queued.
 //
-// Per-point sigma (truncated mode only): point i weighs 2^(la_i - kappa_i d^2)
-// (pp_consts) and counts where d^2 <= k^2 sigma_i^2; the candidate window is
-// that of the bound sigma >= sigma_i, and the factorisation is unchanged:
-// gx = 2^(-kappa_i dx^2), gy = 2^(la_i - kappa_i dy^2).
+// Per-point sigma (truncated mode only; isotropic or axis-aligned): point i
+// weighs 2^(la_i - kx_i dx^2 - ky_i dy^2) (pp_consts) and counts inside its
+// ellipse kx_i dx^2 + ky_i dy^2 <= k^2 log2(e) / 2; the candidate window is
+// that of the bound sigma >= sx_i, sy_i, and the factorisation is unchanged:
+// gx = 2^(-kx_i dx^2), gy = 2^(la_i - ky_i dy^2).
 #include "bin_body.cuh"
 
 namespace gmi {
@@ -356,8 +357,9 @@ __global__ void __launch_bounds__(128, NearOcc<MTH, MTW, C>::value) near_kernel(
     // truncated mode: keep -kappa d^2 >= this
     const float neg_thr = PP ? -g.e_trunc : -g.kappa * g.r2k;
     const float xq0 = (float)x0 + 0.5f, yq0 = (float)y0 + 0.5f;
-    auto consume = [&](const float2 p, const float4 cv, const float2 spc) {
-      const float sk = PP ? spc.x : g.sk;
+    auto consume = [&](const float2 p, const float4 cv, const float4 spc) {
+      const float sk = PP ? spc.x : g.sk;     // along x
+      const float sky = PP ? spc.y : g.sk;    // along y
       const float c4[4] = {cv.x, cv.y, cv.z, cv.w};
       float2 cp[NP];   // (1, c_0), (c_1, c_2)
       cp[0] = make_float2(1.0f, c4[0]);
@@ -365,7 +367,7 @@ __global__ void __launch_bounds__(128, NearOcc<MTH, MTW, C>::value) near_kernel(
       for (int q = 1; q < NP; ++q) cp[q] = make_float2(c4[2 * q - 1], c4[2 * q]);
       const float clast = c4[C - 1];   // the scalar accumulator's value (C even)
       const float u = (xq0 - p.x) * sk;
-      const float v = (yq0 - p.y) * sk;
+      const float v = (yq0 - p.y) * sky;
       float ax[MTW], gx[MTW], ay[MTH], gy[MTH];
       // (per-point sigma: explicit roundings, which the backward pass repeats
       // to keep exactly the same pairs)
@@ -377,9 +379,9 @@ __global__ void __launch_bounds__(128, NearOcc<MTH, MTW, C>::value) near_kernel(
       }
 #pragma unroll
       for (int r = 0; r < MTH; ++r) {
-        const float tt = PP ? __fmaf_rn((float)r, sk, v) : v + (float)r * sk;
+        const float tt = PP ? __fmaf_rn((float)r, sky, v) : v + (float)r * sky;
         ay[r] = PP ? __fmul_rn(-tt, tt) : -tt * tt;
-        gy[r] = ex2(PP ? __fadd_rn(ay[r], spc.y) : ay[r]);
+        gy[r] = ex2(PP ? __fadd_rn(ay[r], spc.z) : ay[r]);
       }
       if (!TRUNC) {
         // separable weight gy[r] * gx[j]: the column factors times the
@@ -439,7 +441,7 @@ __global__ void __launch_bounds__(128, NearOcc<MTH, MTW, C>::value) near_kernel(
       }
       const float2* __restrict__ sxy = a.w.sxy;
       const float4* __restrict__ sval = a.w.sval;
-      const float2* __restrict__ spp = a.w.spp;
+      const float4* __restrict__ spp = a.w.spp;
       int by = w.by_lo - 1;
       unsigned i = 0, end = 0, cum = 0;
       // bounds of the next bin row, loaded one row ahead
@@ -462,12 +464,12 @@ __global__ void __launch_bounds__(128, NearOcc<MTH, MTW, C>::value) near_kernel(
         // the candidate is always loaded one iteration ahead, across bin rows too
         float2 pn = __ldg(&sxy[i]);
         float4 cn = __ldg(&sval[i]);
-        float2 sn = PP ? __ldg(&spp[i]) : make_float2(0.f, 0.f);
+        float4 sn = PP ? __ldg(&spp[i]) : make_float4(0.f, 0.f, 0.f, 0.f);
         bool more = true;
         while (more) {
           const float2 p = pn;
           const float4 cv = cn;
-          const float2 spc = sn;
+          const float4 spc = sn;
           if (++i >= end) more = next_row();
           if (more) {
             pn = __ldg(&sxy[i]);

@@ -255,3 +255,92 @@ def test_sigma_descent_lowers_loss(cuda_device):
             S -= 20.0 * S.grad
             S.clamp_(0.2, 2.0)
     assert losses[-1] < losses[0]
+
+
+# ---------------------------------------------- axis-aligned (sx_i, sy_i) per point
+def check_forward_aniso(im, sxy, bound, dev, k, **kw):
+    out, den = run(im, sxy, bound, dev, k=k, **kw)
+    ref = oracle.forward_aniso(im.points, im.values, sxy, im.H, im.W, mode=oracle.TRUNCATED, k=k)
+    decided = ref["skipped"] < 1e-3
+    assert decided.mean() > 0.99
+    assert np.isfinite(out).all()
+    assert np.abs(out.astype(np.float64) - ref["image"])[decided].max() <= TOL_FWD
+    scaled = ref["den"] * float(bound) ** 2
+    live = decided & (scaled > 0)
+    assert (np.abs(den.astype(np.float64) - scaled)[live] / scaled[live]).max() <= 1e-4
+    empty = (ref["den"] == 0) & decided
+    assert (out[empty] == 0).all()
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: "s%d_N%d_%dx%d_C%d" % c[:5])
+@pytest.mark.parametrize("variant", [1, 2, 3])
+def test_aniso_forward_matches_oracle(cuda_device, case, variant):
+    seed, N, H, W, C, lo, hi, k, clustered = case
+    im = wl.tiny_random(seed, N, H, W, C=C, sigma=hi, clustered=clustered, margin=2.0 if not clustered else 0.0)
+    sxy = wl.point_sigmas(seed + 8, N, lo, hi, axes=2)
+    check_forward_aniso(im, sxy, hi, cuda_device, k, variant=variant)
+
+
+def test_aniso_equal_axes_match_isotropic(cuda_device):
+    im = wl.tiny_random(31, 800, 60, 70, C=3, sigma=1.4, clustered=True)
+    sig = wl.point_sigmas(32, im.N, 0.4, 1.4)
+    a, da = run(im, sig, 1.4, cuda_device, k=3.0)
+    b, db = run(im, np.stack([sig, sig], 1), 1.4, cuda_device, k=3.0)
+    assert np.abs(a - b).max() <= 2e-6
+    np.testing.assert_allclose(da, db, rtol=2e-6, atol=1e-30)
+
+
+def test_aniso_range_reported(cuda_device):
+    g = gmi()
+    im = wl.tiny_random(33, 50, 12, 12, C=3, sigma=1.0)
+    P, V = to_dev(im.points, cuda_device), to_dev(im.values, cuda_device)
+    for ax, bad, status in ((0, 1.5, 1), (1, 0.0, 1), (1, np.nan, 2)):
+        sxy = np.full((im.N, 2), 0.5, np.float32)
+        sxy[9, ax] = bad
+        with pytest.raises(g.GmiError) as e:
+            g.interpolate_pp(P, V, to_dev(sxy, cuda_device), 1.0, 12, 12, check=True)
+        assert e.value.status == status, (ax, bad, e.value.status)
+    with pytest.raises(ValueError):
+        g.interpolate_pp(P, V, to_dev(np.full((im.N, 3), 0.5, np.float32), cuda_device), 1.0, 12, 12)
+
+
+def test_aniso_full_size_sampled(cuda_device):
+    """The 1024^2 upsampling workload with sx_i, sy_i independently
+    log-uniform in [0.4, 1.5] px (bound 1.5, k = 3), on a pixel sample."""
+    im = wl.upsample_1024()
+    sxy = wl.point_sigmas(34, im.N, 0.4, 1.5, axes=2)
+    out, den = run(im, sxy, 1.5, cuda_device, k=3.0)
+    pix = sample_pixels(im.points, im.H, im.W, n_far=0)
+    ref = oracle.forward_aniso(im.points, im.values, sxy, im.H, im.W, mode=oracle.TRUNCATED, k=3.0, pixels=pix)
+    decided = ref["skipped"] < 1e-3
+    assert np.abs(out.reshape(-1, 3)[pix] - ref["image"])[decided].max() <= TOL_FWD
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: "s%d_N%d_%dx%d_C%d" % c[:5])
+def test_aniso_backward_matches_oracle(cuda_device, case):
+    seed, N, H, W, C, lo, hi, k, clustered = case
+    im = wl.tiny_random(seed, N, H, W, C=C, sigma=hi, clustered=clustered, margin=2.0 if not clustered else 0.0)
+    sxy = wl.point_sigmas(seed + 8, N, lo, hi, axes=2)
+    g = np.random.default_rng(seed + 100).standard_normal((H, W, C)).astype(np.float32)
+    ref = oracle.backward_aniso(im.points, im.values, sxy, H, W, g, mode=oracle.TRUNCATED, k=k)
+    ref["sigmas"] = ref["sigmas_xy"]
+    got = gpu_grads(im, sxy, hi, g, cuda_device, k)
+    assert got[2].shape == (N, 2)
+    assert_grads(got, ref)
+
+
+def test_aniso_autograd_op(cuda_device):
+    import torch
+    G = gmi()
+    seed, N, H, W, C, lo, hi, k, clustered = CASES[2]
+    im = wl.tiny_random(seed, N, H, W, C=C, sigma=hi, clustered=clustered)
+    sxy = wl.point_sigmas(seed + 8, N, lo, hi, axes=2)
+    g = np.random.default_rng(seed + 100).standard_normal((H, W, C)).astype(np.float32)
+    P = to_dev(im.points, cuda_device).requires_grad_(True)
+    V = to_dev(im.values, cuda_device).requires_grad_(True)
+    S = to_dev(sxy, cuda_device).requires_grad_(True)
+    img = G.gmi_interpolate_pp(P, V, S, hi, H, W, radius_sigmas=k)
+    (img * to_dev(g, cuda_device)).sum().backward()
+    ref = oracle.backward_aniso(im.points, im.values, sxy, H, W, g, mode=oracle.TRUNCATED, k=k)
+    ref["sigmas"] = ref["sigmas_xy"]
+    assert_grads((P.grad.cpu().numpy(), V.grad.cpu().numpy(), S.grad.cpu().numpy()), ref)

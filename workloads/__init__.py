@@ -222,10 +222,12 @@ def fd_subcase(seed: int = 4, side: int = 32, n: int = 256, C: int = 3,
     return Image(pts, vals, sigma, side, side), grad
 
 
-def point_sigmas(seed: int, n: int, lo: float, hi: float) -> np.ndarray:
-    """Per-point sigmas, log-uniform in [lo, hi] (float32)."""
+def point_sigmas(seed: int, n: int, lo: float, hi: float, axes: int = 1) -> np.ndarray:
+    """Per-point sigmas, log-uniform in [lo, hi] (float32): shape [n], or
+    [n, axes] with independent draws per axis."""
     rng = np.random.default_rng(seed)
-    return _f32(np.exp(rng.uniform(np.log(lo), np.log(hi), n)))
+    size = n if axes == 1 else (n, axes)
+    return _f32(np.exp(rng.uniform(np.log(lo), np.log(hi), size)))
 
 def tiny_random(seed: int, N: int, H: int, W: int, C: int = 3, sigma: float = 1.0,
                 clustered: bool = False, margin: float = 0.0) -> Image:
