@@ -10,10 +10,10 @@ Every function here is pinned by ``tests/test_oracle.py`` against closed forms,
 invariants and library routines (see that file's docstring).  Parity status of
 each function: forward exact/truncated pinned; backward pinned (finite
 differences and torch autograd); pair counts pinned against a k-d tree count;
-the per-point and anisotropic extensions (forward_pp, backward_pp,
-forward_aniso, backward_aniso) pinned by their reductions to the shared-sigma
-and isotropic forms, closed forms, an independent torch evaluation with
-autograd and finite differences.
+the per-point, anisotropic and full-covariance extensions (forward_pp,
+backward_pp, forward_aniso, backward_aniso, forward_cov, backward_cov) pinned
+by their reductions to the simpler forms, closed forms, symmetries, an
+independent torch evaluation with autograd and finite differences.
 """
 from __future__ import annotations
 
@@ -74,6 +74,10 @@ def _load():
             lib.oracle_forward_aniso.restype = ctypes.c_int
             lib.oracle_backward_aniso.argtypes = lib.oracle_backward_pp.argtypes
             lib.oracle_backward_aniso.restype = ctypes.c_int
+            lib.oracle_forward_cov.argtypes = lib.oracle_forward_pp.argtypes
+            lib.oracle_forward_cov.restype = ctypes.c_int
+            lib.oracle_backward_cov.argtypes = lib.oracle_backward_pp.argtypes
+            lib.oracle_backward_cov.restype = ctypes.c_int
             lib.oracle_num_threads.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -264,3 +268,58 @@ def backward_aniso(points, values, sigmas_xy, H: int, W: int, grad, mode: int = 
     if rc != 0:
         raise ValueError("oracle_backward_aniso rejected its arguments (rc=%d)" % rc)
     return {"points": gp, "values": gv, "sigmas_xy": gs}
+
+
+def forward_cov(points, values, cov, H: int, W: int, mode: int = EXACT, k: float = 6.0, pixels=None):
+    """Eq. 1 / Eq. 2 with a full covariance per point, ``cov[N,3]`` =
+    (sx, sy, rho) (see ``oracle_forward_cov``).  Same outputs as
+    ``forward_pp``."""
+    lib = _load()
+    pts = _f32(points).reshape(-1, 2)
+    N = pts.shape[0]
+    vals = _f32(values).reshape(N, -1) if N else _f32(values).reshape(0, np.asarray(values).shape[-1])
+    C = int(vals.shape[1])
+    cv = _f32(cov).reshape(N, 3)
+    if pixels is None:
+        n = H * W
+        pix = None
+    else:
+        pix = np.ascontiguousarray(np.asarray(pixels, dtype=np.int64).ravel())
+        n = pix.size
+    out = np.empty((n, C), np.float64)
+    den = np.empty(n, np.float64)
+    shift = np.empty(n, np.float64)
+    skipped = np.empty(n, np.float64)
+    pairs = np.empty(n, np.int64)
+    rc = lib.oracle_forward_cov(_ptr(pts, ctypes.c_float), _ptr(vals, ctypes.c_float), _ptr(cv, ctypes.c_float),
+                                N, C, H, W, int(mode), float(k), _ptr(pix, ctypes.c_int64), n,
+                                _ptr(out, ctypes.c_double), _ptr(den, ctypes.c_double),
+                                _ptr(shift, ctypes.c_double), _ptr(skipped, ctypes.c_double),
+                                _ptr(pairs, ctypes.c_int64))
+    if rc != 0:
+        raise ValueError("oracle_forward_cov rejected its arguments (rc=%d)" % rc)
+    if pixels is None:
+        out, den, shift = out.reshape(H, W, C), den.reshape(H, W), shift.reshape(H, W)
+        skipped, pairs = skipped.reshape(H, W), pairs.reshape(H, W)
+    return {"image": out, "den": den, "shift": shift, "skipped": skipped, "pairs": pairs}
+
+
+def backward_cov(points, values, cov, H: int, W: int, grad, mode: int = EXACT, k: float = 6.0):
+    """Analytic gradient of sum(grad * image) w.r.t. points, values and each
+    point's (sx, sy, rho)."""
+    lib = _load()
+    pts = _f32(points).reshape(-1, 2)
+    N = pts.shape[0]
+    vals = _f32(values).reshape(N, -1)
+    C = vals.shape[1]
+    cv = _f32(cov).reshape(N, 3)
+    g = _f32(grad).reshape(H, W, C)
+    gp = np.zeros((N, 2), np.float64)
+    gv = np.zeros((N, C), np.float64)
+    gc = np.zeros((N, 3), np.float64)
+    rc = lib.oracle_backward_cov(_ptr(pts, ctypes.c_float), _ptr(vals, ctypes.c_float), _ptr(cv, ctypes.c_float),
+                                 N, C, H, W, int(mode), float(k), _ptr(g, ctypes.c_float),
+                                 _ptr(gp, ctypes.c_double), _ptr(gv, ctypes.c_double), _ptr(gc, ctypes.c_double))
+    if rc != 0:
+        raise ValueError("oracle_backward_cov rejected its arguments (rc=%d)" % rc)
+    return {"points": gp, "values": gv, "cov": gc}

@@ -612,3 +612,200 @@ int oracle_backward_aniso(const float* points, const float* values, const float*
     free(wbuf_all);
     return 0;
 }
+
+/*
+ * Full-covariance extension: point i is N(mu_i, S_i) with
+ *     S_i = [[sx^2, rho sx sy], [rho sx sy, sy^2]],  |rho| < 1,
+ * and its normaliser 1/(2 pi sqrt(det S_i)) = 1/(2 pi sx sy sqrt(1 - rho^2))
+ * kept.  With d = q - mu_i and the quadratic form
+ *     Q = d^T S_i^-1 d = (dx^2/sx^2 - 2 rho dx dy/(sx sy) + dy^2/sy^2) / (1 - rho^2),
+ *     ln w_i(q) = -Q/2 - ln sx - ln sy - ln(1 - rho^2)/2,
+ *     c(q) = sum_i w_i c_i / sum_i w_i                          (Eq. 1)
+ * EXACT / TRUNCATED (Q <= k^2) and the outputs as for oracle_forward_aniso.
+ * cov [N,3] = (sx, sy, rho) per point, sx, sy > 0, |rho| < 1.
+ */
+static double quad_cov(double dx, double dy, const float* cv) {
+    double sx = (double)cv[0], sy = (double)cv[1], r = (double)cv[2];
+    return (dx * dx / (sx * sx) - 2.0 * r * dx * dy / (sx * sy) + dy * dy / (sy * sy)) / (1.0 - r * r);
+}
+static double log_norm_cov(const float* cv) {
+    double sx = (double)cv[0], sy = (double)cv[1], r = (double)cv[2];
+    return -log(sx) - log(sy) - 0.5 * log(1.0 - r * r);
+}
+static int cov_valid(const float* cov, int64_t N) {
+    for (int64_t i = 0; i < N; ++i) {
+        double sx = (double)cov[3 * i], sy = (double)cov[3 * i + 1], r = (double)cov[3 * i + 2];
+        if (!(sx > 0) || !(sy > 0) || !(fabs(r) < 1.0)) return 0;
+    }
+    return 1;
+}
+
+int oracle_forward_cov(const float* points, const float* values, const float* cov, int64_t N, int C,
+                       int64_t H, int64_t W, int mode, double k, const int64_t* pix, int64_t n_pix,
+                       double* out, double* den, double* shift, double* skipped, int64_t* pairs) {
+    if (N < 0 || C < 1 || H < 1 || W < 1 || !(k > 0) || (N > 0 && !cov)) return -1;
+    if (mode != ORACLE_EXACT && mode != ORACLE_TRUNCATED) return -1;
+    if (!cov_valid(cov, N)) return -1;
+    if (pix == NULL) n_pix = H * W;
+
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t t = 0; t < n_pix; ++t) {
+        int64_t p = pix ? pix[t] : t;
+        double qx, qy;
+        pixel_centre(p, W, &qx, &qy);
+        double num[8];
+        double* acc = C <= 8 ? num : (double*)calloc((size_t)C, sizeof(double));
+        for (int c = 0; c < C; ++c) acc[c] = 0.0;
+        double z = 0.0, L = 0.0, skip = 0.0;
+        int64_t cnt = 0;
+        if (N > 0 && mode == ORACLE_EXACT) {
+            L = -INFINITY;
+            for (int64_t i = 0; i < N; ++i) {
+                double lw = -0.5 * quad_cov(qx - (double)points[2 * i], qy - (double)points[2 * i + 1], cov + 3 * i)
+                            + log_norm_cov(cov + 3 * i);
+                if (lw > L) L = lw;
+            }
+            for (int64_t i = 0; i < N; ++i) {
+                double lw = -0.5 * quad_cov(qx - (double)points[2 * i], qy - (double)points[2 * i + 1], cov + 3 * i)
+                            + log_norm_cov(cov + 3 * i);
+                double w = exp(lw - L);
+                z += w;
+                ++cnt;
+                for (int c = 0; c < C; ++c) acc[c] += w * (double)values[i * C + c];
+            }
+            for (int c = 0; c < C; ++c) acc[c] /= z;
+        } else if (N > 0) {
+            double amb = 0.0;
+            for (int64_t i = 0; i < N; ++i) {
+                double Q = quad_cov(qx - (double)points[2 * i], qy - (double)points[2 * i + 1], cov + 3 * i);
+                double r2 = k * k;
+                double lw = -0.5 * Q + log_norm_cov(cov + 3 * i);
+                if (fabs(Q - r2) <= 1e-5 * r2) amb += exp(lw);
+                if (Q > r2) continue;
+                double w = exp(lw);
+                z += w;
+                ++cnt;
+                for (int c = 0; c < C; ++c) acc[c] += w * (double)values[i * C + c];
+            }
+            if (z > 0) {
+                for (int c = 0; c < C; ++c) acc[c] /= z;
+                skip = amb / z;
+            } else {
+                for (int c = 0; c < C; ++c) acc[c] = 0.0;
+                skip = amb > 0 ? 1.0 : 0.0;
+            }
+        }
+        if (out)
+            for (int c = 0; c < C; ++c) out[t * C + c] = acc[c];
+        if (den) den[t] = z;
+        if (shift) shift[t] = L;
+        if (skipped) skipped[t] = skip;
+        if (pairs) pairs[t] = cnt;
+        if (acc != num) free(acc);
+    }
+    return 0;
+}
+
+/*
+ * Backward pass of the full-covariance extension, by the chain rule on
+ * Eq. 1.  With m = dx dy / (sx sy) and e = 1 - rho^2:
+ *   d ln w / d mu   = S^-1 d
+ *   d ln w / d sx   = (dx^2/sx^3 - rho dx dy/(sx^2 sy)) / e - 1/sx
+ *   d ln w / d sy   = (dy^2/sy^3 - rho dx dy/(sx sy^2)) / e - 1/sy
+ *   d ln w / d rho  = (m - rho Q) / e + rho / e
+ * each gradient being sum_q (w_i / Z_q) t_i(q) times that factor, t_i as for
+ * oracle_backward_pp.  Outputs (each may be NULL): gpoints [N,2], gvalues
+ * [N,C], gcov [N,3] = d/d(sx, sy, rho).
+ */
+int oracle_backward_cov(const float* points, const float* values, const float* cov, int64_t N, int C,
+                        int64_t H, int64_t W, int mode, double k, const float* grad, double* gpoints,
+                        double* gvalues, double* gcov) {
+    if (N < 0 || C < 1 || C > 8 || H < 1 || W < 1 || !(k > 0) || (N > 0 && !cov)) return -1;
+    if (mode != ORACLE_EXACT && mode != ORACLE_TRUNCATED) return -1;
+    if (!cov_valid(cov, N)) return -1;
+    const int64_t P = H * W;
+    int nt = oracle_num_threads();
+    size_t per = (size_t)N * (size_t)(5 + C) + 1;
+    double* part = (double*)calloc(per * (size_t)nt, sizeof(double));
+    double* wbuf_all = (double*)malloc(sizeof(double) * (size_t)(N > 0 ? N : 1) * (size_t)nt);
+    if (!part || !wbuf_all) { free(part); free(wbuf_all); return -2; }
+
+#pragma omp parallel
+    {
+        int tid = 0;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+#endif
+        double* acc = part + per * (size_t)tid;   /* [N*2 | N*C | N*3] */
+        double* w = wbuf_all + (size_t)(N > 0 ? N : 1) * (size_t)tid;
+        double chat[8], G[8];
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t p = 0; p < P; ++p) {
+            if (N == 0) continue;
+            int any = 0;
+            for (int c = 0; c < C; ++c) any |= grad[p * C + c] != 0.0f;
+            if (!any) continue;
+            double qx, qy;
+            pixel_centre(p, W, &qx, &qy);
+            double L = 0.0;
+            if (mode == ORACLE_EXACT) {
+                L = -INFINITY;
+                for (int64_t i = 0; i < N; ++i) {
+                    double lw = -0.5 * quad_cov(qx - (double)points[2 * i], qy - (double)points[2 * i + 1],
+                                                cov + 3 * i) + log_norm_cov(cov + 3 * i);
+                    if (lw > L) L = lw;
+                }
+            }
+            double z = 0.0;
+            for (int c = 0; c < C; ++c) chat[c] = 0.0;
+            for (int64_t i = 0; i < N; ++i) {
+                double Q = quad_cov(qx - (double)points[2 * i], qy - (double)points[2 * i + 1], cov + 3 * i);
+                double wi = (mode == ORACLE_TRUNCATED && Q > k * k) ? 0.0
+                                                                     : exp(-0.5 * Q + log_norm_cov(cov + 3 * i) - L);
+                w[i] = wi;
+                z += wi;
+                for (int c = 0; c < C; ++c) chat[c] += wi * (double)values[i * C + c];
+            }
+            if (!(z > 0)) continue;
+            for (int c = 0; c < C; ++c) {
+                chat[c] /= z;
+                G[c] = (double)grad[p * C + c] / z;
+            }
+            for (int64_t i = 0; i < N; ++i) {
+                if (w[i] == 0.0) continue;
+                double sx = (double)cov[3 * i], sy = (double)cov[3 * i + 1], r = (double)cov[3 * i + 2];
+                double e = 1.0 - r * r;
+                double t = 0.0;
+                for (int c = 0; c < C; ++c) {
+                    acc[2 * N + i * C + c] += w[i] * G[c];
+                    t += G[c] * ((double)values[i * C + c] - chat[c]);
+                }
+                double dx = qx - (double)points[2 * i];
+                double dy = qy - (double)points[2 * i + 1];
+                double wt = w[i] * t;
+                /* S^-1 = [[1/sx^2, -rho/(sx sy)], [-rho/(sx sy), 1/sy^2]] / e */
+                double ix = (dx / (sx * sx) - r * dy / (sx * sy)) / e;
+                double iy = (dy / (sy * sy) - r * dx / (sx * sy)) / e;
+                double Q = quad_cov(dx, dy, cov + 3 * i);
+                double m = dx * dy / (sx * sy);
+                double* gc = acc + (size_t)N * (2 + C);
+                acc[2 * i] += wt * ix;
+                acc[2 * i + 1] += wt * iy;
+                gc[3 * i] += wt * ((dx * dx / (sx * sx * sx) - r * dx * dy / (sx * sx * sy)) / e - 1.0 / sx);
+                gc[3 * i + 1] += wt * ((dy * dy / (sy * sy * sy) - r * dx * dy / (sx * sy * sy)) / e - 1.0 / sy);
+                gc[3 * i + 2] += wt * ((m - r * Q) / e + r / e);
+            }
+        }
+    }
+    for (size_t e = 0; e < per; ++e) {
+        double s = 0.0;
+        for (int t = 0; t < nt; ++t) s += part[per * (size_t)t + e];
+        part[e] = s;
+    }
+    if (gpoints) memcpy(gpoints, part, sizeof(double) * (size_t)N * 2);
+    if (gvalues) memcpy(gvalues, part + 2 * N, sizeof(double) * (size_t)N * (size_t)C);
+    if (gcov) memcpy(gcov, part + (size_t)N * (2 + C), sizeof(double) * (size_t)N * 3);
+    free(part);
+    free(wbuf_all);
+    return 0;
+}

@@ -546,3 +546,152 @@ def test_aniso_permutation_invariance():
     a = oracle.forward_aniso(pts, vals, sxy, 8, 9)["image"]
     b = oracle.forward_aniso(pts[perm], vals[perm], sxy[perm], 8, 9)["image"]
     np.testing.assert_allclose(a, b, rtol=0, atol=1e-14)
+
+
+# --------------------------------------------------- full covariance per point (extension)
+def _cov_case(seed, n, H, W, C=3, lo=0.6, hi=2.0, rmax=0.8):
+    pts, vals, _ = _pp_case(seed, n, H, W, C=C)
+    rng = np.random.default_rng(seed + 2000)
+    cov = np.concatenate([rng.uniform(lo, hi, (n, 2)), rng.uniform(-rmax, rmax, (n, 1))], 1).astype(np.float32)
+    return pts, vals, cov
+
+
+def _cov_matrix(c):
+    sx, sy, r = (float(v) for v in c)
+    return np.array([[sx * sx, r * sx * sy], [r * sx * sy, sy * sy]])
+
+
+@pytest.mark.parametrize("mode", [oracle.EXACT, oracle.TRUNCATED])
+def test_cov_zero_correlation_reduces_to_aniso(mode):
+    pts, vals, cov = _cov_case(41, 30, 12, 14)
+    cov[:, 2] = 0.0
+    k = 6.0 if mode == oracle.EXACT else 2.5
+    a = oracle.forward_cov(pts, vals, cov, 12, 14, mode=mode, k=k)
+    b = oracle.forward_aniso(pts, vals, cov[:, :2].copy(), 12, 14, mode=mode, k=k)
+    for key in ("image", "den", "shift"):
+        np.testing.assert_allclose(a[key], b[key], rtol=1e-13, atol=1e-13)
+    assert (a["pairs"] == b["pairs"]).all()
+    g = np.random.default_rng(42).standard_normal((12, 14, 3)).astype(np.float32)
+    ga = oracle.backward_cov(pts, vals, cov, 12, 14, g, mode=mode, k=k)
+    gb = oracle.backward_aniso(pts, vals, cov[:, :2].copy(), 12, 14, g, mode=mode, k=k)
+    np.testing.assert_allclose(ga["points"], gb["points"], rtol=1e-10, atol=1e-12)
+    np.testing.assert_allclose(ga["values"], gb["values"], rtol=1e-10, atol=1e-12)
+    np.testing.assert_allclose(ga["cov"][:, :2], gb["sigmas_xy"], rtol=1e-10, atol=1e-12)
+
+
+def test_cov_single_point_ellipse_and_density():
+    """One point: colour inside the rotated ellipse d^T S^-1 d <= k^2 and 0
+    outside; den = exp(-Q/2) / sqrt(det S), with S^-1 and det S taken by
+    numpy's matrix routines."""
+    H, W, k = 12, 13, 2.0
+    xx, yy = _grid(H, W)
+    p1 = np.float32([[6.2, 5.7]])
+    c1 = np.float32([[0.4, 0.1, 0.8]])
+    cv = np.float32([[2.3, 1.1, 0.65]])
+    r = oracle.forward_cov(p1, c1, cv, H, W, mode=oracle.TRUNCATED, k=k)
+    S = _cov_matrix(cv[0])
+    Si = np.linalg.inv(S)
+    d = np.stack([xx - float(p1[0, 0]), yy - float(p1[0, 1])], -1)
+    Q = np.einsum("...i,ij,...j->...", d, Si, d)
+    inside = Q <= k * k
+    assert inside.sum() > 5 and (~inside).sum() > 5
+    np.testing.assert_allclose(r["image"][inside], np.broadcast_to(c1[0], (inside.sum(), 3)), atol=1e-15)
+    assert (r["image"][~inside] == 0).all()
+    np.testing.assert_allclose(r["den"][inside], np.exp(-0.5 * Q[inside]) / math.sqrt(np.linalg.det(S)),
+                               rtol=1e-12)
+
+
+@pytest.mark.parametrize("mode", [oracle.EXACT, oracle.TRUNCATED])
+def test_cov_symmetries(mode):
+    """Transposing the problem (x <-> y, sx <-> sy, H <-> W) transposes the
+    image; mirroring x (x -> W - x, rho -> -rho) mirrors the columns; the
+    gradients follow (the mirrored x and rho gradients change sign)."""
+    H, W = 10, 9
+    pts, vals, cov = _cov_case(43, 28, H, W)
+    pts = (np.round(pts * 1024.0) / 1024.0).astype(np.float32)   # W - x stays exact in float32
+    k = 6.0 if mode == oracle.EXACT else 2.0
+    g = np.random.default_rng(44).standard_normal((H, W, 3)).astype(np.float32)
+    a = oracle.forward_cov(pts, vals, cov, H, W, mode=mode, k=k)
+    ga = oracle.backward_cov(pts, vals, cov, H, W, g, mode=mode, k=k)
+    tc = cov[:, [1, 0, 2]].copy()
+    b = oracle.forward_cov(pts[:, ::-1].copy(), vals, tc, W, H, mode=mode, k=k)
+    np.testing.assert_allclose(b["image"], a["image"].transpose(1, 0, 2), rtol=0, atol=1e-13)
+    gb = oracle.backward_cov(pts[:, ::-1].copy(), vals, tc, W, H, g.transpose(1, 0, 2).copy(), mode=mode, k=k)
+    np.testing.assert_allclose(gb["points"], ga["points"][:, ::-1], rtol=1e-10, atol=1e-12)
+    np.testing.assert_allclose(gb["cov"], ga["cov"][:, [1, 0, 2]], rtol=1e-10, atol=1e-12)
+    mp = pts.copy()
+    mp[:, 0] = np.float32(W) - mp[:, 0]
+    mc = cov.copy()
+    mc[:, 2] = -mc[:, 2]
+    m = oracle.forward_cov(mp, vals, mc, H, W, mode=mode, k=k)
+    np.testing.assert_allclose(m["image"], a["image"][:, ::-1], rtol=0, atol=1e-13)
+    gm = oracle.backward_cov(mp, vals, mc, H, W, g[:, ::-1].copy(), mode=mode, k=k)
+    np.testing.assert_allclose(gm["points"], ga["points"] * np.array([-1.0, 1.0]), rtol=1e-10, atol=1e-12)
+    np.testing.assert_allclose(gm["cov"], ga["cov"] * np.array([1.0, 1.0, -1.0]), rtol=1e-10, atol=1e-12)
+
+
+@pytest.mark.parametrize("mode", [oracle.EXACT, oracle.TRUNCATED])
+def test_cov_torch_autograd(mode):
+    """An independent FP64 torch evaluation built from the covariance matrix
+    (torch.linalg.inv, torch.logdet) and its autograd gradients with respect
+    to positions, values and (sx, sy, rho)."""
+    torch = pytest.importorskip("torch")
+    H, W, k = 12, 13, 2.5
+    pts, vals, cov = _cov_case(45, 26, H, W)
+    g = np.random.default_rng(46).standard_normal((H, W, 3)).astype(np.float32)
+    P = torch.tensor(pts, dtype=torch.float64, requires_grad=True)
+    V = torch.tensor(vals, dtype=torch.float64, requires_grad=True)
+    CV = torch.tensor(cov, dtype=torch.float64, requires_grad=True)
+    sx, sy, r = CV[:, 0], CV[:, 1], CV[:, 2]
+    S = torch.stack([torch.stack([sx * sx, r * sx * sy], -1), torch.stack([r * sx * sy, sy * sy], -1)], -2)
+    Si = torch.linalg.inv(S)
+    yy, xx = torch.meshgrid(torch.arange(H, dtype=torch.float64) + 0.5,
+                            torch.arange(W, dtype=torch.float64) + 0.5, indexing="ij")
+    q = torch.stack([xx.reshape(-1), yy.reshape(-1)], 1)
+    d = q[:, None, :] - P[None]
+    Q = torch.einsum("pni,nij,pnj->pn", d, Si, d)
+    logw = -0.5 * Q - 0.5 * torch.logdet(S)
+    if mode == oracle.EXACT:
+        wgt = torch.softmax(logw, dim=1)
+    else:
+        w = torch.where(Q <= k * k, torch.exp(logw), torch.zeros_like(Q))
+        z = w.sum(1, keepdim=True)
+        wgt = torch.where(z > 0, w / torch.where(z > 0, z, torch.ones_like(z)), torch.zeros_like(w))
+    img = (wgt @ V).reshape(H, W, 3)
+    (img * torch.tensor(g, dtype=torch.float64)).sum().backward()
+    ref = oracle.forward_cov(pts, vals, cov, H, W, mode=mode, k=k)
+    np.testing.assert_allclose(ref["image"], img.detach().numpy(), rtol=0, atol=1e-12)
+    gr = oracle.backward_cov(pts, vals, cov, H, W, g, mode=mode, k=k)
+    np.testing.assert_allclose(gr["points"], P.grad.numpy(), rtol=1e-8, atol=1e-10)
+    np.testing.assert_allclose(gr["values"], V.grad.numpy(), rtol=1e-8, atol=1e-10)
+    np.testing.assert_allclose(gr["cov"], CV.grad.numpy(), rtol=1e-8, atol=1e-10)
+
+
+def test_cov_gradient_finite_differences():
+    H, W = 10, 11
+    pts, vals, cov = _cov_case(47, 14, H, W)
+    g = np.random.default_rng(48).standard_normal((H, W, 3)).astype(np.float32)
+
+    def loss(c):
+        return float((oracle.forward_cov(pts, vals, c, H, W)["image"] * g).sum())
+
+    gr = oracle.backward_cov(pts, vals, cov, H, W, g)
+    h = 2.0 ** -10
+    for i, ax in ((0, 0), (3, 1), (6, 2), (11, 2), (13, 0)):
+        cp, cm = cov.copy(), cov.copy()
+        cp[i, ax] += h
+        cm[i, ax] -= h
+        fd = (loss(cp) - loss(cm)) / (float(cp[i, ax]) - float(cm[i, ax]))
+        assert abs(fd - gr["cov"][i, ax]) <= 1e-4 * max(1.0, abs(fd)), (i, ax, fd, gr["cov"][i, ax])
+
+
+def test_cov_permutation_invariance_and_rejects_degenerate():
+    pts, vals, cov = _cov_case(49, 25, 8, 9)
+    perm = np.random.default_rng(50).permutation(25)
+    a = oracle.forward_cov(pts, vals, cov, 8, 9)["image"]
+    b = oracle.forward_cov(pts[perm], vals[perm], cov[perm], 8, 9)["image"]
+    np.testing.assert_allclose(a, b, rtol=0, atol=1e-14)
+    bad = cov.copy()
+    bad[3, 2] = 1.0
+    with pytest.raises(ValueError):
+        oracle.forward_cov(pts, vals, bad, 8, 9)
