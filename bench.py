@@ -472,6 +472,13 @@ def bench_per_point_sigma(dev, steps, warmup, flush, stream, lo=0.5, hi=1.5, k=3
     def fwd_aniso():
         gmi.interpolate_pp(P, V, Sxy, hi, im.H, im.W, radius_sigmas=k, graph=True, out=out)
 
+    Scov = torch.as_tensor(wl.point_cov(24, im.N, lo, hi, rmax=0.9), device=dev)
+
+    cov_bound = wl.cov_bound(Scov.cpu().numpy())
+
+    def fwd_cov():
+        gmi.interpolate_pp(P, V, Scov, cov_bound, im.H, im.W, radius_sigmas=k, graph=True, out=out)
+
     Pg, Vg, Sg = (t.clone().requires_grad_(True) for t in (P, V, S))
     sg = torch.tensor(hi, dtype=torch.float32, device=dev, requires_grad=True)
 
@@ -483,6 +490,7 @@ def bench_per_point_sigma(dev, steps, warmup, flush, stream, lo=0.5, hi=1.5, k=3
 
     res = {}
     for name, fn in (("forward_pp", fwd_pp), ("forward_shared", fwd_shared), ("forward_aniso", fwd_aniso),
+                     ("forward_cov", fwd_cov),
                      ("fwd_bwd_pp", fb_pp),
                      ("fwd_bwd_shared", fb_shared)):
         for _ in range(max(3, warmup)):
@@ -522,7 +530,8 @@ def bench_per_point_sigma(dev, steps, warmup, flush, stream, lo=0.5, hi=1.5, k=3
     res["oracle"] = pp_oracle_rate(im, sig, k)
     res["workload"] = ("1024x1024x3 f32 from 262,144 jittered-grid points, sigma_i log-uniform in [%g, %g] px "
                        "(bound %g), truncated at %g sigma_i; forward_aniso draws sx_i, sy_i independently from "
-                       "the same range; shared-sigma rows use sigma = %g with the same window; fwd_bwd through "
+                       "the same range, forward_cov adds rho_i uniform in [-0.9, 0.9] (bound: the largest sqrt of a "
+                       "covariance eigenvalue); shared-sigma rows use sigma = %g with the same window; fwd_bwd through "
                        "the autograd ops (positions, values, sigmas), upstream N(0,1)" % (lo, hi, hi, k, hi))
     return res
 

@@ -75,7 +75,7 @@ typedef enum { GMI_MODE_EXACT = 0, GMI_MODE_TRUNCATED = 1 } gmi_mode;
 
 /* params->flags */
 #define GMI_FLAG_SYNC_CHECK 0x1u   /* synchronise and return the device status */
-/* gmi_forward, gmi_forward_pp and gmi_forward_aniso only: run the launch
+/* gmi_forward and the per-point forward calls only: run the launch
  * sequence as a cached CUDA graph.  The first call with a given device, set of
  * pointers (points, values, sigmas, image, den_out, shift_out, workspace),
  * sizes (N, C, H, W, ws_bytes) and params captures it; later calls with the
@@ -244,6 +244,40 @@ gmi_status gmi_backward_aniso(const float* points, const float* values, const fl
                               const float* image, const float* den, const float* grad_image,
                               float* grad_points, float* grad_values, float* grad_sigmas_xy,
                               void* workspace, size_t ws_bytes, gmi_stream_t stream);
+
+/*
+ * Forward and backward passes with a full covariance per point: point i is
+ * N(mu_i, S_i), S_i = [[sx^2, rho sx sy], [rho sx sy, sy^2]], with its
+ * normaliser 1/(2 pi sqrt(det S_i)) kept, and counts at pixel q inside its
+ * rotated ellipse d^T S_i^-1 d <= k^2 (truncated mode only).  With rho = 0
+ * they compute what gmi_forward_aniso / gmi_backward_aniso compute.  The cross
+ * term of the quadratic form does not factorise into a column and a row
+ * factor, so every (pixel, candidate) takes its own exponential.
+ *   cov         device [N,3] float32 (sx, sy, rho) per point, 4-byte aligned;
+ *               finite, sx, sy >= p->sigma * 2^-32, |rho| <= 0.99 (nearer 1
+ *               the quadratic form's terms grow as 1/(1 - rho^2) and float32
+ *               loses the accuracy the forward promises)
+ *   p           p->sigma bounds the square root of the largest eigenvalue of
+ *               every S_i (a rotated ellipse reaches k sqrt(lambda_max) from
+ *               its centre, which can exceed k max(sx, sy)); checked on the
+ *               device to a relative 2^-20
+ *   den_out/den sum_i sigma^2 / sqrt(det S_i) exp(-d^T S_i^-1 d / 2) over
+ *               the points that count
+ *   grad_points [N,2]: sum_q (w_i/Z_q) t_i(q) S_i^-1 d
+ *   grad_cov    [N,3]: d/d(sx, sy, rho) of L, from the chain rule on
+ *               ln w_i = -d^T S_i^-1 d / 2 - ln sx - ln sy - ln(1 - rho^2) / 2
+ * Everything else as for gmi_forward_pp / gmi_backward_pp.
+ */
+gmi_status gmi_forward_cov(const float* points, const float* values, const float* cov,
+                           int64_t N, int C, int H, int W, const gmi_params* p,
+                           float* image, float* den_out, void* workspace, size_t ws_bytes,
+                           gmi_stream_t stream);
+
+gmi_status gmi_backward_cov(const float* points, const float* values, const float* cov,
+                            int64_t N, int C, int H, int W, const gmi_params* p,
+                            const float* image, const float* den, const float* grad_image,
+                            float* grad_points, float* grad_values, float* grad_cov,
+                            void* workspace, size_t ws_bytes, gmi_stream_t stream);
 
 /*
  * Reads the device status word of a workspace after its stream has finished

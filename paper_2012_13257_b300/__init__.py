@@ -282,16 +282,21 @@ def gmi_interpolate(points, values, sigma, H: int, W: int, *, radius_sigmas: flo
 
 
 def _check_sigmas(sigmas, points):
-    """(contiguous sigmas, anisotropic?): [N] isotropic, [N,2] = (sx, sy)."""
+    """(contiguous sigmas, floats per point): [N] isotropic, [N,2] = (sx, sy),
+    [N,3] = (sx, sy, rho)."""
     import torch
     if not isinstance(sigmas, torch.Tensor) or sigmas.dtype != torch.float32 or sigmas.device != points.device:
         raise TypeError("sigmas must be a float32 tensor on the points' device")
     N = points.shape[0]
-    if sigmas.dim() == 2 and tuple(sigmas.shape) == (N, 2):
-        return sigmas.contiguous(), True
+    if sigmas.dim() == 2 and sigmas.shape[0] == N and sigmas.shape[1] in (2, 3):
+        return sigmas.contiguous(), int(sigmas.shape[1])
     if sigmas.dim() == 1 and sigmas.shape[0] == N:
-        return sigmas.contiguous(), False
-    raise ValueError("sigmas must have shape [N] (isotropic) or [N, 2] (sx, sy)")
+        return sigmas.contiguous(), 1
+    raise ValueError("sigmas must have shape [N] (isotropic), [N, 2] (sx, sy) or [N, 3] (sx, sy, rho)")
+
+
+_PP_CALLS = {1: ("gmi_forward_pp", "gmi_backward_pp"), 2: ("gmi_forward_aniso", "gmi_backward_aniso"),
+             3: ("gmi_forward_cov", "gmi_backward_cov")}
 
 
 def interpolate_pp(points, values, sigmas, sigma_bound: float, H: int, W: int, *, radius_sigmas: float = 6.0,
@@ -299,15 +304,18 @@ def interpolate_pp(points, values, sigmas, sigma_bound: float, H: int, W: int, *
                    graph: bool = False, out=None):
     """Forward pass with a sigma per point, truncated inside each point's
     ``radius_sigmas``-sigma disc or ellipse; normalisers kept.  ``sigmas`` is
-    ``[N]`` (isotropic sigma_i) or ``[N, 2]`` (axis-aligned (sx_i, sy_i)).
+    ``[N]`` (isotropic sigma_i), ``[N, 2]`` (axis-aligned (sx_i, sy_i)) or
+    ``[N, 3]`` (a full covariance (sx_i, sy_i, rho_i), |rho_i| <= 0.99).
     ``sigma_bound`` must bound every sigma from above (it sets the search
-    radius; a tight bound is faster).  With ``return_aux`` also returns
+    radius; a tight bound is faster); for a full covariance it bounds the
+    square root of each covariance's largest eigenvalue.  With ``return_aux`` also returns
     ``den`` = sum_i sigma_bound^2 / (sx_i sy_i) exp(-(dx^2/sx_i^2 +
-    dy^2/sy_i^2)/2).  ``check=True`` synchronises and raises on out-of-range
+    dy^2/sy_i^2)/2) (full covariance: sigma_bound^2 / sqrt(det S_i)
+    exp(-d^T S_i^-1 d / 2)).  ``check=True`` synchronises and raises on out-of-range
     or non-finite sigmas (and the other device-detected errors)."""
     import torch
     points, values = _check_inputs(points, values)
-    sigmas, aniso = _check_sigmas(sigmas, points)
+    sigmas, kind = _check_sigmas(sigmas, points)
     N, C = int(points.shape[0]), int(values.shape[1])
     H, W = int(H), int(W)
     dev = points.device
@@ -325,10 +333,11 @@ def interpolate_pp(points, values, sigmas, sigma_bound: float, H: int, W: int, *
                                   graph=graph, out=out)
     stream = _stream_handle(dev)
     ws = _workspace(dev, stream, nbytes)
-    fn = _lib.load().gmi_forward_aniso if aniso else _lib.load().gmi_forward_pp
-    st = fn(points.data_ptr(), values.data_ptr(), sigmas.data_ptr(), N, C, H, W, ctypes.byref(p), out.data_ptr(),
-            den.data_ptr() if den is not None else None, ws.data_ptr(), ws.numel(), stream)
-    _lib.check(st, "gmi_forward_aniso" if aniso else "gmi_forward_pp")
+    name = _PP_CALLS[kind][0]
+    st = getattr(_lib.load(), name)(points.data_ptr(), values.data_ptr(), sigmas.data_ptr(), N, C, H, W,
+                                    ctypes.byref(p), out.data_ptr(), den.data_ptr() if den is not None else None,
+                                    ws.data_ptr(), ws.numel(), stream)
+    _lib.check(st, name)
     if return_aux:
         return out, den
     return out
@@ -344,7 +353,7 @@ def interpolate_backward_pp(points, values, sigmas, sigma_bound: float, H: int, 
     are None."""
     import torch
     points, values = _check_inputs(points, values)
-    sigmas, aniso = _check_sigmas(sigmas, points)
+    sigmas, kind = _check_sigmas(sigmas, points)
     N, C = int(points.shape[0]), int(values.shape[1])
     dev = points.device
     for t in (image, den, grad_image):
@@ -366,12 +375,13 @@ def interpolate_backward_pp(points, values, sigmas, sigma_bound: float, H: int, 
                                            need=need, check=check)
     stream = _stream_handle(dev)
     ws = _workspace(dev, stream, nbytes)
-    fn = _lib.load().gmi_backward_aniso if aniso else _lib.load().gmi_backward_pp
-    st = fn(points.data_ptr(), values.data_ptr(), sigmas.data_ptr(), N, C, H, W, ctypes.byref(p), image.data_ptr(),
-            den.data_ptr(), grad_image.data_ptr(), gp.data_ptr() if gp is not None else None,
-            gv.data_ptr() if gv is not None else None, gs.data_ptr() if gs is not None else None, ws.data_ptr(),
-            ws.numel(), stream)
-    _lib.check(st, "gmi_backward_aniso" if aniso else "gmi_backward_pp")
+    name = _PP_CALLS[kind][1]
+    st = getattr(_lib.load(), name)(points.data_ptr(), values.data_ptr(), sigmas.data_ptr(), N, C, H, W,
+                                    ctypes.byref(p), image.data_ptr(), den.data_ptr(), grad_image.data_ptr(),
+                                    gp.data_ptr() if gp is not None else None,
+                                    gv.data_ptr() if gv is not None else None,
+                                    gs.data_ptr() if gs is not None else None, ws.data_ptr(), ws.numel(), stream)
+    _lib.check(st, name)
     return gp, gv, gs
 
 
@@ -415,8 +425,8 @@ def gmi_interpolate_pp(points, values, sigmas, sigma_bound: float, H: int, W: in
                        bin_px: int = 0, variant: int = 0):
     """Differentiable per-point-sigma interpolation (truncated inside each
     point's ``radius_sigmas``-sigma disc or ellipse): gradients flow to
-    ``points``, ``values`` and ``sigmas`` ([N] isotropic or [N, 2] axis-aligned
-    (sx, sy)).  ``sigma_bound`` >= every sigma.  Returns [H, W, C]."""
+    ``points``, ``values`` and ``sigmas`` ([N] isotropic, [N, 2] axis-aligned
+    (sx, sy) or [N, 3] full (sx, sy, rho)).  ``sigma_bound`` >= every sigma.  Returns [H, W, C]."""
     global _GMIPPFunction
     if _GMIPPFunction is None:
         _GMIPPFunction = _pp_function()

@@ -80,6 +80,10 @@ SIGNATURES = {
                                  _vp, _sz, _vp]),
     "gmi_backward_aniso": (_int, [_vp, _vp, _vp, _i64, _int, _int, _int, ctypes.POINTER(Params), _vp, _vp,
                                   _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "gmi_forward_cov": (_int, [_vp, _vp, _vp, _i64, _int, _int, _int, ctypes.POINTER(Params), _vp, _vp,
+                               _vp, _sz, _vp]),
+    "gmi_backward_cov": (_int, [_vp, _vp, _vp, _i64, _int, _int, _int, ctypes.POINTER(Params), _vp, _vp,
+                                _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "gmi_workspace_status": (_int, [_vp, _vp]),
     "gmi_forward_noalloc": (_int, [_vp, _vp, _i64, _int, _int, _int, ctypes.POINTER(Params), _vp, _vp, _vp,
                                    _vp]),

@@ -15,9 +15,9 @@
 
 namespace gmi {
 
-cudaError_t launch_near(const KArgs& a, int mth, int mtw, bool trunc, bool pp, int grid, cudaStream_t s);
+cudaError_t launch_near(const KArgs& a, int mth, int mtw, bool trunc, int ppk, int grid, cudaStream_t s);
 cudaError_t launch_scatter_plan(const KArgs& a, bool trunc, int n_scatter, cudaStream_t s);
-int near_blocks_per_sm(int mth, int mtw, int C, bool trunc, bool pp);
+int near_blocks_per_sm(int mth, int mtw, int C, bool trunc, int ppk);
 cudaError_t launch_far(const KArgs& a, int mth, int mtw, int sms, cudaStream_t s);
 __global__ void bin_count_kernel(KArgs a);
 __global__ void scan_partial_kernel(const unsigned* cnt, long long nb, unsigned* partials, const long long* totals);
@@ -199,15 +199,15 @@ gmi_status run_bin_and_plan(KArgs& a, const WsLayout& L, void* ws, int mth, int 
 
 // Binning + plan + near + far on prepared arguments (single image or batch).
 gmi_status run_forward_pipeline(KArgs& a, const WsLayout& L, void* ws, int mth, int mtw, bool trunc,
-                                cudaStream_t s, bool pp) {
+                                cudaStream_t s, int ppk) {
   gmi_status st = run_bin_and_plan(a, L, ws, mth, mtw, trunc, s, true);
   if (st != GMI_OK) return st;
   const int sms = device_sm_count();
-  const int per_sm = near_blocks_per_sm(mth, mtw, a.C, trunc, pp);
+  const int per_sm = near_blocks_per_sm(mth, mtw, a.C, trunc, ppk);
   // persistent: at most one resident wave, and no more warps than work items can use
   const int gn = (int)std::max<long long>(1, std::min<long long>(a.wt_total * 4, (long long)sms * per_sm));
   const ProfileMark pn = profile_begin(GMI_STAGE_NEAR, s);
-  if (launch_near(a, mth, mtw, trunc, pp, gn, s) != cudaSuccess) return GMI_ERR_CUDA;
+  if (launch_near(a, mth, mtw, trunc, ppk, gn, s) != cudaSuccess) return GMI_ERR_CUDA;
   profile_end(pn, s);
   if (!trunc) {
     const ProfileMark pf = profile_begin(GMI_STAGE_FAR, s);
@@ -231,9 +231,9 @@ gmi_status read_status(const void* ws, cudaStream_t s) {
 
 using namespace gmi;
 
-// Forward pass with one shared sigma (sigmas == null) or per-point sigmas
-// (isotropic [N], or axis-aligned [N,2] with aniso).
-static gmi_status forward_impl(const float* points, const float* values, const float* sigmas, bool aniso,
+// Forward pass with one shared sigma (sigmas == null) or per-point sigmas,
+// pp_kind floats per point: isotropic [N], axis-aligned [N,2] or full [N,3].
+static gmi_status forward_impl(const float* points, const float* values, const float* sigmas, int pp_kind,
                                int64_t N, int C, int H, int W, const gmi_params* p, float* image, float* den_out,
                                float* shift_out, void* workspace, size_t ws_bytes, gmi_stream_t stream) {
   gmi_status st = check_params(p);
@@ -254,7 +254,7 @@ static gmi_status forward_impl(const float* points, const float* values, const f
   g.den = den_out;
   g.shift = shift_out;
   g.sigmas = sigmas;
-  g.aniso = sigmas && aniso ? 1 : 0;
+  g.pp_kind = sigmas ? pp_kind : 0;
   set_vec_ok(g);
   const long long nb = (long long)g.nbx * g.nby;
   const long long mt = (long long)g.mtx * g.mty;
@@ -283,7 +283,7 @@ static gmi_status forward_impl(const float* points, const float* values, const f
   a.ch_total = (N + kChunk - 1) / kChunk;
   a.mt_total = mt;
   const bool trunc = p->mode == GMI_MODE_TRUNCATED;
-  const bool pp = sigmas != nullptr;
+  const int ppk = g.pp_kind == 3 ? 2 : (g.pp_kind ? 1 : 0);
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   if ((p->flags & GMI_FLAG_GRAPH) && !profile_on() && cudaStreamIsCapturing(s, &cap) == cudaSuccess &&
       cap == cudaStreamCaptureStatusNone) {
@@ -297,7 +297,7 @@ static gmi_status forward_impl(const float* points, const float* values, const f
     key.points = points;
     key.values = values;
     key.sigmas = sigmas;
-    key.aniso = g.aniso;
+    key.pp_kind = g.pp_kind;
     key.image = image;
     key.den = den_out;
     key.shift = shift_out;
@@ -306,22 +306,23 @@ static gmi_status forward_impl(const float* points, const float* values, const f
     key.params = *p;
     // fill the host-side caches the launch sequence reads before any capture starts
     device_sm_count();
-    near_blocks_per_sm(mth, mtw, C, trunc, pp);
+    near_blocks_per_sm(mth, mtw, C, trunc, ppk);
     struct Ctx {
       const KArgs* a;
       const WsLayout* L;
       void* ws;
       int mth, mtw;
-      bool trunc, pp;
-    } ctx{&a, &L, workspace, mth, mtw, trunc, pp};
+      bool trunc;
+      int ppk;
+    } ctx{&a, &L, workspace, mth, mtw, trunc, ppk};
     auto launch = [](void* c, cudaStream_t cs) -> gmi_status {
       const Ctx* x = static_cast<const Ctx*>(c);
       KArgs ka = *x->a;
-      return run_forward_pipeline(ka, *x->L, x->ws, x->mth, x->mtw, x->trunc, cs, x->pp);
+      return run_forward_pipeline(ka, *x->L, x->ws, x->mth, x->mtw, x->trunc, cs, x->ppk);
     };
     st = forward_graphed(key, launch, &ctx, s);
   } else {
-    st = run_forward_pipeline(a, L, workspace, mth, mtw, trunc, s, pp);
+    st = run_forward_pipeline(a, L, workspace, mth, mtw, trunc, s, ppk);
   }
   if (st != GMI_OK) return st;
   return (p->flags & GMI_FLAG_SYNC_CHECK) ? read_status(workspace, s) : GMI_OK;
@@ -377,33 +378,39 @@ gmi_status gmi_workspace_size(int64_t N, int C, int H, int W, const gmi_params* 
 gmi_status gmi_forward(const float* points, const float* values, int64_t N, int C, int H, int W,
                        const gmi_params* p, float* image, float* den_out, float* shift_out,
                        void* workspace, size_t ws_bytes, gmi_stream_t stream) {
-  return forward_impl(points, values, nullptr, false, N, C, H, W, p, image, den_out, shift_out, workspace,
+  return forward_impl(points, values, nullptr, 0, N, C, H, W, p, image, den_out, shift_out, workspace,
                       ws_bytes, stream);
 }
 
-static gmi_status forward_per_point(const float* points, const float* values, const float* sigmas, bool aniso,
+static gmi_status forward_per_point(const float* points, const float* values, const float* sigmas, int pp_kind,
                                     int64_t N, int C, int H, int W, const gmi_params* p, float* image,
                                     float* den_out, void* workspace, size_t ws_bytes, gmi_stream_t stream) {
   gmi_status st = check_params(p);
   if (st != GMI_OK) return st;
   if (p->mode != GMI_MODE_TRUNCATED) return GMI_ERR_UNSUPPORTED;
   if (N > 0 && (!sigmas || ((uintptr_t)sigmas & 3u) != 0)) return GMI_ERR_INVALID_ARG;
-  return forward_impl(points, values, N > 0 ? sigmas : nullptr, aniso, N, C, H, W, p, image, den_out, nullptr,
+  return forward_impl(points, values, N > 0 ? sigmas : nullptr, pp_kind, N, C, H, W, p, image, den_out, nullptr,
                       workspace, ws_bytes, stream);
 }
 
 gmi_status gmi_forward_pp(const float* points, const float* values, const float* sigmas, int64_t N, int C, int H,
                           int W, const gmi_params* p, float* image, float* den_out, void* workspace,
                           size_t ws_bytes, gmi_stream_t stream) {
-  return forward_per_point(points, values, sigmas, false, N, C, H, W, p, image, den_out, workspace, ws_bytes,
+  return forward_per_point(points, values, sigmas, 1, N, C, H, W, p, image, den_out, workspace, ws_bytes,
                            stream);
 }
 
 gmi_status gmi_forward_aniso(const float* points, const float* values, const float* sigmas_xy, int64_t N, int C,
                              int H, int W, const gmi_params* p, float* image, float* den_out, void* workspace,
                              size_t ws_bytes, gmi_stream_t stream) {
-  return forward_per_point(points, values, sigmas_xy, true, N, C, H, W, p, image, den_out, workspace, ws_bytes,
+  return forward_per_point(points, values, sigmas_xy, 2, N, C, H, W, p, image, den_out, workspace, ws_bytes,
                            stream);
+}
+
+gmi_status gmi_forward_cov(const float* points, const float* values, const float* cov, int64_t N, int C, int H,
+                           int W, const gmi_params* p, float* image, float* den_out, void* workspace,
+                           size_t ws_bytes, gmi_stream_t stream) {
+  return forward_per_point(points, values, cov, 3, N, C, H, W, p, image, den_out, workspace, ws_bytes, stream);
 }
 
 gmi_status gmi_workspace_status(const void* workspace, gmi_stream_t stream) {

@@ -28,9 +28,10 @@ WsLayout ws_layout(long long n_total, long long nb_total, long long mt_total, lo
 DevWork bind_ws(void* ws, const WsLayout& L);
 gmi_status run_bin_and_plan(KArgs& a, const WsLayout& L, void* ws, int mth, int mtw, bool trunc,
                             cudaStream_t s, bool plan);
-// pp: per-point sigmas (a.g0.sigmas set; truncated mode)
+// ppk: per-point sigmas (a.g0.sigmas set; truncated mode): 1 separable
+// (isotropic or axis-aligned), 2 full covariance; 0 without
 gmi_status run_forward_pipeline(KArgs& a, const WsLayout& L, void* ws, int mth, int mtw, bool trunc,
-                                cudaStream_t s, bool pp = false);
+                                cudaStream_t s, int ppk = 0);
 gmi_status read_status(const void* ws, cudaStream_t s);
 
 // Stage timing (profile.cu): no-ops unless gmi_profile_enable(1) was called.
@@ -50,7 +51,7 @@ struct FwdGraphKey {
   int C, H, W;
   long long N;
   const void *points, *values, *sigmas, *image, *den, *shift, *ws;
-  int aniso;
+  int pp_kind;
   size_t ws_bytes;
   gmi_params params;
 };

@@ -207,8 +207,8 @@ __global__ void __launch_bounds__(256) bwd_point_kernel(KArgs a_in, BwdArgs b, f
       const unsigned o = a.w.perm[i];
       if (PP) {
         // d ln w / d sx = dx^2 / sx^3 - 1 / sx (likewise y); isotropic: their sum
-        const float sx = g.sigmas[g.aniso ? 2LL * o : o];
-        const float sy = g.aniso ? g.sigmas[2LL * o + 1] : sx;
+        const float sx = g.sigmas[(long long)g.pp_kind * o];
+        const float sy = g.pp_kind == 2 ? g.sigmas[2LL * o + 1] : sx;
         const float isx2 = 1.0f / (sx * sx), isy2 = 1.0f / (sy * sy);
         if (bi.gpts) {
           bi.gpts[2LL * o] = Bx * isx2;
@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(256) bwd_point_kernel(KArgs a_in, BwdArgs b, f
         }
         if (bi.gsigs) {
           const float gx = (Dp * isx2 - Sw) / sx, gy = (Dy * isy2 - Sw) / sy;
-          if (g.aniso) {
+          if (g.pp_kind == 2) {
             bi.gsigs[2LL * o] = gx;
             bi.gsigs[2LL * o + 1] = gy;
           } else {
@@ -251,6 +251,96 @@ __global__ void __launch_bounds__(256) bwd_point_kernel(KArgs a_in, BwdArgs b, f
   }
   if constexpr (!PP) {
     if (!b.table) sigma_block_total(a, b, D);
+  }
+}
+
+// Full covariance per point (truncated mode): one thread per bin-sorted point
+// walks the bounding rows of its ellipse d^T S_i^-1 d <= k^2 (a little wider)
+// and keeps exactly the pairs the forward kept, by the forward's roundings
+// from each micro-tile's first pixel centre.  With the moments
+// Bx = sum wt dx, By = sum wt dy, Sxx = sum wt dx^2, Sxy = sum wt dx dy,
+// Syy = sum wt dy^2, S = sum wt (wt = (w_i / Z_q) t_i(q)) and e = 1 - rho^2:
+//   dL/dmu   = S_i^-1 (Bx, By)
+//   dL/dsx   = (Sxx / sx^3 - rho Sxy / (sx^2 sy)) / e - S / sx     (sy likewise)
+//   dL/drho  = (Sxy / (sx sy) - rho SQ + rho S) / e,
+//   SQ = sum wt Q = (Sxx / sx^2 - 2 rho Sxy / (sx sy) + Syy / sy^2) / e.
+template <int C>
+__global__ void __launch_bounds__(256) bwd_cov_kernel(KArgs a, BwdArgs b) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.n_total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const ImageGeom& g = a.g0;
+    const BwdImage bi = b.one;
+    const float4* __restrict__ plane = a.w.pplane;
+    const float4* __restrict__ plane2 = a.w.pplane + a.px_total;
+    const unsigned o = a.w.perm[i];
+    const float sx = g.sigmas[3LL * o], sy = g.sigmas[3LL * o + 1], rho = g.sigmas[3LL * o + 2];
+    const float4 kc = a.w.spp[i];   // (kxx, kxy, kyy, la)
+    const float neg_thr = -g.e_trunc;
+    const float kw = 1.0001f * sqrtf(g.r2k) / g.sigma;   // k, widened
+    const float e1 = fmaf(-rho, rho, 1.0f);
+    const float2 p = a.w.sxy[i];
+    const float4 cv = a.w.sval[i];
+    const float c4[4] = {cv.x, cv.y, cv.z, cv.w};
+    float A[4] = {0.f, 0.f, 0.f, 0.f};
+    float Bx = 0.f, By = 0.f, Sxx = 0.f, Sxy = 0.f, Syy = 0.f, S = 0.f;
+    const float ry = kw * sy;
+    const int iy0 = max(0, (int)ceilf(p.y - ry - 0.5f));
+    const int iy1 = min(g.H - 1, (int)floorf(p.y + ry - 0.5f));
+    for (int iy = iy0; iy <= iy1; ++iy) {
+      const int y0 = iy & ~(a.mth - 1);
+      const float dy = __fadd_rn((float)y0 + 0.5f - p.y, (float)(iy - y0));
+      const float ay = __fmul_rn(-__fmul_rn(kc.z, dy), dy);
+      const float by = __fmul_rn(-kc.y, dy);
+      // the row's chord: |dx/sx - rho dy/sy| <= sqrt(e (k^2 - dy^2/sy^2))
+      const float t = dy / sy;
+      const float rem = e1 * fmaf(kw, kw, -t * t);
+      if (rem < 0.0f) continue;
+      const float cx = p.x + rho * sx * t, hw = sx * sqrtf(rem);
+      const int ix0 = max(0, (int)ceilf(cx - hw - 0.5f));
+      const int ix1 = min(g.W - 1, (int)floorf(cx + hw - 0.5f));
+      const float4* __restrict__ P = plane + (long long)iy * g.W;
+      float rowWt = 0.f, rowBx = 0.f;
+      for (int ix = ix0; ix <= ix1; ++ix) {
+        const int x0 = ix & ~(a.mtw - 1);
+        const float dx = __fadd_rn((float)x0 + 0.5f - p.x, (float)(ix - x0));
+        const float ax = __fmul_rn(-__fmul_rn(kc.x, dx), dx);
+        const float e = __fmaf_rn(by, dx, __fadd_rn(ax, ay));
+        if (!(e >= neg_thr)) continue;
+        const float w = ex2(__fadd_rn(e, kc.w));
+        const float4 pv = __ldg(&P[ix]);
+        const float Gv[4] = {pv.x, pv.y, pv.z, pv.w};
+        const float sp = C == 4 ? __ldg(&plane2[(long long)iy * g.W + ix]).x : pv.w;
+        float tq = -sp;
+#pragma unroll
+        for (int c = 0; c < C; ++c) tq = fmaf(Gv[c], c4[c], tq);
+#pragma unroll
+        for (int c = 0; c < C; ++c) A[c] = fmaf(w, Gv[c], A[c]);
+        const float wt = w * tq;
+        rowWt += wt;
+        rowBx = fmaf(wt, dx, rowBx);
+        Sxx = fmaf(wt * dx, dx, Sxx);
+      }
+      S += rowWt;
+      Bx += rowBx;
+      By = fmaf(rowWt, dy, By);
+      Sxy = fmaf(rowBx, dy, Sxy);
+      Syy = fmaf(rowWt * dy, dy, Syy);
+    }
+    if (bi.gvals) {
+#pragma unroll
+      for (int c = 0; c < C; ++c) bi.gvals[(long long)o * C + c] = A[c];
+    }
+    const float isx = 1.0f / sx, isy = 1.0f / sy, ie = 1.0f / e1;
+    if (bi.gpts) {
+      bi.gpts[2LL * o] = (Bx * isx * isx - rho * By * isx * isy) * ie;
+      bi.gpts[2LL * o + 1] = (By * isy * isy - rho * Bx * isx * isy) * ie;
+    }
+    if (bi.gsigs) {
+      const float sq = (Sxx * isx * isx - 2.0f * rho * Sxy * isx * isy + Syy * isy * isy) * ie;
+      bi.gsigs[3LL * o] = (Sxx * isx * isx * isx - rho * Sxy * isx * isx * isy) * ie - S * isx;
+      bi.gsigs[3LL * o + 1] = (Syy * isy * isy * isy - rho * Sxy * isx * isy * isy) * ie - S * isy;
+      bi.gsigs[3LL * o + 2] = (Sxy * isx * isy - rho * sq + rho * S) * ie;
+    }
   }
 }
 
@@ -385,7 +475,8 @@ static cudaError_t launch_bwd_c(const KArgs& a, const BwdArgs& b, cudaStream_t s
   bwd_prep_kernel<C><<<prep_blocks, 256, 0, s>>>(a, b);
   const float rcore_log2 = kRelLog2 + kCoreLog2;   // kappa * R_core^2
   const unsigned blocks = (unsigned)std::max<long long>(1, std::min<long long>((a.n_total + 255) / 256, kSigParts));
-  if (b.pp) bwd_point_kernel<C, true, true><<<blocks, 256, 0, s>>>(a, b, rcore_log2);
+  if (b.pp == 2) bwd_cov_kernel<C><<<blocks, 256, 0, s>>>(a, b);
+  else if (b.pp) bwd_point_kernel<C, true, true><<<blocks, 256, 0, s>>>(a, b, rcore_log2);
   else if (b.trunc) bwd_point_kernel<C, true, false><<<blocks, 256, 0, s>>>(a, b, rcore_log2);
   else bwd_point_kernel<C, false, false><<<blocks, 256, 0, s>>>(a, b, rcore_log2);
   if (!b.trunc) bwd_fallback_kernel<C><<<sms * 4, 32 * kFarWarps, 0, s>>>(a, b);
@@ -411,7 +502,7 @@ static gmi_status backward_impl(const float* points, const float* values, const 
                                 int H, int W, const gmi_params* p, const float* image, const float* den,
                                 const float* shift, const float* grad_image, float* grad_points,
                                 float* grad_values, float* grad_sigma, float* grad_sigmas, bool per_point,
-                                bool aniso, void* workspace, size_t ws_bytes, gmi_stream_t stream) {
+                                int pp_kind, void* workspace, size_t ws_bytes, gmi_stream_t stream) {
   gmi_status st = check_params(p);
   if (st != GMI_OK) return st;
   if ((st = check_shape(N, C, H, W)) != GMI_OK) return st;
@@ -427,7 +518,7 @@ static gmi_status backward_impl(const float* points, const float* values, const 
   g.points = points;
   g.values = values;
   g.sigmas = sigmas;
-  g.aniso = aniso ? 1 : 0;
+  g.pp_kind = sigmas ? pp_kind : 0;
   const long long nb = (long long)g.nbx * g.nby;
   const long long mt = (long long)g.mtx * g.mty;
   const long long wt = (long long)g.wtx * g.wty;
@@ -436,7 +527,7 @@ static gmi_status backward_impl(const float* points, const float* values, const 
   if (grad_points && cudaMemsetAsync(grad_points, 0, sizeof(float) * 2 * (size_t)N, s) != cudaSuccess) return GMI_ERR_CUDA;
   if (grad_values && cudaMemsetAsync(grad_values, 0, sizeof(float) * (size_t)C * (size_t)N, s) != cudaSuccess) return GMI_ERR_CUDA;
   if (grad_sigma && cudaMemsetAsync(grad_sigma, 0, sizeof(float), s) != cudaSuccess) return GMI_ERR_CUDA;
-  if (grad_sigmas && cudaMemsetAsync(grad_sigmas, 0, sizeof(float) * (size_t)N * (aniso ? 2 : 1), s) != cudaSuccess)
+  if (grad_sigmas && cudaMemsetAsync(grad_sigmas, 0, sizeof(float) * (size_t)N * (size_t)pp_kind, s) != cudaSuccess)
     return GMI_ERR_CUDA;
   if (N == 0) return GMI_OK;
 
@@ -471,7 +562,7 @@ static gmi_status backward_impl(const float* points, const float* values, const 
   b.one.inv_s3 = (float)(1.0 / ((double)p->sigma * p->sigma * p->sigma));
   b.table = nullptr;
   b.trunc = trunc ? 1 : 0;
-  b.pp = sigmas ? 1 : 0;
+  b.pp = g.pp_kind == 3 ? 2 : (g.pp_kind ? 1 : 0);
   const ProfileMark pm = profile_begin(GMI_STAGE_BACKWARD, s);
   if (launch_backward(a, b, s) != cudaSuccess) return GMI_ERR_CUDA;
   profile_end(pm, s);
@@ -483,21 +574,22 @@ extern "C" gmi_status gmi_backward(const float* points, const float* values, int
                                    const float* grad_image, float* grad_points, float* grad_values,
                                    float* grad_sigma, void* workspace, size_t ws_bytes, gmi_stream_t stream) {
   return backward_impl(points, values, nullptr, N, C, H, W, p, image, den, shift, grad_image, grad_points,
-                       grad_values, grad_sigma, nullptr, false, false, workspace, ws_bytes, stream);
+                       grad_values, grad_sigma, nullptr, false, 0, workspace, ws_bytes, stream);
 }
 
-// Per-point sigmas, isotropic ([N]) or axis-aligned ([N,2]).
+// Per-point sigmas: pp_kind floats per point, isotropic ([N]), axis-aligned
+// ([N,2]) or a full covariance ([N,3]).
 static gmi_status backward_per_point(const float* points, const float* values, const float* sigmas, int64_t N,
                                      int C, int H, int W, const gmi_params* p, const float* image,
                                      const float* den, const float* grad_image, float* grad_points,
-                                     float* grad_values, float* grad_sigmas, bool aniso, void* workspace,
+                                     float* grad_values, float* grad_sigmas, int pp_kind, void* workspace,
                                      size_t ws_bytes, gmi_stream_t stream) {
   gmi_status st = check_params(p);
   if (st != GMI_OK) return st;
   if (p->mode != GMI_MODE_TRUNCATED) return GMI_ERR_UNSUPPORTED;
   if (N > 0 && (!sigmas || ((uintptr_t)sigmas & 3u) != 0)) return GMI_ERR_INVALID_ARG;
   return backward_impl(points, values, N > 0 ? sigmas : nullptr, N, C, H, W, p, image, den, nullptr, grad_image,
-                       grad_points, grad_values, nullptr, grad_sigmas, true, aniso, workspace, ws_bytes, stream);
+                       grad_points, grad_values, nullptr, grad_sigmas, true, pp_kind, workspace, ws_bytes, stream);
 }
 
 extern "C" gmi_status gmi_backward_pp(const float* points, const float* values, const float* sigmas, int64_t N,
@@ -506,7 +598,7 @@ extern "C" gmi_status gmi_backward_pp(const float* points, const float* values, 
                                       float* grad_values, float* grad_sigmas, void* workspace, size_t ws_bytes,
                                       gmi_stream_t stream) {
   return backward_per_point(points, values, sigmas, N, C, H, W, p, image, den, grad_image, grad_points,
-                            grad_values, grad_sigmas, false, workspace, ws_bytes, stream);
+                            grad_values, grad_sigmas, 1, workspace, ws_bytes, stream);
 }
 
 extern "C" gmi_status gmi_backward_aniso(const float* points, const float* values, const float* sigmas_xy,
@@ -515,5 +607,14 @@ extern "C" gmi_status gmi_backward_aniso(const float* points, const float* value
                                          float* grad_values, float* grad_sigmas_xy, void* workspace,
                                          size_t ws_bytes, gmi_stream_t stream) {
   return backward_per_point(points, values, sigmas_xy, N, C, H, W, p, image, den, grad_image, grad_points,
-                            grad_values, grad_sigmas_xy, true, workspace, ws_bytes, stream);
+                            grad_values, grad_sigmas_xy, 2, workspace, ws_bytes, stream);
+}
+
+extern "C" gmi_status gmi_backward_cov(const float* points, const float* values, const float* cov, int64_t N,
+                                       int C, int H, int W, const gmi_params* p, const float* image,
+                                       const float* den, const float* grad_image, float* grad_points,
+                                       float* grad_values, float* grad_cov, void* workspace, size_t ws_bytes,
+                                       gmi_stream_t stream) {
+  return backward_per_point(points, values, cov, N, C, H, W, p, image, den, grad_image, grad_points, grad_values,
+                            grad_cov, 3, workspace, ws_bytes, stream);
 }

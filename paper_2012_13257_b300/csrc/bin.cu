@@ -14,6 +14,28 @@
 
 namespace gmi {
 
+// Per-point sigmas of one point: false when finite but out of range (sx, sy
+// in [sigma 2^-32, sigma]; a full covariance also needs |rho| <= 0.99 and
+// its largest eigenvalue <= sigma^2, so that its ellipse stays inside the
+// k sigma search radius); clears fin when one is NaN or Inf.
+static __device__ __forceinline__ bool sigmas_ok(const ImageGeom& g, const float* sg, bool& fin) {
+  bool f = true;
+  for (int e = 0; e < g.pp_kind; ++e) f = f && isfinite(sg[e]);
+  if (!f) {
+    fin = false;
+    return true;
+  }
+  const float lo = g.sigma * 0x1p-32f;
+  const float sy = g.pp_kind >= 2 ? sg[1] : sg[0];
+  bool ok = sg[0] >= lo && sg[0] <= g.sigma && sy >= lo && sy <= g.sigma;
+  if (g.pp_kind == 3) {
+    const float a = sg[0] * sg[0], c = sy * sy, b = sg[2] * sg[0] * sy, h = 0.5f * (a - c);
+    const float lam = 0.5f * (a + c) + sqrtf(fmaf(h, h, b * b));
+    ok = ok && fabsf(sg[2]) <= 0.99f && lam <= g.sigma * g.sigma * (1.0f + 0x1p-20f);
+  }
+  return ok;
+}
+
 __global__ void __launch_bounds__(256) bin_count_kernel(KArgs a_in) {
   const KArgs a = resolve(a_in);
   unsigned bad = 0, bad_sigma = 0;
@@ -25,11 +47,7 @@ __global__ void __launch_bounds__(256) bin_count_kernel(KArgs a_in) {
       float2 p = reinterpret_cast<const float2*>(g.points)[i];
       bool fin = isfinite(p.x) && isfinite(p.y);
       for (int c = 0; c < a.C; ++c) fin = fin && isfinite(g.values[i * a.C + c]);
-      for (int e = 0; g.sigmas && e <= g.aniso; ++e) {
-        const float si = g.sigmas[(1 + g.aniso) * i + e];
-        fin = fin && isfinite(si);
-        if (isfinite(si) && !(si <= g.sigma && si >= g.sigma * 0x1p-32f)) bad_sigma = 1;
-      }
+      if (g.sigmas && !sigmas_ok(g, g.sigmas + g.pp_kind * i, fin)) bad_sigma = 1;
       if (!fin) bad = 1;
       long long bin;
       bool oob;

@@ -37,8 +37,9 @@ static __device__ __forceinline__ void bin_scatter_body(const KArgs& a, int nblo
       a.w.sval[dst] = c;
       a.w.perm[dst] = (unsigned)i;
       if (g.sigmas) {
-        const float sx = g.sigmas[g.aniso ? 2 * i : i];
-        a.w.spp[dst] = pp_consts(g.sigma, sx, g.aniso ? g.sigmas[2 * i + 1] : sx);
+        const float* sg = g.sigmas + g.pp_kind * i;
+        if (g.pp_kind == 3) a.w.spp[dst] = pp_cov_consts(g.sigma, sg[0], sg[1], sg[2]);
+        else a.w.spp[dst] = pp_consts(g.sigma, sg[0], g.pp_kind == 2 ? sg[1] : sg[0]);
       }
     }
   }

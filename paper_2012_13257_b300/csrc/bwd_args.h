@@ -14,7 +14,7 @@ struct BwdImage {
   float* gpts;          // [N,2] or null
   float* gvals;         // [N,C] or null
   float* gsig;          // [1] or null
-  float* gsigs;         // [N] per-point sigma gradients (per-point sigma calls) or null
+  float* gsigs;         // per-point sigma gradients, pp_kind floats per point, or null
   float inv_s2, inv_s3; // 1/sigma^2, 1/sigma^3
 };
 
@@ -22,7 +22,7 @@ struct BwdArgs {
   BwdImage one;              // the image of a single-image call
   const BwdImage* table;     // batched: per-image table (else null)
   int trunc;
-  int pp;                    // per-point sigmas (single image, truncated mode)
+  int pp;                    // per-point sigmas (single image, truncated mode): 1 separable, 2 full
 };
 
 cudaError_t launch_backward(const KArgs& a, const BwdArgs& b, cudaStream_t s);

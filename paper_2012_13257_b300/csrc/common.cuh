@@ -20,7 +20,7 @@ enum : unsigned {
   ST_NONFINITE = 1u,   // NaN/Inf among point coordinates or values
   ST_INTERNAL = 2u,    // a consistency check failed (e.g. a list overflowed)
   ST_TIMEOUT = 4u,     // a bounded wait gave up
-  ST_SIGMA = 8u,       // a per-point sigma outside [sigma * 2^-32, sigma]
+  ST_SIGMA = 8u,       // a per-point sigma outside its range (sigmas_ok)
 };
 
 // Slots of the status/counter block at the start of every workspace.
@@ -45,8 +45,9 @@ struct ImageGeom {
   float* image;          // [H,W,C]
   float* den;            // [H,W] or null
   float* shift;          // [H,W] or null
-  const float* sigmas;   // per-point sigmas (bounded by `sigma`): [n], or [n,2] = (sx, sy) when
-                         //   aniso; null: every point has `sigma`
+  const float* sigmas;   // per-point sigmas, pp_kind floats each (sx, sy bounded by `sigma`):
+                         //   [n] sigma_i, [n,2] (sx, sy) or [n,3] (sx, sy, rho); null: every
+                         //   point has `sigma`
   long long n;           // points of this image
   long long pt_base;     // first point in the concatenated point space
   long long bin_base;    // first bin in the concatenated bin space
@@ -65,7 +66,7 @@ struct ImageGeom {
   float u_near_max;      // largest nearest-distance bound the near kernel accepts
   float e_trunc;         // k^2 log2(e) / 2: per-point sigma keeps kappa_i d^2 <= this
   int vec_ok;            // rows of image/den/shift may use 16-byte stores
-  int aniso;             // sigmas holds an axis-aligned (sx, sy) pair per point
+  int pp_kind;           // floats per point in sigmas: 1, 2 or 3 (0 without sigmas)
   long long px_base;     // first pixel in the concatenated pixel space
   long long mt_base;     // first micro-tile in the concatenated micro-tile space
 };
@@ -87,7 +88,7 @@ struct DevWork {
                          //   distance (+inf: far-field micro-tile), written by the plan
   unsigned* perm;        // [n_total]: input index of each bin-sorted point
   float4* spp;           // [n_total]: per-point sigma constants of each bin-sorted point
-                         //   (pp_consts); written only with sigmas
+                         //   (pp_consts or pp_cov_consts); written only with sigmas
   // backward pass only
   float4* pplane;        // [pixels * (C == 4 ? 2 : 1)]: g_c / den and s' per core pixel
   unsigned* fbflag;      // [mt_total]: micro-tile holds a non-core pixel
@@ -203,6 +204,21 @@ __device__ __forceinline__ float shifted_sqdist(float qx, float qy, float px, fl
 __device__ __forceinline__ float4 pp_consts(float sigma, float sx, float sy) {
   constexpr float kSqrtHalfLog2e = 0.84932180028801907f;   // sqrt(log2(e) / 2)
   return make_float4(kSqrtHalfLog2e / sx, kSqrtHalfLog2e / sy, log2f(sigma / sx) + log2f(sigma / sy), 0.0f);
+}
+
+// Full covariance S_i = [[sx^2, rho sx sy], [rho sx sy, sy^2]] per point: the
+// weight is N(q | mu_i, S_i), up to the same common factor
+//   2^(la_i - (kxx dx^2 + kxy dx dy + kyy dy^2)),
+//   kxx = log2(e) / (2 sx^2 (1 - rho^2)),  kyy = log2(e) / (2 sy^2 (1 - rho^2)),
+//   kxy = -log2(e) rho / (sx sy (1 - rho^2)),
+//   la_i = log2(sigma^2 / (sx sy sqrt(1 - rho^2))),
+// the bracket being d^T S_i^-1 d log2(e) / 2.  Returns (kxx, kxy, kyy, la_i).
+__device__ __forceinline__ float4 pp_cov_consts(float sigma, float sx, float sy, float rho) {
+  constexpr float kHalfLog2e = 0.72134752044448170f;   // log2(e) / 2
+  const float e = fmaf(-rho, rho, 1.0f);
+  const float kxx = kHalfLog2e / (sx * sx * e), kyy = kHalfLog2e / (sy * sy * e);
+  const float kxy = -2.0f * kHalfLog2e * rho / (sx * sy * e);
+  return make_float4(kxx, kxy, kyy, log2f(sigma / sx) + log2f(sigma / sy) - 0.5f * log2f(e));
 }
 
 // Bin coordinate of a position along one axis, clamped to [0, nb-1]; NaN maps to 0.

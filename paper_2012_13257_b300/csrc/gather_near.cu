@@ -32,11 +32,14 @@
 // In truncated mode (the literal "radius k sigma" reading) R = k sigma, each
 // pixel keeps only points with d^2 <= k^2 sigma^2, and nothing is queued.
 //
-// Per-point sigma (truncated mode only; isotropic or axis-aligned): point i
-// weighs 2^(la_i - kx_i dx^2 - ky_i dy^2) (pp_consts) and counts inside its
-// ellipse kx_i dx^2 + ky_i dy^2 <= k^2 log2(e) / 2; the candidate window is
-// that of the bound sigma >= sx_i, sy_i, and the factorisation is unchanged:
-// gx = 2^(-kx_i dx^2), gy = 2^(la_i - ky_i dy^2).
+// Per-point sigma (truncated mode only; PPK = 1: isotropic or axis-aligned):
+// point i weighs 2^(la_i - kx_i dx^2 - ky_i dy^2) (pp_consts) and counts
+// inside its ellipse kx_i dx^2 + ky_i dy^2 <= k^2 log2(e) / 2; the candidate
+// window is that of the bound sigma >= sx_i, sy_i, and the factorisation is
+// unchanged: gx = 2^(-kx_i dx^2), gy = 2^(la_i - ky_i dy^2).  PPK = 2, a full
+// covariance (pp_cov_consts): the cross term kxy dx dy does not factorise,
+// so every pixel takes its own exponential of
+// la_i - (kxx dx^2 + kyy dy^2 + kxy dx dy), from per-column and per-row parts.
 #include "bin_body.cuh"
 
 namespace gmi {
@@ -302,8 +305,9 @@ struct NearOcc {
 
 constexpr int kNearWarps = 4;   // warps per near-kernel block
 
-template <int MTH, int MTW, int C, bool TRUNC, bool PP>
+template <int MTH, int MTW, int C, bool TRUNC, int PPK>
 __global__ void __launch_bounds__(128, NearOcc<MTH, MTW, C>::value) near_kernel(KArgs a_in) {
+  constexpr bool PP = PPK != 0;   // per-point sigmas (1: separable, 2: full covariance)
   static_assert(TRUNC || !PP, "per-point sigma is built for truncated mode only");
   const KArgs a = resolve(a_in);
   constexpr int NA = MTH * MTW * (C + 1);   // accumulators per thread
@@ -366,6 +370,37 @@ __global__ void __launch_bounds__(128, NearOcc<MTH, MTW, C>::value) near_kernel(
 #pragma unroll
       for (int q = 1; q < NP; ++q) cp[q] = make_float2(c4[2 * q - 1], c4[2 * q]);
       const float clast = c4[C - 1];   // the scalar accumulator's value (C even)
+      if constexpr (PPK == 2) {
+        // full covariance: e = -(kxx dx^2 + kyy dy^2 + kxy dx dy) per pixel
+        const float dx0 = xq0 - p.x, dy0 = yq0 - p.y;
+        float dx[MTW], ax[MTW], ay[MTH], by[MTH];
+#pragma unroll
+        for (int j = 0; j < MTW; ++j) {
+          dx[j] = __fadd_rn(dx0, (float)j);
+          ax[j] = __fmul_rn(-__fmul_rn(spc.x, dx[j]), dx[j]);
+        }
+#pragma unroll
+        for (int r = 0; r < MTH; ++r) {
+          const float dy = __fadd_rn(dy0, (float)r);
+          ay[r] = __fmul_rn(-__fmul_rn(spc.z, dy), dy);
+          by[r] = __fmul_rn(-spc.y, dy);
+        }
+#pragma unroll
+        for (int r = 0; r < MTH; ++r)
+#pragma unroll
+          for (int j = 0; j < MTW; ++j) {
+            const float e = __fmaf_rn(by[r], dx[j], __fadd_rn(ax[j], ay[r]));
+            const float wgt = e >= neg_thr ? ex2(__fadd_rn(e, spc.w)) : 0.0f;
+            const float2 ww = make_float2(wgt, wgt);
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+              float2& acq = accp[(r * MTW + j) * NP + q];
+              acq = __ffma2_rn(ww, cp[q], acq);
+            }
+            if (ODD) accs[(r * MTW + j) * ODD] = fmaf(wgt, clast, accs[(r * MTW + j) * ODD]);
+          }
+        return;
+      }
       const float u = (xq0 - p.x) * sk;
       const float v = (yq0 - p.y) * sky;
       float ax[MTW], gx[MTW], ay[MTH], gy[MTH];
@@ -578,29 +613,31 @@ __global__ void __launch_bounds__(128, NearOcc<MTH, MTW, C>::value) near_kernel(
 
 // Resident blocks per SM of one near-kernel instantiation (register-limited,
 // as the launch bounds ask), cached; all devices of a process are taken to be alike.
-template <int MTH, int MTW, int C, bool TRUNC, bool PP>
+template <int MTH, int MTW, int C, bool TRUNC, int PPK>
 static int near_occ() {
   static const int n = [] {
     int b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, near_kernel<MTH, MTW, C, TRUNC, PP>, 32 * kNearWarps, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, near_kernel<MTH, MTW, C, TRUNC, PPK>, 32 * kNearWarps, 0);
     return b > 0 ? b : 1;
   }();
   return n;
 }
 
-template <int MTH, int MTW, int C, bool TRUNC, bool PP>
+template <int MTH, int MTW, int C, bool TRUNC, int PPK>
 static cudaError_t launch_near_k(const KArgs& a, int grid, cudaStream_t s) {
-  near_kernel<MTH, MTW, C, TRUNC, PP><<<grid, 32 * kNearWarps, 0, s>>>(a);
+  near_kernel<MTH, MTW, C, TRUNC, PPK><<<grid, 32 * kNearWarps, 0, s>>>(a);
   return cudaGetLastError();
 }
 
-// mode: 0 exact, 1 truncated, 2 truncated with per-point sigma
+// mode: 0 exact, 1 truncated, 2 truncated with separable per-point sigmas,
+// 3 truncated with a full covariance per point
 template <int MTH, int MTW, int C>
 static cudaError_t launch_near_c(const KArgs& a, int mode, int grid, cudaStream_t s) {
   switch (mode) {
-    case 0: return launch_near_k<MTH, MTW, C, false, false>(a, grid, s);
-    case 1: return launch_near_k<MTH, MTW, C, true, false>(a, grid, s);
-    default: return launch_near_k<MTH, MTW, C, true, true>(a, grid, s);
+    case 0: return launch_near_k<MTH, MTW, C, false, 0>(a, grid, s);
+    case 1: return launch_near_k<MTH, MTW, C, true, 0>(a, grid, s);
+    case 2: return launch_near_k<MTH, MTW, C, true, 1>(a, grid, s);
+    default: return launch_near_k<MTH, MTW, C, true, 2>(a, grid, s);
   }
 }
 
@@ -625,10 +662,11 @@ cudaError_t launch_scatter_plan(const KArgs& a, bool trunc, int n_scatter, cudaS
   return cudaGetLastError();
 }
 
-static int near_mode(bool trunc, bool pp) { return pp ? 2 : (trunc ? 1 : 0); }
+// ppk: 0 shared sigma, 1 separable per-point sigmas, 2 full covariance per point
+static int near_mode(bool trunc, int ppk) { return ppk ? 1 + ppk : (trunc ? 1 : 0); }
 
-cudaError_t launch_near(const KArgs& a, int mth, int mtw, bool trunc, bool pp, int grid, cudaStream_t s) {
-  const int m = near_mode(trunc, pp);
+cudaError_t launch_near(const KArgs& a, int mth, int mtw, bool trunc, int ppk, int grid, cudaStream_t s) {
+  const int m = near_mode(trunc, ppk);
   if (mth == 4 && mtw == 4) return launch_near_mt<4, 4>(a, m, grid, s);
   if (mth == 4 && mtw == 8) return launch_near_mt<4, 8>(a, m, grid, s);
   if (mth == 2 && mtw == 4) return launch_near_mt<2, 4>(a, m, grid, s);
@@ -639,9 +677,10 @@ cudaError_t launch_near(const KArgs& a, int mth, int mtw, bool trunc, bool pp, i
 template <int MTH, int MTW, int C>
 static int occ_c(int mode) {
   switch (mode) {
-    case 0: return near_occ<MTH, MTW, C, false, false>();
-    case 1: return near_occ<MTH, MTW, C, true, false>();
-    default: return near_occ<MTH, MTW, C, true, true>();
+    case 0: return near_occ<MTH, MTW, C, false, 0>();
+    case 1: return near_occ<MTH, MTW, C, true, 0>();
+    case 2: return near_occ<MTH, MTW, C, true, 1>();
+    default: return near_occ<MTH, MTW, C, true, 2>();
   }
 }
 
@@ -655,9 +694,9 @@ static int occ_mt(int C, int mode) {
   }
 }
 
-int near_blocks_per_sm(int mth, int mtw, int C, bool trunc, bool pp) {
+int near_blocks_per_sm(int mth, int mtw, int C, bool trunc, int ppk) {
   const int c = C < 1 ? 1 : (C > 4 ? 4 : C);
-  const int m = near_mode(trunc, pp);
+  const int m = near_mode(trunc, ppk);
   if (mth == 4 && mtw == 8) return occ_mt<4, 8>(c, m);
   if (mth == 2 && mtw == 4) return occ_mt<2, 4>(c, m);
   return occ_mt<4, 4>(c, m);

@@ -301,7 +301,7 @@ def test_aniso_range_reported(cuda_device):
             g.interpolate_pp(P, V, to_dev(sxy, cuda_device), 1.0, 12, 12, check=True)
         assert e.value.status == status, (ax, bad, e.value.status)
     with pytest.raises(ValueError):
-        g.interpolate_pp(P, V, to_dev(np.full((im.N, 3), 0.5, np.float32), cuda_device), 1.0, 12, 12)
+        g.interpolate_pp(P, V, to_dev(np.full((im.N, 4), 0.5, np.float32), cuda_device), 1.0, 12, 12)
 
 
 def test_aniso_full_size_sampled(cuda_device):
@@ -343,4 +343,123 @@ def test_aniso_autograd_op(cuda_device):
     (img * to_dev(g, cuda_device)).sum().backward()
     ref = oracle.backward_aniso(im.points, im.values, sxy, H, W, g, mode=oracle.TRUNCATED, k=k)
     ref["sigmas"] = ref["sigmas_xy"]
+    assert_grads((P.grad.cpu().numpy(), V.grad.cpu().numpy(), S.grad.cpu().numpy()), ref)
+
+
+# ---------------------------------------------- full covariance (sx_i, sy_i, rho_i) per point
+def check_forward_cov(im, cov, bound, dev, k, **kw):
+    out, den = run(im, cov, bound, dev, k=k, **kw)
+    ref = oracle.forward_cov(im.points, im.values, cov, im.H, im.W, mode=oracle.TRUNCATED, k=k)
+    decided = ref["skipped"] < 1e-3
+    assert decided.mean() > 0.99
+    assert np.isfinite(out).all()
+    assert np.abs(out.astype(np.float64) - ref["image"])[decided].max() <= TOL_FWD
+    scaled = ref["den"] * float(bound) ** 2
+    live = decided & (scaled > 0)
+    assert (np.abs(den.astype(np.float64) - scaled)[live] / scaled[live]).max() <= 1e-4
+    empty = (ref["den"] == 0) & decided
+    assert (out[empty] == 0).all()
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: "s%d_N%d_%dx%d_C%d" % c[:5])
+@pytest.mark.parametrize("variant", [1, 2, 3])
+def test_cov_forward_matches_oracle(cuda_device, case, variant):
+    seed, N, H, W, C, lo, hi, k, clustered = case
+    im = wl.tiny_random(seed, N, H, W, C=C, sigma=hi, clustered=clustered, margin=2.0 if not clustered else 0.0)
+    cov = wl.point_cov(seed + 9, N, lo, hi, rmax=0.9)
+    check_forward_cov(im, cov, wl.cov_bound(cov), cuda_device, k, variant=variant)
+
+
+def test_cov_zero_correlation_matches_aniso(cuda_device):
+    im = wl.tiny_random(35, 800, 60, 70, C=3, sigma=1.4, clustered=True)
+    cov = wl.point_cov(36, im.N, 0.4, 1.4)
+    cov[:, 2] = 0.0
+    a, da = run(im, cov, 1.4, cuda_device, k=3.0)
+    b, db = run(im, cov[:, :2].copy(), 1.4, cuda_device, k=3.0)
+    ref = oracle.forward_aniso(im.points, im.values, cov[:, :2].copy(), im.H, im.W, mode=oracle.TRUNCATED, k=3.0)
+    decided = ref["skipped"] < 1e-3
+    assert np.abs(a - b)[decided].max() <= 2e-6
+    np.testing.assert_allclose(da[decided], db[decided], rtol=2e-6, atol=1e-30)
+
+
+def test_cov_range_reported(cuda_device):
+    g = gmi()
+    im = wl.tiny_random(37, 50, 12, 12, C=3, sigma=1.0)
+    P, V = to_dev(im.points, cuda_device), to_dev(im.values, cuda_device)
+    for ax, bad, status in ((2, 0.995, 1), (2, -1.5, 1), (0, 1.2, 1), (2, np.nan, 2)):
+        cov = np.tile(np.float32([0.5, 0.6, 0.3]), (im.N, 1))
+        cov[11, ax] = bad
+        with pytest.raises(g.GmiError) as e:
+            g.interpolate_pp(P, V, to_dev(cov, cuda_device), 1.0, 12, 12, check=True)
+        assert e.value.status == status, (ax, bad, e.value.status)
+    # sx = sy = bound with rho = 0.5: inside the box, but the ellipse's major
+    # axis reaches k sqrt(1.5) bound, past the search radius
+    cov = np.tile(np.float32([1.0, 1.0, 0.5]), (im.N, 1))
+    with pytest.raises(g.GmiError) as e:
+        g.interpolate_pp(P, V, to_dev(cov, cuda_device), 1.0, 12, 12, check=True)
+    assert e.value.status == 1
+    g.interpolate_pp(P, V, to_dev(cov, cuda_device), wl.cov_bound(cov), 12, 12, check=True)
+
+
+def test_cov_full_size_sampled(cuda_device):
+    """The 1024^2 upsampling workload with sx_i, sy_i log-uniform in
+    [0.4, 1.5] px and rho_i uniform in [-0.9, 0.9] (bound 1.5, k = 3), on a
+    pixel sample."""
+    im = wl.upsample_1024()
+    cov = wl.point_cov(38, im.N, 0.4, 1.5, rmax=0.9)
+    out, den = run(im, cov, wl.cov_bound(cov), cuda_device, k=3.0)
+    pix = sample_pixels(im.points, im.H, im.W, n_far=0)
+    ref = oracle.forward_cov(im.points, im.values, cov, im.H, im.W, mode=oracle.TRUNCATED, k=3.0, pixels=pix)
+    decided = ref["skipped"] < 1e-3
+    assert np.abs(out.reshape(-1, 3)[pix] - ref["image"])[decided].max() <= TOL_FWD
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: "s%d_N%d_%dx%d_C%d" % c[:5])
+def test_cov_backward_matches_oracle(cuda_device, case):
+    seed, N, H, W, C, lo, hi, k, clustered = case
+    im = wl.tiny_random(seed, N, H, W, C=C, sigma=hi, clustered=clustered, margin=2.0 if not clustered else 0.0)
+    cov = wl.point_cov(seed + 9, N, lo, hi, rmax=0.9)
+    g = np.random.default_rng(seed + 100).standard_normal((H, W, C)).astype(np.float32)
+    ref = oracle.backward_cov(im.points, im.values, cov, H, W, g, mode=oracle.TRUNCATED, k=k)
+    ref["sigmas"] = ref["cov"]
+    got = gpu_grads(im, cov, wl.cov_bound(cov), g, cuda_device, k)
+    assert got[2].shape == (N, 3)
+    assert_grads(got, ref)
+
+
+def test_cov_backward_variants_and_determinism(cuda_device):
+    import torch
+    G = gmi()
+    seed, N, H, W, C, lo, hi, k, clustered = CASES[1]
+    im = wl.tiny_random(seed, N, H, W, C=C, sigma=hi, clustered=clustered)
+    cov = wl.point_cov(seed + 9, N, lo, hi, rmax=0.9)
+    g = np.random.default_rng(seed + 100).standard_normal((H, W, C)).astype(np.float32)
+    ref = oracle.backward_cov(im.points, im.values, cov, H, W, g, mode=oracle.TRUNCATED, k=k)
+    ref["sigmas"] = ref["cov"]
+    bound = wl.cov_bound(cov)
+    for variant in (2, 3):
+        assert_grads(gpu_grads(im, cov, bound, g, cuda_device, k, variant=variant), ref)
+    P, V, S = to_dev(im.points, cuda_device), to_dev(im.values, cuda_device), to_dev(cov, cuda_device)
+    img, den = G.interpolate_pp(P, V, S, bound, H, W, radius_sigmas=k, return_aux=True)
+    gg = to_dev(g, cuda_device)
+    a = G.interpolate_backward_pp(P, V, S, bound, H, W, img, den, gg, radius_sigmas=k)
+    b = G.interpolate_backward_pp(P, V, S, bound, H, W, img, den, gg, radius_sigmas=k)
+    torch.cuda.synchronize()
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
+
+
+def test_cov_autograd_op(cuda_device):
+    G = gmi()
+    seed, N, H, W, C, lo, hi, k, clustered = CASES[2]
+    im = wl.tiny_random(seed, N, H, W, C=C, sigma=hi, clustered=clustered)
+    cov = wl.point_cov(seed + 9, N, lo, hi, rmax=0.9)
+    g = np.random.default_rng(seed + 100).standard_normal((H, W, C)).astype(np.float32)
+    P = to_dev(im.points, cuda_device).requires_grad_(True)
+    V = to_dev(im.values, cuda_device).requires_grad_(True)
+    S = to_dev(cov, cuda_device).requires_grad_(True)
+    img = G.gmi_interpolate_pp(P, V, S, wl.cov_bound(cov), H, W, radius_sigmas=k)
+    (img * to_dev(g, cuda_device)).sum().backward()
+    ref = oracle.backward_cov(im.points, im.values, cov, H, W, g, mode=oracle.TRUNCATED, k=k)
+    ref["sigmas"] = ref["cov"]
     assert_grads((P.grad.cpu().numpy(), V.grad.cpu().numpy(), S.grad.cpu().numpy()), ref)

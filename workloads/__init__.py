@@ -229,6 +229,23 @@ def point_sigmas(seed: int, n: int, lo: float, hi: float, axes: int = 1) -> np.n
     size = n if axes == 1 else (n, axes)
     return _f32(np.exp(rng.uniform(np.log(lo), np.log(hi), size)))
 
+def point_cov(seed: int, n: int, lo: float, hi: float, rmax: float = 0.8) -> np.ndarray:
+    """Per-point covariances (sx, sy, rho) [n, 3] (float32): sx, sy
+    log-uniform in [lo, hi], rho uniform in [-rmax, rmax]."""
+    rng = np.random.default_rng(seed)
+    s = np.exp(rng.uniform(np.log(lo), np.log(hi), (n, 2)))
+    return _f32(np.concatenate([s, rng.uniform(-rmax, rmax, (n, 1))], 1))
+
+
+def cov_bound(cov) -> float:
+    """The largest sqrt(lambda_max) over the covariances (sx, sy, rho) [n, 3]
+    (float64, rounded up by a relative 1e-6): the search-radius bound a full
+    covariance per point needs."""
+    c = np.asarray(cov, np.float64).reshape(-1, 3)
+    a, d, b = c[:, 0] ** 2, c[:, 1] ** 2, c[:, 2] * c[:, 0] * c[:, 1]
+    lam = 0.5 * (a + d) + np.sqrt((0.5 * (a - d)) ** 2 + b * b)
+    return float(np.sqrt(lam.max()) * (1 + 1e-6)) if c.shape[0] else 1.0
+
 def tiny_random(seed: int, N: int, H: int, W: int, C: int = 3, sigma: float = 1.0,
                 clustered: bool = False, margin: float = 0.0) -> Image:
     """Small random case; ``margin`` widens the position range beyond the frame
