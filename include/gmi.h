@@ -319,10 +319,13 @@ gmi_status gmi_autotune(const float* points, const float* values, int64_t N, int
  * the library holds it until the process exits).  It calls no cudaMalloc,
  * cudaFree or other allocating routine.
  *
- *   - Limit: problems whose gmi_workspace_size exceeds
- *     GMI_NOALLOC_SCRATCH_BYTES are rejected with GMI_ERR_CAPACITY before
- *     anything is enqueued (a 1024x1024 output from 262,144 points with C = 3
- *     needs about 28 MiB and fits; use gmi_forward beyond the limit).
+ *   - Limit: the forward uses only the leading part of the workspace layout
+ *     (gmi_workspace_size less the backward pass's planes); problems whose
+ *     forward part exceeds GMI_NOALLOC_SCRATCH_BYTES are rejected with
+ *     GMI_ERR_CAPACITY before anything is enqueued.  A 768x768 output from
+ *     147,456 points with C = 3 needs about 18.6 MiB and fits; a 1024x1024
+ *     output from 262,144 points needs about 33 MiB and does not: use
+ *     gmi_forward beyond the limit.
  *   - The first call on each device looks up the device address of the array
  *     (cudaGetSymbolAddress) with that device current; make that first call
  *     before any stream capture.

@@ -110,8 +110,11 @@ void set_vec_ok(ImageGeom& g) {
 size_t slot_bytes_for(int mth, int mtw, int C) { return sizeof(float) * 32u * mth * mtw * (C + 1); }
 
 // Workspace layout for totals (points, bins, micro-tiles, warp tiles); bytes.
+long long sat_entries(const ImageGeom& g) { return (long long)(g.nby + 1) * (long long)(g.nbx + 1); }
+long long sat_jobs(const ImageGeom& g) { return (g.nbx + 1 + 31) / 32; }
+
 WsLayout ws_layout(long long n_total, long long nb_total, long long mt_total, long long wt_total,
-                   size_t slot_bytes, long long extra_bytes) {
+                   long long sat_entries, size_t slot_bytes, long long extra_bytes) {
   WsLayout L;
   size_t o = 0;
   L.cap_items = (unsigned)std::min<long long>(wt_total * kSplitMax, 0x7fffffffLL);
@@ -131,6 +134,7 @@ WsLayout ws_layout(long long n_total, long long nb_total, long long mt_total, lo
   L.items = o;  o = align_up(o + sizeof(uint4) * (size_t)(L.cap_items > 0 ? L.cap_items : 1), 256);
   L.slots = o;  o = align_up(o + slot_bytes * (size_t)L.cap_slots, 256);
   L.ubound = o; o = align_up(o + sizeof(float) * 32u * (size_t)(wt_total > 0 ? wt_total : 1), 256);
+  L.sat = o;    o = align_up(o + sizeof(unsigned) * (size_t)(sat_entries > 0 ? sat_entries : 1), 256);
   L.extra = o;  o = align_up(o + (size_t)extra_bytes, 256);
   L.total = o;
   return L;
@@ -153,6 +157,7 @@ DevWork bind_ws(void* ws, const WsLayout& L) {
   w.ubound = (float*)(b + L.ubound);
   w.perm = (unsigned*)(b + L.perm);
   w.spp = (float4*)(b + L.spp);
+  w.sat = (unsigned*)(b + L.sat);
   w.pplane = nullptr;
   w.fbflag = nullptr;
   w.fbq = nullptr;
@@ -233,9 +238,13 @@ using namespace gmi;
 
 // Forward pass with one shared sigma (sigmas == null) or per-point sigmas,
 // pp_kind floats per point: isotropic [N], axis-aligned [N,2] or full [N,3].
+// fwd_share: the workspace need only hold the forward's leading part of the
+// layout (everything before the backward's region), which the forward alone
+// touches.
 static gmi_status forward_impl(const float* points, const float* values, const float* sigmas, int pp_kind,
                                int64_t N, int C, int H, int W, const gmi_params* p, float* image, float* den_out,
-                               float* shift_out, void* workspace, size_t ws_bytes, gmi_stream_t stream) {
+                               float* shift_out, void* workspace, size_t ws_bytes, gmi_stream_t stream,
+                               bool fwd_share = false) {
   gmi_status st = check_params(p);
   if (st != GMI_OK) return st;
   if ((st = check_shape(N, C, H, W)) != GMI_OK) return st;
@@ -259,8 +268,10 @@ static gmi_status forward_impl(const float* points, const float* values, const f
   const long long nb = (long long)g.nbx * g.nby;
   const long long mt = (long long)g.mtx * g.mty;
   const long long wt = (long long)g.wtx * g.wty;
-  const WsLayout L = ws_layout(N, nb, mt, wt, slot_bytes_for(mth, mtw, C), bwd_extra_bytes(N, C, H, W));
-  if (!workspace || ((uintptr_t)workspace & 255u) != 0 || ws_bytes < L.total) return GMI_ERR_WORKSPACE;
+  const WsLayout L =
+      ws_layout(N, nb, mt, wt, sat_entries(g), slot_bytes_for(mth, mtw, C), bwd_extra_bytes(N, C, H, W));
+  if (!workspace || ((uintptr_t)workspace & 255u) != 0 || ws_bytes < (fwd_share ? L.extra : L.total))
+    return GMI_ERR_WORKSPACE;
 
   if (N == 0) {  // no known point: colour 0 and den 0 everywhere
     const size_t px = (size_t)H * (size_t)W;
@@ -282,6 +293,7 @@ static gmi_status forward_impl(const float* points, const float* values, const f
   a.wt_total = wt;
   a.ch_total = (N + kChunk - 1) / kChunk;
   a.mt_total = mt;
+  a.satj_total = sat_jobs(g);
   const bool trunc = p->mode == GMI_MODE_TRUNCATED;
   const int ppk = g.pp_kind == 3 ? 2 : (g.pp_kind ? 1 : 0);
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -328,6 +340,33 @@ static gmi_status forward_impl(const float* points, const float* values, const f
   return (p->flags & GMI_FLAG_SYNC_CHECK) ? read_status(workspace, s) : GMI_OK;
 }
 
+namespace gmi {
+
+gmi_status forward_share_bytes(int64_t N, int C, int H, int W, const gmi_params* p, size_t* bytes) {
+  gmi_status st = check_params(p);
+  if (st != GMI_OK) return st;
+  if ((st = check_shape(N, C, H, W)) != GMI_OK) return st;
+  int mth, mtw;
+  variant_dims(p->variant, &mth, &mtw);
+  ImageGeom g;
+  memset(&g, 0, sizeof(g));
+  fill_geom(g, N, H, W, p->sigma, p->radius_sigmas, p->bin_px, mth, mtw);
+  const long long nb = (long long)g.nbx * g.nby;
+  const long long mt = (long long)g.mtx * g.mty;
+  const long long wt = (long long)g.wtx * g.wty;
+  *bytes = ws_layout(N, nb, mt, wt, sat_entries(g), slot_bytes_for(mth, mtw, C), 0).extra;
+  return GMI_OK;
+}
+
+gmi_status forward_in_share(const float* points, const float* values, int64_t N, int C, int H, int W,
+                            const gmi_params* p, float* image, float* den_out, float* shift_out, void* workspace,
+                            size_t ws_bytes, gmi_stream_t stream) {
+  return forward_impl(points, values, nullptr, 0, N, C, H, W, p, image, den_out, shift_out, workspace, ws_bytes,
+                      stream, true);
+}
+
+}  // namespace gmi
+
 extern "C" {
 
 const char* gmi_version(void) { return "gmi 0.1.0 sm_103a"; }
@@ -371,7 +410,7 @@ gmi_status gmi_workspace_size(int64_t N, int C, int H, int W, const gmi_params* 
   const long long nb = (long long)g.nbx * g.nby;
   const long long mt = (long long)g.mtx * g.mty;
   const long long wt = (long long)g.wtx * g.wty;
-  *bytes = ws_layout(N, nb, mt, wt, slot_bytes_for(mth, mtw, C), bwd_extra_bytes(N, C, H, W)).total;
+  *bytes = ws_layout(N, nb, mt, wt, sat_entries(g), slot_bytes_for(mth, mtw, C), bwd_extra_bytes(N, C, H, W)).total;
   return GMI_OK;
 }
 

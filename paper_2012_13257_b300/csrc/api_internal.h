@@ -10,7 +10,8 @@ namespace gmi {
 
 // Byte offsets of the regions of a workspace.
 struct WsLayout {
-  size_t status, off, oob, tile_done, zero_end, rank, sxy, sval, perm, spp, partials, farq, items, slots, ubound, extra, total;
+  size_t status, off, oob, tile_done, zero_end, rank, sxy, sval, perm, spp, partials, farq, items, slots, ubound, sat,
+      extra, total;
   unsigned cap_items, cap_slots;
 };
 
@@ -24,7 +25,10 @@ void set_vec_ok(ImageGeom& g);
 bool aligned16(const void* p);
 size_t slot_bytes_for(int mth, int mtw, int C);
 WsLayout ws_layout(long long n_total, long long nb_total, long long mt_total, long long wt_total,
-                   size_t slot_bytes, long long extra_bytes);
+                   long long sat_entries, size_t slot_bytes, long long extra_bytes);
+// Summed-area table of one image's bins: entries and 32-column build jobs.
+long long sat_entries(const ImageGeom& g);
+long long sat_jobs(const ImageGeom& g);
 DevWork bind_ws(void* ws, const WsLayout& L);
 gmi_status run_bin_and_plan(KArgs& a, const WsLayout& L, void* ws, int mth, int mtw, bool trunc,
                             cudaStream_t s, bool plan);
@@ -60,6 +64,13 @@ struct FwdGraphKey {
 // cached graph for `key`, or captures, instantiates, caches and launches one.
 gmi_status forward_graphed(const FwdGraphKey& key, gmi_status (*launch)(void*, cudaStream_t), void* ctx,
                            cudaStream_t s);
+
+// The forward's leading share of the workspace layout (the backward's region
+// excluded), and a forward pass that needs only that share (no-alloc path).
+gmi_status forward_share_bytes(int64_t N, int C, int H, int W, const gmi_params* p, size_t* bytes);
+gmi_status forward_in_share(const float* points, const float* values, int64_t N, int C, int H, int W,
+                            const gmi_params* p, float* image, float* den_out, float* shift_out, void* workspace,
+                            size_t ws_bytes, gmi_stream_t stream);
 
 // Extra workspace bytes the backward pass needs beyond the forward layout,
 // and where its regions start inside the extra block.

@@ -522,7 +522,8 @@ static gmi_status backward_impl(const float* points, const float* values, const 
   const long long nb = (long long)g.nbx * g.nby;
   const long long mt = (long long)g.mtx * g.mty;
   const long long wt = (long long)g.wtx * g.wty;
-  const WsLayout L = ws_layout(N, nb, mt, wt, slot_bytes_for(mth, mtw, C), bwd_extra_bytes(N, C, H, W));
+  const WsLayout L =
+      ws_layout(N, nb, mt, wt, sat_entries(g), slot_bytes_for(mth, mtw, C), bwd_extra_bytes(N, C, H, W));
   if (!workspace || ((uintptr_t)workspace & 255u) != 0 || ws_bytes < L.total) return GMI_ERR_WORKSPACE;
   if (grad_points && cudaMemsetAsync(grad_points, 0, sizeof(float) * 2 * (size_t)N, s) != cudaSuccess) return GMI_ERR_CUDA;
   if (grad_values && cudaMemsetAsync(grad_values, 0, sizeof(float) * (size_t)C * (size_t)N, s) != cudaSuccess) return GMI_ERR_CUDA;

@@ -34,7 +34,7 @@ struct gmi_batch_plan {
   int C = 3;
   gmi_params params;
   int mth = 4, mtw = 4;
-  long long cap_nb = 0, cap_mt = 0, cap_wt = 0, cap_ch = 0;
+  long long cap_nb = 0, cap_mt = 0, cap_wt = 0, cap_ch = 0, cap_sat = 0;
   gmi::WsLayout L;
   void* base = nullptr;             // one device allocation: workspace + tables
   size_t base_bytes = 0;
@@ -74,7 +74,8 @@ static size_t al256(size_t v) { return (v + 255) / 256 * 256; }
 
 // Geometry of image i of a batch (bases from the running totals).
 static void batch_geom(ImageGeom& g, const gmi_batch_plan* p, long long N, int H, int W, float sigma, int bin_px,
-                       long long* npt, long long* nb, long long* nwt, long long* nch, long long* nmt, long long* npx) {
+                       long long* npt, long long* nb, long long* nwt, long long* nch, long long* nmt, long long* npx,
+                       long long* nsat, long long* nsj) {
   memset(&g, 0, sizeof(g));
   fill_geom(g, N, H, W, sigma, p->params.radius_sigmas, bin_px > 0 ? bin_px : p->params.bin_px, p->mth, p->mtw);
   g.pt_base = *npt;
@@ -83,6 +84,10 @@ static void batch_geom(ImageGeom& g, const gmi_batch_plan* p, long long N, int H
   g.ch_base = *nch;
   g.mt_base = *nmt;
   g.px_base = *npx;
+  g.sat_base = *nsat;
+  g.satj_base = *nsj;
+  *nsat += sat_entries(g);
+  *nsj += sat_jobs(g);
   *npt += N;
   *nb += (long long)g.nbx * g.nby;
   *nwt += (long long)g.wtx * g.wty;
@@ -116,7 +121,9 @@ extern "C" gmi_status gmi_batch_plan_create(int max_images, int64_t max_points, 
   p->cap_mt = max_pixels / (p->mth * p->mtw) * 2 + 64LL * max_images + 1024;
   p->cap_wt = p->cap_mt / 32 * 2 + 8LL * max_images + 64;
   p->cap_ch = (max_points + kChunk - 1) / kChunk + max_images;
-  p->L = ws_layout(max_points, p->cap_nb, p->cap_mt, p->cap_wt, slot_bytes_for(p->mth, p->mtw, C), 0);
+  // sum over images of (nby + 1)(nbx + 1) <= bins + pixels + 2 images (nby + nbx <= H W + 1)
+  p->cap_sat = p->cap_nb + max_pixels + 2LL * max_images;
+  p->L = ws_layout(max_points, p->cap_nb, p->cap_mt, p->cap_wt, p->cap_sat, slot_bytes_for(p->mth, p->mtw, C), 0);
   p->stage_bytes = (stage_size(max_images) + 255) / 256 * 256;
   p->base_bytes = p->L.total + 2 * p->stage_bytes;
   if (cudaGetDevice(&p->device) != cudaSuccess || cudaMalloc(&p->base, p->base_bytes) != cudaSuccess ||
@@ -203,11 +210,11 @@ extern "C" gmi_status gmi_forward_batched(gmi_batch_plan* p, const gmi_image_des
 
   long long* tot = (long long*)sl.host;
   ImageGeom* table = (ImageGeom*)(sl.host + kTotCount * sizeof(long long));
-  long long npt = 0, nb = 0, nwt = 0, nch = 0, nmt = 0, npx = 0;
+  long long npt = 0, nb = 0, nwt = 0, nch = 0, nmt = 0, npx = 0, nsat = 0, nsj = 0;
   for (int i = 0; i < B; ++i) {
     const gmi_image_desc& d = descs[i];
     ImageGeom& g = table[i];
-    batch_geom(g, p, d.N, d.H, d.W, d.sigma, d.bin_px, &npt, &nb, &nwt, &nch, &nmt, &npx);
+    batch_geom(g, p, d.N, d.H, d.W, d.sigma, d.bin_px, &npt, &nb, &nwt, &nch, &nmt, &npx, &nsat, &nsj);
     g.points = d.points;
     g.values = d.values;
     g.image = d.image;
@@ -216,7 +223,7 @@ extern "C" gmi_status gmi_forward_batched(gmi_batch_plan* p, const gmi_image_des
     set_vec_ok(g);
   }
   if (npt > p->max_points || nb > p->cap_nb || nwt > p->cap_wt || nch > p->cap_ch || nmt > p->cap_mt ||
-      npx > p->max_pixels)
+      npx > p->max_pixels || nsat > p->cap_sat)
     return GMI_ERR_CAPACITY;
   tot[kTotImages] = B;
   tot[kTotPoints] = npt;
@@ -225,6 +232,7 @@ extern "C" gmi_status gmi_forward_batched(gmi_batch_plan* p, const gmi_image_des
   tot[kTotChunks] = nch;
   tot[kTotMicroTiles] = nmt;
   tot[kTotPixels] = npx;
+  tot[kTotSatJobs] = nsj;
 
   KArgs a;
   memset(&a, 0, sizeof(a));
@@ -238,6 +246,7 @@ extern "C" gmi_status gmi_forward_batched(gmi_batch_plan* p, const gmi_image_des
   a.wt_total = p->cap_wt;
   a.ch_total = p->cap_ch;
   a.mt_total = p->cap_mt;
+  a.satj_total = nsj;   // read from the device totals at run time
   const bool trunc = p->params.mode == GMI_MODE_TRUNCATED;
   const size_t copy_bytes = stage_size(p->max_images);
 
@@ -292,11 +301,11 @@ extern "C" gmi_status gmi_backward_batched(gmi_batch_plan* p, const gmi_grad_des
   long long* tot = (long long*)host;
   ImageGeom* table = (ImageGeom*)(host + kTotCount * sizeof(long long));
   BwdImage* btab = (BwdImage*)(host + stage_size(p->max_images));
-  long long npt = 0, nb = 0, nwt = 0, nch = 0, nmt = 0, npx = 0;
+  long long npt = 0, nb = 0, nwt = 0, nch = 0, nmt = 0, npx = 0, nsat = 0, nsj = 0;
   for (int i = 0; i < B; ++i) {
     const gmi_grad_desc& d = descs[i];
     ImageGeom& g = table[i];
-    batch_geom(g, p, d.N, d.H, d.W, d.sigma, d.bin_px, &npt, &nb, &nwt, &nch, &nmt, &npx);
+    batch_geom(g, p, d.N, d.H, d.W, d.sigma, d.bin_px, &npt, &nb, &nwt, &nch, &nmt, &npx, &nsat, &nsj);
     g.points = d.points;
     g.values = d.values;
     BwdImage& bi = btab[i];
@@ -311,7 +320,7 @@ extern "C" gmi_status gmi_backward_batched(gmi_batch_plan* p, const gmi_grad_des
     bi.inv_s3 = (float)(1.0 / ((double)d.sigma * d.sigma * d.sigma));
   }
   if (npt > p->max_points || nb > p->cap_nb || nwt > p->cap_wt || nch > p->cap_ch || nmt > p->cap_mt ||
-      npx > p->max_pixels)
+      npx > p->max_pixels || nsat > p->cap_sat)
     return GMI_ERR_CAPACITY;
   tot[kTotImages] = B;
   tot[kTotPoints] = npt;
@@ -320,6 +329,7 @@ extern "C" gmi_status gmi_backward_batched(gmi_batch_plan* p, const gmi_grad_des
   tot[kTotChunks] = nch;
   tot[kTotMicroTiles] = nmt;
   tot[kTotPixels] = npx;
+  tot[kTotSatJobs] = nsj;
   if (cudaMemcpyAsync(p->bwd_dev, host, bwd_stage_size(p->max_images), cudaMemcpyHostToDevice, s) != cudaSuccess)
     return GMI_ERR_CUDA;
 

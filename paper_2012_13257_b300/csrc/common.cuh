@@ -35,6 +35,7 @@ enum : int {
   kFbCount = 7,        // micro-tiles queued for the backward fallback kernel
   kFbHead = 8,         // next entry of that queue
   kSigDone = 9,        // blocks of the point-centric backward that have finished
+  kSatHead = 10,       // next summed-area-table column job
   kStatusWords = 64,
 };
 
@@ -69,6 +70,8 @@ struct ImageGeom {
   int pp_kind;           // floats per point in sigmas: 1, 2 or 3 (0 without sigmas)
   long long px_base;     // first pixel in the concatenated pixel space
   long long mt_base;     // first micro-tile in the concatenated micro-tile space
+  long long sat_base;    // first entry of this image's summed-area table ((nby+1) x (nbx+1))
+  long long satj_base;   // first of its table's column jobs (32 columns each)
 };
 
 // Device pointers into a workspace.
@@ -94,6 +97,8 @@ struct DevWork {
   unsigned* fbflag;      // [mt_total]: micro-tile holds a non-core pixel
   uint2* fbq;            // [mt_total]: queue of such micro-tiles (image, micro-tile)
   float* sig_part;       // [kSigParts]: per-block sigma-gradient partials
+  unsigned* sat;         // per image [(nby+1) x (nbx+1)]: points in bins [0,by) x [0,bx), built
+                         //   by the near kernel when the far-field queue is not empty
   const ImageGeom* table;// device descriptor table (batched) or null (single image)
 };
 
@@ -108,6 +113,7 @@ struct KArgs {
   long long ch_total;    // point chunks over all images
   long long mt_total;    // micro-tiles over all images
   long long px_total;    // output pixels over all images
+  long long satj_total;  // summed-area-table column jobs over all images
   unsigned cap_items;    // capacity of w.items
   unsigned cap_slots;    // capacity of w.slots, in slots
   int mth, mtw;          // micro-tile of the near kernel
@@ -116,7 +122,10 @@ struct KArgs {
 
 // Layout of the device totals of a batch (uploaded with its descriptor table),
 // so that one captured launch sequence serves any batch within capacity.
-enum : int { kTotImages = 0, kTotPoints, kTotBins, kTotWarpTiles, kTotChunks, kTotMicroTiles, kTotPixels, kTotCount = 8 };
+enum : int {
+  kTotImages = 0, kTotPoints, kTotBins, kTotWarpTiles, kTotChunks, kTotMicroTiles, kTotPixels, kTotSatJobs,
+  kTotCount = 8
+};
 
 // Kernel arguments with the totals of a batched call read from the device.
 __device__ __forceinline__ KArgs resolve(const KArgs& in) {
@@ -129,6 +138,7 @@ __device__ __forceinline__ KArgs resolve(const KArgs& in) {
     a.ch_total = in.totals[kTotChunks];
     a.mt_total = in.totals[kTotMicroTiles];
     a.px_total = in.totals[kTotPixels];
+    a.satj_total = in.totals[kTotSatJobs];
   }
   return a;
 }
@@ -144,7 +154,7 @@ __device__ __forceinline__ const ImageGeom* geom_ptr(const KArgs& a, int img) {
 }
 
 // Largest image index whose base (Field 0: chunks, 1: warp tiles, 2: points,
-// 3: pixels) is <= idx.
+// 3: pixels, 4: summed-area-table column jobs) is <= idx.
 template <int Field>
 __device__ __forceinline__ int find_image(const KArgs& a, long long idx) {
   if (a.w.table == nullptr) return 0;
@@ -152,7 +162,11 @@ __device__ __forceinline__ int find_image(const KArgs& a, long long idx) {
   while (lo < hi) {
     int mid = (lo + hi + 1) >> 1;
     const ImageGeom& t = a.w.table[mid];
-    const long long base = Field == 0 ? t.ch_base : (Field == 1 ? t.wt_base : (Field == 2 ? t.pt_base : t.px_base));
+    const long long base = Field == 0 ? t.ch_base
+                         : Field == 1 ? t.wt_base
+                         : Field == 2 ? t.pt_base
+                         : Field == 3 ? t.px_base
+                                      : t.satj_base;
     if (base <= idx) lo = mid; else hi = mid - 1;
   }
   return lo;

@@ -1,9 +1,9 @@
 // Candidate collection around a micro-tile, shared by the far-field forward
 // kernel and the backward fallback kernel: Chebyshev windows over the bin
-// grid, counted or enumerated one warp at a time.
+// grid, counted (summed-area table) or enumerated one warp at a time.
 #pragma once
 
-#include "common.cuh"
+#include "sat.cuh"
 
 namespace gmi {
 
@@ -22,80 +22,32 @@ __device__ __forceinline__ void window_bins(const ImageGeom& g, const FarTile& t
   by_hi = bin_coord(t.yb + h, g.inv_b, g.nby);
 }
 
-// Number of points in the bins covering the Chebyshev window of half-width h.
-static __device__ unsigned window_count(const KArgs& a, const ImageGeom& g, const FarTile& t, float h) {
-  int bx_lo, bx_hi, by_lo, by_hi;
-  window_bins(g, t, h, bx_lo, bx_hi, by_lo, by_hi);
-  const int lane = threadIdx.x & 31;
-  unsigned s = 0;
-  for (int by = by_lo + lane; by <= by_hi; by += 32) {
-    const long long rowb = g.bin_base + (long long)by * g.nbx;
-    s += a.w.off[rowb + bx_hi + 1] - a.w.off[rowb + bx_lo];
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  return s;
-}
-
-// Counts of points in the bins covering K nested Chebyshev windows of
-// half-widths h[0] <= ... <= h[K-1], in one pass over the rows of the
-// largest (each lane takes rows; the loads of all windows are independent).
-template <int K>
-static __device__ void window_counts(const KArgs& a, const ImageGeom& g, const FarTile& t, const float (&h)[K],
-                                     unsigned (&cnt)[K]) {
-  int bx_lo[K], bx_hi[K], by_lo[K], by_hi[K];
-#pragma unroll
-  for (int k = 0; k < K; ++k) window_bins(g, t, h[k], bx_lo[k], bx_hi[k], by_lo[k], by_hi[k]);
-  const int lane = threadIdx.x & 31;
-  unsigned s[K];
-#pragma unroll
-  for (int k = 0; k < K; ++k) s[k] = 0;
-  for (int by = by_lo[K - 1] + lane; by <= by_hi[K - 1]; by += 32) {
-    const long long rowb = g.bin_base + (long long)by * g.nbx;
-#pragma unroll
-    for (int k = 0; k < K; ++k)
-      if (by >= by_lo[k] && by <= by_hi[k]) s[k] += a.w.off[rowb + bx_hi[k] + 1] - a.w.off[rowb + bx_lo[k]];
-  }
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s[k] += __shfl_xor_sync(0xffffffffu, s[k], o);
-    cnt[k] = s[k];
-  }
-}
-
 // Half-width (a multiple of the bin edge) of the smallest Chebyshev window
-// around t, at bin resolution, that holds any point; -1 when none up to hmax.
-// Doubling four levels per pass, then eight bisection points per pass.
+// around t, at bin resolution, that holds any point; -1 when the image has
+// none.  Every count comes from the summed-area table (four loads), one
+// window per lane: a pass of doubling half-widths b 2^lane, then bisection
+// passes of 32 evenly spaced half-widths between the largest empty and the
+// smallest non-empty window found so far.
 static __device__ float smallest_window(const KArgs& a, const ImageGeom& g, const FarTile& t) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
   const float bf = (float)g.b;
-  const float hmax = 2.0f * (float)max(g.W, g.H) + bf;
-  float lo = 0.0f, hi = -1.0f;   // window lo is empty (or lo == 0), window hi is not
-  for (float h0 = bf; h0 < 2.0f * hmax; h0 *= 16.0f) {
-    const float h[4] = {h0, 2.0f * h0, 4.0f * h0, 8.0f * h0};
-    unsigned c[4];
-    window_counts<4>(a, g, t, h, c);
-    int k = 0;
-    while (k < 4 && c[k] == 0) ++k;
-    if (k < 4) {
-      hi = h[k];
-      lo = k > 0 ? h[k - 1] : (h0 > bf ? 0.5f * h0 : 0.0f);
-      break;
-    }
-  }
-  if (hi < 0.0f) return -1.0f;
-  // bisection at bin resolution: eight evenly spaced half-widths in (lo, hi)
+  auto nonempty = [&](float h) {
+    int bx_lo, bx_hi, by_lo, by_hi;
+    window_bins(g, t, h, bx_lo, bx_hi, by_lo, by_hi);
+    return sat_count(a, g, bx_lo, bx_hi, by_lo, by_hi) > 0u;
+  };
+  const unsigned nz = __ballot_sync(full, nonempty(ldexpf(bf, lane)));
+  if (nz == 0u) return -1.0f;
+  const int k = __ffs(nz) - 1;
+  float hi = ldexpf(bf, k);
+  float lo = k > 0 ? ldexpf(bf, k - 1) : 0.0f;   // window lo is empty (or lo == 0), window hi is not
   while (hi - lo > bf) {
-    const float step = fmaxf(bf, floorf((hi - lo) / (9.0f * bf)) * bf);
-    float h[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) h[j] = fminf(lo + (float)(j + 1) * step, hi);
-    unsigned c[8];
-    window_counts<8>(a, g, t, h, c);
-    int j = 0;
-    while (j < 8 && c[j] == 0) ++j;
-    const float nlo = j > 0 ? h[j - 1] : lo;
-    const float nhi = j < 8 ? h[j] : hi;
+    const float step = fmaxf(bf, floorf((hi - lo) / (32.0f * bf)) * bf);
+    const unsigned m = __ballot_sync(full, nonempty(fminf(lo + (float)(lane + 1) * step, hi)));
+    const int j = m ? __ffs(m) - 1 : 32;
+    const float nlo = j > 0 ? fminf(lo + (float)j * step, hi) : lo;
+    const float nhi = j < 32 ? fminf(lo + (float)(j + 1) * step, hi) : hi;
     if (nhi - nlo >= hi - lo) break;   // no progress (cannot happen; guards the loop)
     lo = nlo;
     hi = nhi;

@@ -41,6 +41,7 @@
 // so every pixel takes its own exponential of
 // la_i - (kxx dx^2 + kyy dy^2 + kxy dx dy), from per-column and per-row parts.
 #include "bin_body.cuh"
+#include "sat.cuh"
 
 namespace gmi {
 
@@ -608,6 +609,11 @@ __global__ void __launch_bounds__(128, NearOcc<MTH, MTW, C>::value) near_kernel(
       }
     }
     t = __shfl_sync(full, nt, 0);
+  }
+  // far-field micro-tiles queued: warps out of work build the summed-area
+  // table the far kernel's window search reads
+  if constexpr (!TRUNC) {
+    if (__ldcg(&a.w.status[kFarCount]) > 0u) sat_build(a);
   }
 }
 

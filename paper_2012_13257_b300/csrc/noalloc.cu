@@ -2,7 +2,8 @@
 // device memory (host applications that own the GPU memory pool, loops that
 // must not stall on cudaMalloc/cudaFree, bindings that cannot pass a
 // workspace).  Its scratch is one statically sized device array compiled into
-// this library; the pipeline it runs is gmi_forward's, unchanged.
+// this library; the pipeline it runs is gmi_forward's, unchanged, in the
+// forward's share of the workspace layout (the backward's region left out).
 #include <mutex>
 
 #include "api_internal.h"
@@ -41,11 +42,11 @@ gmi_status scratch_address(void** out) {
 extern "C" gmi_status gmi_forward_noalloc(const float* points, const float* values, int64_t N, int C, int H,
                                           int W, const gmi_params* p, float* image, float* den_out,
                                           float* shift_out, gmi_stream_t stream) {
-  size_t need = 0;
-  gmi_status st = gmi_workspace_size(N, C, H, W, p, &need);
+  size_t need = 0;   // the forward's share of the workspace: it never touches the backward's region
+  gmi_status st = gmi::forward_share_bytes(N, C, H, W, p, &need);
   if (st != GMI_OK) return st;
   if (need > kScratchBytes) return GMI_ERR_CAPACITY;   // too large for the static scratch
   void* ws = nullptr;
   if ((st = scratch_address(&ws)) != GMI_OK) return st;
-  return gmi_forward(points, values, N, C, H, W, p, image, den_out, shift_out, ws, kScratchBytes, stream);
+  return gmi::forward_in_share(points, values, N, C, H, W, p, image, den_out, shift_out, ws, kScratchBytes, stream);
 }
