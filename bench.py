@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--impl", default="gmi", choices=["gmi", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="headline workload only")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="batched: the default micro-tile and bin rule instead of the autotuned ones (for ncu "
+                         "captures, whose serialised timings mislead the autotuner)")
     ap.add_argument("--only", choices=["batched", "fwd_bwd", "serving", "reconstruction", "point_optimization",
                                        "per_point_sigma"],
                     help="run only this secondary workload and print its object (for profiling it)")
@@ -304,7 +307,7 @@ def e2e_pipelined(gmi, im, hP, hV, steps, D, world):
             "ms_per_step": total / steps, "note": "uploads, computes and downloads of consecutive steps overlap"}
 
 
-def bench_batched(dev, steps, warmup, flush, stream):
+def bench_batched(dev, steps, warmup, flush, stream, autotune=True):
     """64 uneven clustered images (sides log-uniform in [128, 1024],
     N = 0.25 H W, sigma U[0.5, 2]): one batched graph launch per step versus
     64 plain single-image launches, autotuned bin sizes and micro-tile."""
@@ -324,8 +327,10 @@ def bench_batched(dev, steps, warmup, flush, stream):
         if key not in rep or im.H * im.W > imgs[rep[key]].H * imgs[rep[key]].W:
             rep[key] = i
     t0 = time.perf_counter()
-    work = {}
-    for key, i in rep.items():
+    work = {1: 1}   # without tuning: the 4x4 micro-tile and the automatic bin rule
+    if autotune:
+        work = {}
+    for key, i in (rep.items() if autotune else ()):
         best, _ = tuner.tune(dimgs[i]["points"], dimgs[i]["values"], imgs[i].sigma, imgs[i].H, imgs[i].W,
                              reps=3, warmup=1, save=False)
         work.setdefault(best["variant"], 0)
@@ -358,7 +363,7 @@ def bench_batched(dev, steps, warmup, flush, stream):
             "plain_ms_per_step": sum(tp) / steps, "speedup_vs_plain": mb / mp, "images": len(imgs),
             "pixels": px, "points": int(sum(im.N for im in imgs)),
             "pairs_est": pairs, "pair_rate_gpair_s": pairs / (sum(tb) / steps * 1e-3) / 1e9,
-            "autotune": {"variant": variant, "buckets": len(rep), "tune_s": tune_s},
+            "autotune": {"variant": variant, "buckets": len(rep), "tune_s": tune_s, "on": bool(autotune)},
             "workload": "64 images, sides log-uniform [128,1024], N=0.25HW clustered (8 clusters), "
                         "sigma U[0.5,2], RGB f32; one CUDA-graph batched launch per step vs 64 plain launches"}
 
@@ -779,7 +784,8 @@ def main():
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     if args.only:
         stream = torch.cuda.current_stream(dev)
-        fn = {"batched": lambda: bench_batched(dev, args.steps, args.warmup, flush, stream),
+        fn = {"batched": lambda: bench_batched(dev, args.steps, args.warmup, flush, stream,
+                                               autotune=not args.no_autotune),
               "fwd_bwd": lambda: bench_fwd_bwd(dev, args.steps, args.warmup, flush, stream),
               "serving": lambda: bench_serving(dev),
               "reconstruction": lambda: bench_reconstruction(dev),
