@@ -4,6 +4,8 @@ binding) against the FP64 oracle, element by element.
 Bar: max-abs error <= 1e-4 on colours in [0, 1] (exact mode); truncated mode
 the same, on pixels whose result is not decided by a point lying on the
 radius within rounding (the oracle reports those)."""
+import math
+
 import numpy as np
 import pytest
 
@@ -231,3 +233,30 @@ def test_graph_replay(cuda_device):
     gr.replay()
     torch.cuda.synchronize()
     assert same(out3, out)
+
+
+def test_graph_replay_switches_the_far_field_on_and_off(cuda_device):
+    """One replayed graph, the same buffers: points spread over the frame (no
+    far-field micro-tile: the far kernel finds an empty queue) and then,
+    written in place, squeezed into a corner (most micro-tiles far, and the
+    summed-area table gets built), then spread again; each replay matches the
+    oracle."""
+    import torch
+    g = gmi()
+    rng = np.random.default_rng(61)
+    H, W, n = 120, 150, 4000
+    spread = np.stack([rng.uniform(0, W, n), rng.uniform(0, H, n)], 1).astype(np.float32)
+    corner = rng.uniform(0, 10, (n, 2)).astype(np.float32)
+    vals = rng.uniform(0, 1, (n, 3)).astype(np.float32)
+    P, V = to_dev(spread, cuda_device), to_dev(vals, cuda_device)
+    out = torch.empty((H, W, 3), device=cuda_device)
+    shift = torch.empty((H, W), device=cuda_device)
+    for pts in (spread, corner, spread, corner):
+        P.copy_(torch.as_tensor(pts, device=cuda_device))
+        g.interpolate(P, V, 0.8, H, W, graph=True, out=out)
+        torch.cuda.synchronize()
+        ref = oracle.forward(pts, vals, H, W, 0.8)
+        assert np.abs(out.cpu().numpy() - ref["image"]).max() <= TOL_FWD
+        # far field: nearest squared distance beyond 100 / kappa, kappa = log2(e) / (2 sigma^2)
+        far = ref["shift"] > 100.0 * 2 * 0.8 ** 2 / math.log2(math.e)
+        assert far.any() == (pts is corner)
