@@ -239,11 +239,24 @@ def pair_estimate(imgs, k=6.0, frac=16, seed=0):
     return total
 
 
-def timed_steps(fn, steps, flush, stream):
-    """Per-step CUDA-event times (ms) with an untimed L2 flush before each step."""
+def prequeue(steps, per_step_s=400e-6):
+    """A device spin long enough for the host to enqueue `steps` steps behind
+    it, so that no timed step waits for the host inside its events (the spin
+    runs before the first start event, outside the timed region)."""
+    import torch
+    torch.cuda._sleep(int(steps * per_step_s * SM_MAX_MHZ * 1e6))
+
+
+def timed_steps(fn, steps, flush, stream, queued=False):
+    """Per-step CUDA-event times (ms) with an untimed L2 flush before each
+    step; with `queued`, the steps are enqueued behind a device spin (device
+    time only; otherwise a slow host can leave the device idle inside a
+    step's events)."""
     import torch
     st = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     en = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    if queued:
+        prequeue(steps)
     for k in range(steps):
         flush.zero_()
         st[k].record(stream)
@@ -345,7 +358,7 @@ def bench_batched(dev, steps, warmup, flush, stream, autotune=True):
     for _ in range(max(3, warmup)):
         plan.forward(dimgs, use_graph=True)
     torch.cuda.synchronize()
-    tb = timed_steps(lambda: plan.forward(dimgs, use_graph=True), steps, flush, stream)
+    tb = timed_steps(lambda: plan.forward(dimgs, use_graph=True), steps, flush, stream, queued=True)
 
     def plain():
         for d in dimgs:
@@ -501,7 +514,7 @@ def bench_per_point_sigma(dev, steps, warmup, flush, stream, lo=0.5, hi=1.5, k=3
         for _ in range(max(3, warmup)):
             fn()
         torch.cuda.synchronize()
-        t = timed_steps(fn, steps, flush, stream)
+        t = timed_steps(fn, steps, flush, stream, queued=name.startswith("forward"))
         ms = sum(t) / len(t)
         res[name] = {"ms_per_step": ms, "value": im.H * im.W / (ms * 1e-3) / 1e6}
     res["unit"] = "Mpix/s"
@@ -809,7 +822,9 @@ def main():
         step_plain()
     torch.cuda.synchronize()
 
-    # ---- headline: device-resident inputs, per-step events, L2 flushed between steps
+    # ---- headline: device-resident inputs, per-step events, L2 flushed between
+    # steps; the steps are enqueued behind a device spin, so that no step waits
+    # for the host inside its events (the spin precedes the first start event)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     clocks = ClockSampler(local)
@@ -817,6 +832,7 @@ def main():
     torch.cuda.synchronize()
     clocks.start()
     time.sleep(0.3)
+    prequeue(args.steps)
     for k in range(args.steps):
         flush.zero_()
         starts[k].record(stream)
