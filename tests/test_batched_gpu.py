@@ -139,3 +139,34 @@ def test_batch_channels_modes_variants(cuda_device, C, mode, variant):
             err = err[ref["skipped"] < 1e-3]   # pixels not decided by a point on the radius
         assert err.max() <= TOL_FWD, (C, mode, variant, im.H, im.W, im.N)
     plan.close()
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_degenerate_images_with_far_field(cuda_device, use_graph):
+    """A batch of degenerate shapes beside far-field images (which make the
+    near kernel build the summed-area table of every image): 1x1 and 1xN /
+    Nx1 strips, an image without points, a point outside its frame, a
+    corner cluster in a wide frame; each result equals the oracle."""
+    import torch
+    G = gmi()
+    rng = np.random.default_rng(71)
+
+    def img(pts, H, W, sigma=0.7):
+        pts = np.asarray(pts, np.float32).reshape(-1, 2)
+        vals = rng.uniform(0, 1, (pts.shape[0], 3)).astype(np.float32)
+        return wl.Image(pts, vals, sigma, H, W)
+
+    imgs = [img([[0.3, 0.6]], 1, 1),
+            img(np.stack([rng.uniform(0, 97, 20), rng.uniform(0, 1, 20)], 1), 1, 97),
+            img(np.stack([rng.uniform(0, 1, 15), rng.uniform(0, 83, 15)], 1), 83, 1),
+            img(np.zeros((0, 2)), 17, 23),
+            img([[-3.5, 4.0], [40.0, 60.0]], 31, 29, sigma=1.3),
+            img(rng.uniform(0, 6, (50, 2)), 90, 140),
+            img(rng.uniform(0, 6, (50, 2)) + np.float32([200, 0]), 40, 210, sigma=1.8)]
+    plan = G.BatchPlan(16, 1000, 50000, 3)
+    outs = plan.forward(dev_images(imgs, cuda_device), use_graph=use_graph)
+    torch.cuda.synchronize()
+    for im, o in zip(imgs, outs):
+        ref = oracle.forward(im.points, im.values, im.H, im.W, im.sigma)["image"]
+        assert np.abs(o.cpu().numpy() - ref).max() <= TOL_FWD, (im.H, im.W, im.N)
+    plan.close()
