@@ -66,6 +66,9 @@ __global__ void __launch_bounds__(256) scan_partial_kernel(const unsigned* __res
   __shared__ unsigned red[8];
   if (totals) nb = totals[kTotBins];
   const long long base = (long long)blockIdx.x * kScanChunk;
+  // batched calls size the grid by the plan's capacity: blocks past the bins
+  // leave at once (no later block reads their partial)
+  if (base >= nb) return;
   unsigned s = 0;
   for (int k = threadIdx.x; k < kScanChunk; k += blockDim.x) {
     long long j = base + k;
@@ -89,6 +92,9 @@ __global__ void __launch_bounds__(256) scan_final_kernel(unsigned* __restrict__ 
                                                          const unsigned* __restrict__ partials, const long long* totals) {
   constexpr int kPer = kScanChunk / 256;
   if (totals) nb = totals[kTotBins];
+  // blocks past the bins (capacity-sized grids of batched calls) leave at
+  // once, before summing their predecessors' partials; block 0 stays for nb = 0
+  if ((long long)blockIdx.x * kScanChunk >= nb && blockIdx.x > 0) return;
   __shared__ unsigned warp_tot[8];
   __shared__ unsigned block_prefix;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
