@@ -43,7 +43,11 @@
 #include "bin_body.cuh"
 #include "sat.cuh"
 
+#include <algorithm>
+
 namespace gmi {
+
+int device_sm_count();
 
 constexpr int kRingMax = 16;   // most bin rings searched for the nearest-distance bound
 
@@ -285,12 +289,19 @@ __device__ void near_plan_body(const KArgs& a, int trunc, long long wt) {
 // offsets and flags, which the scan has already produced, so the two run side
 // by side.  The plan's warps are latency-bound chains of small loads, so they
 // get the low block indices and start first; the scatter streams around them.
-template <int MTH, int MTW>
-__global__ void __launch_bounds__(256) scatter_plan_kernel(KArgs a_in, int trunc, int n_scatter, int n_plan) {
+// STRIDE (batched calls, whose grids follow the plan's capacity, often far
+// above the batch's warp tiles): fewer plan blocks, their warps striding over
+// the warp tiles.
+template <int MTH, int MTW, bool STRIDE>
+__global__ void __launch_bounds__(256, 3) scatter_plan_kernel(KArgs a_in, int trunc, int n_scatter, int n_plan) {
   const KArgs a = resolve(a_in);
   if ((int)blockIdx.x < n_plan) {
-    const long long wt = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
-    near_plan_body<MTH, MTW>(a, trunc, wt);
+    const long long wt0 = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (STRIDE) {
+      for (long long wt = wt0; wt < a.wt_total; wt += (long long)n_plan * 8) near_plan_body<MTH, MTW>(a, trunc, wt);
+    } else {
+      near_plan_body<MTH, MTW>(a, trunc, wt0);
+    }
   } else {
     bin_scatter_body(a, n_scatter, (int)blockIdx.x - n_plan);
   }
@@ -659,12 +670,22 @@ static cudaError_t launch_near_mt(const KArgs& a, int mode, int grid, cudaStream
 
 // n_scatter scatter blocks (0: scatter not needed) followed by the plan's blocks.
 cudaError_t launch_scatter_plan(const KArgs& a, bool trunc, int n_scatter, cudaStream_t s) {
-  const int n_plan = (int)((a.wt_total + 7) / 8);
+  // one block per 8 warp tiles; batched (capacity-sized): at most 64 blocks
+  // per SM, the warps striding
+  const bool stride = a.totals != nullptr;
+  const long long need = (a.wt_total + 7) / 8;
+  const int n_plan = (int)(stride ? std::min<long long>(need, 64LL * device_sm_count()) : need);
   const unsigned blocks = (unsigned)(n_scatter + n_plan);
   const int t = trunc ? 1 : 0;
-  if (a.mth == 4 && a.mtw == 8) scatter_plan_kernel<4, 8><<<blocks, 256, 0, s>>>(a, t, n_scatter, n_plan);
-  else if (a.mth == 2 && a.mtw == 4) scatter_plan_kernel<2, 4><<<blocks, 256, 0, s>>>(a, t, n_scatter, n_plan);
-  else scatter_plan_kernel<4, 4><<<blocks, 256, 0, s>>>(a, t, n_scatter, n_plan);
+  if (stride) {
+    if (a.mth == 4 && a.mtw == 8) scatter_plan_kernel<4, 8, true><<<blocks, 256, 0, s>>>(a, t, n_scatter, n_plan);
+    else if (a.mth == 2 && a.mtw == 4) scatter_plan_kernel<2, 4, true><<<blocks, 256, 0, s>>>(a, t, n_scatter, n_plan);
+    else scatter_plan_kernel<4, 4, true><<<blocks, 256, 0, s>>>(a, t, n_scatter, n_plan);
+  } else {
+    if (a.mth == 4 && a.mtw == 8) scatter_plan_kernel<4, 8, false><<<blocks, 256, 0, s>>>(a, t, n_scatter, n_plan);
+    else if (a.mth == 2 && a.mtw == 4) scatter_plan_kernel<2, 4, false><<<blocks, 256, 0, s>>>(a, t, n_scatter, n_plan);
+    else scatter_plan_kernel<4, 4, false><<<blocks, 256, 0, s>>>(a, t, n_scatter, n_plan);
+  }
   return cudaGetLastError();
 }
 
