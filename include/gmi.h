@@ -458,6 +458,29 @@ typedef struct {
 gmi_status gmi_backward_batched(gmi_batch_plan* plan, const gmi_grad_desc* descs, int B,
                                 gmi_stream_t stream);
 
+/*
+ * Equal-shaped batches given as stacked arrays: image i of B has N points
+ * at points + i*N*2 and values + i*N*C, its output at image + i*H*W*C and
+ * den/shift + i*H*W, its sigma sigmas[i] (a HOST array of B floats); the
+ * gradients likewise (grad_sigma + i).  The same as gmi_forward_batched /
+ * gmi_backward_batched with the descriptors built from these strides, which
+ * saves a caller holding [B, ...] tensors from building B descriptors.
+ * den, shift may be NULL in the forward; in the backward they and image,
+ * grad_image must not be.  Errors: as the batched calls, and
+ * GMI_ERR_INVALID_ARG for B outside [1, the plan's max_images] or a NULL
+ * sigmas.
+ */
+gmi_status gmi_forward_stacked(gmi_batch_plan* plan, const float* points, const float* values,
+                               int B, int64_t N, int H, int W, const float* sigmas,
+                               float* image, float* den, float* shift, int use_graph,
+                               gmi_stream_t stream);
+
+gmi_status gmi_backward_stacked(gmi_batch_plan* plan, const float* points, const float* values,
+                                int B, int64_t N, int H, int W, const float* sigmas,
+                                const float* image, const float* den, const float* shift,
+                                const float* grad_image, float* grad_points, float* grad_values,
+                                float* grad_sigma, gmi_stream_t stream);
+
 /* ------------------------------------------------------------------------
  * Serving: a persistent request loop with continuous batching.  Requests are
  * admitted while their device memory fits the budget, their points are binned

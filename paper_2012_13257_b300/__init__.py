@@ -766,13 +766,14 @@ def _stacked_function():
     import numpy as np
     import torch
 
-    ptrs = _ptrs
+    fptr = ctypes.POINTER(ctypes.c_float)
 
     class GMIStackedFunction(torch.autograd.Function):
         """B equal-shaped images ([B,N,2] points, [B,N,C] values, [B] sigmas)
-        through one batched forward and one batched backward; descriptor
-        tables are built with vector operations, so the host work does not
-        grow with B."""
+        through one batched forward and one batched backward
+        (gmi_forward_stacked / gmi_backward_stacked: the per-image
+        descriptors are built in the library from the stacked tensors'
+        addresses, so the host work does not grow with B)."""
 
         @staticmethod
         def forward(ctx, plan, H, W, points, values, sigmas):
@@ -780,13 +781,13 @@ def _stacked_function():
             C = int(values.shape[2])
             dev = points.device
             points, values = points.contiguous(), values.contiguous()
-            sig = _sigma_list(sigmas, B)
-            out, den, shift = _flat_views([(B, H, W, C), (B, H, W), (B, H, W)], dev)
-            tab = _scratch_table(_lib.ImageDesc, B)
-            tab["points"], tab["values"], tab["image"] = ptrs(points, B), ptrs(values, B), ptrs(out, B)
-            tab["den"], tab["shift"] = ptrs(den, B), ptrs(shift, B)
-            tab["N"], tab["H"], tab["W"], tab["sigma"] = N, H, W, sig
-            plan.forward_table(tab, B, _stream_handle(dev))
+            sig = np.ascontiguousarray(_sigma_list(sigmas, B), dtype=np.float32)
+            out = torch.empty((B, H, W, C), dtype=torch.float32, device=dev)
+            den = torch.empty((B, H, W), dtype=torch.float32, device=dev)
+            shift = torch.empty((B, H, W), dtype=torch.float32, device=dev)
+            _lib.check(_lib.load().gmi_forward_stacked(
+                plan._h, points.data_ptr(), values.data_ptr(), B, N, H, W, sig.ctypes.data_as(fptr),
+                out.data_ptr(), den.data_ptr(), shift.data_ptr(), 1, _stream_handle(dev)), "gmi_forward_stacked")
             ctx.set_materialize_grads(False)
             # tensors (the output included) through save_for_backward: no
             # reference cycle between the output and its grad_fn
@@ -805,20 +806,15 @@ def _stacked_function():
             dev = points.device
             g = g.contiguous().float()
             need = ctx.needs_input_grad
-            gp, gv, gs = _flat_views([(B, N, 2), (B, N, C), (B,)], dev)
-            tab = _scratch_table(_lib.GradDesc, B)
-            tab["points"], tab["values"] = ptrs(points, B), ptrs(values, B)
-            tab["image"], tab["den"], tab["shift"], tab["grad_image"] = ptrs(out, B), ptrs(den, B), ptrs(shift, B), ptrs(g, B)
-            if need[3]:
-                tab["grad_points"] = ptrs(gp, B)
-            if need[4]:
-                tab["grad_values"] = ptrs(gv, B)
-            if need[5] and sig_t:
-                tab["grad_sigma"] = ptrs(gs, B)
-            tab["N"], tab["H"], tab["W"], tab["sigma"] = N, H, W, sig
-            ctx.plan.backward_table(tab, B, _stream_handle(dev))
-            return (None, None, None, gp if need[3] else None, gv if need[4] else None,
-                    gs if (need[5] and sig_t) else None)
+            gp = torch.empty((B, N, 2), dtype=torch.float32, device=dev) if need[3] else None
+            gv = torch.empty((B, N, C), dtype=torch.float32, device=dev) if need[4] else None
+            gs = torch.empty((B,), dtype=torch.float32, device=dev) if (need[5] and sig_t) else None
+            _lib.check(_lib.load().gmi_backward_stacked(
+                ctx.plan._h, points.data_ptr(), values.data_ptr(), B, N, H, W, sig.ctypes.data_as(fptr),
+                out.data_ptr(), den.data_ptr(), shift.data_ptr(), g.data_ptr(),
+                gp.data_ptr() if gp is not None else None, gv.data_ptr() if gv is not None else None,
+                gs.data_ptr() if gs is not None else None, _stream_handle(dev)), "gmi_backward_stacked")
+            return (None, None, None, gp, gv, gs)
 
     return GMIStackedFunction
 

@@ -98,6 +98,10 @@ SIGNATURES = {
     "gmi_batch_plan_bytes": (_sz, [_vp]),
     "gmi_forward_batched": (_int, [_vp, ctypes.POINTER(ImageDesc), _int, _int, _vp]),
     "gmi_backward_batched": (_int, [_vp, ctypes.POINTER(GradDesc), _int, _vp]),
+    "gmi_forward_stacked": (_int, [_vp, _vp, _vp, _int, _i64, _int, _int, ctypes.POINTER(_f), _vp, _vp, _vp, _int,
+                                   _vp]),
+    "gmi_backward_stacked": (_int, [_vp, _vp, _vp, _int, _i64, _int, _int, ctypes.POINTER(_f), _vp, _vp, _vp, _vp,
+                                    _vp, _vp, _vp, _vp]),
     "gmi_server_config_default": (_int, [ctypes.POINTER(ServerConfig)]),
     "gmi_server_create": (_int, [ctypes.POINTER(ServerConfig), ctypes.POINTER(_vp)]),
     "gmi_server_submit": (_int, [_vp, _vp, _vp, _i64, _int, _int, _f, _vp, _u64p]),

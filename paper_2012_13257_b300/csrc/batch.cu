@@ -11,6 +11,7 @@
 #include <string.h>
 
 #include <mutex>
+#include <vector>
 
 #include "api_internal.h"
 #include "bwd_args.h"
@@ -363,4 +364,60 @@ extern "C" gmi_status gmi_backward_batched(gmi_batch_plan* p, const gmi_grad_des
   p->bwd_used[hs] = true;
   p->bwd_next = hs ^ 1;
   return (p->params.flags & GMI_FLAG_SYNC_CHECK) ? read_status(p->base, s) : GMI_OK;
+}
+
+// Equal-shaped (stacked) batches: the descriptor tables built here from base
+// pointers and strides, so that a caller holding [B, ...] tensors passes
+// their addresses instead of building B descriptors itself.
+extern "C" gmi_status gmi_forward_stacked(gmi_batch_plan* p, const float* points, const float* values, int B,
+                                          int64_t N, int H, int W, const float* sigmas, float* image, float* den,
+                                          float* shift, int use_graph, gmi_stream_t stream) {
+  if (!p || !sigmas || B < 1 || B > p->max_images || N < 0 || H < 1 || W < 1 || !image)
+    return GMI_ERR_INVALID_ARG;
+  const long long px = (long long)H * W;
+  std::vector<gmi_image_desc> d((size_t)B);
+  for (int i = 0; i < B; ++i) {
+    gmi_image_desc& e = d[(size_t)i];
+    memset(&e, 0, sizeof(e));
+    e.points = points ? points + (size_t)i * N * 2 : nullptr;
+    e.values = values ? values + (size_t)i * N * p->C : nullptr;
+    e.image = image + (size_t)i * px * p->C;
+    e.den = den ? den + (size_t)i * px : nullptr;
+    e.shift = shift ? shift + (size_t)i * px : nullptr;
+    e.N = N;
+    e.H = H;
+    e.W = W;
+    e.sigma = sigmas[i];
+  }
+  return gmi_forward_batched(p, d.data(), B, use_graph, stream);
+}
+
+extern "C" gmi_status gmi_backward_stacked(gmi_batch_plan* p, const float* points, const float* values, int B,
+                                           int64_t N, int H, int W, const float* sigmas, const float* image,
+                                           const float* den, const float* shift, const float* grad_image,
+                                           float* grad_points, float* grad_values, float* grad_sigma,
+                                           gmi_stream_t stream) {
+  if (!p || !sigmas || B < 1 || B > p->max_images || N < 0 || H < 1 || W < 1 || !image || !den || !shift ||
+      !grad_image)
+    return GMI_ERR_INVALID_ARG;
+  const long long px = (long long)H * W;
+  std::vector<gmi_grad_desc> d((size_t)B);
+  for (int i = 0; i < B; ++i) {
+    gmi_grad_desc& e = d[(size_t)i];
+    memset(&e, 0, sizeof(e));
+    e.points = points ? points + (size_t)i * N * 2 : nullptr;
+    e.values = values ? values + (size_t)i * N * p->C : nullptr;
+    e.image = image + (size_t)i * px * p->C;
+    e.den = den + (size_t)i * px;
+    e.shift = shift + (size_t)i * px;
+    e.grad_image = grad_image + (size_t)i * px * p->C;
+    e.grad_points = grad_points ? grad_points + (size_t)i * N * 2 : nullptr;
+    e.grad_values = grad_values ? grad_values + (size_t)i * N * p->C : nullptr;
+    e.grad_sigma = grad_sigma ? grad_sigma + i : nullptr;
+    e.N = N;
+    e.H = H;
+    e.W = W;
+    e.sigma = sigmas[i];
+  }
+  return gmi_backward_batched(p, d.data(), B, stream);
 }
