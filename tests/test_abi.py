@@ -127,3 +127,12 @@ def test_per_point_calls_reject_bad_arguments_without_launching(kind):
                None) == 1
     # the workspace is checked too
     assert fwd(256, 256, 256, 10, 3, 8, 8, ctypes.byref(trunc), 256, None, 256, 16, None) == 3
+
+
+def test_stacked_calls_reject_bad_arguments_without_launching():
+    """No plan, B < 1 or a NULL sigma array: GMI_ERR_INVALID_ARG on the host."""
+    lib = _lib.load()
+    sig = (ctypes.c_float * 2)(1.0, 1.0)
+    assert lib.gmi_forward_stacked(None, 256, 256, 2, 10, 8, 8, sig, 256, None, None, 1, None) == 1
+    assert lib.gmi_backward_stacked(None, 256, 256, 2, 10, 8, 8, sig, 256, 256, 256, 256, None, None, None,
+                                    None) == 1
