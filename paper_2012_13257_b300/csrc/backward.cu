@@ -409,30 +409,56 @@ __global__ void __launch_bounds__(32 * kFarWarps) bwd_fallback_kernel(KArgs a_in
     for (unsigned skip = 0; skip < total; skip += kFarCap) {
       if (skip > 0) collect(a, g, t, R, R2, skip, L);
       const unsigned n = min(total - skip, (unsigned)kFarCap);
-      if (mine) {
-        for (unsigned k = part; k < n; k += nparts) {
-          const unsigned idx = L[k];
-          const float2 p = a.w.sxy[idx];
-          const float dx = qx - p.x, dy = qy - p.y;
-          const float ee = sh > 0.0f ? shifted_sqdist(qx, qy, p.x, p.y, sh) : fmaf(dx, dx, dy * dy);
-          if (!(ee <= emax)) continue;
-          const float w = ex2(-g.kappa * ee);
-          const float4 cv = a.w.sval[idx];
-          const float c4[4] = {cv.x, cv.y, cv.z, cv.w};
-          float tt = -sp;
+      // the lanes of one part take the same candidate at once: their pairs'
+      // contributions are summed over the part's pixel lanes (shuffles), and
+      // one lane per part adds them to the point's gradients
+      for (unsigned k0 = 0; k0 < n; k0 += nparts) {
+        const unsigned k = k0 + part;
+        float cg[4] = {0.f, 0.f, 0.f, 0.f}, gx = 0.0f, gy = 0.0f;
+        unsigned idx = 0;
+        bool hit = false;   // this lane's pixel keeps the pair
+        if (k < n) {
+          idx = L[k];
+          if (mine) {
+            const float2 p = a.w.sxy[idx];
+            const float dx = qx - p.x, dy = qy - p.y;
+            const float ee = sh > 0.0f ? shifted_sqdist(qx, qy, p.x, p.y, sh) : fmaf(dx, dx, dy * dy);
+            if (ee <= emax) {
+              hit = true;
+              const float w = ex2(-g.kappa * ee);
+              const float4 cv = a.w.sval[idx];
+              const float c4[4] = {cv.x, cv.y, cv.z, cv.w};
+              float tt = -sp;
 #pragma unroll
-          for (int c = 0; c < C; ++c) tt = fmaf(G[c], c4[c], tt);
-          const float wt = w * tt;
+              for (int c = 0; c < C; ++c) tt = fmaf(G[c], c4[c], tt);
+              const float wt = w * tt;
+#pragma unroll
+              for (int c = 0; c < C; ++c) cg[c] = w * G[c];
+              gx = wt * dx;
+              gy = wt * dy;
+              sig = fmaf(wt, ee - s0, sig);   // ee is already d^2 - shift when shift > 0
+            }
+          }
+        }
+        // any pair of this part kept?  (its PS lanes' bits of the ballot)
+        const unsigned hits = __ballot_sync(full, hit);
+        const unsigned pmask = PS == 32 ? full : ((1u << PS) - 1u) << (part * PS);
+        for (int o = PS >> 1; o > 0; o >>= 1) {
+#pragma unroll
+          for (int c = 0; c < C; ++c) cg[c] += __shfl_xor_sync(full, cg[c], o);
+          gx += __shfl_xor_sync(full, gx, o);
+          gy += __shfl_xor_sync(full, gy, o);
+        }
+        if (slot == 0 && (hits & pmask) != 0u) {
           const unsigned o = a.w.perm[idx];
           if (bi.gvals) {
 #pragma unroll
-            for (int c = 0; c < C; ++c) atomicAdd(&bi.gvals[(long long)o * C + c], w * G[c]);
+            for (int c = 0; c < C; ++c) atomicAdd(&bi.gvals[(long long)o * C + c], cg[c]);
           }
           if (bi.gpts) {
-            atomicAdd(&bi.gpts[2LL * o], wt * dx * bi.inv_s2);
-            atomicAdd(&bi.gpts[2LL * o + 1], wt * dy * bi.inv_s2);
+            atomicAdd(&bi.gpts[2LL * o], gx * bi.inv_s2);
+            atomicAdd(&bi.gpts[2LL * o + 1], gy * bi.inv_s2);
           }
-          sig = fmaf(wt, ee - s0, sig);   // ee is already d^2 - shift when shift > 0
         }
       }
       __syncwarp();
