@@ -9,8 +9,10 @@ is interpolated output Mpix/s (H*W per step, all ranks) through
 ``gmi.interpolate(..., graph=True)`` (the six kernels replayed as one CUDA
 graph), timed with CUDA events per step on the launching stream with L2
 flushed (256 MB write) between steps; ``plain_launch`` is the same without
-graph replay; ``e2e`` repeats the measurement through the public call with
-the host<->device copies of inputs and image inside the timed region.
+graph replay; ``e2e`` repeats the measurement through the host-buffer call
+(``gmi.interpolate_host``, the C ABI's gmi_forward_host: pinned inputs
+uploaded, the kernels, the image downloaded, replayed as one CUDA graph) with
+the host<->device copies inside the timed region.
 
 Further objects on the same line: the dominant kernel's roofline, the FP64
 oracle's CPU throughput, SM clocks sampled during the timed region and, as
@@ -867,26 +869,20 @@ def main():
     ms_per_step = t_total / args.steps
     value = replica_throughput(im.H * im.W, args.steps, world, t_total)
 
-    # ---- e2e: pinned host buffers, copies inside the timed region
+    # ---- e2e: pinned host buffers through the host-buffer C-ABI call
+    # (gmi_forward_host: uploads, kernels and download, one graph per step),
+    # copies inside the timed region
     hP = torch.as_tensor(im.points).pin_memory()
     hV = torch.as_tensor(im.values).pin_memory()
     hO = torch.empty((im.H, im.W, im.C), dtype=torch.float32).pin_memory()
-    dP = torch.empty_like(P)
-    dV = torch.empty_like(V)
     for _ in range(3):
-        dP.copy_(hP, non_blocking=True)
-        dV.copy_(hV, non_blocking=True)
-        gmi.interpolate(dP, dV, im.sigma, im.H, im.W, out=out, graph=True)
-        hO.copy_(out, non_blocking=True)
+        gmi.interpolate_host(hP, hV, im.sigma, im.H, im.W, out=hO, graph=True)
     torch.cuda.synchronize()
     D.barrier()
     for k in range(args.steps):
         flush.zero_()
         starts[k].record(stream)
-        dP.copy_(hP, non_blocking=True)
-        dV.copy_(hV, non_blocking=True)
-        gmi.interpolate(dP, dV, im.sigma, im.H, im.W, out=out, graph=True)
-        hO.copy_(out, non_blocking=True)
+        gmi.interpolate_host(hP, hV, im.sigma, im.H, im.W, out=hO, graph=True)
         ends[k].record(stream)
     torch.cuda.synchronize()
     e_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]

@@ -342,6 +342,30 @@ gmi_status gmi_forward_noalloc(const float* points, const float* values, int64_t
                                float* den_out, float* shift_out, gmi_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * The forward pass end to end from HOST memory (the problem statement's call,
+ * section 2 / Eq. 1, with the transfers included): uploads points [N,2] and
+ * values [N,C] from host buffers, runs gmi_forward's pipeline on device
+ * copies, and downloads the image [H,W,C] into a host buffer, all in order
+ * on `stream`.  Asynchronous: image_host holds the result once the stream
+ * has passed the call (synchronise before reading it).  Host buffers should
+ * be pinned (cudaHostAlloc / cudaHostRegister); pageable ones work, with
+ * copies the driver stages synchronously, and are never captured in a graph.
+ *
+ * workspace: device memory, 256-byte aligned, of at least
+ * gmi_forward_host_workspace_size() bytes; it holds the forward's workspace
+ * and the device copies of points, values and image.  Flags as gmi_forward;
+ * with GMI_FLAG_GRAPH and pinned buffers the two uploads, the kernels and the
+ * download replay as one cached CUDA graph for the same buffers and sizes.
+ * No den or shift planes (use gmi_forward for those).
+ * Errors: as gmi_forward.
+ * ---------------------------------------------------------------------- */
+gmi_status gmi_forward_host_workspace_size(int64_t N, int C, int H, int W, const gmi_params* p,
+                                           size_t* bytes);
+gmi_status gmi_forward_host(const float* points_host, const float* values_host, int64_t N, int C,
+                            int H, int W, const gmi_params* p, float* image_host, void* workspace,
+                            size_t ws_bytes, gmi_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * Measurement aid (no counterpart in the paper): while enabled, the compute
  * entry points bracket each stage of their pipeline with CUDA events recorded
  * on their own stream, so kernel times can be read without a profiler.

@@ -18,7 +18,7 @@ import ctypes
 from . import _lib
 from ._lib import GmiError, MODE_EXACT, MODE_TRUNCATED
 
-__all__ = ["release_workspaces", "interpolate", "interpolate_backward", "gmi_interpolate", "interpolate_pp",
+__all__ = ["release_workspaces", "interpolate", "interpolate_host", "interpolate_backward", "gmi_interpolate", "interpolate_pp",
            "interpolate_backward_pp", "gmi_interpolate_pp", "BatchPlan", "gmi_interpolate_batch", "gmi_interpolate_stacked", "Server", "workspace_size", "GmiError", "MODE_EXACT", "MODE_TRUNCATED", "version", "lib"]
 
 
@@ -157,6 +157,57 @@ def interpolate(points, values, sigma: float, H: int, W: int, *, radius_sigmas: 
     _lib.check(st, "gmi_forward")
     if return_aux:
         return out, den, shift
+    return out
+
+
+_host_ws_size_cache = {}
+
+
+def interpolate_host(points, values, sigma: float, H: int, W: int, *, radius_sigmas: float = 6.0,
+                     mode="exact", bin_px: int = 0, variant: int = 0, check: bool = False,
+                     graph: bool = False, out=None, device=None):
+    """Eq. 1 / Eq. 2 end to end from host memory (``gmi_forward_host``):
+    ``points [N, 2]`` and ``values [N, C]`` are CPU float32 tensors (pinned
+    for asynchronous copies), the image comes back in ``out`` (a CPU float32
+    tensor ``[H, W, C]``, allocated pinned when not given).  The uploads, the
+    kernels and the download run in order on the current CUDA stream of
+    ``device`` (default: the current device); synchronise that stream before
+    reading ``out``, or pass ``check=True``.  ``graph=True`` replays the copies
+    and the kernels as one cached CUDA graph for the same buffers."""
+    import torch
+    if not (isinstance(points, torch.Tensor) and isinstance(values, torch.Tensor)):
+        raise TypeError("points and values must be torch tensors")
+    if points.device.type != "cpu" or values.device.type != "cpu":
+        raise ValueError("points and values must be host (CPU) tensors")
+    if points.dtype != torch.float32 or values.dtype != torch.float32:
+        raise TypeError("points and values must be float32")
+    if points.dim() != 2 or points.shape[1] != 2 or values.dim() != 2 or values.shape[0] != points.shape[0]:
+        raise ValueError("points must have shape [N, 2] and values [N, C]")
+    points, values = points.contiguous(), values.contiguous()
+    N, C = int(points.shape[0]), int(values.shape[1])
+    H, W = int(H), int(W)
+    dev = torch.device("cuda", torch.cuda.current_device() if device is None else torch.device(device).index)
+    flags = (_lib.FLAG_SYNC_CHECK if check else 0) | (_lib.FLAG_GRAPH if graph else 0)
+    md = _mode(mode)
+    p = _params(sigma, radius_sigmas, md, flags, bin_px, variant)
+    key = (N, C, H, W, float(sigma), float(radius_sigmas), md, bin_px, variant)
+    nbytes = _host_ws_size_cache.get(key)
+    if nbytes is None:
+        c = ctypes.c_size_t(0)
+        _lib.check(_lib.load().gmi_forward_host_workspace_size(N, C, H, W, ctypes.byref(p), ctypes.byref(c)),
+                   "gmi_forward_host_workspace_size")
+        nbytes = _host_ws_size_cache[key] = int(c.value)
+    if out is None:
+        out = torch.empty((H, W, C), dtype=torch.float32).pin_memory()
+    elif out.device.type != "cpu" or out.dtype != torch.float32 or tuple(out.shape) != (H, W, C) \
+            or not out.is_contiguous():
+        raise ValueError("out must be a contiguous CPU float32 tensor of shape [H, W, C]")
+    with torch.cuda.device(dev):
+        stream = _stream_handle(dev)
+        ws = _workspace(dev, stream, nbytes)
+        st = _lib.load().gmi_forward_host(points.data_ptr(), values.data_ptr(), N, C, H, W, ctypes.byref(p),
+                                          out.data_ptr(), ws.data_ptr(), ws.numel(), stream)
+    _lib.check(st, "gmi_forward_host")
     return out
 
 

@@ -87,6 +87,9 @@ SIGNATURES = {
     "gmi_workspace_status": (_int, [_vp, _vp]),
     "gmi_forward_noalloc": (_int, [_vp, _vp, _i64, _int, _int, _int, ctypes.POINTER(Params), _vp, _vp, _vp,
                                    _vp]),
+    "gmi_forward_host_workspace_size": (_int, [_i64, _int, _int, _int, ctypes.POINTER(Params),
+                                               ctypes.POINTER(_sz)]),
+    "gmi_forward_host": (_int, [_vp, _vp, _i64, _int, _int, _int, ctypes.POINTER(Params), _vp, _vp, _sz, _vp]),
     "gmi_profile_enable": (_int, [_int]),
     "gmi_profile_read": (_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), _int]),
     "gmi_measure_unit_rates": (_int, [ctypes.POINTER(ctypes.c_double)]),

@@ -222,6 +222,13 @@ gmi_status run_forward_pipeline(KArgs& a, const WsLayout& L, void* ws, int mth, 
   return GMI_OK;
 }
 
+void warm_forward_caches(int C, const gmi_params* p) {
+  int mth, mtw;
+  variant_dims(p->variant, &mth, &mtw);
+  device_sm_count();
+  near_blocks_per_sm(mth, mtw, C, p->mode == GMI_MODE_TRUNCATED, 0);
+}
+
 gmi_status read_status(const void* ws, cudaStream_t s) {
   if (cudaStreamSynchronize(s) != cudaSuccess) return GMI_ERR_CUDA;
   unsigned st = 0;

@@ -37,6 +37,9 @@ gmi_status run_bin_and_plan(KArgs& a, const WsLayout& L, void* ws, int mth, int 
 gmi_status run_forward_pipeline(KArgs& a, const WsLayout& L, void* ws, int mth, int mtw, bool trunc,
                                 cudaStream_t s, int ppk = 0);
 gmi_status read_status(const void* ws, cudaStream_t s);
+// Fills the host-side caches a forward launch sequence reads (SM count,
+// near-kernel occupancy), so that none is first computed inside a capture.
+void warm_forward_caches(int C, const gmi_params* p);
 
 // Stage timing (profile.cu): no-ops unless gmi_profile_enable(1) was called.
 struct ProfileMark {
@@ -56,6 +59,7 @@ struct FwdGraphKey {
   long long N;
   const void *points, *values, *sigmas, *image, *den, *shift, *ws;
   int pp_kind;
+  int host;   // gmi_forward_host: points/values/image are host buffers, copies captured too
   size_t ws_bytes;
   gmi_params params;
 };
