@@ -145,7 +145,10 @@ def test_nonfinite_input_reported(cuda_device):
 
 def test_upsample_1024_sampled(cuda_device):
     """The 512^2 -> 1024^2 upsampling workload at full size, in the launch
-    configuration the benchmark times, checked on a pixel sample."""
+    configurations the benchmark times (plain launches, the cached graph
+    captured then replayed, and the host-buffer call with its graph),
+    checked on a pixel sample."""
+    import torch
     im = wl.upsample_1024()
     out, den, shift = run(im, cuda_device)
     pix = sample_pixels(im.points, im.H, im.W)
@@ -155,6 +158,16 @@ def test_upsample_1024_sampled(cuda_device):
     assert err <= TOL_FWD, err
     # every pixel is finite and inside the colour range (convexity)
     assert np.isfinite(out).all() and out.min() >= -1e-6 and out.max() <= 1 + 1e-6
+    P, V = to_dev(im.points, cuda_device), to_dev(im.values, cuda_device)
+    dout = torch.empty((im.H, im.W, 3), dtype=torch.float32, device=cuda_device)
+    hP, hV = torch.as_tensor(im.points).pin_memory(), torch.as_tensor(im.values).pin_memory()
+    hout = torch.empty((im.H, im.W, 3), dtype=torch.float32).pin_memory()
+    for _ in range(2):   # capture, then replay
+        gmi().interpolate(P, V, im.sigma, im.H, im.W, out=dout, graph=True)
+        gmi().interpolate_host(hP, hV, im.sigma, im.H, im.W, out=hout, graph=True)
+    torch.cuda.synchronize()
+    for img in (dout.cpu().numpy(), hout.numpy()):
+        assert np.abs(img.reshape(-1, 3)[pix] - ref["image"]).max() <= TOL_FWD
 
 
 def test_batched_images_sampled_single_launches(cuda_device):
