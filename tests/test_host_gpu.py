@@ -43,6 +43,21 @@ def test_host_call_matches_oracle_and_device_call(cuda_device, pin, graph):
     np.testing.assert_allclose(out.numpy(), dev.cpu().numpy(), rtol=0, atol=1e-6)
 
 
+@pytest.mark.parametrize("C,mode", [(1, "exact"), (2, "truncated"), (4, "exact"), (3, "truncated")])
+def test_host_call_channels_and_modes(cuda_device, C, mode):
+    im = wl.tiny_random(12, 3000, 131, 67, C=C, sigma=1.1, margin=1.0, clustered=True)
+    k = 3.0 if mode == "truncated" else 6.0
+    out = gmi().interpolate_host(host(im.points, True), host(im.values, True), im.sigma, im.H, im.W,
+                                 radius_sigmas=k, mode=mode, graph=True, check=True)
+    ref = oracle.forward(im.points, im.values, im.H, im.W, im.sigma,
+                         mode=oracle.TRUNCATED if mode == "truncated" else oracle.EXACT, k=k)
+    err = np.abs(out.numpy().astype(np.float64) - ref["image"])
+    # truncated mode: skip pixels decided by a point on the radius within rounding
+    decided = ref["skipped"] < 1e-3 if mode == "truncated" else np.ones((im.H, im.W), bool)
+    assert decided.mean() > 0.99
+    assert err[decided].max() <= TOL_FWD
+
+
 def test_host_call_graph_replay_sees_new_host_contents(cuda_device):
     import torch
     im = wl.tiny_random(2, 500, 37, 53, C=3, sigma=0.7, margin=3.0)
