@@ -45,79 +45,46 @@ __device__ __forceinline__ BwdImage bwd_image(const BwdArgs& b, int img) { retur
 // elsewhere); micro-tiles with a non-core pixel are queued for the fallback.
 template <int C>
 __global__ void __launch_bounds__(256) bwd_prep_kernel(KArgs a_in, BwdArgs b) {
-  constexpr int kPix = 4;   // pixels per thread per step, loaded before any is used
   const KArgs a = resolve(a_in);
   const long long stride = (long long)gridDim.x * blockDim.x;
-  const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  for (long long gb = t0; gb < a.px_total; gb += stride * kPix) {
-    float d[kPix], sh[kPix], gr[kPix][4], im[kPix][4];
-    int imgs[kPix];
-    long long pxs[kPix];
+  for (long long gp = (long long)blockIdx.x * blockDim.x + threadIdx.x; gp < a.px_total; gp += stride) {
+    const int img = find_image<3>(a, gp);
+    const ImageGeom& g = *geom_ptr(a, img);
+    const BwdImage bi = bwd_image(b, img);
+    const long long px = gp - g.px_base;
+    if (px == 0 && bi.gsig) *bi.gsig = 0.0f;   // accumulated by the later kernels
+    const float d = bi.den[px];
+    const float sh = bi.shift ? bi.shift[px] : 0.0f;
+    float G[4] = {0.f, 0.f, 0.f, 0.f};
+    float sp = 0.0f;
+    if (d > 0.0f) {
+      const float inv = 1.0f / d;
 #pragma unroll
-    for (int u = 0; u < kPix; ++u) {
-      const long long gp = gb + u * stride;
-      d[u] = 0.0f;
-      sh[u] = 0.0f;
-      imgs[u] = 0;
-      pxs[u] = 0;
-#pragma unroll
-      for (int c = 0; c < 4; ++c) gr[u][c] = im[u][c] = 0.0f;
-      if (gp < a.px_total) {
-        const int img = find_image<3>(a, gp);
-        const ImageGeom& g = *geom_ptr(a, img);
-        const BwdImage bi = bwd_image(b, img);
-        const long long px = gp - g.px_base;
-        imgs[u] = img;
-        pxs[u] = px;
-        d[u] = bi.den[px];
-        sh[u] = bi.shift ? bi.shift[px] : 0.0f;
-#pragma unroll
-        for (int c = 0; c < C; ++c) {
-          gr[u][c] = bi.grad[px * C + c];
-          im[u][c] = bi.image[px * C + c];
-        }
+      for (int c = 0; c < C; ++c) {
+        G[c] = bi.grad[px * C + c] * inv;
+        sp = fmaf(G[c], bi.image[px * C + c], sp);
       }
     }
-#pragma unroll
-    for (int u = 0; u < kPix; ++u) {
-      const long long gp = gb + u * stride;
-      if (gp >= a.px_total) continue;
-      const int img = imgs[u];
-      const ImageGeom& g = *geom_ptr(a, img);
-      const BwdImage bi = bwd_image(b, img);
-      const long long px = pxs[u];
-      if (px == 0 && bi.gsig) *bi.gsig = 0.0f;   // accumulated by the later kernels
-      float G[4] = {0.f, 0.f, 0.f, 0.f};
-      float sp = 0.0f;
-      if (d[u] > 0.0f) {
-        const float inv = 1.0f / d[u];
-#pragma unroll
-        for (int c = 0; c < C; ++c) {
-          G[c] = gr[u][c] * inv;
-          sp = fmaf(G[c], im[u][c], sp);
-        }
-      }
-      const bool core = d[u] > 0.0f && (b.trunc || (sh[u] == 0.0f && d[u] >= exp2f(-kCoreLog2)));
-      float4 v0, v1 = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (!core) {
-        v0 = make_float4(0.f, 0.f, 0.f, 0.f);
-      } else if (C == 4) {
-        v0 = make_float4(G[0], G[1], G[2], G[3]);
-        v1.x = sp;
-      } else {
-        v0 = make_float4(G[0], G[1], G[2], 0.0f);
-        if (C == 1) v0.y = 0.0f;
-        v0.w = sp;
-      }
-      a.w.pplane[gp] = v0;
-      if (C == 4) a.w.pplane[a.px_total + gp] = v1;
-      if (!core && d[u] > 0.0f) {
-        const int y = (int)(px / g.W), x = (int)(px % g.W);
-        const unsigned mt = (unsigned)((y / a.mth) * g.mtx + x / a.mtw);
-        if (atomicOr(&a.w.fbflag[g.mt_base + mt], 1u) == 0u) {
-          const unsigned q = atomicAdd(&a.w.status[kFbCount], 1u);
-          a.w.fbq[q] = make_uint2((unsigned)img, mt);
-        }
+    const bool core = d > 0.0f && (b.trunc || (sh == 0.0f && d >= exp2f(-kCoreLog2)));
+    float4 v0, v1 = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (!core) {
+      v0 = make_float4(0.f, 0.f, 0.f, 0.f);
+    } else if (C == 4) {
+      v0 = make_float4(G[0], G[1], G[2], G[3]);
+      v1.x = sp;
+    } else {
+      v0 = make_float4(G[0], G[1], G[2], 0.0f);
+      if (C == 1) v0.y = 0.0f;
+      v0.w = sp;
+    }
+    a.w.pplane[gp] = v0;
+    if (C == 4) a.w.pplane[a.px_total + gp] = v1;
+    if (!core && d > 0.0f) {
+      const int y = (int)(px / g.W), x = (int)(px % g.W);
+      const unsigned mt = (unsigned)((y / a.mth) * g.mtx + x / a.mtw);
+      if (atomicOr(&a.w.fbflag[g.mt_base + mt], 1u) == 0u) {
+        const unsigned q = atomicAdd(&a.w.status[kFbCount], 1u);
+        a.w.fbq[q] = make_uint2((unsigned)img, mt);
       }
     }
   }
@@ -542,8 +509,7 @@ void bind_bwd(DevWork& w, void* extra, long long N, int C, int H, int W, long lo
 template <int C>
 static cudaError_t launch_bwd_c(const KArgs& a, const BwdArgs& b, cudaStream_t s) {
   const int sms = device_sm_count();
-  // four pixels per thread per step (bwd_prep_kernel's kPix)
-  const unsigned prep_blocks = (unsigned)std::max<long long>(1, std::min<long long>((a.px_total + 1023) / 1024, sms * 8LL));
+  const unsigned prep_blocks = (unsigned)std::max<long long>(1, std::min<long long>((a.px_total + 255) / 256, sms * 32LL));
   bwd_prep_kernel<C><<<prep_blocks, 256, 0, s>>>(a, b);
   const float rcore_log2 = kRelLog2 + kCoreLog2;   // kappa * R_core^2
   const unsigned blocks = (unsigned)std::max<long long>(1, std::min<long long>((a.n_total + 255) / 256, kSigParts));
