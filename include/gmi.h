@@ -280,6 +280,29 @@ gmi_status gmi_backward_cov(const float* points, const float* values, const floa
                             void* workspace, size_t ws_bytes, gmi_stream_t stream);
 
 /*
+ * Where gmi_forward leaves the binned points in its workspace (byte offsets
+ * from the workspace start), for inspection and tests of the binning step
+ * (section 2's "close enough" points, found through bins of b x b pixels):
+ *   off  [nbx*nby + 1] uint32: exclusive prefix sums of the bin counts
+ *        (off[nb] = N); bin = by * nbx + bx, bx = clamp(floor(x / b), 0,
+ *        nbx - 1), by likewise from y;
+ *   oob  [nbx*nby] uint8: 1 where the bin holds a point outside [0,W)x[0,H);
+ *   sxy  [N] float2, sval [N] float4 (colours padded with 0), perm [N]
+ *        uint32: the points sorted by bin (sxy[k] = points[perm[k]]); the
+ *        order inside a bin is unspecified.
+ * Valid after a gmi_forward call with N > 0 on that workspace has finished.
+ * Errors: GMI_ERR_INVALID_ARG (as gmi_workspace_size).
+ */
+typedef struct {
+    size_t off, oob, sxy, sval, perm;  /* byte offsets into the workspace */
+    int bin_px, nbx, nby;               /* bin edge in pixels, bins across and down */
+    size_t total;                       /* gmi_workspace_size */
+} gmi_ws_layout;
+
+gmi_status gmi_workspace_layout(int64_t N, int C, int H, int W, const gmi_params* p,
+                                gmi_ws_layout* out);
+
+/*
  * Reads the device status word of a workspace after its stream has finished
  * (synchronises `stream` first).  Returns GMI_OK, GMI_ERR_NONFINITE or
  * GMI_ERR_INTERNAL for the last call that used the workspace.

@@ -40,6 +40,12 @@ class Params(ctypes.Structure):
                 ("reserved", ctypes.c_int * 2)]
 
 
+class WsLayout(ctypes.Structure):
+    _fields_ = [("off", ctypes.c_size_t), ("oob", ctypes.c_size_t), ("sxy", ctypes.c_size_t),
+                ("sval", ctypes.c_size_t), ("perm", ctypes.c_size_t), ("bin_px", ctypes.c_int),
+                ("nbx", ctypes.c_int), ("nby", ctypes.c_int), ("total", ctypes.c_size_t)]
+
+
 class ImageDesc(ctypes.Structure):
     _fields_ = [("points", ctypes.c_void_p), ("values", ctypes.c_void_p), ("image", ctypes.c_void_p),
                 ("den", ctypes.c_void_p), ("shift", ctypes.c_void_p), ("N", ctypes.c_int64),
@@ -85,6 +91,7 @@ SIGNATURES = {
     "gmi_backward_cov": (_int, [_vp, _vp, _vp, _i64, _int, _int, _int, ctypes.POINTER(Params), _vp, _vp,
                                 _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "gmi_workspace_status": (_int, [_vp, _vp]),
+    "gmi_workspace_layout": (_int, [_i64, _int, _int, _int, ctypes.POINTER(Params), ctypes.POINTER(WsLayout)]),
     "gmi_forward_noalloc": (_int, [_vp, _vp, _i64, _int, _int, _int, ctypes.POINTER(Params), _vp, _vp, _vp,
                                    _vp]),
     "gmi_forward_host_workspace_size": (_int, [_i64, _int, _int, _int, ctypes.POINTER(Params),

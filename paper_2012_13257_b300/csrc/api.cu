@@ -421,6 +421,32 @@ gmi_status gmi_workspace_size(int64_t N, int C, int H, int W, const gmi_params* 
   return GMI_OK;
 }
 
+gmi_status gmi_workspace_layout(int64_t N, int C, int H, int W, const gmi_params* p, gmi_ws_layout* out) {
+  if (!out) return GMI_ERR_INVALID_ARG;
+  gmi_status st = check_params(p);
+  if (st != GMI_OK) return st;
+  if ((st = check_shape(N, C, H, W)) != GMI_OK) return st;
+  int mth, mtw;
+  variant_dims(p->variant, &mth, &mtw);
+  ImageGeom g;
+  memset(&g, 0, sizeof(g));
+  fill_geom(g, N, H, W, p->sigma, p->radius_sigmas, p->bin_px, mth, mtw);
+  const long long nb = (long long)g.nbx * g.nby;
+  const long long mt = (long long)g.mtx * g.mty;
+  const long long wt = (long long)g.wtx * g.wty;
+  const WsLayout L = ws_layout(N, nb, mt, wt, sat_entries(g), slot_bytes_for(mth, mtw, C), bwd_extra_bytes(N, C, H, W));
+  out->off = L.off;
+  out->oob = L.oob;
+  out->sxy = L.sxy;
+  out->sval = L.sval;
+  out->perm = L.perm;
+  out->bin_px = g.b;
+  out->nbx = g.nbx;
+  out->nby = g.nby;
+  out->total = L.total;
+  return GMI_OK;
+}
+
 gmi_status gmi_forward(const float* points, const float* values, int64_t N, int C, int H, int W,
                        const gmi_params* p, float* image, float* den_out, float* shift_out,
                        void* workspace, size_t ws_bytes, gmi_stream_t stream) {

@@ -1,0 +1,86 @@
+"""The binning step (bin keys, counts, exclusive scan, scatter) checked bit
+for bit: after gmi_forward, the bin offsets, out-of-frame flags and sorted
+point arrays in the workspace (located by gmi_workspace_layout) against a
+numpy counting sort of the same float32 bin keys.  The order of points
+inside a bin is not unique (atomic ranks), so the sorted arrays are checked
+as a permutation of the input that is consistent with the offsets."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+def bin_keys(points, H, W, b, nbx, nby):
+    """Bin of every point as the kernels form it: clamp(floor(x * (1/b)), 0, nb - 1)
+    in float32 (1/b is exact for the power-of-two edges), row-major."""
+    inv = np.float32(1.0) / np.float32(b)
+    x, y = points[:, 0].astype(np.float32), points[:, 1].astype(np.float32)
+    fx = np.floor(x * inv)
+    fy = np.floor(y * inv)
+    fx = np.nan_to_num(np.clip(fx, 0, nbx - 1))
+    fy = np.nan_to_num(np.clip(fy, 0, nby - 1))
+    return fy.astype(np.int64) * nbx + fx.astype(np.int64)
+
+
+def run_and_read(im, dev, bin_px=0):
+    import torch
+    from paper_2012_13257_b300 import _lib
+    L = _lib.load()
+    p = _lib.make_params(im.sigma, bin_px=bin_px)
+    lay = _lib.WsLayout()
+    assert L.gmi_workspace_layout(im.N, im.C, im.H, im.W, ctypes.byref(p), ctypes.byref(lay)) == 0
+    ws = torch.zeros(lay.total, dtype=torch.uint8, device=dev)
+    P = torch.as_tensor(np.ascontiguousarray(im.points), device=dev)
+    V = torch.as_tensor(np.ascontiguousarray(im.values), device=dev)
+    out = torch.empty((im.H, im.W, im.C), dtype=torch.float32, device=dev)
+    p.flags = _lib.FLAG_SYNC_CHECK
+    assert L.gmi_forward(P.data_ptr(), V.data_ptr(), im.N, im.C, im.H, im.W, ctypes.byref(p), out.data_ptr(),
+                         None, None, ws.data_ptr(), ws.numel(), None) == 0
+    torch.cuda.synchronize()
+    raw = ws.cpu().numpy()
+    nb = lay.nbx * lay.nby
+
+    def view(offset, dtype, count):
+        return raw[offset:offset + count * np.dtype(dtype).itemsize].view(dtype)
+
+    return (lay, view(lay.off, np.uint32, nb + 1), view(lay.oob, np.uint8, nb),
+            view(lay.sxy, np.float32, 2 * im.N).reshape(im.N, 2), view(lay.sval, np.float32, 4 * im.N).reshape(im.N, 4),
+            view(lay.perm, np.uint32, im.N))
+
+
+CASES = [  # (name, image)
+    ("ragged_out_of_frame", lambda: wl.tiny_random(2, 500, 37, 53, C=3, sigma=0.7, margin=3.0)),
+    ("clustered_c4", lambda: wl.tiny_random(12, 3000, 131, 67, C=4, sigma=1.1, margin=1.0, clustered=True)),
+    ("one_row", lambda: wl.tiny_random(7, 50, 1, 100, C=3, sigma=1.0)),
+    ("upsample_1024", wl.upsample_1024),
+]
+
+
+@pytest.mark.parametrize("name,make", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("bin_px", [0, 4])
+def test_binning_is_an_exact_counting_sort(cuda_device, name, make, bin_px):
+    im = make()
+    lay, off, oob, sxy, sval, perm = run_and_read(im, cuda_device, bin_px)
+    nb = lay.nbx * lay.nby
+    pts = np.ascontiguousarray(im.points, np.float32)
+    vals = np.ascontiguousarray(im.values, np.float32)
+    keys = bin_keys(pts, im.H, im.W, lay.bin_px, lay.nbx, lay.nby)
+    # counts and the exclusive scan, bit for bit
+    want_off = np.concatenate([[0], np.cumsum(np.bincount(keys, minlength=nb))]).astype(np.uint32)
+    np.testing.assert_array_equal(off, want_off)
+    # out-of-frame flags per bin
+    outside = ~((pts[:, 0] >= 0) & (pts[:, 0] < im.W) & (pts[:, 1] >= 0) & (pts[:, 1] < im.H))
+    want_oob = np.zeros(nb, np.uint8)
+    want_oob[keys[outside]] = 1
+    np.testing.assert_array_equal(oob, want_oob)
+    # the scatter: a permutation of the input, every point inside its bin's range
+    assert np.array_equal(np.sort(perm.astype(np.int64)), np.arange(im.N))
+    np.testing.assert_array_equal(sxy, pts[perm])
+    np.testing.assert_array_equal(sval[:, :im.C], vals[perm])
+    assert not sval[:, im.C:].any()   # padding channels are zero
+    bin_of_slot = np.repeat(np.arange(nb), np.diff(want_off.astype(np.int64)))
+    np.testing.assert_array_equal(keys[perm], bin_of_slot)
