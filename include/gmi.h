@@ -289,7 +289,12 @@ gmi_status gmi_backward_cov(const float* points, const float* values, const floa
  *   oob  [nbx*nby] uint8: 1 where the bin holds a point outside [0,W)x[0,H);
  *   sxy  [N] float2, sval [N] float4 (colours padded with 0), perm [N]
  *        uint32: the points sorted by bin (sxy[k] = points[perm[k]]); the
- *        order inside a bin is unspecified.
+ *        order inside a bin is unspecified;
+ *   ubound [wtx*wty*32] float, exact mode: per micro-tile of mth x mtw pixels
+ *        an upper bound U on the squared distance from each of its pixels to
+ *        the nearest point (+inf: the micro-tile went to the far-field
+ *        kernel); entry (wt * 32 + l) is micro-tile (l % 8, l / 8) of warp
+ *        tile wt = wty_index * wtx + wtx_index (8 x 4 micro-tiles each).
  * Valid after a gmi_forward call with N > 0 on that workspace has finished.
  * Errors: GMI_ERR_INVALID_ARG (as gmi_workspace_size).
  */
@@ -297,6 +302,8 @@ typedef struct {
     size_t off, oob, sxy, sval, perm;  /* byte offsets into the workspace */
     int bin_px, nbx, nby;               /* bin edge in pixels, bins across and down */
     size_t total;                       /* gmi_workspace_size */
+    size_t ubound;                      /* byte offset of the micro-tile bounds */
+    int mth, mtw, wtx, wty;             /* micro-tile rows x columns; warp tiles across, down */
 } gmi_ws_layout;
 
 gmi_status gmi_workspace_layout(int64_t N, int C, int H, int W, const gmi_params* p,

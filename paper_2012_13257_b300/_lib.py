@@ -43,7 +43,9 @@ class Params(ctypes.Structure):
 class WsLayout(ctypes.Structure):
     _fields_ = [("off", ctypes.c_size_t), ("oob", ctypes.c_size_t), ("sxy", ctypes.c_size_t),
                 ("sval", ctypes.c_size_t), ("perm", ctypes.c_size_t), ("bin_px", ctypes.c_int),
-                ("nbx", ctypes.c_int), ("nby", ctypes.c_int), ("total", ctypes.c_size_t)]
+                ("nbx", ctypes.c_int), ("nby", ctypes.c_int), ("total", ctypes.c_size_t),
+                ("ubound", ctypes.c_size_t), ("mth", ctypes.c_int), ("mtw", ctypes.c_int),
+                ("wtx", ctypes.c_int), ("wty", ctypes.c_int)]
 
 
 class ImageDesc(ctypes.Structure):

@@ -444,6 +444,11 @@ gmi_status gmi_workspace_layout(int64_t N, int C, int H, int W, const gmi_params
   out->nbx = g.nbx;
   out->nby = g.nby;
   out->total = L.total;
+  out->ubound = L.ubound;
+  out->mth = mth;
+  out->mtw = mtw;
+  out->wtx = g.wtx;
+  out->wty = g.wty;
   return GMI_OK;
 }
 

@@ -3,11 +3,14 @@ for bit: after gmi_forward, the bin offsets, out-of-frame flags and sorted
 point arrays in the workspace (located by gmi_workspace_layout) against a
 numpy counting sort of the same float32 bin keys.  The order of points
 inside a bin is not unique (atomic ranks), so the sorted arrays are checked
-as a permutation of the input that is consistent with the offsets."""
+as a permutation of the input that is consistent with the offsets.  The
+plan's nearest-distance bounds are checked by their defining property
+against a k-d tree."""
 import ctypes
 
 import numpy as np
 import pytest
+from scipy.spatial import cKDTree
 
 import workloads as wl
 
@@ -47,6 +50,7 @@ def run_and_read(im, dev, bin_px=0):
     def view(offset, dtype, count):
         return raw[offset:offset + count * np.dtype(dtype).itemsize].view(dtype)
 
+    run_and_read.ubound = view(lay.ubound, np.float32, lay.wtx * lay.wty * 32)
     return (lay, view(lay.off, np.uint32, nb + 1), view(lay.oob, np.uint8, nb),
             view(lay.sxy, np.float32, 2 * im.N).reshape(im.N, 2), view(lay.sval, np.float32, 4 * im.N).reshape(im.N, 4),
             view(lay.perm, np.uint32, im.N))
@@ -84,3 +88,43 @@ def test_binning_is_an_exact_counting_sort(cuda_device, name, make, bin_px):
     assert not sval[:, im.C:].any()   # padding channels are zero
     bin_of_slot = np.repeat(np.arange(nb), np.diff(want_off.astype(np.int64)))
     np.testing.assert_array_equal(keys[perm], bin_of_slot)
+
+
+BOUND_CASES = [  # (name, image, every point inside the frame)
+    ("ragged_out_of_frame", lambda: wl.tiny_random(2, 500, 37, 53, C=3, sigma=0.7, margin=3.0), False),
+    ("clustered_far_field", lambda: wl.tiny_random(11, 800, 64, 96, C=3, sigma=2.0, clustered=True), True),
+    ("sparse_small_sigma", lambda: wl.tiny_random(10, 800, 64, 96, C=3, sigma=0.5, clustered=True), True),
+    ("upsample_1024", wl.upsample_1024, True),
+]
+
+
+@pytest.mark.parametrize("name,make,inside", BOUND_CASES, ids=[c[0] for c in BOUND_CASES])
+def test_plan_bounds_cover_the_nearest_distance(cuda_device, name, make, inside):
+    """Every near micro-tile's U is at least the squared distance from each of
+    its pixels to the nearest point (float64 k-d tree) and at most the
+    near-field limit 100 / kappa; +inf marks the far-field micro-tiles.  With
+    every point inside the frame (every non-empty bin usable), the ring
+    search stops within about sqrt(m)/b + 2 rings, so U <= 2 (t + sqrt(m) +
+    3 b)^2 (t the micro-tile's side, m its largest nearest squared distance),
+    and only micro-tiles where that exceeds the limit may go to the far field."""
+    im = make()
+    lay = run_and_read(im, cuda_device)[0]
+    U = run_and_read.ubound.astype(np.float64).reshape(lay.wty, lay.wtx, 4, 8)   # [wty, wtx, ly, lx]
+    U = U.transpose(0, 2, 1, 3).reshape(lay.wty * 4, lay.wtx * 8)                 # micro-tile rows x columns
+    yy, xx = np.meshgrid(np.arange(im.H) + 0.5, np.arange(im.W) + 0.5, indexing="ij")
+    d, _ = cKDTree(np.asarray(im.points, np.float64)).query(np.stack([xx.ravel(), yy.ravel()], 1), workers=-1)
+    m = (d * d).reshape(im.H, im.W)
+    mty, mtx = -(-im.H // lay.mth), -(-im.W // lay.mtw)
+    pad = np.full((mty * lay.mth, mtx * lay.mtw), -np.inf)
+    pad[:im.H, :im.W] = m
+    mmax = pad.reshape(mty, lay.mth, mtx, lay.mtw).max(axis=(1, 3))   # largest m_q per micro-tile
+    Ut = U[:mty, :mtx]
+    limit = 100.0 / (np.log2(np.e) / (2.0 * im.sigma ** 2))
+    near = np.isfinite(Ut)
+    assert near.any()
+    assert (Ut[near] >= mmax[near] * (1 - 1e-6) - 1e-5).all()
+    assert (Ut[near] <= limit * (1 + 1e-6)).all()
+    if inside:
+        loose = 2.0 * (max(lay.mth, lay.mtw) + np.sqrt(mmax) + 3.0 * lay.bin_px) ** 2
+        assert (Ut[near] <= loose[near]).all()
+        assert (loose[~near] > limit).all()
