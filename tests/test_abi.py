@@ -136,3 +136,32 @@ def test_stacked_calls_reject_bad_arguments_without_launching():
     assert lib.gmi_forward_stacked(None, 256, 256, 2, 10, 8, 8, sig, 256, None, None, 1, None) == 1
     assert lib.gmi_backward_stacked(None, 256, 256, 2, 10, 8, 8, sig, 256, 256, 256, 256, None, None, None,
                                     None) == 1
+
+
+def test_workspace_layout_is_consistent_without_a_gpu():
+    """gmi_workspace_layout is host arithmetic: its total equals
+    gmi_workspace_size, its regions are 256-byte aligned, in order and large
+    enough for their arrays, and bad arguments are rejected."""
+    from paper_2012_13257_b300 import _lib
+    L = _lib.load()
+    for N, C, H, W, sigma, bin_px in ((262144, 3, 1024, 1024, 1.0, 0), (500, 4, 37, 53, 0.7, 4), (1, 1, 1, 1, 2.0, 0)):
+        p = _lib.make_params(sigma, bin_px=bin_px)
+        lay = _lib.WsLayout()
+        assert L.gmi_workspace_layout(N, C, H, W, ctypes.byref(p), ctypes.byref(lay)) == 0
+        size = ctypes.c_size_t(0)
+        assert L.gmi_workspace_size(N, C, H, W, ctypes.byref(p), ctypes.byref(size)) == 0
+        assert lay.total == size.value
+        nb = lay.nbx * lay.nby
+        assert lay.nbx == -(-W // lay.bin_px) and lay.nby == -(-H // lay.bin_px)
+        assert lay.wtx == -(-W // (8 * lay.mtw)) and lay.wty == -(-H // (4 * lay.mth))
+        regions = [(lay.off, 4 * (nb + 1)), (lay.oob, nb), (lay.sxy, 8 * N), (lay.sval, 16 * N), (lay.perm, 4 * N),
+                   (lay.ubound, 4 * 32 * lay.wtx * lay.wty)]
+        for start, nbytes in regions:
+            assert start % 256 == 0 and start + nbytes <= lay.total
+        assert lay.off < lay.oob and lay.sxy < lay.sval < lay.perm
+    p = _lib.make_params(1.0)
+    lay = _lib.WsLayout()
+    assert L.gmi_workspace_layout(10, 0, 8, 8, ctypes.byref(p), ctypes.byref(lay)) != 0   # C = 0
+    assert L.gmi_workspace_layout(10, 3, 8, 8, ctypes.byref(p), None) == 1                  # no output
+    bad = _lib.make_params(-1.0)
+    assert L.gmi_workspace_layout(10, 3, 8, 8, ctypes.byref(bad), ctypes.byref(lay)) == 1   # sigma <= 0
