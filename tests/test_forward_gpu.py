@@ -273,3 +273,22 @@ def test_graph_replay_switches_the_far_field_on_and_off(cuda_device):
         # far field: nearest squared distance beyond 100 / kappa, kappa = log2(e) / (2 sigma^2)
         far = ref["shift"] > 100.0 * 2 * 0.8 ** 2 / math.log2(math.e)
         assert far.any() == (pts is corner)
+
+
+def test_graph_cache_evicts_and_recaptures(cuda_device):
+    """More distinct (buffer, size) keys than the graph cache holds (32): the
+    least recently used graphs are dropped, a dropped key is captured again
+    on its next call, and every call matches the plain launches."""
+    import torch
+    g = gmi()
+    im = wl.tiny_random(5, 600, 40, 56, sigma=0.9)
+    P, V = to_dev(im.points, cuda_device), to_dev(im.values, cuda_device)
+    plain = g.interpolate(P, V, im.sigma, im.H, im.W)
+    outs = [torch.empty_like(plain) for _ in range(40)]
+    for rnd in range(2):   # the second round finds the first keys evicted
+        for o in outs:
+            o.zero_()
+            g.interpolate(P, V, im.sigma, im.H, im.W, graph=True, out=o)
+        torch.cuda.synchronize()
+        for o in outs:
+            assert torch.allclose(o, plain, rtol=0, atol=2e-6)
