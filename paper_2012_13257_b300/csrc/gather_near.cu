@@ -432,13 +432,15 @@ __global__ void __launch_bounds__(128, NearOcc<MTH, MTW, C>::value) near_kernel(
       }
       if (!TRUNC) {
         // separable weight gy[r] * gx[j]: the column factors times the
-        // point's values once, then one FFMA2 per pair and pixel
+        // point's values once, then one FFMA2 per pair and pixel (the first
+        // pair (gx, gx c_0) is one scalar product: its other half is gx * 1)
         float2 hx[MTW][NP];
         float hs[MTW];
 #pragma unroll
         for (int j = 0; j < MTW; ++j) {
 #pragma unroll
-          for (int q = 0; q < NP; ++q) hx[j][q] = __fmul2_rn(make_float2(gx[j], gx[j]), cp[q]);
+          for (int q = 0; q < NP; ++q)
+            hx[j][q] = q == 0 ? make_float2(gx[j], gx[j] * cp[0].y) : __fmul2_rn(make_float2(gx[j], gx[j]), cp[q]);
           if (ODD) hs[j] = gx[j] * clast;
         }
 #pragma unroll
