@@ -294,7 +294,10 @@ gmi_status gmi_backward_cov(const float* points, const float* values, const floa
  *        an upper bound U on the squared distance from each of its pixels to
  *        the nearest point (+inf: the micro-tile went to the far-field
  *        kernel); entry (wt * 32 + l) is micro-tile (l % 8, l / 8) of warp
- *        tile wt = wty_index * wtx + wtx_index (8 x 4 micro-tiles each).
+ *        tile wt = wty_index * wtx + wtx_index (8 x 4 micro-tiles each);
+ *   sat  [(nby+1)*(nbx+1)] uint32, exact mode, built only when the plan sent
+ *        micro-tiles to the far-field kernel: entry (by, bx) = points in
+ *        bins [0, by) x [0, bx) (row stride nbx + 1).
  * Valid after a gmi_forward call with N > 0 on that workspace has finished.
  * Errors: GMI_ERR_INVALID_ARG (as gmi_workspace_size).
  */
@@ -304,6 +307,7 @@ typedef struct {
     size_t total;                       /* gmi_workspace_size */
     size_t ubound;                      /* byte offset of the micro-tile bounds */
     int mth, mtw, wtx, wty;             /* micro-tile rows x columns; warp tiles across, down */
+    size_t sat;                         /* byte offset of the summed-area table */
 } gmi_ws_layout;
 
 gmi_status gmi_workspace_layout(int64_t N, int C, int H, int W, const gmi_params* p,

@@ -45,7 +45,7 @@ class WsLayout(ctypes.Structure):
                 ("sval", ctypes.c_size_t), ("perm", ctypes.c_size_t), ("bin_px", ctypes.c_int),
                 ("nbx", ctypes.c_int), ("nby", ctypes.c_int), ("total", ctypes.c_size_t),
                 ("ubound", ctypes.c_size_t), ("mth", ctypes.c_int), ("mtw", ctypes.c_int),
-                ("wtx", ctypes.c_int), ("wty", ctypes.c_int)]
+                ("wtx", ctypes.c_int), ("wty", ctypes.c_int), ("sat", ctypes.c_size_t)]
 
 
 class ImageDesc(ctypes.Structure):

@@ -449,6 +449,7 @@ gmi_status gmi_workspace_layout(int64_t N, int C, int H, int W, const gmi_params
   out->mtw = mtw;
   out->wtx = g.wtx;
   out->wty = g.wty;
+  out->sat = L.sat;
   return GMI_OK;
 }
 

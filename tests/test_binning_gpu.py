@@ -51,6 +51,7 @@ def run_and_read(im, dev, bin_px=0):
         return raw[offset:offset + count * np.dtype(dtype).itemsize].view(dtype)
 
     run_and_read.ubound = view(lay.ubound, np.float32, lay.wtx * lay.wty * 32)
+    run_and_read.sat = view(lay.sat, np.uint32, (lay.nbx + 1) * (lay.nby + 1))
     return (lay, view(lay.off, np.uint32, nb + 1), view(lay.oob, np.uint8, nb),
             view(lay.sxy, np.float32, 2 * im.N).reshape(im.N, 2), view(lay.sval, np.float32, 4 * im.N).reshape(im.N, 4),
             view(lay.perm, np.uint32, im.N))
@@ -128,3 +129,20 @@ def test_plan_bounds_cover_the_nearest_distance(cuda_device, name, make, inside)
         loose = 2.0 * (max(lay.mth, lay.mtw) + np.sqrt(mmax) + 3.0 * lay.bin_px) ** 2
         assert (Ut[near] <= loose[near]).all()
         assert (loose[~near] > limit).all()
+
+
+def test_summed_area_table_is_exact(cuda_device):
+    """With far-field micro-tiles queued (points squeezed into a corner), the
+    summed-area table the near kernel's idle warps build equals numpy's 2D
+    cumulative sum of the bin counts, entry for entry."""
+    rng = np.random.default_rng(71)
+    n, H, W = 3000, 150, 190
+    pts = rng.uniform(0, 12, (n, 2)).astype(np.float32)
+    im = wl.Image(pts, rng.uniform(0, 1, (n, 3)).astype(np.float32), 0.6, H, W)
+    lay, off = run_and_read(im, cuda_device)[:2]
+    U = run_and_read.ubound
+    assert np.isinf(U).any()   # the far field is in use, so the table was built
+    counts = np.diff(off.astype(np.int64)).reshape(lay.nby, lay.nbx)
+    want = np.zeros((lay.nby + 1, lay.nbx + 1), np.int64)
+    want[1:, 1:] = counts.cumsum(0).cumsum(1)
+    np.testing.assert_array_equal(run_and_read.sat.reshape(lay.nby + 1, lay.nbx + 1).astype(np.int64), want)
