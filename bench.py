@@ -249,6 +249,13 @@ def prequeue(steps, per_step_s=400e-6):
     torch.cuda._sleep(int(steps * per_step_s * SM_MAX_MHZ * 1e6))
 
 
+def step_stats(ms):
+    """Spread of the per-step times behind ms_per_step (their mean): median,
+    min and max in ms (this rank's)."""
+    s = sorted(ms)
+    return {"median": s[len(s) // 2], "min": s[0], "max": s[-1]} if s else None
+
+
 def timed_steps(fn, steps, flush, stream, queued=False):
     """Per-step CUDA-event times (ms) with an untimed L2 flush before each
     step; with `queued`, the steps are enqueued behind a device spin (device
@@ -258,7 +265,9 @@ def timed_steps(fn, steps, flush, stream, queued=False):
     st = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     en = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     if queued:
-        prequeue(steps)
+        prequeue(steps + 1)
+        flush.zero_()
+        fn()   # one more warm-up step in the queue, so no timed step starts the queued run
     for k in range(steps):
         flush.zero_()
         st[k].record(stream)
@@ -834,7 +843,9 @@ def main():
     torch.cuda.synchronize()
     clocks.start()
     time.sleep(0.3)
-    prequeue(args.steps)
+    prequeue(args.steps + 1)
+    flush.zero_()
+    step()   # one more warm-up step in the queue, so no timed step starts the queued run
     for k in range(args.steps):
         flush.zero_()
         starts[k].record(stream)
@@ -926,7 +937,8 @@ def main():
                        "sigma": im.sigma, "parallelism": "replicas" if world > 1 else "single",
                        "l2": "flushed between steps (256 MB write), not timed"},
             "roofline": roof, "e2e": e2e, "gpu_launches": LAUNCHES_PER_FORWARD * args.steps, "clocks": clk,
-            "stage_ms": stages, "plain_launch": plain, "e2e_pipelined": e2e_pipe}
+            "stage_ms": stages, "plain_launch": plain, "e2e_pipelined": e2e_pipe,
+            "step_ms": step_stats(ms_steps)}
     if rank == 0 and not args.no_extras:
         for name, fn in (("batched", lambda: bench_batched(dev, args.steps, args.warmup, flush, stream)),
                          ("fwd_bwd", lambda: bench_fwd_bwd(dev, args.steps, args.warmup, flush, stream)),
