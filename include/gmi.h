@@ -92,6 +92,15 @@ typedef enum { GMI_MODE_EXACT = 0, GMI_MODE_TRUNCATED = 1 } gmi_mode;
 #define GMI_VARIANT_MT4x4 1        /* each thread owns a 4x4 pixel micro-tile */
 #define GMI_VARIANT_MT4x8 2        /* 4 rows x 8 columns */
 #define GMI_VARIANT_MT2x4 3        /* 2 rows x 4 columns */
+#define GMI_VARIANT_MT4x2 4        /* 4 rows x 2 columns */
+
+/* How the near-field gather reads its candidate points (params->gather).
+ * Both compute the same sums; they differ only in speed. */
+#define GMI_GATHER_AUTO 0          /* staged for one shared sigma, direct for per-point sigmas */
+#define GMI_GATHER_STAGED 1        /* each warp stages its candidate window in shared memory
+                                      (bulk copies) and its threads walk it there */
+#define GMI_GATHER_DIRECT 2        /* each thread loads its candidates from global memory
+                                      through the L1 cache */
 
 typedef struct {
     float sigma;          /* std of every point's Gaussian, output px; finite, > 0 */
@@ -100,7 +109,9 @@ typedef struct {
     unsigned flags;       /* GMI_FLAG_* */
     int bin_px;           /* edge of the square point bins in px; 0 = auto (1..64) */
     int variant;          /* GMI_VARIANT_*; 0 = auto */
-    int reserved[2];      /* set to 0 */
+    int gather;           /* GMI_GATHER_*; 0 = auto.  Per-point sigmas always use the
+                             direct gather */
+    int reserved;         /* set to 0 */
 } gmi_params;
 
 /* Library version string, e.g. "gmi 0.1.0 sm_103a". */

@@ -18,7 +18,7 @@ import ctypes
 from . import _lib
 from ._lib import GmiError, MODE_EXACT, MODE_TRUNCATED
 
-__all__ = ["release_workspaces", "interpolate", "interpolate_host", "interpolate_backward", "gmi_interpolate", "interpolate_pp",
+__all__ = ["set_gather", "release_workspaces", "interpolate", "interpolate_host", "interpolate_backward", "gmi_interpolate", "interpolate_pp",
            "interpolate_backward_pp", "gmi_interpolate_pp", "BatchPlan", "gmi_interpolate_batch", "gmi_interpolate_stacked", "Server", "workspace_size", "GmiError", "MODE_EXACT", "MODE_TRUNCATED", "version", "lib"]
 
 
@@ -55,8 +55,20 @@ def _stream_handle(dev):
 _ws_buffers = {}
 
 
+def set_gather(kind: str) -> None:
+    """Chooses how the near-field gather reads its candidates, for every later
+    call of this process: "auto" (the default: staged for one shared sigma),
+    "staged" (each warp stages its window in shared memory) or "direct"
+    (each thread loads its candidates through the L1 cache).  Both give the
+    same sums; the choice exists to compare their speed."""
+    kinds = {"auto": _lib.GATHER_AUTO, "staged": _lib.GATHER_STAGED, "direct": _lib.GATHER_DIRECT}
+    if kind not in kinds:
+        raise ValueError("gather must be one of %s" % sorted(kinds))
+    _lib.DEFAULT_GATHER = kinds[kind]
+
+
 def _params(sigma, radius_sigmas, mode, flags, bin_px, variant):
-    key = (float(sigma), float(radius_sigmas), mode, flags, bin_px, variant)
+    key = (float(sigma), float(radius_sigmas), mode, flags, bin_px, variant, _lib.DEFAULT_GATHER)
     p = _param_cache.get(key)
     if p is None:
         if len(_param_cache) > 4096:

@@ -22,7 +22,10 @@ MODE_EXACT = 0
 MODE_TRUNCATED = 1
 FLAG_SYNC_CHECK = 0x1
 FLAG_GRAPH = 0x2
-VARIANT_AUTO, VARIANT_MT4x4, VARIANT_MT4x8, VARIANT_MT2x4 = 0, 1, 2, 3
+VARIANT_AUTO, VARIANT_MT4x4, VARIANT_MT4x8, VARIANT_MT2x4, VARIANT_MT4x2 = 0, 1, 2, 3, 4
+GATHER_AUTO, GATHER_STAGED, GATHER_DIRECT = 0, 1, 2
+# params.gather of every call this process makes (set through gmi.set_gather)
+DEFAULT_GATHER = GATHER_AUTO
 STAGES = ("bin", "near", "far", "backward")
 NOALLOC_SCRATCH_BYTES = 32 << 20   # GMI_NOALLOC_SCRATCH_BYTES
 
@@ -37,7 +40,7 @@ class GmiError(RuntimeError):
 class Params(ctypes.Structure):
     _fields_ = [("sigma", ctypes.c_float), ("radius_sigmas", ctypes.c_float), ("mode", ctypes.c_int),
                 ("flags", ctypes.c_uint), ("bin_px", ctypes.c_int), ("variant", ctypes.c_int),
-                ("reserved", ctypes.c_int * 2)]
+                ("gather", ctypes.c_int), ("reserved", ctypes.c_int)]
 
 
 class WsLayout(ctypes.Structure):
@@ -157,4 +160,5 @@ def make_params(sigma: float, radius_sigmas: float = 6.0, mode: int = MODE_EXACT
     p.flags = int(flags)
     p.bin_px = int(bin_px)
     p.variant = int(variant)
+    p.gather = int(DEFAULT_GATHER)
     return p

@@ -16,6 +16,8 @@
 namespace gmi {
 
 cudaError_t launch_near(const KArgs& a, int mth, int mtw, bool trunc, int ppk, int grid, cudaStream_t s);
+cudaError_t launch_near_staged(const KArgs& a, int mth, int mtw, bool trunc, int grid, cudaStream_t s);
+int staged_blocks_per_sm(int mth, int mtw, int C, bool trunc);
 cudaError_t launch_scatter_plan(const KArgs& a, bool trunc, int n_scatter, cudaStream_t s);
 int near_blocks_per_sm(int mth, int mtw, int C, bool trunc, int ppk);
 cudaError_t launch_far(const KArgs& a, int mth, int mtw, int sms, cudaStream_t s);
@@ -45,6 +47,7 @@ void variant_dims(int variant, int* mth, int* mtw) {
   switch (variant) {
     case GMI_VARIANT_MT4x8: *mth = 4; *mtw = 8; break;
     case GMI_VARIANT_MT2x4: *mth = 2; *mtw = 4; break;
+    case GMI_VARIANT_MT4x2: *mth = 4; *mtw = 2; break;
     default: *mth = 4; *mtw = 4; break;
   }
 }
@@ -66,7 +69,8 @@ gmi_status check_params(const gmi_params* p) {
   if (!(isfinite(p->radius_sigmas) && p->radius_sigmas > 0.0f)) return GMI_ERR_INVALID_ARG;
   if (p->mode != GMI_MODE_EXACT && p->mode != GMI_MODE_TRUNCATED) return GMI_ERR_INVALID_ARG;
   if (p->bin_px < 0 || p->bin_px > 1024) return GMI_ERR_INVALID_ARG;
-  if (p->variant < 0 || p->variant > GMI_VARIANT_MT2x4) return GMI_ERR_INVALID_ARG;
+  if (p->variant < 0 || p->variant > GMI_VARIANT_MT4x2) return GMI_ERR_INVALID_ARG;
+  if (p->gather < GMI_GATHER_AUTO || p->gather > GMI_GATHER_DIRECT) return GMI_ERR_INVALID_ARG;
   if (p->flags & ~(GMI_FLAG_SYNC_CHECK | GMI_FLAG_GRAPH)) return GMI_ERR_INVALID_ARG;
   return GMI_OK;
 }
@@ -120,13 +124,15 @@ WsLayout ws_layout(long long n_total, long long nb_total, long long mt_total, lo
   L.cap_items = (unsigned)std::min<long long>(wt_total * kSplitMax, 0x7fffffffLL);
   L.cap_slots = (unsigned)std::min<long long>(wt_total > 0 ? wt_total : 1, 0x7fffffffLL);
   L.status = o; o = align_up(o + sizeof(unsigned) * kStatusWords, 256);
-  L.off = o;    o = align_up(o + sizeof(unsigned) * (size_t)(nb_total + 1), 256);
+  L.off = o;    o = align_up(o + sizeof(unsigned) * (size_t)(nb_total + 1) + 16, 256);   // (+ slack, as below)
   L.oob = o;    o = align_up(o + (size_t)nb_total, 256);
   L.tile_done = o; o = align_up(o + sizeof(unsigned) * (size_t)(wt_total > 0 ? wt_total : 1), 256);
   L.zero_end = o;                               // [0, zero_end) is cleared per call
   L.rank = o;   o = align_up(o + sizeof(unsigned) * (size_t)n_total, 256);
-  L.sxy = o;    o = align_up(o + sizeof(float2) * (size_t)n_total, 256);
-  L.sval = o;   o = align_up(o + sizeof(float4) * (size_t)n_total, 256);
+  // (16 bytes of slack after each sorted array: the staged gather's bulk
+  // copies widen their ranges to even indices, one record past the end at most)
+  L.sxy = o;    o = align_up(o + sizeof(float2) * (size_t)n_total + 16, 256);
+  L.sval = o;   o = align_up(o + sizeof(float4) * (size_t)n_total + 16, 256);
   L.perm = o;   o = align_up(o + sizeof(unsigned) * (size_t)n_total, 256);
   L.spp = o;    o = align_up(o + sizeof(float4) * (size_t)n_total, 256);
   L.partials = o; o = align_up(o + sizeof(unsigned) * (size_t)((nb_total + kScanChunk - 1) / kScanChunk + 1), 256);
@@ -208,11 +214,13 @@ gmi_status run_forward_pipeline(KArgs& a, const WsLayout& L, void* ws, int mth, 
   gmi_status st = run_bin_and_plan(a, L, ws, mth, mtw, trunc, s, true);
   if (st != GMI_OK) return st;
   const int sms = device_sm_count();
-  const int per_sm = near_blocks_per_sm(mth, mtw, a.C, trunc, ppk);
+  const bool staged = uses_staged_gather(a.gather, ppk);
+  const int per_sm = staged ? staged_blocks_per_sm(mth, mtw, a.C, trunc) : near_blocks_per_sm(mth, mtw, a.C, trunc, ppk);
   // persistent: at most one resident wave, and no more warps than work items can use
   const int gn = (int)std::max<long long>(1, std::min<long long>(a.wt_total * 4, (long long)sms * per_sm));
   const ProfileMark pn = profile_begin(GMI_STAGE_NEAR, s);
-  if (launch_near(a, mth, mtw, trunc, ppk, gn, s) != cudaSuccess) return GMI_ERR_CUDA;
+  const cudaError_t en = staged ? launch_near_staged(a, mth, mtw, trunc, gn, s) : launch_near(a, mth, mtw, trunc, ppk, gn, s);
+  if (en != cudaSuccess) return GMI_ERR_CUDA;
   profile_end(pn, s);
   if (!trunc) {
     const ProfileMark pf = profile_begin(GMI_STAGE_FAR, s);
@@ -222,11 +230,18 @@ gmi_status run_forward_pipeline(KArgs& a, const WsLayout& L, void* ws, int mth, 
   return GMI_OK;
 }
 
+bool uses_staged_gather(int gather, int ppk) { return ppk == 0 && gather != GMI_GATHER_DIRECT; }
+
+void warm_near_caches(int mth, int mtw, int C, bool trunc, int ppk, int gather) {
+  device_sm_count();
+  if (uses_staged_gather(gather, ppk)) staged_blocks_per_sm(mth, mtw, C, trunc);
+  else near_blocks_per_sm(mth, mtw, C, trunc, ppk);
+}
+
 void warm_forward_caches(int C, const gmi_params* p) {
   int mth, mtw;
   variant_dims(p->variant, &mth, &mtw);
-  device_sm_count();
-  near_blocks_per_sm(mth, mtw, C, p->mode == GMI_MODE_TRUNCATED, 0);
+  warm_near_caches(mth, mtw, C, p->mode == GMI_MODE_TRUNCATED, 0, p->gather);
 }
 
 gmi_status read_status(const void* ws, cudaStream_t s) {
@@ -301,6 +316,7 @@ static gmi_status forward_impl(const float* points, const float* values, const f
   a.ch_total = (N + kChunk - 1) / kChunk;
   a.mt_total = mt;
   a.satj_total = sat_jobs(g);
+  a.gather = p->gather;
   const bool trunc = p->mode == GMI_MODE_TRUNCATED;
   const int ppk = g.pp_kind == 3 ? 2 : (g.pp_kind ? 1 : 0);
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -324,8 +340,7 @@ static gmi_status forward_impl(const float* points, const float* values, const f
     key.ws_bytes = ws_bytes;
     key.params = *p;
     // fill the host-side caches the launch sequence reads before any capture starts
-    device_sm_count();
-    near_blocks_per_sm(mth, mtw, C, trunc, ppk);
+    warm_near_caches(mth, mtw, C, trunc, ppk, p->gather);
     struct Ctx {
       const KArgs* a;
       const WsLayout* L;

@@ -40,6 +40,11 @@ gmi_status read_status(const void* ws, cudaStream_t s);
 // Fills the host-side caches a forward launch sequence reads (SM count,
 // near-kernel occupancy), so that none is first computed inside a capture.
 void warm_forward_caches(int C, const gmi_params* p);
+// Whether a forward uses the staged near-field gather, given params->gather and the
+// per-point kind (per-point sigmas use the direct gather).
+bool uses_staged_gather(int gather, int ppk);
+// Fills the SM-count and occupancy caches of the near kernel a call will launch.
+void warm_near_caches(int mth, int mtw, int C, bool trunc, int ppk, int gather);
 
 // Stage timing (profile.cu): no-ops unless gmi_profile_enable(1) was called.
 struct ProfileMark {

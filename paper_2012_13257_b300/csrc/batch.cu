@@ -237,6 +237,7 @@ extern "C" gmi_status gmi_forward_batched(gmi_batch_plan* p, const gmi_image_des
 
   KArgs a;
   memset(&a, 0, sizeof(a));
+  a.gather = p->params.gather;
   a.w = bind_ws(p->base, p->L);
   a.w.table = (const ImageGeom*)(sl.dev + kTotCount * sizeof(long long));
   a.totals = (const long long*)sl.dev;
@@ -257,6 +258,7 @@ extern "C" gmi_status gmi_forward_batched(gmi_batch_plan* p, const gmi_image_des
       // default stream, which cannot be captured); replayed on the caller's
       cudaGraph_t graph = nullptr;
       cudaStream_t cs = p->cap_stream;
+      warm_near_caches(p->mth, p->mtw, p->C, trunc, 0, p->params.gather);   // host caches, outside the capture
       if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return GMI_ERR_CUDA;
       cudaError_t e = cudaMemcpyAsync(sl.dev, sl.host, copy_bytes, cudaMemcpyHostToDevice, cs);
       gmi_status st = e == cudaSuccess ? run_forward_pipeline(a, p->L, p->base, p->mth, p->mtw, trunc, cs) : GMI_ERR_CUDA;
@@ -336,6 +338,7 @@ extern "C" gmi_status gmi_backward_batched(gmi_batch_plan* p, const gmi_grad_des
 
   KArgs a;
   memset(&a, 0, sizeof(a));
+  a.gather = p->params.gather;
   a.w = bind_ws(p->base, p->L);
   a.w.table = (const ImageGeom*)(p->bwd_dev + kTotCount * sizeof(long long));
   a.w.pplane = p->pplane;

@@ -117,6 +117,7 @@ struct KArgs {
   unsigned cap_items;    // capacity of w.items
   unsigned cap_slots;    // capacity of w.slots, in slots
   int mth, mtw;          // micro-tile of the near kernel
+  int gather;            // GMI_GATHER_* of the call (host-side choice of the near kernel)
   const long long* totals;  // batched: device copy of the totals below (else null)
 };
 

@@ -41,6 +41,7 @@
 // so every pixel takes its own exponential of
 // la_i - (kxx dx^2 + kyy dy^2 + kxy dx dy), from per-column and per-row parts.
 #include "bin_body.cuh"
+#include "near_common.cuh"
 #include "sat.cuh"
 
 #include <algorithm>
@@ -170,43 +171,6 @@ __device__ float near_bound(const KArgs& a, const ImageGeom& g, int x0, int y0, 
     if (u < INFINITY) return u;
   }
   return INFINITY;
-}
-
-// Candidate window of one thread: pixel-centre rectangle and radius.
-struct LaneWin {
-  float xq0, xq1, yq0, yq1;  // first / last pixel centres of the micro-tile
-  float R2;                  // squared radius
-  int by_lo, by_hi;          // bin rows that can hold a point within the radius
-};
-
-__device__ __forceinline__ LaneWin lane_window(const ImageGeom& g, int x0, int y0, int nx, int ny, float R2) {
-  LaneWin w;
-  w.xq0 = (float)x0 + 0.5f;
-  w.yq0 = (float)y0 + 0.5f;
-  w.xq1 = w.xq0 + (float)(nx - 1);
-  w.yq1 = w.yq0 + (float)(ny - 1);
-  w.R2 = R2;
-  const float R = sqrtf(R2);
-  w.by_lo = bin_coord(w.yq0 - R, g.inv_b, g.nby);
-  w.by_hi = bin_coord(w.yq1 + R, g.inv_b, g.nby);
-  return w;
-}
-
-// Sorted-array segment of bin row `by` that can hold a point within the
-// radius of the thread's pixels: the row's y-distance to the pixel rows
-// narrows its x-extent (border rows can hold clamped out-of-frame points, so
-// they are kept whole).
-__device__ __forceinline__ void row_segment(const KArgs& a, const ImageGeom& g, const LaneWin& w, int by,
-                                            unsigned& s, unsigned& e) {
-  const float bf = (float)g.b;
-  float dyr = 0.0f;
-  if (by > 0 && by < g.nby - 1) dyr = fmaxf(fmaxf((float)by * bf - w.yq1, w.yq0 - (float)(by + 1) * bf), 0.0f);
-  const float hx = sqrtf(fmaxf(w.R2 - dyr * dyr, 0.0f));
-  const int bx_lo = bin_coord(w.xq0 - hx, g.inv_b, g.nbx);
-  const int bx_hi = bin_coord(w.xq1 + hx, g.inv_b, g.nbx);
-  const long long rowb = g.bin_base + (long long)by * g.nbx;
-  s = __ldg(&a.w.off[rowb + bx_lo]);
-  e = __ldg(&a.w.off[rowb + bx_hi + 1]);
 }
 
 // Plan: one warp per warp tile.  Each thread bounds the nearest squared
@@ -476,58 +440,9 @@ __global__ void __launch_bounds__(128, NearOcc<MTH, MTW, C>::value) near_kernel(
 
     if (active) {
       const LaneWin w = lane_window(g, x0, y0, nx, ny, R2);
-      // this work item's share [lo, hi) of the thread's candidate sequence
-      unsigned lo = 0, hi = 0xffffffffu;
-      if (S > 1) {
-        unsigned n = 0;
-        for (int yb = w.by_lo; yb <= w.by_hi; ++yb) {
-          unsigned s0, e0;
-          row_segment(a, g, w, yb, s0, e0);
-          n += e0 - s0;
-        }
-        lo = (unsigned)(((unsigned long long)n * split) / S);
-        hi = (unsigned)(((unsigned long long)n * (split + 1)) / S);
-      }
-      const float2* __restrict__ sxy = a.w.sxy;
-      const float4* __restrict__ sval = a.w.sval;
-      const float4* __restrict__ spp = a.w.spp;
-      int by = w.by_lo - 1;
-      unsigned i = 0, end = 0, cum = 0;
-      // bounds of the next bin row, loaded one row ahead
-      unsigned ns = 0, ne = 0;
-      row_segment(a, g, w, w.by_lo, ns, ne);
-      // moves [i, end) to the next bin row holding part of [lo, hi); false at the end
-      auto next_row = [&]() -> bool {
-        for (;;) {
-          if (++by > w.by_hi || cum >= hi) return false;
-          const unsigned s0 = ns, e0 = ne;
-          if (by < w.by_hi) row_segment(a, g, w, by + 1, ns, ne);
-          const unsigned len = e0 - s0, rs = cum;
-          cum += len;
-          i = s0 + (lo > rs ? min(lo - rs, len) : 0u);
-          end = s0 + (hi > rs ? min(hi - rs, len) : 0u);
-          if (i < end) return true;
-        }
-      };
-      if (next_row()) {
-        // the candidate is always loaded one iteration ahead, across bin rows too
-        float2 pn = __ldg(&sxy[i]);
-        float4 cn = __ldg(&sval[i]);
-        float4 sn = PP ? __ldg(&spp[i]) : make_float4(0.f, 0.f, 0.f, 0.f);
-        bool more = true;
-        while (more) {
-          const float2 p = pn;
-          const float4 cv = cn;
-          const float4 spc = sn;
-          if (++i >= end) more = next_row();
-          if (more) {
-            pn = __ldg(&sxy[i]);
-            cn = __ldg(&sval[i]);
-            if (PP) sn = __ldg(&spp[i]);
-          }
-          consume(p, cv, spc);
-        }
-      }
+      unsigned lo, hi;
+      item_share(a, g, w, split, S, lo, hi);
+      direct_walk<PP>(a, g, w, lo, hi, consume);
     }
 
     unsigned nt = 0;
@@ -595,7 +510,7 @@ __global__ void __launch_bounds__(128, NearOcc<MTH, MTW, C>::value) near_kernel(
           for (int ch = 0; ch < C; ++ch) outv[j * C + ch] = q[1 + ch] * inv;
         }
         const long long row = (long long)(y0 + r) * g.W + x0;
-        if (g.vec_ok && nx == MTW) {
+        if (MTW % 4 == 0 && g.vec_ok && nx == MTW) {   // rows of whole float4s
           float4* o = reinterpret_cast<float4*>(g.image + row * C);
 #pragma unroll
           for (int k = 0; k < MTW * C / 4; ++k) o[k] = make_float4(outv[4 * k], outv[4 * k + 1], outv[4 * k + 2], outv[4 * k + 3]);
@@ -682,10 +597,12 @@ cudaError_t launch_scatter_plan(const KArgs& a, bool trunc, int n_scatter, cudaS
   if (stride) {
     if (a.mth == 4 && a.mtw == 8) scatter_plan_kernel<4, 8, true><<<blocks, 256, 0, s>>>(a, t, n_scatter, n_plan);
     else if (a.mth == 2 && a.mtw == 4) scatter_plan_kernel<2, 4, true><<<blocks, 256, 0, s>>>(a, t, n_scatter, n_plan);
+    else if (a.mth == 4 && a.mtw == 2) scatter_plan_kernel<4, 2, true><<<blocks, 256, 0, s>>>(a, t, n_scatter, n_plan);
     else scatter_plan_kernel<4, 4, true><<<blocks, 256, 0, s>>>(a, t, n_scatter, n_plan);
   } else {
     if (a.mth == 4 && a.mtw == 8) scatter_plan_kernel<4, 8, false><<<blocks, 256, 0, s>>>(a, t, n_scatter, n_plan);
     else if (a.mth == 2 && a.mtw == 4) scatter_plan_kernel<2, 4, false><<<blocks, 256, 0, s>>>(a, t, n_scatter, n_plan);
+    else if (a.mth == 4 && a.mtw == 2) scatter_plan_kernel<4, 2, false><<<blocks, 256, 0, s>>>(a, t, n_scatter, n_plan);
     else scatter_plan_kernel<4, 4, false><<<blocks, 256, 0, s>>>(a, t, n_scatter, n_plan);
   }
   return cudaGetLastError();
@@ -699,6 +616,7 @@ cudaError_t launch_near(const KArgs& a, int mth, int mtw, bool trunc, int ppk, i
   if (mth == 4 && mtw == 4) return launch_near_mt<4, 4>(a, m, grid, s);
   if (mth == 4 && mtw == 8) return launch_near_mt<4, 8>(a, m, grid, s);
   if (mth == 2 && mtw == 4) return launch_near_mt<2, 4>(a, m, grid, s);
+  if (mth == 4 && mtw == 2) return launch_near_mt<4, 2>(a, m, grid, s);
   return cudaErrorInvalidValue;
 }
 
@@ -728,6 +646,7 @@ int near_blocks_per_sm(int mth, int mtw, int C, bool trunc, int ppk) {
   const int m = near_mode(trunc, ppk);
   if (mth == 4 && mtw == 8) return occ_mt<4, 8>(c, m);
   if (mth == 2 && mtw == 4) return occ_mt<2, 4>(c, m);
+  if (mth == 4 && mtw == 2) return occ_mt<4, 2>(c, m);
   return occ_mt<4, 4>(c, m);
 }
 

@@ -1,0 +1,612 @@
+// Near-field gather with staged candidates: the forward pass's hot loop
+// (Eq. 1 and Eq. 2 of section 2) for one shared sigma, exact or truncated.
+//
+// The arithmetic is that of the direct-load gather (gather_near.cu): each
+// thread owns an MTH x MTW micro-tile of pixels, the isotropic weight
+// factorises as 2^(-kappa dx^2) 2^(-kappa dy^2), and one candidate costs
+// MTW + MTH exponentials on the SFU and C + 1 fused multiply-adds per pixel,
+// accumulated in FP32 registers.  What differs is how the candidates reach
+// the threads.
+//
+// A thread's candidates are the bin-row segments of the bin-sorted arrays
+// within its radius (row_segment).  The warp stages the union of its threads'
+// windows: lane r takes bin row r of the window, computes that row's segment
+// for the whole warp tile with the largest radius (a superset of every
+// thread's segment in the row, the window arithmetic being monotone), and
+// copies the row's positions, colours and bin offsets from global into
+// shared memory with one bulk copy each (cp.async.bulk on the TMA engine,
+// completion counted in bytes on an mbarrier).  Each thread then builds its
+// own row table from the staged offsets, trims each segment's ends to its
+// x-extent in that row (points outside it lie beyond the radius), and walks
+// its segments out of shared memory: nothing is loaded from global memory in
+// the walk, and neighbouring lanes read neighbouring records.
+//
+// A window with more bin rows or records than the buffer holds (dense
+// clusters, wide radii) is walked straight from global memory instead (the
+// direct walk of near_common.cuh).  A heavy warp tile cut into S work items
+// (the plan in gather_near.cu) gives item k the k-th share of every thread's
+// candidate sequence.  Every wait on the barrier is bounded: if one gives up,
+// the kernel sets ST_TIMEOUT in the status word, waits (bounded again) for
+// its copies still in flight, and leaves.
+#include "near_common.cuh"
+#include "sat.cuh"
+
+#include <climits>
+
+namespace gmi {
+
+constexpr int kPassRows = 16;     // window bin rows per pass (height of the thread table)
+constexpr int kStageWarps = 4;    // warps per block
+constexpr unsigned kWaitPolls = 1u << 22;   // polls of the barrier before a wait gives up
+
+// Candidates one warp can stage at once, by micro-tile shape: the window of a
+// 32 x 16 px warp tile (4 x 4 micro-tiles) at one point per bin and a 6.4 px
+// radius is about 300 records in 14 bin rows.
+template <int MTH, int MTW>
+struct StageCap {
+  static constexpr int value = MTH * MTW >= 16 ? 352 : 224;
+};
+constexpr int kOffCap = 512;   // staged bin offsets per warp (each row's range rounded to 4)
+
+// One warp's shared-memory area.
+template <int CAP>
+struct __align__(16) StageBuf {
+  float4 col[CAP];                // staged colours (padded to four channels)
+  float2 pos[CAP];                // staged positions
+  unsigned off[kOffCap];          // staged bin offsets
+  unsigned tab[32][kPassRows + 1];  // per lane: its non-empty staged segments in walk
+                                  //   order, start | end << 16 (a pad column spreads
+                                  //   the lanes over the banks)
+  uint4 desc[kPassRows];          // per window row: (first record, its staged index,
+                                  //   first bin column, staged index of its offset)
+  unsigned long long bar;         // completes when the item's bulk copies have landed
+};
+
+template <int MTH, int MTW>
+constexpr int stage_bytes() {
+  return (int)sizeof(StageBuf<StageCap<MTH, MTW>::value>) * kStageWarps;
+}
+
+// Resident blocks per SM: the register budget of the accumulators (as for the
+// direct-load kernel), bounded by shared memory (227 KB per SM usable).
+template <int MTH, int MTW, int C>
+struct StagedOcc {
+  static constexpr int acc = MTH * MTW * (C + 1);
+  static constexpr int regs = acc <= 32 ? 5 : (acc <= 64 ? 4 : (acc <= 80 ? 3 : 2));
+  static constexpr int smem = (227 * 1024) / (stage_bytes<MTH, MTW>() + 1024);
+  static constexpr int value = regs < smem ? regs : smem;
+};
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Arrives on the barrier and raises its expected transaction count by `bytes`.
+__device__ __forceinline__ void mbar_arrive_expect(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(unsigned long long* bar, unsigned parity) {
+  unsigned done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return done != 0u;
+}
+
+// Waits for the phase of the given parity; false after kWaitPolls polls.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+  for (unsigned k = 0; k < kWaitPolls; ++k)
+    if (mbar_test(bar, parity)) return true;
+  return false;
+}
+
+// Global -> shared bulk copy on the TMA engine; `bytes` and both addresses are
+// multiples of 16.
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+
+// Orders this thread's earlier shared-memory accesses before later
+// async-proxy (bulk copy) writes to the same memory.
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ int warp_min(int v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+__device__ __forceinline__ float warp_maxf(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+__device__ __forceinline__ int warp_max(int v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// One candidate point (position p, colour cv) into every pixel of the
+// thread's micro-tile (shared sigma): separable weights gx[j] gy[r] with
+// gx[j] = 2^(-(u + j sqrt(kappa))^2), u = (x_q0 - x) sqrt(kappa) (gy alike),
+// then C + 1 fused multiply-adds per pixel as packed FFMA2 pairs.  Truncated
+// mode keeps a pair only where -kappa d^2 >= neg_thr.
+template <int MTH, int MTW, int C, bool TRUNC>
+__device__ __forceinline__ void consume_pt(float2* accp, float* accs, float sk, float xq0, float yq0, float neg_thr,
+                                           const float2 p, const float4 cv) {
+  constexpr int NP = (C + 1) / 2;
+  constexpr int ODD = (C + 1) & 1;
+  const float c4[4] = {cv.x, cv.y, cv.z, cv.w};
+  const float clast = c4[C - 1];   // the scalar accumulator's value (C even)
+  // the coordinate difference first (its rounding is relative to the small
+  // difference, not to the pixel coordinate), then the scale
+  const float u = (xq0 - p.x) * sk;
+  const float v = (yq0 - p.y) * sk;
+  float ax[MTW], gx[MTW], ay[MTH], gy[MTH];
+#pragma unroll
+  for (int j = 0; j < MTW; ++j) {
+    const float tt = u + (float)j * sk;
+    ax[j] = -tt * tt;
+    gx[j] = ex2(ax[j]);
+  }
+#pragma unroll
+  for (int r = 0; r < MTH; ++r) {
+    const float tt = v + (float)r * sk;
+    ay[r] = -tt * tt;
+    gy[r] = ex2(ay[r]);
+  }
+  if (!TRUNC) {
+    // column factors times the colours once (the pair (gx, gx c_0) by one
+    // scalar product), then one FFMA2 per pair and pixel
+    float2 hx[MTW][NP];
+    float hs[MTW];
+#pragma unroll
+    for (int j = 0; j < MTW; ++j) {
+      hx[j][0] = make_float2(gx[j], gx[j] * c4[0]);
+#pragma unroll
+      for (int q = 1; q < NP; ++q) hx[j][q] = make_float2(gx[j] * c4[2 * q - 1], gx[j] * c4[2 * q]);
+      if (ODD) hs[j] = gx[j] * clast;
+    }
+#pragma unroll
+    for (int r = 0; r < MTH; ++r) {
+      const float2 gg = make_float2(gy[r], gy[r]);
+#pragma unroll
+      for (int j = 0; j < MTW; ++j) {
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+          float2& acq = accp[(r * MTW + j) * NP + q];
+          acq = __ffma2_rn(gg, hx[j][q], acq);
+        }
+        if (ODD) accs[(r * MTW + j) * ODD] = fmaf(gy[r], hs[j], accs[(r * MTW + j) * ODD]);
+      }
+    }
+  } else {
+    float2 cp[NP];
+    cp[0] = make_float2(1.0f, c4[0]);
+#pragma unroll
+    for (int q = 1; q < NP; ++q) cp[q] = make_float2(c4[2 * q - 1], c4[2 * q]);
+#pragma unroll
+    for (int r = 0; r < MTH; ++r)
+#pragma unroll
+      for (int j = 0; j < MTW; ++j) {
+        const float e = ax[j] + ay[r];
+        const float wgt = (e >= neg_thr) ? gx[j] * gy[r] : 0.0f;
+        const float2 ww = make_float2(wgt, wgt);
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+          float2& acq = accp[(r * MTW + j) * NP + q];
+          acq = __ffma2_rn(ww, cp[q], acq);
+        }
+        if (ODD) accs[(r * MTW + j) * ODD] = fmaf(wgt, clast, accs[(r * MTW + j) * ODD]);
+      }
+  }
+}
+
+// Normalises the micro-tile's sums (Eq. 1) and stores colours, den and a zero
+// shift; rows of whole float4s when the micro-tile row is one.
+template <int MTH, int MTW, int C>
+__device__ __forceinline__ void store_tile(const ImageGeom& g, int x0, int y0, int nx, int ny, const float* acc) {
+#pragma unroll
+  for (int r = 0; r < MTH; ++r) {
+    if (r >= ny) break;
+    float outv[MTW * C];
+    float denv[MTW];
+#pragma unroll
+    for (int j = 0; j < MTW; ++j) {
+      const float* q = acc + (r * MTW + j) * (C + 1);
+      const float d = q[0];
+      const float inv = d > 0.0f ? 1.0f / d : 0.0f;
+      denv[j] = d;
+#pragma unroll
+      for (int ch = 0; ch < C; ++ch) outv[j * C + ch] = q[1 + ch] * inv;
+    }
+    const long long row = (long long)(y0 + r) * g.W + x0;
+    if (MTW % 4 == 0 && g.vec_ok && nx == MTW) {
+      float4* o = reinterpret_cast<float4*>(g.image + row * C);
+#pragma unroll
+      for (int k = 0; k < MTW * C / 4; ++k)
+        o[k] = make_float4(outv[4 * k], outv[4 * k + 1], outv[4 * k + 2], outv[4 * k + 3]);
+      if (g.den) {
+        float4* dd = reinterpret_cast<float4*>(g.den + row);
+#pragma unroll
+        for (int k = 0; k < MTW / 4; ++k)
+          dd[k] = make_float4(denv[4 * k], denv[4 * k + 1], denv[4 * k + 2], denv[4 * k + 3]);
+      }
+      if (g.shift) {
+        float4* ss = reinterpret_cast<float4*>(g.shift + row);
+#pragma unroll
+        for (int k = 0; k < MTW / 4; ++k) ss[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < MTW; ++j) {
+        if (j >= nx) break;
+#pragma unroll
+        for (int ch = 0; ch < C; ++ch) g.image[(row + j) * C + ch] = outv[j * C + ch];
+        if (g.den) g.den[row + j] = denv[j];
+        if (g.shift) g.shift[row + j] = 0.0f;
+      }
+    }
+  }
+}
+
+// Geometry of one work item for this thread: the warp tile's micro-tile of
+// this lane, its pixels and its squared candidate radius (the plan's bound U
+// plus k^2 sigma^2; +inf U marks a far-field micro-tile, left to the far kernel).
+struct ItemGeo {
+  long long wt;
+  unsigned split, S, slot;
+  int img, x0, y0, nx, ny;
+  bool active;
+  float R2;
+};
+
+template <int MTH, int MTW, bool TRUNC>
+__device__ __forceinline__ ItemGeo item_geo(const KArgs& a, unsigned t, int lane) {
+  ItemGeo it;
+  const uint4 item = a.w.items[t];
+  it.wt = (long long)item.x;
+  it.split = item.y;
+  it.S = item.z;
+  it.slot = item.w;
+  it.img = find_image<1>(a, it.wt);
+  const ImageGeom g = a.w.table ? a.w.table[it.img] : a.g0;   // a copy: no address of a local struct
+  const long long lt = it.wt - g.wt_base;
+  const int mt_x = (int)(lt % g.wtx) * 8 + (lane & 7);
+  const int mt_y = (int)(lt / g.wtx) * 4 + (lane >> 3);
+  it.x0 = mt_x * MTW;
+  it.y0 = mt_y * MTH;
+  it.active = it.x0 < g.W && it.y0 < g.H;
+  it.nx = it.active ? min(MTW, g.W - it.x0) : 0;
+  it.ny = it.active ? min(MTH, g.H - it.y0) : 0;
+  it.R2 = g.r2k;
+  if (!TRUNC) {
+    const float U = __ldcg(&a.w.ubound[it.wt * 32 + lane]);
+    if (!(U <= g.u_near_max)) it.active = false;
+    it.R2 = U + g.r2k;
+  }
+  return it;
+}
+
+template <int MTH, int MTW, int C, bool TRUNC>
+__global__ void __launch_bounds__(32 * kStageWarps, StagedOcc<MTH, MTW, C>::value) near_staged_kernel(KArgs a_in) {
+  constexpr int CAP = StageCap<MTH, MTW>::value;
+  using Buf = StageBuf<CAP>;
+  extern __shared__ __align__(16) unsigned char stage_smem[];
+  const KArgs a = resolve(a_in);
+  constexpr int NA = MTH * MTW * (C + 1);   // accumulators per thread
+  constexpr int NP = (C + 1) / 2;           // packed accumulator pairs per pixel
+  constexpr int ODD = (C + 1) & 1;          // one scalar accumulator left over (C even)
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  Buf& sb = reinterpret_cast<Buf*>(stage_smem)[warp];
+  if (lane == 0) mbar_init(&sb.bar);
+  __syncwarp();
+  unsigned parity = 0;
+  bool stalled = false;   // a bounded wait gave up (warp-uniform)
+
+  const unsigned n_items = min(a.w.status[kItemCount], a.cap_items);
+  const unsigned n_warps = gridDim.x * kStageWarps;
+  unsigned t = blockIdx.x * kStageWarps + warp;
+  while (t < n_items) {
+    // Accumulators in packed pairs: per pixel (r, j) the pairs (den, num_0),
+    // (num_1, num_2), plus num_{C-1} alone when C is even.
+    float2 accp[MTH * MTW * NP];
+    float accs[MTH * MTW * ODD + 1 - ODD];
+#pragma unroll
+    for (int k = 0; k < MTH * MTW * NP; ++k) accp[k] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < MTH * MTW * ODD + 1 - ODD; ++k) accs[k] = 0.0f;
+
+    // ---- set-up: this thread's window and share; the warp's window (when it
+    // fits the buffer) staged and this thread's row table built, else the
+    // direct walk
+    bool staged = false;
+    unsigned nseg = 0;   // this thread's staged segments
+    float sk, xq0, yq0, neg_thr;
+    {
+      const ItemGeo it = item_geo<MTH, MTW, TRUNC>(a, t, lane);
+      const ImageGeom g = a.w.table ? a.w.table[it.img] : a.g0;   // a copy: no address of a local struct
+      sk = g.sk;
+      xq0 = (float)it.x0 + 0.5f;
+      yq0 = (float)it.y0 + 0.5f;
+      neg_thr = -g.kappa * g.r2k;
+      LaneWin w;
+      int my_lo = INT_MAX, my_hi = INT_MIN;
+      unsigned lo = 0u, hi = 0xffffffffu;
+      float myR2 = 0.0f;
+      if (it.active) {
+        w = lane_window(g, it.x0, it.y0, it.nx, it.ny, it.R2);
+        my_lo = w.by_lo;
+        my_hi = w.by_hi;
+        myR2 = it.R2;
+        item_share(a, g, w, it.split, it.S, lo, hi);
+      }
+      const int wy_lo = warp_min(my_lo), wy_hi = warp_max(my_hi);
+      const int rows = wy_hi >= wy_lo ? wy_hi - wy_lo + 1 : 0;
+      bool fits = rows > 0 && rows <= kPassRows;
+      if (fits) {
+        // the warp's window: the warp tile's pixel rectangle (clipped to the
+        // image) with the largest radius of its threads; lane r takes row r
+        const float R2w = warp_maxf(myR2);
+        const long long lt = it.wt - g.wt_base;
+        const int X0 = (int)(lt % g.wtx) * 8 * MTW, Y0 = (int)(lt / g.wtx) * 4 * MTH;
+        const LaneWin ww = lane_window(g, X0, Y0, min(8 * MTW, g.W - X0), min(4 * MTH, g.H - Y0), R2w);
+        unsigned S0 = 0u, need = 0u, ocnt = 0u, oskip = 0u;
+        int bxw_lo = 0;
+        long long o_lo = 0;
+        if (lane < rows) {
+          const int by = wy_lo + lane;
+          int bxw_hi;
+          float hxw;
+          row_bins(g, ww, by, bxw_lo, bxw_hi, hxw);
+          const long long rowb = g.bin_base + (long long)by * g.nbx;
+          S0 = __ldg(&a.w.off[rowb + bxw_lo]);
+          const unsigned E0 = __ldg(&a.w.off[rowb + bxw_hi + 1]);
+          // records [S0, E0) widened to even indices (16-byte boundaries for the
+          // positions), offsets [rowb + bxw_lo, rowb + bxw_hi + 1] widened to
+          // multiples of four
+          need = E0 > S0 ? ((E0 + 1u) & ~1u) - (S0 & ~1u) : 0u;
+          o_lo = (rowb + bxw_lo) & ~3LL;
+          ocnt = (unsigned)(((rowb + bxw_hi + 2 + 3) & ~3LL) - o_lo);
+          oskip = (unsigned)(rowb + bxw_lo - o_lo);
+        }
+        // one scan of both counts (each clamped so the packed sums cannot carry)
+        const unsigned pk = min(need, (unsigned)CAP + 1u) | (min(ocnt, (unsigned)kOffCap + 1u) << 16);
+        unsigned incl = pk;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const unsigned u = __shfl_up_sync(full, incl, o);
+          if (lane >= o) incl += u;
+        }
+        const unsigned tot = __shfl_sync(full, incl, 31);
+        fits = (tot & 0xffffu) <= (unsigned)CAP && (tot >> 16) <= (unsigned)kOffCap;
+        if (fits) {
+          const unsigned excl = incl - pk;
+          const unsigned abase = excl & 0xffffu, obase = excl >> 16;
+          if (lane < rows) sb.desc[lane] = make_uint4(S0, abase + (S0 & 1u), (unsigned)bxw_lo, obase + oskip);
+          // every lane is past its reads of the previous item's buffer
+          fence_async_smem();
+          __syncwarp();
+          if (lane == 0)
+            mbar_arrive_expect(&sb.bar, (tot & 0xffffu) * (unsigned)(sizeof(float2) + sizeof(float4)) +
+                                            (tot >> 16) * (unsigned)sizeof(unsigned));
+          __syncwarp();
+          if (lane < rows) {
+            if (need) {
+              const unsigned s0 = S0 & ~1u;
+              bulk_copy(&sb.pos[abase], a.w.sxy + s0, need * (unsigned)sizeof(float2), &sb.bar);
+              bulk_copy(&sb.col[abase], a.w.sval + s0, need * (unsigned)sizeof(float4), &sb.bar);
+            }
+            bulk_copy(&sb.off[obase], a.w.off + o_lo, ocnt * (unsigned)sizeof(unsigned), &sb.bar);
+          }
+          const bool ok = mbar_wait(&sb.bar, parity);
+          parity ^= 1u;
+          if (__any_sync(full, !ok)) stalled = true;
+          if (!stalled && it.active) {
+            // this thread's list of non-empty segments: per row its segment
+            // from the staged offsets, its share of the sequence, and the ends
+            // trimmed to its x-extent (with a margin above the rounding of the
+            // bounds)
+            const float eps = 1e-3f + fabsf(w.xq1) * 0x1p-20f;
+            unsigned cum = 0;
+            for (int by = w.by_lo; by <= w.by_hi; ++by) {
+              const int r = by - wy_lo;
+              const uint4 d = sb.desc[r];
+              int bx_lo, bx_hi;
+              float hx;
+              row_bins(g, w, by, bx_lo, bx_hi, hx);
+              const unsigned s = sb.off[d.w + (unsigned)(bx_lo - (int)d.z)];
+              const unsigned e = sb.off[d.w + (unsigned)(bx_hi + 1 - (int)d.z)];
+              const unsigned len = e - s;
+              const unsigned a0 = lo > cum ? min(lo - cum, len) : 0u;
+              const unsigned b0 = hi > cum ? min(hi - cum, len) : 0u;
+              cum += len;
+              unsigned i0 = d.y + (s - d.x) + a0, i1 = d.y + (s - d.x) + b0;
+              const float xa = w.xq0 - hx - eps, xb = w.xq1 + hx + eps;
+              while (i0 < i1 && sb.pos[i0].x < xa) ++i0;
+              while (i1 > i0 && sb.pos[i1 - 1].x > xb) --i1;
+              if (i0 < i1) sb.tab[lane][nseg++] = i0 | (i1 << 16);
+            }
+          }
+          staged = true;
+        }
+      }
+      if (!fits && it.active) {
+        // the window does not fit the buffer: straight from global memory
+        auto consume3 = [&](const float2 p, const float4 cv, const float4) {
+          consume_pt<MTH, MTW, C, TRUNC>(accp, accs, sk, xq0, yq0, neg_thr, p, cv);
+        };
+        direct_walk<false>(a, g, w, lo, hi, consume3);
+      }
+    }
+    if (stalled) break;
+
+    // ---- the walk: this thread's records, segment after segment (a tight
+    // loop over each contiguous segment; in a regular grid the lanes' segments
+    // have equal lengths, so the lanes stay together)
+    if (staged) {
+      __syncwarp();
+      const unsigned* tab = sb.tab[lane];
+      for (unsigned sg = 0; sg < nseg; ++sg) {
+        const unsigned te = tab[sg];
+        const unsigned e = te >> 16;
+        for (unsigned i = te & 0xffffu; i < e; ++i)
+          consume_pt<MTH, MTW, C, TRUNC>(accp, accs, sk, xq0, yq0, neg_thr, sb.pos[i], sb.col[i]);
+      }
+      __syncwarp();
+    }
+
+    // ---- epilogue: the item's geometry again (recomputed rather than kept
+    // live through the walk), then the split-tile sums or the stores
+    const ItemGeo it = item_geo<MTH, MTW, TRUNC>(a, t, lane);
+    const ImageGeom g = a.w.table ? a.w.table[it.img] : a.g0;   // a copy: no address of a local struct
+    unsigned nt = 0;
+    if (lane == 0) nt = n_warps + atomicAdd(&a.w.status[kNearHead], 1u);
+
+    float acc[NA];   // per pixel (r, j): [den, num_0 .. num_{C-1}]
+#pragma unroll
+    for (int px = 0; px < MTH * MTW; ++px)
+#pragma unroll
+      for (int k = 0; k <= C; ++k) {
+        if (k < 2 * NP) {
+          const float2 pr = accp[px * NP + k / 2];
+          acc[px * (C + 1) + k] = (k & 1) ? pr.y : pr.x;
+        } else {
+          acc[px * (C + 1) + k] = accs[px * ODD];
+        }
+      }
+
+    bool finish = true;
+    if (it.S > 1) {
+      // split tile: add this item's partial sums into the tile's slot; the
+      // last item to finish reads the totals and writes the pixels
+      float* mine = a.w.slots + ((size_t)it.slot * 32 + lane) * NA;
+      if (it.active) {
+#pragma unroll
+        for (int k = 0; k < NA; k += 4)
+          asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(mine + k), "f"(acc[k]),
+                       "f"(acc[k + 1]), "f"(acc[k + 2]), "f"(acc[k + 3])
+                       : "memory");
+      }
+      __threadfence();
+      __syncwarp();
+      unsigned prev = 0;
+      if (lane == 0) prev = atomicAdd(&a.w.tile_done[it.wt], 1u);
+      prev = __shfl_sync(full, prev, 0);
+      finish = prev == it.S - 1;
+      if (finish) {
+        __threadfence();
+        if (it.active) {
+#pragma unroll
+          for (int k = 0; k < NA; k += 4) {
+            const float4 q = __ldcg(reinterpret_cast<const float4*>(mine + k));
+            acc[k] = q.x;
+            acc[k + 1] = q.y;
+            acc[k + 2] = q.z;
+            acc[k + 3] = q.w;
+          }
+        }
+      }
+    }
+    if (finish && it.active) store_tile<MTH, MTW, C>(g, it.x0, it.y0, it.nx, it.ny, acc);
+    t = __shfl_sync(full, nt, 0);
+  }
+  if (stalled) {
+    // report, and do not leave while this warp's bulk copies may still be
+    // writing into its shared memory (the phase given up on is parity ^ 1)
+    if (lane == 0) atomicOr(&a.w.status[kStatusErr], ST_TIMEOUT);
+    mbar_wait(&sb.bar, parity ^ 1u);
+    return;
+  }
+  // far-field micro-tiles queued: warps out of work build the summed-area
+  // table the far kernel's window search reads
+  if constexpr (!TRUNC) {
+    if (__ldcg(&a.w.status[kFarCount]) > 0u) sat_build(a);
+  }
+}
+
+// Resident blocks per SM of one instantiation with its shared memory (the
+// opt-in size is set on first use), cached; all devices of a process are
+// taken to be alike.
+template <int MTH, int MTW, int C, bool TRUNC>
+static int staged_occ() {
+  static const int n = [] {
+    const int bytes = stage_bytes<MTH, MTW>();
+    cudaFuncSetAttribute(near_staged_kernel<MTH, MTW, C, TRUNC>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, near_staged_kernel<MTH, MTW, C, TRUNC>, 32 * kStageWarps,
+                                                  bytes);
+    return b > 0 ? b : 1;
+  }();
+  return n;
+}
+
+template <int MTH, int MTW, int C>
+static int staged_occ_c(bool trunc) {
+  return trunc ? staged_occ<MTH, MTW, C, true>() : staged_occ<MTH, MTW, C, false>();
+}
+
+template <int MTH, int MTW>
+static int staged_occ_mt(int C, bool trunc) {
+  switch (C) {
+    case 1: return staged_occ_c<MTH, MTW, 1>(trunc);
+    case 2: return staged_occ_c<MTH, MTW, 2>(trunc);
+    case 3: return staged_occ_c<MTH, MTW, 3>(trunc);
+    default: return staged_occ_c<MTH, MTW, 4>(trunc);
+  }
+}
+
+// Resident staged-kernel blocks per SM (each block holds kStageWarps warps).
+int staged_blocks_per_sm(int mth, int mtw, int C, bool trunc) {
+  const int c = C < 1 ? 1 : (C > 4 ? 4 : C);
+  if (mth == 4 && mtw == 8) return staged_occ_mt<4, 8>(c, trunc);
+  if (mth == 2 && mtw == 4) return staged_occ_mt<2, 4>(c, trunc);
+  if (mth == 4 && mtw == 2) return staged_occ_mt<4, 2>(c, trunc);
+  return staged_occ_mt<4, 4>(c, trunc);
+}
+
+template <int MTH, int MTW, int C, bool TRUNC>
+static cudaError_t launch_staged_k(const KArgs& a, int grid, cudaStream_t s) {
+  staged_occ<MTH, MTW, C, TRUNC>();   // sets the shared-memory opt-in once
+  near_staged_kernel<MTH, MTW, C, TRUNC><<<grid, 32 * kStageWarps, stage_bytes<MTH, MTW>(), s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int MTH, int MTW>
+static cudaError_t launch_staged_mt(const KArgs& a, bool trunc, int grid, cudaStream_t s) {
+  switch (a.C) {
+    case 1: return trunc ? launch_staged_k<MTH, MTW, 1, true>(a, grid, s) : launch_staged_k<MTH, MTW, 1, false>(a, grid, s);
+    case 2: return trunc ? launch_staged_k<MTH, MTW, 2, true>(a, grid, s) : launch_staged_k<MTH, MTW, 2, false>(a, grid, s);
+    case 3: return trunc ? launch_staged_k<MTH, MTW, 3, true>(a, grid, s) : launch_staged_k<MTH, MTW, 3, false>(a, grid, s);
+    default: return trunc ? launch_staged_k<MTH, MTW, 4, true>(a, grid, s) : launch_staged_k<MTH, MTW, 4, false>(a, grid, s);
+  }
+}
+
+// grid: blocks of kStageWarps warps.
+cudaError_t launch_near_staged(const KArgs& a, int mth, int mtw, bool trunc, int grid, cudaStream_t s) {
+  if (mth == 4 && mtw == 4) return launch_staged_mt<4, 4>(a, trunc, grid, s);
+  if (mth == 4 && mtw == 8) return launch_staged_mt<4, 8>(a, trunc, grid, s);
+  if (mth == 2 && mtw == 4) return launch_staged_mt<2, 4>(a, trunc, grid, s);
+  if (mth == 4 && mtw == 2) return launch_staged_mt<4, 2>(a, trunc, grid, s);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace gmi

@@ -15,12 +15,20 @@ from gpu_helpers import TOL_FWD, log_scaled_den, sample_pixels, to_dev
 
 pytestmark = pytest.mark.gpu
 
-VARIANTS = [1, 2, 3]   # 4x4, 4x8, 2x4 micro-tiles
+VARIANTS = [1, 2, 3, 4]   # 4x4, 4x8, 2x4, 4x2 micro-tiles
 
 
 def gmi():
     import paper_2012_13257_b300 as g
     return g
+
+
+@pytest.fixture(autouse=True, params=["staged", "direct"])
+def gather(request):
+    """Every forward case runs through both near-field gathers (same sums)."""
+    gmi().set_gather(request.param)
+    yield request.param
+    gmi().set_gather("auto")
 
 
 def run(im, dev, **kw):
