@@ -30,7 +30,7 @@ enum : int {
   kNearHead = 2,       // next work item for the persistent near kernel
   kFarHead = 3,        // next far-queue entry for the far kernel
   kBwdHead = 4,        // next work item for the backward kernels
-  kItemCount = 5,      // near-kernel work items written by the plan kernel
+  kItemCount = 5,      // near-kernel work items past the first one of each warp tile
   kSlotCount = 6,      // partial-sum slots handed out by the plan kernel
   kFbCount = 7,        // micro-tiles queued for the backward fallback kernel
   kFbHead = 8,         // next entry of that queue
@@ -58,7 +58,7 @@ struct ImageGeom {
   int b;                 // bin edge in pixels
   int nbx, nby;          // bins across / down
   int mtx, mty;          // micro-tiles across / down
-  int wtx, wty;          // warp tiles across / down (8 x 4 micro-tiles each)
+  int wtx, wty;          // warp tiles across / down (8 x 4 micro-tiles each; fewer than 2^31 per image)
   float inv_b;           // 1 / b
   float sigma;           // the shared sigma; with per-point sigmas their upper bound
   float kappa;           // log2(e) / (2 sigma^2)
@@ -84,7 +84,8 @@ struct DevWork {
   float4* sval;          // [n_total]: bin-sorted colours, padded to 4 channels
   unsigned* partials;    // scan partial sums
   uint2* farq;           // [mt_total]: (image, micro-tile) queued for the far kernel
-  uint4* items;          // [cap_items]: near-kernel work items (warp tile, split, splits, slot)
+  uint4* items;          // [cap_items]: near-kernel work items (warp tile, split | splits << 16,
+                         //   slot, image); the first item of warp tile wt is items[wt]
   unsigned* tile_done;   // [wt_total]: finished splits per warp tile
   float* slots;          // [cap_slots * slot_floats]: sums of the work items of split warp tiles
   float* ubound;         // [wt_total * 32]: per micro-tile bound U on the nearest squared

@@ -187,8 +187,8 @@ __device__ void near_plan_body(const KArgs& a, int trunc, long long wt) {
   const int img = find_image<1>(a, wt);
   const ImageGeom g = a.w.table ? a.w.table[img] : a.g0;
   const long long lt = wt - g.wt_base;
-  const int mt_x = (int)(lt % g.wtx) * 8 + (lane & 7);
-  const int mt_y = (int)(lt / g.wtx) * 4 + (lane >> 3);
+  const int mt_x = (int)((unsigned)lt % (unsigned)g.wtx) * 8 + (lane & 7);
+  const int mt_y = (int)((unsigned)lt / (unsigned)g.wtx) * 4 + (lane >> 3);
   const int x0 = mt_x * MTW, y0 = mt_y * MTH;
   const bool active = x0 < g.W && y0 < g.H;
   const int nx = active ? min(MTW, g.W - x0) : 0;
@@ -242,9 +242,16 @@ __device__ void near_plan_body(const KArgs& a, int trunc, long long wt) {
       for (int k = 0; k < na / 4; ++k) z[k] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
   }
+  // the tile's first item sits at index wt (so a near-kernel warp can start on
+  // warp tile t without reading the queue first); its other splits follow
+  // all first items
   if (lane == 0) {
-    const unsigned base = atomicAdd(&a.w.status[kItemCount], S);
-    for (unsigned k = 0; k < S && base + k < a.cap_items; ++k) a.w.items[base + k] = make_uint4((unsigned)wt, k, S, slot);
+    a.w.items[wt] = make_uint4((unsigned)wt, S << 16, slot, (unsigned)img);
+    if (S > 1) {
+      const unsigned long long base = (unsigned long long)a.wt_total + atomicAdd(&a.w.status[kItemCount], S - 1);
+      for (unsigned k = 1; k < S && base + k - 1 < a.cap_items; ++k)
+        a.w.items[base + k - 1] = make_uint4((unsigned)wt, k | (S << 16), slot, (unsigned)img);
+    }
   }
 }
 
@@ -294,7 +301,8 @@ __global__ void __launch_bounds__(128, NearOcc<MTH, MTW, C>::value) near_kernel(
   const int lx = lane & 7, ly = lane >> 3;
   const int warp = threadIdx.x >> 5;
 
-  const unsigned n_items = min(a.w.status[kItemCount], a.cap_items);
+  const unsigned n_items = (unsigned)min((unsigned long long)a.wt_total + a.w.status[kItemCount],
+                                         (unsigned long long)a.cap_items);
   const unsigned n_warps = gridDim.x * kNearWarps;
   // first item by warp index, later ones claimed from the queue (the claim is
   // made once the item's sums are complete, so that its latency overlaps the
@@ -303,12 +311,12 @@ __global__ void __launch_bounds__(128, NearOcc<MTH, MTW, C>::value) near_kernel(
   while (t < n_items) {
     const uint4 item = a.w.items[t];
     const long long wt = (long long)item.x;
-    const unsigned split = item.y, S = item.z, slot = item.w;
-    const int img = find_image<1>(a, wt);
+    const unsigned split = item.y & 0xffffu, S = item.y >> 16, slot = item.z;
+    const int img = (int)item.w;
     const ImageGeom g = a.w.table ? a.w.table[img] : a.g0;
     const long long lt = wt - g.wt_base;
-    const int mt_x = (int)(lt % g.wtx) * 8 + lx;
-    const int mt_y = (int)(lt / g.wtx) * 4 + ly;
+    const int mt_x = (int)((unsigned)lt % (unsigned)g.wtx) * 8 + lx;
+    const int mt_y = (int)((unsigned)lt / (unsigned)g.wtx) * 4 + ly;
     const int x0 = mt_x * MTW, y0 = mt_y * MTH;
     bool active = x0 < g.W && y0 < g.H;
     const int nx = active ? min(MTW, g.W - x0) : 0;
@@ -445,8 +453,8 @@ __global__ void __launch_bounds__(128, NearOcc<MTH, MTW, C>::value) near_kernel(
       direct_walk<PP>(a, g, w, lo, hi, consume);
     }
 
-    unsigned nt = 0;
-    if (lane == 0) nt = n_warps + atomicAdd(&a.w.status[kNearHead], 1u);
+    unsigned nt = n_items;   // (no claim when the items do not outnumber the warps)
+    if (lane == 0 && n_items > n_warps) nt = n_warps + atomicAdd(&a.w.status[kNearHead], 1u);
 
     float acc[NA];   // per pixel (r, j): [den, num_0 .. num_{C-1}]
 #pragma unroll
@@ -504,7 +512,7 @@ __global__ void __launch_bounds__(128, NearOcc<MTH, MTW, C>::value) near_kernel(
         for (int j = 0; j < MTW; ++j) {
           const float* q = acc + (r * MTW + j) * (C + 1);
           const float d = q[0];
-          const float inv = d > 0.0f ? 1.0f / d : 0.0f;
+          const float inv = d > 0.0f ? __frcp_rn(d) : 0.0f;   // = 1 / d, correctly rounded
           denv[j] = d;
 #pragma unroll
           for (int ch = 0; ch < C; ++ch) outv[j * C + ch] = q[1 + ch] * inv;

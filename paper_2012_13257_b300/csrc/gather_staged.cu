@@ -10,16 +10,17 @@
 //
 // A thread's candidates are the bin-row segments of the bin-sorted arrays
 // within its radius (row_segment).  The warp stages the union of its threads'
-// windows: lane r takes bin row r of the window, computes that row's segment
-// for the whole warp tile with the largest radius (a superset of every
-// thread's segment in the row, the window arithmetic being monotone), and
-// copies the row's positions, colours and bin offsets from global into
-// shared memory with one bulk copy each (cp.async.bulk on the TMA engine,
-// completion counted in bytes on an mbarrier).  Each thread then builds its
-// own row table from the staged offsets, trims each segment's ends to its
-// x-extent in that row (points outside it lie beyond the radius), and walks
-// its segments out of shared memory: nothing is loaded from global memory in
-// the walk, and neighbouring lanes read neighbouring records.
+// windows: lane r takes bin row r of the window and computes that row's
+// segment for the whole warp tile with the largest radius (a superset of
+// every thread's segment in the row, the window arithmetic being monotone);
+// each row's positions and colours are then copied from global into shared
+// memory with one bulk copy per array (cp.async.bulk on the TMA engine,
+// completion counted in bytes on an mbarrier).  The bin offsets of the union
+// rows and of every thread's own rows are loaded in one round trip, and each
+// thread turns its own segments into indices of the staged copy.  The walk
+// then reads shared memory only, neighbouring lanes reading neighbouring
+// records.  (Trimming each segment's ends to the thread's x-extent in its
+// row was measured: the trim loops cost more than the few records they skip.)
 //
 // A window with more bin rows or records than the buffer holds (dense
 // clusters, wide radii) is walked straight from global memory instead (the
@@ -37,7 +38,11 @@ namespace gmi {
 
 constexpr int kPassRows = 16;     // window bin rows per pass (height of the thread table)
 constexpr int kStageWarps = 4;    // warps per block
-constexpr unsigned kWaitPolls = 1u << 22;   // polls of the barrier before a wait gives up
+// A barrier wait polls at most kWaitPolls times; each poll may suspend the
+// thread for up to kWaitHintNs until the phase completes (so a wait gives up
+// after about a second, and a waiting warp takes no issue slots meanwhile).
+constexpr unsigned kWaitPolls = 10000u;
+constexpr unsigned kWaitHintNs = 100000u;
 
 // Candidates one warp can stage at once, by micro-tile shape: the window of a
 // 32 x 16 px warp tile (4 x 4 micro-tiles) at one point per bin and a 6.4 px
@@ -46,19 +51,18 @@ template <int MTH, int MTW>
 struct StageCap {
   static constexpr int value = MTH * MTW >= 16 ? 352 : 224;
 };
-constexpr int kOffCap = 512;   // staged bin offsets per warp (each row's range rounded to 4)
 
 // One warp's shared-memory area.
 template <int CAP>
 struct __align__(16) StageBuf {
   float4 col[CAP];                // staged colours (padded to four channels)
   float2 pos[CAP];                // staged positions
-  unsigned off[kOffCap];          // staged bin offsets
   unsigned tab[32][kPassRows + 1];  // per lane: its non-empty staged segments in walk
                                   //   order, start | end << 16 (a pad column spreads
                                   //   the lanes over the banks)
-  uint4 desc[kPassRows];          // per window row: (first record, its staged index,
-                                  //   first bin column, staged index of its offset)
+  uint2 desc[kPassRows];          // per window row: (first record, its staged index)
+  uint4 item;                     // the current work item (as queued)
+  unsigned act[32];               // per lane: its micro-tile takes part in the item
   unsigned long long bar;         // completes when the item's bulk copies have landed
 };
 
@@ -96,10 +100,10 @@ __device__ __forceinline__ bool mbar_test(unsigned long long* bar, unsigned pari
   unsigned done;
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}"
       : "=r"(done)
-      : "r"(smem_addr(bar)), "r"(parity)
+      : "r"(smem_addr(bar)), "r"(parity), "r"(kWaitHintNs)
       : "memory");
   return done != 0u;
 }
@@ -231,7 +235,7 @@ __device__ __forceinline__ void store_tile(const ImageGeom& g, int x0, int y0, i
     for (int j = 0; j < MTW; ++j) {
       const float* q = acc + (r * MTW + j) * (C + 1);
       const float d = q[0];
-      const float inv = d > 0.0f ? 1.0f / d : 0.0f;
+      const float inv = d > 0.0f ? __frcp_rn(d) : 0.0f;   // = 1 / d, correctly rounded
       denv[j] = d;
 #pragma unroll
       for (int ch = 0; ch < C; ++ch) outv[j * C + ch] = q[1 + ch] * inv;
@@ -266,6 +270,20 @@ __device__ __forceinline__ void store_tile(const ImageGeom& g, int x0, int y0, i
   }
 }
 
+// Pixels of this lane's micro-tile in warp tile wt: origin (x0, y0) and
+// extent nx x ny (0 x 0 outside the image).
+template <int MTH, int MTW>
+__device__ __forceinline__ bool lane_tile(const ImageGeom& g, long long wt, int lane, int& x0, int& y0, int& nx,
+                                          int& ny) {
+  const long long lt = wt - g.wt_base;
+  x0 = ((int)((unsigned)lt % (unsigned)g.wtx) * 8 + (lane & 7)) * MTW;
+  y0 = ((int)((unsigned)lt / (unsigned)g.wtx) * 4 + (lane >> 3)) * MTH;
+  const bool in = x0 < g.W && y0 < g.H;
+  nx = in ? min(MTW, g.W - x0) : 0;
+  ny = in ? min(MTH, g.H - y0) : 0;
+  return in;
+}
+
 // Geometry of one work item for this thread: the warp tile's micro-tile of
 // this lane, its pixels and its squared candidate radius (the plan's bound U
 // plus k^2 sigma^2; +inf U marks a far-field micro-tile, left to the far kernel).
@@ -280,28 +298,40 @@ struct ItemGeo {
 template <int MTH, int MTW, bool TRUNC>
 __device__ __forceinline__ ItemGeo item_geo(const KArgs& a, unsigned t, int lane) {
   ItemGeo it;
-  const uint4 item = a.w.items[t];
-  it.wt = (long long)item.x;
-  it.split = item.y;
-  it.S = item.z;
-  it.slot = item.w;
-  it.img = find_image<1>(a, it.wt);
+  uint4 item;
+  float U = 0.0f;
+  if ((long long)t < a.wt_total) {
+    // a warp tile's first item: the tile is known before its queue entry is
+    // read, so the entry and the tile's bounds are loaded together
+    it.wt = t;
+    item = a.w.items[t];
+    if (!TRUNC) U = __ldcg(&a.w.ubound[it.wt * 32 + lane]);
+  } else {
+    item = a.w.items[t];
+    it.wt = (long long)item.x;
+    if (!TRUNC) U = __ldcg(&a.w.ubound[it.wt * 32 + lane]);
+  }
+  it.split = item.y & 0xffffu;
+  it.S = item.y >> 16;
+  it.slot = item.z;
+  it.img = (int)item.w;
   const ImageGeom g = a.w.table ? a.w.table[it.img] : a.g0;   // a copy: no address of a local struct
-  const long long lt = it.wt - g.wt_base;
-  const int mt_x = (int)(lt % g.wtx) * 8 + (lane & 7);
-  const int mt_y = (int)(lt / g.wtx) * 4 + (lane >> 3);
-  it.x0 = mt_x * MTW;
-  it.y0 = mt_y * MTH;
-  it.active = it.x0 < g.W && it.y0 < g.H;
-  it.nx = it.active ? min(MTW, g.W - it.x0) : 0;
-  it.ny = it.active ? min(MTH, g.H - it.y0) : 0;
+  it.active = lane_tile<MTH, MTW>(g, it.wt, lane, it.x0, it.y0, it.nx, it.ny);
   it.R2 = g.r2k;
   if (!TRUNC) {
-    const float U = __ldcg(&a.w.ubound[it.wt * 32 + lane]);
     if (!(U <= g.u_near_max)) it.active = false;
     it.R2 = U + g.r2k;
   }
   return it;
+}
+
+// The next work item of a warp: the queue hands out items past the first one
+// of every warp; when the items do not outnumber the warps nothing is left to
+// hand out, and the claim (one counter every warp would hit at about the same
+// time) is skipped.
+__device__ __forceinline__ unsigned claim_next(const KArgs& a, unsigned n_items, unsigned n_warps) {
+  if (n_items <= n_warps) return n_items;
+  return n_warps + atomicAdd(&a.w.status[kNearHead], 1u);
 }
 
 template <int MTH, int MTW, int C, bool TRUNC>
@@ -322,28 +352,31 @@ __global__ void __launch_bounds__(32 * kStageWarps, StagedOcc<MTH, MTW, C>::valu
   unsigned parity = 0;
   bool stalled = false;   // a bounded wait gave up (warp-uniform)
 
-  const unsigned n_items = min(a.w.status[kItemCount], a.cap_items);
+  // (the queue length is needed only past the warp tiles' first items, so
+  // the first item's loads do not wait for it)
+  const unsigned n_items = (unsigned)min((unsigned long long)a.wt_total + a.w.status[kItemCount],
+                                         (unsigned long long)a.cap_items);
   const unsigned n_warps = gridDim.x * kStageWarps;
   unsigned t = blockIdx.x * kStageWarps + warp;
-  while (t < n_items) {
+  while ((long long)t < a.wt_total || t < n_items) {
+    // ---- set-up: this thread's window and share; the warp's window (when it
+    // fits the buffer) staged and this thread's segment list built, else the
+    // direct walk
+    bool staged = false;
+    unsigned nseg = 0;   // this thread's staged segments
+    unsigned nt = 0;     // next item (lane 0), claimed early so the claim overlaps the walk
+    float sk, xq0, yq0, neg_thr;
     // Accumulators in packed pairs: per pixel (r, j) the pairs (den, num_0),
     // (num_1, num_2), plus num_{C-1} alone when C is even.
     float2 accp[MTH * MTW * NP];
     float accs[MTH * MTW * ODD + 1 - ODD];
-#pragma unroll
-    for (int k = 0; k < MTH * MTW * NP; ++k) accp[k] = make_float2(0.f, 0.f);
-#pragma unroll
-    for (int k = 0; k < MTH * MTW * ODD + 1 - ODD; ++k) accs[k] = 0.0f;
-
-    // ---- set-up: this thread's window and share; the warp's window (when it
-    // fits the buffer) staged and this thread's row table built, else the
-    // direct walk
-    bool staged = false;
-    unsigned nseg = 0;   // this thread's staged segments
-    float sk, xq0, yq0, neg_thr;
     {
       const ItemGeo it = item_geo<MTH, MTW, TRUNC>(a, t, lane);
       const ImageGeom g = a.w.table ? a.w.table[it.img] : a.g0;   // a copy: no address of a local struct
+      // what the epilogue needs, kept in shared memory rather than live
+      // through the walk
+      if (lane == 0) sb.item = make_uint4((unsigned)it.wt, it.split | (it.S << 16), it.slot, (unsigned)it.img);
+      sb.act[lane] = it.active ? 1u : 0u;
       sk = g.sk;
       xq0 = (float)it.x0 + 0.5f;
       yq0 = (float)it.y0 + 0.5f;
@@ -363,92 +396,93 @@ __global__ void __launch_bounds__(32 * kStageWarps, StagedOcc<MTH, MTW, C>::valu
       const int rows = wy_hi >= wy_lo ? wy_hi - wy_lo + 1 : 0;
       bool fits = rows > 0 && rows <= kPassRows;
       if (fits) {
-        // the warp's window: the warp tile's pixel rectangle (clipped to the
-        // image) with the largest radius of its threads; lane r takes row r
+        // The warp's window: the warp tile's pixel rectangle (clipped to the
+        // image) with the largest radius of its threads; lane r takes row r.
+        // Its offsets and this thread's own rows' offsets are loaded in one
+        // round trip.
         const float R2w = warp_maxf(myR2);
         const long long lt = it.wt - g.wt_base;
-        const int X0 = (int)(lt % g.wtx) * 8 * MTW, Y0 = (int)(lt / g.wtx) * 4 * MTH;
+        const int X0 = (int)((unsigned)lt % (unsigned)g.wtx) * 8 * MTW, Y0 = (int)((unsigned)lt / (unsigned)g.wtx) * 4 * MTH;
         const LaneWin ww = lane_window(g, X0, Y0, min(8 * MTW, g.W - X0), min(4 * MTH, g.H - Y0), R2w);
-        unsigned S0 = 0u, need = 0u, ocnt = 0u, oskip = 0u;
-        int bxw_lo = 0;
-        long long o_lo = 0;
+        unsigned S0 = 0u, E0 = 0u;
         if (lane < rows) {
           const int by = wy_lo + lane;
-          int bxw_hi;
+          int bxw_lo, bxw_hi;
           float hxw;
           row_bins(g, ww, by, bxw_lo, bxw_hi, hxw);
           const long long rowb = g.bin_base + (long long)by * g.nbx;
           S0 = __ldg(&a.w.off[rowb + bxw_lo]);
-          const unsigned E0 = __ldg(&a.w.off[rowb + bxw_hi + 1]);
-          // records [S0, E0) widened to even indices (16-byte boundaries for the
-          // positions), offsets [rowb + bxw_lo, rowb + bxw_hi + 1] widened to
-          // multiples of four
-          need = E0 > S0 ? ((E0 + 1u) & ~1u) - (S0 & ~1u) : 0u;
-          o_lo = (rowb + bxw_lo) & ~3LL;
-          ocnt = (unsigned)(((rowb + bxw_hi + 2 + 3) & ~3LL) - o_lo);
-          oskip = (unsigned)(rowb + bxw_lo - o_lo);
+          E0 = __ldg(&a.w.off[rowb + bxw_hi + 1]);
         }
-        // one scan of both counts (each clamped so the packed sums cannot carry)
-        const unsigned pk = min(need, (unsigned)CAP + 1u) | (min(ocnt, (unsigned)kOffCap + 1u) << 16);
-        unsigned incl = pk;
+        unsigned segs[kPassRows], sege[kPassRows];   // this thread's rows: global [start, end)
+#pragma unroll
+        for (int k = 0; k < kPassRows; ++k) {
+          segs[k] = sege[k] = 0u;
+          if (it.active && w.by_lo + k <= w.by_hi) {
+            int bx_lo, bx_hi;
+            float hx;
+            row_bins(g, w, w.by_lo + k, bx_lo, bx_hi, hx);
+            const long long rowb = g.bin_base + (long long)(w.by_lo + k) * g.nbx;
+            segs[k] = __ldg(&a.w.off[rowb + bx_lo]);
+            sege[k] = __ldg(&a.w.off[rowb + bx_hi + 1]);
+          }
+        }
+        // records [S0, E0) of row r widened to even indices, so that every
+        // position copy starts and ends on a 16-byte boundary
+        const unsigned need = E0 > S0 ? ((E0 + 1u) & ~1u) - (S0 & ~1u) : 0u;
+        unsigned incl = min(need, (unsigned)CAP + 1u);   // clamped: the sum cannot wrap
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
           const unsigned u = __shfl_up_sync(full, incl, o);
           if (lane >= o) incl += u;
         }
-        const unsigned tot = __shfl_sync(full, incl, 31);
-        fits = (tot & 0xffffu) <= (unsigned)CAP && (tot >> 16) <= (unsigned)kOffCap;
+        const unsigned total = __shfl_sync(full, incl, 31);
+        fits = total <= (unsigned)CAP;
         if (fits) {
-          const unsigned excl = incl - pk;
-          const unsigned abase = excl & 0xffffu, obase = excl >> 16;
-          if (lane < rows) sb.desc[lane] = make_uint4(S0, abase + (S0 & 1u), (unsigned)bxw_lo, obase + oskip);
+          const unsigned abase = incl - need;
+          if (lane < rows) sb.desc[lane] = make_uint2(S0, abase + (S0 & 1u));
           // every lane is past its reads of the previous item's buffer
           fence_async_smem();
           __syncwarp();
-          if (lane == 0)
-            mbar_arrive_expect(&sb.bar, (tot & 0xffffu) * (unsigned)(sizeof(float2) + sizeof(float4)) +
-                                            (tot >> 16) * (unsigned)sizeof(unsigned));
-          __syncwarp();
-          if (lane < rows) {
-            if (need) {
-              const unsigned s0 = S0 & ~1u;
-              bulk_copy(&sb.pos[abase], a.w.sxy + s0, need * (unsigned)sizeof(float2), &sb.bar);
-              bulk_copy(&sb.col[abase], a.w.sval + s0, need * (unsigned)sizeof(float4), &sb.bar);
-            }
-            bulk_copy(&sb.off[obase], a.w.off + o_lo, ocnt * (unsigned)sizeof(unsigned), &sb.bar);
+          if (lane == 0) {
+            mbar_arrive_expect(&sb.bar, total * (unsigned)(sizeof(float2) + sizeof(float4)));
+            nt = claim_next(a, n_items, n_warps);
           }
-          const bool ok = mbar_wait(&sb.bar, parity);
-          parity ^= 1u;
-          if (__any_sync(full, !ok)) stalled = true;
-          if (!stalled && it.active) {
-            // this thread's list of non-empty segments: per row its segment
-            // from the staged offsets, its share of the sequence, and the ends
-            // trimmed to its x-extent (with a margin above the rounding of the
-            // bounds)
-            const float eps = 1e-3f + fabsf(w.xq1) * 0x1p-20f;
+          __syncwarp();
+          if (lane < rows && need) {
+            const unsigned s0 = S0 & ~1u;
+            bulk_copy(&sb.pos[abase], a.w.sxy + s0, need * (unsigned)sizeof(float2), &sb.bar);
+            bulk_copy(&sb.col[abase], a.w.sval + s0, need * (unsigned)sizeof(float4), &sb.bar);
+          }
+          if (it.active) {
+            // this thread's list of non-empty segments (staged indices), with
+            // its share of the sequence
             unsigned cum = 0;
-            for (int by = w.by_lo; by <= w.by_hi; ++by) {
-              const int r = by - wy_lo;
-              const uint4 d = sb.desc[r];
-              int bx_lo, bx_hi;
-              float hx;
-              row_bins(g, w, by, bx_lo, bx_hi, hx);
-              const unsigned s = sb.off[d.w + (unsigned)(bx_lo - (int)d.z)];
-              const unsigned e = sb.off[d.w + (unsigned)(bx_hi + 1 - (int)d.z)];
-              const unsigned len = e - s;
-              const unsigned a0 = lo > cum ? min(lo - cum, len) : 0u;
-              const unsigned b0 = hi > cum ? min(hi - cum, len) : 0u;
-              cum += len;
-              unsigned i0 = d.y + (s - d.x) + a0, i1 = d.y + (s - d.x) + b0;
-              const float xa = w.xq0 - hx - eps, xb = w.xq1 + hx + eps;
-              while (i0 < i1 && sb.pos[i0].x < xa) ++i0;
-              while (i1 > i0 && sb.pos[i1 - 1].x > xb) --i1;
-              if (i0 < i1) sb.tab[lane][nseg++] = i0 | (i1 << 16);
+#pragma unroll
+            for (int k = 0; k < kPassRows; ++k) {
+              if (w.by_lo + k <= w.by_hi) {
+                const uint2 d = sb.desc[w.by_lo + k - wy_lo];
+                const unsigned len = sege[k] - segs[k];
+                const unsigned a0 = lo > cum ? min(lo - cum, len) : 0u;
+                const unsigned b0 = hi > cum ? min(hi - cum, len) : 0u;
+                cum += len;
+                const unsigned i0 = d.y + (segs[k] - d.x) + a0, i1 = d.y + (segs[k] - d.x) + b0;
+                if (i0 < i1) sb.tab[lane][nseg++] = i0 | (i1 << 16);
+              }
             }
+          }
+          if (total > 0u) {
+            const bool ok = mbar_wait(&sb.bar, parity);
+            parity ^= 1u;
+            if (__any_sync(full, !ok)) stalled = true;
           }
           staged = true;
         }
       }
+#pragma unroll
+      for (int k = 0; k < MTH * MTW * NP; ++k) accp[k] = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k < MTH * MTW * ODD + 1 - ODD; ++k) accs[k] = 0.0f;
       if (!fits && it.active) {
         // the window does not fit the buffer: straight from global memory
         auto consume3 = [&](const float2 p, const float4 cv, const float4) {
@@ -474,12 +508,21 @@ __global__ void __launch_bounds__(32 * kStageWarps, StagedOcc<MTH, MTW, C>::valu
       __syncwarp();
     }
 
-    // ---- epilogue: the item's geometry again (recomputed rather than kept
-    // live through the walk), then the split-tile sums or the stores
-    const ItemGeo it = item_geo<MTH, MTW, TRUNC>(a, t, lane);
+    // ---- epilogue: the item back from shared memory, then the split-tile
+    // sums or the stores
+    __syncwarp();
+    ItemGeo it;
+    {
+      const uint4 rec = sb.item;
+      it.wt = (long long)rec.x;
+      it.S = rec.y >> 16;
+      it.slot = rec.z;
+      it.img = (int)rec.w;
+    }
     const ImageGeom g = a.w.table ? a.w.table[it.img] : a.g0;   // a copy: no address of a local struct
-    unsigned nt = 0;
-    if (lane == 0) nt = n_warps + atomicAdd(&a.w.status[kNearHead], 1u);
+    lane_tile<MTH, MTW>(g, it.wt, lane, it.x0, it.y0, it.nx, it.ny);
+    it.active = sb.act[lane] != 0u;
+    if (!staged && lane == 0) nt = claim_next(a, n_items, n_warps);
 
     float acc[NA];   // per pixel (r, j): [den, num_0 .. num_{C-1}]
 #pragma unroll
