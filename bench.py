@@ -244,9 +244,21 @@ def pair_estimate(imgs, k=6.0, frac=16, seed=0):
 def prequeue(steps, per_step_s=400e-6):
     """A device spin long enough for the host to enqueue `steps` steps behind
     it, so that no timed step waits for the host inside its events (the spin
-    runs before the first start event, outside the timed region)."""
+    runs before the first start event, outside the timed region).  Returns an
+    event recorded right after the spin: if it has already completed once the
+    host has queued the timed steps, the host did not keep ahead of the device
+    (see queued_in_time)."""
     import torch
     torch.cuda._sleep(int(steps * per_step_s * SM_MAX_MHZ * 1e6))
+    ev = torch.cuda.Event()
+    ev.record()
+    return ev
+
+
+def queued_in_time(spin_done) -> bool:
+    """True while the device is still in the spin, i.e. every timed step was
+    enqueued before the device reached it."""
+    return not spin_done.query()
 
 
 def step_stats(ms):
@@ -256,24 +268,35 @@ def step_stats(ms):
     return {"median": s[len(s) // 2], "min": s[0], "max": s[-1]} if s else None
 
 
-def timed_steps(fn, steps, flush, stream, queued=False):
+def timed_steps(fn, steps, flush, stream, queued=False, info=None):
     """Per-step CUDA-event times (ms) with an untimed L2 flush before each
     step; with `queued`, the steps are enqueued behind a device spin (device
     time only; otherwise a slow host can leave the device idle inside a
-    step's events)."""
+    step's events).  If the host fell behind the spin, the queued run is
+    repeated once with a spin four times as long; `info` (a dict) receives
+    queue_ok (whether the steps kept ahead of the device)."""
     import torch
-    st = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
-    en = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
-    if queued:
-        prequeue(steps + 1)
-        flush.zero_()
-        fn()   # one more warm-up step in the queue, so no timed step starts the queued run
-    for k in range(steps):
-        flush.zero_()
-        st[k].record(stream)
-        fn()
-        en[k].record(stream)
-    torch.cuda.synchronize()
+    per_step = 400e-6
+    for attempt in range(2 if queued else 1):
+        st = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        en = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        spin = None
+        if queued:
+            spin = prequeue(steps + 1, per_step)
+            flush.zero_()
+            fn()   # one more warm-up step in the queue, so no timed step starts the queued run
+        for k in range(steps):
+            flush.zero_()
+            st[k].record(stream)
+            fn()
+            en[k].record(stream)
+        ok = queued_in_time(spin) if spin is not None else None
+        torch.cuda.synchronize()
+        if ok is not False:
+            break
+        per_step *= 4
+    if info is not None and queued:
+        info["queue_ok"] = ok
     return [a.elapsed_time(b) for a, b in zip(st, en)]
 
 
@@ -331,6 +354,68 @@ def e2e_pipelined(gmi, im, hP, hV, steps, D, world):
             "ms_per_step": total / steps, "note": "uploads, computes and downloads of consecutive steps overlap"}
 
 
+def _sig(v, digits=4):
+    """A float rounded to `digits` significant digits (short JSON)."""
+    if isinstance(v, float) and v == v and v not in (float("inf"), float("-inf")) and v != 0.0:
+        from math import floor, log10
+        return round(v, digits - 1 - int(floor(log10(abs(v)))))
+    return v
+
+
+def summary(d, keys, **sub):
+    """The named keys of a result dict, rounded, with the named keys of its
+    sub-objects; an error result passes through."""
+    if not isinstance(d, dict) or "error" in d:
+        return d
+    out = {k: _sig(d[k]) for k in keys if k in d}
+    for name, ks in sub.items():
+        if isinstance(d.get(name), dict):
+            out[name] = {k: _sig(d[name][k]) for k in ks if k in d[name]}
+    return out
+
+
+def e2e_breakdown(gmi, im, hP, hV, hO, steps, flush, stream):
+    """Where the end-to-end step's time goes: the same step as four pieces on
+    one stream with events between them (pinned upload of points and values,
+    the graph-replayed forward, the download of the image), L2 flushed before
+    each step.  The pieces are timed separately from the e2e number above
+    (which runs them as one captured graph through gmi_forward_host)."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    dP = torch.empty(hP.shape, dtype=hP.dtype, device=dev)
+    dV = torch.empty(hV.shape, dtype=hV.dtype, device=dev)
+    dO = torch.empty((im.H, im.W, im.C), dtype=torch.float32, device=dev)
+
+    def once(ev=None):
+        if ev:
+            ev[0].record(stream)
+        dP.copy_(hP, non_blocking=True)
+        dV.copy_(hV, non_blocking=True)
+        if ev:
+            ev[1].record(stream)
+        gmi.interpolate(dP, dV, im.sigma, im.H, im.W, out=dO, graph=True)
+        if ev:
+            ev[2].record(stream)
+        hO.copy_(dO, non_blocking=True)
+        if ev:
+            ev[3].record(stream)
+    for _ in range(3):
+        once()
+    torch.cuda.synchronize()
+    acc = [0.0, 0.0, 0.0]
+    for _ in range(steps):
+        flush.zero_()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        once(ev)
+        torch.cuda.synchronize()
+        for i in range(3):
+            acc[i] += ev[i].elapsed_time(ev[i + 1])
+    up, comp, down = (a / steps for a in acc)
+    return {"upload_ms": up, "compute_ms": comp, "download_ms": down, "sum_ms": up + comp + down,
+            "upload_gbs": (hP.numel() + hV.numel()) * 4 / (up * 1e-3) / 1e9,
+            "download_gbs": hO.numel() * 4 / (down * 1e-3) / 1e9}
+
+
 def bench_batched(dev, steps, warmup, flush, stream, autotune=True):
     """64 uneven clustered images (sides log-uniform in [128, 1024],
     N = 0.25 H W, sigma U[0.5, 2]): one batched graph launch per step versus
@@ -369,7 +454,24 @@ def bench_batched(dev, steps, warmup, flush, stream, autotune=True):
     for _ in range(max(3, warmup)):
         plan.forward(dimgs, use_graph=True)
     torch.cuda.synchronize()
-    tb = timed_steps(lambda: plan.forward(dimgs, use_graph=True), steps, flush, stream, queued=True)
+    qinfo = {}
+    tb = timed_steps(lambda: plan.forward(dimgs, use_graph=True), steps, flush, stream, queued=True, info=qinfo)
+    # per-stage times of the same batched forward (events around each stage,
+    # no graph), for the near kernel's roofline
+    from paper_2012_13257_b300 import _lib
+    L = _lib.load()
+    L.gmi_profile_enable(1)
+    L.gmi_profile_read(None, None, 1)
+    torch.cuda._sleep(int(steps * 2e-3 * SM_MAX_MHZ * 1e6))
+    for _ in range(steps):
+        flush.zero_()
+        plan.forward(dimgs, use_graph=False)
+    torch.cuda.synchronize()
+    st_ms = (ctypes.c_double * 4)()
+    st_n = (ctypes.c_int * 4)()
+    L.gmi_profile_read(st_ms, st_n, 1)
+    L.gmi_profile_enable(0)
+    stage = {name: (st_ms[i] / st_n[i] if st_n[i] else None) for i, name in enumerate(_lib.STAGES)}
 
     def plain():
         for d in dimgs:
@@ -383,10 +485,21 @@ def bench_batched(dev, steps, warmup, flush, stream, autotune=True):
     mb = px / (sum(tb) / steps * 1e-3) / 1e6
     mp = px / (sum(tp) / steps * 1e-3) / 1e6
     plan.close()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = sms * FP32_PER_SM_CLK / FP32_OPS_PER_PAIR * SM_MAX_MHZ * 1e6 / 1e9
+    near_ms = stage["near"]
+    achieved = pairs / (near_ms * 1e-3) / 1e9 if near_ms else None
     return {"value": mb, "unit": "Mpix/s", "ms_per_step": sum(tb) / steps, "plain_per_image_value": mp,
             "plain_ms_per_step": sum(tp) / steps, "speedup_vs_plain": mb / mp, "images": len(imgs),
-            "pixels": px, "points": int(sum(im.N for im in imgs)),
+            "pixels": px, "points": int(sum(im.N for im in imgs)), "queue_ok": qinfo.get("queue_ok"),
             "pairs_est": pairs, "pair_rate_gpair_s": pairs / (sum(tb) / steps * 1e-3) / 1e9,
+            "stage_ms": stage,
+            "roofline": {"bound": "alu", "kernel": "near gather (batched)", "launch_ms": near_ms,
+                         "pairs_per_launch": pairs, "achieved": achieved, "peak": peak, "unit": "Gpair/s",
+                         "frac": achieved / peak if achieved else None,
+                         "frac_step": pairs / (sum(tb) / steps * 1e-3) / 1e9 / peak,
+                         "peak_basis": "FP32 pipe at %.0f MHz, %d FP32 ops per algorithmic pair" %
+                                       (SM_MAX_MHZ, FP32_OPS_PER_PAIR)},
             "autotune": {"variant": variant, "buckets": len(rep), "tune_s": tune_s, "on": bool(autotune)},
             "workload": "64 images, sides log-uniform [128,1024], N=0.25HW clustered (8 clusters), "
                         "sigma U[0.5,2], RGB f32; one CUDA-graph batched launch per step vs 64 plain launches"}
@@ -843,7 +956,7 @@ def main():
     torch.cuda.synchronize()
     clocks.start()
     time.sleep(0.3)
-    prequeue(args.steps + 1)
+    spin = prequeue(args.steps + 1)
     flush.zero_()
     step()   # one more warm-up step in the queue, so no timed step starts the queued run
     for k in range(args.steps):
@@ -851,7 +964,20 @@ def main():
         starts[k].record(stream)
         step()
         ends[k].record(stream)
+    queue_ok = queued_in_time(spin)
     torch.cuda.synchronize()
+    if not queue_ok:
+        # the host fell behind the spin: once more, with a spin four times as long
+        spin = prequeue(args.steps + 1, 1.6e-3)
+        flush.zero_()
+        step()
+        for k in range(args.steps):
+            flush.zero_()
+            starts[k].record(stream)
+            step()
+            ends[k].record(stream)
+        queue_ok = queued_in_time(spin)
+        torch.cuda.synchronize()
     clk = clocks.stop()
     D.barrier()
     ms_steps = [s.elapsed_time(e) for s, e in zip(starts, ends)]
@@ -903,6 +1029,7 @@ def main():
            "d2h_bytes_per_step": int(hO.numel() * 4),
            "ms_per_step": e_total / args.steps}
     e2e_pipe = e2e_pipelined(gmi, im, hP, hV, args.steps, D, world)
+    e2e["breakdown"] = e2e_breakdown(gmi, im, hP, hV, hO, args.steps, flush, stream)
 
     # ---- roofline of the dominant kernel (near-field gather), timed live above
     props = torch.cuda.get_device_properties(dev)
@@ -919,7 +1046,7 @@ def main():
     roof = {"bound": "alu", "achieved": achieved, "peak": peak_gpair, "unit": "Gpair/s",
             "frac": (achieved / peak_gpair) if achieved else None,
             "traffic": near_kernel_traffic(),
-            "kernel": "near_kernel<4,4,3,exact>", "launch_ms": near_ms, "pairs_per_launch": pairs,
+            "kernel": "near_staged_kernel<4,4,3,exact>", "launch_ms": near_ms, "pairs_per_launch": pairs,
             "peak_basis": "FP32 pipe: %d SMs x %d FMA/clk / %d FP32 ops per algorithmic pair x %.0f MHz "
                           "(SM clock sampled during the timed steps); the SFU allows %.0f Gpair/s "
                           "(%d ex2/clk, one per pair); per-clock rates from the unit counts, checked by "
@@ -938,8 +1065,9 @@ def main():
                        "l2": "flushed between steps (256 MB write), not timed"},
             "roofline": roof, "e2e": e2e, "gpu_launches": LAUNCHES_PER_FORWARD * args.steps, "clocks": clk,
             "stage_ms": stages, "plain_launch": plain, "e2e_pipelined": e2e_pipe,
-            "step_ms": step_stats(ms_steps)}
+            "step_ms": step_stats(ms_steps), "queue_ok": queue_ok}
     if rank == 0 and not args.no_extras:
+        extras = {}
         for name, fn in (("batched", lambda: bench_batched(dev, args.steps, args.warmup, flush, stream)),
                          ("fwd_bwd", lambda: bench_fwd_bwd(dev, args.steps, args.warmup, flush, stream)),
                          ("serving", lambda: bench_serving(dev)),
@@ -948,12 +1076,28 @@ def main():
                          ("per_point_sigma", lambda: bench_per_point_sigma(dev, args.steps, args.warmup, flush,
                                                                            stream))):
             try:
-                line[name] = fn()
+                extras[name] = fn()
             except Exception as e:   # a failed extra must not hide the headline
-                line[name] = {"error": "%s: %s" % (type(e).__name__, e)}
+                extras[name] = {"error": "%s: %s" % (type(e).__name__, e)}
+        # the long objects first (with the full details of the metric's own
+        # workloads); the metric's batched, served and fwd+bwd figures close
+        # the line in a compact form
+        for name in ("per_point_sigma", "reconstruction", "point_optimization"):
+            line[name] = extras[name]
+        line["details"] = {k: extras[k] for k in ("batched", "serving", "fwd_bwd")}
     D.barrier()
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(im)
+    if rank == 0 and not args.no_extras:
+        line["batched"] = summary(extras["batched"], ["value", "plain_per_image_value", "speedup_vs_plain",
+                                                      "ms_per_step", "queue_ok"],
+                                  roofline=["frac", "frac_step", "achieved", "launch_ms", "pairs_per_launch"])
+        line["serving"] = summary(extras["serving"], ["p50_ms", "p99_ms", "plain_p50_ms", "plain_p99_ms", "value",
+                                                      "plain_value", "launches", "max_in_flight"],
+                                  saturated=["value", "plain_value", "speedup_vs_plain"],
+                                  device_resident=["p50_ms", "p99_ms", "value"])
+        line["fwd_bwd"] = summary(extras["fwd_bwd"], ["value", "ms_per_step", "list_batched_autograd_value",
+                                                      "per_image_autograd_value", "backward_ms"])
     if rank == 0:
         print(json.dumps(line), flush=True)
     D.close()
