@@ -118,7 +118,7 @@ long long sat_entries(const ImageGeom& g) { return (long long)(g.nby + 1) * (lon
 long long sat_jobs(const ImageGeom& g) { return (g.nbx + 1 + 31) / 32; }
 
 WsLayout ws_layout(long long n_total, long long nb_total, long long mt_total, long long wt_total,
-                   long long sat_entries, size_t slot_bytes, long long extra_bytes) {
+                   long long sat_entries, size_t slot_bytes, long long extra_bytes, bool tile_plans) {
   WsLayout L;
   size_t o = 0;
   L.cap_items = (unsigned)std::min<long long>(wt_total * kSplitMax, 0x7fffffffLL);
@@ -141,6 +141,8 @@ WsLayout ws_layout(long long n_total, long long nb_total, long long mt_total, lo
   L.slots = o;  o = align_up(o + slot_bytes * (size_t)L.cap_slots, 256);
   L.ubound = o; o = align_up(o + sizeof(float) * 32u * (size_t)(wt_total > 0 ? wt_total : 1), 256);
   L.sat = o;    o = align_up(o + sizeof(unsigned) * (size_t)(sat_entries > 0 ? sat_entries : 1), 256);
+  L.has_tplan = tile_plans;
+  L.tplan = o;  o = align_up(o + (tile_plans ? sizeof(TilePlanRec) * (size_t)(wt_total > 0 ? wt_total : 1) : 0), 256);
   L.extra = o;  o = align_up(o + (size_t)extra_bytes, 256);
   L.total = o;
   return L;
@@ -164,6 +166,7 @@ DevWork bind_ws(void* ws, const WsLayout& L) {
   w.perm = (unsigned*)(b + L.perm);
   w.spp = (float4*)(b + L.spp);
   w.sat = (unsigned*)(b + L.sat);
+  w.tplan = L.has_tplan ? (TilePlanRec*)(b + L.tplan) : nullptr;
   w.pplane = nullptr;
   w.fbflag = nullptr;
   w.fbq = nullptr;
@@ -291,7 +294,7 @@ static gmi_status forward_impl(const float* points, const float* values, const f
   const long long mt = (long long)g.mtx * g.mty;
   const long long wt = (long long)g.wtx * g.wty;
   const WsLayout L =
-      ws_layout(N, nb, mt, wt, sat_entries(g), slot_bytes_for(mth, mtw, C), bwd_extra_bytes(N, C, H, W));
+      ws_layout(N, nb, mt, wt, sat_entries(g), slot_bytes_for(mth, mtw, C), bwd_extra_bytes(N, C, H, W), true);
   if (!workspace || ((uintptr_t)workspace & 255u) != 0 || ws_bytes < (fwd_share ? L.extra : L.total))
     return GMI_ERR_WORKSPACE;
 
@@ -319,6 +322,7 @@ static gmi_status forward_impl(const float* points, const float* values, const f
   a.gather = p->gather;
   const bool trunc = p->mode == GMI_MODE_TRUNCATED;
   const int ppk = g.pp_kind == 3 ? 2 : (g.pp_kind ? 1 : 0);
+  if (!uses_staged_gather(p->gather, ppk)) a.w.tplan = nullptr;   // the plan writes none
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   if ((p->flags & GMI_FLAG_GRAPH) && !profile_on() && cudaStreamIsCapturing(s, &cap) == cudaSuccess &&
       cap == cudaStreamCaptureStatusNone) {
@@ -376,7 +380,7 @@ gmi_status forward_share_bytes(int64_t N, int C, int H, int W, const gmi_params*
   const long long nb = (long long)g.nbx * g.nby;
   const long long mt = (long long)g.mtx * g.mty;
   const long long wt = (long long)g.wtx * g.wty;
-  *bytes = ws_layout(N, nb, mt, wt, sat_entries(g), slot_bytes_for(mth, mtw, C), 0).extra;
+  *bytes = ws_layout(N, nb, mt, wt, sat_entries(g), slot_bytes_for(mth, mtw, C), 0, true).extra;
   return GMI_OK;
 }
 
@@ -432,7 +436,7 @@ gmi_status gmi_workspace_size(int64_t N, int C, int H, int W, const gmi_params* 
   const long long nb = (long long)g.nbx * g.nby;
   const long long mt = (long long)g.mtx * g.mty;
   const long long wt = (long long)g.wtx * g.wty;
-  *bytes = ws_layout(N, nb, mt, wt, sat_entries(g), slot_bytes_for(mth, mtw, C), bwd_extra_bytes(N, C, H, W)).total;
+  *bytes = ws_layout(N, nb, mt, wt, sat_entries(g), slot_bytes_for(mth, mtw, C), bwd_extra_bytes(N, C, H, W), true).total;
   return GMI_OK;
 }
 
@@ -449,7 +453,7 @@ gmi_status gmi_workspace_layout(int64_t N, int C, int H, int W, const gmi_params
   const long long nb = (long long)g.nbx * g.nby;
   const long long mt = (long long)g.mtx * g.mty;
   const long long wt = (long long)g.wtx * g.wty;
-  const WsLayout L = ws_layout(N, nb, mt, wt, sat_entries(g), slot_bytes_for(mth, mtw, C), bwd_extra_bytes(N, C, H, W));
+  const WsLayout L = ws_layout(N, nb, mt, wt, sat_entries(g), slot_bytes_for(mth, mtw, C), bwd_extra_bytes(N, C, H, W), true);
   out->off = L.off;
   out->oob = L.oob;
   out->sxy = L.sxy;

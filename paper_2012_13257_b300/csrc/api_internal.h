@@ -11,7 +11,8 @@ namespace gmi {
 // Byte offsets of the regions of a workspace.
 struct WsLayout {
   size_t status, off, oob, tile_done, zero_end, rank, sxy, sval, perm, spp, partials, farq, items, slots, ubound, sat,
-      extra, total;
+      tplan, extra, total;
+  bool has_tplan;
   unsigned cap_items, cap_slots;
 };
 
@@ -25,7 +26,7 @@ void set_vec_ok(ImageGeom& g);
 bool aligned16(const void* p);
 size_t slot_bytes_for(int mth, int mtw, int C);
 WsLayout ws_layout(long long n_total, long long nb_total, long long mt_total, long long wt_total,
-                   long long sat_entries, size_t slot_bytes, long long extra_bytes);
+                   long long sat_entries, size_t slot_bytes, long long extra_bytes, bool tile_plans = false);
 // Summed-area table of one image's bins: entries and 32-column build jobs.
 long long sat_entries(const ImageGeom& g);
 long long sat_jobs(const ImageGeom& g);

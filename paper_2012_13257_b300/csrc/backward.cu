@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(256) bwd_prep_kernel(KArgs a_in, BwdArgs b) {
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long gp = (long long)blockIdx.x * blockDim.x + threadIdx.x; gp < a.px_total; gp += stride) {
     const int img = find_image<3>(a, gp);
-    const ImageGeom& g = *geom_ptr(a, img);
+    const ImageGeom g = a.w.table ? a.w.table[img] : a.g0;   // a copy: no address of a local struct
     const BwdImage bi = bwd_image(b, img);
     const long long px = gp - g.px_base;
     if (px == 0 && bi.gsig) *bi.gsig = 0.0f;   // accumulated by the later kernels
@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(256) bwd_point_kernel(KArgs a_in, BwdArgs b, f
     float Dp = 0.0f;
     if (valid) {
       img = find_image<2>(a, i);
-      const ImageGeom& g = *geom_ptr(a, img);
+      const ImageGeom g = a.w.table ? a.w.table[img] : a.g0;   // a copy: no address of a local struct
       const BwdImage bi = bwd_image(b, img);
       const float4* __restrict__ plane = a.w.pplane + g.px_base;
       const float4* __restrict__ plane2 = a.w.pplane + a.px_total + g.px_base;
@@ -561,7 +561,7 @@ static gmi_status backward_impl(const float* points, const float* values, const 
   const long long mt = (long long)g.mtx * g.mty;
   const long long wt = (long long)g.wtx * g.wty;
   const WsLayout L =
-      ws_layout(N, nb, mt, wt, sat_entries(g), slot_bytes_for(mth, mtw, C), bwd_extra_bytes(N, C, H, W));
+      ws_layout(N, nb, mt, wt, sat_entries(g), slot_bytes_for(mth, mtw, C), bwd_extra_bytes(N, C, H, W), true);
   if (!workspace || ((uintptr_t)workspace & 255u) != 0 || ws_bytes < L.total) return GMI_ERR_WORKSPACE;
   if (grad_points && cudaMemsetAsync(grad_points, 0, sizeof(float) * 2 * (size_t)N, s) != cudaSuccess) return GMI_ERR_CUDA;
   if (grad_values && cudaMemsetAsync(grad_values, 0, sizeof(float) * (size_t)C * (size_t)N, s) != cudaSuccess) return GMI_ERR_CUDA;

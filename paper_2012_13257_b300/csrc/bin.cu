@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(256) bin_count_kernel(KArgs a_in) {
   unsigned bad = 0, bad_sigma = 0;
   for (long long ch = blockIdx.x; ch < a.ch_total; ch += gridDim.x) {
     const int img = find_image<0>(a, ch);
-    const ImageGeom& g = *geom_ptr(a, img);
+    const ImageGeom g = a.w.table ? a.w.table[img] : a.g0;   // a copy: no address of a local struct
     const long long i = (ch - g.ch_base) * kChunk + threadIdx.x;
     if (i < g.n) {
       float2 p = reinterpret_cast<const float2*>(g.points)[i];

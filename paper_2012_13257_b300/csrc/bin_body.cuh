@@ -19,7 +19,7 @@ static __device__ __forceinline__ void point_bin(const ImageGeom& g, float x, fl
 static __device__ __forceinline__ void bin_scatter_body(const KArgs& a, int nblocks, int block) {
   for (long long ch = block; ch < a.ch_total; ch += nblocks) {
     const int img = find_image<0>(a, ch);
-    const ImageGeom& g = *geom_ptr(a, img);
+    const ImageGeom g = a.w.table ? a.w.table[img] : a.g0;   // a copy: no address of a local struct
     const long long i = (ch - g.ch_base) * kChunk + threadIdx.x;
     if (i < g.n) {
       float2 p = reinterpret_cast<const float2*>(g.points)[i];

@@ -39,6 +39,22 @@ enum : int {
   kStatusWords = 64,
 };
 
+constexpr int kPassRows = 16;     // most window bin rows the staged gather stages at once
+
+// A warp tile's staging plan, written by the plan kernel for the staged
+// gather's first work item of the tile (single-image calls):
+//   hdr    (window rows | valid << 31, staged records, first window bin row, 0);
+//          valid = 0: the item sets itself up (split tile, window too large)
+//   rowc   per window row r: (first record copied (even), records | staged index << 16)
+//   lane   per lane: non-empty segments | active << 31
+//   seg    per segment k and lane: staged start | end << 16
+struct TilePlanRec {
+  uint4 hdr;
+  uint2 rowc[kPassRows];
+  unsigned lane[32];
+  unsigned seg[kPassRows][32];
+};
+
 // Per-image geometry and constants, computed on the host.
 struct ImageGeom {
   const float* points;   // [n,2] (x, y)
@@ -101,6 +117,8 @@ struct DevWork {
   unsigned* sat;         // per image [(nby+1) x (nbx+1)]: points in bins [0,by) x [0,bx), built
                          //   by the near kernel when the far-field queue is not empty
   const ImageGeom* table;// device descriptor table (batched) or null (single image)
+  TilePlanRec* tplan;    // [wt_total] staging plans of the staged gather (written by
+                         //   the plan kernel), or null: the gather sets up every item itself
 };
 
 struct KArgs {
@@ -151,9 +169,6 @@ constexpr int kSigParts = 4096;         // sigma-gradient partials (one per back
 constexpr int kSplitMax = 64;           // most work items one warp tile is split into
 constexpr unsigned kSplitTarget = 160;  // candidates per thread per work item
 
-__device__ __forceinline__ const ImageGeom* geom_ptr(const KArgs& a, int img) {
-  return a.w.table ? a.w.table + img : &a.g0;
-}
 
 // Largest image index whose base (Field 0: chunks, 1: warp tiles, 2: points,
 // 3: pixels, 4: summed-area-table column jobs) is <= idx.

@@ -173,6 +173,83 @@ __device__ float near_bound(const KArgs& a, const ImageGeom& g, int x0, int y0, 
   return INFINITY;
 }
 
+// The staged gather's plan for warp tile wt (its first work item): the
+// window bin rows, each row's union segment over the warp's threads (the
+// warp tile's rectangle with the largest radius, a superset of every
+// thread's segment), its place in the warp's staging buffer, and each
+// thread's non-empty segments as indices of the staged copy.  The gather
+// then issues its bulk copies after one round of loads.  A split tile, or a
+// window larger than the buffer, is marked invalid (the gather sets such
+// items up itself).  `act`: the thread's micro-tile takes part (in the image,
+// not far field); R2 its squared radius.
+template <int MTH, int MTW>
+__device__ void tile_stage_plan(const KArgs& a, const ImageGeom& g, long long wt, bool act, float R2, int x0, int y0,
+                                int nx, int ny, unsigned S) {
+  constexpr int CAP = StageCap<MTH, MTW>::value;
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  TilePlanRec* rec = a.w.tplan + wt;
+  LaneWin w;
+  int my_lo = INT_MAX, my_hi = INT_MIN;
+  if (act) {
+    w = lane_window(g, x0, y0, nx, ny, R2);
+    my_lo = w.by_lo;
+    my_hi = w.by_hi;
+  }
+  const int wy_lo = warp_min(my_lo), wy_hi = warp_max(my_hi);
+  const int rows = wy_hi >= wy_lo ? wy_hi - wy_lo + 1 : 0;
+  bool valid = S == 1 && rows > 0 && rows <= kPassRows;
+  unsigned total = 0;
+  if (valid) {
+    const float R2w = warp_maxf(act ? R2 : 0.0f);
+    const unsigned lt = (unsigned)(wt - g.wt_base);
+    const int X0 = (int)(lt % (unsigned)g.wtx) * 8 * MTW, Y0 = (int)(lt / (unsigned)g.wtx) * 4 * MTH;
+    const LaneWin ww = lane_window(g, X0, Y0, min(8 * MTW, g.W - X0), min(4 * MTH, g.H - Y0), R2w);
+    unsigned S0 = 0u, E0 = 0u;
+    if (lane < rows) {
+      int bxw_lo, bxw_hi;
+      float hxw;
+      row_bins(g, ww, wy_lo + lane, bxw_lo, bxw_hi, hxw);
+      const long long rowb = g.bin_base + (long long)(wy_lo + lane) * g.nbx;
+      S0 = __ldg(&a.w.off[rowb + bxw_lo]);
+      E0 = __ldg(&a.w.off[rowb + bxw_hi + 1]);
+    }
+    unsigned segs[kPassRows], sege[kPassRows];
+#pragma unroll
+    for (int k = 0; k < kPassRows; ++k) {
+      segs[k] = sege[k] = 0u;
+      if (act && w.by_lo + k <= w.by_hi) row_segment(a, g, w, w.by_lo + k, segs[k], sege[k]);
+    }
+    // records [S0, E0) of row r widened to even indices (16-byte boundaries
+    // for the position copies), placed one after the other
+    const unsigned need = E0 > S0 ? ((E0 + 1u) & ~1u) - (S0 & ~1u) : 0u;
+    unsigned incl = min(need, (unsigned)CAP + 1u);
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned u = __shfl_up_sync(full, incl, o);
+      if (lane >= o) incl += u;
+    }
+    total = __shfl_sync(full, incl, 31);
+    valid = total <= (unsigned)CAP;
+    if (valid) {
+      const unsigned abase = incl - need;
+      const unsigned B = abase + (S0 & 1u);   // staged index of record S0
+      unsigned nseg = 0;
+#pragma unroll
+      for (int k = 0; k < kPassRows; ++k) {
+        const bool v = act && w.by_lo + k <= w.by_hi;
+        const int r = v ? w.by_lo + k - wy_lo : 0;
+        const unsigned Sr = __shfl_sync(full, S0, r), Br = __shfl_sync(full, B, r);
+        const unsigned i0 = Br + (segs[k] - Sr), i1 = i0 + (sege[k] - segs[k]);
+        if (v && i0 < i1) rec->seg[nseg++][lane] = i0 | (i1 << 16);
+      }
+      rec->lane[lane] = nseg | (act ? 0x80000000u : 0u);
+      if (lane < rows) rec->rowc[lane] = make_uint2(S0 & ~1u, need | (abase << 16));
+    }
+  }
+  if (lane == 0) rec->hdr = make_uint4((unsigned)rows | (valid ? 0x80000000u : 0u), total, (unsigned)wy_lo, 0u);
+}
+
 // Plan: one warp per warp tile.  Each thread bounds the nearest squared
 // distance U of its micro-tile once (stored for the gather), queues far-field
 // micro-tiles for the far kernel, and counts its candidates within
@@ -242,6 +319,7 @@ __device__ void near_plan_body(const KArgs& a, int trunc, long long wt) {
       for (int k = 0; k < na / 4; ++k) z[k] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
   }
+  if (a.w.tplan) tile_stage_plan<MTH, MTW>(a, g, wt, active && !far, U + g.r2k, x0, y0, nx, ny, S);
   // the tile's first item sits at index wt (so a near-kernel warp can start on
   // warp tile t without reading the queue first); its other splits follow
   // all first items

@@ -36,21 +36,12 @@
 
 namespace gmi {
 
-constexpr int kPassRows = 16;     // window bin rows per pass (height of the thread table)
 constexpr int kStageWarps = 4;    // warps per block
 // A barrier wait polls at most kWaitPolls times; each poll may suspend the
 // thread for up to kWaitHintNs until the phase completes (so a wait gives up
 // after about a second, and a waiting warp takes no issue slots meanwhile).
 constexpr unsigned kWaitPolls = 10000u;
 constexpr unsigned kWaitHintNs = 100000u;
-
-// Candidates one warp can stage at once, by micro-tile shape: the window of a
-// 32 x 16 px warp tile (4 x 4 micro-tiles) at one point per bin and a 6.4 px
-// radius is about 300 records in 14 bin rows.
-template <int MTH, int MTW>
-struct StageCap {
-  static constexpr int value = MTH * MTW >= 16 ? 352 : 224;
-};
 
 // One warp's shared-memory area.
 template <int CAP>
@@ -127,24 +118,6 @@ __device__ __forceinline__ void bulk_copy(void* dst, const void* src, unsigned b
 // Orders this thread's earlier shared-memory accesses before later
 // async-proxy (bulk copy) writes to the same memory.
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-__device__ __forceinline__ int warp_min(int v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
-
-__device__ __forceinline__ float warp_maxf(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
-
-__device__ __forceinline__ int warp_max(int v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
 
 // One candidate point (position p, colour cv) into every pixel of the
 // thread's micro-tile (shared sigma): separable weights gx[j] gy[r] with
@@ -370,7 +343,60 @@ __global__ void __launch_bounds__(32 * kStageWarps, StagedOcc<MTH, MTW, C>::valu
     // (num_1, num_2), plus num_{C-1} alone when C is even.
     float2 accp[MTH * MTW * NP];
     float accs[MTH * MTW * ODD + 1 - ODD];
-    {
+    // A warp tile's first item with a valid staging plan (single images):
+    // the plan, the lane's segments and the copy ranges in one round of
+    // loads, then the bulk copies.
+    bool planned = false;
+    if (a.w.tplan && (long long)t < a.wt_total) {
+      const TilePlanRec* rec = a.w.tplan + t;
+      const uint4 hdr = __ldcg(&rec->hdr);
+      const unsigned lw = __ldcg(&rec->lane[lane]);
+      const uint2 rc = lane < kPassRows ? __ldcg(&rec->rowc[lane]) : make_uint2(0u, 0u);
+      unsigned sg[kPassRows];
+#pragma unroll
+      for (int k = 0; k < kPassRows; ++k) sg[k] = __ldcg(&rec->seg[k][lane]);
+      if (hdr.x >> 31) {
+        planned = staged = true;
+        const int rows = (int)(hdr.x & 0xffffu);
+        const unsigned total = hdr.y;
+        const ImageGeom& g = a.g0;   // tile plans exist for single images only
+        int x0, y0, nx, ny;
+        lane_tile<MTH, MTW>(g, t, lane, x0, y0, nx, ny);
+        sk = g.sk;
+        xq0 = (float)x0 + 0.5f;
+        yq0 = (float)y0 + 0.5f;
+        neg_thr = -g.kappa * g.r2k;
+        nseg = lw & 0xffffu;
+        if (lane == 0) sb.item = make_uint4(t, 1u << 16, 0xffffffffu, 0u);
+        sb.act[lane] = lw >> 31;
+#pragma unroll
+        for (int k = 0; k < kPassRows; ++k)
+          if ((unsigned)k < nseg) sb.tab[lane][k] = sg[k];
+        // every lane is past its reads of the previous item's buffer
+        fence_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive_expect(&sb.bar, total * (unsigned)(sizeof(float2) + sizeof(float4)));
+          nt = claim_next(a, n_items, n_warps);
+        }
+        __syncwarp();
+        const unsigned need = rc.y & 0xffffu, abase = rc.y >> 16;
+        if (lane < rows && need) {
+          bulk_copy(&sb.pos[abase], a.w.sxy + rc.x, need * (unsigned)sizeof(float2), &sb.bar);
+          bulk_copy(&sb.col[abase], a.w.sval + rc.x, need * (unsigned)sizeof(float4), &sb.bar);
+        }
+#pragma unroll
+        for (int k = 0; k < MTH * MTW * NP; ++k) accp[k] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < MTH * MTW * ODD + 1 - ODD; ++k) accs[k] = 0.0f;
+        if (total > 0u) {
+          const bool ok = mbar_wait(&sb.bar, parity);
+          parity ^= 1u;
+          if (__any_sync(full, !ok)) stalled = true;
+        }
+      }
+    }
+    if (!planned) {
       const ItemGeo it = item_geo<MTH, MTW, TRUNC>(a, t, lane);
       const ImageGeom g = a.w.table ? a.w.table[it.img] : a.g0;   // a copy: no address of a local struct
       // what the epilogue needs, kept in shared memory rather than live

@@ -6,7 +6,35 @@
 
 #include "common.cuh"
 
+#include <climits>
+
 namespace gmi {
+
+// Candidates one warp of the staged gather can stage at once, by micro-tile
+// shape: the window of a 32 x 16 px warp tile (4 x 4 micro-tiles) at one
+// point per bin and a 6.4 px radius is about 300 records in 14 bin rows.
+template <int MTH, int MTW>
+struct StageCap {
+  static constexpr int value = MTH * MTW >= 16 ? 352 : 224;
+};
+
+__device__ __forceinline__ int warp_min(int v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+__device__ __forceinline__ int warp_max(int v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+__device__ __forceinline__ float warp_maxf(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
 
 // Candidate window of one thread: pixel-centre rectangle and radius.
 struct LaneWin {
