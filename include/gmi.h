@@ -368,12 +368,13 @@ gmi_status gmi_autotune(const float* points, const float* values, int64_t N, int
  *     (gmi_workspace_size less the backward pass's planes); problems whose
  *     forward part exceeds GMI_NOALLOC_SCRATCH_BYTES are rejected with
  *     GMI_ERR_CAPACITY before anything is enqueued.  A 768x768 output from
- *     147,456 points with C = 3 needs about 18.6 MiB and fits; a 1024x1024
- *     output from 262,144 points needs about 33 MiB and does not: use
+ *     147,456 points with C = 3 needs about 21 MiB and fits; a 1024x1024
+ *     output from 262,144 points needs about 37 MiB and does not: use
  *     gmi_forward beyond the limit.
- *   - The first call on each device looks up the device address of the array
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.
+ *   - Every call looks up the device address of the array on the current
+ *     device (cudaGetSymbolAddress, which allocates nothing); the first call
+ *     on a device loads the library's device code there, so make that first
+ *     call before any stream capture.
  *   - Every call on a device shares the one array, which keeps the previous
  *     call's contents (the call clears what must start at zero itself).
  *     Calls that overlap on the GPU race on it: serialise them, e.g. issue

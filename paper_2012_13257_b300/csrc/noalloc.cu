@@ -4,8 +4,6 @@
 // workspace).  Its scratch is one statically sized device array compiled into
 // this library; the pipeline it runs is gmi_forward's, unchanged, in the
 // forward's share of the workspace layout (the backward's region left out).
-#include <mutex>
-
 #include "api_internal.h"
 
 namespace {
@@ -14,26 +12,23 @@ constexpr size_t kScratchBytes = GMI_NOALLOC_SCRATCH_BYTES;
 constexpr int kMaxDevices = 64;
 
 // The scratch array.  Its name is only a host-side stand-in in host code; the
-// device address is looked up below, once per device.
+// device address is looked up below.
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
-std::mutex g_mu;
-void* g_addr[kMaxDevices];   // device address of g_scratch, per device
-
-// Device address of the scratch array on the current device (looked up on
-// the first call for that device, with that device current).
+// Device address of the scratch array on the current device, looked up on
+// every call with that device current: the lookup allocates nothing and is
+// cheap, and an address kept from an earlier call could be stale after the
+// device's context was reset and the module loaded again.  The first call on a
+// device loads the module's symbols, so it should come before any stream
+// capture.
 gmi_status scratch_address(void** out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) return GMI_ERR_CUDA;
   if (dev < 0 || dev >= kMaxDevices) return GMI_ERR_UNSUPPORTED;
-  std::lock_guard<std::mutex> lk(g_mu);
-  if (g_addr[dev] == nullptr) {
-    void* a = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&a, g_scratch);
-    if (e != cudaSuccess || a == nullptr) return GMI_ERR_CUDA;
-    g_addr[dev] = a;
-  }
-  *out = g_addr[dev];
+  void* a = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&a, g_scratch);
+  if (e != cudaSuccess || a == nullptr) return GMI_ERR_CUDA;
+  *out = a;
   return GMI_OK;
 }
 
