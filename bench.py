@@ -761,11 +761,17 @@ def bench_serving(dev, n_requests=10000, rate=2000.0, n_templates=128):
     hV = [torch.as_tensor(t.values).pin_memory() for t in tmpl]
     hO = [torch.empty((t.H, t.W, 3), dtype=torch.float32).pin_memory() for t in tmpl]
 
-    def run_server():
+    dP = dV = dO = None
+
+    def run_server(device=False):
         srv = gmi.Server(budget_bytes=40 << 30, max_batch_images=64, max_batch_pixels=1 << 25, n_streams=2)
+        if device:
+            submit = lambda j, t: srv.submit_device(dP[j], dV[j], t.sigma, t.H, t.W, dO[j])
+        else:
+            submit = lambda j, t: srv.submit(hP[j], hV[j], t.sigma, t.H, t.W, hO[j])
         # warm-up (graph capture for both slots)
         for j in range(4):
-            srv.wait(srv.submit(hP[j], hV[j], tmpl[j].sigma, tmpl[j].H, tmpl[j].W, hO[j]))
+            srv.wait(submit(j, tmpl[j]))
         sched, ids, sub = [], [], []
         lat = [0.0] * n_requests
         t0 = time.perf_counter()
@@ -790,11 +796,11 @@ def bench_serving(dev, n_requests=10000, rate=2000.0, n_templates=128):
             t = tmpl[j]
             sched.append(t_sched)
             sub.append(time.perf_counter())
-            ids.append(srv.submit(hP[j], hV[j], t.sigma, t.H, t.W, hO[j]))
+            ids.append(submit(j, t))
         done_ev.wait()
         th.join()
         wall = time.perf_counter() - t0
-        st = srv.stats()
+        st = srv.counters()
         srv.close()
         return lat, wall, st
 
@@ -858,15 +864,24 @@ def bench_serving(dev, n_requests=10000, rate=2000.0, n_templates=128):
     lat_s, wall_s, st = run_server()
     lat_p, wall_p = run_plain()
     sat = run_saturated(2000)
+    # the same stream with the payloads already on the device (no copies)
+    dP = [p.to(dev) for p in hP]
+    dV = [v.to(dev) for v in hV]
+    dO = [torch.empty((t.H, t.W, 3), dtype=torch.float32, device=dev) for t in tmpl]
+    lat_d, wall_d, st_d = run_server(device=True)
     q = lambda v, p: float(np.percentile(np.asarray(v) * 1e3, p))
     return {"p50_ms": q(lat_s, 50), "p99_ms": q(lat_s, 99), "value": px / wall_s / 1e6, "unit": "Mpix/s",
-            "wall_s": wall_s, "launches": st["launches"], "requests": n_requests,
+            "wall_s": wall_s, "launches": st["launches"], "max_in_flight": st["max_in_flight"],
+            "requests": n_requests,
+            "device_resident": {"p50_ms": q(lat_d, 50), "p99_ms": q(lat_d, 99), "value": px / wall_d / 1e6,
+                                "launches": st_d["launches"], "max_in_flight": st_d["max_in_flight"]},
             "plain_p50_ms": q(lat_p, 50), "plain_p99_ms": q(lat_p, 99), "plain_value": px / wall_p / 1e6,
             "plain_wall_s": wall_p, "offered_req_s": rate, "saturated": sat,
             "workload": "%d requests, Poisson %.0f req/s, sides log-uniform [64,2048], N=U[0.1,1]HW, "
                         "uniform/clustered, sigma U[0.5,2]; payloads cycle %d pinned templates; 40 GB budget, "
-                        "2 batch slots; latency from scheduled arrival; 'saturated': the first 2000 requests "
-                        "offered at once, wall-clock throughput" % (n_requests, rate, n_templates)}
+                        "2 batch slots; latency from scheduled arrival; 'device_resident': the same stream with the "
+                        "payloads already on the device (gmi_server_submit_device, no copies); 'saturated': the "
+                        "first 2000 requests offered at once, wall-clock throughput" % (n_requests, rate, n_templates)}
 
 
 def run_reference(args, rank, world):

@@ -601,10 +601,49 @@ gmi_status gmi_server_wait(gmi_server* s, uint64_t id, int timeout_ms, double* l
 /* Non-blocking: GMI_OK if done, GMI_ERR_TIMEOUT if still pending. */
 gmi_status gmi_server_poll(gmi_server* s, uint64_t id);
 
+/*
+ * Submits one request whose buffers are DEVICE memory on the server's device
+ * (points [N,2] 8-byte aligned, values [N,C], image [H,W,C]).  Nothing is
+ * copied: the batched forward reads the inputs and writes the image in place,
+ * so the request takes none of the server's pool.  The buffers must stay
+ * valid, and the inputs unchanged, until the request completes.  Errors: as
+ * gmi_server_submit, and GMI_ERR_INVALID_ARG when a buffer is not device
+ * memory of the server's device.
+ */
+gmi_status gmi_server_submit_device(gmi_server* s, const float* points, const float* values,
+                                    int64_t N, int H, int W, float sigma, float* image,
+                                    uint64_t* id);
+
 /* Server counters: completed requests, batched launches, pixels served, and
  * the device bytes currently held by admitted requests. */
 gmi_status gmi_server_stats(gmi_server* s, uint64_t* completed, uint64_t* launches,
                             uint64_t* pixels, size_t* bytes_in_use);
+
+typedef struct {
+    uint64_t completed;      /* requests completed */
+    uint64_t launches;       /* batched launches queued */
+    uint64_t pixels;         /* output pixels served */
+    size_t bytes_in_use;     /* pool bytes held by admitted requests */
+    int in_flight;           /* batches queued on the GPU and not yet seen complete */
+    int max_in_flight;       /* the most that were at any one time */
+    uint64_t reserved[4];
+} gmi_server_counters;
+
+/* All counters at once (the in-flight figures show whether batches overlapped
+ * on the device). */
+gmi_status gmi_server_get_counters(gmi_server* s, gmi_server_counters* out);
+
+/*
+ * Per-request log: from now on every completed request appends one JSON line
+ * to the file at `path` (truncated first): id, device (1 for device buffers),
+ * N, H, W, batch (launch number), slot (stream slot), status, and the times in
+ * seconds since the server was created at which it was submitted, admitted
+ * (pool memory reserved and taken into a batch), launched (its batch queued on
+ * the GPU) and done (its batch's completion seen by the server, within ~20 us).
+ * NULL closes the log.  Errors: GMI_ERR_INVALID_ARG if the file cannot be
+ * opened.
+ */
+gmi_status gmi_server_set_log(gmi_server* s, const char* path);
 
 /* Drains pending requests, stops the threads and frees the pool. */
 gmi_status gmi_server_destroy(gmi_server* s);

@@ -719,6 +719,35 @@ class Server:
         self._keep[rid.value] = (points, values, out)
         return int(rid.value)
 
+    def submit_device(self, points, values, sigma: float, H: int, W: int, out) -> int:
+        """Submits a request whose tensors live on the server's CUDA device:
+        no copies, the image is written into ``out`` in place.  The tensors
+        must stay alive, and the inputs unchanged, until the request
+        completes."""
+        import torch
+        for t in (points, values, out):
+            if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous() and t.dtype == torch.float32):
+                raise ValueError("device requests take contiguous float32 CUDA tensors")
+        rid = ctypes.c_uint64(0)
+        n = int(points.shape[0])
+        _lib.check(_lib.load().gmi_server_submit_device(self._h, points.data_ptr() if n else None,
+                                                        values.data_ptr() if n else None, n, int(H), int(W),
+                                                        float(sigma), out.data_ptr(), ctypes.byref(rid)),
+                   "gmi_server_submit_device")
+        self._keep[rid.value] = (points, values, out)
+        return int(rid.value)
+
+    def counters(self):
+        c = _lib.ServerCounters()
+        _lib.check(_lib.load().gmi_server_get_counters(self._h, ctypes.byref(c)), "gmi_server_get_counters")
+        return {"completed": c.completed, "launches": c.launches, "pixels": c.pixels,
+                "bytes_in_use": c.bytes_in_use, "in_flight": c.in_flight, "max_in_flight": c.max_in_flight}
+
+    def set_log(self, path):
+        """One JSON line per completed request (submit, admit, launch and done
+        times in seconds since the server started) to ``path``; None stops."""
+        _lib.check(_lib.load().gmi_server_set_log(self._h, path.encode() if path else None), "gmi_server_set_log")
+
     def wait(self, rid: int, timeout_ms: int = -1) -> float:
         lat = ctypes.c_double(0.0)
         st = _lib.load().gmi_server_wait(self._h, int(rid), int(timeout_ms), ctypes.byref(lat))

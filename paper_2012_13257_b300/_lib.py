@@ -71,6 +71,12 @@ class ServerConfig(ctypes.Structure):
                 ("radius_sigmas", ctypes.c_float), ("mode", ctypes.c_int), ("reserved", ctypes.c_int)]
 
 
+class ServerCounters(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_uint64), ("launches", ctypes.c_uint64), ("pixels", ctypes.c_uint64),
+                ("bytes_in_use", ctypes.c_size_t), ("in_flight", ctypes.c_int), ("max_in_flight", ctypes.c_int),
+                ("reserved", ctypes.c_uint64 * 4)]
+
+
 # name -> (restype, argtypes), mirroring include/gmi.h
 _vp, _i64, _int, _f, _sz = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_float, ctypes.c_size_t
 _u64p = ctypes.POINTER(ctypes.c_uint64)
@@ -120,6 +126,9 @@ SIGNATURES = {
     "gmi_server_config_default": (_int, [ctypes.POINTER(ServerConfig)]),
     "gmi_server_create": (_int, [ctypes.POINTER(ServerConfig), ctypes.POINTER(_vp)]),
     "gmi_server_submit": (_int, [_vp, _vp, _vp, _i64, _int, _int, _f, _vp, _u64p]),
+    "gmi_server_submit_device": (_int, [_vp, _vp, _vp, _i64, _int, _int, _f, _vp, _u64p]),
+    "gmi_server_get_counters": (_int, [_vp, ctypes.POINTER(ServerCounters)]),
+    "gmi_server_set_log": (_int, [_vp, ctypes.c_char_p]),
     "gmi_server_wait": (_int, [_vp, ctypes.c_uint64, _int, ctypes.POINTER(ctypes.c_double)]),
     "gmi_server_poll": (_int, [_vp, ctypes.c_uint64]),
     "gmi_server_stats": (_int, [_vp, _u64p, _u64p, _u64p, ctypes.POINTER(_sz)]),

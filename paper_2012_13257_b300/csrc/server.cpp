@@ -7,10 +7,15 @@
 //                a free stream slot, downloads the images, records an event;
 //                up to n_streams batches are on the GPU at once, so requests
 //                arriving meanwhile form the next batch and overlap with it
-//   completer -> waits for batch events in launch order, stamps completion,
-//                frees device memory, wakes waiters
+//   completer -> polls the events of every batch in flight (a short batch on
+//                one stream slot completes before a long one launched earlier
+//                on another), stamps each batch's completion when its event
+//                is seen, frees device memory, wakes waiters, and appends one
+//                JSON line per request to the log when one is set
 // One device allocation of budget_bytes holds the batch plans' workspaces and
-// every admitted request's points, values and image.
+// every admitted request's points, values and image.  Requests submitted with
+// device buffers are read and written in place and take none of the pool.
+#include <stdio.h>
 #include <string.h>
 
 #include <chrono>
@@ -82,7 +87,10 @@ struct Request {
   int64_t N;
   int H, W;
   float sigma;
-  Clock::time_point t_submit, t_done;
+  bool on_device = false;        // buffers are device memory (no copies, no pool region)
+  Clock::time_point t_submit, t_admit, t_launch, t_done;
+  uint64_t batch = 0;
+  int slot = -1;
   size_t off = 0, bytes = 0;     // device region (points | values | image)
   bool done = false;
   gmi_status status = GMI_OK;
@@ -93,6 +101,8 @@ struct Inflight {
   cudaEvent_t ev;
   std::vector<Request*> reqs;
 };
+
+double secs(Clock::time_point a, Clock::time_point b) { return std::chrono::duration<double>(b - a).count(); }
 
 }  // namespace
 
@@ -117,10 +127,23 @@ struct gmi_server {
   bool stop = false;
   bool launching = false;             // the launcher holds a batch it has not queued yet
   uint64_t n_completed = 0, n_launches = 0, n_pixels = 0;
+  int max_in_flight = 0;
+  Clock::time_point t0 = Clock::now();   // origin of the log's times
+  FILE* log = nullptr;
   std::thread launcher, completer;
 
   size_t footprint(const Request& r) const {
+    if (r.on_device) return 0;
     return align256((size_t)r.N * 8) + align256((size_t)r.N * cfg.C * 4) + align256((size_t)r.H * r.W * cfg.C * 4);
+  }
+  void log_request(const Request& r) {
+    if (!log) return;
+    fprintf(log,
+            "{\"id\": %llu, \"device\": %d, \"N\": %lld, \"H\": %d, \"W\": %d, \"batch\": %llu, \"slot\": %d, "
+            "\"submit\": %.7f, \"admit\": %.7f, \"launch\": %.7f, \"done\": %.7f, \"status\": %d}\n",
+            (unsigned long long)r.id, r.on_device ? 1 : 0, (long long)r.N, r.H, r.W, (unsigned long long)r.batch,
+            r.slot, secs(t0, r.t_submit), secs(t0, r.t_admit), secs(t0, r.t_launch), secs(t0, r.t_done),
+            (int)r.status);
   }
 
   void launcher_loop();
@@ -148,7 +171,8 @@ void gmi_server::launcher_loop() {
           Request* r = pending.front();
           const int64_t rpx = (int64_t)r->H * r->W;
           if (!batch.empty() && (px + rpx > cfg.max_batch_pixels || pts + r->N > max_batch_points)) break;
-          if (!pool->alloc(r->bytes, &r->off)) break;   // wait for memory to free up
+          if (r->bytes > 0 && !pool->alloc(r->bytes, &r->off)) break;   // wait for memory to free up
+          r->t_admit = Clock::now();
           pending.pop_front();
           batch.push_back(r);
           px += rpx;
@@ -168,10 +192,11 @@ void gmi_server::launcher_loop() {
     for (size_t i = 0; i < batch.size(); ++i) {
       Request* r = batch[i];
       char* b = dev_base + r->off;
-      float* dp = (float*)b;
-      float* dv = (float*)(b + align256((size_t)r->N * 8));
-      float* di = (float*)(b + align256((size_t)r->N * 8) + align256((size_t)r->N * cfg.C * 4));
-      if (r->N > 0) {
+      float* dp = r->on_device ? (float*)r->points : (float*)b;
+      float* dv = r->on_device ? (float*)r->values : (float*)(b + align256((size_t)r->N * 8));
+      float* di = r->on_device ? r->image
+                               : (float*)(b + align256((size_t)r->N * 8) + align256((size_t)r->N * cfg.C * 4));
+      if (r->N > 0 && !r->on_device) {
         if (cudaMemcpyAsync(dp, r->points, (size_t)r->N * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
             cudaMemcpyAsync(dv, r->values, (size_t)r->N * cfg.C * 4, cudaMemcpyHostToDevice, s) != cudaSuccess)
           st = GMI_ERR_CUDA;
@@ -189,15 +214,23 @@ void gmi_server::launcher_loop() {
     if (st == GMI_OK) st = gmi_forward_batched(plans[slot], descs.data(), (int)descs.size(), 1, (gmi_stream_t)s);
     for (size_t i = 0; i < batch.size() && st == GMI_OK; ++i) {
       Request* r = batch[i];
+      if (r->on_device) continue;
       if (cudaMemcpyAsync(r->image, descs[i].image, (size_t)r->H * r->W * cfg.C * 4, cudaMemcpyDeviceToHost, s) !=
           cudaSuccess)
         st = GMI_ERR_CUDA;
     }
     cudaEventRecord(events[slot], s);
 
+    const auto t_launch = Clock::now();
     lk.lock();
-    for (Request* r : batch) r->status = st;
+    for (Request* r : batch) {
+      r->status = st;
+      r->t_launch = t_launch;
+      r->batch = n_launches;
+      r->slot = slot;
+    }
     inflight.push_back(Inflight{slot, events[slot], batch});
+    if ((int)inflight.size() > max_in_flight) max_in_flight = (int)inflight.size();
     launching = false;
     n_launches += 1;
     cv_complete.notify_all();
@@ -212,21 +245,40 @@ void gmi_server::completer_loop() {
       if (stop && pending.empty() && !launching) return;
       cv_complete.wait(lk);
     }
-    Inflight f = inflight.front();
-    inflight.pop_front();
-    lk.unlock();
-    const cudaError_t e = cudaEventSynchronize(f.ev);
-    const auto now = Clock::now();
-    lk.lock();
-    for (Request* r : f.reqs) {
-      if (e != cudaSuccess) r->status = GMI_ERR_CUDA;
-      r->t_done = now;
-      r->done = true;
-      pool->release(r->off, r->bytes);
-      n_completed += 1;
-      n_pixels += (uint64_t)r->H * r->W;
+    // every batch in flight whose event has completed (any order); when none
+    // has, look again shortly (the stamp is within that interval of the
+    // event's completion)
+    std::vector<Inflight> finished;
+    std::vector<cudaError_t> errs;
+    for (auto it = inflight.begin(); it != inflight.end();) {
+      const cudaError_t q = cudaEventQuery(it->ev);
+      if (q == cudaErrorNotReady) {
+        ++it;
+        continue;
+      }
+      finished.push_back(*it);
+      errs.push_back(q);
+      it = inflight.erase(it);
     }
-    slot_busy[f.slot] = false;
+    if (finished.empty()) {
+      lk.unlock();
+      std::this_thread::sleep_for(std::chrono::microseconds(20));
+      lk.lock();
+      continue;
+    }
+    const auto now = Clock::now();
+    for (size_t k = 0; k < finished.size(); ++k) {
+      for (Request* r : finished[k].reqs) {
+        if (errs[k] != cudaSuccess) r->status = GMI_ERR_CUDA;
+        r->t_done = now;
+        r->done = true;
+        if (r->bytes > 0) pool->release(r->off, r->bytes);
+        n_completed += 1;
+        n_pixels += (uint64_t)r->H * r->W;
+        log_request(*r);
+      }
+      slot_busy[finished[k].slot] = false;
+    }
     cv_done.notify_all();
     cv_launch.notify_all();
   }
@@ -299,12 +351,31 @@ gmi_status gmi_server_create(const gmi_server_config* cfg, gmi_server** out) {
   return GMI_OK;
 }
 
-gmi_status gmi_server_submit(gmi_server* s, const float* points, const float* values, int64_t N, int H, int W,
-                             float sigma, float* image, uint64_t* id) {
+}  // extern "C"
+
+namespace {
+
+bool on_device_of(const void* p, int device) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == device;
+}
+
+gmi_status submit_impl(gmi_server* s, const float* points, const float* values, int64_t N, int H, int W,
+                       float sigma, float* image, bool on_device, uint64_t* id) {
   if (!s || !id || !image || N < 0 || H < 1 || W < 1 || !(sigma > 0.0f) || !(sigma < 3.0e38f) ||
       (N > 0 && (!points || !values)))
     return GMI_ERR_INVALID_ARG;
   if ((int64_t)H * W > s->cfg.max_batch_pixels || N > s->max_batch_points) return GMI_ERR_CAPACITY;
+  if (on_device) {
+    if (((uintptr_t)points & 7u) || ((uintptr_t)values & 3u) || ((uintptr_t)image & 3u)) return GMI_ERR_INVALID_ARG;
+    if (!on_device_of(image, s->device) || (N > 0 && (!on_device_of(points, s->device) ||
+                                                      !on_device_of(values, s->device))))
+      return GMI_ERR_INVALID_ARG;
+  }
   Request* r = new Request();
   r->points = points;
   r->values = values;
@@ -313,6 +384,7 @@ gmi_status gmi_server_submit(gmi_server* s, const float* points, const float* va
   r->H = H;
   r->W = W;
   r->sigma = sigma;
+  r->on_device = on_device;
   r->bytes = s->footprint(*r);
   if (r->bytes > s->req_bytes) {
     delete r;
@@ -329,6 +401,47 @@ gmi_status gmi_server_submit(gmi_server* s, const float* points, const float* va
   s->pending.push_back(r);
   *id = r->id;
   s->cv_launch.notify_all();
+  return GMI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+gmi_status gmi_server_submit(gmi_server* s, const float* points, const float* values, int64_t N, int H, int W,
+                             float sigma, float* image, uint64_t* id) {
+  return submit_impl(s, points, values, N, H, W, sigma, image, false, id);
+}
+
+gmi_status gmi_server_submit_device(gmi_server* s, const float* points, const float* values, int64_t N, int H,
+                                    int W, float sigma, float* image, uint64_t* id) {
+  return submit_impl(s, points, values, N, H, W, sigma, image, true, id);
+}
+
+gmi_status gmi_server_get_counters(gmi_server* s, gmi_server_counters* out) {
+  if (!s || !out) return GMI_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);
+  memset(out, 0, sizeof(*out));
+  out->completed = s->n_completed;
+  out->launches = s->n_launches;
+  out->pixels = s->n_pixels;
+  out->bytes_in_use = s->pool ? s->pool->used() : 0;
+  out->in_flight = (int)s->inflight.size();
+  out->max_in_flight = s->max_in_flight;
+  return GMI_OK;
+}
+
+gmi_status gmi_server_set_log(gmi_server* s, const char* path) {
+  if (!s) return GMI_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (s->log) {
+    fclose(s->log);
+    s->log = nullptr;
+  }
+  if (path) {
+    s->log = fopen(path, "w");
+    if (!s->log) return GMI_ERR_INVALID_ARG;
+  }
   return GMI_OK;
 }
 
@@ -388,6 +501,7 @@ gmi_status gmi_server_destroy(gmi_server* s) {
   for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
   for (cudaEvent_t e : s->events) cudaEventDestroy(e);
   if (s->dev_base) cudaFree(s->dev_base);
+  if (s->log) fclose(s->log);
   delete s->pool;
   delete s;
   return GMI_OK;
