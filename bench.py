@@ -604,7 +604,10 @@ def bench_per_point_sigma(dev, steps, warmup, flush, stream, lo=0.5, hi=1.5, k=3
     G = torch.randn((im.H, im.W, im.C), generator=torch.Generator(device=dev).manual_seed(9), device=dev)
 
     def fwd_pp():
-        gmi.interpolate_pp(P, V, S, hi, im.H, im.W, radius_sigmas=k, graph=True, out=out)
+        gmi.interpolate_pp(P, V, S, hi, im.H, im.W, radius_sigmas=k, mode="truncated", graph=True, out=out)
+
+    def fwd_pp_exact():
+        gmi.interpolate_pp(P, V, S, hi, im.H, im.W, mode="exact", graph=True, out=out)
 
     def fwd_shared():
         gmi.interpolate(P, V, hi, im.H, im.W, mode="truncated", radius_sigmas=k, graph=True, out=out)
@@ -612,28 +615,36 @@ def bench_per_point_sigma(dev, steps, warmup, flush, stream, lo=0.5, hi=1.5, k=3
     Sxy = torch.as_tensor(wl.point_sigmas(23, im.N, lo, hi, axes=2), device=dev)
 
     def fwd_aniso():
-        gmi.interpolate_pp(P, V, Sxy, hi, im.H, im.W, radius_sigmas=k, graph=True, out=out)
+        gmi.interpolate_pp(P, V, Sxy, hi, im.H, im.W, radius_sigmas=k, mode="truncated", graph=True, out=out)
 
     Scov = torch.as_tensor(wl.point_cov(24, im.N, lo, hi, rmax=0.9), device=dev)
 
     cov_bound = wl.cov_bound(Scov.cpu().numpy())
 
     def fwd_cov():
-        gmi.interpolate_pp(P, V, Scov, cov_bound, im.H, im.W, radius_sigmas=k, graph=True, out=out)
+        gmi.interpolate_pp(P, V, Scov, cov_bound, im.H, im.W, radius_sigmas=k, mode="truncated", graph=True,
+                           out=out)
+
+    def fwd_cov_exact():
+        gmi.interpolate_pp(P, V, Scov, cov_bound, im.H, im.W, mode="exact", graph=True, out=out)
 
     Pg, Vg, Sg = (t.clone().requires_grad_(True) for t in (P, V, S))
     sg = torch.tensor(hi, dtype=torch.float32, device=dev, requires_grad=True)
 
     def fb_pp():
-        gmi.gmi_interpolate_pp(Pg, Vg, Sg, hi, im.H, im.W, radius_sigmas=k).backward(G)
+        gmi.gmi_interpolate_pp(Pg, Vg, Sg, hi, im.H, im.W, radius_sigmas=k, mode="truncated").backward(G)
+
+    def fb_pp_exact():
+        gmi.gmi_interpolate_pp(Pg, Vg, Sg, hi, im.H, im.W, mode="exact").backward(G)
 
     def fb_shared():
         gmi.gmi_interpolate(Pg, Vg, sg, im.H, im.W, mode="truncated", radius_sigmas=k).backward(G)
 
     res = {}
     for name, fn in (("forward_pp", fwd_pp), ("forward_shared", fwd_shared), ("forward_aniso", fwd_aniso),
-                     ("forward_cov", fwd_cov),
-                     ("fwd_bwd_pp", fb_pp),
+                     ("forward_cov", fwd_cov), ("forward_pp_exact", fwd_pp_exact),
+                     ("forward_cov_exact", fwd_cov_exact),
+                     ("fwd_bwd_pp", fb_pp), ("fwd_bwd_pp_exact", fb_pp_exact),
                      ("fwd_bwd_shared", fb_shared)):
         for _ in range(max(3, warmup)):
             fn()
@@ -651,7 +662,7 @@ def bench_per_point_sigma(dev, steps, warmup, flush, stream, lo=0.5, hi=1.5, k=3
     torch.cuda._sleep(int(steps * 200e-6 * SM_MAX_MHZ * 1e6))
     for _ in range(steps):
         flush.zero_()
-        gmi.interpolate_pp(P, V, S, hi, im.H, im.W, radius_sigmas=k, out=out)
+        gmi.interpolate_pp(P, V, S, hi, im.H, im.W, radius_sigmas=k, mode="truncated", out=out)
     torch.cuda.synchronize()
     st_ms = (ctypes.c_double * 4)()
     st_n = (ctypes.c_int * 4)()
@@ -674,7 +685,8 @@ def bench_per_point_sigma(dev, steps, warmup, flush, stream, lo=0.5, hi=1.5, k=3
                        "(bound %g), truncated at %g sigma_i; forward_aniso draws sx_i, sy_i independently from "
                        "the same range, forward_cov adds rho_i uniform in [-0.9, 0.9] (bound: the largest sqrt of a "
                        "covariance eigenvalue); shared-sigma rows use sigma = %g with the same window; fwd_bwd through "
-                       "the autograd ops (positions, values, sigmas), upstream N(0,1)" % (lo, hi, hi, k, hi))
+                       "the autograd ops (positions, values, sigmas), upstream N(0,1); *_exact rows: exact mode "
+                       "(every point, k = 6)" % (lo, hi, hi, k, hi))
     return res
 
 def bench_reconstruction(dev, side=768, factors=(2, 3, 4, 6, 8), sigma_scales=(0.2, 0.25, 0.35, 0.5, 0.7)):

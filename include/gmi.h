@@ -186,20 +186,26 @@ gmi_status gmi_backward(const float* points, const float* values, int64_t N, int
  * one fixed sigma, and the point-optimisation experiment (section 3, Fig. 4)
  * finds the choice of sigma to matter more than the point positions; with
  * gmi_backward_pp a sigma per point can be fitted by gradient descent.
- * Truncated mode only: point i counts at pixel q when |q - mu_i| <= k
- * sigma_i (k = radius_sigmas).
+ * GMI_MODE_EXACT: every point counts at every pixel (Eq. 1 over all
+ * points); weights are evaluated relative to the pixel's largest one, so a
+ * pixel far from every point still gets its nearest points' blend, and a
+ * point weighing less than exp(-k^2/2) of the largest may be left out
+ * (k = radius_sigmas), as in gmi_forward's exact mode.
+ * GMI_MODE_TRUNCATED: point i counts at pixel q when |q - mu_i| <= k
+ * sigma_i; a pixel no point reaches gets 0.
  *   sigmas   device [N] float32, 4-byte aligned; each finite and in
  *            [p->sigma * 2^-32, p->sigma]
- *   p        p->mode must be GMI_MODE_TRUNCATED; p->sigma is an upper bound
- *            on every sigmas[i] (it sets the search radius k * p->sigma, so
- *            a tight bound is faster) and the reference scale of den_out
- *   den_out  device [H,W] float32 or NULL: sum_i (sigma/sigma_i)^2
- *            exp(-d_i^2 / (2 sigma_i^2)) over the points that count
- *            (sigma = p->sigma; with every sigma_i = sigma it is
- *            gmi_forward's den); no shift plane (truncated mode never shifts)
+ *   p        p->sigma is an upper bound on every sigmas[i] (it sets the
+ *            search radius, so a tight bound is faster) and the reference
+ *            scale of den_out in truncated mode
+ *   den_out  device [H,W] float32 or NULL.  Truncated: sum_i (sigma /
+ *            sigma_i)^2 exp(-d_i^2 / (2 sigma_i^2)) over the points that
+ *            count (sigma = p->sigma; with every sigma_i = sigma it is
+ *            gmi_forward's den).  Exact: sum_i w_i(q) / max_j w_j(q) >= 1,
+ *            w_i = exp(-d_i^2 / (2 sigma_i^2)) / sigma_i^2.  No shift plane.
  *   points, values, image, workspace (gmi_workspace_size with the same N,
  *   C, H, W and params), GMI_FLAG_GRAPH: as gmi_forward
- * Errors: as gmi_forward, plus GMI_ERR_UNSUPPORTED (exact mode) and
+ * Errors: as gmi_forward, plus
  * GMI_ERR_INVALID_ARG (sigmas NULL or misaligned with N > 0; with
  * GMI_FLAG_SYNC_CHECK also a sigma outside its range, found on the device,
  * and GMI_ERR_NONFINITE for a NaN/Inf sigma).  Out-of-range sigmas without
@@ -218,10 +224,13 @@ gmi_status gmi_forward_pp(const float* points, const float* values, const float*
  *   grad_sigmas[i]   = sum_q (w_i(q)/Z_q) t_i(q) (|q - mu_i|^2 / sigma_i^3
  *                      - 2 / sigma_i)
  *   with t_i(q) as for gmi_backward.  image, den: the outputs of the matching
- *   gmi_forward_pp (den must not be NULL); grad_points [N,2], grad_values
- *   [N,C], grad_sigmas [N]: device, written (each may be NULL to skip it).
- * Each gradient is written by one thread (no atomics): the result does not
- * vary from run to run.  Errors: as gmi_forward_pp.
+ *   gmi_forward_pp (den must not be NULL; exact mode recomputes each pixel's
+ *   sums and reads neither); grad_points [N,2], grad_values [N,C],
+ *   grad_sigmas [N]: device, written (each may be NULL to skip it).
+ * Truncated mode writes each gradient from one thread (no atomics): the
+ * result does not vary from run to run.  Exact mode adds every (pixel,
+ * point) term into per-point sums with float atomics, so its low bits can
+ * vary between runs.  Errors: as gmi_forward_pp.
  */
 gmi_status gmi_backward_pp(const float* points, const float* values, const float* sigmas,
                            int64_t N, int C, int H, int W, const gmi_params* p,
@@ -232,13 +241,16 @@ gmi_status gmi_backward_pp(const float* points, const float* values, const float
 /*
  * Forward and backward passes with an axis-aligned covariance per point:
  * point i is N(mu_i, diag(sx_i^2, sy_i^2)) with its normaliser
- * 1/(2 pi sx_i sy_i) kept, and counts at pixel q inside its ellipse
- * dx^2/sx_i^2 + dy^2/sy_i^2 <= k^2 (truncated mode only).  With sx_i = sy_i
+ * 1/(2 pi sx_i sy_i) kept; in truncated mode it counts at pixel q inside
+ * its ellipse dx^2/sx_i^2 + dy^2/sy_i^2 <= k^2, in exact mode everywhere
+ * (relative to the pixel's largest weight, as gmi_forward_pp).  With sx_i = sy_i
  * they compute what gmi_forward_pp / gmi_backward_pp compute.
  *   sigmas_xy      device [N,2] float32 (sx, sy) per point, 4-byte aligned;
  *                  each finite and in [p->sigma * 2^-32, p->sigma]
- *   den_out / den  sum_i sigma^2 / (sx_i sy_i) exp(-(dx^2/sx_i^2 +
- *                  dy^2/sy_i^2) / 2) over the points that count
+ *   den_out / den  truncated: sum_i sigma^2 / (sx_i sy_i) exp(-(dx^2/sx_i^2
+ *                  + dy^2/sy_i^2) / 2) over the points that count; exact:
+ *                  the weights' sum relative to the largest (as
+ *                  gmi_forward_pp)
  *   grad_points    [N,2]: sum_q (w_i/Z_q) t_i(q) (dx / sx_i^2, dy / sy_i^2)
  *   grad_sigmas_xy [N,2]: sum_q (w_i/Z_q) t_i(q) (dx^2/sx_i^3 - 1/sx_i,
  *                  dy^2/sy_i^3 - 1/sy_i)
@@ -259,8 +271,9 @@ gmi_status gmi_backward_aniso(const float* points, const float* values, const fl
 /*
  * Forward and backward passes with a full covariance per point: point i is
  * N(mu_i, S_i), S_i = [[sx^2, rho sx sy], [rho sx sy, sy^2]], with its
- * normaliser 1/(2 pi sqrt(det S_i)) kept, and counts at pixel q inside its
- * rotated ellipse d^T S_i^-1 d <= k^2 (truncated mode only).  With rho = 0
+ * normaliser 1/(2 pi sqrt(det S_i)) kept; in truncated mode it counts at
+ * pixel q inside its rotated ellipse d^T S_i^-1 d <= k^2, in exact mode
+ * everywhere (as gmi_forward_pp).  With rho = 0
  * they compute what gmi_forward_aniso / gmi_backward_aniso compute.  The cross
  * term of the quadratic form does not factorise into a column and a row
  * factor, so every (pixel, candidate) takes its own exponential.
@@ -272,8 +285,9 @@ gmi_status gmi_backward_aniso(const float* points, const float* values, const fl
  *               every S_i (a rotated ellipse reaches k sqrt(lambda_max) from
  *               its centre, which can exceed k max(sx, sy)); checked on the
  *               device to a relative 2^-20
- *   den_out/den sum_i sigma^2 / sqrt(det S_i) exp(-d^T S_i^-1 d / 2) over
- *               the points that count
+ *   den_out/den truncated: sum_i sigma^2 / sqrt(det S_i) exp(-d^T S_i^-1
+ *               d / 2) over the points that count; exact: relative to the
+ *               largest weight (as gmi_forward_pp)
  *   grad_points [N,2]: sum_q (w_i/Z_q) t_i(q) S_i^-1 d
  *   grad_cov    [N,3]: d/d(sx, sy, rho) of L, from the chain rule on
  *               ln w_i = -d^T S_i^-1 d / 2 - ln sx - ln sy - ln(1 - rho^2) / 2

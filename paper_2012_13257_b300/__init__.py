@@ -363,18 +363,21 @@ _PP_CALLS = {1: ("gmi_forward_pp", "gmi_backward_pp"), 2: ("gmi_forward_aniso", 
 
 
 def interpolate_pp(points, values, sigmas, sigma_bound: float, H: int, W: int, *, radius_sigmas: float = 6.0,
-                   bin_px: int = 0, variant: int = 0, return_aux: bool = False, check: bool = False,
+                   mode="exact", bin_px: int = 0, variant: int = 0, return_aux: bool = False, check: bool = False,
                    graph: bool = False, out=None):
-    """Forward pass with a sigma per point, truncated inside each point's
-    ``radius_sigmas``-sigma disc or ellipse; normalisers kept.  ``sigmas`` is
+    """Forward pass with a sigma per point, normalisers kept: over all points
+    (``mode="exact"``, weights relative to each pixel's largest; points below
+    exp(-radius_sigmas^2/2) of it may be left out) or inside each point's
+    ``radius_sigmas``-sigma disc or ellipse (``mode="truncated"``).  ``sigmas`` is
     ``[N]`` (isotropic sigma_i), ``[N, 2]`` (axis-aligned (sx_i, sy_i)) or
     ``[N, 3]`` (a full covariance (sx_i, sy_i, rho_i), |rho_i| <= 0.99).
     ``sigma_bound`` must bound every sigma from above (it sets the search
     radius; a tight bound is faster); for a full covariance it bounds the
     square root of each covariance's largest eigenvalue.  With ``return_aux`` also returns
-    ``den`` = sum_i sigma_bound^2 / (sx_i sy_i) exp(-(dx^2/sx_i^2 +
+    ``den``: in truncated mode sum_i sigma_bound^2 / (sx_i sy_i) exp(-(dx^2/sx_i^2 +
     dy^2/sy_i^2)/2) (full covariance: sigma_bound^2 / sqrt(det S_i)
-    exp(-d^T S_i^-1 d / 2)).  ``check=True`` synchronises and raises on out-of-range
+    exp(-d^T S_i^-1 d / 2)); in exact mode the weights' sum relative to the
+    pixel's largest weight (>= 1).  ``check=True`` synchronises and raises on out-of-range
     or non-finite sigmas (and the other device-detected errors)."""
     import torch
     points, values = _check_inputs(points, values)
@@ -383,7 +386,7 @@ def interpolate_pp(points, values, sigmas, sigma_bound: float, H: int, W: int, *
     H, W = int(H), int(W)
     dev = points.device
     flags = (_lib.FLAG_SYNC_CHECK if check else 0) | (_lib.FLAG_GRAPH if graph else 0)
-    md = MODE_TRUNCATED
+    md = _mode(mode)
     p = _params(sigma_bound, radius_sigmas, md, flags, bin_px, variant)
     nbytes = _ws_bytes(N, C, H, W, p, (N, C, H, W, float(sigma_bound), float(radius_sigmas), md, bin_px, variant))
     if out is None:
@@ -392,7 +395,7 @@ def interpolate_pp(points, values, sigmas, sigma_bound: float, H: int, W: int, *
     if torch.cuda.current_device() != dev.index:
         with torch.cuda.device(dev):
             return interpolate_pp(points, values, sigmas, sigma_bound, H, W, radius_sigmas=radius_sigmas,
-                                  bin_px=bin_px, variant=variant, return_aux=return_aux, check=check,
+                                  mode=mode, bin_px=bin_px, variant=variant, return_aux=return_aux, check=check,
                                   graph=graph, out=out)
     stream = _stream_handle(dev)
     ws = _workspace(dev, stream, nbytes)
@@ -407,7 +410,7 @@ def interpolate_pp(points, values, sigmas, sigma_bound: float, H: int, W: int, *
 
 
 def interpolate_backward_pp(points, values, sigmas, sigma_bound: float, H: int, W: int, image, den, grad_image, *,
-                            radius_sigmas: float = 6.0, bin_px: int = 0, variant: int = 0,
+                            radius_sigmas: float = 6.0, mode="exact", bin_px: int = 0, variant: int = 0,
                             need=(True, True, True), check: bool = False):
     """Gradients of sum(grad_image * image) w.r.t. points, values and the
     per-point sigmas (``image``, ``den`` from ``interpolate_pp(...,
@@ -425,7 +428,7 @@ def interpolate_backward_pp(points, values, sigmas, sigma_bound: float, H: int, 
     image, den, grad_image = (t.contiguous() for t in (image, den, grad_image))
     H, W = int(H), int(W)
     flags = _lib.FLAG_SYNC_CHECK if check else 0
-    md = MODE_TRUNCATED
+    md = _mode(mode)
     p = _params(sigma_bound, radius_sigmas, md, flags, bin_px, variant)
     nbytes = _ws_bytes(N, C, H, W, p, (N, C, H, W, float(sigma_bound), float(radius_sigmas), md, bin_px, variant))
     gp = torch.empty((N, 2), dtype=torch.float32, device=dev) if need[0] else None
@@ -434,7 +437,7 @@ def interpolate_backward_pp(points, values, sigmas, sigma_bound: float, H: int, 
     if torch.cuda.current_device() != dev.index:
         with torch.cuda.device(dev):
             return interpolate_backward_pp(points, values, sigmas, sigma_bound, H, W, image, den, grad_image,
-                                           radius_sigmas=radius_sigmas, bin_px=bin_px, variant=variant,
+                                           radius_sigmas=radius_sigmas, mode=mode, bin_px=bin_px, variant=variant,
                                            need=need, check=check)
     stream = _stream_handle(dev)
     ws = _workspace(dev, stream, nbytes)
@@ -456,27 +459,27 @@ def _pp_function():
         backward run in libgmi's kernels."""
 
         @staticmethod
-        def forward(ctx, points, values, sigmas, sigma_bound, H, W, radius_sigmas, bin_px, variant):
+        def forward(ctx, points, values, sigmas, sigma_bound, H, W, radius_sigmas, mode, bin_px, variant):
             img, den = interpolate_pp(points, values, sigmas, sigma_bound, H, W, radius_sigmas=radius_sigmas,
-                                      bin_px=bin_px, variant=variant, return_aux=True)
+                                      mode=mode, bin_px=bin_px, variant=variant, return_aux=True)
             ctx.set_materialize_grads(False)
             ctx.save_for_backward(points, values, sigmas, img, den)
-            ctx.cfg = (sigma_bound, H, W, radius_sigmas, bin_px, variant)
+            ctx.cfg = (sigma_bound, H, W, radius_sigmas, mode, bin_px, variant)
             return img
 
         @staticmethod
         def backward(ctx, g):
             if g is None:
-                return (None,) * 9
+                return (None,) * 10
             points, values, sigmas, img, den = ctx.saved_tensors
-            bound, H, W, k, bin_px, variant = ctx.cfg
+            bound, H, W, k, mode, bin_px, variant = ctx.cfg
             need = tuple(ctx.needs_input_grad[:3])
             gp, gv, gs = interpolate_backward_pp(points.detach(), values.detach(), sigmas.detach(), bound, H, W,
-                                                 img, den, g.float(), radius_sigmas=k, bin_px=bin_px,
+                                                 img, den, g.float(), radius_sigmas=k, mode=mode, bin_px=bin_px,
                                                  variant=variant, need=need)
             if gs is not None:
                 gs = gs.reshape(sigmas.shape)
-            return gp, gv, gs, None, None, None, None, None, None
+            return gp, gv, gs, None, None, None, None, None, None, None
 
     return GMIPPFunction
 
@@ -485,16 +488,17 @@ _GMIPPFunction = None
 
 
 def gmi_interpolate_pp(points, values, sigmas, sigma_bound: float, H: int, W: int, *, radius_sigmas: float = 6.0,
-                       bin_px: int = 0, variant: int = 0):
-    """Differentiable per-point-sigma interpolation (truncated inside each
-    point's ``radius_sigmas``-sigma disc or ellipse): gradients flow to
-    ``points``, ``values`` and ``sigmas`` ([N] isotropic, [N, 2] axis-aligned
-    (sx, sy) or [N, 3] full (sx, sy, rho)).  ``sigma_bound`` >= every sigma.  Returns [H, W, C]."""
+                       mode="exact", bin_px: int = 0, variant: int = 0):
+    """Differentiable per-point-sigma interpolation (over all points, or
+    truncated inside each point's ``radius_sigmas``-sigma disc or ellipse
+    with ``mode="truncated"``): gradients flow to ``points``, ``values`` and
+    ``sigmas`` ([N] isotropic, [N, 2] axis-aligned (sx, sy) or [N, 3] full
+    (sx, sy, rho)).  ``sigma_bound`` >= every sigma.  Returns [H, W, C]."""
     global _GMIPPFunction
     if _GMIPPFunction is None:
         _GMIPPFunction = _pp_function()
     return _GMIPPFunction.apply(points, values, sigmas, float(sigma_bound), int(H), int(W), float(radius_sigmas),
-                                int(bin_px), int(variant))
+                                _mode(mode), int(bin_px), int(variant))
 
 
 def _flat_views(shapes, dev, dtype=None):

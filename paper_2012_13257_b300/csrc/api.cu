@@ -17,6 +17,8 @@ namespace gmi {
 
 cudaError_t launch_near(const KArgs& a, int mth, int mtw, bool trunc, int ppk, int grid, cudaStream_t s);
 cudaError_t launch_near_staged(const KArgs& a, int mth, int mtw, bool trunc, int grid, cudaStream_t s);
+cudaError_t launch_pp_exact_forward(const KArgs& a, int mth, int mtw, int ppk, cudaStream_t s);
+void warm_pp_exact(int C, int ppk);
 int staged_blocks_per_sm(int mth, int mtw, int C, bool trunc);
 cudaError_t launch_scatter_plan(const KArgs& a, bool trunc, int n_scatter, cudaStream_t s);
 int near_blocks_per_sm(int mth, int mtw, int C, bool trunc, int ppk);
@@ -171,6 +173,7 @@ DevWork bind_ws(void* ws, const WsLayout& L) {
   w.fbflag = nullptr;
   w.fbq = nullptr;
   w.sig_part = nullptr;
+  w.ppmom = nullptr;
   w.table = nullptr;
   return w;
 }
@@ -214,6 +217,16 @@ gmi_status run_bin_and_plan(KArgs& a, const WsLayout& L, void* ws, int mth, int 
 // Binning + plan + near + far on prepared arguments (single image or batch).
 gmi_status run_forward_pipeline(KArgs& a, const WsLayout& L, void* ws, int mth, int mtw, bool trunc,
                                 cudaStream_t s, int ppk) {
+  if (ppk && !trunc) {
+    // exact mode with per-point sigmas: the bins, then every micro-tile
+    // through the per-pixel shifted gather (no plan, no near kernel)
+    gmi_status st = run_bin_and_plan(a, L, ws, mth, mtw, trunc, s, false);
+    if (st != GMI_OK) return st;
+    const ProfileMark pf = profile_begin(GMI_STAGE_FAR, s);
+    if (launch_pp_exact_forward(a, mth, mtw, ppk, s) != cudaSuccess) return GMI_ERR_CUDA;
+    profile_end(pf, s);
+    return GMI_OK;
+  }
   gmi_status st = run_bin_and_plan(a, L, ws, mth, mtw, trunc, s, true);
   if (st != GMI_OK) return st;
   const int sms = device_sm_count();
@@ -237,6 +250,10 @@ bool uses_staged_gather(int gather, int ppk) { return ppk == 0 && gather != GMI_
 
 void warm_near_caches(int mth, int mtw, int C, bool trunc, int ppk, int gather) {
   device_sm_count();
+  if (ppk && !trunc) {
+    warm_pp_exact(C, ppk);
+    return;
+  }
   if (uses_staged_gather(gather, ppk)) staged_blocks_per_sm(mth, mtw, C, trunc);
   else near_blocks_per_sm(mth, mtw, C, trunc, ppk);
 }
@@ -484,7 +501,6 @@ static gmi_status forward_per_point(const float* points, const float* values, co
                                     float* den_out, void* workspace, size_t ws_bytes, gmi_stream_t stream) {
   gmi_status st = check_params(p);
   if (st != GMI_OK) return st;
-  if (p->mode != GMI_MODE_TRUNCATED) return GMI_ERR_UNSUPPORTED;
   if (N > 0 && (!sigmas || ((uintptr_t)sigmas & 3u) != 0)) return GMI_ERR_INVALID_ARG;
   return forward_impl(points, values, N > 0 ? sigmas : nullptr, pp_kind, N, C, H, W, p, image, den_out, nullptr,
                       workspace, ws_bytes, stream);

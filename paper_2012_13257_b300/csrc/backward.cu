@@ -486,8 +486,7 @@ long long bwd_extra_bytes(long long N, int C, int H, int W) {
   const long long mt = ((long long)H + 1) / 2 * (((long long)W + 3) / 4);   // smallest micro-tile: 2x4
   const long long planes = px * 16 * (C == 4 ? 2 : 1);
   auto al = [](long long v) { return (v + 255) / 256 * 256; };
-  (void)N;
-  return al(planes) + al(mt * 4) + al(mt * 8) + al((long long)kSigParts * 4);
+  return al(planes) + al(mt * 4) + al(mt * 8) + al((long long)kSigParts * 4) + al(N * 4 * kPpMomentFloats);
 }
 
 void bind_bwd(DevWork& w, void* extra, long long N, int C, int H, int W, long long mt_total) {
@@ -504,6 +503,8 @@ void bind_bwd(DevWork& w, void* extra, long long N, int C, int H, int W, long lo
   w.fbq = (uint2*)p;
   p += al(mt * 8);
   w.sig_part = (float*)p;
+  p += al((long long)kSigParts * 4);
+  w.ppmom = (float*)p;
 }
 
 template <int C>
@@ -520,6 +521,9 @@ static cudaError_t launch_bwd_c(const KArgs& a, const BwdArgs& b, cudaStream_t s
   if (!b.trunc) bwd_fallback_kernel<C><<<sms * fallback_blocks_per_sm<C>(), 32 * kFarWarps, 0, s>>>(a, b);
   return cudaGetLastError();
 }
+
+cudaError_t launch_pp_exact_backward(const KArgs& a, const BwdImage& bi, int mth, int mtw, int ppk, float* mom,
+                                     cudaStream_t s);
 
 cudaError_t launch_backward(const KArgs& a, const BwdArgs& b, cudaStream_t s) {
   switch (a.C) {
@@ -582,9 +586,25 @@ static gmi_status backward_impl(const float* points, const float* values, const 
   a.wt_total = wt;
   a.ch_total = (N + kChunk - 1) / kChunk;
   a.mt_total = mt;
+  a.satj_total = sat_jobs(g);
   const bool trunc = p->mode == GMI_MODE_TRUNCATED;
   // the bins only: the fallback derives its radii from den, not from the plan
   if ((st = run_bin_and_plan(a, L, workspace, mth, mtw, trunc, s, false)) != GMI_OK) return st;
+  if (per_point && !trunc) {
+    // exact mode with per-point sigmas: every pixel's shift and den again,
+    // the pairs' terms into per-point moments, then the gradients
+    BwdImage bi;
+    memset(&bi, 0, sizeof(bi));
+    bi.grad = grad_image;
+    bi.gpts = grad_points;
+    bi.gvals = grad_values;
+    bi.gsigs = grad_sigmas;
+    const ProfileMark pm = profile_begin(GMI_STAGE_BACKWARD, s);
+    if (launch_pp_exact_backward(a, bi, mth, mtw, g.pp_kind == 3 ? 2 : 1, a.w.ppmom, s) != cudaSuccess)
+      return GMI_ERR_CUDA;
+    profile_end(pm, s);
+    return (p->flags & GMI_FLAG_SYNC_CHECK) ? read_status(workspace, s) : GMI_OK;
+  }
   if (cudaMemsetAsync(a.w.fbflag, 0, sizeof(unsigned) * (size_t)mt, s) != cudaSuccess) return GMI_ERR_CUDA;
   a.px_total = (long long)H * W;
   BwdArgs b;
@@ -625,7 +645,6 @@ static gmi_status backward_per_point(const float* points, const float* values, c
                                      size_t ws_bytes, gmi_stream_t stream) {
   gmi_status st = check_params(p);
   if (st != GMI_OK) return st;
-  if (p->mode != GMI_MODE_TRUNCATED) return GMI_ERR_UNSUPPORTED;
   if (N > 0 && (!sigmas || ((uintptr_t)sigmas & 3u) != 0)) return GMI_ERR_INVALID_ARG;
   return backward_impl(points, values, N > 0 ? sigmas : nullptr, N, C, H, W, p, image, den, nullptr, grad_image,
                        grad_points, grad_values, nullptr, grad_sigmas, true, pp_kind, workspace, ws_bytes, stream);

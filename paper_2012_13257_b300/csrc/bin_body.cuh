@@ -21,6 +21,7 @@ static __device__ __forceinline__ void bin_scatter_body(const KArgs& a, int nblo
     const int img = find_image<0>(a, ch);
     const ImageGeom g = a.w.table ? a.w.table[img] : a.g0;   // a copy: no address of a local struct
     const long long i = (ch - g.ch_base) * kChunk + threadIdx.x;
+    float la = 0.0f;   // this point's log2 normaliser (per-point sigmas)
     if (i < g.n) {
       float2 p = reinterpret_cast<const float2*>(g.points)[i];
       long long bin;
@@ -38,9 +39,19 @@ static __device__ __forceinline__ void bin_scatter_body(const KArgs& a, int nblo
       a.w.perm[dst] = (unsigned)i;
       if (g.sigmas) {
         const float* sg = g.sigmas + g.pp_kind * i;
-        if (g.pp_kind == 3) a.w.spp[dst] = pp_cov_consts(g.sigma, sg[0], sg[1], sg[2]);
-        else a.w.spp[dst] = pp_consts(g.sigma, sg[0], g.pp_kind == 2 ? sg[1] : sg[0]);
+        const float4 k = g.pp_kind == 3 ? pp_cov_consts(g.sigma, sg[0], sg[1], sg[2])
+                                        : pp_consts(g.sigma, sg[0], g.pp_kind == 2 ? sg[1] : sg[0]);
+        a.w.spp[dst] = k;
+        la = g.pp_kind == 3 ? k.w : k.z;
       }
+    }
+    if (g.sigmas) {
+      // the image's largest normaliser (exact mode's candidate radius): one
+      // atomic per warp; la >= 0, so its bits order as the values do
+      la = (la >= 0.0f && la < INFINITY) ? la : 0.0f;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) la = fmaxf(la, __shfl_xor_sync(0xffffffffu, la, o));
+      if ((threadIdx.x & 31) == 0) atomicMax(&a.w.status[kLaMax], __float_as_uint(la));
     }
   }
 }

@@ -36,6 +36,7 @@ enum : int {
   kFbHead = 8,         // next entry of that queue
   kSigDone = 9,        // blocks of the point-centric backward that have finished
   kSatHead = 10,       // next summed-area-table column job
+  kLaMax = 11,         // per-point sigmas: the largest log2 normaliser la_i (float bits; la_i >= 0)
   kStatusWords = 64,
 };
 
@@ -114,6 +115,8 @@ struct DevWork {
   unsigned* fbflag;      // [mt_total]: micro-tile holds a non-core pixel
   uint2* fbq;            // [mt_total]: queue of such micro-tiles (image, micro-tile)
   float* sig_part;       // [kSigParts]: per-block sigma-gradient partials
+  float* ppmom;          // [n_total * kPpMomentFloats]: per-point moments of the exact-mode
+                         //   per-point-sigma backward
   unsigned* sat;         // per image [(nby+1) x (nbx+1)]: points in bins [0,by) x [0,bx), built
                          //   by the near kernel when the far-field queue is not empty
   const ImageGeom* table;// device descriptor table (batched) or null (single image)
@@ -166,6 +169,7 @@ __device__ __forceinline__ KArgs resolve(const KArgs& in) {
 constexpr int kChunk = 256;             // points per chunk (one per thread) in the binning kernels
 constexpr int kScanChunk = 1024;        // bins per block in the scan kernels
 constexpr int kSigParts = 4096;         // sigma-gradient partials (one per backward block)
+constexpr int kPpMomentFloats = 10;     // per-point moments of the exact per-point-sigma backward
 constexpr int kSplitMax = 64;           // most work items one warp tile is split into
 constexpr unsigned kSplitTarget = 160;  // candidates per thread per work item
 

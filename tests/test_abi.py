@@ -110,23 +110,22 @@ def test_autotune_rejects_bad_arguments_without_launching():
 
 @pytest.mark.parametrize("kind", ["pp", "aniso", "cov"])
 def test_per_point_calls_reject_bad_arguments_without_launching(kind):
-    """Exact mode is not built for per-point sigmas (GMI_ERR_UNSUPPORTED);
-    a missing or misaligned sigma array is GMI_ERR_INVALID_ARG; both are
-    found on the host before anything is enqueued (the fake pointers are
-    never dereferenced)."""
+    """A missing or misaligned sigma array is GMI_ERR_INVALID_ARG, and a
+    short workspace GMI_ERR_WORKSPACE, in either mode; all are found on the
+    host before anything is enqueued (the fake pointers are never
+    dereferenced)."""
     lib = _lib.load()
     fwd, bwd = getattr(lib, "gmi_forward_" + kind), getattr(lib, "gmi_backward_" + kind)
-    exact = _lib.make_params(1.0, mode=_lib.MODE_EXACT)
-    trunc = _lib.make_params(1.0, mode=_lib.MODE_TRUNCATED)
-    assert fwd(256, 256, 256, 10, 3, 8, 8, ctypes.byref(exact), 256, None, 256, 1 << 20, None) == 7
-    assert fwd(256, 256, None, 10, 3, 8, 8, ctypes.byref(trunc), 256, None, 256, 1 << 20, None) == 1
-    assert fwd(256, 256, 258, 10, 3, 8, 8, ctypes.byref(trunc), 256, None, 256, 1 << 20, None) == 1
-    assert bwd(256, 256, 256, 10, 3, 8, 8, ctypes.byref(exact), 256, 256, 256, None, None, None, 256, 1 << 20,
-               None) == 7
-    assert bwd(256, 256, None, 10, 3, 8, 8, ctypes.byref(trunc), 256, 256, 256, None, None, None, 256, 1 << 20,
-               None) == 1
-    # the workspace is checked too
-    assert fwd(256, 256, 256, 10, 3, 8, 8, ctypes.byref(trunc), 256, None, 256, 16, None) == 3
+    for mode in (_lib.MODE_EXACT, _lib.MODE_TRUNCATED):
+        p = _lib.make_params(1.0, mode=mode)
+        assert fwd(256, 256, None, 10, 3, 8, 8, ctypes.byref(p), 256, None, 256, 1 << 20, None) == 1
+        assert fwd(256, 256, 258, 10, 3, 8, 8, ctypes.byref(p), 256, None, 256, 1 << 20, None) == 1
+        assert bwd(256, 256, None, 10, 3, 8, 8, ctypes.byref(p), 256, 256, 256, None, None, None, 256, 1 << 20,
+                   None) == 1
+        assert bwd(256, 256, 258, 10, 3, 8, 8, ctypes.byref(p), 256, 256, 256, None, None, None, 256, 1 << 20,
+                   None) == 1
+        # the workspace is checked too
+        assert fwd(256, 256, 256, 10, 3, 8, 8, ctypes.byref(p), 256, None, 256, 16, None) == 3
 
 
 def test_stacked_calls_reject_bad_arguments_without_launching():

@@ -92,7 +92,7 @@ def test_cuda_path_reproduces_the_stored_values(cuda_device, case):
     if "sigmas" in case:
         sig = case["sigmas"].astype(np.float32)
         out = gmi.interpolate_pp(P, V, to_dev(sig, cuda_device), float(sig.max()), case["H"], case["W"],
-                                 radius_sigmas=case["k"], check=True)
+                                 radius_sigmas=case["k"], check=True, mode="truncated")
     else:
         out = gmi.interpolate(P, V, float(case["sigma"][0]), case["H"], case["W"], mode=mode,
                               radius_sigmas=case["k"], check=True)

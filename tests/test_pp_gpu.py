@@ -1,5 +1,6 @@
 """Per-point sigma (each point its own N(mu_i, sigma_i^2 I), normalisers
-kept; truncated at k sigma_i): the CUDA path against the FP64 oracle's
+kept), truncated mode (each point counts within k sigma_i; exact mode is
+covered by test_pp_exact_gpu.py): the CUDA path against the FP64 oracle's
 forward_pp / backward_pp.
 
 Bars as for the shared-sigma tests: forward max-abs <= 1e-4 on colours in
@@ -28,7 +29,7 @@ def gmi():
 def run(im, sig, bound, dev, k=6.0, **kw):
     import torch
     img, den = gmi().interpolate_pp(to_dev(im.points, dev), to_dev(im.values, dev), to_dev(sig, dev), bound,
-                                    im.H, im.W, radius_sigmas=k, return_aux=True, check=True, **kw)
+                                    im.H, im.W, radius_sigmas=k, return_aux=True, check=True, **kw, mode="truncated")
     torch.cuda.synchronize()
     return img.cpu().numpy(), den.cpu().numpy()
 
@@ -106,6 +107,7 @@ def test_empty_and_single_point(cuda_device):
 
 
 def test_sigma_range_and_nonfinite_reported(cuda_device):
+    import torch
     g = gmi()
     im = wl.tiny_random(14, 50, 12, 12, C=3, sigma=1.0)
     P, V = to_dev(im.points, cuda_device), to_dev(im.values, cuda_device)
@@ -113,9 +115,9 @@ def test_sigma_range_and_nonfinite_reported(cuda_device):
         sig = np.full(im.N, 0.5, np.float32)
         sig[7] = bad
         with pytest.raises(g.GmiError) as e:
-            g.interpolate_pp(P, V, to_dev(sig, cuda_device), 1.0, 12, 12, check=True)
+            g.interpolate_pp(P, V, to_dev(sig, cuda_device), 1.0, 12, 12, check=True, mode="truncated")
         assert e.value.status == status, (bad, e.value.status)
-    # exact mode is not built for per-point sigmas
+    # the same call through the C-ABI in exact mode
     lib = g.lib()
     from paper_2012_13257_b300 import _lib
     p = _lib.make_params(1.0, 6.0, _lib.MODE_EXACT, 0, 0, 0)
@@ -127,7 +129,10 @@ def test_sigma_range_and_nonfinite_reported(cuda_device):
     base = (ws.data_ptr() + 255) // 256 * 256
     st = lib.gmi_forward_pp(P.data_ptr(), V.data_ptr(), sig.data_ptr(), im.N, 3, 12, 12, ctypes.byref(p),
                             out.data_ptr(), None, base, n.value, None)
-    assert st == 7
+    assert st == 0
+    ref = oracle.forward_pp(im.points, im.values, np.full(im.N, 0.5, np.float32), 12, 12, mode=oracle.EXACT)
+    torch.cuda.synchronize()
+    assert np.abs(out.cpu().numpy() - ref["image"]).max() <= TOL_FWD
 
 
 def test_graph_replay(cuda_device):
@@ -137,11 +142,11 @@ def test_graph_replay(cuda_device):
     sig = wl.point_sigmas(16, im.N, 0.4, 1.2)
     P, V, S = to_dev(im.points, cuda_device), to_dev(im.values, cuda_device), to_dev(sig, cuda_device)
     out = torch.empty((64, 64, 3), device=cuda_device)
-    ref = g.interpolate_pp(P, V, S, 1.2, 64, 64, radius_sigmas=4.0).cpu().numpy()
+    ref = g.interpolate_pp(P, V, S, 1.2, 64, 64, radius_sigmas=4.0, mode="truncated").cpu().numpy()
     for step in range(3):
         S.mul_(0.99 if step else 1.0)   # new contents, same buffers: replay reads them
-        got = g.interpolate_pp(P, V, S, 1.2, 64, 64, radius_sigmas=4.0, graph=True, out=out)
-        want = g.interpolate_pp(P, V, S, 1.2, 64, 64, radius_sigmas=4.0)
+        got = g.interpolate_pp(P, V, S, 1.2, 64, 64, radius_sigmas=4.0, graph=True, out=out, mode="truncated")
+        want = g.interpolate_pp(P, V, S, 1.2, 64, 64, radius_sigmas=4.0, mode="truncated")
         torch.cuda.synchronize()
         np.testing.assert_allclose(got.cpu().numpy(), want.cpu().numpy(), rtol=0, atol=2e-6)
     assert np.abs(out.cpu().numpy() - ref).max() > 0   # the sigmas did change the image
@@ -165,9 +170,9 @@ def gpu_grads(im, sig, bound, g_up, dev, k, **kw):
     import torch
     G = gmi()
     P, V, S = to_dev(im.points, dev), to_dev(im.values, dev), to_dev(sig, dev)
-    img, den = G.interpolate_pp(P, V, S, bound, im.H, im.W, radius_sigmas=k, return_aux=True, **kw)
+    img, den = G.interpolate_pp(P, V, S, bound, im.H, im.W, radius_sigmas=k, return_aux=True, **kw, mode="truncated")
     gp, gv, gs = G.interpolate_backward_pp(P, V, S, bound, im.H, im.W, img, den, to_dev(g_up, dev),
-                                           radius_sigmas=k, check=True, **kw)
+                                           radius_sigmas=k, check=True, **kw, mode="truncated")
     torch.cuda.synchronize()
     return gp.cpu().numpy(), gv.cpu().numpy(), gs.cpu().numpy()
 
@@ -210,9 +215,9 @@ def test_backward_is_deterministic(cuda_device):
     sig = wl.point_sigmas(19, im.N, 0.5, 1.5)
     g = to_dev(np.random.default_rng(18).standard_normal((64, 64, 3)).astype(np.float32), cuda_device)
     P, V, S = to_dev(im.points, cuda_device), to_dev(im.values, cuda_device), to_dev(sig, cuda_device)
-    img, den = G.interpolate_pp(P, V, S, 1.5, 64, 64, radius_sigmas=3.0, return_aux=True)
-    a = G.interpolate_backward_pp(P, V, S, 1.5, 64, 64, img, den, g, radius_sigmas=3.0)
-    b = G.interpolate_backward_pp(P, V, S, 1.5, 64, 64, img, den, g, radius_sigmas=3.0)
+    img, den = G.interpolate_pp(P, V, S, 1.5, 64, 64, radius_sigmas=3.0, return_aux=True, mode="truncated")
+    a = G.interpolate_backward_pp(P, V, S, 1.5, 64, 64, img, den, g, radius_sigmas=3.0, mode="truncated")
+    b = G.interpolate_backward_pp(P, V, S, 1.5, 64, 64, img, den, g, radius_sigmas=3.0, mode="truncated")
     torch.cuda.synchronize()
     for x, y in zip(a, b):
         assert torch.equal(x, y)
@@ -228,7 +233,7 @@ def test_autograd_op(cuda_device):
     P = to_dev(im.points, cuda_device).requires_grad_(True)
     V = to_dev(im.values, cuda_device).requires_grad_(True)
     S = to_dev(sig, cuda_device).requires_grad_(True)
-    img = G.gmi_interpolate_pp(P, V, S, hi, H, W, radius_sigmas=k)
+    img = G.gmi_interpolate_pp(P, V, S, hi, H, W, radius_sigmas=k, mode="truncated")
     (img * to_dev(g, cuda_device)).sum().backward()
     ref = oracle.backward_pp(im.points, im.values, sig, H, W, g, mode=oracle.TRUNCATED, k=k)
     assert_grads((P.grad.cpu().numpy(), V.grad.cpu().numpy(), S.grad.cpu().numpy()), ref)
@@ -242,11 +247,11 @@ def test_sigma_descent_lowers_loss(cuda_device):
     im = wl.tiny_random(20, 400, 48, 48, C=3, sigma=2.0)
     P, V = to_dev(im.points, cuda_device), to_dev(im.values, cuda_device)
     target = G.interpolate_pp(P, V, to_dev(np.full(im.N, 1.0, np.float32), cuda_device), 2.0, 48, 48,
-                              radius_sigmas=4.0).detach()
+                              radius_sigmas=4.0, mode="truncated").detach()
     S = to_dev(wl.point_sigmas(21, im.N, 0.6, 1.8), cuda_device).requires_grad_(True)
     losses = []
     for _ in range(5):
-        img = G.gmi_interpolate_pp(P, V, S, 2.0, 48, 48, radius_sigmas=4.0)
+        img = G.gmi_interpolate_pp(P, V, S, 2.0, 48, 48, radius_sigmas=4.0, mode="truncated")
         loss = ((img - target) ** 2).mean()
         losses.append(float(loss.detach()))
         S.grad = None
@@ -298,10 +303,10 @@ def test_aniso_range_reported(cuda_device):
         sxy = np.full((im.N, 2), 0.5, np.float32)
         sxy[9, ax] = bad
         with pytest.raises(g.GmiError) as e:
-            g.interpolate_pp(P, V, to_dev(sxy, cuda_device), 1.0, 12, 12, check=True)
+            g.interpolate_pp(P, V, to_dev(sxy, cuda_device), 1.0, 12, 12, check=True, mode="truncated")
         assert e.value.status == status, (ax, bad, e.value.status)
     with pytest.raises(ValueError):
-        g.interpolate_pp(P, V, to_dev(np.full((im.N, 4), 0.5, np.float32), cuda_device), 1.0, 12, 12)
+        g.interpolate_pp(P, V, to_dev(np.full((im.N, 4), 0.5, np.float32), cuda_device), 1.0, 12, 12, mode="truncated")
 
 
 def test_aniso_full_size_sampled(cuda_device):
@@ -339,7 +344,7 @@ def test_aniso_autograd_op(cuda_device):
     P = to_dev(im.points, cuda_device).requires_grad_(True)
     V = to_dev(im.values, cuda_device).requires_grad_(True)
     S = to_dev(sxy, cuda_device).requires_grad_(True)
-    img = G.gmi_interpolate_pp(P, V, S, hi, H, W, radius_sigmas=k)
+    img = G.gmi_interpolate_pp(P, V, S, hi, H, W, radius_sigmas=k, mode="truncated")
     (img * to_dev(g, cuda_device)).sum().backward()
     ref = oracle.backward_aniso(im.points, im.values, sxy, H, W, g, mode=oracle.TRUNCATED, k=k)
     ref["sigmas"] = ref["sigmas_xy"]
@@ -390,15 +395,15 @@ def test_cov_range_reported(cuda_device):
         cov = np.tile(np.float32([0.5, 0.6, 0.3]), (im.N, 1))
         cov[11, ax] = bad
         with pytest.raises(g.GmiError) as e:
-            g.interpolate_pp(P, V, to_dev(cov, cuda_device), 1.0, 12, 12, check=True)
+            g.interpolate_pp(P, V, to_dev(cov, cuda_device), 1.0, 12, 12, check=True, mode="truncated")
         assert e.value.status == status, (ax, bad, e.value.status)
     # sx = sy = bound with rho = 0.5: inside the box, but the ellipse's major
     # axis reaches k sqrt(1.5) bound, past the search radius
     cov = np.tile(np.float32([1.0, 1.0, 0.5]), (im.N, 1))
     with pytest.raises(g.GmiError) as e:
-        g.interpolate_pp(P, V, to_dev(cov, cuda_device), 1.0, 12, 12, check=True)
+        g.interpolate_pp(P, V, to_dev(cov, cuda_device), 1.0, 12, 12, check=True, mode="truncated")
     assert e.value.status == 1
-    g.interpolate_pp(P, V, to_dev(cov, cuda_device), wl.cov_bound(cov), 12, 12, check=True)
+    g.interpolate_pp(P, V, to_dev(cov, cuda_device), wl.cov_bound(cov), 12, 12, check=True, mode="truncated")
 
 
 def test_cov_full_size_sampled(cuda_device):
@@ -440,10 +445,10 @@ def test_cov_backward_variants_and_determinism(cuda_device):
     for variant in (2, 3):
         assert_grads(gpu_grads(im, cov, bound, g, cuda_device, k, variant=variant), ref)
     P, V, S = to_dev(im.points, cuda_device), to_dev(im.values, cuda_device), to_dev(cov, cuda_device)
-    img, den = G.interpolate_pp(P, V, S, bound, H, W, radius_sigmas=k, return_aux=True)
+    img, den = G.interpolate_pp(P, V, S, bound, H, W, radius_sigmas=k, return_aux=True, mode="truncated")
     gg = to_dev(g, cuda_device)
-    a = G.interpolate_backward_pp(P, V, S, bound, H, W, img, den, gg, radius_sigmas=k)
-    b = G.interpolate_backward_pp(P, V, S, bound, H, W, img, den, gg, radius_sigmas=k)
+    a = G.interpolate_backward_pp(P, V, S, bound, H, W, img, den, gg, radius_sigmas=k, mode="truncated")
+    b = G.interpolate_backward_pp(P, V, S, bound, H, W, img, den, gg, radius_sigmas=k, mode="truncated")
     torch.cuda.synchronize()
     for x, y in zip(a, b):
         assert torch.equal(x, y)
@@ -458,7 +463,7 @@ def test_cov_autograd_op(cuda_device):
     P = to_dev(im.points, cuda_device).requires_grad_(True)
     V = to_dev(im.values, cuda_device).requires_grad_(True)
     S = to_dev(cov, cuda_device).requires_grad_(True)
-    img = G.gmi_interpolate_pp(P, V, S, wl.cov_bound(cov), H, W, radius_sigmas=k)
+    img = G.gmi_interpolate_pp(P, V, S, wl.cov_bound(cov), H, W, radius_sigmas=k, mode="truncated")
     (img * to_dev(g, cuda_device)).sum().backward()
     ref = oracle.backward_cov(im.points, im.values, cov, H, W, g, mode=oracle.TRUNCATED, k=k)
     ref["sigmas"] = ref["cov"]
