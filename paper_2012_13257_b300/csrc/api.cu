@@ -19,6 +19,7 @@ cudaError_t launch_near(const KArgs& a, int mth, int mtw, bool trunc, int ppk, i
 cudaError_t launch_near_staged(const KArgs& a, int mth, int mtw, bool trunc, int grid, cudaStream_t s);
 cudaError_t launch_pp_exact_forward(const KArgs& a, int mth, int mtw, int ppk, cudaStream_t s);
 void warm_pp_exact(int C, int ppk);
+void warm_scatter_plan();
 int staged_blocks_per_sm(int mth, int mtw, int C, bool trunc);
 cudaError_t launch_scatter_plan(const KArgs& a, bool trunc, int n_scatter, cudaStream_t s);
 int near_blocks_per_sm(int mth, int mtw, int C, bool trunc, int ppk);
@@ -254,6 +255,7 @@ void warm_near_caches(int mth, int mtw, int C, bool trunc, int ppk, int gather) 
     warm_pp_exact(C, ppk);
     return;
   }
+  warm_scatter_plan();
   if (uses_staged_gather(gather, ppk)) staged_blocks_per_sm(mth, mtw, C, trunc);
   else near_blocks_per_sm(mth, mtw, C, trunc, ppk);
 }

@@ -5,11 +5,12 @@
 // section 2) is what makes spatial binning sufficient.
 //
 //   bin_count    key = (clamped bin row, bin column); rank = atomic slot in the
-//                bin; flags non-finite inputs, per-point sigmas out of range
+//                bin; flags non-finite positions, per-point sigmas out of range
 //                and bins holding out-of-frame points
 //   scan_partial per-block sums of the bin counts
 //   scan_final   exclusive scan of the counts, in place, into bin offsets
-//   bin_scatter  bin-sorted copies of positions (float2) and colours (float4)
+//   bin_scatter  bin-sorted copies of positions (float2) and colours (float4);
+//                flags non-finite colours
 #include "bin_body.cuh"
 
 namespace gmi {
@@ -45,8 +46,7 @@ __global__ void __launch_bounds__(256) bin_count_kernel(KArgs a_in) {
     const long long i = (ch - g.ch_base) * kChunk + threadIdx.x;
     if (i < g.n) {
       float2 p = reinterpret_cast<const float2*>(g.points)[i];
-      bool fin = isfinite(p.x) && isfinite(p.y);
-      for (int c = 0; c < a.C; ++c) fin = fin && isfinite(g.values[i * a.C + c]);
+      bool fin = isfinite(p.x) && isfinite(p.y);   // (the colours are checked by the scatter, which reads them)
       if (g.sigmas && !sigmas_ok(g, g.sigmas + g.pp_kind * i, fin)) bad_sigma = 1;
       if (!fin) bad = 1;
       long long bin;

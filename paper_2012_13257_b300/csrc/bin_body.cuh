@@ -14,9 +14,42 @@ static __device__ __forceinline__ void point_bin(const ImageGeom& g, float x, fl
   oob = !(x >= 0.0f && x < (float)g.W && y >= 0.0f && y < (float)g.H);
 }
 
+// Scatter of a single image with one shared sigma: the image's geometry
+// read once, nothing but the copies per point.
+static __device__ __forceinline__ void scatter_single(const KArgs& a, int nblocks, int block) {
+  const ImageGeom g = a.g0;
+  bool fin = true;
+  for (long long ch = block; ch < a.ch_total; ch += nblocks) {
+    const long long i = ch * kChunk + threadIdx.x;
+    if (i < g.n) {
+      const float2 p = reinterpret_cast<const float2*>(g.points)[i];
+      long long bin;
+      bool oob;
+      point_bin(g, p.x, p.y, bin, oob);
+      const unsigned dst = a.w.off[bin] + a.w.rank[i];
+      float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
+      const float* v = g.values + i * a.C;
+      c.x = v[0];
+      if (a.C > 1) c.y = v[1];
+      if (a.C > 2) c.z = v[2];
+      if (a.C > 3) c.w = v[3];
+      fin = fin && isfinite(c.x) && isfinite(c.y) && isfinite(c.z) && isfinite(c.w);
+      a.w.sxy[dst] = p;
+      a.w.sval[dst] = c;
+      a.w.perm[dst] = (unsigned)i;
+    }
+  }
+  if (__any_sync(0xffffffffu, !fin) && (threadIdx.x & 31) == 0) atomicOr(&a.w.status[kStatusErr], ST_NONFINITE);
+}
+
 // Scatter body: `nblocks` blocks stride over the chunks; this block is number
 // `block` of them.
 static __device__ __forceinline__ void bin_scatter_body(const KArgs& a, int nblocks, int block) {
+  if (!a.w.table && !a.g0.sigmas) {
+    scatter_single(a, nblocks, block);
+    return;
+  }
+  bool fin = true;
   for (long long ch = block; ch < a.ch_total; ch += nblocks) {
     const int img = find_image<0>(a, ch);
     const ImageGeom g = a.w.table ? a.w.table[img] : a.g0;   // a copy: no address of a local struct
@@ -34,6 +67,7 @@ static __device__ __forceinline__ void bin_scatter_body(const KArgs& a, int nblo
       if (a.C > 1) c.y = v[1];
       if (a.C > 2) c.z = v[2];
       if (a.C > 3) c.w = v[3];
+      fin = fin && isfinite(c.x) && isfinite(c.y) && isfinite(c.z) && isfinite(c.w);
       a.w.sxy[dst] = p;
       a.w.sval[dst] = c;
       a.w.perm[dst] = (unsigned)i;
@@ -54,6 +88,7 @@ static __device__ __forceinline__ void bin_scatter_body(const KArgs& a, int nblo
       if ((threadIdx.x & 31) == 0) atomicMax(&a.w.status[kLaMax], __float_as_uint(la));
     }
   }
+  if (__any_sync(0xffffffffu, !fin) && (threadIdx.x & 31) == 0) atomicOr(&a.w.status[kStatusErr], ST_NONFINITE);
 }
 
 }  // namespace gmi

@@ -103,8 +103,52 @@ __device__ float near_bound(const KArgs& a, const ImageGeom& g, int x0, int y0, 
     }
   };
 
-  // ring 0: the micro-tile's own bins; in dense regions they bound every pixel
-  for (int by = by0; by <= by1; ++by) scan_row(by, bx0, bx1);
+  // ring 0: the micro-tile's own bins; in dense regions they bound every
+  // pixel.  With bins of two or more pixels they are at most RR rows of RC
+  // bins, and every offset and flag of the ring is loaded in one round before
+  // any is folded; 1-px bins walk the rows.
+  constexpr int RR = MTH / 2 + 1, RC = MTW / 2 + 1;
+  if (by1 - by0 < RR && bx1 - bx0 < RC) {
+    unsigned o[RR][RC + 1];
+    unsigned char fl[RR][RC];
+#pragma unroll
+    for (int r = 0; r < RR; ++r) {
+      const bool rin = by0 + r <= by1;
+      const long long rowb = g.bin_base + (long long)(by0 + r) * g.nbx + bx0;
+#pragma unroll
+      for (int c = 0; c <= RC; ++c) o[r][c] = (rin && bx0 + c <= bx1 + 1) ? __ldg(&a.w.off[rowb + c]) : 0u;
+#pragma unroll
+      for (int c = 0; c < RC; ++c) fl[r][c] = (rin && bx0 + c <= bx1) ? __ldg(&a.w.oob[rowb + c]) : (unsigned char)1;
+    }
+#pragma unroll
+    for (int rb = 0; rb < RR; ++rb) {
+      if (by0 + rb > by1) break;
+      const int by = by0 + rb;
+      float cy[MTH];
+#pragma unroll
+      for (int r = 0; r < MTH; ++r) {
+        const float q = yq0 + (float)r;
+        const float d0 = q - (float)by * bf, d1 = q - (float)(by + 1) * bf;
+        cy[r] = fmaxf(d0 * d0, d1 * d1);
+      }
+#pragma unroll
+      for (int c = 0; c < RC; ++c) {
+        if (bx0 + c > bx1) break;
+        if (!(o[rb][c + 1] > o[rb][c] && fl[rb][c] == 0)) continue;
+        const int bx = bx0 + c;
+#pragma unroll
+        for (int j = 0; j < MTW; ++j) {
+          const float q = xq0 + (float)j;
+          const float d0 = q - (float)bx * bf, d1 = q - (float)(bx + 1) * bf;
+          const float cx = fmaxf(d0 * d0, d1 * d1);
+#pragma unroll
+          for (int r = 0; r < MTH; ++r) best[r][j] = fminf(best[r][j], cx + cy[r]);
+        }
+      }
+    }
+  } else {
+    for (int by = by0; by <= by1; ++by) scan_row(by, bx0, bx1);
+  }
   {
     float u = 0.0f;
 #pragma unroll
@@ -173,56 +217,74 @@ __device__ float near_bound(const KArgs& a, const ImageGeom& g, int x0, int y0, 
   return INFINITY;
 }
 
-// The staged gather's plan for warp tile wt (its first work item): the
-// window bin rows, each row's union segment over the warp's threads (the
-// warp tile's rectangle with the largest radius, a superset of every
-// thread's segment), its place in the warp's staging buffer, and each
-// thread's non-empty segments as indices of the staged copy.  The gather
-// then issues its bulk copies after one round of loads.  A split tile, or a
-// window larger than the buffer, is marked invalid (the gather sets such
-// items up itself).  `act`: the thread's micro-tile takes part (in the image,
-// not far field); R2 its squared radius.
-template <int MTH, int MTW>
-__device__ void tile_stage_plan(const KArgs& a, const ImageGeom& g, long long wt, bool act, float R2, int x0, int y0,
-                                int nx, int ny, unsigned S) {
-  constexpr int CAP = StageCap<MTH, MTW>::value;
-  const unsigned full = 0xffffffffu;
-  const int lane = threadIdx.x & 31;
-  TilePlanRec* rec = a.w.tplan + wt;
+// What the plan loads for one warp tile in a single round: every thread's
+// window row segments (its first kPassRows bin rows) and, for the staged
+// gather, the warp window's union rows (lane r: row r).
+struct PlanLoads {
   LaneWin w;
+  unsigned segs[kPassRows], sege[kPassRows];   // this thread's rows: [start, end) of the sorted arrays
+  unsigned S0, E0;                             // union row `lane`
+  int wy_lo, rows;                             // the warp window's bin rows
+};
+
+template <int MTH, int MTW>
+__device__ __forceinline__ void plan_loads(const KArgs& a, const ImageGeom& g, long long wt, bool act, float R2,
+                                           int x0, int y0, int nx, int ny, PlanLoads& P) {
+  const int lane = threadIdx.x & 31;
   int my_lo = INT_MAX, my_hi = INT_MIN;
+  P.w.by_lo = 0;
+  P.w.by_hi = -1;
   if (act) {
-    w = lane_window(g, x0, y0, nx, ny, R2);
-    my_lo = w.by_lo;
-    my_hi = w.by_hi;
+    P.w = lane_window(g, x0, y0, nx, ny, R2);
+    my_lo = P.w.by_lo;
+    my_hi = P.w.by_hi;
   }
-  const int wy_lo = warp_min(my_lo), wy_hi = warp_max(my_hi);
-  const int rows = wy_hi >= wy_lo ? wy_hi - wy_lo + 1 : 0;
-  bool valid = S == 1 && rows > 0 && rows <= kPassRows;
-  unsigned total = 0;
-  if (valid) {
+  P.wy_lo = warp_min(my_lo);
+  const int wy_hi = warp_max(my_hi);
+  P.rows = wy_hi >= P.wy_lo ? wy_hi - P.wy_lo + 1 : 0;
+  P.S0 = P.E0 = 0u;
+  if (a.w.tplan && P.rows > 0 && P.rows <= kPassRows) {
+    // the warp tile's pixel rectangle (clipped to the image) with the largest
+    // radius of its threads: a superset of every thread's segment per row
     const float R2w = warp_maxf(act ? R2 : 0.0f);
     const unsigned lt = (unsigned)(wt - g.wt_base);
     const int X0 = (int)(lt % (unsigned)g.wtx) * 8 * MTW, Y0 = (int)(lt / (unsigned)g.wtx) * 4 * MTH;
     const LaneWin ww = lane_window(g, X0, Y0, min(8 * MTW, g.W - X0), min(4 * MTH, g.H - Y0), R2w);
-    unsigned S0 = 0u, E0 = 0u;
-    if (lane < rows) {
+    if (lane < P.rows) {
       int bxw_lo, bxw_hi;
       float hxw;
-      row_bins(g, ww, wy_lo + lane, bxw_lo, bxw_hi, hxw);
-      const long long rowb = g.bin_base + (long long)(wy_lo + lane) * g.nbx;
-      S0 = __ldg(&a.w.off[rowb + bxw_lo]);
-      E0 = __ldg(&a.w.off[rowb + bxw_hi + 1]);
+      row_bins(g, ww, P.wy_lo + lane, bxw_lo, bxw_hi, hxw);
+      const long long rowb = g.bin_base + (long long)(P.wy_lo + lane) * g.nbx;
+      P.S0 = __ldg(&a.w.off[rowb + bxw_lo]);
+      P.E0 = __ldg(&a.w.off[rowb + bxw_hi + 1]);
     }
-    unsigned segs[kPassRows], sege[kPassRows];
+  }
 #pragma unroll
-    for (int k = 0; k < kPassRows; ++k) {
-      segs[k] = sege[k] = 0u;
-      if (act && w.by_lo + k <= w.by_hi) row_segment(a, g, w, w.by_lo + k, segs[k], sege[k]);
-    }
+  for (int k = 0; k < kPassRows; ++k) {
+    P.segs[k] = P.sege[k] = 0u;
+    if (act && P.w.by_lo + k <= P.w.by_hi) row_segment(a, g, P.w, P.w.by_lo + k, P.segs[k], P.sege[k]);
+  }
+}
+
+// The staged gather's plan for warp tile wt (its first work item), from the
+// loads above: the window bin rows, each row's union segment over the warp's
+// threads, its place in the warp's staging buffer, and each thread's
+// non-empty segments as indices of the staged copy.  The gather then issues
+// its bulk copies after one round of loads.  A split tile, or a window larger
+// than the buffer, is marked invalid (the gather sets such items up itself).
+// `act`: the thread's micro-tile takes part (in the image, not far field).
+template <int MTH, int MTW>
+__device__ void tile_stage_plan(const KArgs& a, long long wt, bool act, const PlanLoads& P, unsigned S) {
+  constexpr int CAP = StageCap<MTH, MTW>::value;
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  TilePlanRec* rec = a.w.tplan + wt;
+  bool valid = S == 1 && P.rows > 0 && P.rows <= kPassRows;
+  unsigned total = 0;
+  if (valid) {
     // records [S0, E0) of row r widened to even indices (16-byte boundaries
     // for the position copies), placed one after the other
-    const unsigned need = E0 > S0 ? ((E0 + 1u) & ~1u) - (S0 & ~1u) : 0u;
+    const unsigned need = P.E0 > P.S0 ? ((P.E0 + 1u) & ~1u) - (P.S0 & ~1u) : 0u;
     unsigned incl = min(need, (unsigned)CAP + 1u);
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -233,21 +295,21 @@ __device__ void tile_stage_plan(const KArgs& a, const ImageGeom& g, long long wt
     valid = total <= (unsigned)CAP;
     if (valid) {
       const unsigned abase = incl - need;
-      const unsigned B = abase + (S0 & 1u);   // staged index of record S0
+      const unsigned B = abase + (P.S0 & 1u);   // staged index of record S0
       unsigned nseg = 0;
 #pragma unroll
       for (int k = 0; k < kPassRows; ++k) {
-        const bool v = act && w.by_lo + k <= w.by_hi;
-        const int r = v ? w.by_lo + k - wy_lo : 0;
-        const unsigned Sr = __shfl_sync(full, S0, r), Br = __shfl_sync(full, B, r);
-        const unsigned i0 = Br + (segs[k] - Sr), i1 = i0 + (sege[k] - segs[k]);
+        const bool v = act && P.w.by_lo + k <= P.w.by_hi;
+        const int r = v ? P.w.by_lo + k - P.wy_lo : 0;
+        const unsigned Sr = __shfl_sync(full, P.S0, r), Br = __shfl_sync(full, B, r);
+        const unsigned i0 = Br + (P.segs[k] - Sr), i1 = i0 + (P.sege[k] - P.segs[k]);
         if (v && i0 < i1) rec->seg[nseg++][lane] = i0 | (i1 << 16);
       }
       rec->lane[lane] = nseg | (act ? 0x80000000u : 0u);
-      if (lane < rows) rec->rowc[lane] = make_uint2(S0 & ~1u, need | (abase << 16));
+      if (lane < P.rows) rec->rowc[lane] = make_uint2(P.S0 & ~1u, need | (abase << 16));
     }
   }
-  if (lane == 0) rec->hdr = make_uint4((unsigned)rows | (valid ? 0x80000000u : 0u), total, (unsigned)wy_lo, 0u);
+  if (lane == 0) rec->hdr = make_uint4((unsigned)P.rows | (valid ? 0x80000000u : 0u), total, (unsigned)P.wy_lo, 0u);
 }
 
 // Plan: one warp per warp tile.  Each thread bounds the nearest squared
@@ -255,7 +317,8 @@ __device__ void tile_stage_plan(const KArgs& a, const ImageGeom& g, long long wt
 // micro-tiles for the far kernel, and counts its candidates within
 // R = sqrt(U + k^2 sigma^2); the tile is cut into S = ceil(max / kSplitTarget)
 // work items, so that no single thread walks thousands of candidates while
-// the rest of the GPU idles.
+// the rest of the GPU idles.  The count and the staging plan come from one
+// round of loads.
 template <int MTH, int MTW>
 __device__ void near_plan_body(const KArgs& a, int trunc, long long wt) {
   const unsigned full = 0xffffffffu;
@@ -288,14 +351,18 @@ __device__ void near_plan_body(const KArgs& a, int trunc, long long wt) {
     }
   }
   a.w.ubound[wt * 32 + lane] = far ? INFINITY : U;
+  const bool act = active && !far;
+  PlanLoads P;
+  plan_loads<MTH, MTW>(a, g, wt, act, U + g.r2k, x0, y0, nx, ny, P);
   unsigned cnt = 0;
-  if (active && !far) {
-    const LaneWin w = lane_window(g, x0, y0, nx, ny, U + g.r2k);
-#pragma unroll 4
-    for (int by = w.by_lo; by <= w.by_hi; ++by) {
-      unsigned s, e;
-      row_segment(a, g, w, by, s, e);
-      cnt += e - s;
+#pragma unroll
+  for (int k = 0; k < kPassRows; ++k) cnt += P.sege[k] - P.segs[k];
+  if (act) {
+    // rows past the first kPassRows (wide windows)
+    for (int by = P.w.by_lo + kPassRows; by <= P.w.by_hi; ++by) {
+      unsigned s0, e0;
+      row_segment(a, g, P.w, by, s0, e0);
+      cnt += e0 - s0;
     }
   }
 #pragma unroll
@@ -319,7 +386,7 @@ __device__ void near_plan_body(const KArgs& a, int trunc, long long wt) {
       for (int k = 0; k < na / 4; ++k) z[k] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
   }
-  if (a.w.tplan) tile_stage_plan<MTH, MTW>(a, g, wt, active && !far, U + g.r2k, x0, y0, nx, ny, S);
+  if (a.w.tplan) tile_stage_plan<MTH, MTW>(a, wt, act, P, S);
   // the tile's first item sits at index wt (so a near-kernel warp can start on
   // warp tile t without reading the queue first); its other splits follow
   // all first items
@@ -671,6 +738,22 @@ static cudaError_t launch_near_mt(const KArgs& a, int mode, int grid, cudaStream
   }
 }
 
+// Resident 256-thread blocks of the fused scatter + plan kernel on the whole
+// device (the 4 x 4 instantiation stands for all: they share the register
+// bound), cached.
+static int scatter_plan_slots() {
+  static const int n = [] {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, scatter_plan_kernel<4, 4, false>, 256, 0) != cudaSuccess ||
+        b < 1)
+      b = 1;
+    return b * device_sm_count();
+  }();
+  return n;
+}
+
+void warm_scatter_plan() { scatter_plan_slots(); }
+
 // n_scatter scatter blocks (0: scatter not needed) followed by the plan's blocks.
 cudaError_t launch_scatter_plan(const KArgs& a, bool trunc, int n_scatter, cudaStream_t s) {
   // one block per 8 warp tiles; batched (capacity-sized): at most 64 blocks
@@ -678,6 +761,13 @@ cudaError_t launch_scatter_plan(const KArgs& a, bool trunc, int n_scatter, cudaS
   const bool stride = a.totals != nullptr;
   const long long need = (a.wt_total + 7) / 8;
   const int n_plan = (int)(stride ? std::min<long long>(need, 64LL * device_sm_count()) : need);
+  if (!stride && n_scatter > 0) {
+    // single image: the scatter's blocks take the resident slots the plan's
+    // blocks leave free (one wave), each looping over its chunks; the plan's
+    // blocks, the longer chains, then never wait for a slot
+    const int slots = scatter_plan_slots();
+    n_scatter = std::min(n_scatter, std::max(device_sm_count(), slots - n_plan));
+  }
   const unsigned blocks = (unsigned)(n_scatter + n_plan);
   const int t = trunc ? 1 : 0;
   if (stride) {
