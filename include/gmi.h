@@ -346,6 +346,35 @@ gmi_status gmi_workspace_layout(int64_t N, int C, int H, int W, const gmi_params
 gmi_status gmi_workspace_status(const void* workspace, gmi_stream_t stream);
 
 /*
+ * Memory-safety checks of a checked build (no counterpart in the paper; the
+ * library built with -DGMI_CHECKED, libgmi_checked.so, stands in for a
+ * sanitizer).  Such a build tests every index it derives from a counter, a
+ * queue entry or another kernel's output before using it (a failed test
+ * skips the access and records where), and leaves a 256-byte guard area
+ * after every workspace region, written with a known pattern at the start of
+ * each call.  Its workspaces are larger: size them with this build's
+ * gmi_workspace_size.  Other builds return GMI_ERR_UNSUPPORTED from both calls
+ * and 0 from gmi_is_checked_build.
+ *
+ * gmi_check_workspace: after a single-image call (forward, backward, per
+ * point) with the same N, C, H, W and params on `workspace` (ws_bytes as
+ * given to that call), tests the guard areas on `stream`, synchronises it
+ * and returns GMI_OK when no bounds check failed and every guard is intact,
+ * else GMI_ERR_INTERNAL.  report (NULL or uint32_t[4]): the status bits, the
+ * first failed check's site (CheckSite in the sources) and index, the first
+ * overwritten guard's number + 1.
+ * gmi_batch_check_workspace: the same for a batched plan's workspace after
+ * a batched call.
+ */
+struct gmi_batch_plan;   /* opaque, see gmi_batch_plan_create */
+gmi_status gmi_check_workspace(int64_t N, int C, int H, int W, const gmi_params* p,
+                               void* workspace, size_t ws_bytes, gmi_stream_t stream,
+                               uint32_t* report);
+gmi_status gmi_batch_check_workspace(const struct gmi_batch_plan* plan, gmi_stream_t stream,
+                                     uint32_t* report);
+int gmi_is_checked_build(void);
+
+/*
  * Autotuner core (the batching pattern's choice of micro-tile and bin edge;
  * no counterpart in the paper): times gmi_forward on the caller's problem for
  * every micro-tile variant (GMI_VARIANT_MT4x4, MT4x8, MT2x4) and every bin

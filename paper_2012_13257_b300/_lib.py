@@ -10,7 +10,10 @@ import ctypes
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libgmi.so")
+# GMI_CHECKED=1 in the environment loads the checked build (bounds checks
+# that record instead of trapping, guard areas after workspace regions)
+CHECKED = os.environ.get("GMI_CHECKED", "") not in ("", "0")
+LIB_PATH = os.path.join(HERE, "libgmi_checked.so" if CHECKED else "libgmi.so")
 
 GMI_OK = 0
 STATUS_NAMES = {
@@ -102,6 +105,10 @@ SIGNATURES = {
     "gmi_backward_cov": (_int, [_vp, _vp, _vp, _i64, _int, _int, _int, ctypes.POINTER(Params), _vp, _vp,
                                 _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "gmi_workspace_status": (_int, [_vp, _vp]),
+    "gmi_check_workspace": (_int, [_i64, _int, _int, _int, ctypes.POINTER(Params), _vp, ctypes.c_size_t, _vp,
+                                   ctypes.POINTER(ctypes.c_uint32)]),
+    "gmi_batch_check_workspace": (_int, [_vp, _vp, ctypes.POINTER(ctypes.c_uint32)]),
+    "gmi_is_checked_build": (_int, []),
     "gmi_workspace_layout": (_int, [_i64, _int, _int, _int, ctypes.POINTER(Params), ctypes.POINTER(WsLayout)]),
     "gmi_forward_noalloc": (_int, [_vp, _vp, _i64, _int, _int, _int, ctypes.POINTER(Params), _vp, _vp, _vp,
                                    _vp]),
@@ -143,7 +150,7 @@ def load():
     global _lib
     if _lib is None:
         if not os.path.exists(LIB_PATH):
-            raise ImportError("libgmi.so is not built (run paper_2012_13257_b300/build.py or "
+            raise ImportError(os.path.basename(LIB_PATH) + " is not built (run paper_2012_13257_b300/build.py or "
                               "__graft_entry__.build()); there is no non-CUDA fallback")
         lib = ctypes.CDLL(LIB_PATH)
         for name, (res, args) in SIGNATURES.items():

@@ -123,29 +123,40 @@ long long sat_jobs(const ImageGeom& g) { return (g.nbx + 1 + 31) / 32; }
 WsLayout ws_layout(long long n_total, long long nb_total, long long mt_total, long long wt_total,
                    long long sat_entries, size_t slot_bytes, long long extra_bytes, bool tile_plans) {
   WsLayout L;
+  L.guards.n = 0;
   size_t o = 0;
+  // the next region of `bytes` (256-byte aligned), and its guard area
+  auto region = [&](size_t bytes) {
+    const size_t at = o;
+    o = align_up(o + bytes, 256);
+    if (kGuardBytes > 0 && L.guards.n < kMaxGuards) {
+      L.guards.off[L.guards.n++] = o;
+      o += kGuardBytes;
+    }
+    return at;
+  };
   L.cap_items = (unsigned)std::min<long long>(wt_total * kSplitMax, 0x7fffffffLL);
   L.cap_slots = (unsigned)std::min<long long>(wt_total > 0 ? wt_total : 1, 0x7fffffffLL);
-  L.status = o; o = align_up(o + sizeof(unsigned) * kStatusWords, 256);
-  L.off = o;    o = align_up(o + sizeof(unsigned) * (size_t)(nb_total + 1) + 16, 256);   // (+ slack, as below)
-  L.oob = o;    o = align_up(o + (size_t)nb_total, 256);
-  L.tile_done = o; o = align_up(o + sizeof(unsigned) * (size_t)(wt_total > 0 ? wt_total : 1), 256);
+  L.status = region(sizeof(unsigned) * kStatusWords);
+  L.off = region(sizeof(unsigned) * (size_t)(nb_total + 1) + 16);   // (+ slack, as below)
+  L.oob = region((size_t)nb_total);
+  L.tile_done = region(sizeof(unsigned) * (size_t)(wt_total > 0 ? wt_total : 1));
   L.zero_end = o;                               // [0, zero_end) is cleared per call
-  L.rank = o;   o = align_up(o + sizeof(unsigned) * (size_t)n_total, 256);
+  L.rank = region(sizeof(unsigned) * (size_t)n_total);
   // (16 bytes of slack after each sorted array: the staged gather's bulk
   // copies widen their ranges to even indices, one record past the end at most)
-  L.sxy = o;    o = align_up(o + sizeof(float2) * (size_t)n_total + 16, 256);
-  L.sval = o;   o = align_up(o + sizeof(float4) * (size_t)n_total + 16, 256);
-  L.perm = o;   o = align_up(o + sizeof(unsigned) * (size_t)n_total, 256);
-  L.spp = o;    o = align_up(o + sizeof(float4) * (size_t)n_total, 256);
-  L.partials = o; o = align_up(o + sizeof(unsigned) * (size_t)((nb_total + kScanChunk - 1) / kScanChunk + 1), 256);
-  L.farq = o;   o = align_up(o + sizeof(uint2) * (size_t)(mt_total > 0 ? mt_total : 1), 256);
-  L.items = o;  o = align_up(o + sizeof(uint4) * (size_t)(L.cap_items > 0 ? L.cap_items : 1), 256);
-  L.slots = o;  o = align_up(o + slot_bytes * (size_t)L.cap_slots, 256);
-  L.ubound = o; o = align_up(o + sizeof(float) * 32u * (size_t)(wt_total > 0 ? wt_total : 1), 256);
-  L.sat = o;    o = align_up(o + sizeof(unsigned) * (size_t)(sat_entries > 0 ? sat_entries : 1), 256);
+  L.sxy = region(sizeof(float2) * (size_t)n_total + 16);
+  L.sval = region(sizeof(float4) * (size_t)n_total + 16);
+  L.perm = region(sizeof(unsigned) * (size_t)n_total);
+  L.spp = region(sizeof(float4) * (size_t)n_total);
+  L.partials = region(sizeof(unsigned) * (size_t)((nb_total + kScanChunk - 1) / kScanChunk + 1));
+  L.farq = region(sizeof(uint2) * (size_t)(mt_total > 0 ? mt_total : 1));
+  L.items = region(sizeof(uint4) * (size_t)(L.cap_items > 0 ? L.cap_items : 1));
+  L.slots = region(slot_bytes * (size_t)L.cap_slots);
+  L.ubound = region(sizeof(float) * 32u * (size_t)(wt_total > 0 ? wt_total : 1));
+  L.sat = region(sizeof(unsigned) * (size_t)(sat_entries > 0 ? sat_entries : 1));
   L.has_tplan = tile_plans;
-  L.tplan = o;  o = align_up(o + (tile_plans ? sizeof(TilePlanRec) * (size_t)(wt_total > 0 ? wt_total : 1) : 0), 256);
+  L.tplan = region(tile_plans ? sizeof(TilePlanRec) * (size_t)(wt_total > 0 ? wt_total : 1) : 0);
   L.extra = o;  o = align_up(o + (size_t)extra_bytes, 256);
   L.total = o;
   return L;
@@ -189,9 +200,16 @@ gmi_status run_bin_and_plan(KArgs& a, const WsLayout& L, void* ws, int mth, int 
   const int sms = device_sm_count();
   if (a.totals) {
     batch_clear_kernel<<<sms * 4, 256, 0, s>>>(a);
-  } else if (cudaMemsetAsync(ws, 0, L.zero_end, s) != cudaSuccess) {
-    return GMI_ERR_CUDA;
+  } else if (kGuardBytes == 0) {
+    if (cudaMemsetAsync(ws, 0, L.zero_end, s) != cudaSuccess) return GMI_ERR_CUDA;
+  } else {
+    // checked builds: the cleared regions one by one, around their guards
+    const size_t starts[4] = {L.status, L.off, L.oob, L.tile_done};
+    for (int k = 0; k < 4; ++k)
+      if (cudaMemsetAsync((char*)ws + starts[k], 0, L.guards.off[k] - starts[k], s) != cudaSuccess)
+        return GMI_ERR_CUDA;
   }
+  if (kGuardBytes > 0 && launch_canaries(ws, L.guards, false, a.w.status, s) != cudaSuccess) return GMI_ERR_CUDA;
   a.cap_items = L.cap_items;
   a.cap_slots = L.cap_slots;
   a.mth = mth;
@@ -272,7 +290,7 @@ gmi_status read_status(const void* ws, cudaStream_t s) {
   if (cudaMemcpy(&st, ws, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess) return GMI_ERR_CUDA;
   if (st & ST_NONFINITE) return GMI_ERR_NONFINITE;
   if (st & ST_SIGMA) return GMI_ERR_INVALID_ARG;
-  if (st & (ST_INTERNAL | ST_TIMEOUT)) return GMI_ERR_INTERNAL;
+  if (st & (ST_INTERNAL | ST_TIMEOUT | ST_BOUNDS | ST_CANARY)) return GMI_ERR_INTERNAL;
   return GMI_OK;
 }
 
@@ -323,6 +341,11 @@ static gmi_status forward_impl(const float* points, const float* values, const f
     if (den_out && cudaMemsetAsync(den_out, 0, px * sizeof(float), s) != cudaSuccess) return GMI_ERR_CUDA;
     if (shift_out && cudaMemsetAsync(shift_out, 0, px * sizeof(float), s) != cudaSuccess) return GMI_ERR_CUDA;
     if (cudaMemsetAsync(workspace, 0, sizeof(unsigned) * kStatusWords, s) != cudaSuccess) return GMI_ERR_CUDA;
+    if (kGuardBytes > 0) {   // checked builds: every guard written, as by any other call
+      Guards gx = L.guards;
+      if (!fwd_share) bwd_guards(N, C, H, W, L.extra, gx);
+      if (launch_canaries(workspace, gx, false, (unsigned*)workspace, s) != cudaSuccess) return GMI_ERR_CUDA;
+    }
     return (p->flags & GMI_FLAG_SYNC_CHECK) ? read_status(workspace, s) : GMI_OK;
   }
 
@@ -342,6 +365,14 @@ static gmi_status forward_impl(const float* points, const float* values, const f
   const bool trunc = p->mode == GMI_MODE_TRUNCATED;
   const int ppk = g.pp_kind == 3 ? 2 : (g.pp_kind ? 1 : 0);
   if (!uses_staged_gather(p->gather, ppk)) a.w.tplan = nullptr;   // the plan writes none
+  if (kGuardBytes > 0 && !fwd_share) {
+    // checked builds: the backward region's guards too, so that a check after
+    // any full-size call finds every guard written
+    Guards gx;
+    gx.n = 0;
+    bwd_guards(N, C, H, W, L.extra, gx);
+    if (launch_canaries(workspace, gx, false, a.w.status, s) != cudaSuccess) return GMI_ERR_CUDA;
+  }
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   if ((p->flags & GMI_FLAG_GRAPH) && !profile_on() && cudaStreamIsCapturing(s, &cap) == cudaSuccess &&
       cap == cudaStreamCaptureStatusNone) {

@@ -8,13 +8,34 @@
 
 namespace gmi {
 
+// Checked builds (-DGMI_CHECKED) leave a guard area of kGuardBytes after
+// every workspace region, filled with kCanary at the start of each call and
+// verified by gmi_check_workspace: a kernel writing past its region shows up
+// there.  Other builds leave no guards.
+#ifdef GMI_CHECKED
+constexpr size_t kGuardBytes = 256;
+#else
+constexpr size_t kGuardBytes = 0;
+#endif
+constexpr unsigned kCanary = 0xC0DEFACEu;
+constexpr int kMaxGuards = 24;
+struct Guards {
+  int n;
+  size_t off[kMaxGuards];   // byte offsets of the guard areas from the workspace start
+};
+
 // Byte offsets of the regions of a workspace.
 struct WsLayout {
   size_t status, off, oob, tile_done, zero_end, rank, sxy, sval, perm, spp, partials, farq, items, slots, ubound, sat,
       tplan, extra, total;
   bool has_tplan;
   unsigned cap_items, cap_slots;
+  Guards guards;   // after every region (checked builds); the first four follow the cleared regions
 };
+
+// Checked builds: writes (verify = false) or tests (verify = true, ST_CANARY
+// and the first bad guard's number + 1 in status[kBadGuard]) the guard areas.
+cudaError_t launch_canaries(void* ws, const Guards& g, bool verify, unsigned* status, cudaStream_t s);
 
 int device_sm_count();
 void variant_dims(int variant, int* mth, int* mtw);
@@ -48,9 +69,13 @@ bool uses_staged_gather(int gather, int ppk);
 void warm_near_caches(int mth, int mtw, int C, bool trunc, int ppk, int gather);
 
 // Stage timing (profile.cu): no-ops unless gmi_profile_enable(1) was called.
+// Every stage is also an NVTX range on the host thread that enqueues it
+// ("gmi.bin", "gmi.near", "gmi.far", "gmi.backward"), for ncu --nvtx filters
+// and timeline tools; without a tool attached the ranges cost nothing.
 struct ProfileMark {
   int stage;
   cudaEvent_t a, b;
+  bool range;   // an NVTX range was pushed
 };
 bool profile_on();
 ProfileMark profile_begin(int stage, cudaStream_t s);
@@ -86,5 +111,8 @@ gmi_status forward_in_share(const float* points, const float* values, int64_t N,
 // and where its regions start inside the extra block.
 long long bwd_extra_bytes(long long N, int C, int H, int W);
 void bind_bwd(DevWork& w, void* extra, long long N, int C, int H, int W, long long mt_total);
+// The guard areas of the backward's region (checked builds), appended to g
+// with offsets from the workspace start (extra_at: where the region starts).
+void bwd_guards(long long N, int C, int H, int W, size_t extra_at, Guards& g);
 
 }  // namespace gmi

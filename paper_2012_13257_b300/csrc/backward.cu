@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(256) bwd_prep_kernel(KArgs a_in, BwdArgs b) {
       const unsigned mt = (unsigned)((y / a.mth) * g.mtx + x / a.mtw);
       if (atomicOr(&a.w.fbflag[g.mt_base + mt], 1u) == 0u) {
         const unsigned q = atomicAdd(&a.w.status[kFbCount], 1u);
-        a.w.fbq[q] = make_uint2((unsigned)img, mt);
+        if (GMI_IN_BOUNDS(a.w, q, a.mt_total, CK_FBQ)) a.w.fbq[q] = make_uint2((unsigned)img, mt);
       }
     }
   }
@@ -362,7 +362,7 @@ __global__ void __launch_bounds__(32 * kFarWarps) bwd_fallback_kernel(KArgs a_in
     e = __shfl_sync(full, e, 0);
     if (e >= nq) break;
     const uint2 qe = a.w.fbq[e];
-    const int img = (int)qe.x;
+    const int img = GMI_IN_BOUNDS(a.w, qe.x, a.n_images, CK_FBQ) ? (int)qe.x : 0;
     const unsigned mt = qe.y;
     const ImageGeom g = a.w.table ? a.w.table[img] : a.g0;
     const BwdImage bi = bwd_image(b, img);
@@ -481,30 +481,46 @@ static int fallback_blocks_per_sm() {
   return n;
 }
 
-long long bwd_extra_bytes(long long N, int C, int H, int W) {
+// The backward's region: per-pixel plane, fallback flags and queue, sigma
+// partials, per-point moments, each 256-byte aligned and (checked builds)
+// followed by a guard area.  sizes[] in bytes; returns the region's size.
+static long long bwd_parts(long long N, int C, int H, int W, long long at[5], long long guard_at[5]) {
   const long long px = (long long)H * W;
   const long long mt = ((long long)H + 1) / 2 * (((long long)W + 3) / 4);   // smallest micro-tile: 2x4
-  const long long planes = px * 16 * (C == 4 ? 2 : 1);
-  auto al = [](long long v) { return (v + 255) / 256 * 256; };
-  return al(planes) + al(mt * 4) + al(mt * 8) + al((long long)kSigParts * 4) + al(N * 4 * kPpMomentFloats);
+  const long long sizes[5] = {px * 16 * (C == 4 ? 2 : 1), mt * 4, mt * 8, (long long)kSigParts * 4,
+                              N * 4 * kPpMomentFloats};
+  long long o = 0;
+  for (int k = 0; k < 5; ++k) {
+    at[k] = o;
+    o += (sizes[k] + 255) / 256 * 256;
+    guard_at[k] = o;
+    o += (long long)kGuardBytes;
+  }
+  return o;
+}
+
+long long bwd_extra_bytes(long long N, int C, int H, int W) {
+  long long at[5], ga[5];
+  return bwd_parts(N, C, H, W, at, ga);
 }
 
 void bind_bwd(DevWork& w, void* extra, long long N, int C, int H, int W, long long mt_total) {
-  (void)N;
   (void)mt_total;
-  const long long px = (long long)H * W;
-  const long long mt = ((long long)H + 1) / 2 * (((long long)W + 3) / 4);
-  auto al = [](long long v) { return (v + 255) / 256 * 256; };
+  long long at[5], ga[5];
+  bwd_parts(N, C, H, W, at, ga);
   char* p = (char*)extra;
-  w.pplane = (float4*)p;
-  p += al(px * 16 * (C == 4 ? 2 : 1));
-  w.fbflag = (unsigned*)p;
-  p += al(mt * 4);
-  w.fbq = (uint2*)p;
-  p += al(mt * 8);
-  w.sig_part = (float*)p;
-  p += al((long long)kSigParts * 4);
-  w.ppmom = (float*)p;
+  w.pplane = (float4*)(p + at[0]);
+  w.fbflag = (unsigned*)(p + at[1]);
+  w.fbq = (uint2*)(p + at[2]);
+  w.sig_part = (float*)(p + at[3]);
+  w.ppmom = (float*)(p + at[4]);
+}
+
+void bwd_guards(long long N, int C, int H, int W, size_t extra_at, Guards& g) {
+  if (kGuardBytes == 0) return;
+  long long at[5], ga[5];
+  bwd_parts(N, C, H, W, at, ga);
+  for (int k = 0; k < 5 && g.n < kMaxGuards; ++k) g.off[g.n++] = extra_at + (size_t)ga[k];
 }
 
 template <int C>
@@ -588,6 +604,12 @@ static gmi_status backward_impl(const float* points, const float* values, const 
   a.mt_total = mt;
   a.satj_total = sat_jobs(g);
   const bool trunc = p->mode == GMI_MODE_TRUNCATED;
+  if (kGuardBytes > 0) {
+    Guards gx;
+    gx.n = 0;
+    bwd_guards(N, C, H, W, L.extra, gx);
+    if (launch_canaries(workspace, gx, false, a.w.status, s) != cudaSuccess) return GMI_ERR_CUDA;
+  }
   // the bins only: the fallback derives its radii from den, not from the plan
   if ((st = run_bin_and_plan(a, L, workspace, mth, mtw, trunc, s, false)) != GMI_OK) return st;
   if (per_point && !trunc) {

@@ -101,6 +101,13 @@ static void batch_geom(ImageGeom& g, const gmi_batch_plan* p, long long N, int H
 
 using namespace gmi;
 
+namespace gmi {
+void batch_plan_workspace(const gmi_batch_plan* p, void** base, const WsLayout** L) {
+  *base = p->base;
+  *L = &p->L;
+}
+}  // namespace gmi
+
 extern "C" gmi_status gmi_batch_plan_create(int max_images, int64_t max_points, int64_t max_pixels, int C,
                                             const gmi_params* params, gmi_batch_plan** out) {
   if (!out) return GMI_ERR_INVALID_ARG;

@@ -52,8 +52,10 @@ __global__ void __launch_bounds__(256) bin_count_kernel(KArgs a_in) {
       long long bin;
       bool oob;
       point_bin(g, p.x, p.y, bin, oob);
-      a.w.rank[g.pt_base + i] = atomicAdd(&a.w.off[bin], 1u);
-      if (oob) a.w.oob[bin] = 1;
+      if (GMI_IN_BOUNDS(a.w, bin, a.nb_total, CK_BIN)) {
+        a.w.rank[g.pt_base + i] = atomicAdd(&a.w.off[bin], 1u);
+        if (oob) a.w.oob[bin] = 1;
+      }
     }
   }
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&a.w.status[kStatusErr], ST_NONFINITE);

@@ -34,9 +34,11 @@ static __device__ __forceinline__ void scatter_single(const KArgs& a, int nblock
       if (a.C > 2) c.z = v[2];
       if (a.C > 3) c.w = v[3];
       fin = fin && isfinite(c.x) && isfinite(c.y) && isfinite(c.z) && isfinite(c.w);
-      a.w.sxy[dst] = p;
-      a.w.sval[dst] = c;
-      a.w.perm[dst] = (unsigned)i;
+      if (GMI_IN_BOUNDS(a.w, dst, a.n_total, CK_SCATTER)) {
+        a.w.sxy[dst] = p;
+        a.w.sval[dst] = c;
+        a.w.perm[dst] = (unsigned)i;
+      }
     }
   }
   if (__any_sync(0xffffffffu, !fin) && (threadIdx.x & 31) == 0) atomicOr(&a.w.status[kStatusErr], ST_NONFINITE);
@@ -68,10 +70,13 @@ static __device__ __forceinline__ void bin_scatter_body(const KArgs& a, int nblo
       if (a.C > 2) c.z = v[2];
       if (a.C > 3) c.w = v[3];
       fin = fin && isfinite(c.x) && isfinite(c.y) && isfinite(c.z) && isfinite(c.w);
-      a.w.sxy[dst] = p;
-      a.w.sval[dst] = c;
-      a.w.perm[dst] = (unsigned)i;
-      if (g.sigmas) {
+      const bool ok = GMI_IN_BOUNDS(a.w, dst, a.n_total, CK_SCATTER);
+      if (ok) {
+        a.w.sxy[dst] = p;
+        a.w.sval[dst] = c;
+        a.w.perm[dst] = (unsigned)i;
+      }
+      if (g.sigmas && ok) {
         const float* sg = g.sigmas + g.pp_kind * i;
         const float4 k = g.pp_kind == 3 ? pp_cov_consts(g.sigma, sg[0], sg[1], sg[2])
                                         : pp_consts(g.sigma, sg[0], g.pp_kind == 2 ? sg[1] : sg[0]);

@@ -21,6 +21,8 @@ enum : unsigned {
   ST_INTERNAL = 2u,    // a consistency check failed (e.g. a list overflowed)
   ST_TIMEOUT = 4u,     // a bounded wait gave up
   ST_SIGMA = 8u,       // a per-point sigma outside its range (sigmas_ok)
+  ST_BOUNDS = 16u,     // checked builds: an index failed its bounds check (the access was skipped)
+  ST_CANARY = 32u,     // checked builds: a guard area after a workspace region was overwritten
 };
 
 // Slots of the status/counter block at the start of every workspace.
@@ -37,6 +39,9 @@ enum : int {
   kSigDone = 9,        // blocks of the point-centric backward that have finished
   kSatHead = 10,       // next summed-area-table column job
   kLaMax = 11,         // per-point sigmas: the largest log2 normaliser la_i (float bits; la_i >= 0)
+  kBadSite = 12,       // checked builds: the first failed bounds check's site (CheckSite), 0 if none
+  kBadIndex = 13,      // checked builds: its index (low 32 bits)
+  kBadGuard = 14,      // checked builds: the first overwritten guard area's number + 1
   kStatusWords = 64,
 };
 
@@ -123,6 +128,44 @@ struct DevWork {
   TilePlanRec* tplan;    // [wt_total] staging plans of the staged gather (written by
                          //   the plan kernel), or null: the gather sets up every item itself
 };
+
+// Bounds checks of a checked build (compiled with -DGMI_CHECKED): every index
+// into the workspace's queues, slots and sorted arrays that a kernel computes
+// from a counter, a queue entry or another kernel's output is tested before
+// the access.  A failed test skips the access, sets ST_BOUNDS and records the
+// first site and index; it never traps.  Without GMI_CHECKED a check is the
+// constant true and costs nothing.
+enum CheckSite : unsigned {
+  CK_BIN = 1,          // bin_count: the point's bin
+  CK_SCATTER = 2,      // scatter: the point's slot in the sorted arrays
+  CK_FARQ = 3,         // plan: far-field queue entry
+  CK_STAGE = 4,        // staged gather: a segment of the staging buffer
+  CK_CAND = 5,         // gathers: a candidate's sorted index
+  CK_FARQ_READ = 6,    // far kernel: a queue entry read back (image, micro-tile)
+  CK_FBQ = 7,          // backward: fallback queue entry
+  CK_PIXEL = 8,        // backward: a pixel of the per-pixel plane
+  CK_MOMENT = 9,       // per-point exact backward: a point's moments
+  CK_SLOT = 10,        // split tiles: a partial-sum slot
+  CK_ITEM = 11,        // near kernel: a work item index
+  CK_SAT = 12,         // summed-area table entry
+};
+
+__device__ __forceinline__ bool checked_index(unsigned* status, long long i, long long n, unsigned site) {
+#ifdef GMI_CHECKED
+  if (i >= 0 && i < n) return true;
+  atomicOr(&status[kStatusErr], ST_BOUNDS);
+  if (atomicCAS(&status[kBadSite], 0u, site) == 0u) status[kBadIndex] = (unsigned)i;
+  return false;
+#else
+  (void)status;
+  (void)i;
+  (void)n;
+  (void)site;
+  return true;
+#endif
+}
+
+#define GMI_IN_BOUNDS(w, i, n, site) ::gmi::checked_index((w).status, (long long)(i), (long long)(n), (site))
 
 struct KArgs {
   DevWork w;

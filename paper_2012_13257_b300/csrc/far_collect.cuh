@@ -101,7 +101,8 @@ static __device__ unsigned collect(const KArgs& a, const ImageGeom& g, const Far
       const unsigned base = total + incl - len;
       for (unsigned k = 0; k < len; ++k) {
         const unsigned pos = base + k;
-        if (pos >= skip && pos < skip + kFarCap) L[pos - skip] = s + k;
+        if (pos >= skip && pos < skip + kFarCap)
+          L[pos - skip] = GMI_IN_BOUNDS(a.w, s + k, a.n_total, CK_CAND) ? s + k : 0u;
       }
       total += __shfl_sync(full, incl, 31);
       continue;
@@ -128,7 +129,7 @@ static __device__ unsigned collect(const KArgs& a, const ImageGeom& g, const Far
       const unsigned rs = __shfl_sync(full, s, r), rex = __shfl_sync(full, excl, r);
       bool pass = false;
       unsigned idx = 0;
-      if (f < n) {
+      if (f < n && GMI_IN_BOUNDS(a.w, rs + (f - rex), a.n_total, CK_CAND)) {
         idx = rs + (f - rex);
         const float2 p = a.w.sxy[idx];
         const float dx = fmaxf(fmaxf(t.xa - p.x, p.x - t.xb), 0.0f);

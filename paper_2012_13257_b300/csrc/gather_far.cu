@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(32 * kFarWarps) far_kernel(KArgs a_in, int mth
   unsigned e = blockIdx.x * kFarWarps + wid;
   while (e < nfar) {
     const uint2 q = a.w.farq[e];
-    const int img = (int)q.x;
+    const int img = GMI_IN_BOUNDS(a.w, q.x, a.n_images, CK_FARQ_READ) ? (int)q.x : 0;
     const ImageGeom g = a.w.table ? a.w.table[img] : a.g0;
     const int mt_x = (int)(q.y % (unsigned)g.mtx), mt_y = (int)(q.y / (unsigned)g.mtx);
     const int x0 = mt_x * mtw, y0 = mt_y * mth;

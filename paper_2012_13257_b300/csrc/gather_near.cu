@@ -346,8 +346,9 @@ __device__ void near_plan_body(const KArgs& a, int trunc, long long wt) {
       unsigned base = 0;
       if (lane == leader) base = atomicAdd(&a.w.status[kFarCount], (unsigned)__popc(fm));
       base = __shfl_sync(full, base, leader);
-      if (far)
-        a.w.farq[base + __popc(fm & ((1u << lane) - 1u))] = make_uint2((unsigned)img, (unsigned)(mt_y * g.mtx + mt_x));
+      const unsigned q = base + __popc(fm & ((1u << lane) - 1u));
+      if (far && GMI_IN_BOUNDS(a.w, q, a.mt_total, CK_FARQ))
+        a.w.farq[q] = make_uint2((unsigned)img, (unsigned)(mt_y * g.mtx + mt_x));
     }
   }
   a.w.ubound[wt * 32 + lane] = far ? INFINITY : U;
@@ -615,7 +616,7 @@ __global__ void __launch_bounds__(128, NearOcc<MTH, MTW, C>::value) near_kernel(
       }
 
     bool finish = true;
-    if (S > 1) {
+    if (S > 1 && GMI_IN_BOUNDS(a.w, slot, a.cap_slots, CK_SLOT)) {
       // split tile: add this item's partial sums into the tile's slot; the
       // last item to finish reads the totals and writes the pixels
       float* mine = a.w.slots + ((size_t)slot * 32 + lane) * NA;

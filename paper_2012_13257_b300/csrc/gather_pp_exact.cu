@@ -299,7 +299,7 @@ __global__ void __launch_bounds__(32 * kFarWarps) pp_exact_bwd_kernel(KArgs a, i
         for (int j = 0; j < kPpMoments; ++j)
           for (int o = PS >> 1; o > 0; o >>= 1) m[j] += __shfl_xor_sync(full, m[j], o);
         const bool any = (__ballot_sync(full, k < n && valid) & pmask) != 0u;
-        if (slot == 0 && any) {
+        if (slot == 0 && any && GMI_IN_BOUNDS(a.w, idx, a.n_total, CK_MOMENT)) {
           float* dst = mom + (size_t)idx * kPpMoments;
 #pragma unroll
           for (int j = 0; j < kPpMoments; ++j)

@@ -528,6 +528,7 @@ __global__ void __launch_bounds__(32 * kStageWarps, StagedOcc<MTH, MTW, C>::valu
       for (unsigned sg = 0; sg < nseg; ++sg) {
         const unsigned te = tab[sg];
         const unsigned e = te >> 16;
+        if (!GMI_IN_BOUNDS(a.w, e - 1u, CAP, CK_STAGE)) continue;
         for (unsigned i = te & 0xffffu; i < e; ++i)
           consume_pt<MTH, MTW, C, TRUNC>(accp, accs, sk, xq0, yq0, neg_thr, sb.pos[i], sb.col[i]);
       }
@@ -564,7 +565,7 @@ __global__ void __launch_bounds__(32 * kStageWarps, StagedOcc<MTH, MTW, C>::valu
       }
 
     bool finish = true;
-    if (it.S > 1) {
+    if (it.S > 1 && GMI_IN_BOUNDS(a.w, it.slot, a.cap_slots, CK_SLOT)) {
       // split tile: add this item's partial sums into the tile's slot; the
       // last item to finish reads the totals and writes the pixels
       float* mine = a.w.slots + ((size_t)it.slot * 32 + lane) * NA;

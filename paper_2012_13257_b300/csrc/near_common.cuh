@@ -126,6 +126,7 @@ __device__ __forceinline__ void direct_walk(const KArgs& a, const ImageGeom& g, 
       cum += len;
       i = s0 + (lo > rs ? min(lo - rs, len) : 0u);
       end = s0 + (hi > rs ? min(hi - rs, len) : 0u);
+      if (i < end && !GMI_IN_BOUNDS(a.w, end - 1u, a.n_total, CK_CAND)) end = i;
       if (i < end) return true;
     }
   };

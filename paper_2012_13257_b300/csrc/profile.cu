@@ -2,6 +2,8 @@
 #include <mutex>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "api_internal.h"
 
 namespace gmi {
@@ -24,7 +26,12 @@ bool profile_on() { return g_on; }
 
 // Records the opening event of a stage (stage -1 in the mark when off or exhausted).
 ProfileMark profile_begin(int stage, cudaStream_t s) {
-  ProfileMark m{-1, nullptr, nullptr};
+  static const char* const kRange[GMI_STAGE_COUNT] = {"gmi.bin", "gmi.near", "gmi.far", "gmi.backward"};
+  ProfileMark m{-1, nullptr, nullptr, false};
+  if (stage >= 0 && stage < GMI_STAGE_COUNT) {
+    nvtxRangePushA(kRange[stage]);
+    m.range = true;
+  }
   if (!g_on) return m;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return m;  // not inside graphs
@@ -38,6 +45,7 @@ ProfileMark profile_begin(int stage, cudaStream_t s) {
 }
 
 void profile_end(const ProfileMark& m, cudaStream_t s) {
+  if (m.range) nvtxRangePop();
   if (m.stage < 0) return;
   cudaEventRecord(m.b, s);
   std::lock_guard<std::mutex> lk(g_mu);

@@ -164,3 +164,30 @@ def test_workspace_layout_is_consistent_without_a_gpu():
     assert L.gmi_workspace_layout(10, 3, 8, 8, ctypes.byref(p), None) == 1                  # no output
     bad = _lib.make_params(-1.0)
     assert L.gmi_workspace_layout(10, 3, 8, 8, ctypes.byref(bad), ctypes.byref(lay)) == 1   # sigma <= 0
+
+
+def test_checked_build_exports_and_layout():
+    """The checked build (libgmi_checked.so) exports the same entry points,
+    says it is checked, and sizes its workspaces larger (a guard area after
+    every region); the normal build answers the check calls with
+    GMI_ERR_UNSUPPORTED before touching anything."""
+    path = os.path.join(ROOT, "paper_2012_13257_b300", "libgmi_checked.so")
+    if not os.path.exists(path):
+        from paper_2012_13257_b300 import build as b
+        b.build(checked=True)
+    chk = ctypes.CDLL(path)
+    missing = [n for n in declared_functions() if not hasattr(chk, n)]
+    assert not missing, missing
+    lib = _lib.load()
+    assert chk.gmi_is_checked_build() == 1 and lib.gmi_is_checked_build() == 0
+    p = _lib.make_params(1.0)
+    for fn in (lib.gmi_workspace_size, chk.gmi_workspace_size):
+        fn.argtypes = [ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_lib.Params),
+                       ctypes.POINTER(ctypes.c_size_t)]
+    a, b = ctypes.c_size_t(0), ctypes.c_size_t(0)
+    assert lib.gmi_workspace_size(1000, 3, 64, 64, ctypes.byref(p), ctypes.byref(a)) == 0
+    assert chk.gmi_workspace_size(1000, 3, 64, 64, ctypes.byref(p), ctypes.byref(b)) == 0
+    assert b.value >= a.value + 17 * 256
+    rep = (ctypes.c_uint32 * 4)()
+    assert lib.gmi_check_workspace(1000, 3, 64, 64, ctypes.byref(p), 256, a.value, None, rep) == 7
+    assert lib.gmi_batch_check_workspace(256, None, rep) == 7
