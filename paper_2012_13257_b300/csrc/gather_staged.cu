@@ -391,9 +391,9 @@ __global__ void __launch_bounds__(32 * kStageWarps, StagedOcc<MTH, MTW, C>::valu
         for (int k = 0; k < MTH * MTW * ODD + 1 - ODD; ++k) accs[k] = 0.0f;
         if (total > 0u) {
           const bool ok = mbar_wait(&sb.bar, parity);
-          parity ^= 1u;
           if (__any_sync(full, !ok)) stalled = true;
         }
+        parity ^= 1u;   // the arrival completes a phase even when nothing is copied
       }
     }
     if (!planned) {
@@ -499,9 +499,9 @@ __global__ void __launch_bounds__(32 * kStageWarps, StagedOcc<MTH, MTW, C>::valu
           }
           if (total > 0u) {
             const bool ok = mbar_wait(&sb.bar, parity);
-            parity ^= 1u;
             if (__any_sync(full, !ok)) stalled = true;
           }
+          parity ^= 1u;   // the arrival completes a phase even when nothing is copied
           staged = true;
         }
       }
@@ -511,6 +511,8 @@ __global__ void __launch_bounds__(32 * kStageWarps, StagedOcc<MTH, MTW, C>::valu
       for (int k = 0; k < MTH * MTW * ODD + 1 - ODD; ++k) accs[k] = 0.0f;
       if (!fits && it.active) {
         // the window does not fit the buffer: straight from global memory
+        // (staging it in passes of rows that fit was measured slower on
+        // dense clustered windows: each pass waits for its copies)
         auto consume3 = [&](const float2 p, const float4 cv, const float4) {
           consume_pt<MTH, MTW, C, TRUNC>(accp, accs, sk, xq0, yq0, neg_thr, p, cv);
         };
