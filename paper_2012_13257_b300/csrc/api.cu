@@ -27,6 +27,18 @@ cudaError_t launch_far(const KArgs& a, int mth, int mtw, int sms, cudaStream_t s
 __global__ void bin_count_kernel(KArgs a);
 __global__ void scan_partial_kernel(const unsigned* cnt, long long nb, unsigned* partials, const long long* totals);
 __global__ void scan_final_kernel(unsigned* off, long long nb, const unsigned* partials, const long long* totals);
+__global__ void scan_one_kernel(unsigned* off, long long nb, unsigned* partials, unsigned* status);
+
+// Blocks of the one-launch scan that can be resident on the device at once
+// (cached; filled before any capture by warm_near_caches).
+static int scan_one_capacity() {
+  static const int n = [] {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, scan_one_kernel, 256, 0) != cudaSuccess || b < 1) b = 0;
+    return b * device_sm_count();
+  }();
+  return n;
+}
 __global__ void bin_scatter_kernel(KArgs a);
 __global__ void batch_clear_kernel(KArgs a);
 
@@ -219,8 +231,24 @@ gmi_status run_bin_and_plan(KArgs& a, const WsLayout& L, void* ws, int mth, int 
     gb = (int)std::min<long long>(a.ch_total, (long long)sms * 32);
     bin_count_kernel<<<gb, 256, 0, s>>>(a);
     const int ns = (int)((a.nb_total + kScanChunk - 1) / kScanChunk);
-    scan_partial_kernel<<<ns, 256, 0, s>>>(a.w.off, a.nb_total, a.w.partials, a.totals);
-    scan_final_kernel<<<ns, 256, 0, s>>>(a.w.off, a.nb_total, a.w.partials, a.totals);
+    if (!a.totals && ns <= scan_one_capacity()) {
+      // single image, every block resident at once: one cooperative launch
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeCooperative;
+      attr[0].val.cooperative = 1;
+      cfg.gridDim = dim3((unsigned)ns);
+      cfg.blockDim = dim3(256);
+      cfg.stream = s;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      if (cudaLaunchKernelEx(&cfg, scan_one_kernel, a.w.off, (long long)a.nb_total, a.w.partials, a.w.status) !=
+          cudaSuccess)
+        return GMI_ERR_CUDA;
+    } else {
+      scan_partial_kernel<<<ns, 256, 0, s>>>(a.w.off, a.nb_total, a.w.partials, a.totals);
+      scan_final_kernel<<<ns, 256, 0, s>>>(a.w.off, a.nb_total, a.w.partials, a.totals);
+    }
     if (cudaGetLastError() != cudaSuccess) return GMI_ERR_CUDA;
   }
   if (plan) {
@@ -269,6 +297,7 @@ bool uses_staged_gather(int gather, int ppk) { return ppk == 0 && gather != GMI_
 
 void warm_near_caches(int mth, int mtw, int C, bool trunc, int ppk, int gather) {
   device_sm_count();
+  scan_one_capacity();
   if (ppk && !trunc) {
     warm_pp_exact(C, ppk);
     return;

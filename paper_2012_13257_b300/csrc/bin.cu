@@ -146,6 +146,83 @@ __global__ void __launch_bounds__(256) scan_final_kernel(unsigned* __restrict__ 
 }
 
 
+// The same exclusive scan in one launch, for grids that are resident all at
+// once (launched cooperatively, so the hardware guarantees it): each block
+// sums its chunk and publishes the sum, waits at a grid barrier until every
+// block has, then adds the sums of the earlier chunks to its own scan.  The
+// wait is bounded (about 0.1 s); a block that gives up sets ST_TIMEOUT and
+// goes on (the offsets are then wrong and the call reports an error).
+constexpr unsigned kScanWaitPolls = 1u << 20;
+
+__global__ void __launch_bounds__(256) scan_one_kernel(unsigned* __restrict__ off, long long nb,
+                                                       unsigned* __restrict__ partials, unsigned* status) {
+  constexpr int kPer = kScanChunk / 256;
+  __shared__ unsigned warp_tot[8];
+  __shared__ unsigned block_prefix;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const long long base = (long long)blockIdx.x * kScanChunk + (long long)tid * kPer;
+  unsigned v[kPer];
+  unsigned s = 0;
+#pragma unroll
+  for (int k = 0; k < kPer; ++k) {
+    v[k] = base + k < nb ? off[base + k] : 0u;
+    s += v[k];
+  }
+  unsigned incl = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) warp_tot[wid] = incl;
+  __syncthreads();
+  unsigned wpre = 0, btot = 0;
+#pragma unroll
+  for (int w = 0; w < 8; ++w) {
+    if (w < wid) wpre += warp_tot[w];
+    btot += warp_tot[w];
+  }
+  // publish this chunk's sum, then wait for every block's
+  if (tid == 0) {
+    partials[blockIdx.x] = btot;
+    __threadfence();
+    atomicAdd(&status[kScanArrive], 1u);
+    unsigned k = 0;
+    while (true) {
+      unsigned n;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(n) : "l"(status + kScanArrive) : "memory");
+      if (n >= gridDim.x) break;
+      if (++k == kScanWaitPolls) {
+        atomicOr(&status[kStatusErr], ST_TIMEOUT);
+        break;
+      }
+      __nanosleep(64);
+    }
+  }
+  __syncthreads();
+  // the sums of the earlier chunks
+  unsigned pre = 0;
+  for (int k = tid; k < (int)blockIdx.x; k += blockDim.x) pre += __ldcg(&partials[k]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) pre += __shfl_xor_sync(0xffffffffu, pre, o);
+  __syncthreads();   // warp_tot is free again
+  if (lane == 0) warp_tot[wid] = pre;
+  __syncthreads();
+  if (tid == 0) {
+    unsigned t = 0;
+    for (int w = 0; w < 8; ++w) t += warp_tot[w];
+    block_prefix = t;
+  }
+  __syncthreads();
+  unsigned run = block_prefix + wpre + incl - s;
+#pragma unroll
+  for (int k = 0; k < kPer; ++k) {
+    if (base + k < nb) off[base + k] = run;
+    run += v[k];
+  }
+  if (nb > 0 && base <= nb - 1 && nb - 1 < base + kPer) off[nb] = run;
+}
+
 __global__ void __launch_bounds__(256) bin_scatter_kernel(KArgs a_in) {
   const KArgs a = resolve(a_in);
   bin_scatter_body(a, gridDim.x, blockIdx.x);

@@ -42,6 +42,7 @@ enum : int {
   kBadSite = 12,       // checked builds: the first failed bounds check's site (CheckSite), 0 if none
   kBadIndex = 13,      // checked builds: its index (low 32 bits)
   kBadGuard = 14,      // checked builds: the first overwritten guard area's number + 1
+  kScanArrive = 15,    // blocks of the one-launch scan past their chunk sums (its grid barrier)
   kStatusWords = 64,
 };
 
