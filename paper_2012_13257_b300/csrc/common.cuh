@@ -43,6 +43,7 @@ enum : int {
   kBadIndex = 13,      // checked builds: its index (low 32 bits)
   kBadGuard = 14,      // checked builds: the first overwritten guard area's number + 1
   kScanArrive = 15,    // blocks of the one-launch scan past their chunk sums (its grid barrier)
+  kSatDone = 16,       // summed-area-table column jobs finished
   kStatusWords = 64,
 };
 
@@ -184,6 +185,7 @@ struct KArgs {
   unsigned cap_slots;    // capacity of w.slots, in slots
   int mth, mtw;          // micro-tile of the near kernel
   int gather;            // GMI_GATHER_* of the call (host-side choice of the near kernel)
+  int far_in_near;       // the staged near kernel takes the far-field micro-tiles (no far kernel)
   const long long* totals;  // batched: device copy of the totals below (else null)
 };
 

@@ -1,24 +1,10 @@
 // Far-field gather: exact Eq. 1 / Eq. 2 for micro-tiles that the near kernel
 // could not take (pixels far from every known point, where the unshifted
-// weights 2^(-kappa d^2) would underflow).
-//
-// For such a pixel the relevant points lie in a thin shell
-// m_q <= d^2 <= m_q + k^2 sigma^2 around its nearest distance m_q, and the
-// weights must be evaluated relative to m_q: w = 2^(-kappa (d^2 - m_q)), with
-// d^2 - m_q accurate in absolute terms although d^2 and m_q are large.  One
-// warp handles one queued micro-tile:
-//   A. bracket the smallest Chebyshev window around the micro-tile that holds
-//      any point (doubling, then bisection, on bin counts) and bound
-//      U >= max_q m_q with up to kFarCap of those points;
-//   B. collect every point within Euclidean distance R = sqrt(U + k^2 sigma^2)
-//      of the micro-tile (indices in shared memory, in chunks if many);
-//   C. per pixel, m~_q = min d^2 over the candidates (float32);
-//   D. per pixel, sum w = 2^(-kappa e) c over candidates in the shell, with
-//      e = d^2 - m~_q from error-free transformations (common.cuh).
-// Lanes are split as (pixel slot, part): pixels of the micro-tile times
-// 32 / (MTH * MTW) interleaved parts of the candidate list, combined with
-// shuffles in a fixed order (the result does not depend on scheduling).
-#include "far_collect.cuh"
+// weights 2^(-kappa d^2) would underflow), one warp per queued micro-tile
+// (far_entry in far_tile.cuh).  With the staged near kernel the same work runs
+// in the near kernel's warps once their near work is done, and this kernel is
+// not launched; the direct-load near kernel leaves it to this kernel.
+#include "far_tile.cuh"
 
 namespace gmi {
 
@@ -30,103 +16,13 @@ __global__ void __launch_bounds__(32 * kFarWarps) far_kernel(KArgs a_in, int mth
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   unsigned* L = lists[wid];
   const unsigned nfar = a.w.status[kFarCount];
-  const int PS = mth * mtw;              // pixel slots: 8, 16 or 32
-  const int nparts = 32 / PS;
-  const int slot = lane % PS, part = lane / PS;
-  const int pr = slot / mtw, pj = slot % mtw;
 
   // first entry by warp index, later ones claimed from the queue; with an
   // empty queue (the usual case for dense inputs) warps leave at once
   const unsigned n_warps = gridDim.x * kFarWarps;
   unsigned e = blockIdx.x * kFarWarps + wid;
   while (e < nfar) {
-    const uint2 q = a.w.farq[e];
-    const int img = GMI_IN_BOUNDS(a.w, q.x, a.n_images, CK_FARQ_READ) ? (int)q.x : 0;
-    const ImageGeom g = a.w.table ? a.w.table[img] : a.g0;
-    const int mt_x = (int)(q.y % (unsigned)g.mtx), mt_y = (int)(q.y / (unsigned)g.mtx);
-    const int x0 = mt_x * mtw, y0 = mt_y * mth;
-    const int nx = min(mtw, g.W - x0), ny = min(mth, g.H - y0);
-    FarTile t;
-    t.xa = (float)x0 + 0.5f;
-    t.xb = (float)(x0 + nx) - 0.5f;
-    t.ya = (float)y0 + 0.5f;
-    t.yb = (float)(y0 + ny) - 0.5f;
-    const bool valid = pr < ny && pj < nx;
-    const float qx = (float)(x0 + pj) + 0.5f, qy = (float)(y0 + pr) + 0.5f;
-
-    // A. smallest non-empty window (bin resolution), then U from its points
-    const float hi = smallest_window(a, g, t);
-    float accd[kMaxC + 1];
-#pragma unroll
-    for (int k = 0; k <= kMaxC; ++k) accd[k] = 0.0f;
-    float mshift = 0.0f;
-    if (hi >= 0.0f) {
-      const unsigned ns = min(collect(a, g, t, hi, -1.0f, 0u, L), (unsigned)kFarCap);
-      float best = INFINITY;
-      for (unsigned k = part; k < ns; k += nparts) {
-        const float2 p = a.w.sxy[L[k]];
-        const float dx = qx - p.x, dy = qy - p.y;
-        best = fminf(best, fmaf(dx, dx, dy * dy));
-      }
-      for (int o = PS; o < 32; o <<= 1) best = fminf(best, __shfl_xor_sync(full, best, o));
-      float U = valid ? best : 0.0f;
-      for (int o = 16; o > 0; o >>= 1) U = fmaxf(U, __shfl_xor_sync(full, U, o));
-      __syncwarp();
-
-      // B. candidates within R of the micro-tile
-      const float R2 = (U + g.r2k) * (1.0f + 1e-6f) + 1e-6f;
-      const float R = sqrtf(R2);
-      const unsigned total = collect(a, g, t, R, R2, 0u, L);
-
-      // C. nearest squared distance per pixel
-      float m = INFINITY;
-      for (unsigned skip = 0; skip < total; skip += kFarCap) {
-        if (skip > 0) collect(a, g, t, R, R2, skip, L);
-        const unsigned n = min(total - skip, (unsigned)kFarCap);
-        for (unsigned k = part; k < n; k += nparts) {
-          const float2 p = a.w.sxy[L[k]];
-          const float dx = qx - p.x, dy = qy - p.y;
-          m = fminf(m, fmaf(dx, dx, dy * dy));
-        }
-        __syncwarp();
-      }
-      for (int o = PS; o < 32; o <<= 1) m = fminf(m, __shfl_xor_sync(full, m, o));
-      mshift = m;
-
-      // D. shell sum with shifted, compensated exponents
-      const float thr = (m + g.r2k) * (1.0f + 4e-7f) + 1e-30f;
-      for (unsigned skip = 0; skip < total; skip += kFarCap) {
-        if (skip > 0 || total > (unsigned)kFarCap) collect(a, g, t, R, R2, skip, L);
-        const unsigned n = min(total - skip, (unsigned)kFarCap);
-        for (unsigned k = part; k < n; k += nparts) {
-          const unsigned idx = L[k];
-          const float2 p = a.w.sxy[idx];
-          const float dx = qx - p.x, dy = qy - p.y;
-          if (fmaf(dx, dx, dy * dy) <= thr) {
-            const float ee = shifted_sqdist(qx, qy, p.x, p.y, m);
-            const float w = ex2(-g.kappa * ee);
-            const float4 cv = a.w.sval[idx];
-            accd[0] += w;
-            accd[1] = fmaf(w, cv.x, accd[1]);
-            if (C > 1) accd[2] = fmaf(w, cv.y, accd[2]);
-            if (C > 2) accd[3] = fmaf(w, cv.z, accd[3]);
-            if (C > 3) accd[4] = fmaf(w, cv.w, accd[4]);
-          }
-        }
-        __syncwarp();
-      }
-#pragma unroll
-      for (int k = 0; k <= C; ++k)
-        for (int o = PS; o < 32; o <<= 1) accd[k] += __shfl_xor_sync(full, accd[k], o);
-    }
-    if (valid && part == 0) {
-      const long long pix = (long long)(y0 + pr) * g.W + (x0 + pj);
-      const float inv = accd[0] > 0.0f ? 1.0f / accd[0] : 0.0f;
-#pragma unroll
-      for (int ch = 0; ch < C; ++ch) g.image[pix * C + ch] = accd[1 + ch] * inv;
-      if (g.den) g.den[pix] = accd[0];
-      if (g.shift) g.shift[pix] = mshift;
-    }
+    far_entry<C>(a, mth, mtw, a.w.farq[e], L);
     __syncwarp();   // the candidate list is rewritten by the next entry
     unsigned ne = 0;
     if (lane == 0) ne = n_warps + atomicAdd(&a.w.status[kFarHead], 1u);

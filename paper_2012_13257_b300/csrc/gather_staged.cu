@@ -29,6 +29,7 @@
 // candidate sequence.  Every wait on the barrier is bounded: if one gives up,
 // the kernel sets ST_TIMEOUT in the status word, waits (bounded again) for
 // its copies still in flight, and leaves.
+#include "far_tile.cuh"
 #include "near_common.cuh"
 #include "sat.cuh"
 
@@ -608,10 +609,29 @@ __global__ void __launch_bounds__(32 * kStageWarps, StagedOcc<MTH, MTW, C>::valu
     mbar_wait(&sb.bar, parity ^ 1u);
     return;
   }
-  // far-field micro-tiles queued: warps out of work build the summed-area
-  // table the far kernel's window search reads
+  // far-field micro-tiles queued: warps out of near work build the
+  // summed-area table the far-field window search reads; with far_in_near
+  // they wait until it is complete, then take the far-field micro-tiles one
+  // at a time (no far kernel follows), the staging buffer holding their
+  // candidate lists
   if constexpr (!TRUNC) {
-    if (__ldcg(&a.w.status[kFarCount]) > 0u) sat_build(a);
+    const unsigned nfar = __ldcg(&a.w.status[kFarCount]);
+    if (nfar > 0u && !a.far_in_near) sat_build(a);   // for the far kernel that follows
+    if (nfar > 0u && a.far_in_near) {
+      static_assert(sizeof(float4) * CAP + sizeof(float2) * CAP >= sizeof(unsigned) * kFarCap,
+                    "the far-field list fits the staging buffer");
+      sat_build(a);
+      if (!sat_wait(a)) return;
+      unsigned* Lf = reinterpret_cast<unsigned*>(&sb.col[0]);
+      for (;;) {
+        unsigned e = 0;
+        if (lane == 0) e = atomicAdd(&a.w.status[kFarHead], 1u);
+        e = __shfl_sync(full, e, 0);
+        if (e >= nfar || !GMI_IN_BOUNDS(a.w, e, a.mt_total, CK_FARQ_READ)) break;
+        far_entry<C>(a, MTH, MTW, a.w.farq[e], Lf);
+        __syncwarp();   // the list is rewritten by the next entry
+      }
+    }
   }
 }
 

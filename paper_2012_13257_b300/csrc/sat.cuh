@@ -3,7 +3,8 @@
 // search counts any window of bins with four loads instead of two per bin
 // row.  Built from the scanned bin offsets, column by column, by near-kernel
 // warps that have run out of work, and only when the far-field queue is not
-// empty; read by the far kernel, which runs after the near kernel.
+// empty; read by the far-field work that follows in the same kernel (after
+// sat_wait) or in the far kernel.
 #pragma once
 
 #include "common.cuh"
@@ -37,7 +38,27 @@ static __device__ void sat_build(const KArgs& a) {
         S[(long long)(r + 1) * st + c] = run;
       }
     }
+    // the job's columns are visible device-wide before it counts as done
+    __threadfence();
+    __syncwarp();
+    if (lane == 0) atomicAdd(&a.w.status[kSatDone], 1u);
   }
+}
+
+// Waits (bounded: about 0.1 s) until every column job of the table is done;
+// false, with ST_TIMEOUT set, if it gave up.  Every lane reads the counter
+// with acquire semantics, so its later loads of the table see the entries.
+constexpr unsigned kSatWaitPolls = 1u << 20;
+
+static __device__ bool sat_wait(const KArgs& a) {
+  for (unsigned k = 0; k < kSatWaitPolls; ++k) {
+    unsigned n;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(n) : "l"(a.w.status + kSatDone) : "memory");
+    if ((long long)n >= a.satj_total) return true;
+    __nanosleep(64);
+  }
+  if ((threadIdx.x & 31) == 0) atomicOr(&a.w.status[kStatusErr], ST_TIMEOUT);
+  return false;
 }
 
 // Points in the bins [bx_lo, bx_hi] x [by_lo, by_hi] of image g.
@@ -46,7 +67,8 @@ static __device__ __forceinline__ unsigned sat_count(const KArgs& a, const Image
   const unsigned* __restrict__ S = a.w.sat + g.sat_base;
   const long long st = g.nbx + 1;
   const long long y0 = (long long)by_lo * st, y1 = (long long)(by_hi + 1) * st;
-  return __ldg(&S[y1 + bx_hi + 1]) - __ldg(&S[y0 + bx_hi + 1]) - __ldg(&S[y1 + bx_lo]) + __ldg(&S[y0 + bx_lo]);
+  // (coherent loads: the table may have been written earlier in the same kernel)
+  return __ldcg(&S[y1 + bx_hi + 1]) - __ldcg(&S[y0 + bx_hi + 1]) - __ldcg(&S[y1 + bx_lo]) + __ldcg(&S[y0 + bx_lo]);
 }
 
 }  // namespace gmi
