@@ -308,6 +308,85 @@ __device__ __forceinline__ unsigned claim_next(const KArgs& a, unsigned n_items,
   return n_warps + atomicAdd(&a.w.status[kNearHead], 1u);
 }
 
+// Ring slots per lane of the pipelined direct walk (records in flight + 1;
+// 8 measured no faster than 4 on the clustered batch).
+constexpr int kRing = 4;
+
+// cp.async of 8 / 16 bytes from global into shared memory (cached in L1),
+// and the per-thread group commit and wait.
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Shared memory of the pipelined direct walk, in the staging buffer's records
+// (which a window too large to stage leaves unused): per-lane rings of
+// kRing colours and positions, laid out [slot][lane] so that lanes at the
+// same step touch neighbouring words, then per lane its list of segments
+// (global [start, end) pairs; rows padded by one entry against bank conflicts).
+template <int CAP>
+struct WalkArea {
+  float4 col[kRing][32];
+  float2 pos[kRing][32];
+  uint2 list[32][kPassRows + 1];
+};
+
+template <int CAP>
+__device__ __forceinline__ WalkArea<CAP>& walk_area(StageBuf<CAP>& sb) {
+  static_assert(sizeof(WalkArea<CAP>) <= CAP * (sizeof(float4) + sizeof(float2)) + sizeof(sb.tab),
+                "the walk's rings and lists fit the staging buffer's records and segment table");
+  return *reinterpret_cast<WalkArea<CAP>*>(&sb.col[0]);
+}
+
+template <int CAP>
+__device__ __forceinline__ uint2* walk_list(StageBuf<CAP>& sb, int lane) { return walk_area(sb).list[lane]; }
+
+// Walks the nwalk records of the lane's nlist segments in order: the lane's
+// next kRing - 1 records are always being copied into its ring slots, and
+// consume(position, colour) takes each from shared memory once its copy has
+// landed.  Every active lane consumes one record per step, so the slot is
+// the same across the warp.
+template <int CAP, typename F>
+__device__ __forceinline__ void pipelined_walk(StageBuf<CAP>& sb, int lane, const float2* __restrict__ sxy,
+                                               const float4* __restrict__ sval, unsigned nlist, unsigned nwalk,
+                                               F&& consume) {
+  WalkArea<CAP>& A = walk_area(sb);
+  const uint2* L = A.list[lane];
+  // producer cursor: segment kp, record ip of [ip, ep)
+  unsigned kp = 0u, ip = 0u, ep = 0u;
+  if (nlist > 0u) {
+    const uint2 s0 = L[0];
+    ip = s0.x;
+    ep = s0.y;
+  }
+  auto issue = [&](unsigned slot) {   // the producer's next record into `slot` (if any left)
+    if (kp < nlist) {
+      cp_async8(&A.pos[slot][lane], &sxy[ip]);
+      cp_async16(&A.col[slot][lane], &sval[ip]);
+      if (++ip == ep && ++kp < nlist) {
+        const uint2 sn = L[kp];
+        ip = sn.x;
+        ep = sn.y;
+      }
+    }
+    cp_async_commit();   // one group per step, empty once the records run out
+  };
+#pragma unroll
+  for (int j = 0; j < kRing - 1; ++j) issue((unsigned)j);
+  for (unsigned j = 0; j < nwalk; ++j) {
+    issue((j + kRing - 1) % kRing);
+    cp_async_wait<kRing - 1>();   // this lane's copy for step j has landed
+    const unsigned slot = j % kRing;
+    consume(A.pos[slot][lane], A.col[slot][lane]);
+  }
+  cp_async_wait<0>();
+}
+
 template <int MTH, int MTW, int C, bool TRUNC>
 __global__ void __launch_bounds__(32 * kStageWarps, StagedOcc<MTH, MTW, C>::value) near_staged_kernel(KArgs a_in) {
   constexpr int CAP = StageCap<MTH, MTW>::value;
@@ -338,6 +417,8 @@ __global__ void __launch_bounds__(32 * kStageWarps, StagedOcc<MTH, MTW, C>::valu
     // direct walk
     bool staged = false;
     unsigned nseg = 0;   // this thread's staged segments
+    bool listed = false; // this thread's window rows listed for the pipelined direct walk
+    unsigned nlist = 0, nwalk = 0;   // its non-empty segments and their records
     unsigned nt = 0;     // next item (lane 0), claimed early so the claim overlaps the walk
     float sk, xq0, yq0, neg_thr;
     // Accumulators in packed pairs: per pixel (r, j) the pairs (den, num_0),
@@ -465,6 +546,25 @@ __global__ void __launch_bounds__(32 * kStageWarps, StagedOcc<MTH, MTW, C>::valu
         }
         const unsigned total = __shfl_sync(full, incl, 31);
         fits = total <= (unsigned)CAP;
+        if (!fits && it.active) {
+          // too many records to stage, but this thread's rows are known: its
+          // share of each non-empty row segment, as global [start, end)
+          // pairs in its list for the pipelined direct walk below
+          uint2* L = walk_list(sb, lane);
+          unsigned cum = 0;
+#pragma unroll
+          for (int k = 0; k < kPassRows; ++k) {
+            const unsigned len = sege[k] - segs[k];
+            const unsigned a0 = lo > cum ? min(lo - cum, len) : 0u;
+            const unsigned b0 = hi > cum ? min(hi - cum, len) : 0u;
+            cum += len;
+            if (a0 < b0 && GMI_IN_BOUNDS(a.w, segs[k] + b0 - 1u, a.n_total, CK_CAND)) {
+              L[nlist++] = make_uint2(segs[k] + a0, segs[k] + b0);
+              nwalk += b0 - a0;
+            }
+          }
+          listed = true;
+        }
         if (fits) {
           const unsigned abase = incl - need;
           if (lane < rows) sb.desc[lane] = make_uint2(S0, abase + (S0 & 1u));
@@ -510,10 +610,19 @@ __global__ void __launch_bounds__(32 * kStageWarps, StagedOcc<MTH, MTW, C>::valu
       for (int k = 0; k < MTH * MTW * NP; ++k) accp[k] = make_float2(0.f, 0.f);
 #pragma unroll
       for (int k = 0; k < MTH * MTW * ODD + 1 - ODD; ++k) accs[k] = 0.0f;
-      if (!fits && it.active) {
-        // the window does not fit the buffer: straight from global memory
-        // (staging it in passes of rows that fit was measured slower on
-        // dense clustered windows: each pass waits for its copies)
+      if (listed) {
+        // the window does not fit the buffer: this thread's segments straight
+        // from global memory through a ring of records per lane in the
+        // (unused) staging buffer, all but one of them in flight ahead of
+        // the one consumed (cp.async; each lane waits on its own copies only)
+        pipelined_walk(sb, lane, a.w.sxy, a.w.sval, nlist, nwalk, [&](const float2 p, const float4 cv) {
+          consume_pt<MTH, MTW, C, TRUNC>(accp, accs, sk, xq0, yq0, neg_thr, p, cv);
+        });
+      } else if (!fits && it.active) {
+        // more window rows than the segment list holds: straight from global
+        // memory row by row (staging such windows in passes of rows that fit
+        // was measured slower on dense clustered windows: each pass waits for
+        // its copies)
         auto consume3 = [&](const float2 p, const float4 cv, const float4) {
           consume_pt<MTH, MTW, C, TRUNC>(accp, accs, sk, xq0, yq0, neg_thr, p, cv);
         };
