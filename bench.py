@@ -6,7 +6,7 @@ Headline workload (one "step" = one forward pass, binning included, of one
 synthetic image): a 512^2 source grid jittered by U[-0.5, 0.5] px, upsampled
 x2 to 1024 x 1024 x 3 float32 with sigma = 1 px, exact mode, k = 6.  ``value``
 is interpolated output Mpix/s (H*W per step, all ranks) through
-``gmi.interpolate(..., graph=True)`` (the six kernels replayed as one CUDA
+``gmi.interpolate(..., graph=True)`` (the four kernels replayed as one CUDA
 graph), timed with CUDA events per step on the launching stream with L2
 flushed (256 MB write) between steps; ``plain_launch`` is the same without
 graph replay; ``e2e`` repeats the measurement through the host-buffer call
@@ -50,7 +50,7 @@ FP32_PER_SM_CLK = 128    # FP32 FMA results per SM per clock (4 x 32 lanes; meas
 SFU_PER_SM_CLK = 32      # ex2 results per SM per clock on B300 (measured 32.0)
 FP32_OPS_PER_PAIR = 8    # per algorithmic pair: ~4 for d^2, 1 exponent scale, C + 1 = 4 accumulations (C = 3)
 SM_MAX_MHZ = 2032.0      # B300 maximum SM clock
-LAUNCHES_PER_FORWARD = 6  # count, scan x2, scatter+plan, near, far
+LAUNCHES_PER_FORWARD = 4  # headline forward: count, one-launch scan, scatter+plan, near (no far kernel: none queued)
 
 
 def parse():
@@ -185,7 +185,7 @@ def near_kernel_traffic():
     """DRAM bytes per launch of the near kernel from the committed ncu summary,
     or None when the kernel source changed since the counters were taken."""
     path = os.path.join(ROOT, "profiles", "near_kernel_upsample_1024.txt")
-    src = os.path.join(ROOT, "paper_2012_13257_b300", "csrc", "gather_near.cu")
+    src = os.path.join(ROOT, "paper_2012_13257_b300", "csrc", "gather_staged.cu")
     if not os.path.exists(path):
         return None
     want = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]

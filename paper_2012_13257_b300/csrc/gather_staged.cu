@@ -22,9 +22,12 @@
 // records.  (Trimming each segment's ends to the thread's x-extent in its
 // row was measured: the trim loops cost more than the few records they skip.)
 //
-// A window with more bin rows or records than the buffer holds (dense
-// clusters, wide radii) is walked straight from global memory instead (the
-// direct walk of near_common.cuh).  A heavy warp tile cut into S work items
+// A window with more records than the buffer holds (dense clusters, wide
+// radii) is walked straight from global memory instead: each thread lists its
+// row segments in the warp's (then unused) staging buffer and keeps its next
+// few candidates in flight through a per-lane ring there (cp.async); a window
+// with more bin rows than the list holds takes the row-by-row direct walk of
+// near_common.cuh.  A heavy warp tile cut into S work items
 // (the plan in gather_near.cu) gives item k the k-th share of every thread's
 // candidate sequence.  Every wait on the barrier is bounded: if one gives up,
 // the kernel sets ST_TIMEOUT in the status word, waits (bounded again) for
