@@ -344,18 +344,25 @@ __global__ void __launch_bounds__(256) bwd_cov_kernel(KArgs a, BwdArgs b) {
   }
 }
 
-// Non-core pixels: one warp per queued micro-tile, lanes = (pixel, part).
+// Non-core pixels: one warp per queued micro-tile.  Its pixels (lanes
+// 0 .. PS - 1) put what their pairs need into shared memory; the candidates
+// are then taken 32 at a time, one per lane, and each lane walks the
+// micro-tile's non-core pixels (the same for every lane, read as shared-memory
+// broadcasts), summing its candidate's terms in registers; it then adds them
+// to the point's gradients with its own atomics (no cross-lane sums).
 template <int C>
 __global__ void __launch_bounds__(32 * kFarWarps) bwd_fallback_kernel(KArgs a_in, BwdArgs b) {
   const KArgs a = resolve(a_in);
   __shared__ unsigned lists[kFarWarps][kFarCap];
+  __shared__ float4 pxG[kFarWarps][32];   // per pixel: G_c = g_c / den
+  __shared__ float4 pxQ[kFarWarps][32];   // per pixel: centre x, y, s', pair limit emax
+  __shared__ float2 pxS[kFarWarps][32];   // per pixel: shift, sigma-term offset s0
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   unsigned* L = lists[wid];
   const unsigned nq = a.w.status[kFbCount];
-  const int PS = a.mth * a.mtw, nparts = 32 / PS;
-  const int slot = lane % PS, part = lane / PS;
-  const int pr = slot / a.mtw, pj = slot % a.mtw;
+  const int PS = a.mth * a.mtw;
+  const int pr = lane / a.mtw, pj = lane % a.mtw;
   for (;;) {
     unsigned e = 0;
     if (lane == 0) e = atomicAdd(&a.w.status[kFbHead], 1u);
@@ -374,7 +381,7 @@ __global__ void __launch_bounds__(32 * kFarWarps) bwd_fallback_kernel(KArgs a_in
     t.xb = (float)(x0 + nx) - 0.5f;
     t.ya = (float)y0 + 0.5f;
     t.yb = (float)(y0 + ny) - 0.5f;
-    const bool valid = pr < ny && pj < nx;
+    const bool valid = lane < PS && pr < ny && pj < nx;
     const float qx = (float)(x0 + pj) + 0.5f, qy = (float)(y0 + pr) + 0.5f;
     const long long px = (long long)(y0 + pr) * g.W + (x0 + pj);
     float d = 0.0f, sh = 0.0f, G[4] = {0.f, 0.f, 0.f, 0.f}, sp = 0.0f;
@@ -399,57 +406,59 @@ __global__ void __launch_bounds__(32 * kFarWarps) bwd_fallback_kernel(KArgs a_in
     // squared distance keeps the float32 rounding of t_i from being amplified
     // by a large d^2 (far field)
     const float s0 = sh > 0.0f ? 0.0f : (mine ? fmaxf(-log2f(d) / g.kappa, 0.0f) : 0.0f);
+    if (lane < PS) {
+      pxG[wid][lane] = make_float4(G[0], G[1], G[2], G[3]);
+      pxQ[wid][lane] = make_float4(qx, qy, sp, emax);
+      pxS[wid][lane] = make_float2(sh, s0);
+    }
+    const unsigned mm = __ballot_sync(full, mine);   // the micro-tile's non-core pixels
     float R2 = mine ? sh + emax : 0.0f;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) R2 = fmaxf(R2, __shfl_xor_sync(full, R2, o));
     R2 = R2 * (1.0f + 1e-6f) + 1e-6f;
     const float R = sqrtf(R2);
-    const unsigned total = collect(a, g, t, R, R2, 0u, L);
+    const unsigned total = collect(a, g, t, R, R2, 0u, L);   // (ends with a warp sync: the pixels are in place)
     float sig = 0.0f;
     for (unsigned skip = 0; skip < total; skip += kFarCap) {
       if (skip > 0) collect(a, g, t, R, R2, skip, L);
       const unsigned n = min(total - skip, (unsigned)kFarCap);
-      // the lanes of one part take the same candidate at once: their pairs'
-      // contributions are summed over the part's pixel lanes (shuffles), and
-      // one lane per part adds them to the point's gradients
-      for (unsigned k0 = 0; k0 < n; k0 += nparts) {
-        const unsigned k = k0 + part;
-        float cg[4] = {0.f, 0.f, 0.f, 0.f}, gx = 0.0f, gy = 0.0f;
+      for (unsigned c0 = 0; c0 < n; c0 += 32) {
+        const unsigned k = c0 + (unsigned)lane;
+        const bool act = k < n;
         unsigned idx = 0;
-        bool hit = false;   // this lane's pixel keeps the pair
-        if (k < n) {
+        float2 p = make_float2(0.f, 0.f);
+        float4 cv = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (act) {
           idx = L[k];
-          if (mine) {
-            const float2 p = a.w.sxy[idx];
-            const float dx = qx - p.x, dy = qy - p.y;
-            const float ee = sh > 0.0f ? shifted_sqdist(qx, qy, p.x, p.y, sh) : fmaf(dx, dx, dy * dy);
-            if (ee <= emax) {
-              hit = true;
-              const float w = ex2(-g.kappa * ee);
-              const float4 cv = a.w.sval[idx];
-              const float c4[4] = {cv.x, cv.y, cv.z, cv.w};
-              float tt = -sp;
+          p = a.w.sxy[idx];
+          cv = a.w.sval[idx];
+        }
+        const float c4[4] = {cv.x, cv.y, cv.z, cv.w};
+        float cg[4] = {0.f, 0.f, 0.f, 0.f}, gx = 0.0f, gy = 0.0f;
+        bool hit = false;   // some pixel keeps the pair
+        for (unsigned rem = mm; rem; rem &= rem - 1u) {
+          const int q = __ffs(rem) - 1;
+          const float4 Gq = pxG[wid][q];
+          const float4 Q = pxQ[wid][q];
+          const float2 Sq = pxS[wid][q];
+          const float dx = Q.x - p.x, dy = Q.y - p.y;
+          const float ee = Sq.x > 0.0f ? shifted_sqdist(Q.x, Q.y, p.x, p.y, Sq.x) : fmaf(dx, dx, dy * dy);
+          if (act && ee <= Q.w) {
+            hit = true;
+            const float w = ex2(-g.kappa * ee);
+            const float Gv[4] = {Gq.x, Gq.y, Gq.z, Gq.w};
+            float tt = -Q.z;
 #pragma unroll
-              for (int c = 0; c < C; ++c) tt = fmaf(G[c], c4[c], tt);
-              const float wt = w * tt;
+            for (int c = 0; c < C; ++c) tt = fmaf(Gv[c], c4[c], tt);
+            const float wt = w * tt;
 #pragma unroll
-              for (int c = 0; c < C; ++c) cg[c] = w * G[c];
-              gx = wt * dx;
-              gy = wt * dy;
-              sig = fmaf(wt, ee - s0, sig);   // ee is already d^2 - shift when shift > 0
-            }
+            for (int c = 0; c < C; ++c) cg[c] = fmaf(w, Gv[c], cg[c]);
+            gx = fmaf(wt, dx, gx);
+            gy = fmaf(wt, dy, gy);
+            sig = fmaf(wt, ee - Sq.y, sig);   // ee is already d^2 - shift when shift > 0
           }
         }
-        // any pair of this part kept?  (its PS lanes' bits of the ballot)
-        const unsigned hits = __ballot_sync(full, hit);
-        const unsigned pmask = PS == 32 ? full : ((1u << PS) - 1u) << (part * PS);
-        for (int o = PS >> 1; o > 0; o >>= 1) {
-#pragma unroll
-          for (int c = 0; c < C; ++c) cg[c] += __shfl_xor_sync(full, cg[c], o);
-          gx += __shfl_xor_sync(full, gx, o);
-          gy += __shfl_xor_sync(full, gy, o);
-        }
-        if (slot == 0 && (hits & pmask) != 0u) {
+        if (hit) {
           const unsigned o = a.w.perm[idx];
           if (bi.gvals) {
 #pragma unroll
@@ -461,8 +470,9 @@ __global__ void __launch_bounds__(32 * kFarWarps) bwd_fallback_kernel(KArgs a_in
           }
         }
       }
-      __syncwarp();
+      __syncwarp();   // the list (and, after the last chunk, the pixels) are rewritten next
     }
+    __syncwarp();
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) sig += __shfl_xor_sync(full, sig, o);
     if (lane == 0 && sig != 0.0f && bi.gsig) atomicAdd(bi.gsig, sig * bi.inv_s3);
