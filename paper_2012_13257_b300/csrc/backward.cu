@@ -21,9 +21,16 @@
 // Work is split by pixel:
 //   * core pixels (no shift, den_q >= 2^-12): point-centric.  One thread per
 //     bin-sorted point sweeps the disc of pixels within R_core, with
-//     kappa R_core^2 = 26 + 12, which holds every pair whose weight is at least
-//     2^-26 of its pixel's density sum; the thread owns its point's gradient,
+//     kappa R_core^2 = 20 + 12, which holds every pair whose weight is at least
+//     2^-20 of its pixel's density sum; the thread owns its point's gradient,
 //     so it is stored without atomics.
+//     What the cut drops: a point's pairs outside its disc carry together a
+//     normalised weight of at most 2 pi sigma^2 2^(-kappa R_core^2) / den_q
+//     (the Gaussian tail), i.e. 2 pi sigma^2 2^-20 (6e-6 at sigma = 1) times
+//     max |g| for the colour gradient even if every such pixel had the least
+//     core density 2^-12; the position and sigma terms carry the extra
+//     factors d / sigma^2 and d^2 / sigma^3 of the tail pairs.  Both stay far
+//     below the 1e-3 gradient tolerance.
 //   * other pixels (sparse neighbourhoods and the far field): one warp per
 //     micro-tile holding such pixels collects the points within the largest
 //     radius its pixels need, and adds the pairs' contributions atomically
@@ -37,7 +44,7 @@
 namespace gmi {
 
 constexpr float kCoreLog2 = 12.0f;   // core pixel: den >= 2^-kCoreLog2 and no shift
-constexpr float kRelLog2 = 26.0f;    // pairs below 2^-kRelLog2 of their pixel's den are dropped
+constexpr float kRelLog2 = 20.0f;    // pairs below 2^-kRelLog2 of their pixel's den are dropped
 
 __device__ __forceinline__ BwdImage bwd_image(const BwdArgs& b, int img) { return b.table ? b.table[img] : b.one; }
 

@@ -106,10 +106,13 @@ def test_plan_bounds_cover_the_nearest_distance(cuda_device, name, make, inside)
     near-field limit 100 / kappa; +inf marks the far-field micro-tiles.  With
     every point inside the frame (every non-empty bin usable), the ring
     search stops within about sqrt(m)/b + 2 rings, so U <= 2 (t + sqrt(m) +
-    3 b)^2 (t the micro-tile's side, m its largest nearest squared distance),
-    and only micro-tiles where that exceeds the limit may go to the far field."""
+    3 b)^2 (t the micro-tile's side, m its largest nearest squared distance).
+    The search walks at most RINGS bin rings, so a micro-tile may go to the
+    far field only when no point lies within RINGS rings of its bins, or when
+    that bound exceeds the limit."""
+    RINGS = 3
     im = make()
-    lay = run_and_read(im, cuda_device)[0]
+    lay, off = run_and_read(im, cuda_device)[:2]
     U = run_and_read.ubound.astype(np.float64).reshape(lay.wty, lay.wtx, 4, 8)   # [wty, wtx, ly, lx]
     U = U.transpose(0, 2, 1, 3).reshape(lay.wty * 4, lay.wtx * 8)                 # micro-tile rows x columns
     yy, xx = np.meshgrid(np.arange(im.H) + 0.5, np.arange(im.W) + 0.5, indexing="ij")
@@ -128,7 +131,22 @@ def test_plan_bounds_cover_the_nearest_distance(cuda_device, name, make, inside)
     if inside:
         loose = 2.0 * (max(lay.mth, lay.mtw) + np.sqrt(mmax) + 3.0 * lay.bin_px) ** 2
         assert (Ut[near] <= loose[near]).all()
-        assert (loose[~near] > limit).all()
+        # points within RINGS bin rings of each micro-tile's own bins (from the
+        # bin counts' 2D prefix sum)
+        b = lay.bin_px
+        counts = np.diff(off.astype(np.int64)).reshape(lay.nby, lay.nbx)
+        cs = np.zeros((lay.nby + 1, lay.nbx + 1), np.int64)
+        cs[1:, 1:] = counts.cumsum(0).cumsum(1)
+        x0 = np.arange(mtx) * lay.mtw
+        y0 = np.arange(mty) * lay.mth
+        bx0 = np.floor((x0 + 0.5) / b).astype(np.int64)
+        bx1 = np.floor((np.minimum(x0 + lay.mtw, im.W) - 0.5) / b).astype(np.int64)
+        by0 = np.floor((y0 + 0.5) / b).astype(np.int64)
+        by1 = np.floor((np.minimum(y0 + lay.mth, im.H) - 0.5) / b).astype(np.int64)
+        xa, xb = np.clip(bx0 - RINGS, 0, lay.nbx), np.clip(bx1 + RINGS + 1, 0, lay.nbx)
+        ya, yb = np.clip(by0 - RINGS, 0, lay.nby), np.clip(by1 + RINGS + 1, 0, lay.nby)
+        within = (cs[yb][:, xb] - cs[ya][:, xb] - cs[yb][:, xa] + cs[ya][:, xa]) > 0
+        assert ((~within[~near]) | (loose[~near] > limit)).all()
 
 
 def test_summed_area_table_is_exact(cuda_device):

@@ -4,7 +4,8 @@ must not stall on cudaMalloc/cudaFree, a binding that cannot pass a
 workspace).  It is called through the C ABI and must reproduce the
 workspace-based gmi_forward on two calls in a row (the second call must not
 be disturbed by what the first left in the shared static scratch), in exact
-and truncated mode, with and without the graph flag; it must fit a problem
+and truncated mode, with and without the graph flag, and match the FP64
+oracle directly (not only through gmi_forward); it must fit a problem
 near its limit, refuse problems larger than its scratch, and allocate no
 device memory.  Collected last on purpose."""
 import ctypes
@@ -12,6 +13,7 @@ import ctypes
 import numpy as np
 import pytest
 
+import oracle
 import workloads as wl
 from gpu_helpers import TOL_FWD, to_dev
 from paper_2012_13257_b300 import _lib
@@ -57,13 +59,25 @@ def _compare(got, ref):
     np.testing.assert_allclose(gshift, rshift, rtol=1e-6, atol=0)
 
 
+def _compare_oracle(got, im, mode):
+    """The image against the FP64 oracle (default k = 6); in truncated mode
+    only pixels that no point on the radius could decide are compared."""
+    ref = oracle.forward(im.points, im.values, im.H, im.W, im.sigma,
+                         mode=oracle.TRUNCATED if mode == "truncated" else oracle.EXACT, k=6.0)
+    decided = ref["skipped"] < 1e-3
+    assert decided.mean() > 0.99
+    assert np.abs(got[0] - ref["image"])[decided].max() <= TOL_FWD
+
+
 @pytest.mark.parametrize("graph", [False, True])
 @pytest.mark.parametrize("mode", ["exact", "truncated"])
 def test_noalloc_matches_gmi_forward_on_two_calls(cuda_device, mode, graph):
     first = wl.small_uniform()
     second = wl.tiny_random(5, 3000, 97, 131, C=3, sigma=0.9, clustered=True)   # has far-field pixels
     for im in (first, second):
-        _compare(_noalloc(im, cuda_device, mode, graph), _reference(im, cuda_device, mode))
+        got = _noalloc(im, cuda_device, mode, graph)
+        _compare(got, _reference(im, cuda_device, mode))
+        _compare_oracle(got, im, mode)
 
 
 def test_noalloc_near_its_limit(cuda_device):
