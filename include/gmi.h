@@ -150,7 +150,8 @@ gmi_status gmi_workspace_size(int64_t N, int C, int H, int W, const gmi_params* 
  *   workspace device, >= gmi_workspace_size bytes, 256-byte aligned; its
  *            contents on entry are ignored
  * Errors: as gmi_workspace_size, plus GMI_ERR_WORKSPACE, GMI_ERR_CUDA; with
- * GMI_FLAG_SYNC_CHECK also GMI_ERR_NONFINITE / GMI_ERR_INTERNAL.  On an
+ * GMI_FLAG_SYNC_CHECK also GMI_ERR_NONFINITE / GMI_ERR_TIMEOUT (a bounded
+ * device wait gave up; see gmi_set_wait_polls) / GMI_ERR_INTERNAL.  On an
  * argument error nothing is enqueued.
  */
 gmi_status gmi_forward(const float* points, const float* values, int64_t N, int C,
@@ -487,6 +488,18 @@ gmi_status gmi_profile_read(double* ms, int* launches, int reset);
  * Synchronous (device-wide), a few milliseconds; allocates and frees two small
  * device buffers.  Errors: GMI_ERR_INVALID_ARG (rates NULL), GMI_ERR_CUDA. */
 gmi_status gmi_measure_unit_rates(double* rates);
+
+/* Test aid for the device-side bounded waits (no counterpart in the paper).
+ * The near-field gather's staged path waits on an mbarrier for each work
+ * item's bulk copies, at most 10,000 polls (about a second); a warp that gives
+ * up records a timeout in the workspace's status word, waits (with the full
+ * limit) for its copies still in flight and leaves, so the context stays
+ * usable and a GMI_FLAG_SYNC_CHECK call returns GMI_ERR_TIMEOUT.  This sets,
+ * process-wide, how many polls that first wait gets in launches made from now
+ * on: polls in [0, 10000] (0: give up at once; larger values are capped at
+ * 10000), negative: back to the default.  CUDA graphs captured earlier keep
+ * the value they were captured with.  Always GMI_OK. */
+gmi_status gmi_set_wait_polls(int64_t polls);
 
 /* ------------------------------------------------------------------------
  * Batched forward: B independent images of uneven size in one persistent

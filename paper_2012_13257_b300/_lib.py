@@ -118,6 +118,7 @@ SIGNATURES = {
     "gmi_profile_enable": (_int, [_int]),
     "gmi_profile_read": (_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), _int]),
     "gmi_measure_unit_rates": (_int, [ctypes.POINTER(ctypes.c_double)]),
+    "gmi_set_wait_polls": (_int, [_i64]),
     "gmi_autotune": (_int, [_vp, _vp, ctypes.c_int64, _int, _int, _int, ctypes.POINTER(Params),
                             ctypes.POINTER(_int), _int, _int, ctypes.POINTER(Params),
                             ctypes.POINTER(ctypes.c_float), _vp]),

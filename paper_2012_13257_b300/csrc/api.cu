@@ -290,6 +290,7 @@ gmi_status run_forward_pipeline(KArgs& a, const WsLayout& L, void* ws, int mth, 
   constexpr long long kFarInNearPixels = 1LL << 21;
   a.far_in_near =
       staged && !trunc && !a.totals && (long long)a.g0.H * a.g0.W <= kFarInNearPixels ? 1 : 0;
+  a.stage_wait_polls = stage_wait_polls();
   const ProfileMark pn = profile_begin(GMI_STAGE_NEAR, s);
   const cudaError_t en = staged ? launch_near_staged(a, mth, mtw, trunc, gn, s) : launch_near(a, mth, mtw, trunc, ppk, gn, s);
   if (en != cudaSuccess) return GMI_ERR_CUDA;
@@ -328,7 +329,8 @@ gmi_status read_status(const void* ws, cudaStream_t s) {
   if (cudaMemcpy(&st, ws, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess) return GMI_ERR_CUDA;
   if (st & ST_NONFINITE) return GMI_ERR_NONFINITE;
   if (st & ST_SIGMA) return GMI_ERR_INVALID_ARG;
-  if (st & (ST_INTERNAL | ST_TIMEOUT | ST_BOUNDS | ST_CANARY)) return GMI_ERR_INTERNAL;
+  if (st & (ST_INTERNAL | ST_BOUNDS | ST_CANARY)) return GMI_ERR_INTERNAL;
+  if (st & ST_TIMEOUT) return GMI_ERR_TIMEOUT;
   return GMI_OK;
 }
 
@@ -480,6 +482,11 @@ gmi_status forward_in_share(const float* points, const float* values, int64_t N,
 }
 
 }  // namespace gmi
+
+extern "C" gmi_status gmi_set_wait_polls(int64_t polls) {
+  set_stage_wait_polls((long long)polls);
+  return GMI_OK;
+}
 
 extern "C" {
 

@@ -52,6 +52,10 @@ WsLayout ws_layout(long long n_total, long long nb_total, long long mt_total, lo
 long long sat_entries(const ImageGeom& g);
 long long sat_jobs(const ImageGeom& g);
 DevWork bind_ws(void* ws, const WsLayout& L);
+// Poll limit of the staged gather's first wait on its copies (gmi_set_wait_polls).
+void set_stage_wait_polls(long long polls);
+unsigned stage_wait_polls();
+
 gmi_status run_bin_and_plan(KArgs& a, const WsLayout& L, void* ws, int mth, int mtw, bool trunc,
                             cudaStream_t s, bool plan);
 // ppk: per-point sigmas (a.g0.sigmas set; truncated mode): 1 separable

@@ -186,6 +186,7 @@ struct KArgs {
   int mth, mtw;          // micro-tile of the near kernel
   int gather;            // GMI_GATHER_* of the call (host-side choice of the near kernel)
   int far_in_near;       // the staged near kernel takes the far-field micro-tiles (no far kernel)
+  unsigned stage_wait_polls;  // polls of the staged gather's first wait on its copies (gmi_set_wait_polls)
   const long long* totals;  // batched: device copy of the totals below (else null)
 };
 

@@ -36,6 +36,8 @@
 #include "near_common.cuh"
 #include "sat.cuh"
 
+#include <algorithm>
+#include <atomic>
 #include <climits>
 
 namespace gmi {
@@ -46,6 +48,19 @@ constexpr int kStageWarps = 4;    // warps per block
 // after about a second, and a waiting warp takes no issue slots meanwhile).
 constexpr unsigned kWaitPolls = 10000u;
 constexpr unsigned kWaitHintNs = 100000u;
+
+// Polls of the first wait on a work item's copies for launches from now on
+// (set_stage_wait_polls: fewer than kWaitPolls, 0 to give up at once, which
+// exercises the error path; negative: kWaitPolls).  The wait for copies still
+// in flight after a give-up always keeps kWaitPolls.
+static std::atomic<long long> g_stage_wait_polls{-1};
+
+void set_stage_wait_polls(long long polls) { g_stage_wait_polls.store(polls); }
+
+unsigned stage_wait_polls() {
+  const long long v = g_stage_wait_polls.load();
+  return v < 0 ? kWaitPolls : (unsigned)std::min<long long>(v, (long long)kWaitPolls);
+}
 
 // One warp's shared-memory area.
 template <int CAP>
@@ -103,9 +118,10 @@ __device__ __forceinline__ bool mbar_test(unsigned long long* bar, unsigned pari
   return done != 0u;
 }
 
-// Waits for the phase of the given parity; false after kWaitPolls polls.
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
-  for (unsigned k = 0; k < kWaitPolls; ++k)
+// Waits for the phase of the given parity; false after `polls` polls (none:
+// false at once).
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, unsigned polls = kWaitPolls) {
+  for (unsigned k = 0; k < polls; ++k)
     if (mbar_test(bar, parity)) return true;
   return false;
 }
@@ -475,7 +491,7 @@ __global__ void __launch_bounds__(32 * kStageWarps, StagedOcc<MTH, MTW, C>::valu
 #pragma unroll
         for (int k = 0; k < MTH * MTW * ODD + 1 - ODD; ++k) accs[k] = 0.0f;
         if (total > 0u) {
-          const bool ok = mbar_wait(&sb.bar, parity);
+          const bool ok = mbar_wait(&sb.bar, parity, a.stage_wait_polls);
           if (__any_sync(full, !ok)) stalled = true;
         }
         parity ^= 1u;   // the arrival completes a phase even when nothing is copied
@@ -602,7 +618,7 @@ __global__ void __launch_bounds__(32 * kStageWarps, StagedOcc<MTH, MTW, C>::valu
             }
           }
           if (total > 0u) {
-            const bool ok = mbar_wait(&sb.bar, parity);
+            const bool ok = mbar_wait(&sb.bar, parity, a.stage_wait_polls);
             if (__any_sync(full, !ok)) stalled = true;
           }
           parity ^= 1u;   // the arrival completes a phase even when nothing is copied
