@@ -490,15 +490,21 @@ gmi_status gmi_profile_read(double* ms, int* launches, int reset);
 gmi_status gmi_measure_unit_rates(double* rates);
 
 /* Test aid for the device-side bounded waits (no counterpart in the paper).
- * The near-field gather's staged path waits on an mbarrier for each work
- * item's bulk copies, at most 10,000 polls (about a second); a warp that gives
- * up records a timeout in the workspace's status word, waits (with the full
- * limit) for its copies still in flight and leaves, so the context stays
- * usable and a GMI_FLAG_SYNC_CHECK call returns GMI_ERR_TIMEOUT.  This sets,
- * process-wide, how many polls that first wait gets in launches made from now
- * on: polls in [0, 10000] (0: give up at once; larger values are capped at
- * 10000), negative: back to the default.  CUDA graphs captured earlier keep
- * the value they were captured with.  Always GMI_OK. */
+ * Two waits can give up without harm, and each records a timeout in the
+ * workspace's status word, so that a GMI_FLAG_SYNC_CHECK call returns
+ * GMI_ERR_TIMEOUT and the context stays usable:
+ *   - the one-launch bin-count scan of single images waits at a grid
+ *     barrier (at most 2^20 polls, about 0.1 s); a block that gives up also
+ *     marks the bin offsets invalid, and the kernels after it then keep to
+ *     their arrays and do no gather work;
+ *   - the near-field gather's staged path waits on an mbarrier for each work
+ *     item's bulk copies (at most 10,000 polls, about a second); a warp that
+ *     gives up waits (with the full limit) for its copies still in flight
+ *     and leaves.
+ * This sets, process-wide, how many polls those waits get in launches made
+ * from now on: polls >= 0 (0: give up at once; each wait keeps at most its
+ * own default), negative: back to the defaults.  CUDA graphs captured
+ * earlier keep the values they were captured with.  Always GMI_OK. */
 gmi_status gmi_set_wait_polls(int64_t polls);
 
 /* ------------------------------------------------------------------------

@@ -8,6 +8,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
 #include <mutex>
 
 #include "api_internal.h"
@@ -27,7 +28,7 @@ cudaError_t launch_far(const KArgs& a, int mth, int mtw, int sms, cudaStream_t s
 __global__ void bin_count_kernel(KArgs a);
 __global__ void scan_partial_kernel(const unsigned* cnt, long long nb, unsigned* partials, const long long* totals);
 __global__ void scan_final_kernel(unsigned* off, long long nb, const unsigned* partials, const long long* totals);
-__global__ void scan_one_kernel(unsigned* off, long long nb, unsigned* partials, unsigned* status);
+__global__ void scan_one_kernel(unsigned* off, long long nb, unsigned* partials, unsigned* status, unsigned polls);
 
 // Blocks of the one-launch scan that can be resident on the device at once
 // (cached; filled before any capture by warm_near_caches).
@@ -242,8 +243,8 @@ gmi_status run_bin_and_plan(KArgs& a, const WsLayout& L, void* ws, int mth, int 
       cfg.stream = s;
       cfg.attrs = attr;
       cfg.numAttrs = 1;
-      if (cudaLaunchKernelEx(&cfg, scan_one_kernel, a.w.off, (long long)a.nb_total, a.w.partials, a.w.status) !=
-          cudaSuccess)
+      if (cudaLaunchKernelEx(&cfg, scan_one_kernel, a.w.off, (long long)a.nb_total, a.w.partials, a.w.status,
+                             scan_wait_polls()) != cudaSuccess)
         return GMI_ERR_CUDA;
     } else {
       scan_partial_kernel<<<ns, 256, 0, s>>>(a.w.off, a.nb_total, a.w.partials, a.totals);
@@ -330,7 +331,7 @@ gmi_status read_status(const void* ws, cudaStream_t s) {
   if (st & ST_NONFINITE) return GMI_ERR_NONFINITE;
   if (st & ST_SIGMA) return GMI_ERR_INVALID_ARG;
   if (st & (ST_INTERNAL | ST_BOUNDS | ST_CANARY)) return GMI_ERR_INTERNAL;
-  if (st & ST_TIMEOUT) return GMI_ERR_TIMEOUT;
+  if (st & (ST_TIMEOUT | ST_BINS)) return GMI_ERR_TIMEOUT;
   return GMI_OK;
 }
 
@@ -483,8 +484,16 @@ gmi_status forward_in_share(const float* points, const float* values, int64_t N,
 
 }  // namespace gmi
 
+namespace gmi {
+
+static std::atomic<long long> g_wait_polls{-1};
+
+long long wait_polls_setting() { return g_wait_polls.load(); }
+
+}  // namespace gmi
+
 extern "C" gmi_status gmi_set_wait_polls(int64_t polls) {
-  set_stage_wait_polls((long long)polls);
+  g_wait_polls.store((long long)polls);
   return GMI_OK;
 }
 

@@ -52,9 +52,13 @@ WsLayout ws_layout(long long n_total, long long nb_total, long long mt_total, lo
 long long sat_entries(const ImageGeom& g);
 long long sat_jobs(const ImageGeom& g);
 DevWork bind_ws(void* ws, const WsLayout& L);
-// Poll limit of the staged gather's first wait on its copies (gmi_set_wait_polls).
-void set_stage_wait_polls(long long polls);
+// gmi_set_wait_polls: the process-wide poll limit of the device waits that
+// may be made to give up (negative: their defaults), and each wait's limit
+// from it: the staged gather's first wait on its copies, the one-launch
+// scan's grid barrier.
+long long wait_polls_setting();
 unsigned stage_wait_polls();
+unsigned scan_wait_polls();
 
 gmi_status run_bin_and_plan(KArgs& a, const WsLayout& L, void* ws, int mth, int mtw, bool trunc,
                             cudaStream_t s, bool plan);

@@ -128,6 +128,7 @@ template <int C, bool TRUNC, bool PP>
 __global__ void __launch_bounds__(256) bwd_point_kernel(KArgs a_in, BwdArgs b, float rcore_log2) {
   static_assert(TRUNC || !PP, "per-point sigma is built for truncated mode only");
   const KArgs a = resolve(a_in);
+  if (bins_invalid(a.w.status)) return;
   const unsigned full = 0xffffffffu;
   float D = 0.0f;
   for (long long i0 = (long long)blockIdx.x * blockDim.x; i0 < a.n_total; i0 += (long long)gridDim.x * blockDim.x) {
@@ -273,6 +274,7 @@ __global__ void __launch_bounds__(256) bwd_point_kernel(KArgs a_in, BwdArgs b, f
 //   SQ = sum wt Q = (Sxx / sx^2 - 2 rho Sxy / (sx sy) + Syy / sy^2) / e.
 template <int C>
 __global__ void __launch_bounds__(256) bwd_cov_kernel(KArgs a, BwdArgs b) {
+  if (bins_invalid(a.w.status)) return;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.n_total;
        i += (long long)gridDim.x * blockDim.x) {
     const ImageGeom& g = a.g0;
@@ -360,6 +362,7 @@ __global__ void __launch_bounds__(256) bwd_cov_kernel(KArgs a, BwdArgs b) {
 template <int C>
 __global__ void __launch_bounds__(32 * kFarWarps) bwd_fallback_kernel(KArgs a_in, BwdArgs b) {
   const KArgs a = resolve(a_in);
+  if (bins_invalid(a.w.status)) return;
   __shared__ unsigned lists[kFarWarps][kFarCap];
   __shared__ float4 pxG[kFarWarps][32];   // per pixel: G_c = g_c / den
   __shared__ float4 pxQ[kFarWarps][32];   // per pixel: centre x, y, s', pair limit emax

@@ -12,6 +12,9 @@
 //   bin_scatter  bin-sorted copies of positions (float2) and colours (float4);
 //                flags non-finite colours
 #include "bin_body.cuh"
+#include "api_internal.h"
+
+#include <algorithm>
 
 namespace gmi {
 
@@ -150,12 +153,22 @@ __global__ void __launch_bounds__(256) scan_final_kernel(unsigned* __restrict__ 
 // once (launched cooperatively, so the hardware guarantees it): each block
 // sums its chunk and publishes the sum, waits at a grid barrier until every
 // block has, then adds the sums of the earlier chunks to its own scan.  The
-// wait is bounded (about 0.1 s); a block that gives up sets ST_TIMEOUT and
-// goes on (the offsets are then wrong and the call reports an error).
+// wait is bounded (`polls` polls, at most kScanWaitPolls, about 0.1 s); a
+// block that gives up sets ST_TIMEOUT and ST_BINS and goes on: its offsets
+// are then wrong, so the scatter keeps every write inside its arrays, the
+// plan marks every micro-tile inactive and queues no far-field work, the
+// other kernels that follow the offsets leave at once (bins_invalid), and the
+// call reports the timeout.
 constexpr unsigned kScanWaitPolls = 1u << 20;
 
+unsigned scan_wait_polls() {
+  const long long v = wait_polls_setting();
+  return v < 0 ? kScanWaitPolls : (unsigned)std::min<long long>(v, (long long)kScanWaitPolls);
+}
+
 __global__ void __launch_bounds__(256) scan_one_kernel(unsigned* __restrict__ off, long long nb,
-                                                       unsigned* __restrict__ partials, unsigned* status) {
+                                                       unsigned* __restrict__ partials, unsigned* status,
+                                                       unsigned polls) {
   constexpr int kPer = kScanChunk / 256;
   __shared__ unsigned warp_tot[8];
   __shared__ unsigned block_prefix;
@@ -187,15 +200,14 @@ __global__ void __launch_bounds__(256) scan_one_kernel(unsigned* __restrict__ of
     partials[blockIdx.x] = btot;
     __threadfence();
     atomicAdd(&status[kScanArrive], 1u);
-    unsigned k = 0;
-    while (true) {
+    for (unsigned k = 0;; ++k) {
+      if (k >= polls) {
+        atomicOr(&status[kStatusErr], ST_TIMEOUT | ST_BINS);
+        break;
+      }
       unsigned n;
       asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(n) : "l"(status + kScanArrive) : "memory");
       if (n >= gridDim.x) break;
-      if (++k == kScanWaitPolls) {
-        atomicOr(&status[kStatusErr], ST_TIMEOUT);
-        break;
-      }
       __nanosleep(64);
     }
   }
@@ -225,6 +237,7 @@ __global__ void __launch_bounds__(256) scan_one_kernel(unsigned* __restrict__ of
 
 __global__ void __launch_bounds__(256) bin_scatter_kernel(KArgs a_in) {
   const KArgs a = resolve(a_in);
+  if (bins_invalid(a.w.status)) return;
   bin_scatter_body(a, gridDim.x, blockIdx.x);
 }
 

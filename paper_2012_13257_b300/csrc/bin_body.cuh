@@ -34,7 +34,8 @@ static __device__ __forceinline__ void scatter_single(const KArgs& a, int nblock
       if (a.C > 2) c.z = v[2];
       if (a.C > 3) c.w = v[3];
       fin = fin && isfinite(c.x) && isfinite(c.y) && isfinite(c.z) && isfinite(c.w);
-      if (GMI_IN_BOUNDS(a.w, dst, a.n_total, CK_SCATTER)) {
+      // (dst < n_total also when the scan gave up and the offsets are not valid)
+      if (GMI_IN_BOUNDS(a.w, dst, a.n_total, CK_SCATTER) && dst < (unsigned long long)a.n_total) {
         a.w.sxy[dst] = p;
         a.w.sval[dst] = c;
         a.w.perm[dst] = (unsigned)i;
@@ -70,7 +71,7 @@ static __device__ __forceinline__ void bin_scatter_body(const KArgs& a, int nblo
       if (a.C > 2) c.z = v[2];
       if (a.C > 3) c.w = v[3];
       fin = fin && isfinite(c.x) && isfinite(c.y) && isfinite(c.z) && isfinite(c.w);
-      const bool ok = GMI_IN_BOUNDS(a.w, dst, a.n_total, CK_SCATTER);
+      const bool ok = GMI_IN_BOUNDS(a.w, dst, a.n_total, CK_SCATTER) && dst < (unsigned long long)a.n_total;
       if (ok) {
         a.w.sxy[dst] = p;
         a.w.sval[dst] = c;

@@ -23,6 +23,7 @@ enum : unsigned {
   ST_SIGMA = 8u,       // a per-point sigma outside its range (sigmas_ok)
   ST_BOUNDS = 16u,     // checked builds: an index failed its bounds check (the access was skipped)
   ST_CANARY = 32u,     // checked builds: a guard area after a workspace region was overwritten
+  ST_BINS = 64u,       // the one-launch scan gave up at its grid barrier: the bin offsets are not valid
 };
 
 // Slots of the status/counter block at the start of every workspace.
@@ -46,6 +47,16 @@ enum : int {
   kSatDone = 16,       // summed-area-table column jobs finished
   kStatusWords = 64,
 };
+
+// True when the bin offsets of this call are not valid (the one-launch scan
+// gave up at its grid barrier): every kernel that follows the offsets or the
+// bin-sorted arrays leaves at once, so that nothing indexes past its arrays,
+// and the call reports the timeout.  The word cannot change while those
+// kernels run, so every thread takes the same decision.
+__device__ __forceinline__ bool bins_invalid(const unsigned* status) {
+  return (__ldcg(&status[kStatusErr]) & ST_BINS) != 0u;
+}
+
 
 constexpr int kPassRows = 16;     // most window bin rows the staged gather stages at once
 

@@ -11,6 +11,7 @@ namespace gmi {
 template <int C>
 __global__ void __launch_bounds__(32 * kFarWarps) far_kernel(KArgs a_in, int mth, int mtw) {
   const KArgs a = resolve(a_in);
+  if (bins_invalid(a.w.status)) return;
   __shared__ unsigned lists[kFarWarps][kFarCap];
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;

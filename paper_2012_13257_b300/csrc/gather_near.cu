@@ -323,11 +323,21 @@ __device__ void near_plan_body(const KArgs& a, int trunc, long long wt) {
   const bool active = x0 < g.W && y0 < g.H;
   const int nx = active ? min(MTW, g.W - x0) : 0;
   const int ny = active ? min(MTH, g.H - y0) : 0;
+  // Bin offsets left invalid by a scan that gave up (ST_BINS; the load
+  // overlaps near_bound's): the micro-tiles are then all marked inactive, no
+  // far-field work is queued and no staging plan is valid, so that the
+  // gathers after this kernel have nothing to walk (every read above stays
+  // inside its array whatever the offsets hold).
+  const bool bins_bad = bins_invalid(a.w.status);
   float U = 0.0f;
   bool far = false;
   if (!trunc && active) {
     U = near_bound<MTH, MTW>(a, g, x0, y0, nx, ny);
     far = !(U <= g.u_near_max);
+  }
+  if (bins_bad) {
+    U = INFINITY;
+    far = false;
   }
   if (!trunc) {
     const unsigned fm = __ballot_sync(full, far);
@@ -342,7 +352,7 @@ __device__ void near_plan_body(const KArgs& a, int trunc, long long wt) {
     }
   }
   a.w.ubound[wt * 32 + lane] = far ? INFINITY : U;
-  const bool act = active && !far;
+  const bool act = active && !far && !bins_bad;
   PlanLoads P;
   plan_loads<MTH, MTW>(a, g, wt, act, U + g.r2k, x0, y0, nx, ny, P);
   unsigned cnt = 0;

@@ -70,7 +70,10 @@ __device__ __forceinline__ double pp_lw_d(const KArgs& a, const ImageGeom& g, un
 
 // The summed-area table of the bin counts (the smallest-window search reads
 // it), as a kernel of its own: no near kernel runs in this mode.
-__global__ void __launch_bounds__(128) pp_sat_kernel(KArgs a) { sat_build(a); }
+__global__ void __launch_bounds__(128) pp_sat_kernel(KArgs a) {
+  if (bins_invalid(a.w.status)) return;
+  sat_build(a);
+}
 
 // Per-micro-tile state of steps A and B: the candidate radius, whether the
 // quadratic forms can exceed kPpNarrowQ (then FP64), and whether the image
@@ -179,6 +182,7 @@ __device__ __forceinline__ void pp_pixel_sums(const KArgs& a, const ImageGeom& g
 template <int C, int PPK>
 __global__ void __launch_bounds__(32 * kFarWarps) pp_exact_kernel(KArgs a, int mth, int mtw) {
   __shared__ unsigned lists[kFarWarps][kFarCap];
+  if (bins_invalid(a.w.status)) return;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   unsigned* L = lists[wid];
   const ImageGeom g = a.g0;
@@ -226,6 +230,7 @@ template <int C, int PPK>
 __global__ void __launch_bounds__(32 * kFarWarps) pp_exact_bwd_kernel(KArgs a, int mth, int mtw, const float* grad,
                                                                       float* mom) {
   __shared__ unsigned lists[kFarWarps][kFarCap];
+  if (bins_invalid(a.w.status)) return;
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   unsigned* L = lists[wid];
@@ -321,6 +326,7 @@ __global__ void __launch_bounds__(32 * kFarWarps) pp_exact_bwd_kernel(KArgs a, i
 // an isotropic sigma_i gets dL/dsx + dL/dsy.
 template <int C>
 __global__ void __launch_bounds__(256) pp_exact_finish_kernel(KArgs a, BwdImage bi, const float* mom) {
+  if (bins_invalid(a.w.status)) return;
   const ImageGeom g = a.g0;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.n_total;
        i += (long long)gridDim.x * blockDim.x) {

@@ -37,7 +37,6 @@
 #include "sat.cuh"
 
 #include <algorithm>
-#include <atomic>
 #include <climits>
 
 namespace gmi {
@@ -49,16 +48,14 @@ constexpr int kStageWarps = 4;    // warps per block
 constexpr unsigned kWaitPolls = 10000u;
 constexpr unsigned kWaitHintNs = 100000u;
 
-// Polls of the first wait on a work item's copies for launches from now on
-// (set_stage_wait_polls: fewer than kWaitPolls, 0 to give up at once, which
-// exercises the error path; negative: kWaitPolls).  The wait for copies still
-// in flight after a give-up always keeps kWaitPolls.
-static std::atomic<long long> g_stage_wait_polls{-1};
-
-void set_stage_wait_polls(long long polls) { g_stage_wait_polls.store(polls); }
+// Polls of the first wait on a work item's copies in launches from now on:
+// the gmi_set_wait_polls setting capped at kWaitPolls (0 gives up at once,
+// which exercises the error path; negative: kWaitPolls).  The wait for copies
+// still in flight after a give-up always keeps kWaitPolls.
+long long wait_polls_setting();   // api.cu: the gmi_set_wait_polls setting
 
 unsigned stage_wait_polls() {
-  const long long v = g_stage_wait_polls.load();
+  const long long v = wait_polls_setting();
   return v < 0 ? kWaitPolls : (unsigned)std::min<long long>(v, (long long)kWaitPolls);
 }
 
