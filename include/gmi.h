@@ -341,8 +341,10 @@ gmi_status gmi_workspace_layout(int64_t N, int C, int H, int W, const gmi_params
 
 /*
  * Reads the device status word of a workspace after its stream has finished
- * (synchronises `stream` first).  Returns GMI_OK, GMI_ERR_NONFINITE or
- * GMI_ERR_INTERNAL for the last call that used the workspace.
+ * (synchronises `stream` first).  Returns GMI_OK, GMI_ERR_NONFINITE,
+ * GMI_ERR_INVALID_ARG (a per-point sigma out of range), GMI_ERR_TIMEOUT (a
+ * bounded device wait gave up) or GMI_ERR_INTERNAL for the last call that
+ * used the workspace.
  */
 gmi_status gmi_workspace_status(const void* workspace, gmi_stream_t stream);
 
