@@ -191,3 +191,13 @@ def test_checked_build_exports_and_layout():
     rep = (ctypes.c_uint32 * 4)()
     assert lib.gmi_check_workspace(1000, 3, 64, 64, ctypes.byref(p), 256, a.value, None, rep) == 7
     assert lib.gmi_batch_check_workspace(256, None, rep) == 7
+
+
+def test_wait_limit_setting_is_host_only():
+    """gmi_set_wait_polls only records the limit for later launches: it needs
+    no GPU, takes any value (negative restores the defaults) and always
+    returns GMI_OK."""
+    lib = _lib.load()
+    for polls in (0, 1, 10_000, 1 << 40, -1):
+        assert lib.gmi_set_wait_polls(polls) == 0
+    assert lib.gmi_set_wait_polls(-1) == 0
