@@ -428,21 +428,23 @@ def bench_batched(dev, steps, warmup, flush, stream, autotune=True):
         if key not in rep or im.H * im.W > imgs[rep[key]].H * imgs[rep[key]].W:
             rep[key] = i
     t0 = time.perf_counter()
-    work = {1: 1}   # without tuning: the 4x4 micro-tile and the automatic bin rule
-    if autotune:
-        work = {}
+    # without tuning: the 4x4 micro-tile, the automatic bin rule and the staged gather
+    work, gwork = ({1: 1}, {"staged": 1}) if not autotune else ({}, {})
     for key, i in (rep.items() if autotune else ()):
         best, _ = tuner.tune(dimgs[i]["points"], dimgs[i]["values"], imgs[i].sigma, imgs[i].H, imgs[i].W,
                              reps=3, warmup=1, save=False)
-        work.setdefault(best["variant"], 0)
-        work[best["variant"]] += sum(im.H * im.W for im in imgs
-                                     if bucket(im.sigma, im.N / float(im.H * im.W), 3) == key)
+        px = sum(im.H * im.W for im in imgs if bucket(im.sigma, im.N / float(im.H * im.W), 3) == key)
+        work[best["variant"]] = work.get(best["variant"], 0) + px
+        gwork[best["gather"]] = gwork.get(best["gather"], 0) + px
         for j, im in enumerate(imgs):
             if bucket(im.sigma, im.N / float(im.H * im.W), 3) == key:
                 dimgs[j]["bin_px"] = best["bin_px"]
+    # one launch takes one micro-tile and one gather: those the most pixels' buckets chose
     variant = max(work, key=work.get)
+    gather = max(gwork, key=gwork.get)
     tune_s = time.perf_counter() - t0
-    plan = gmi.BatchPlan(64, sum(im.N for im in imgs), sum(im.H * im.W for im in imgs), 3, variant=variant)
+    plan = gmi.BatchPlan(64, sum(im.N for im in imgs), sum(im.H * im.W for im in imgs), 3, variant=variant,
+                         gather=gather)
     for _ in range(max(3, warmup)):
         plan.forward(dimgs, use_graph=True)
     torch.cuda.synchronize()
@@ -467,7 +469,7 @@ def bench_batched(dev, steps, warmup, flush, stream, autotune=True):
 
     def plain():
         for d in dimgs:
-            gmi.interpolate(d["points"], d["values"], d["sigma"], d["H"], d["W"], out=d["out"])
+            gmi.interpolate(d["points"], d["values"], d["sigma"], d["H"], d["W"], out=d["out"], gather=gather)
     for _ in range(2):
         plain()
     torch.cuda.synchronize()
@@ -492,7 +494,8 @@ def bench_batched(dev, steps, warmup, flush, stream, autotune=True):
                          "frac_step": pairs / (sum(tb) / steps * 1e-3) / 1e9 / peak,
                          "peak_basis": "FP32 pipe at %.0f MHz, %d FP32 ops per algorithmic pair" %
                                        (SM_MAX_MHZ, FP32_OPS_PER_PAIR)},
-            "autotune": {"variant": variant, "buckets": len(rep), "tune_s": tune_s, "on": bool(autotune)},
+            "autotune": {"variant": variant, "gather": gather, "buckets": len(rep), "tune_s": tune_s,
+                         "on": bool(autotune)},
             "workload": "64 images, sides log-uniform [128,1024], N=0.25HW clustered (8 clusters), "
                         "sigma U[0.5,2], RGB f32; one CUDA-graph batched launch per step vs 64 plain launches"}
 

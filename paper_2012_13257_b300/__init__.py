@@ -61,19 +61,34 @@ def set_gather(kind: str) -> None:
     "staged" (each warp stages its window in shared memory) or "direct"
     (each thread loads its candidates through the L1 cache).  Both give the
     same sums; the choice exists to compare their speed."""
-    kinds = {"auto": _lib.GATHER_AUTO, "staged": _lib.GATHER_STAGED, "direct": _lib.GATHER_DIRECT}
-    if kind not in kinds:
-        raise ValueError("gather must be one of %s" % sorted(kinds))
-    _lib.DEFAULT_GATHER = kinds[kind]
+    if kind not in _GATHERS:
+        raise ValueError("gather must be one of %s" % sorted(_GATHERS))
+    _lib.DEFAULT_GATHER = _GATHERS[kind]
 
 
-def _params(sigma, radius_sigmas, mode, flags, bin_px, variant):
-    key = (float(sigma), float(radius_sigmas), mode, flags, bin_px, variant, _lib.DEFAULT_GATHER)
+_GATHERS = {"auto": _lib.GATHER_AUTO, "staged": _lib.GATHER_STAGED, "direct": _lib.GATHER_DIRECT}
+
+
+def _gather_code(gather) -> int:
+    """params.gather for a call: the process default (set_gather) when None,
+    else "auto", "staged" or "direct"."""
+    if gather is None:
+        return int(_lib.DEFAULT_GATHER)
+    if gather not in _GATHERS:
+        raise ValueError("gather must be one of %s" % sorted(_GATHERS))
+    return _GATHERS[gather]
+
+
+def _params(sigma, radius_sigmas, mode, flags, bin_px, variant, gather=None):
+    g = _gather_code(gather)
+    key = (float(sigma), float(radius_sigmas), mode, flags, bin_px, variant, g)
     p = _param_cache.get(key)
     if p is None:
         if len(_param_cache) > 4096:
             _param_cache.clear()
-        p = _param_cache[key] = _lib.make_params(sigma, radius_sigmas, mode, flags, bin_px, variant)
+        p = _lib.make_params(sigma, radius_sigmas, mode, flags, bin_px, variant)
+        p.gather = g
+        _param_cache[key] = p
     return p
 
 
@@ -131,7 +146,7 @@ def _check_inputs(points, values):
 
 def interpolate(points, values, sigma: float, H: int, W: int, *, radius_sigmas: float = 6.0,
                 mode="exact", bin_px: int = 0, variant: int = 0, return_aux: bool = False,
-                check: bool = False, graph: bool = False, out=None):
+                check: bool = False, graph: bool = False, out=None, gather=None):
     """Forward pass of Eq. 1 / Eq. 2 onto an H x W raster.
 
     Returns the image ``[H, W, C]``; with ``return_aux`` also the per-pixel
@@ -140,7 +155,9 @@ def interpolate(points, values, sigma: float, H: int, W: int, *, radius_sigmas: 
     (non-finite inputs).  ``graph=True`` replays a cached CUDA graph of the
     launch sequence when the same tensors (``out`` included) and sizes come
     again: pass ``out`` to reuse buffers across calls.  Runs on the current
-    CUDA stream.
+    CUDA stream.  ``gather`` ("staged", "direct" or "auto"; None: the
+    process default of set_gather) chooses how the near-field gather reads
+    its candidates, e.g. as the autotuner picked it.
     """
     import torch
     points, values = _check_inputs(points, values)
@@ -149,7 +166,7 @@ def interpolate(points, values, sigma: float, H: int, W: int, *, radius_sigmas: 
     dev = points.device
     flags = (_lib.FLAG_SYNC_CHECK if check else 0) | (_lib.FLAG_GRAPH if graph else 0)
     md = _mode(mode)
-    p = _params(sigma, radius_sigmas, md, flags, bin_px, variant)
+    p = _params(sigma, radius_sigmas, md, flags, bin_px, variant, gather)
     nbytes = _ws_bytes(N, C, H, W, p, (N, C, H, W, float(sigma), float(radius_sigmas), md, bin_px, variant))
     if out is None:
         out = torch.empty((H, W, C), dtype=torch.float32, device=dev)
@@ -161,7 +178,7 @@ def interpolate(points, values, sigma: float, H: int, W: int, *, radius_sigmas: 
         with torch.cuda.device(dev):
             return interpolate(points, values, sigma, H, W, radius_sigmas=radius_sigmas, mode=mode,
                                bin_px=bin_px, variant=variant, return_aux=return_aux, check=check,
-                               graph=graph, out=out)
+                               graph=graph, out=out, gather=gather)
     st = _lib.load().gmi_forward(points.data_ptr(), values.data_ptr(), N, C, H, W, ctypes.byref(p),
                                  out.data_ptr(), den.data_ptr() if den is not None else None,
                                  shift.data_ptr() if shift is not None else None, ws.data_ptr(),
@@ -560,8 +577,9 @@ class BatchPlan:
 
     def __init__(self, max_images: int, max_points: int, max_pixels: int, C: int = 3, *,
                  radius_sigmas: float = 6.0, mode="exact", variant: int = 0, bin_px: int = 0,
-                 check: bool = False):
+                 check: bool = False, gather=None):
         p = _lib.make_params(1.0, radius_sigmas, _mode(mode), _lib.FLAG_SYNC_CHECK if check else 0, bin_px, variant)
+        p.gather = _gather_code(gather)
         h = ctypes.c_void_p()
         _lib.check(_lib.load().gmi_batch_plan_create(int(max_images), int(max_points), int(max_pixels), int(C),
                                                      ctypes.byref(p), ctypes.byref(h)), "gmi_batch_plan_create")

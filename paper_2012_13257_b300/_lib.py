@@ -27,7 +27,8 @@ FLAG_SYNC_CHECK = 0x1
 FLAG_GRAPH = 0x2
 VARIANT_AUTO, VARIANT_MT4x4, VARIANT_MT4x8, VARIANT_MT2x4, VARIANT_MT4x2 = 0, 1, 2, 3, 4
 GATHER_AUTO, GATHER_STAGED, GATHER_DIRECT = 0, 1, 2
-# params.gather of every call this process makes (set through gmi.set_gather)
+# default params.gather of the calls this process makes (gmi.set_gather; interpolate and
+# BatchPlan also take a per-call choice)
 DEFAULT_GATHER = GATHER_AUTO
 STAGES = ("bin", "near", "far", "backward")
 NOALLOC_SCRATCH_BYTES = 32 << 20   # GMI_NOALLOC_SCRATCH_BYTES

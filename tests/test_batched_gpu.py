@@ -101,18 +101,28 @@ def test_uneven_clustered_batch_sampled(cuda_device):
 
 
 def test_autotuner_picks_the_fastest_measured_candidate(cuda_device, tmp_path):
-    """gmi_autotune times every (variant, bin edge) and returns the fastest;
-    the Python Autotuner records it for the problem's bucket."""
-    from paper_2012_13257_b300.autotune import Autotuner, DEFAULT_VARIANTS, bucket
+    """gmi_autotune times every (variant, bin edge), once per staging choice
+    (points per stage: the staged window or none); the Python Autotuner
+    records the fastest for the problem's bucket, and a forward with the
+    tuned choices matches the oracle."""
+    import torch
+    import paper_2012_13257_b300 as G
+    from paper_2012_13257_b300.autotune import Autotuner, DEFAULT_GATHERS, DEFAULT_VARIANTS, bucket
     im = wl.tiny_random(5, 6000, 120, 150, sigma=1.2)
     t = Autotuner(path=str(tmp_path / "tune.json"))
-    best, times = t.tune(to_dev(im.points, cuda_device), to_dev(im.values, cuda_device), im.sigma, im.H, im.W,
-                         bins=(0, 2, 4), reps=3)
-    assert len(times) == 3 * len(DEFAULT_VARIANTS) and all(v > 0 for v in times.values())
-    assert best["variant"] in DEFAULT_VARIANTS and best["bin_px"] in (0, 2, 4)
+    P, V = to_dev(im.points, cuda_device), to_dev(im.values, cuda_device)
+    best, times = t.tune(P, V, im.sigma, im.H, im.W, bins=(0, 2, 4), reps=3)
+    assert len(times) == 3 * len(DEFAULT_VARIANTS) * len(DEFAULT_GATHERS) and all(v > 0 for v in times.values())
+    assert {k.split("/")[2] for k in times} == set(DEFAULT_GATHERS)
+    assert best["variant"] in DEFAULT_VARIANTS and best["bin_px"] in (0, 2, 4) and best["gather"] in DEFAULT_GATHERS
     assert best["ms"] == min(times.values())
     assert t.lookup(im.sigma, im.N / float(im.H * im.W), 3) == best
     assert bucket(im.sigma, im.N / float(im.H * im.W), 3) in t.table[t.gpu_name()]
+    out = G.interpolate(P, V, im.sigma, im.H, im.W, variant=best["variant"], bin_px=best["bin_px"],
+                        gather=best["gather"], check=True)
+    torch.cuda.synchronize()
+    ref = oracle.forward(im.points, im.values, im.H, im.W, im.sigma)["image"]
+    assert np.abs(out.cpu().numpy().astype(np.float64) - ref).max() <= TOL_FWD
 
 
 @pytest.mark.parametrize("C,mode,variant", [(1, "exact", 1), (2, "exact", 3), (4, "exact", 2),
