@@ -33,12 +33,15 @@ def small_batch(seed=0, B=12):
     return out
 
 
+@pytest.mark.parametrize("gather", ["staged", "direct"])
 @pytest.mark.parametrize("use_graph", [False, True])
-def test_batch_matches_oracle_and_single(cuda_device, use_graph):
+def test_batch_matches_oracle_and_single(cuda_device, use_graph, gather):
+    """A batch against the oracle and against single-image calls, with each
+    staging choice the autotuner can pick (per plan and per call)."""
     import torch
     G = gmi()
     imgs = small_batch(1)
-    plan = G.BatchPlan(32, 20000, 200000, 3)
+    plan = G.BatchPlan(32, 20000, 200000, 3, gather=gather)
     outs = plan.forward(dev_images(imgs, cuda_device), use_graph=use_graph)
     torch.cuda.synchronize()
     for im, o in zip(imgs, outs):
@@ -46,7 +49,7 @@ def test_batch_matches_oracle_and_single(cuda_device, use_graph):
         ref = oracle.forward(im.points, im.values, im.H, im.W, im.sigma)["image"]
         assert np.abs(got - ref).max() <= TOL_FWD, (im.H, im.W, im.N)
         single = G.interpolate(to_dev(im.points, cuda_device), to_dev(im.values, cuda_device), im.sigma,
-                               im.H, im.W).cpu().numpy()
+                               im.H, im.W, gather=gather).cpu().numpy()
         assert np.abs(got - single).max() <= 1e-6
     plan.close()
 
